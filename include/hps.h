@@ -1,0 +1,178 @@
+/*
+ * hps.h -- C ABI of libhps.so: the HPS direct solver inside the implicit stages of an
+ * additive Runge-Kutta (ESDIRK + ERK) step, on one GB300 GPU (sm_103a).
+ *
+ * Method: Chen, Appelo, Babb, Martinsson, "Fast and high-order approximation of parabolic
+ * equations using hierarchical direct solvers and implicit Runge-Kutta methods".
+ * Problem (eq. ``general``):  u_t = L u + q + g(u) on a rectangle, u = f on its boundary,
+ *   L u = a11 u_xx + a22 u_yy + a1 u_x + a2 u_y + a0 u    (eq. ``operatorA`` with c12 = 0).
+ *
+ * Discretization (Sec. 2.1): n1 x n2 equal leaves (n1, n2 powers of two), p x p Chebyshev
+ * nodes per leaf, leaf corners dropped, shared edge nodes stored once:
+ *   N = (p-2)(p n1 n2 + n1 + n2) unknowns, m = p-2, N_int = n1 n2 m^2, N_bd = 2 m (n1 + n2).
+ * Global vector order (every array named "global" below uses it):
+ *   [0, N_int)        leaf interiors: leaf l = iy*n1 + ix, node (i, j) in 1..m (i along x)
+ *                     at l*m*m + (j-1)*m + (i-1);
+ *   then N_v = (n1+1) n2 m vertical-edge nodes: x-line L (0..n1), leaf row iy, node j:
+ *                     N_int + (L*n2 + iy)*m + (j-1);
+ *   then N_h = (n2+1) n1 m horizontal-edge nodes: y-line L (0..n2), leaf column ix, node i:
+ *                     N_int + N_v + (L*n1 + ix)*m + (i-1).
+ * A leaf's local node (i, j), 0 <= i, j < p, sits at
+ *   x = x0 + hx*(ix + (1 + xi_i)/2),  y = y0 + hy*(iy + (1 + xi_j)/2),  xi_k = -cos(k pi/(p-1)).
+ * "Interior order" = the first N_int entries.  "Boundary order" = the N_bd entries of the
+ * outer boundary in ascending global index (hps_boundary_index lists them).
+ *
+ * Ownership: every vector argument is caller-owned DEVICE memory unless marked "host";
+ * the handle owns its operators and work buffers (allocated by hps_build, released by
+ * hps_free).  All GPU work is enqueued on the given stream (NULL = legacy default stream);
+ * functions return after enqueueing.  A handle's work buffers are shared by its calls:
+ * calls on the same handle must be ordered on one stream.
+ * Errors: every int-returning function returns HPS_OK (0) or a negative HPS_E* code.
+ */
+#ifndef HPS_H
+#define HPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hps_handle hps_handle;
+typedef struct CUstream_st *hps_stream_t; /* identical to cudaStream_t */
+
+enum {
+  HPS_OK = 0,
+  HPS_EINVAL = -1,    /* bad argument: tree not a power of two, p out of [4, 32], NULL pointer ... */
+  HPS_ENOMEM = -2,    /* device allocation failed */
+  HPS_ESINGULAR = -3, /* zero or non-finite pivot in a Gauss-Jordan elimination of the build */
+  HPS_ETIMEOUT = -4,  /* a bounded device-side wait expired */
+  HPS_ECUDA = -5,     /* a CUDA runtime call or kernel launch failed */
+  HPS_EDT = -6        /* ark_step: gamma*dt differs from the gamma_dt the handle was built for */
+};
+
+/* Domain [x0,x1] x [y0,y1] cut into n1 x n2 equal leaves; n1, n2 powers of two, n1*n2 <= 65536,
+ * and every box boundary at most 24576 points (2 (n1 + n2)(p - 2) <= 24576).
+ * Sec. 2.1 halves the domain repeatedly; a box is cut across its longer side (in leaves),
+ * a tie is cut by a vertical line. */
+typedef struct hps_tree {
+  int n1, n2;
+  double x0, x1, y0, y1;
+} hps_tree;
+
+enum { HPS_COEF_CONST = 0, HPS_COEF_NODAL = 1 };
+
+/* Coefficients of L (eq. ``operatorA`` with c12 = 0, signs as in u_t = L u).
+ * CONST: the c_* scalars are used.  NODAL: a11..a0 are device arrays of N_int doubles in
+ * interior order (values at the interior nodes, the only rows where L is collocated);
+ * hps_build copies them. */
+typedef struct hps_coeffs {
+  int kind;
+  double c_a11, c_a22, c_a1, c_a2, c_a0;
+  const double *a11, *a22, *a1, *a2, *a0;
+} hps_coeffs;
+
+/* hps_build flags */
+enum {
+  HPS_FLAG_PER_NODE = 1 /* keep one operator per tree node even for CONST coefficients
+                           (default for CONST: one operator per tree level, shared) */
+};
+
+/* Sizes of the discretization (Sec. 2.1 point count).  Host outputs; any may be NULL. */
+int hps_sizes(const hps_tree *tree, int p, int64_t *N, int64_t *N_int, int64_t *N_bd);
+
+/* Coordinates of all N global points into host arrays x[N], y[N]. */
+int hps_coords(const hps_tree *tree, int p, double *x, double *y);
+
+/* Global indices of the N_bd outer-boundary points, ascending, into host idx[N_bd]. */
+int hps_boundary_index(const hps_tree *tree, int p, int64_t *idx);
+
+/* Device bytes a handle for this discretization holds (operators + work buffers), for
+ * admission control.  coeff_kind: HPS_COEF_CONST or HPS_COEF_NODAL. Returns 0 on bad input. */
+size_t hps_bytes(const hps_tree *tree, int p, int coeff_kind, int flags);
+
+/* Build the HPS solution operators of A = I - gamma_dt L (Sec. 2.1: leaf S = -A_ii^{-1} A_ib,
+ * T = D S (eq. ``leaf``); merges X = (T^a_33 - T^b_33)^{-1}, S^t = X[-T^a_31 | T^b_32],
+ * T^t = diag(T^a_11, T^b_22) + [T^a_13; T^b_23] S^t), in FP64 on the GPU, plus the operators
+ * of the identity on the same tree (the "explicit equation" of Sec. 3.1.1, used to close
+ * an ARK step).  gamma_dt >= 0.  Synchronizes `stream` before returning (the build is
+ * one-off).  On success *out receives a new handle. */
+int hps_build(const hps_tree *tree, int p, const hps_coeffs *coeffs, double gamma_dt, int flags,
+              hps_stream_t stream, hps_handle **out);
+
+/* One HPS solve (upward body-load sweep, then Alg. 1 downward sweep) of the collocation
+ * system of eq. ``sparse_A``: (I - gamma_dt L) u = rhs at interior points, flux continuity
+ * across shared edges, u = f on the outer boundary.
+ *   rhs: N_int (interior order);  f: N_bd (boundary order) or NULL for f = 0;
+ *   u:   N (global order), written completely.  rhs/f must not alias u. */
+int hps_solve(hps_handle *h, const double *rhs, const double *f, double *u, hps_stream_t stream);
+
+/* Nonlinear term presets g(u) (Sec. 1: at most first derivatives), evaluated at interior
+ * points; derivatives by leaf-local Chebyshev differentiation. */
+enum {
+  HPS_G_NONE = 0,
+  HPS_G_ALLEN_CAHN = 1, /* g = k0 (u - u^3) */
+  HPS_G_FISHER = 2,     /* g = k0 u (1 - u) */
+  HPS_G_BURGERS = 3     /* g = -u (k0 u_x + k1 u_y) */
+};
+
+/* Explicit terms of one ARK step.  Stage times t_j = t + c_j dt, j = 1..6 (hps_ark_abscissae).
+ *   q: device, 6 * N_int doubles, q(t_j) at interior points, stage-major; NULL means q = 0.
+ *   f: device, 6 * N_bd doubles, f(t_j) in boundary order, stage-major; NULL means f = 0.
+ *      Entry j = 1 is not read (the first stage is u^n itself); entry 6 (c_6 = 1) is also
+ *      the boundary value of u^{n+1}. */
+typedef struct hps_ark_terms {
+  const double *q;
+  const double *f;
+  int g_kind;
+  double g_param[2];
+} hps_ark_terms;
+
+/* Abscissae c_1..c_6 of ARK4(3)6L[2]SA (host output, 6 doubles); gamma = 1/4. */
+int hps_ark_abscissae(double *c);
+
+/* One ARK4(3)6L[2]SA step of eq. ``stage2`` in place on u (global order, N doubles):
+ * u_1 = u^n; for i = 2..6 one hps_solve of (I - dt gamma L) u_i = u^n + dt sum_j a_ij L u_j
+ * + dt sum_j ahat_ij (q_j + g_j) with u_i = f(t_i) on the boundary; L u^n by leaf-local
+ * differentiation, dt L u_j = (u_j - R_j)/gamma for j >= 2; then
+ * u^{n+1} = u^n + dt sum_j b_j L u_j + dt sum_j bhat_j (q_j + g_j) at interior points,
+ * f(t + dt) on the boundary and shared-edge values from the identity-operator solve.
+ * The handle must have been built with gamma_dt == dt/4 (else HPS_EDT).  No allocation,
+ * no host synchronization: the call can be captured in a CUDA graph. */
+int ark_step(hps_handle *h, double *u, double t, double dt, const hps_ark_terms *terms,
+             hps_stream_t stream);
+
+/* Kernels of the solve path, for launch counting and timing. */
+enum {
+  HPS_K_LEAF_UP = 0,     /* a1+a2: stage right-hand side, w = A_ii^{-1} R, h = D_bi w   */
+  HPS_K_MERGE_UP_W3 = 1, /* a3: w3 = X (h^b_3 - h^a_3)                                  */
+  HPS_K_MERGE_UP_H = 2,  /* a3: h^t = [h^a_1 ; h^b_2] + [T^a_13 ; T^b_23] w3              */
+  HPS_K_MERGE_DOWN = 3,  /* a4: u3 = S^t u_b + w3                                       */
+  HPS_K_LEAF_DOWN = 4,   /* a5: u_i = w + S u_b and the fused ARK stage epilogue          */
+  HPS_K_LEAF_EVAL = 5,   /* explicit first stage: dt L u^n, dt (q + g(u^n))               */
+  HPS_K_SET_BOUNDARY = 6 /* Dirichlet data onto the outer boundary                        */
+};
+
+/* Tracing (no effect on results).  Every launch of the solve path is counted per kernel;
+ * kernels whose bit (1 << HPS_K_*) is set in `mask` are also bracketed by CUDA events
+ * recorded on the launch stream.  hps_trace_enable resets all counters; mask 0 stops the
+ * event timing.  Do not enable event timing while capturing a CUDA graph. */
+int hps_trace_enable(hps_handle *h, unsigned mask);
+
+/* Counters of one kernel since the last hps_trace_enable: launches, launches timed and
+ * their summed device time in ms.  Synchronizes on the recorded events.  Host outputs,
+ * any may be NULL. */
+int hps_trace_read(hps_handle *h, int kernel, int64_t *launches, int64_t *timed, double *total_ms);
+
+/* Release the handle and all its device memory (synchronizes the device first). */
+void hps_free(hps_handle *h);
+
+/* Static description of an error code. */
+const char *hps_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HPS_H */

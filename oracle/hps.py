@@ -100,11 +100,18 @@ class HPS:
         for lev in self.levels:
             for nd in lev:
                 nd.bd = grid.box_boundary(nd.ix0, nd.iy0, nd.a, nd.c)
-        # leaves (eq. ``leaf``)
+        # leaves (eq. ``leaf``); with scalar coefficients every leaf has the same operators,
+        # so they are formed once and shared
+        scalar = all(np.ndim(coef.get(k, 0.0)) == 0 for k in COEF_NAMES)
+        shared_ops = None
         for lev in self.levels:
             for nd in lev:
                 if nd.is_leaf:
-                    ops = LeafOps(grid.p, grid.hx, grid.hy, slices[(nd.ix0, nd.iy0)], gamma_dt)
+                    if scalar and shared_ops is not None:
+                        ops = shared_ops
+                    else:
+                        ops = LeafOps(grid.p, grid.hx, grid.hy, slices[(nd.ix0, nd.iy0)], gamma_dt)
+                        shared_ops = ops if scalar else None
                     g = grid.local_to_global(nd.ix0, nd.iy0).reshape(-1)
                     assert np.array_equal(g[ops.B], nd.bd), "leaf edge order must match box order"
                     nd.ops = ops
@@ -125,31 +132,28 @@ class HPS:
         assert J3 == J3_b, "both children list the interface in the same order"
         ia3 = np.array([pos_a[g] for g in J3])
         ib3 = np.array([pos_b[g] for g in J3])
-        src = []  # parent boundary point -> (child, position in that child)
-        for g in nd.bd:
-            if g in pos_a:
-                src.append((0, pos_a[g]))
-            else:
-                src.append((1, pos_b[g]))
+        # parent boundary point -> (child, position in that child); J1 from alpha, J2 from beta
+        src_child = np.array([0 if g in pos_a else 1 for g in nd.bd])
+        src_pos = np.array([pos_a[g] if g in pos_a else pos_b[g] for g in nd.bd])
+        A1 = np.nonzero(src_child == 0)[0]   # parent positions of J1
+        B2 = np.nonzero(src_child == 1)[0]   # parent positions of J2
+        pa1, pb2 = src_pos[A1], src_pos[B2]
         nb, n3 = len(nd.bd), len(J3)
-        M = al.T[np.ix_(ia3, ia3)] - be.T[np.ix_(ib3, ib3)]
-        Bm = np.empty((n3, nb))
-        Tcat = np.empty((nb, n3))
-        Tdiag = np.zeros((nb, nb))
-        for k, (ch, pk) in enumerate(src):
-            if ch == 0:
-                Bm[:, k] = -al.T[ia3, pk]
-                Tcat[k, :] = al.T[pk, ia3]
-            else:
-                Bm[:, k] = be.T[ib3, pk]
-                Tcat[k, :] = be.T[pk, ib3]
-            for k2, (ch2, pk2) in enumerate(src):
-                if ch2 == ch:
-                    Tdiag[k, k2] = (al.T if ch == 0 else be.T)[pk, pk2]
+        M = al.T[np.ix_(ia3, ia3)] - be.T[np.ix_(ib3, ib3)]          # T^a_33 - T^b_33
+        Bm = np.empty((n3, nb))                                      # [-T^a_31 | T^b_32]
+        Bm[:, A1] = -al.T[np.ix_(ia3, pa1)]
+        Bm[:, B2] = be.T[np.ix_(ib3, pb2)]
+        Tcat = np.empty((nb, n3))                                    # [T^a_13 ; T^b_23]
+        Tcat[A1, :] = al.T[np.ix_(pa1, ia3)]
+        Tcat[B2, :] = be.T[np.ix_(pb2, ib3)]
+        Tdiag = np.zeros((nb, nb))                                   # diag(T^a_11, T^b_22)
+        Tdiag[np.ix_(A1, A1)] = al.T[np.ix_(pa1, pa1)]
+        Tdiag[np.ix_(B2, B2)] = be.T[np.ix_(pb2, pb2)]
         X = np.linalg.inv(M)
         S = X @ Bm
         nd.J3 = np.array(J3, dtype=np.int64)
-        nd.ia3, nd.ib3, nd.src = ia3, ib3, src
+        nd.ia3, nd.ib3 = ia3, ib3
+        nd.A1, nd.B2, nd.pa1, nd.pb2 = A1, B2, pa1, pb2
         nd.X, nd.S, nd.Tcat = X, S, Tcat
         nd.T = Tdiag + Tcat @ S
 
@@ -177,7 +181,9 @@ class HPS:
                     if jump is not None:
                         d = d + np.asarray(jump)[nd.J3]
                     nd.w3 = nd.X @ d
-                    hc = np.array([h[id(al) if ch == 0 else id(be)][pk] for ch, pk in nd.src])
+                    hc = np.empty(len(nd.bd))
+                    hc[nd.A1] = h[id(al)][nd.pa1]
+                    hc[nd.B2] = h[id(be)][nd.pb2]
                     h[id(nd)] = hc + nd.Tcat @ nd.w3
         # downward sweep (Alg. 1 with the particular parts added)
         if f_bd is not None:

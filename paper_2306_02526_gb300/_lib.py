@@ -1,0 +1,83 @@
+"""ctypes declarations of the C ABI in include/hps.h (argument marshalling only)."""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhps.so")
+
+c_double_p = ctypes.POINTER(ctypes.c_double)
+c_int64_p = ctypes.POINTER(ctypes.c_int64)
+
+HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ETIMEOUT, HPS_ECUDA, HPS_EDT = 0, -1, -2, -3, -4, -5, -6
+HPS_COEF_CONST, HPS_COEF_NODAL = 0, 1
+HPS_FLAG_PER_NODE = 1
+HPS_G_NONE, HPS_G_ALLEN_CAHN, HPS_G_FISHER, HPS_G_BURGERS = 0, 1, 2, 3
+KERNELS = ("leaf_up", "merge_up_w3", "merge_up_h", "merge_down", "leaf_down", "leaf_eval", "set_boundary")
+
+
+class hps_tree(ctypes.Structure):
+    _fields_ = [("n1", ctypes.c_int), ("n2", ctypes.c_int), ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("y0", ctypes.c_double), ("y1", ctypes.c_double)]
+
+
+class hps_coeffs(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("c_a11", ctypes.c_double), ("c_a22", ctypes.c_double),
+                ("c_a1", ctypes.c_double), ("c_a2", ctypes.c_double), ("c_a0", ctypes.c_double),
+                ("a11", ctypes.c_void_p), ("a22", ctypes.c_void_p), ("a1", ctypes.c_void_p),
+                ("a2", ctypes.c_void_p), ("a0", ctypes.c_void_p)]
+
+
+class hps_ark_terms(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_void_p), ("f", ctypes.c_void_p), ("g_kind", ctypes.c_int),
+                ("g_param", ctypes.c_double * 2)]
+
+
+# name -> (restype, argtypes); the list is also the set of exported symbols include/hps.h declares
+SIGNATURES = {
+    "hps_sizes": (ctypes.c_int, [ctypes.POINTER(hps_tree), ctypes.c_int, c_int64_p, c_int64_p, c_int64_p]),
+    "hps_coords": (ctypes.c_int, [ctypes.POINTER(hps_tree), ctypes.c_int, c_double_p, c_double_p]),
+    "hps_boundary_index": (ctypes.c_int, [ctypes.POINTER(hps_tree), ctypes.c_int, c_int64_p]),
+    "hps_bytes": (ctypes.c_size_t, [ctypes.POINTER(hps_tree), ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "hps_build": (ctypes.c_int, [ctypes.POINTER(hps_tree), ctypes.c_int, ctypes.POINTER(hps_coeffs), ctypes.c_double,
+                                 ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "hps_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p]),
+    "hps_ark_abscissae": (ctypes.c_int, [c_double_p]),
+    "ark_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                ctypes.POINTER(hps_ark_terms), ctypes.c_void_p]),
+    "hps_trace_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint]),
+    "hps_trace_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int64_p, c_int64_p,
+                                      ctypes.POINTER(ctypes.c_double)]),
+    "hps_free": (None, [ctypes.c_void_p]),
+    "hps_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libhps.so; raises if it has not been built (there is no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libhps.so is not built (run `python -m paper_2306_02526_gb300.build` "
+                               "or __graft_entry__.build()); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class HPSError(RuntimeError):
+    def __init__(self, code, what):
+        msg = lib().hps_strerror(code).decode()
+        super().__init__("%s failed: %s (%d)" % (what, msg, code))
+        self.code = code
+
+
+def check(code, what):
+    if code != HPS_OK:
+        raise HPSError(code, what)

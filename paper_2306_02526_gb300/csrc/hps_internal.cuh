@@ -1,0 +1,147 @@
+// Internal declarations shared by the translation units of libhps.so.
+// Layout conventions are those documented in include/hps.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "hps.h"
+
+namespace hps {
+
+constexpr int kMaxP = 32;          // Chebyshev points per leaf side
+constexpr int kMaxBd = 24576;      // largest box boundary (doubles staged in shared memory)
+constexpr int kCombo = 16;         // terms of a right-hand-side linear combination
+
+// Sizes of the global vector (include/hps.h ordering).
+struct GridDims {
+  int n1, n2, m, p;
+  int64_t N_int, N_v, N_h, N, N_bd;
+};
+
+__host__ __device__ inline int64_t vseg(const GridDims &g, int line, int iy, int j0) {
+  return g.N_int + ((int64_t)line * g.n2 + iy) * g.m + j0;
+}
+__host__ __device__ inline int64_t hseg(const GridDims &g, int line, int ix, int i0) {
+  return g.N_int + g.N_v + ((int64_t)line * g.n1 + ix) * g.m + i0;
+}
+
+// Global index of position `pos` of the boundary of the a x c box at leaf (ix0, iy0);
+// box order: south (ascending x), east (ascending y), north (ascending x), west (ascending y).
+__host__ __device__ inline int64_t box_bd(const GridDims &g, int ix0, int iy0, int a, int c, int pos) {
+  const int m = g.m, am = a * m, cm = c * m;
+  if (pos < am) return hseg(g, iy0, ix0 + pos / m, pos % m);
+  pos -= am;
+  if (pos < cm) return vseg(g, ix0 + a, iy0 + pos / m, pos % m);
+  pos -= cm;
+  if (pos < am) return hseg(g, iy0 + c, ix0 + pos / m, pos % m);
+  pos -= am;
+  return vseg(g, ix0, iy0 + pos / m, pos % m);
+}
+
+// Global index of position `pos` of the interface a node's split creates.
+__host__ __device__ inline int64_t iface_bd(const GridDims &g, int ix0, int iy0, int a, int c, int split, int pos) {
+  const int m = g.m;
+  if (split == 0) return vseg(g, ix0 + a / 2, iy0 + pos / m, pos % m);
+  return hseg(g, iy0 + c / 2, ix0 + pos / m, pos % m);
+}
+
+// One level of the uniform binary tree (all boxes on a level have the same shape).
+struct Level {
+  int nodes = 0, a = 0, c = 0;
+  int split = -1;     // 0: vertical cut (x), 1: horizontal cut (y), -1: leaf level
+  int nb = 0;         // boundary points of a box on this level: 2(a+c)m
+  int n3 = 0;         // interface points of the cut (merge levels)
+  int nbc = 0;        // boundary points of a child box
+  int j3a = 0, j3b = 0;  // offset of the interface in the alpha / beta child boundary
+  int *d_origin = nullptr;  // nodes x (ix0, iy0)
+  int *d_hsrc = nullptr;    // nb: parent boundary position -> child*nbc + position in child
+  std::vector<int> origin, hsrc;
+};
+
+// Merge operators of one level, FP64, row-major, per node (stride) or shared (stride 0).
+struct MergeOps {
+  double *X = nullptr, *S = nullptr, *Tcat = nullptr;
+  int ldX = 0, ldS = 0, ldT = 0;
+  int64_t strX = 0, strS = 0, strT = 0;
+};
+
+struct OpSet {
+  bool identity = false;
+  double *Ainv = nullptr, *Sleaf = nullptr;
+  int ldA = 0, ldSl = 0;
+  int64_t strA = 0, strSl = 0;
+  std::vector<MergeOps> merge;  // index = level (0 .. L-1)
+};
+
+// Kernel slots for launch counting and optional CUDA-event timing (hps_trace_*).
+enum Slot { kLeafUp = 0, kMergeUpW3, kMergeUpH, kMergeDown, kLeafDown, kLeafEval, kSetBoundary, kNumSlots };
+
+struct Trace {
+  int64_t launches[kNumSlots] = {};
+  int64_t timed[kNumSlots] = {};
+  double ms[kNumSlots] = {};
+  unsigned mask = 0;
+  std::vector<cudaEvent_t> pool;   // pairs (start, end)
+  std::vector<int> pair_slot;
+  size_t used = 0;                 // pairs in flight
+  int open_slot = -1;
+  void begin(int slot, cudaStream_t st);
+  void end(int slot, cudaStream_t st);
+  void drain();                    // synchronizes the recorded events, accumulates ms
+  void release();
+};
+
+struct Combo {
+  const double *ptr[kCombo];
+  double coef[kCombo];
+  int n;
+};
+
+}  // namespace hps
+
+struct hps_handle {
+  hps_tree tree;
+  hps::GridDims g;
+  int p, m, q, b, L;
+  double hx, hy, gamma_dt;
+  bool shared;
+  int coef_kind;
+  double cst[5];
+  double *d_coef = nullptr;   // 5 x N_int (NODAL)
+  double *d_D = nullptr;      // D1x, D1y, Dxx, Dyy: 4 p*p doubles, row-major
+  std::vector<hps::Level> lev;  // 0 (root) .. L (leaves)
+  hps::OpSet impl, ident;
+  // work buffers
+  double *ustage = nullptr, *R = nullptr, *KL = nullptr, *KE = nullptr, *wleaf = nullptr;
+  std::vector<double *> h;    // per level: nodes x nb
+  std::vector<double *> w3;   // per merge level: nodes x n3
+  std::vector<void *> allocs;
+  hps::Trace trace;
+};
+
+namespace hps {
+
+// ---- build (build.cu) --------------------------------------------------------------
+int build_operators(hps_handle *H, OpSet &ops, double gamma_dt, bool identity, cudaStream_t st);
+
+// ---- solve (sweep.cu) ----------------------------------------------------------------
+struct Epilogue {          // fused ARK stage epilogue at the leaves (a5)
+  double *KL = nullptr;    // dt L u_i = (u_i - R_i) / gamma
+  double *KE = nullptr;    // dt (q_i + g(u_i))
+  const double *Rsaved = nullptr;
+  const double *q = nullptr;
+  double inv_gamma = 0.0, dt = 0.0;
+  int g_kind = 0;
+  double gp0 = 0.0, gp1 = 0.0;
+};
+
+int sweep(hps_handle *H, const OpSet &ops, const Combo &rhs, double *Rsave, double *gvec,
+          double *out_interior, const Epilogue *ep, cudaStream_t st);
+int set_boundary(hps_handle *H, double *gvec, const double *f, cudaStream_t st);
+int leaf_eval(hps_handle *H, const double *u, double *KL, double *KE, const double *q, double dt,
+              int g_kind, double gp0, double gp1, cudaStream_t st);
+
+}  // namespace hps

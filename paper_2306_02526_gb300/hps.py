@@ -1,0 +1,164 @@
+"""Python binding of libhps.so: the names of include/hps.h over torch device tensors.
+
+PyTorch provides device memory and the current CUDA stream; every step of the solve runs
+in the library's CUDA kernels.  Vectors use the library's global ordering (include/hps.h).
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import check, lib
+
+G_KINDS = {None: _lib.HPS_G_NONE, "none": _lib.HPS_G_NONE, "allen_cahn": _lib.HPS_G_ALLEN_CAHN,
+           "fisher": _lib.HPS_G_FISHER, "burgers": _lib.HPS_G_BURGERS}
+COEF_NAMES = ("a11", "a22", "a1", "a2", "a0")
+
+
+def _tree(n1, n2, x0=0.0, x1=1.0, y0=0.0, y1=1.0):
+    return _lib.hps_tree(int(n1), int(n2), float(x0), float(x1), float(y0), float(y1))
+
+
+class Tree:
+    """n1 x n2 equal leaves on [x0, x1] x [y0, y1] (n1, n2 powers of two)."""
+
+    def __init__(self, n1, n2, x0=0.0, x1=1.0, y0=0.0, y1=1.0):
+        self.n1, self.n2, self.x0, self.x1, self.y0, self.y1 = int(n1), int(n2), x0, x1, y0, y1
+        self.c = _tree(n1, n2, x0, x1, y0, y1)
+
+
+def hps_sizes(tree: Tree, p):
+    N, Ni, Nb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    check(lib().hps_sizes(ctypes.byref(tree.c), int(p), ctypes.byref(N), ctypes.byref(Ni), ctypes.byref(Nb)),
+          "hps_sizes")
+    return N.value, Ni.value, Nb.value
+
+
+def hps_coords(tree: Tree, p):
+    N, _, _ = hps_sizes(tree, p)
+    x = np.empty(N)
+    y = np.empty(N)
+    check(lib().hps_coords(ctypes.byref(tree.c), int(p), x.ctypes.data_as(_lib.c_double_p),
+                           y.ctypes.data_as(_lib.c_double_p)), "hps_coords")
+    return x, y
+
+
+def hps_boundary_index(tree: Tree, p):
+    _, _, Nb = hps_sizes(tree, p)
+    idx = np.empty(Nb, dtype=np.int64)
+    check(lib().hps_boundary_index(ctypes.byref(tree.c), int(p), idx.ctypes.data_as(_lib.c_int64_p)),
+          "hps_boundary_index")
+    return idx
+
+
+def hps_bytes(tree: Tree, p, nodal=False, per_node=False):
+    return int(lib().hps_bytes(ctypes.byref(tree.c), int(p), _lib.HPS_COEF_NODAL if nodal else _lib.HPS_COEF_CONST,
+                               _lib.HPS_FLAG_PER_NODE if per_node else 0))
+
+
+def hps_ark_abscissae():
+    c = (ctypes.c_double * 6)()
+    check(lib().hps_ark_abscissae(c), "hps_ark_abscissae")
+    return np.array(list(c))
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t, n, name):
+    import torch
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("%s must be a contiguous float64 CUDA tensor" % name)
+    if t.numel() != n:
+        raise ValueError("%s has %d entries, expected %d" % (name, t.numel(), n))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class HPSSolver:
+    """A built handle: the HPS operators of I - gamma_dt L (plus the identity set).
+
+    coef: dict with a11, a22, a1, a2, a0; all Python scalars -> constant coefficients,
+    otherwise float64 CUDA tensors of N_int values (interior order; scalars are broadcast).
+    """
+
+    def __init__(self, tree: Tree, p, coef, gamma_dt, per_node=False, stream=None):
+        import torch
+        self.tree, self.p, self.gamma_dt = tree, int(p), float(gamma_dt)
+        self.N, self.N_int, self.N_bd = hps_sizes(tree, p)
+        nodal = any(isinstance(coef.get(k, 0.0), torch.Tensor) for k in COEF_NAMES)
+        c = _lib.hps_coeffs()
+        keep = []
+        if nodal:
+            c.kind = _lib.HPS_COEF_NODAL
+            for k in COEF_NAMES:
+                v = coef.get(k, 0.0)
+                if not isinstance(v, torch.Tensor):
+                    v = torch.full((self.N_int,), float(v), dtype=torch.float64, device="cuda")
+                v = v.to(device="cuda", dtype=torch.float64).contiguous()
+                keep.append(v)
+                setattr(c, k, _dptr(v, self.N_int, k))
+        else:
+            c.kind = _lib.HPS_COEF_CONST
+            for k in COEF_NAMES:
+                setattr(c, "c_" + k, float(coef.get(k, 0.0)))
+        self.nodal = nodal
+        h = ctypes.c_void_p()
+        check(lib().hps_build(ctypes.byref(tree.c), self.p, ctypes.byref(c), self.gamma_dt,
+                              _lib.HPS_FLAG_PER_NODE if per_node else 0, _stream_ptr(stream), ctypes.byref(h)),
+              "hps_build")
+        self._h = h
+        del keep
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hps_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def trace_enable(self, kernels=()):
+        """Reset the per-kernel counters; time the named kernels (see _lib.KERNELS) with CUDA events."""
+        mask = 0
+        for k in kernels:
+            mask |= 1 << _lib.KERNELS.index(k)
+        check(lib().hps_trace_enable(self._h, mask), "hps_trace_enable")
+
+    def trace_read(self):
+        """{kernel: (launches, launches timed, total ms)} since the last trace_enable."""
+        out = {}
+        for i, name in enumerate(_lib.KERNELS):
+            n, nt, ms = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+            check(lib().hps_trace_read(self._h, i, ctypes.byref(n), ctypes.byref(nt), ctypes.byref(ms)),
+                  "hps_trace_read")
+            out[name] = (n.value, nt.value, ms.value)
+        return out
+
+    def solve(self, rhs, f=None, u=None, stream=None):
+        """u (length N) solving (I - gamma_dt L) u = rhs, u = f on the boundary (hps_solve)."""
+        import torch
+        if u is None:
+            u = torch.empty(self.N, dtype=torch.float64, device="cuda")
+        check(lib().hps_solve(self._h, _dptr(rhs, self.N_int, "rhs"), _dptr(f, self.N_bd, "f"),
+                              _dptr(u, self.N, "u"), _stream_ptr(stream)), "hps_solve")
+        return u
+
+    def ark_step(self, u, t, dt, q=None, f=None, g=None, g_param=(1.0, 1.0), stream=None):
+        """One ARK4(3)6L[2]SA step in place on u (ark_step).  q: (6, N_int) stage sources or
+        None; f: (6, N_bd) stage boundary data or None; g: None, 'allen_cahn', 'fisher', 'burgers'."""
+        terms = _lib.hps_ark_terms()
+        terms.q = _dptr(q, 6 * self.N_int, "q")
+        terms.f = _dptr(f, 6 * self.N_bd, "f")
+        terms.g_kind = G_KINDS[g]
+        terms.g_param[0], terms.g_param[1] = float(g_param[0]), float(g_param[1])
+        check(lib().ark_step(self._h, _dptr(u, self.N, "u"), float(t), float(dt), ctypes.byref(terms),
+                             _stream_ptr(stream)), "ark_step")
+        return u
