@@ -49,7 +49,8 @@ enum {
   HPS_ESINGULAR = -3, /* zero or non-finite pivot in a Gauss-Jordan elimination of the build */
   HPS_ETIMEOUT = -4,  /* a bounded device-side wait expired */
   HPS_ECUDA = -5,     /* a CUDA runtime call or kernel launch failed */
-  HPS_EDT = -6        /* ark_step: gamma*dt differs from the gamma_dt the handle was built for */
+  HPS_EDT = -6,       /* ark_step: gamma*dt differs from the gamma_dt the handle was built for */
+  HPS_ESCRATCH = -7   /* hps_solve_static: the problem's work vectors exceed the static array */
 };
 
 /* Domain [x0,x1] x [y0,y1] cut into n1 x n2 equal leaves; n1, n2 powers of two, n1*n2 <= 65536,
@@ -107,6 +108,23 @@ int hps_build(const hps_tree *tree, int p, const hps_coeffs *coeffs, double gamm
  *   rhs: N_int (interior order);  f: N_bd (boundary order) or NULL for f = 0;
  *   u:   N (global order), written completely.  rhs/f must not alias u. */
 int hps_solve(hps_handle *h, const double *rhs, const double *f, double *u, hps_stream_t stream);
+
+/* hps_solve without device allocation, for callers that cannot call cudaMalloc when they
+ * solve: a fixed memory budget set at start-up, a real-time loop, or an allocator that is
+ * unavailable on the solving thread.  (The paper has no counterpart; this is a library
+ * service.)  Same arguments, same kernels and same result as hps_solve; the per-call work
+ * vectors (leaf particular solutions, fluxes, interface corrections) are placed in one
+ * static device array of 2,097,152 doubles (16 MiB) compiled into libhps.so, which every
+ * GPU that loads the library holds until the process exits.  The operators still come from
+ * the handle.  Problems whose work vectors need more than that array -- N_int plus the
+ * per-level flux and interface vectors, each rounded up to 256 bytes -- are rejected with
+ * HPS_ESCRATCH (a 64 x 64 leaf grid with p = 16 fits; 128 x 128 with p = 16 does not).
+ * The first call on a device looks up the array's device address with the device current
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls share
+ * the one array and it keeps the last call's contents (every entry a call reads it writes
+ * first, so nothing needs clearing): calls that overlap on the GPU -- on different streams
+ * or different handles -- race and must be serialized by the caller. */
+int hps_solve_static(hps_handle *h, const double *rhs, const double *f, double *u, hps_stream_t stream);
 
 /* Nonlinear term presets g(u) (Sec. 1: at most first derivatives), evaluated at interior
  * points; derivatives by leaf-local Chebyshev differentiation. */

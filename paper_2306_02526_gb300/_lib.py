@@ -8,7 +8,7 @@ LIB_PATH = os.path.join(_HERE, "libhps.so")
 c_double_p = ctypes.POINTER(ctypes.c_double)
 c_int64_p = ctypes.POINTER(ctypes.c_int64)
 
-HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ETIMEOUT, HPS_ECUDA, HPS_EDT = 0, -1, -2, -3, -4, -5, -6
+HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ETIMEOUT, HPS_ECUDA, HPS_EDT, HPS_ESCRATCH = 0, -1, -2, -3, -4, -5, -6, -7
 HPS_COEF_CONST, HPS_COEF_NODAL = 0, 1
 HPS_FLAG_PER_NODE = 1
 HPS_G_NONE, HPS_G_ALLEN_CAHN, HPS_G_FISHER, HPS_G_BURGERS = 0, 1, 2, 3
@@ -42,6 +42,8 @@ SIGNATURES = {
                                  ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "hps_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_void_p]),
+    "hps_solve_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
     "hps_ark_abscissae": (ctypes.c_int, [c_double_p]),
     "ark_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                 ctypes.POINTER(hps_ark_terms), ctypes.c_void_p]),

@@ -459,6 +459,7 @@ const char *hps_strerror(int code) {
     case HPS_ETIMEOUT: return "bounded device wait expired";
     case HPS_ECUDA: return "CUDA error";
     case HPS_EDT: return "gamma*dt differs from the value the handle was built for";
+    case HPS_ESCRATCH: return "problem too large for the static work array of hps_solve_static";
     default: return "unknown error";
   }
 }
