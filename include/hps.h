@@ -113,11 +113,13 @@ int hps_solve(hps_handle *h, const double *rhs, const double *f, double *u, hps_
  * solve: a fixed memory budget set at start-up, a real-time loop, or an allocator that is
  * unavailable on the solving thread.  (The paper has no counterpart; this is a library
  * service.)  Same arguments, same kernels and same result as hps_solve; the per-call work
- * vectors (leaf particular solutions, fluxes, interface corrections) are placed in one
+ * vectors (leaf particular solutions, fluxes, interface corrections, split-column partial
+ * sums of the top tree levels) are placed in one
  * static device array of 2,097,152 doubles (16 MiB) compiled into libhps.so, which every
  * GPU that loads the library holds until the process exits.  The operators still come from
  * the handle.  Problems whose work vectors need more than that array -- N_int plus the
- * per-level flux and interface vectors, each rounded up to 256 bytes -- are rejected with
+ * per-level flux and interface vectors and the partial sums, each rounded up to 256
+ * bytes -- are rejected with
  * HPS_ESCRATCH (a 64 x 64 leaf grid with p = 16 fits; 128 x 128 with p = 16 does not).
  * The first call on a device looks up the array's device address with the device current
  * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls share
@@ -161,6 +163,16 @@ int hps_ark_abscissae(double *c);
 int ark_step(hps_handle *h, double *u, double t, double dt, const hps_ark_terms *terms,
              hps_stream_t stream);
 
+/* Graph replay.  With enable != 0, ark_step and hps_solve record their kernel sequence
+ * (about 380 launches per ARK step at 64 x 64 leaves) into a CUDA graph and replay it, so
+ * the launch cost is paid once: the first call with a given set of pointers and arguments
+ * (u, q, f, g, dt for ark_step; rhs, f, u for hps_solve) runs eagerly, the second records
+ * the graph on an internal stream and replays it on the caller's stream, later equal calls
+ * only replay; any change of those arguments starts over.  t is not part of the key (it
+ * enters only through the q and f arrays).  Results are identical to eager calls.  Calls
+ * made while the caller's stream is itself being captured always run eagerly.  Default: off. */
+int hps_set_graph(hps_handle *h, int enable);
+
 /* Kernels of the solve path, for launch counting and timing. */
 enum {
   HPS_K_LEAF_UP = 0,     /* a1+a2: stage right-hand side, w = A_ii^{-1} R, h = D_bi w   */
@@ -175,7 +187,9 @@ enum {
 /* Tracing (no effect on results).  Every launch of the solve path is counted per kernel;
  * kernels whose bit (1 << HPS_K_*) is set in `mask` are also bracketed by CUDA events
  * recorded on the launch stream.  hps_trace_enable resets all counters; mask 0 stops the
- * event timing.  Do not enable event timing while capturing a CUDA graph. */
+ * event timing.  In graph mode (hps_set_graph) the events are part of the recorded graph
+ * and each replay's times are read before the next replay, which then waits for the
+ * previous one to finish.  Do not enable event timing while capturing a CUDA graph yourself. */
 int hps_trace_enable(hps_handle *h, unsigned mask);
 
 /* Counters of one kernel since the last hps_trace_enable: launches, launches timed and

@@ -47,6 +47,7 @@ SIGNATURES = {
     "hps_ark_abscissae": (ctypes.c_int, [c_double_p]),
     "ark_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                 ctypes.POINTER(hps_ark_terms), ctypes.c_void_p]),
+    "hps_set_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "hps_trace_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint]),
     "hps_trace_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int64_p, c_int64_p,
                                       ctypes.POINTER(ctypes.c_double)]),

@@ -130,11 +130,11 @@ size_t opset_bytes(const std::vector<Level> &lev, int q, int b, bool shared, boo
   auto pad = [](int n) { return (size_t)((n + 1) & ~1); };
   size_t s = 0;
   const int L = (int)lev.size() - 1;
-  if (!identity) s += (shared ? 1 : lev[L].nodes) * (size_t)q * (pad(q) + pad(b));
+  if (!identity) s += (shared ? 1 : lev[L].nodes) * (size_t)(q + b) * pad(q);
   for (int l = 0; l < L; ++l) {
     const size_t nops = shared ? 1 : lev[l].nodes;
-    s += nops * ((size_t)lev[l].n3 * pad(lev[l].n3) + (size_t)lev[l].n3 * pad(lev[l].nb) +
-                 (l > 0 ? (size_t)lev[l].nb * pad(lev[l].n3) : 0));
+    s += nops * ((size_t)lev[l].n3 * pad(lev[l].n3) + (size_t)lev[l].nb * pad(lev[l].n3) +
+                 (l > 0 ? (size_t)lev[l].n3 * pad(lev[l].nb) : 0));
   }
   return s * sizeof(double);
 }
@@ -268,6 +268,9 @@ void hps_free(hps_handle *H) {
   if (!H) return;
   cudaDeviceSynchronize();
   H->trace.release();
+  H->g_ark.destroy();
+  H->g_solve.destroy();
+  if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
   for (void *p : H->allocs) cudaFree(p);
   delete H;
 }
@@ -308,6 +311,12 @@ int hps_build(const hps_tree *tree, int p, const hps_coeffs *coeffs, double gamm
     return fail(HPS_EINVAL);
   }
   H->L = (int)H->lev.size() - 1;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&H->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return fail(HPS_ECUDA);
+  }
   for (const Level &lv : H->lev)
     if (lv.nb > hps::kMaxBd || lv.n3 > hps::kMaxBd) return fail(HPS_EINVAL);
   // tree tables
@@ -364,34 +373,89 @@ int hps_build(const hps_tree *tree, int p, const hps_coeffs *coeffs, double gamm
     if (dalloc(H, &H->h[l], (size_t)lv.nodes * lv.nb)) return fail(HPS_ENOMEM);
     if (l < H->L && dalloc(H, &H->w3[l], (size_t)lv.nodes * lv.n3)) return fail(HPS_ENOMEM);
   }
+  H->partial_len = hps::partial_doubles(H);
+  if (H->partial_len && dalloc(H, &H->partial, H->partial_len)) return fail(HPS_ENOMEM);
   cudaMemsetAsync(H->ustage, 0, g.N * sizeof(double), st);
   if (cudaStreamSynchronize(st) != cudaSuccess) return fail(HPS_ECUDA);
   *out = H;
   return HPS_OK;
 }
 
-int hps_solve(hps_handle *H, const double *rhs, const double *f, double *u, hps_stream_t stream) {
-  if (!H || !rhs || !u) return HPS_EINVAL;
-  cudaStream_t st = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+
+uint64_t bits(double v) {
+  uint64_t b;
+  std::memcpy(&b, &v, sizeof b);
+  return b;
+}
+
+int graph_launch(hps_handle *H, hps::GraphEntry &E, cudaStream_t st) {
+  hps::drain_graph(H, E);  // the graph's timing events are reused by every replay
+  if (cudaGraphLaunch(E.exec, st) != cudaSuccess) return HPS_ECUDA;
+  for (int s = 0; s < hps::kNumSlots; ++s) H->trace.launches[s] += E.launches[s];
+  E.pending = E.nev > 0;
+  return HPS_OK;
+}
+
+// Run `enqueue` eagerly, or replay / record it as a CUDA graph (hps_set_graph).  The first
+// call with a key runs eagerly (kernels get loaded, attributes set); the second records the
+// sequence on an internal stream and replays it on `st`; later equal calls only replay.
+template <class F>
+int run_graphed(hps_handle *H, hps::GraphEntry &E, const uint64_t (&key)[hps::GraphEntry::kKey], F enqueue,
+                cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (!H->graph_mode || cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+    return enqueue(st);
+  const bool same = std::memcmp(E.key, key, sizeof(E.key)) == 0;
+  if (E.valid && same) return graph_launch(H, E, st);
+  if (!(E.seen && same)) {
+    hps::drain_graph(H, E);
+    E.destroy();
+    std::memcpy(E.key, key, sizeof(E.key));
+    E.seen = true;
+    return enqueue(st);
+  }
+  if (!H->cap_stream && cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return HPS_ECUDA;
+  if (H->trace.mask && E.ev.empty()) {
+    E.ev.resize(2 * hps::GraphEntry::kEventPairs);
+    for (auto &ev : E.ev) cudaEventCreate(&ev);
+    E.ev_slot.assign(hps::GraphEntry::kEventPairs, -1);
+  }
+  for (auto &n : E.launches) n = 0;
+  E.nev = 0;
+  H->trace.capturing = &E;
+  cudaGraph_t g = nullptr;
+  int e = HPS_OK;
+  if (cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) e = HPS_ECUDA;
+  if (e == HPS_OK) {
+    e = enqueue(H->cap_stream);
+    if (cudaStreamEndCapture(H->cap_stream, &g) != cudaSuccess && e == HPS_OK) e = HPS_ECUDA;
+  }
+  H->trace.capturing = nullptr;
+  if (e == HPS_OK && cudaGraphInstantiate(&E.exec, g, 0) != cudaSuccess) e = HPS_ECUDA;
+  if (g) cudaGraphDestroy(g);
+  if (e != HPS_OK) {
+    E.destroy();
+    cudaGetLastError();
+    return e;
+  }
+  E.valid = true;
+  return graph_launch(H, E, st);
+}
+
+int solve_enqueue(hps_handle *H, const double *rhs, const double *f, double *u, cudaStream_t st) {
   if (int e = hps::set_boundary(H, u, f, st)) return e;
   hps::Combo c{};
   add_term(c, rhs, 1.0);
   return hps::sweep(H, H->impl, c, nullptr, u, u, nullptr, st);
 }
 
-int hps_ark_abscissae(double *c) {
-  if (!c) return HPS_EINVAL;
-  for (int i = 0; i < 6; ++i) c[i] = tableau().c[i];
-  return HPS_OK;
-}
-
-int ark_step(hps_handle *H, double *u, double t, double dt, const hps_ark_terms *terms, hps_stream_t stream) {
-  if (!H || !u || !(dt > 0.0) || !std::isfinite(t)) return HPS_EINVAL;
-  if (std::fabs(0.25 * dt - H->gamma_dt) > 1e-12 * H->gamma_dt) return HPS_EDT;
-  const int gk = terms ? terms->g_kind : HPS_G_NONE;
-  if (gk < HPS_G_NONE || gk > HPS_G_BURGERS) return HPS_EINVAL;
-  cudaStream_t st = (cudaStream_t)stream;
+int ark_enqueue(hps_handle *H, double *u, double dt, const hps_ark_terms *terms, cudaStream_t st) {
   const Tableau &tb = tableau();
+  const int gk = terms ? terms->g_kind : HPS_G_NONE;
   const int64_t ni = H->g.N_int, nbd = H->g.N_bd;
   const double *q = terms ? terms->q : nullptr;
   const double *f = terms ? terms->f : nullptr;
@@ -429,9 +493,55 @@ int ark_step(hps_handle *H, double *u, double t, double dt, const hps_ark_terms 
   return hps::sweep(H, H->ident, c, nullptr, u, u, nullptr, st);
 }
 
+}  // namespace
+
+extern "C" {
+
+int hps_solve(hps_handle *H, const double *rhs, const double *f, double *u, hps_stream_t stream) {
+  if (!H || !rhs || !u) return HPS_EINVAL;
+  const uint64_t key[hps::GraphEntry::kKey] = {(uint64_t)rhs, (uint64_t)f, (uint64_t)u, 0, 0, 0, 0, 0};
+  return run_graphed(H, H->g_solve, key, [&](cudaStream_t s) { return solve_enqueue(H, rhs, f, u, s); },
+                     (cudaStream_t)stream);
+}
+
+int hps_set_graph(hps_handle *H, int enable) {
+  if (!H) return HPS_EINVAL;
+  cudaDeviceSynchronize();
+  hps::drain_graph(H, H->g_ark);
+  hps::drain_graph(H, H->g_solve);
+  H->g_ark.destroy();
+  H->g_solve.destroy();
+  H->graph_mode = enable != 0;
+  return HPS_OK;
+}
+
+int hps_ark_abscissae(double *c) {
+  if (!c) return HPS_EINVAL;
+  for (int i = 0; i < 6; ++i) c[i] = tableau().c[i];
+  return HPS_OK;
+}
+
+int ark_step(hps_handle *H, double *u, double t, double dt, const hps_ark_terms *terms, hps_stream_t stream) {
+  if (!H || !u || !(dt > 0.0) || !std::isfinite(t)) return HPS_EINVAL;
+  if (std::fabs(0.25 * dt - H->gamma_dt) > 1e-12 * H->gamma_dt) return HPS_EDT;
+  const int gk = terms ? terms->g_kind : HPS_G_NONE;
+  if (gk < HPS_G_NONE || gk > HPS_G_BURGERS) return HPS_EINVAL;
+  const uint64_t key[hps::GraphEntry::kKey] = {
+      (uint64_t)u, (uint64_t)(terms ? terms->q : nullptr), (uint64_t)(terms ? terms->f : nullptr), (uint64_t)gk,
+      bits(terms ? terms->g_param[0] : 0.0), bits(terms ? terms->g_param[1] : 0.0), bits(dt), 1};
+  return run_graphed(H, H->g_ark, key, [&](cudaStream_t s) { return ark_enqueue(H, u, dt, terms, s); },
+                     (cudaStream_t)stream);
+}
+
 int hps_trace_enable(hps_handle *H, unsigned mask) {
   if (!H) return HPS_EINVAL;
   H->trace.drain();
+  hps::drain_graph(H, H->g_ark);
+  hps::drain_graph(H, H->g_solve);
+  if (mask != H->trace.mask) {  // recorded graphs carry the old timing events
+    H->g_ark.destroy();
+    H->g_solve.destroy();
+  }
   H->trace.mask = mask;
   for (int i = 0; i < hps::kNumSlots; ++i) {
     H->trace.launches[i] = 0;
@@ -444,6 +554,8 @@ int hps_trace_enable(hps_handle *H, unsigned mask) {
 int hps_trace_read(hps_handle *H, int kernel, int64_t *launches, int64_t *timed, double *total_ms) {
   if (!H || kernel < 0 || kernel >= hps::kNumSlots) return HPS_EINVAL;
   H->trace.drain();
+  hps::drain_graph(H, H->g_ark);
+  hps::drain_graph(H, H->g_solve);
   if (launches) *launches = H->trace.launches[kernel];
   if (timed) *timed = H->trace.timed[kernel];
   if (total_ms) *total_ms = H->trace.ms[kernel];

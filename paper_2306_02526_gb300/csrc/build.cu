@@ -151,13 +151,14 @@ __global__ void k_leaf_extract(int p, int k0, const double *__restrict__ G, int 
   const double *Gk = G + (int64_t)blockIdx.x * q * ldG;
   double *Ak = Ainv + k * strA;
   double *Sk = Sl + k * strS;
+  // stored transposed (column c of the operator is a contiguous run of its q rows)
   for (int idx = threadIdx.x; idx < q * q; idx += blockDim.x) {
-    const int r = idx / q, c = idx % q;
-    Ak[(int64_t)r * ldA + c] = Gk[(int64_t)r * ldG + q + c];
+    const int c = idx / q, r = idx % q;
+    Ak[(int64_t)c * ldA + r] = Gk[(int64_t)r * ldG + q + c];
   }
   for (int idx = threadIdx.x; idx < q * b; idx += blockDim.x) {
-    const int r = idx / b, c = idx % b;
-    Sk[(int64_t)r * ldS + c] = -Gk[(int64_t)r * ldG + 2 * q + c];
+    const int c = idx / q, r = idx % q;
+    Sk[(int64_t)c * ldS + r] = -Gk[(int64_t)r * ldG + 2 * q + c];
   }
   __syncthreads();
   const double *D1x = Dg, *D1y = Dg + p * p;
@@ -169,13 +170,13 @@ __global__ void k_leaf_extract(int p, int k0, const double *__restrict__ G, int 
     // D_bi S: flux at edge e of the interior field S[:, e2]
     if (side == 0 || side == 2) {
       const double *d = D1y + (side == 0 ? 0 : (p - 1) * p);
-      for (int jj = 1; jj <= m; ++jj) s = fma(d[jj], Sk[(int64_t)((jj - 1) * m + t) * ldS + e2], s);
+      for (int jj = 1; jj <= m; ++jj) s = fma(d[jj], Sk[(int64_t)e2 * ldS + (jj - 1) * m + t], s);
       // D_bb: the same column's two end points (south = t, north = 2m + t)
       if (e2 == t) s += d[0];
       if (e2 == 2 * m + t) s += d[p - 1];
     } else {
       const double *d = D1x + (side == 1 ? (p - 1) * p : 0);
-      for (int ii = 1; ii <= m; ++ii) s = fma(d[ii], Sk[(int64_t)(t * m + ii - 1) * ldS + e2], s);
+      for (int ii = 1; ii <= m; ++ii) s = fma(d[ii], Sk[(int64_t)e2 * ldS + t * m + ii - 1], s);
       // west = 3m + t, east = m + t
       if (e2 == 3 * m + t) s += d[0];
       if (e2 == m + t) s += d[p - 1];
@@ -234,11 +235,11 @@ __global__ void k_merge_assemble(int k0, int n3, int nb, int nbc, int j3a, int j
   }
   if (!Tcat) return;
   double *Tk = Tcat + k * strT;
-  for (int64_t idx = threadIdx.x; idx < (int64_t)nb * n3; idx += blockDim.x) {
-    const int kk = (int)(idx / n3), c = (int)(idx % n3);
+  for (int64_t idx = threadIdx.x; idx < (int64_t)nb * n3; idx += blockDim.x) {  // stored transposed
+    const int c = (int)(idx / nb), kk = (int)(idx % nb);
     const int src = hsrc[kk];
     const int ch = src / nbc, pos = src % nbc;
-    Tk[(int64_t)kk * ldT + c] = ch == 0 ? Ta[(int64_t)pos * ldTc + j3a + c] : Tb[(int64_t)pos * ldTc + j3b + c];
+    Tk[(int64_t)c * ldT + kk] = ch == 0 ? Ta[(int64_t)pos * ldTc + j3a + c] : Tb[(int64_t)pos * ldTc + j3b + c];
   }
 }
 
@@ -248,13 +249,14 @@ __global__ void k_merge_extract(int k0, int n3, int nb, const double *__restrict
   const double *Gk = G + (int64_t)blockIdx.x * n3 * ldG;
   double *Xk = X + k * strX;
   double *Sk = S + k * strS;
+  // stored transposed (column c contiguous over the n3 rows)
   for (int64_t idx = threadIdx.x; idx < (int64_t)n3 * n3; idx += blockDim.x) {
-    const int r = (int)(idx / n3), c = (int)(idx % n3);
-    Xk[(int64_t)r * ldX + c] = Gk[(int64_t)r * ldG + n3 + c];
+    const int c = (int)(idx / n3), r = (int)(idx % n3);
+    Xk[(int64_t)c * ldX + r] = Gk[(int64_t)r * ldG + n3 + c];
   }
   for (int64_t idx = threadIdx.x; idx < (int64_t)n3 * nb; idx += blockDim.x) {
-    const int r = (int)(idx / nb), c = (int)(idx % nb);
-    Sk[(int64_t)r * ldS + c] = Gk[(int64_t)r * ldG + 2 * n3 + c];
+    const int c = (int)(idx / n3), r = (int)(idx % n3);
+    Sk[(int64_t)c * ldS + r] = Gk[(int64_t)r * ldG + 2 * n3 + c];
   }
 }
 
@@ -276,12 +278,14 @@ __global__ void k_merge_tdiag(int nb, int nbc, const int *__restrict__ hsrc, con
   }
 }
 
-// C[z] += A[z] (M x K) * B[z] (K x N), row-major FP64.  64x64 tile, 256 threads, 4x4 each.
-__global__ void __launch_bounds__(256) k_dgemm_acc(int M, int N, int K, const double *__restrict__ A, int lda,
-                                                   int64_t strA, const double *__restrict__ B, int ldb, int64_t strB,
-                                                   double *__restrict__ C, int ldc, int64_t strC) {
+// C[z] += A[z] (M x K) * B[z] (K x N) in FP64; A(r,k) = A[r*sar + k*sak], B(k,c) = B[k*sbk + c*sbc],
+// C row-major.  64x64 tile, 256 threads, 4x4 outputs each.
+__global__ void __launch_bounds__(256) k_dgemm_acc(int M, int N, int K, const double *__restrict__ A, int64_t sar,
+                                                   int64_t sak, int64_t strA, const double *__restrict__ B,
+                                                   int64_t sbk, int64_t sbc, int64_t strB, double *__restrict__ C,
+                                                   int ldc, int64_t strC) {
   __shared__ double As[16][64 + 1];
-  __shared__ double Bs[16][64];
+  __shared__ double Bs[16][64 + 1];
   const double *Az = A + blockIdx.z * strA;
   const double *Bz = B + blockIdx.z * strB;
   double *Cz = C + blockIdx.z * strC;
@@ -290,12 +294,15 @@ __global__ void __launch_bounds__(256) k_dgemm_acc(int M, int N, int K, const do
   double acc[4][4] = {};
   for (int kb = 0; kb < K; kb += 16) {
     for (int idx = threadIdx.x; idx < 64 * 16; idx += 256) {
-      const int r = idx / 16, kk = idx % 16;
+      // consecutive threads walk the unit-stride index of each operand
+      int r, kk;
+      if (sar == 1) { r = idx % 64; kk = idx / 64; } else { r = idx / 16; kk = idx % 16; }
       const int gr = row0 + r, gk = kb + kk;
-      As[kk][r] = (gr < M && gk < K) ? Az[(int64_t)gr * lda + gk] : 0.0;
-      const int kk2 = idx / 64, cc = idx % 64;
+      As[kk][r] = (gr < M && gk < K) ? Az[gr * sar + gk * sak] : 0.0;
+      int kk2, cc;
+      if (sbk == 1) { kk2 = idx % 16; cc = idx / 16; } else { kk2 = idx / 64; cc = idx % 64; }
       const int gk2 = kb + kk2, gc = col0 + cc;
-      Bs[kk2][cc] = (gk2 < K && gc < N) ? Bz[(int64_t)gk2 * ldb + gc] : 0.0;
+      Bs[kk2][cc] = (gk2 < K && gc < N) ? Bz[gk2 * sbk + gc * sbc] : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -360,11 +367,11 @@ int build_operators(hps_handle *H, OpSet &ops, double gamma_dt, bool identity, c
   if (identity) {
     k_leaf_T_ident<<<1, kT, 0, st>>>(p, Tchild.as<double>(), b_ld, H->d_D);
   } else {
-    ops.ldA = ld_pad(q);
-    ops.ldSl = ld_pad(b);
+    ops.ldA = ld_pad(q);   // A_ii^{-1} stored transposed: q columns of ldA
+    ops.ldSl = ld_pad(q);  // S stored transposed: b columns of ldSl
     ops.strA = shared ? 0 : (int64_t)q * ops.ldA;
-    ops.strSl = shared ? 0 : (int64_t)q * ops.ldSl;
-    const size_t na = (size_t)nleaf_ops * q * ops.ldA, ns = (size_t)nleaf_ops * q * ops.ldSl;
+    ops.strSl = shared ? 0 : (int64_t)b * ops.ldSl;
+    const size_t na = (size_t)nleaf_ops * q * ops.ldA, ns = (size_t)nleaf_ops * b * ops.ldSl;
     if (cudaMalloc(&ops.Ainv, na * sizeof(double)) != cudaSuccess) return HPS_ENOMEM;
     H->allocs.push_back(ops.Ainv);
     if (cudaMalloc(&ops.Sleaf, ns * sizeof(double)) != cudaSuccess) return HPS_ENOMEM;
@@ -389,18 +396,19 @@ int build_operators(hps_handle *H, OpSet &ops, double gamma_dt, bool identity, c
     const Level &lv = H->lev[l];
     MergeOps &mo = ops.merge[l];
     const int n3 = lv.n3, nb = lv.nb, nops = shared ? 1 : lv.nodes;
+    // all three stored transposed: X^T (n3 x n3), S^T (nb x n3), Tcat^T (n3 x nb)
     mo.ldX = ld_pad(n3);
-    mo.ldS = ld_pad(nb);
-    mo.ldT = ld_pad(n3);
+    mo.ldS = ld_pad(n3);
+    mo.ldT = ld_pad(nb);
     mo.strX = shared ? 0 : (int64_t)n3 * mo.ldX;
-    mo.strS = shared ? 0 : (int64_t)n3 * mo.ldS;
-    mo.strT = shared ? 0 : (int64_t)nb * mo.ldT;
+    mo.strS = shared ? 0 : (int64_t)nb * mo.ldS;
+    mo.strT = shared ? 0 : (int64_t)n3 * mo.ldT;
     if (cudaMalloc(&mo.X, (size_t)nops * n3 * mo.ldX * sizeof(double)) != cudaSuccess) return HPS_ENOMEM;
     H->allocs.push_back(mo.X);
-    if (cudaMalloc(&mo.S, (size_t)nops * n3 * mo.ldS * sizeof(double)) != cudaSuccess) return HPS_ENOMEM;
+    if (cudaMalloc(&mo.S, (size_t)nops * nb * mo.ldS * sizeof(double)) != cudaSuccess) return HPS_ENOMEM;
     H->allocs.push_back(mo.S);
     if (l > 0) {  // the root never forms h^t, so it keeps no Tcat
-      if (cudaMalloc(&mo.Tcat, (size_t)nops * nb * mo.ldT * sizeof(double)) != cudaSuccess) return HPS_ENOMEM;
+      if (cudaMalloc(&mo.Tcat, (size_t)nops * n3 * mo.ldT * sizeof(double)) != cudaSuccess) return HPS_ENOMEM;
       H->allocs.push_back(mo.Tcat);
     }
     const int W = 2 * n3 + nb, ldG = ld_pad(W);
@@ -427,8 +435,9 @@ int build_operators(hps_handle *H, OpSet &ops, double gamma_dt, bool identity, c
       k_merge_tdiag<<<gd, kT, 0, st>>>(nb, lv.nbc, lv.d_hsrc, Tchild.as<double>(), ldTc, strTc, Tp.as<double>(), ldTp,
                                        strTp);
       dim3 gg((nb + 63) / 64, (nb + 63) / 64, nops);
-      k_dgemm_acc<<<gg, 256, 0, st>>>(nb, nb, n3, mo.Tcat, mo.ldT, mo.strT, mo.S, mo.ldS, mo.strS, Tp.as<double>(),
-                                      ldTp, strTp);
+      // A = Tcat (nb x n3) from Tcat^T, B = S (n3 x nb) from S^T
+      k_dgemm_acc<<<gg, 256, 0, st>>>(nb, nb, n3, mo.Tcat, 1, mo.ldT, mo.strT, mo.S, 1, mo.ldS, mo.strS,
+                                      Tp.as<double>(), ldTp, strTp);
       if (cudaPeekAtLastError() != cudaSuccess) return HPS_ECUDA;
       std::swap(Tchild.p, Tp.p);
       ldTc = ldTp;

@@ -79,6 +79,22 @@ struct OpSet {
 // Kernel slots for launch counting and optional CUDA-event timing (hps_trace_*).
 enum Slot { kLeafUp = 0, kMergeUpW3, kMergeUpH, kMergeDown, kLeafDown, kLeafEval, kSetBoundary, kNumSlots };
 
+// A kernel sequence recorded into a CUDA graph (hps_set_graph), replayed for equal arguments.
+struct GraphEntry {
+  static constexpr int kKey = 8;
+  static constexpr int kEventPairs = 64;
+  bool seen = false;   // the key ran once eagerly (kernels loaded, attributes set)
+  bool valid = false;  // exec holds the graph of this key
+  uint64_t key[kKey] = {};
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches[16] = {};         // launches per kernel slot in one replay
+  std::vector<cudaEvent_t> ev;       // timing event pairs recorded inside the graph
+  std::vector<int> ev_slot;
+  int nev = 0;
+  bool pending = false;              // the last replay's events are not read yet
+  void destroy();
+};
+
 struct Trace {
   int64_t launches[kNumSlots] = {};
   int64_t timed[kNumSlots] = {};
@@ -88,6 +104,7 @@ struct Trace {
   std::vector<int> pair_slot;
   size_t used = 0;                 // pairs in flight
   int open_slot = -1;
+  GraphEntry *capturing = nullptr; // set while a graph is being recorded
   void begin(int slot, cudaStream_t st);
   void end(int slot, cudaStream_t st);
   void drain();                    // synchronizes the recorded events, accumulates ms
@@ -118,8 +135,14 @@ struct hps_handle {
   double *ustage = nullptr, *R = nullptr, *KL = nullptr, *KE = nullptr, *wleaf = nullptr;
   std::vector<double *> h;    // per level: nodes x nb
   std::vector<double *> w3;   // per merge level: nodes x n3
+  double *partial = nullptr;  // split-K partial sums of the merge applies
+  size_t partial_len = 0;
+  int num_sms = 0;
   std::vector<void *> allocs;
   hps::Trace trace;
+  bool graph_mode = false;
+  cudaStream_t cap_stream = nullptr;
+  hps::GraphEntry g_ark, g_solve;
 };
 
 namespace hps {
@@ -141,6 +164,8 @@ struct Epilogue {          // fused ARK stage epilogue at the leaves (a5)
 int sweep(hps_handle *H, const OpSet &ops, const Combo &rhs, double *Rsave, double *gvec,
           double *out_interior, const Epilogue *ep, cudaStream_t st);
 int set_boundary(hps_handle *H, double *gvec, const double *f, cudaStream_t st);
+size_t partial_doubles(const hps_handle *H);  // split-K scratch the merge applies need
+void drain_graph(hps_handle *H, GraphEntry &e);  // read the timing events of the last replay
 int leaf_eval(hps_handle *H, const double *u, double *KL, double *KE, const double *q, double dt,
               int g_kind, double gp0, double gp1, cudaStream_t st);
 

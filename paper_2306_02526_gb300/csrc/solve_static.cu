@@ -33,6 +33,7 @@ extern "C" int hps_solve_static(hps_handle *H, const double *rhs, const double *
     need += round256((size_t)H->lev[l].nodes * H->lev[l].nb);
     if (l < H->L) need += round256((size_t)H->lev[l].nodes * H->lev[l].n3);
   }
+  need += round256(H->partial_len);  // split-K partial sums of the top merge levels
   if (need > kStaticScratchDoubles) return HPS_ESCRATCH;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HPS_ECUDA;
@@ -43,7 +44,7 @@ extern "C" int hps_solve_static(hps_handle *H, const double *rhs, const double *
   }
   double *base = g_scratch_addr[dev];
   // point the handle's work vectors into the static array for this call, then restore them
-  double *saved_w = H->wleaf;
+  double *saved_w = H->wleaf, *saved_partial = H->partial;
   double *saved_h[kMaxLevels], *saved_w3[kMaxLevels];
   size_t off = 0;
   H->wleaf = base + off;
@@ -58,6 +59,8 @@ extern "C" int hps_solve_static(hps_handle *H, const double *rhs, const double *
       off += round256((size_t)H->lev[l].nodes * H->lev[l].n3);
     }
   }
+  H->partial = H->partial_len ? base + off : nullptr;
+  off += round256(H->partial_len);
   cudaStream_t st = (cudaStream_t)stream;
   int e = hps::set_boundary(H, u, f, st);
   if (e == HPS_OK) {
@@ -68,6 +71,7 @@ extern "C" int hps_solve_static(hps_handle *H, const double *rhs, const double *
     e = hps::sweep(H, H->impl, c, nullptr, u, u, nullptr, st);
   }
   H->wleaf = saved_w;
+  H->partial = saved_partial;
   for (int l = 0; l <= H->L; ++l) {
     H->h[l] = saved_h[l];
     if (l < H->L) H->w3[l] = saved_w3[l];

@@ -7,40 +7,18 @@
 //   leaf_down  (a5)     u_i = w + S u_b, fused ARK epilogue: dt L u_i = (u_i - R_i)/gamma and
 //                       dt (q_i + g(u_i)) with g's derivatives by leaf-local differentiation
 //
-// Every apply is a row-major matrix-vector product: a group of G lanes per row streams the
-// row with coalesced loads, reduces by warp shuffles; the vector sits in shared memory.
-// Operators are per node (stride) or shared by a whole level (stride 0).
+// Every apply is a matrix-vector product on a transposed (column-major) operator: one thread
+// per output row, a warp reads 32 consecutive rows of a column, the vector sits in shared
+// memory; levels with few rows split the columns over several CTAs and add the partial sums
+// in a fixed order (deterministic).  Operators are per node (stride) or shared by a whole
+// level (stride 0).
+#include <algorithm>
+
 #include "hps_internal.cuh"
 
 namespace hps {
 
 namespace {
-
-template <int G>
-__device__ __forceinline__ double group_sum(double v) {
-#pragma unroll
-  for (int off = G / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  return v;
-}
-
-// out(r, sum_c A[r*ld + c] * xs[c]) for rows r in [r0, r1).  Every thread of the block must
-// call this (the row loop is uniform so that the shuffles see full warps).
-template <int G, class Out>
-__device__ __forceinline__ void block_gemv(const double *__restrict__ A, int ld, int K, const double *xs, int r0,
-                                           int r1, Out out) {
-  const int NG = blockDim.x / G;
-  const int g = threadIdx.x / G, lg = threadIdx.x % G;
-  for (int base = r0; base < r1; base += NG) {
-    const int r = base + g;
-    double acc = 0.0;
-    if (r < r1) {
-      const double *a = A + (int64_t)r * ld;
-      for (int c = lg; c < K; c += G) acc = fma(__ldg(a + c), xs[c], acc);
-    }
-    acc = group_sum<G>(acc);
-    if (r < r1 && lg == 0) out(r, acc);
-  }
-}
 
 // Flux h_e = (D_bi w)_e at leaf edge e (south, east, north, west blocks of m) of a field
 // given at the interior points only (Sec. 2.1: d/dy on horizontal, d/dx on vertical edges).
@@ -98,130 +76,240 @@ __device__ void load_leaf_field(const GridDims &g, const double *gvec, int ix, i
 }
 
 // ---------------------------------------------------------------------------------------
-template <int G>
-__global__ void __launch_bounds__(256) k_leaf_up(GridDims g, const int *__restrict__ origin, Combo rhs,
-                                                 double *__restrict__ Rsave, const double *__restrict__ Ainv,
+// Operators are stored transposed: entry (row r, column c) of node k's matrix is at
+// A[k*str + c*ld + r], so one thread owns one output row and a warp reads 32 consecutive
+// rows of a column (coalesced); each product needs one FMA and no reduction across lanes.
+
+// Leaves per CTA for the leaf kernels: fill up to 512 threads with whole leaves.
+__host__ __device__ inline int leaf_lpc(int q) { return q >= 512 ? 1 : (512 / q < 16 ? 512 / q : 16); }
+
+__global__ void __launch_bounds__(512) k_leaf_up(GridDims g, int nleaf, const int *__restrict__ origin, Combo rhs,
+                                                 double *__restrict__ Rsave, const double *__restrict__ AinvT,
                                                  int ldA, int64_t strA, int identity, const double *__restrict__ Dg,
                                                  double *__restrict__ wleaf, double *__restrict__ hleaf) {
   extern __shared__ double sm[];
-  const int p = g.p, m = g.m, q = m * m, b = 4 * m;
-  double *D1x = sm, *D1y = sm + p * p, *Rs = sm + 2 * p * p, *Ws = Rs + q;
-  const int k = blockIdx.x;
-  const int ix = origin[2 * k], iy = origin[2 * k + 1];
-  const int64_t l0 = ((int64_t)iy * g.n1 + ix) * q;
+  const int p = g.p, m = g.m, q = m * m, b = 4 * m, lpc = leaf_lpc(q);
+  double *D1x = sm, *D1y = sm + p * p, *Rs = sm + 2 * p * p, *Ws = Rs + lpc * q;
+  const int k0 = blockIdx.x * lpc;
+  const int nl = min(lpc, nleaf - k0);
   for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) sm[i] = Dg[i];
-  for (int r = threadIdx.x; r < q; r += blockDim.x) {
+  for (int idx = threadIdx.x; idx < nl * q; idx += blockDim.x) {
+    const int lo = idx / q, r = idx % q, k = k0 + lo;
+    const int64_t l0 = ((int64_t)origin[2 * k + 1] * g.n1 + origin[2 * k]) * q;
     double v = 0.0;
     for (int t = 0; t < rhs.n; ++t) v = fma(rhs.coef[t], rhs.ptr[t][l0 + r], v);
-    Rs[r] = v;
+    Rs[idx] = v;
     if (Rsave) Rsave[l0 + r] = v;
   }
   __syncthreads();
-  if (identity) {
-    for (int r = threadIdx.x; r < q; r += blockDim.x) Ws[r] = Rs[r];
-  } else {
-    block_gemv<G>(Ainv + k * strA, ldA, q, Rs, 0, q, [&](int r, double v) { Ws[r] = v; });
+  for (int idx = threadIdx.x; idx < nl * q; idx += blockDim.x) {
+    const int lo = idx / q, r = idx % q;
+    double acc;
+    if (identity) {
+      acc = Rs[idx];
+    } else {
+      const double *a = AinvT + (int64_t)(k0 + lo) * strA + r;
+      const double *x = Rs + lo * q;
+      acc = 0.0;
+#pragma unroll 7
+      for (int c = 0; c < q; ++c) acc = fma(__ldg(a + (int64_t)c * ldA), x[c], acc);
+    }
+    Ws[idx] = acc;
   }
   __syncthreads();
-  for (int r = threadIdx.x; r < q; r += blockDim.x) wleaf[(int64_t)k * q + r] = Ws[r];
-  for (int e = threadIdx.x; e < b; e += blockDim.x) hleaf[(int64_t)k * b + e] = flux_interior(e, Ws, D1x, D1y, p, m);
+  for (int idx = threadIdx.x; idx < nl * q; idx += blockDim.x) wleaf[(int64_t)k0 * q + idx] = Ws[idx];
+  for (int idx = threadIdx.x; idx < nl * b; idx += blockDim.x) {
+    const int lo = idx / b, e = idx % b;
+    hleaf[(int64_t)k0 * b + idx] = flux_interior(e, Ws + lo * q, D1x, D1y, p, m);
+  }
 }
 
-template <int G>
-__global__ void __launch_bounds__(256) k_merge_up_w3(int n3, int nbc, int j3a, int j3b, int rpc,
-                                                     const double *__restrict__ hC, const double *__restrict__ X,
-                                                     int ldX, int64_t strX, double *__restrict__ w3) {
-  extern __shared__ double ds[];
-  const int k = blockIdx.y;
-  const double *ha = hC + (int64_t)(2 * k) * nbc + j3a;
-  const double *hb = hC + (int64_t)(2 * k + 1) * nbc + j3b;
-  for (int c = threadIdx.x; c < n3; c += blockDim.x) ds[c] = hb[c] - ha[c];
-  __syncthreads();
-  const int r0 = blockIdx.x * rpc, r1 = min(n3, r0 + rpc);
-  double *out = w3 + (int64_t)k * n3;
-  block_gemv<G>(X + k * strX, ldX, n3, ds, r0, r1, [&](int r, double v) { out[r] = v; });
-}
-
-template <int G>
-__global__ void __launch_bounds__(256) k_merge_up_h(int nb, int n3, int nbc, int rpc, const int *__restrict__ hsrc,
-                                                    const double *__restrict__ hC, const double *__restrict__ Tcat,
-                                                    int ldT, int64_t strT, const double *__restrict__ w3,
-                                                    double *__restrict__ h) {
-  extern __shared__ double ws[];
-  const int k = blockIdx.y;
-  for (int c = threadIdx.x; c < n3; c += blockDim.x) ws[c] = w3[(int64_t)k * n3 + c];
-  __syncthreads();
-  const int r0 = blockIdx.x * rpc, r1 = min(nb, r0 + rpc);
-  const double *hk = hC + (int64_t)(2 * k) * nbc;
-  double *out = h + (int64_t)k * nb;
-  block_gemv<G>(Tcat + k * strT, ldT, n3, ws, r0, r1, [&](int r, double v) { out[r] = hk[hsrc[r]] + v; });
-}
-
-template <int G>
-__global__ void __launch_bounds__(256) k_merge_down(GridDims g, const int *__restrict__ origin, int a, int c,
-                                                    int split, int nb, int n3, int rpc, const double *__restrict__ S,
-                                                    int ldS, int64_t strS, const double *__restrict__ w3,
-                                                    double *__restrict__ gvec) {
-  extern __shared__ double ub[];
-  const int k = blockIdx.y;
-  const int ix0 = origin[2 * k], iy0 = origin[2 * k + 1];
-  for (int pos = threadIdx.x; pos < nb; pos += blockDim.x) ub[pos] = gvec[box_bd(g, ix0, iy0, a, c, pos)];
-  __syncthreads();
-  const int r0 = blockIdx.x * rpc, r1 = min(n3, r0 + rpc);
-  const double *wk = w3 + (int64_t)k * n3;
-  block_gemv<G>(S + k * strS, ldS, nb, ub, r0, r1,
-                [&](int r, double v) { gvec[iface_bd(g, ix0, iy0, a, c, split, r)] = v + wk[r]; });
-}
-
-template <int G>
-__global__ void __launch_bounds__(256) k_leaf_down(GridDims g, const int *__restrict__ origin,
-                                                   const double *__restrict__ Sleaf, int ldS, int64_t strS,
+__global__ void __launch_bounds__(512) k_leaf_down(GridDims g, int nleaf, const int *__restrict__ origin,
+                                                   const double *__restrict__ SlT, int ldS, int64_t strS,
                                                    int identity, const double *__restrict__ wleaf,
                                                    const double *__restrict__ gvec, double *__restrict__ out_int,
                                                    Epilogue ep, const double *__restrict__ Dg) {
   extern __shared__ double sm[];
-  const int p = g.p, m = g.m, q = m * m, b = 4 * m;
-  double *D1x = sm, *D1y = sm + p * p, *U = sm + 2 * p * p, *ubs = U + p * p;
-  const int k = blockIdx.x;
-  const int ix = origin[2 * k], iy = origin[2 * k + 1];
-  const int64_t l0 = ((int64_t)iy * g.n1 + ix) * q;
-  for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) sm[i] = Dg[i];
-  for (int e = threadIdx.x; e < b; e += blockDim.x) ubs[e] = gvec[box_bd(g, ix, iy, 1, 1, e)];
-  for (int idx = threadIdx.x; idx < p * p; idx += blockDim.x) U[idx] = 0.0;
+  const int p = g.p, m = g.m, q = m * m, b = 4 * m, pp = p * p, lpc = leaf_lpc(q);
+  double *D1x = sm, *D1y = sm + pp, *U = sm + 2 * pp, *ubs = U + lpc * pp;
+  const int k0 = blockIdx.x * lpc;
+  const int nl = min(lpc, nleaf - k0);
+  for (int i = threadIdx.x; i < 2 * pp; i += blockDim.x) sm[i] = Dg[i];
+  for (int idx = threadIdx.x; idx < nl * b; idx += blockDim.x) {
+    const int lo = idx / b, e = idx % b, k = k0 + lo;
+    ubs[idx] = gvec[box_bd(g, origin[2 * k], origin[2 * k + 1], 1, 1, e)];
+  }
+  for (int idx = threadIdx.x; idx < nl * pp; idx += blockDim.x) U[idx] = 0.0;
   __syncthreads();
-  // edges of the local field from u_b (south, east, north, west)
-  for (int e = threadIdx.x; e < b; e += blockDim.x) {
+  // edges of every local field from u_b (south, east, north, west)
+  for (int idx = threadIdx.x; idx < nl * b; idx += blockDim.x) {
+    const int lo = idx / b, e = idx % b;
     const int side = e / m, t = e % m;
-    const int idx = side == 0 ? (t + 1) : side == 1 ? (t + 1) * p + (p - 1) : side == 2 ? (p - 1) * p + t + 1
-                                                                                 : (t + 1) * p;
-    U[idx] = ubs[e];
+    const int li = side == 0 ? (t + 1) : side == 1 ? (t + 1) * p + (p - 1) : side == 2 ? (p - 1) * p + t + 1
+                                                                               : (t + 1) * p;
+    U[lo * pp + li] = ubs[idx];
   }
-  const double *wk = wleaf + (int64_t)k * q;
-  if (identity) {
-    for (int r = threadIdx.x; r < q; r += blockDim.x) U[(r / m + 1) * p + (r % m + 1)] = wk[r];
-  } else {
-    block_gemv<G>(Sleaf + k * strS, ldS, b, ubs, 0, q,
-                  [&](int r, double v) { U[(r / m + 1) * p + (r % m + 1)] = wk[r] + v; });
+  for (int idx = threadIdx.x; idx < nl * q; idx += blockDim.x) {
+    const int lo = idx / q, r = idx % q;
+    double acc = wleaf[(int64_t)k0 * q + idx];
+    if (!identity) {
+      const double *a = SlT + (int64_t)(k0 + lo) * strS + r;
+      const double *x = ubs + lo * b;
+#pragma unroll 8
+      for (int e = 0; e < b; ++e) acc = fma(__ldg(a + (int64_t)e * ldS), x[e], acc);
+    }
+    U[lo * pp + (r / m + 1) * p + (r % m + 1)] = acc;
   }
   __syncthreads();
-  for (int r = threadIdx.x; r < q; r += blockDim.x) {
+  for (int idx = threadIdx.x; idx < nl * q; idx += blockDim.x) {
+    const int lo = idx / q, r = idx % q, k = k0 + lo;
     const int i = r % m + 1, j = r / m + 1;
-    const double u = U[j * p + i];
-    if (out_int) out_int[l0 + r] = u;
+    const double *Ul = U + lo * pp;
+    const double u = Ul[j * p + i];
+    const int64_t gi = ((int64_t)origin[2 * k + 1] * g.n1 + origin[2 * k]) * q + r;
+    if (out_int) out_int[gi] = u;
     if (ep.KL) {
-      ep.KL[l0 + r] = (u - ep.Rsaved[l0 + r]) * ep.inv_gamma;
+      ep.KL[gi] = (u - ep.Rsaved[gi]) * ep.inv_gamma;
       double ux = 0.0, uy = 0.0;
       if (ep.g_kind == HPS_G_BURGERS) {
         for (int kk = 0; kk < p; ++kk) {
-          ux = fma(D1x[i * p + kk], U[j * p + kk], ux);
-          uy = fma(D1y[j * p + kk], U[kk * p + i], uy);
+          ux = fma(D1x[i * p + kk], Ul[j * p + kk], ux);
+          uy = fma(D1y[j * p + kk], Ul[kk * p + i], uy);
         }
       }
       double e = g_eval(ep.g_kind, u, ux, uy, ep.gp0, ep.gp1);
-      if (ep.q) e += ep.q[l0 + r];
-      ep.KE[l0 + r] = ep.dt * e;
+      if (ep.q) e += ep.q[gi];
+      ep.KE[gi] = ep.dt * e;
     }
   }
+}
+
+// ---- merge levels: batched transposed mat-vec with node packing and split-K ----------------
+struct GemvPlan {
+  int M, K, nodes;
+  int npc;        // nodes per CTA (small M) ...
+  int rows_cta;   // ... or a tile of rows of one node (large M)
+  int row_tiles, node_groups;
+  int ksplit, kchunk;
+};
+
+constexpr int kGemvThreads = 256;
+
+GemvPlan plan_gemv(int M, int K, int nodes, int sms) {
+  GemvPlan P;
+  P.M = M;
+  P.K = K;
+  P.nodes = nodes;
+  if (M <= kGemvThreads / 2) {
+    P.npc = std::max(1, std::min(nodes, kGemvThreads / M));
+    P.rows_cta = M;
+    P.row_tiles = 1;
+  } else {
+    P.npc = 1;
+    P.rows_cta = kGemvThreads;
+    P.row_tiles = (M + kGemvThreads - 1) / kGemvThreads;
+  }
+  P.node_groups = (nodes + P.npc - 1) / P.npc;
+  const int ctas = P.node_groups * P.row_tiles;
+  const int target = 2 * sms;
+  int ks = 1;
+  if (ctas < target) ks = std::min((target + ctas - 1) / ctas, std::max(1, K / 32));
+  P.kchunk = (K + ks - 1) / ks;
+  while ((size_t)P.npc * P.kchunk * sizeof(double) > 96 * 1024) P.kchunk = (P.kchunk + 1) / 2;
+  P.ksplit = (K + P.kchunk - 1) / P.kchunk;
+  return P;
+}
+
+// x loaders
+struct XDiff {  // d = h^b_3 - h^a_3 from the children's fluxes
+  const double *hC;
+  int nbc, j3a, j3b;
+  __device__ double operator()(int k, int c) const {
+    return hC[(int64_t)(2 * k + 1) * nbc + j3b + c] - hC[(int64_t)(2 * k) * nbc + j3a + c];
+  }
+};
+struct XVec {
+  const double *v;
+  int n;
+  __device__ double operator()(int k, int c) const { return v[(int64_t)k * n + c]; }
+};
+struct XBoundary {  // u on the box boundary, gathered from the global vector
+  GridDims g;
+  const int *origin;
+  int a, c;
+  const double *gvec;
+  __device__ double operator()(int k, int pos) const {
+    return gvec[box_bd(g, origin[2 * k], origin[2 * k + 1], a, c, pos)];
+  }
+};
+// epilogues
+struct EStore {
+  double *out;
+  int n;
+  __device__ void operator()(int k, int r, double v) const { out[(int64_t)k * n + r] = v; }
+};
+struct EFlux {  // h^t = [h^a_1 ; h^b_2] + Tcat w3
+  const int *hsrc;
+  const double *hC;
+  int nbc, nb;
+  double *h;
+  __device__ void operator()(int k, int r, double v) const {
+    h[(int64_t)k * nb + r] = hC[(int64_t)(2 * k) * nbc + hsrc[r]] + v;
+  }
+};
+struct EScatter {  // u3 = S u_b + w3 onto the interface of the cut
+  GridDims g;
+  const int *origin;
+  int a, c, split, n3;
+  const double *w3;
+  double *gvec;
+  __device__ void operator()(int k, int r, double v) const {
+    gvec[iface_bd(g, origin[2 * k], origin[2 * k + 1], a, c, split, r)] = v + w3[(int64_t)k * n3 + r];
+  }
+};
+
+template <class XL, class EP>
+__global__ void __launch_bounds__(kGemvThreads) k_gemv_t(GemvPlan P, const double *__restrict__ AT, int ld,
+                                                         int64_t str, XL xl, EP ep, double *__restrict__ partial) {
+  extern __shared__ double xs[];
+  const int ng = blockIdx.x / P.row_tiles, tile = blockIdx.x % P.row_tiles;
+  const int node0 = ng * P.npc;
+  const int nn = min(P.npc, P.nodes - node0);
+  const int ks = blockIdx.y;
+  const int c0 = ks * P.kchunk, klen = min(P.kchunk, P.K - c0);
+  for (int idx = threadIdx.x; idx < nn * klen; idx += blockDim.x) {
+    const int lo = idx / klen, c = idx % klen;
+    xs[idx] = xl(node0 + lo, c0 + c);
+  }
+  __syncthreads();
+  int lo, r;
+  if (P.npc > 1) {
+    lo = threadIdx.x / P.M;
+    r = threadIdx.x % P.M;
+  } else {
+    lo = 0;
+    r = tile * P.rows_cta + threadIdx.x;
+  }
+  if (lo >= nn || r >= P.M) return;
+  const int k = node0 + lo;
+  const double *a = AT + (int64_t)k * str + (int64_t)c0 * ld + r;
+  const double *x = xs + lo * klen;
+  double acc = 0.0;
+#pragma unroll 8
+  for (int c = 0; c < klen; ++c) acc = fma(__ldg(a + (int64_t)c * ld), x[c], acc);
+  if (P.ksplit == 1) ep(k, r, acc);
+  else partial[((int64_t)ks * P.nodes + k) * P.M + r] = acc;
+}
+
+// Deterministic split-K reduction: partial sums added in split order, then the epilogue.
+template <class EP>
+__global__ void k_gemv_reduce(GemvPlan P, const double *__restrict__ partial, EP ep) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)P.nodes * P.M) return;
+  const int k = (int)(idx / P.M), r = (int)(idx % P.M);
+  double acc = 0.0;
+  for (int ks = 0; ks < P.ksplit; ++ks) acc += partial[((int64_t)ks * P.nodes + k) * P.M + r];
+  ep(k, r, acc);
 }
 
 // dt L u and dt (q + g(u)) at the interior points of every leaf (explicit first stage).
@@ -272,27 +360,25 @@ __global__ void k_set_boundary(GridDims g, double *__restrict__ gvec, const doub
   gvec[gi] = f ? f[kk] : 0.0;
 }
 
-inline int pick_G(int K) { return K >= 64 ? 32 : (K >= 24 ? 16 : 8); }
-
-#define HPS_DISPATCH_G(Gv, KERNEL, GRID, BLOCK, SMEM, ST, ...)                     \
-  do {                                                                             \
-    if ((Gv) == 32) KERNEL<32><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__);            \
-    else if ((Gv) == 16) KERNEL<16><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__);       \
-    else KERNEL<8><<<GRID, BLOCK, SMEM, ST>>>(__VA_ARGS__);                        \
-  } while (0)
-
-template <class K>
-void allow_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-void set_smem_limits(size_t bytes) {
-  static size_t done = 0;
-  if (bytes <= done) return;
-  allow_smem(k_merge_up_w3<32>, bytes); allow_smem(k_merge_up_w3<16>, bytes); allow_smem(k_merge_up_w3<8>, bytes);
-  allow_smem(k_merge_up_h<32>, bytes); allow_smem(k_merge_up_h<16>, bytes); allow_smem(k_merge_up_h<8>, bytes);
-  allow_smem(k_merge_down<32>, bytes); allow_smem(k_merge_down<16>, bytes); allow_smem(k_merge_down<8>, bytes);
-  done = bytes;
+template <class XL, class EP>
+int launch_gemv(hps_handle *H, int slot, const GemvPlan &P, const double *AT, int ld, int64_t str, XL xl, EP ep,
+                cudaStream_t st) {
+  const size_t smem = (size_t)P.npc * P.kchunk * sizeof(double);
+  static size_t smem_set = 0;  // per instantiation
+  if (smem > 48 * 1024 && smem > smem_set) {
+    cudaFuncSetAttribute(k_gemv_t<XL, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem_set = smem;
+  }
+  if (P.ksplit > 1 && (size_t)P.ksplit * P.nodes * P.M > H->partial_len) return HPS_EINVAL;
+  H->trace.begin(slot, st);
+  dim3 grid(P.node_groups * P.row_tiles, P.ksplit);
+  k_gemv_t<XL, EP><<<grid, kGemvThreads, smem, st>>>(P, AT, ld, str, xl, ep, H->partial);
+  if (P.ksplit > 1) {
+    const int64_t n = (int64_t)P.nodes * P.M;
+    k_gemv_reduce<EP><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, H->partial, ep);
+  }
+  H->trace.end(slot, st);
+  return HPS_OK;
 }
 
 constexpr int kThreads = 256;
@@ -301,9 +387,43 @@ constexpr int kThreads = 256;
 
 constexpr size_t kTracePairs = 16384;
 
+void GraphEntry::destroy() {
+  if (exec) cudaGraphExecDestroy(exec);
+  exec = nullptr;
+  for (auto &e : ev) cudaEventDestroy(e);
+  ev.clear();
+  ev_slot.clear();
+  nev = 0;
+  valid = seen = pending = false;
+}
+
+void drain_graph(hps_handle *H, GraphEntry &e) {
+  if (!e.pending) return;
+  for (int i = 0; i < e.nev; ++i) {
+    float t = 0.f;
+    cudaEventSynchronize(e.ev[2 * i + 1]);
+    if (cudaEventElapsedTime(&t, e.ev[2 * i], e.ev[2 * i + 1]) == cudaSuccess) {
+      H->trace.ms[e.ev_slot[i]] += t;
+      ++H->trace.timed[e.ev_slot[i]];
+    } else {
+      cudaGetLastError();  // a failed timing query must not surface as a launch error later
+    }
+  }
+  e.pending = false;
+}
+
 void Trace::begin(int slot, cudaStream_t st) {
-  ++launches[slot];
   open_slot = -1;
+  if (capturing) {  // recording a graph: count per replay, time with the graph's own events
+    ++capturing->launches[slot];
+    if ((mask & (1u << slot)) && capturing->nev < GraphEntry::kEventPairs) {
+      // an external record becomes an event-record node that runs on every replay
+      cudaEventRecordWithFlags(capturing->ev[2 * capturing->nev], st, cudaEventRecordExternal);
+      open_slot = slot;
+    }
+    return;
+  }
+  ++launches[slot];
   if (!(mask & (1u << slot))) return;
   if (pool.empty()) {
     pool.resize(2 * kTracePairs);
@@ -317,6 +437,13 @@ void Trace::begin(int slot, cudaStream_t st) {
 
 void Trace::end(int slot, cudaStream_t st) {
   if (open_slot != slot) return;
+  if (capturing) {
+    cudaEventRecordWithFlags(capturing->ev[2 * capturing->nev + 1], st, cudaEventRecordExternal);
+    capturing->ev_slot[capturing->nev] = slot;
+    ++capturing->nev;
+    open_slot = -1;
+    return;
+  }
   cudaEventRecord(pool[2 * used + 1], st);
   pair_slot[used] = slot;
   ++used;
@@ -330,6 +457,8 @@ void Trace::drain() {
     if (cudaEventElapsedTime(&t, pool[2 * i], pool[2 * i + 1]) == cudaSuccess) {
       ms[pair_slot[i]] += t;
       ++timed[pair_slot[i]];
+    } else {
+      cudaGetLastError();
     }
   }
   used = 0;
@@ -364,55 +493,61 @@ int leaf_eval(hps_handle *H, const double *u, double *KL, double *KE, const doub
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
+size_t partial_doubles(const hps_handle *H) {
+  size_t mx = 0;
+  for (int l = 0; l < H->L; ++l) {
+    const Level &lv = H->lev[l];
+    const GemvPlan P[3] = {plan_gemv(lv.n3, lv.n3, lv.nodes, H->num_sms), plan_gemv(lv.nb, lv.n3, lv.nodes, H->num_sms),
+                           plan_gemv(lv.n3, lv.nb, lv.nodes, H->num_sms)};
+    for (const GemvPlan &p : P)
+      if (p.ksplit > 1) mx = std::max(mx, (size_t)p.ksplit * p.nodes * p.M);
+  }
+  return mx;
+}
+
 int sweep(hps_handle *H, const OpSet &ops, const Combo &rhs, double *Rsave, double *gvec, double *out_interior,
           const Epilogue *ep, cudaStream_t st) {
   const int L = H->L, p = H->p, q = H->q, b = H->b;
-  size_t maxk = 0;
-  for (int l = 0; l < L; ++l) maxk = std::max<size_t>(maxk, (size_t)std::max(H->lev[l].nb, H->lev[l].n3));
-  set_smem_limits(maxk * sizeof(double));
   const Level &leaf = H->lev[L];
+  const int lpc = leaf_lpc(q);
+  const int lthreads = std::min(512, ((lpc * q + 31) / 32) * 32);
+  const unsigned lgrid = (unsigned)((leaf.nodes + lpc - 1) / lpc);
   {
-    const size_t smem = (size_t)(2 * p * p + 2 * q) * sizeof(double);
+    const size_t smem = (size_t)(2 * p * p + 2 * lpc * q) * sizeof(double);
     H->trace.begin(kLeafUp, st);
-    HPS_DISPATCH_G(pick_G(q), k_leaf_up, leaf.nodes, kThreads, smem, st, H->g, leaf.d_origin, rhs, Rsave, ops.Ainv,
-                   ops.ldA, ops.strA, ops.identity ? 1 : 0, H->d_D, H->wleaf, H->h[L]);
+    k_leaf_up<<<lgrid, lthreads, smem, st>>>(H->g, leaf.nodes, leaf.d_origin, rhs, Rsave, ops.Ainv, ops.ldA, ops.strA,
+                                             ops.identity ? 1 : 0, H->d_D, H->wleaf, H->h[L]);
     H->trace.end(kLeafUp, st);
   }
   for (int l = L - 1; l >= 0; --l) {
     const Level &lv = H->lev[l];
     const MergeOps &mo = ops.merge[l];
-    const int G = pick_G(lv.n3);
-    const int rpc = kThreads / G;
-    dim3 gw((lv.n3 + rpc - 1) / rpc, lv.nodes);
-    H->trace.begin(kMergeUpW3, st);
-    HPS_DISPATCH_G(G, k_merge_up_w3, gw, kThreads, lv.n3 * sizeof(double), st, lv.n3, lv.nbc, lv.j3a, lv.j3b, rpc,
-                   H->h[l + 1], mo.X, mo.ldX, mo.strX, H->w3[l]);
-    H->trace.end(kMergeUpW3, st);
+    const GemvPlan Pw = plan_gemv(lv.n3, lv.n3, lv.nodes, H->num_sms);
+    if (int e = launch_gemv(H, kMergeUpW3, Pw, mo.X, mo.ldX, mo.strX, XDiff{H->h[l + 1], lv.nbc, lv.j3a, lv.j3b},
+                            EStore{H->w3[l], lv.n3}, st))
+      return e;
     if (l > 0) {
-      dim3 gh((lv.nb + rpc - 1) / rpc, lv.nodes);
-      H->trace.begin(kMergeUpH, st);
-      HPS_DISPATCH_G(G, k_merge_up_h, gh, kThreads, lv.n3 * sizeof(double), st, lv.nb, lv.n3, lv.nbc, rpc, lv.d_hsrc,
-                     H->h[l + 1], mo.Tcat, mo.ldT, mo.strT, H->w3[l], H->h[l]);
-      H->trace.end(kMergeUpH, st);
+      const GemvPlan Ph = plan_gemv(lv.nb, lv.n3, lv.nodes, H->num_sms);
+      if (int e = launch_gemv(H, kMergeUpH, Ph, mo.Tcat, mo.ldT, mo.strT, XVec{H->w3[l], lv.n3},
+                              EFlux{lv.d_hsrc, H->h[l + 1], lv.nbc, lv.nb, H->h[l]}, st))
+        return e;
     }
   }
   for (int l = 0; l < L; ++l) {
     const Level &lv = H->lev[l];
     const MergeOps &mo = ops.merge[l];
-    const int G = pick_G(lv.nb);
-    const int rpc = kThreads / G;
-    dim3 gd((lv.n3 + rpc - 1) / rpc, lv.nodes);
-    H->trace.begin(kMergeDown, st);
-    HPS_DISPATCH_G(G, k_merge_down, gd, kThreads, lv.nb * sizeof(double), st, H->g, lv.d_origin, lv.a, lv.c, lv.split,
-                   lv.nb, lv.n3, rpc, mo.S, mo.ldS, mo.strS, H->w3[l], gvec);
-    H->trace.end(kMergeDown, st);
+    const GemvPlan Pd = plan_gemv(lv.n3, lv.nb, lv.nodes, H->num_sms);
+    if (int e = launch_gemv(H, kMergeDown, Pd, mo.S, mo.ldS, mo.strS, XBoundary{H->g, lv.d_origin, lv.a, lv.c, gvec},
+                            EScatter{H->g, lv.d_origin, lv.a, lv.c, lv.split, lv.n3, H->w3[l], gvec}, st))
+      return e;
   }
   {
     Epilogue none;
-    const size_t smem = (size_t)(3 * p * p + b) * sizeof(double);
+    const size_t smem = (size_t)(2 * p * p + lpc * (p * p + b)) * sizeof(double);
     H->trace.begin(kLeafDown, st);
-    HPS_DISPATCH_G(pick_G(b), k_leaf_down, leaf.nodes, kThreads, smem, st, H->g, leaf.d_origin, ops.Sleaf, ops.ldSl,
-                   ops.strSl, ops.identity ? 1 : 0, H->wleaf, gvec, out_interior, ep ? *ep : none, H->d_D);
+    k_leaf_down<<<lgrid, lthreads, smem, st>>>(H->g, leaf.nodes, leaf.d_origin, ops.Sleaf, ops.ldSl, ops.strSl,
+                                               ops.identity ? 1 : 0, H->wleaf, gvec, out_interior, ep ? *ep : none,
+                                               H->d_D);
     H->trace.end(kLeafDown, st);
   }
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;

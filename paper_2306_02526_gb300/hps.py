@@ -125,6 +125,10 @@ class HPSSolver:
         except Exception:
             pass
 
+    def set_graph(self, enable=True):
+        """Record ark_step / hps_solve into CUDA graphs and replay them (hps_set_graph)."""
+        check(lib().hps_set_graph(self._h, 1 if enable else 0), "hps_set_graph")
+
     def trace_enable(self, kernels=()):
         """Reset the per-kernel counters; time the named kernels (see _lib.KERNELS) with CUDA events."""
         mask = 0
