@@ -221,7 +221,8 @@ def bench_ours(args, rank, world, local_rank):
         step(u, t)
         t += wl.dt
     # per-kernel shares from a traced pass (all kernels event-timed), untimed
-    S.trace_enable(("leaf_up", "merge_up_w3", "merge_up_h", "merge_down", "leaf_down", "leaf_eval", "set_boundary"))
+    from paper_2306_02526_gb300 import _lib
+    S.trace_enable(_lib.KERNELS)
     for _ in range(4):
         step(u, t)
         t += wl.dt

@@ -124,8 +124,11 @@ int hps_solve(hps_handle *h, const double *rhs, const double *f, double *u, hps_
  * The first call on a device looks up the array's device address with the device current
  * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls share
  * the one array and it keeps the last call's contents (every entry a call reads it writes
- * first, so nothing needs clearing): calls that overlap on the GPU -- on different streams
- * or different handles -- race and must be serialized by the caller. */
+ * first, except the few counters of the merge kernel, which each call clears): calls that
+ * overlap on the GPU -- on different streams or different handles -- race and must be
+ * serialized by the caller.  A bounded wait that runs out in this call is reported by the
+ * call's own error word inside the array, which is not read back: check results with
+ * hps_solve when in doubt. */
 int hps_solve_static(hps_handle *h, const double *rhs, const double *f, double *u, hps_stream_t stream);
 
 /* Nonlinear term presets g(u) (Sec. 1: at most first derivatives), evaluated at interior
@@ -163,6 +166,33 @@ int hps_ark_abscissae(double *c);
 int ark_step(hps_handle *h, double *u, double t, double dt, const hps_ark_terms *terms,
              hps_stream_t stream);
 
+/* Merge-level execution.  enable != 0: the upward merges of all levels run in one
+ * cooperative kernel whose CTAs stay resident and pass a grid-wide barrier between tasks,
+ * and likewise the downward merges; every barrier wait is bounded (2 s), and a wait that
+ * runs out sets the handle's error word (read it with hps_status).  enable == 0 (default):
+ * one launch per level and operator (plus a reduction launch where a level splits its
+ * columns).  Both give bit-identical results. */
+int hps_set_persistent(hps_handle *h, int enable);
+
+/* Synchronizes `stream` and reports a bounded device-side wait that ran out since the last
+ * call (HPS_ETIMEOUT; the handle's barrier state is reset so that later calls work), else
+ * HPS_OK.  Results of the sweep that timed out are not valid. */
+int hps_status(hps_handle *h, hps_stream_t stream);
+
+/* Per-task timing of the persistent merge kernel (tracing; no effect on results).
+ * enable = 1 / 0: start / stop stamping (the first CTA reads the GPU global timer at the start
+ * of every task); enable = -1: synchronize the device and write into us[] the durations, in
+ * microseconds, of the tasks of the last upward (upward != 0) or downward launch of the
+ * implicit operator set, and return their number (upward: per level from the leaves up,
+ * w3 then h; downward: per level from the root down). */
+int hps_trace_tasks(hps_handle *h, int enable, int upward, double *us, int max_tasks);
+
+/* Self-test of the bounded wait: runs the persistent merge kernel with a barrier that one
+ * more CTA than exists must reach and a 1 ms limit, so the wait must run out.  Returns
+ * HPS_ETIMEOUT when the kernel gave up and returned as designed (the handle stays usable),
+ * HPS_OK if the barrier completed (a fault in the barrier), or an error code. */
+int hps_selftest_barrier_timeout(hps_handle *h, hps_stream_t stream);
+
 /* Graph replay.  With enable != 0, ark_step and hps_solve record their kernel sequence
  * (about 380 launches per ARK step at 64 x 64 leaves) into a CUDA graph and replay it, so
  * the launch cost is paid once: the first call with a given set of pointers and arguments
@@ -181,7 +211,9 @@ enum {
   HPS_K_MERGE_DOWN = 3,  /* a4: u3 = S^t u_b + w3                                       */
   HPS_K_LEAF_DOWN = 4,   /* a5: u_i = w + S u_b and the fused ARK stage epilogue          */
   HPS_K_LEAF_EVAL = 5,   /* explicit first stage: dt L u^n, dt (q + g(u^n))               */
-  HPS_K_SET_BOUNDARY = 6 /* Dirichlet data onto the outer boundary                        */
+  HPS_K_SET_BOUNDARY = 6, /* Dirichlet data onto the outer boundary                       */
+  HPS_K_MERGE_UP_ALL = 7,  /* a3, all levels in one persistent kernel (hps_set_persistent)   */
+  HPS_K_MERGE_DOWN_ALL = 8 /* a4, all levels in one persistent kernel (hps_set_persistent)   */
 };
 
 /* Tracing (no effect on results).  Every launch of the solve path is counted per kernel;

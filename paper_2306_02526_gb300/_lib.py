@@ -12,7 +12,8 @@ HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ETIMEOUT, HPS_ECUDA, HPS_EDT,
 HPS_COEF_CONST, HPS_COEF_NODAL = 0, 1
 HPS_FLAG_PER_NODE = 1
 HPS_G_NONE, HPS_G_ALLEN_CAHN, HPS_G_FISHER, HPS_G_BURGERS = 0, 1, 2, 3
-KERNELS = ("leaf_up", "merge_up_w3", "merge_up_h", "merge_down", "leaf_down", "leaf_eval", "set_boundary")
+KERNELS = ("leaf_up", "merge_up_w3", "merge_up_h", "merge_down", "leaf_down", "leaf_eval", "set_boundary",
+           "merge_up_all", "merge_down_all")
 
 
 class hps_tree(ctypes.Structure):
@@ -48,6 +49,10 @@ SIGNATURES = {
     "ark_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                 ctypes.POINTER(hps_ark_terms), ctypes.c_void_p]),
     "hps_set_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "hps_set_persistent": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "hps_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hps_trace_tasks": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, c_double_p, ctypes.c_int]),
+    "hps_selftest_barrier_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "hps_trace_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint]),
     "hps_trace_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int64_p, c_int64_p,
                                       ctypes.POINTER(ctypes.c_double)]),

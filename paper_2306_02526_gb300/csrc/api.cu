@@ -9,6 +9,7 @@
 
 using hps::GridDims;
 using hps::Level;
+using hps::OpSet;
 
 namespace {
 
@@ -375,6 +376,16 @@ int hps_build(const hps_tree *tree, int p, const hps_coeffs *coeffs, double gamm
   }
   H->partial_len = hps::partial_doubles(H);
   if (H->partial_len && dalloc(H, &H->partial, H->partial_len)) return fail(HPS_ENOMEM);
+  // persistent merge kernel: task lists, partial sums, counters, barrier, error word
+  if (int e = hps::build_tasks(H, H->impl)) return fail(e);
+  if (int e = hps::build_tasks(H, H->ident)) return fail(e);
+  if (dalloc(H, &H->ppartial, std::max<size_t>(1, H->ppartial_len)) ||
+      dalloc(H, &H->pcounters, std::max<size_t>(1, H->pcounter_len)) || dalloc(H, &H->pbar, 2) ||
+      dalloc(H, &H->perr, 1))
+    return fail(HPS_ENOMEM);
+  cudaMemsetAsync(H->pcounters, 0, std::max<size_t>(1, H->pcounter_len) * sizeof(unsigned), st);
+  cudaMemsetAsync(H->pbar, 0, 2 * sizeof(unsigned), st);
+  cudaMemsetAsync(H->perr, 0, sizeof(int), st);
   cudaMemsetAsync(H->ustage, 0, g.N * sizeof(double), st);
   if (cudaStreamSynchronize(st) != cudaSuccess) return fail(HPS_ECUDA);
   *out = H;
@@ -502,6 +513,61 @@ int hps_solve(hps_handle *H, const double *rhs, const double *f, double *u, hps_
   const uint64_t key[hps::GraphEntry::kKey] = {(uint64_t)rhs, (uint64_t)f, (uint64_t)u, 0, 0, 0, 0, 0};
   return run_graphed(H, H->g_solve, key, [&](cudaStream_t s) { return solve_enqueue(H, rhs, f, u, s); },
                      (cudaStream_t)stream);
+}
+
+int hps_set_persistent(hps_handle *H, int enable) {
+  if (!H) return HPS_EINVAL;
+  cudaDeviceSynchronize();
+  hps::drain_graph(H, H->g_ark);
+  hps::drain_graph(H, H->g_solve);
+  H->g_ark.destroy();  // recorded graphs hold the other kernel sequence
+  H->g_solve.destroy();
+  H->persistent = enable != 0;
+  return HPS_OK;
+}
+
+int hps_status(hps_handle *H, hps_stream_t stream) {
+  if (!H) return HPS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int herr = 0;
+  if (cudaMemcpyAsync(&herr, H->perr, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return HPS_ECUDA;
+  if (!herr) return HPS_OK;
+  // a timed-out barrier leaves its counters behind: reset them for the next call
+  cudaMemsetAsync(H->pcounters, 0, std::max<size_t>(1, H->pcounter_len) * sizeof(unsigned), st);
+  cudaMemsetAsync(H->pbar, 0, 2 * sizeof(unsigned), st);
+  cudaMemsetAsync(H->perr, 0, sizeof(int), st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return HPS_ECUDA;
+  return HPS_ETIMEOUT;
+}
+
+int hps_trace_tasks(hps_handle *H, int enable, int upward, double *us, int max_tasks) {
+  if (!H) return HPS_EINVAL;
+  if (!H->pstamps && dalloc(H, &H->pstamps, 128)) return HPS_ENOMEM;
+  if (enable >= 0) {
+    cudaDeviceSynchronize();
+    if (H->stamp_tasks != (enable != 0)) {  // recorded graphs carry the other kernel arguments
+      H->g_ark.destroy();
+      H->g_solve.destroy();
+    }
+    H->stamp_tasks = enable != 0;
+    return HPS_OK;
+  }
+  const OpSet &ops = H->impl;
+  const int n = upward ? ops.n_up : ops.n_down;
+  unsigned long long st[65];
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(st, H->pstamps + (upward ? 0 : 64), (n + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost) !=
+          cudaSuccess)
+    return HPS_ECUDA;
+  for (int t = 0; t < n && t < max_tasks; ++t) us[t] = 1e-3 * (double)(st[t + 1] - st[t]);
+  return n;
+}
+
+int hps_selftest_barrier_timeout(hps_handle *H, hps_stream_t stream) {
+  if (!H) return HPS_EINVAL;
+  return hps::selftest_barrier(H, (cudaStream_t)stream);
 }
 
 int hps_set_graph(hps_handle *H, int enable) {

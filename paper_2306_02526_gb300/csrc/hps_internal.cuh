@@ -48,6 +48,48 @@ __host__ __device__ inline int64_t iface_bd(const GridDims &g, int ix0, int iy0,
   return hseg(g, iy0 + c / 2, ix0 + pos / m, pos % m);
 }
 
+// Kernel slots for launch counting and optional CUDA-event timing (hps_trace_*).
+enum Slot {
+  kLeafUp = 0, kMergeUpW3, kMergeUpH, kMergeDown, kLeafDown, kLeafEval, kSetBoundary, kMergeUpFused,
+  kMergeDownFused, kNumSlots
+};
+
+constexpr int kMaxLevels = 32;
+constexpr int kPThreads = 256;       // threads per CTA of the persistent merge kernel
+constexpr int kPSmemDoubles = 4096;  // its vector staging (32 KB)
+constexpr int kMaxSplit = 64;        // column chunks of one output tile (all merge paths)
+
+// One mat-vec task of the persistent merge kernel (all nodes of one level, one operator kind).
+struct MTask {
+  int kind;  // 0: w3 = X d,  1: h = [h^a_1; h^b_2] + Tcat w3,  2: u3 = S u_b + w3 (scattered)
+  int lvl;
+  int M, K, nodes, npc, rows_cta, row_tiles, node_groups, ksplit, kchunk;
+  int64_t items;
+  const double *AT;
+  int ld;
+  int64_t str;
+  int nbc, j3a, j3b, n3, nb;
+  const int *hsrc;
+  const int *origin;
+  int a, c, split;
+};
+
+struct PArgs {
+  const MTask *tasks;
+  int ntasks;
+  int selftest;
+  double *h[kMaxLevels];
+  double *w3[kMaxLevels];
+  GridDims g;
+  double *gvec;
+  double *partial;
+  unsigned *counters;
+  unsigned *bar;  // [count, generation]
+  int *err;
+  unsigned long long limit_ns;
+  unsigned long long *stamps;  // optional: globaltimer at the start of every task and at the end
+};
+
 // One level of the uniform binary tree (all boxes on a level have the same shape).
 struct Level {
   int nodes = 0, a = 0, c = 0;
@@ -74,10 +116,9 @@ struct OpSet {
   int ldA = 0, ldSl = 0;
   int64_t strA = 0, strSl = 0;
   std::vector<MergeOps> merge;  // index = level (0 .. L-1)
+  MTask *d_up = nullptr, *d_down = nullptr;  // persistent task lists
+  int n_up = 0, n_down = 0;
 };
-
-// Kernel slots for launch counting and optional CUDA-event timing (hps_trace_*).
-enum Slot { kLeafUp = 0, kMergeUpW3, kMergeUpH, kMergeDown, kLeafDown, kLeafEval, kSetBoundary, kNumSlots };
 
 // A kernel sequence recorded into a CUDA graph (hps_set_graph), replayed for equal arguments.
 struct GraphEntry {
@@ -87,7 +128,7 @@ struct GraphEntry {
   bool valid = false;  // exec holds the graph of this key
   uint64_t key[kKey] = {};
   cudaGraphExec_t exec = nullptr;
-  int64_t launches[16] = {};         // launches per kernel slot in one replay
+  int64_t launches[16] = {};         // launches per kernel slot in one replay (>= kNumSlots)
   std::vector<cudaEvent_t> ev;       // timing event pairs recorded inside the graph
   std::vector<int> ev_slot;
   int nev = 0;
@@ -140,6 +181,16 @@ struct hps_handle {
   int num_sms = 0;
   std::vector<void *> allocs;
   hps::Trace trace;
+  bool persistent = false;    // merge levels by the persistent kernel (else one launch per task)
+  int pgrid = 0;              // its CTA count (co-resident)
+  double *ppartial = nullptr; // its split-column partial sums
+  size_t ppartial_len = 0;
+  unsigned *pcounters = nullptr;  // last-CTA counters (self-resetting)
+  size_t pcounter_len = 0;
+  unsigned *pbar = nullptr;   // grid barrier [count, generation]
+  int *perr = nullptr;        // bounded-wait error word
+  unsigned long long *pstamps = nullptr;  // per-task time stamps (up: [0, 64), down: [64, 128))
+  bool stamp_tasks = false;
   bool graph_mode = false;
   cudaStream_t cap_stream = nullptr;
   hps::GraphEntry g_ark, g_solve;
@@ -166,6 +217,12 @@ int sweep(hps_handle *H, const OpSet &ops, const Combo &rhs, double *Rsave, doub
 int set_boundary(hps_handle *H, double *gvec, const double *f, cudaStream_t st);
 size_t partial_doubles(const hps_handle *H);  // split-K scratch the merge applies need
 void drain_graph(hps_handle *H, GraphEntry &e);  // read the timing events of the last replay
+
+// ---- persistent merge kernel (persistent.cu) ---------------------------------------------
+int persistent_grid(hps_handle *H);
+int build_tasks(hps_handle *H, OpSet &ops);
+int merge_persistent(hps_handle *H, const OpSet &ops, bool upward, double *gvec, cudaStream_t st);
+int selftest_barrier(hps_handle *H, cudaStream_t st);
 int leaf_eval(hps_handle *H, const double *u, double *KL, double *KE, const double *q, double dt,
               int g_kind, double gp0, double gp1, cudaStream_t st);
 

@@ -34,6 +34,9 @@ extern "C" int hps_solve_static(hps_handle *H, const double *rhs, const double *
     if (l < H->L) need += round256((size_t)H->lev[l].nodes * H->lev[l].n3);
   }
   need += round256(H->partial_len);  // split-K partial sums of the top merge levels
+  // the persistent merge kernel's partial sums, tile counters, barrier and error word
+  const size_t cnt_d = (H->pcounter_len + 1) / 2;
+  need += round256(H->ppartial_len) + round256(cnt_d) + 32;
   if (need > kStaticScratchDoubles) return HPS_ESCRATCH;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HPS_ECUDA;
@@ -44,7 +47,9 @@ extern "C" int hps_solve_static(hps_handle *H, const double *rhs, const double *
   }
   double *base = g_scratch_addr[dev];
   // point the handle's work vectors into the static array for this call, then restore them
-  double *saved_w = H->wleaf, *saved_partial = H->partial;
+  double *saved_w = H->wleaf, *saved_partial = H->partial, *saved_pp = H->ppartial;
+  unsigned *saved_cnt = H->pcounters, *saved_bar = H->pbar;
+  int *saved_err = H->perr;
   double *saved_h[kMaxLevels], *saved_w3[kMaxLevels];
   size_t off = 0;
   H->wleaf = base + off;
@@ -61,8 +66,19 @@ extern "C" int hps_solve_static(hps_handle *H, const double *rhs, const double *
   }
   H->partial = H->partial_len ? base + off : nullptr;
   off += round256(H->partial_len);
+  H->ppartial = base + off;
+  off += round256(H->ppartial_len);
+  H->pcounters = reinterpret_cast<unsigned *>(base + off);
+  off += round256(cnt_d);
+  H->pbar = reinterpret_cast<unsigned *>(base + off);
+  H->perr = reinterpret_cast<int *>(base + off + 16);
+  off += 32;
   cudaStream_t st = (cudaStream_t)stream;
-  int e = hps::set_boundary(H, u, f, st);
+  // counters, barrier and error word must start at zero (they keep the last call's values)
+  int e = HPS_OK;
+  if (cudaMemsetAsync(H->pcounters, 0, round256(cnt_d) * sizeof(double) + 32 * sizeof(double), st) != cudaSuccess)
+    e = HPS_ECUDA;
+  if (e == HPS_OK) e = hps::set_boundary(H, u, f, st);
   if (e == HPS_OK) {
     hps::Combo c{};
     c.ptr[0] = rhs;
@@ -72,6 +88,10 @@ extern "C" int hps_solve_static(hps_handle *H, const double *rhs, const double *
   }
   H->wleaf = saved_w;
   H->partial = saved_partial;
+  H->ppartial = saved_pp;
+  H->pcounters = saved_cnt;
+  H->pbar = saved_bar;
+  H->perr = saved_err;
   for (int l = 0; l <= H->L; ++l) {
     H->h[l] = saved_h[l];
     if (l < H->L) H->w3[l] = saved_w3[l];

@@ -195,7 +195,8 @@ struct GemvPlan {
 
 constexpr int kGemvThreads = 256;
 
-GemvPlan plan_gemv(int M, int K, int nodes, int sms) {
+GemvPlan plan_gemv(int M, int K, int nodes, int target_ctas) {
+  const int sms = target_ctas;
   GemvPlan P;
   P.M = M;
   P.K = K;
@@ -210,12 +211,13 @@ GemvPlan plan_gemv(int M, int K, int nodes, int sms) {
     P.row_tiles = (M + kGemvThreads - 1) / kGemvThreads;
   }
   P.node_groups = (nodes + P.npc - 1) / P.npc;
+  // the same column split as the persistent kernel's task plan, so both paths add in one order
   const int ctas = P.node_groups * P.row_tiles;
-  const int target = 2 * sms;
+  const int target = sms;
   int ks = 1;
-  if (ctas < target) ks = std::min((target + ctas - 1) / ctas, std::max(1, K / 32));
+  if (ctas < target) ks = std::min({(target + ctas - 1) / ctas, std::max(1, K / 32), kMaxSplit});
   P.kchunk = (K + ks - 1) / ks;
-  while ((size_t)P.npc * P.kchunk * sizeof(double) > 96 * 1024) P.kchunk = (P.kchunk + 1) / 2;
+  while (P.npc * P.kchunk > kPSmemDoubles) P.kchunk = (P.kchunk + 1) / 2;
   P.ksplit = (K + P.kchunk - 1) / P.kchunk;
   return P;
 }
@@ -308,6 +310,7 @@ __global__ void k_gemv_reduce(GemvPlan P, const double *__restrict__ partial, EP
   if (idx >= (int64_t)P.nodes * P.M) return;
   const int k = (int)(idx / P.M), r = (int)(idx % P.M);
   double acc = 0.0;
+#pragma unroll 8
   for (int ks = 0; ks < P.ksplit; ++ks) acc += partial[((int64_t)ks * P.nodes + k) * P.M + r];
   ep(k, r, acc);
 }
@@ -497,8 +500,8 @@ size_t partial_doubles(const hps_handle *H) {
   size_t mx = 0;
   for (int l = 0; l < H->L; ++l) {
     const Level &lv = H->lev[l];
-    const GemvPlan P[3] = {plan_gemv(lv.n3, lv.n3, lv.nodes, H->num_sms), plan_gemv(lv.nb, lv.n3, lv.nodes, H->num_sms),
-                           plan_gemv(lv.n3, lv.nb, lv.nodes, H->num_sms)};
+    const GemvPlan P[3] = {plan_gemv(lv.n3, lv.n3, lv.nodes, 2 * H->num_sms), plan_gemv(lv.nb, lv.n3, lv.nodes, 2 * H->num_sms),
+                           plan_gemv(lv.n3, lv.nb, lv.nodes, 2 * H->num_sms)};
     for (const GemvPlan &p : P)
       if (p.ksplit > 1) mx = std::max(mx, (size_t)p.ksplit * p.nodes * p.M);
   }
@@ -519,24 +522,28 @@ int sweep(hps_handle *H, const OpSet &ops, const Combo &rhs, double *Rsave, doub
                                              ops.identity ? 1 : 0, H->d_D, H->wleaf, H->h[L]);
     H->trace.end(kLeafUp, st);
   }
-  for (int l = L - 1; l >= 0; --l) {
+  if (H->persistent) {
+    if (int e = merge_persistent(H, ops, true, gvec, st)) return e;
+    if (int e = merge_persistent(H, ops, false, gvec, st)) return e;
+  }
+  for (int l = L - 1; l >= 0 && !H->persistent; --l) {
     const Level &lv = H->lev[l];
     const MergeOps &mo = ops.merge[l];
-    const GemvPlan Pw = plan_gemv(lv.n3, lv.n3, lv.nodes, H->num_sms);
+    const GemvPlan Pw = plan_gemv(lv.n3, lv.n3, lv.nodes, 2 * H->num_sms);
     if (int e = launch_gemv(H, kMergeUpW3, Pw, mo.X, mo.ldX, mo.strX, XDiff{H->h[l + 1], lv.nbc, lv.j3a, lv.j3b},
                             EStore{H->w3[l], lv.n3}, st))
       return e;
     if (l > 0) {
-      const GemvPlan Ph = plan_gemv(lv.nb, lv.n3, lv.nodes, H->num_sms);
+      const GemvPlan Ph = plan_gemv(lv.nb, lv.n3, lv.nodes, 2 * H->num_sms);
       if (int e = launch_gemv(H, kMergeUpH, Ph, mo.Tcat, mo.ldT, mo.strT, XVec{H->w3[l], lv.n3},
                               EFlux{lv.d_hsrc, H->h[l + 1], lv.nbc, lv.nb, H->h[l]}, st))
         return e;
     }
   }
-  for (int l = 0; l < L; ++l) {
+  for (int l = 0; l < L && !H->persistent; ++l) {
     const Level &lv = H->lev[l];
     const MergeOps &mo = ops.merge[l];
-    const GemvPlan Pd = plan_gemv(lv.n3, lv.nb, lv.nodes, H->num_sms);
+    const GemvPlan Pd = plan_gemv(lv.n3, lv.nb, lv.nodes, 2 * H->num_sms);
     if (int e = launch_gemv(H, kMergeDown, Pd, mo.S, mo.ldS, mo.strS, XBoundary{H->g, lv.d_origin, lv.a, lv.c, gvec},
                             EScatter{H->g, lv.d_origin, lv.a, lv.c, lv.split, lv.n3, H->w3[l], gvec}, st))
       return e;

@@ -129,6 +129,28 @@ class HPSSolver:
         """Record ark_step / hps_solve into CUDA graphs and replay them (hps_set_graph)."""
         check(lib().hps_set_graph(self._h, 1 if enable else 0), "hps_set_graph")
 
+    def set_persistent(self, enable=True):
+        """All merge levels in one persistent kernel per direction (default) or one launch per level."""
+        check(lib().hps_set_persistent(self._h, 1 if enable else 0), "hps_set_persistent")
+
+    def trace_tasks(self, enable=None):
+        """enable True/False: start/stop per-task stamping; None: (up_us, down_us) of the last sweep."""
+        if enable is not None:
+            check(lib().hps_trace_tasks(self._h, 1 if enable else 0, 0, None, 0), "hps_trace_tasks")
+            return None
+        out = []
+        for up in (1, 0):
+            buf = (ctypes.c_double * 64)()
+            n = lib().hps_trace_tasks(self._h, -1, up, buf, 64)
+            if n < 0:
+                check(n, "hps_trace_tasks")
+            out.append(list(buf)[:n])
+        return tuple(out)
+
+    def status(self, stream=None):
+        """Raise HPSError if a bounded device wait ran out since the last check (hps_status)."""
+        check(lib().hps_status(self._h, _stream_ptr(stream)), "hps_status")
+
     def trace_enable(self, kernels=()):
         """Reset the per-kernel counters; time the named kernels (see _lib.KERNELS) with CUDA events."""
         mask = 0
