@@ -229,6 +229,30 @@ int hps_trace_enable(hps_handle *h, unsigned mask);
  * any may be NULL. */
 int hps_trace_read(hps_handle *h, int kernel, int64_t *launches, int64_t *timed, double *total_ms);
 
+/* ---- Batched mixed precision (R right-hand sides, FP32 applies, FP64 refinement) ----------
+ * Vectors with R columns are stored RHS-fastest: entry (point i, column j) at i*R + j, with
+ * the point order of the single-column vector.  Each implicit solve A u = b is done as
+ * u = S32(b), then `refine` times: r = b - A u in FP64 (the collocated rows of eq. ``sparse_A``:
+ * interior R - (u - gamma dt L u) by leaf-local differentiation, shared-edge flux jumps), u +=
+ * S32(r), where S32 is the HPS sweep with FP32 operators, FP32 work vectors and FP32
+ * accumulation.  With refine = 2 the result matches the FP64 solve to about 1e-12 relative
+ * (the FP64 path of the sweep itself is not used). */
+
+/* Convert the operators to FP32 (once) and allocate the R-column work buffers (R <= 64);
+ * must precede the batched calls with this R.  Synchronizes the device. */
+int hps_batch_reserve(hps_handle *h, int R);
+
+/* R solves of hps_solve at once.  rhs: N_int x R; f: N_bd x R or NULL; u: N x R (written);
+ * refine: 0..8 refinement sweeps. */
+int hps_solve_batch(hps_handle *h, int R, const double *rhs, const double *f, double *u, int refine,
+                    hps_stream_t stream);
+
+/* ark_step on R states at once (u: N x R in place; terms->q: 6 x N_int x R, terms->f:
+ * 6 x N_bd x R, both stage-major, or NULL).  Each implicit stage and the closing identity
+ * solve use `refine` FP64 refinement sweeps. */
+int ark_step_batch(hps_handle *h, int R, double *u, double t, double dt, const hps_ark_terms *terms, int refine,
+                   hps_stream_t stream);
+
 /* Release the handle and all its device memory (synchronizes the device first). */
 void hps_free(hps_handle *h);
 

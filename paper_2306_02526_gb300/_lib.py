@@ -56,6 +56,11 @@ SIGNATURES = {
     "hps_trace_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint]),
     "hps_trace_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int64_p, c_int64_p,
                                       ctypes.POINTER(ctypes.c_double)]),
+    "hps_batch_reserve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "hps_solve_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "ark_step_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_double,
+                                      ctypes.c_double, ctypes.POINTER(hps_ark_terms), ctypes.c_int, ctypes.c_void_p]),
     "hps_free": (None, [ctypes.c_void_p]),
     "hps_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }

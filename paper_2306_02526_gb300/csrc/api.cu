@@ -271,6 +271,8 @@ void hps_free(hps_handle *H) {
   H->trace.release();
   H->g_ark.destroy();
   H->g_solve.destroy();
+  H->g_ark_b.destroy();
+  H->g_solve_b.destroy();
   if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
   for (void *p : H->allocs) cudaFree(p);
   delete H;
@@ -522,6 +524,8 @@ int hps_set_persistent(hps_handle *H, int enable) {
   hps::drain_graph(H, H->g_solve);
   H->g_ark.destroy();  // recorded graphs hold the other kernel sequence
   H->g_solve.destroy();
+  H->g_ark_b.destroy();
+  H->g_solve_b.destroy();
   H->persistent = enable != 0;
   return HPS_OK;
 }
@@ -577,6 +581,8 @@ int hps_set_graph(hps_handle *H, int enable) {
   hps::drain_graph(H, H->g_solve);
   H->g_ark.destroy();
   H->g_solve.destroy();
+  H->g_ark_b.destroy();
+  H->g_solve_b.destroy();
   H->graph_mode = enable != 0;
   return HPS_OK;
 }
@@ -599,14 +605,54 @@ int ark_step(hps_handle *H, double *u, double t, double dt, const hps_ark_terms 
                      (cudaStream_t)stream);
 }
 
+int hps_batch_reserve(hps_handle *H, int R) {
+  if (!H) return HPS_EINVAL;
+  return hps::batch_reserve(H, R);
+}
+
+int hps_solve_batch(hps_handle *H, int R, const double *rhs, const double *f, double *u, int refine,
+                    hps_stream_t stream) {
+  if (!H || !rhs || !u || R <= 0 || R > H->batch.Rmax || refine < 0 || refine > 8) return HPS_EINVAL;
+  const uint64_t key[hps::GraphEntry::kKey] = {(uint64_t)rhs, (uint64_t)f, (uint64_t)u, (uint64_t)R,
+                                               (uint64_t)refine, 0, 0, 2};
+  return run_graphed(H, H->g_solve_b, key,
+                     [&](cudaStream_t s) { return hps::solve_batch(H, R, rhs, f, u, refine, s); },
+                     (cudaStream_t)stream);
+}
+
+int ark_step_batch(hps_handle *H, int R, double *u, double t, double dt, const hps_ark_terms *terms, int refine,
+                   hps_stream_t stream) {
+  if (!H || !u || !(dt > 0.0) || !std::isfinite(t) || R <= 0 || R > H->batch.Rmax || refine < 0 || refine > 8)
+    return HPS_EINVAL;
+  if (std::fabs(0.25 * dt - H->gamma_dt) > 1e-12 * H->gamma_dt) return HPS_EDT;
+  const int gk = terms ? terms->g_kind : HPS_G_NONE;
+  if (gk < HPS_G_NONE || gk > HPS_G_BURGERS) return HPS_EINVAL;
+  hps::ArkTable tab;
+  const Tableau &tb = tableau();
+  std::memcpy(tab.A, tb.A, sizeof(tab.A));
+  std::memcpy(tab.Ah, tb.Ah, sizeof(tab.Ah));
+  std::memcpy(tab.b, tb.b, sizeof(tab.b));
+  const uint64_t key[hps::GraphEntry::kKey] = {
+      (uint64_t)u, (uint64_t)(terms ? terms->q : nullptr), (uint64_t)(terms ? terms->f : nullptr),
+      (uint64_t)gk | ((uint64_t)R << 8) | ((uint64_t)refine << 24), bits(terms ? terms->g_param[0] : 0.0),
+      bits(terms ? terms->g_param[1] : 0.0), bits(dt), 3};
+  return run_graphed(H, H->g_ark_b, key,
+                     [&](cudaStream_t s) { return hps::ark_batch(H, R, u, dt, terms, refine, tab, s); },
+                     (cudaStream_t)stream);
+}
+
 int hps_trace_enable(hps_handle *H, unsigned mask) {
   if (!H) return HPS_EINVAL;
   H->trace.drain();
   hps::drain_graph(H, H->g_ark);
   hps::drain_graph(H, H->g_solve);
+  hps::drain_graph(H, H->g_ark_b);
+  hps::drain_graph(H, H->g_solve_b);
   if (mask != H->trace.mask) {  // recorded graphs carry the old timing events
     H->g_ark.destroy();
     H->g_solve.destroy();
+    H->g_ark_b.destroy();
+    H->g_solve_b.destroy();
   }
   H->trace.mask = mask;
   for (int i = 0; i < hps::kNumSlots; ++i) {
@@ -622,6 +668,8 @@ int hps_trace_read(hps_handle *H, int kernel, int64_t *launches, int64_t *timed,
   H->trace.drain();
   hps::drain_graph(H, H->g_ark);
   hps::drain_graph(H, H->g_solve);
+  hps::drain_graph(H, H->g_ark_b);
+  hps::drain_graph(H, H->g_solve_b);
   if (launches) *launches = H->trace.launches[kernel];
   if (timed) *timed = H->trace.timed[kernel];
   if (total_ms) *total_ms = H->trace.ms[kernel];

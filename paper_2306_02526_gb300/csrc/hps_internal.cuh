@@ -120,6 +120,24 @@ struct OpSet {
   int n_up = 0, n_down = 0;
 };
 
+// FP32 copy of an operator set (same layouts, leading dimensions and strides as the FP64 one).
+struct OpSet32 {
+  float *Ainv = nullptr, *Sleaf = nullptr;
+  std::vector<float *> X, S, Tcat;  // per level
+};
+
+// Work buffers of the batched mixed-precision path for up to Rmax right-hand sides.  Vectors
+// with R columns are stored RHS-fastest: entry (point i, column j) at i*R + j.
+struct Batch {
+  int Rmax = 0;
+  OpSet32 impl32, ident32;
+  double *ustage = nullptr, *Rb = nullptr, *KL = nullptr, *KE = nullptr, *r = nullptr;  // FP64
+  float *g32 = nullptr, *w32 = nullptr;
+  std::vector<float *> h32, w332;  // per level
+  float *partial32 = nullptr;
+  size_t partial_len = 0;          // floats
+};
+
 // A kernel sequence recorded into a CUDA graph (hps_set_graph), replayed for equal arguments.
 struct GraphEntry {
   static constexpr int kKey = 8;
@@ -193,7 +211,8 @@ struct hps_handle {
   bool stamp_tasks = false;
   bool graph_mode = false;
   cudaStream_t cap_stream = nullptr;
-  hps::GraphEntry g_ark, g_solve;
+  hps::GraphEntry g_ark, g_solve, g_ark_b, g_solve_b;
+  hps::Batch batch;
 };
 
 namespace hps {
@@ -223,6 +242,15 @@ int persistent_grid(hps_handle *H);
 int build_tasks(hps_handle *H, OpSet &ops);
 int merge_persistent(hps_handle *H, const OpSet &ops, bool upward, double *gvec, cudaStream_t st);
 int selftest_barrier(hps_handle *H, cudaStream_t st);
+
+// ---- batched mixed-precision path (batched.cu) ---------------------------------------------
+int batch_reserve(hps_handle *H, int R);
+int solve_batch(hps_handle *H, int R, const double *rhs, const double *f, double *u, int refine, cudaStream_t st);
+struct ArkTable {
+  double A[6][6], Ah[6][6], b[6];
+};
+int ark_batch(hps_handle *H, int R, double *u, double dt, const hps_ark_terms *terms, int refine, const ArkTable &tb,
+              cudaStream_t st);
 int leaf_eval(hps_handle *H, const double *u, double *KL, double *KE, const double *q, double dt,
               int g_kind, double gp0, double gp1, cudaStream_t st);
 

@@ -188,3 +188,30 @@ class HPSSolver:
         check(lib().ark_step(self._h, _dptr(u, self.N, "u"), float(t), float(dt), ctypes.byref(terms),
                              _stream_ptr(stream)), "ark_step")
         return u
+
+    # ---- batched mixed precision -----------------------------------------------------------
+    def batch_reserve(self, R):
+        """FP32 operator copies and R-column work buffers (hps_batch_reserve)."""
+        check(lib().hps_batch_reserve(self._h, int(R)), "hps_batch_reserve")
+
+    def solve_batch(self, rhs, f=None, u=None, refine=2, stream=None):
+        """R solves at once: rhs (N_int, R), f (N_bd, R) or None -> u (N, R) (hps_solve_batch)."""
+        import torch
+        R = rhs.shape[1]
+        if u is None:
+            u = torch.empty((self.N, R), dtype=torch.float64, device="cuda")
+        check(lib().hps_solve_batch(self._h, R, _dptr(rhs, self.N_int * R, "rhs"), _dptr(f, self.N_bd * R, "f"),
+                                    _dptr(u, self.N * R, "u"), int(refine), _stream_ptr(stream)), "hps_solve_batch")
+        return u
+
+    def ark_step_batch(self, u, t, dt, q=None, f=None, g=None, g_param=(1.0, 1.0), refine=2, stream=None):
+        """ARK step on R states u (N, R) in place (ark_step_batch); q (6, N_int, R), f (6, N_bd, R)."""
+        R = u.shape[1]
+        terms = _lib.hps_ark_terms()
+        terms.q = _dptr(q, 6 * self.N_int * R, "q")
+        terms.f = _dptr(f, 6 * self.N_bd * R, "f")
+        terms.g_kind = G_KINDS[g]
+        terms.g_param[0], terms.g_param[1] = float(g_param[0]), float(g_param[1])
+        check(lib().ark_step_batch(self._h, R, _dptr(u, self.N * R, "u"), float(t), float(dt), ctypes.byref(terms),
+                                   int(refine), _stream_ptr(stream)), "ark_step_batch")
+        return u

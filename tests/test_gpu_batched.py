@@ -1,0 +1,149 @@
+"""Batched mixed precision (FP32 sweeps + FP64 refinement, R right-hand sides) against the
+FP64 path and the oracle.  Tolerance of the mixed path: 1e-10 relative max-norm."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_util import need_gpu, rel_max, to_dev
+from oracle import ark as oark
+from oracle import nonlinear
+from oracle.grid import Grid
+from oracle.hps import HPS
+from paper_2306_02526_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+def _solver(torch, n1, n2, p, coef, gdt, dom=(0.0, 1.0, 0.0, 1.0)):
+    from paper_2306_02526_gb300 import hps
+    tree = hps.Tree(n1, n2, *dom)
+    cg = {k: (to_dev(torch, v) if np.ndim(v) else float(v)) for k, v in coef.items()}
+    return hps.HPSSolver(tree, p, cg, gdt)
+
+
+@pytest.mark.parametrize("n1,n2,p,R,nodal", [(1, 1, 5, 1, False), (2, 2, 7, 3, True), (8, 4, 9, 8, True),
+                                             (16, 16, 12, 32, False), (8, 16, 16, 5, True)])
+def test_solve_batch_matches_fp64(n1, n2, p, R, nodal):
+    torch = need_gpu()
+    g = Grid(n1, n2, p, -0.5, 0.5, 0.0, 1.0)
+    coef = workloads.random_coefficients(p, g.N_int) if nodal else {"a11": 1.0, "a22": 0.7, "a1": 0.3, "a2": 0.0,
+                                                                    "a0": -0.5}
+    S = _solver(torch, n1, n2, p, coef, 0.013, (-0.5, 0.5, 0.0, 1.0))
+    S.batch_reserve(R)
+    r = np.random.default_rng(R + p)
+    rhs = r.standard_normal((g.N_int, R))
+    f = r.standard_normal((g.boundary_indices().size, R))
+    errs = []
+    for refine in (0, 1, 2):
+        u = S.solve_batch(to_dev(torch, rhs), to_dev(torch, f), refine=refine).cpu().numpy()
+        err = 0.0
+        for j in range(R):
+            want = S.solve(to_dev(torch, rhs[:, j].copy()), to_dev(torch, f[:, j].copy())).cpu().numpy()
+            err = max(err, rel_max(u[:, j], want))
+        errs.append(err)
+    assert errs[0] < 1e-4               # FP32 sweep alone
+    assert errs[2] <= TOL, errs         # refined to FP64 accuracy
+    assert errs[2] < errs[0]
+    if g.N <= 1500:
+        want = HPS(g, coef, 0.013).solve(rhs[:, 0], f[:, 0])
+        assert rel_max(S.solve_batch(to_dev(torch, rhs), to_dev(torch, f), refine=2).cpu().numpy()[:, 0], want) <= TOL
+    S.close()
+
+
+def test_ark_batch_heat_matches_oracle():
+    """4 different initial states of the heat problem (4x4 leaves, p = 8), 20 ARK steps."""
+    torch = need_gpu()
+    from paper_2306_02526_gb300 import hps
+    wl = workloads.Heat4x4()
+    g = Grid(wl.n1, wl.n2, wl.p)
+    X, Y = g.coords()
+    I, bd = np.arange(g.N_int), g.boundary_indices()
+    coef = wl.coef(X[I], Y[I])
+    R = 4
+    S = _solver(torch, wl.n1, wl.n2, wl.p, coef, 0.25 * wl.dt)
+    S.batch_reserve(R)
+    c = hps.hps_ark_abscissae()
+    u0 = np.stack([wl.u0(X, Y, bd) * (1 + 0.25 * j) + 0.01 * j * np.sin(3 * X) * np.sin(2 * math.pi * Y)
+                   for j in range(R)], axis=1)
+    for j in range(R):
+        u0[bd, j] = 0.0
+    ug = to_dev(torch, u0)
+    prob = oark.Problem(g, coef, q=lambda t: wl.q(X, Y, t)[I])
+    Hi, Hid = HPS(g, coef, 0.25 * wl.dt), HPS(g, coef, 0.0)
+    uo = [u0[:, j].copy() for j in range(R)]
+    t = 0.0
+    for n in range(20):
+        q = np.stack([np.repeat(wl.q(X, Y, t + cj * wl.dt)[I][:, None], R, axis=1) for cj in c])
+        S.ark_step_batch(ug, t, wl.dt, q=to_dev(torch, q), refine=2)
+        for j in range(R):
+            uo[j], _ = oark.ark_step(prob, Hi, Hid, uo[j], t, wl.dt)
+        t += wl.dt
+    got = ug.cpu().numpy()
+    for j in range(R):
+        assert rel_max(got[:, j], uo[j]) <= TOL
+    S.close()
+
+
+@pytest.mark.parametrize("gname", ["allen_cahn", "burgers"])
+def test_ark_batch_varcoef_inhomogeneous_matches_fp64(gname):
+    torch = need_gpu()
+    from paper_2306_02526_gb300 import hps
+    n1, n2, p, dt, R = 8, 4, 10, 0.02, 6
+    g = Grid(n1, n2, p)
+    X, Y = g.coords()
+    I, bd = np.arange(g.N_int), g.boundary_indices()
+    coef = workloads.VarCoef128().coef(X[I], Y[I])
+    S = _solver(torch, n1, n2, p, coef, 0.25 * dt)
+    S.batch_reserve(R)
+    c = hps.hps_ark_abscissae()
+    gp = (0.8, -0.3)
+    qf = lambda t: np.cos(X[I] + t) * np.sin(2 * Y[I])
+    ff = lambda t: (np.sin(X + 2 * Y) * (1 + t))[bd]
+    u0 = np.stack([0.3 * np.sin(math.pi * X) * np.cos(Y + j) for j in range(R)], axis=1)
+    u0[bd, :] = ff(0.0)[:, None]
+    ub = to_dev(torch, u0)
+    us = [to_dev(torch, u0[:, j].copy()) for j in range(R)]
+    t = 0.0
+    for n in range(4):
+        qs = np.stack([qf(t + cj * dt) for cj in c])
+        fs = np.stack([ff(t + cj * dt) for cj in c])
+        qb = np.repeat(qs[:, :, None], R, axis=2)
+        fb = np.repeat(fs[:, :, None], R, axis=2)
+        S.ark_step_batch(ub, t, dt, q=to_dev(torch, qb), f=to_dev(torch, fb), g=gname, g_param=gp, refine=2)
+        for j in range(R):
+            S.ark_step(us[j], t, dt, q=to_dev(torch, qs.reshape(-1)), f=to_dev(torch, fs.reshape(-1)), g=gname,
+                       g_param=gp)
+        t += dt
+    got = ub.cpu().numpy()
+    for j in range(R):
+        assert rel_max(got[:, j], us[j].cpu().numpy()) <= TOL
+    S.close()
+
+
+def test_ark_batch_full_size_allen_cahn():
+    """The bench workload (64x64 leaves, p = 16) with 8 seeded states: 2 batched mixed steps
+    against the FP64 path column by column."""
+    torch = need_gpu()
+    wl = workloads.AllenCahn64()
+    from paper_2306_02526_gb300 import hps
+    tree = hps.Tree(wl.n1, wl.n2)
+    N, N_int, N_bd = hps.hps_sizes(tree, wl.p)
+    x, y = hps.hps_coords(tree, wl.p)
+    bidx = hps.hps_boundary_index(tree, wl.p)
+    S = hps.HPSSolver(tree, wl.p, {"a11": wl.eps, "a22": wl.eps}, 0.25 * wl.dt)
+    R = 8
+    S.batch_reserve(R)
+    u0 = np.stack([workloads.uniform_state(j, N, bidx) for j in range(R)], axis=1)
+    ub = to_dev(torch, u0)
+    us = [to_dev(torch, u0[:, j].copy()) for j in range(R)]
+    for n in range(2):
+        S.ark_step_batch(ub, n * wl.dt, wl.dt, g="allen_cahn", g_param=(1.0, 0.0), refine=2)
+        for j in range(R):
+            S.ark_step(us[j], n * wl.dt, wl.dt, g="allen_cahn", g_param=(1.0, 0.0))
+    got = ub.cpu().numpy()
+    for j in range(R):
+        assert rel_max(got[:, j], us[j].cpu().numpy()) <= TOL
+    S.close()
