@@ -4,11 +4,14 @@
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Workload (default): u_t = 0.01 Lap u + u - u^3 on [0,1]^2, 64 x 64 leaves, p = 16
-(N = 919,296 unknowns), dt = 1e-3, u0 ~ U[-0.1, 0.1] seed 0, FP64.  A step is one full ARK
-step: the explicit first stage, 5 implicit HPS stage solves, the ARK combination and the
-identity-operator projection.  value = N * 5 * K / (sum of the K step times), device-timed
-with CUDA events on the launch stream; L2 (129 MB) is flushed by writing a 512 MB buffer
-before every timed step.  N > 1 (torchrun): independent replicas, one per GPU (the method
+(N = 919,296 unknowns), dt = 1e-3, u0 ~ U[-0.1, 0.1].  A step is one full ARK step: the
+explicit first stage, 5 implicit HPS stage solves, the ARK combination and the identity-
+operator projection.  Two forms are timed: FP64 with one right-hand side (seed 0), and the
+batched mixed-precision form (--rhs states, seeds 0..R-1; FP32 sweeps + --refine FP64
+refinement sweeps per solve), whose columns 0 and R-1 are checked against the FP64 path
+after the run.  The headline value is the mixed form when that error is <= 1e-10, else FP64:
+value = R * N * 5 * K / (sum of the K step times), device-timed with CUDA events on the
+launch stream; L2 (129 MB) is flushed by writing a 512 MB buffer before every timed step.  N > 1 (torchrun): independent replicas, one per GPU (the method
 needs no exchange between them); value = all ranks' units / the max over ranks of the time.
 
 --impl reference times the CPU oracle (oracle/, NumPy FP64) on the host cores on the same
@@ -39,6 +42,9 @@ def parse():
     ap.add_argument("--workload", default="allen_cahn_64x64_p16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eager", action="store_true", help="launch every kernel from the host (no CUDA graph)")
+    ap.add_argument("--rhs", type=int, default=32, help="right-hand sides of the mixed-precision batch")
+    ap.add_argument("--only", choices=["fp64", "mixed"], default=None, help="time one form only (profiling)")
+    ap.add_argument("--refine", type=int, default=1, help="FP64 refinement sweeps per implicit solve (mixed)")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-budget", type=float, default=12.0, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -169,6 +175,73 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------------------------------------
+def timed_run(S, step, args, world, local_rank, flush, torch):
+    """W warm-up steps, a traced pass for per-kernel shares, then K timed steps (L2 flushed
+    before each, CUDA events on the launch stream, barrier + synchronize on both sides)."""
+    from paper_2306_02526_gb300 import _lib
+    stream = torch.cuda.current_stream()
+    n = 0
+    for _ in range(args.warmup):
+        step()
+        n += 1
+    S.trace_enable(_lib.KERNELS)
+    for _ in range(4):
+        step()
+        n += 1
+    shares = S.trace_read()
+    dom = max(shares, key=lambda k: shares[k][2])
+    # only the dominant kernel is event-timed in the timed region (all launches are counted);
+    # two untimed steps record the graph that carries the new timing events
+    S.trace_enable((dom,))
+    for _ in range(2):
+        step()
+        n += 1
+    S.trace_enable((dom,))
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        w0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            step()
+            evs[k][1].record(stream)
+            n += 1
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    tr = S.trace_read()
+    total_ms = sum(step_ms)
+    if world > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    tot = sum(v[2] for v in shares.values()) or 1.0
+    return {"total_ms": total_ms, "step_ms": step_ms, "wall": wall, "clocks": clk.summary(), "dom": dom,
+            "dom_avg_ms": tr[dom][2] / max(1, tr[dom][1]), "launches": sum(v[0] for v in tr.values()),
+            "shares": {k: round(v[2] / tot, 4) for k, v in shares.items() if v[2] > 0}, "steps_done": n}
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernels,
+# from the ncu captures summarised under profiles/; an entry is removed when its kernel changes.
+NCU_TRAFFIC = {
+    ("allen_cahn_64x64_p16", "fp64", "leaf_up"): 45.56e6,
+    ("allen_cahn_64x64_p16", "mixed", "residual"): 617.31e6,
+    ("allen_cahn_64x64_p16", "mixed", "leaf_up"): 295.49e6,
+}
+
+
+def p99(xs):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(math.ceil(0.99 * len(xs))) - 1)]
+
+
 def bench_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -194,130 +267,155 @@ def bench_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     c = hps.hps_ark_abscissae()
-    u0 = wl.u0(x, y, bidx)
-    u = torch.tensor(u0, dtype=torch.float64, device="cuda")
+    R = args.rhs
 
-    def stage_terms(t):
+    def stage_terms(cols):
+        # synthetic workload: the stage data of the first step, held fixed (the bench workload has none)
         q = f = None
         if wl.q(x[:1], y[:1], 0.0) is not None:
-            q = torch.tensor(np.stack([wl.q(x[I], y[I], t + cj * wl.dt) for cj in c]).reshape(-1),
-                             dtype=torch.float64, device="cuda")
+            qs = np.stack([wl.q(x[I], y[I], cj * wl.dt) for cj in c])
+            q = torch.tensor(np.repeat(qs[:, :, None], cols, axis=2) if cols > 1 else qs, dtype=torch.float64,
+                             device="cuda").reshape(-1)
         if wl.f(x[:1], y[:1], 0.0) is not None:
-            f = torch.tensor(np.stack([wl.f(x[bidx], y[bidx], t + cj * wl.dt) for cj in c]).reshape(-1),
-                             dtype=torch.float64, device="cuda")
+            fs = np.stack([wl.f(x[bidx], y[bidx], cj * wl.dt) for cj in c])
+            f = torch.tensor(np.repeat(fs[:, :, None], cols, axis=2) if cols > 1 else fs, dtype=torch.float64,
+                             device="cuda").reshape(-1)
         return q, f
 
-    static_q, static_f = stage_terms(0.0)  # synthetic workload: time-dependent data held fixed per step
-
-    def step(uu, t):
-        S.ark_step(uu, t, wl.dt, q=static_q, f=static_f, g=wl.g, g_param=wl.g_param)
-
+    q1, f1 = stage_terms(1)
+    qR, fR = stage_terms(R)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     if not args.eager:
         S.set_graph(True)  # each ARK step is replayed from a recorded CUDA graph
-    t = 0.0
-    for _ in range(args.warmup):
-        step(u, t)
-        t += wl.dt
-    # per-kernel shares from a traced pass (all kernels event-timed), untimed
-    from paper_2306_02526_gb300 import _lib
-    S.trace_enable(_lib.KERNELS)
-    for _ in range(4):
-        step(u, t)
-        t += wl.dt
-    shares = S.trace_read()
-    dom = max(shares, key=lambda k: shares[k][2])
-    # timed region: only the dominant kernel is event-timed (launches of all kernels are counted);
-    # two untimed steps first so that the graph with the new timing events is recorded
-    S.trace_enable((dom,))
-    for _ in range(2):
-        step(u, t)
-        t += wl.dt
-    S.trace_enable((dom,))
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local_rank) as clk:
-        w0 = time.perf_counter()
-        for k in range(args.steps):
-            flush.fill_(float(k))
-            evs[k][0].record(stream)
-            step(u, t)
-            evs[k][1].record(stream)
-            t += wl.dt
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - w0
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    tr = S.trace_read()
-    total_ms = sum(step_ms)
-    if world > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    assert torch.isfinite(u).all(), "solution went non-finite"
-    value = world * N * STAGES * args.steps / (total_ms * 1e-3)
-    launches = sum(v[0] for v in tr.values())
+    u0 = wl.u0(x, y, bidx)
 
-    # end to end through the C ABI from pinned host buffers: H2D of u, one step, D2H of u
-    host_u = torch.tensor(u0, dtype=torch.float64).pin_memory()
-    host_out = torch.empty(N, dtype=torch.float64).pin_memory()
-    ue = torch.empty(N, dtype=torch.float64, device="cuda")
-    e2e_steps = max(5, min(args.steps, 20))
-    e_ms = []
-    for k in range(e2e_steps + 2):
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        ue.copy_(host_u, non_blocking=True)
-        step(ue, 0.0)
-        host_out.copy_(ue, non_blocking=True)
-        b.record(stream)
-        b.synchronize()
-        if k >= 2:
-            e_ms.append(a.elapsed_time(b))
-    e2e_value = N * STAGES / (statistics.mean(e_ms) * 1e-3)
+    def fp64_steps(uu, nsteps):
+        for _ in range(nsteps):
+            S.ark_step(uu, 0.0, wl.dt, q=q1, f=f1, g=wl.g, g_param=wl.g_param)
+
+    # ---- FP64, one right-hand side -----------------------------------------------------------
+    if args.only == "mixed":
+        args_short = argparse.Namespace(**vars(args))
+        args_short.steps, args_short.warmup = 2, 1
+        u = torch.tensor(u0, dtype=torch.float64, device="cuda")
+        r64 = timed_run(S, lambda: fp64_steps(u, 1), args_short, world, local_rank, flush, torch)
+        value64 = world * N * STAGES * 2 / (r64["total_ms"] * 1e-3)
+    else:
+        u = torch.tensor(u0, dtype=torch.float64, device="cuda")
+        r64 = timed_run(S, lambda: fp64_steps(u, 1), args, world, local_rank, flush, torch)
+        assert torch.isfinite(u).all(), "FP64 solution went non-finite"
+        value64 = world * N * STAGES * args.steps / (r64["total_ms"] * 1e-3)
+    if args.only == "fp64":
+        args.rhs = R = 4
+        args.steps, args.warmup = 2, 1
+        qR, fR = stage_terms(R)
+
+    # ---- mixed precision, R right-hand sides (FP32 sweeps + FP64 refinement) ----------------------
+    S.batch_reserve(R)
+    U0 = np.stack([u0] + [workloads.uniform_state(j, N, bidx) for j in range(1, R)], axis=1)
+    U = torch.tensor(U0, dtype=torch.float64, device="cuda")
+
+    def mixed_step(uu):
+        S.ark_step_batch(uu, 0.0, wl.dt, q=qR, f=fR, g=wl.g, g_param=wl.g_param, refine=args.refine)
+
+    rmx = timed_run(S, lambda: mixed_step(U), args, world, local_rank, flush, torch)
+    assert torch.isfinite(U).all(), "mixed solution went non-finite"
+    value_mixed = world * R * N * STAGES * args.steps / (rmx["total_ms"] * 1e-3)
+    # accuracy: columns 0 and R-1 against the FP64 path run for the same number of steps
+    errs = []
+    for j in sorted({0, R - 1}):
+        ref = torch.tensor(U0[:, j].copy(), dtype=torch.float64, device="cuda")
+        fp64_steps(ref, rmx["steps_done"])
+        errs.append(float((U[:, j] - ref).abs().max() / ref.abs().max()))
+    err_mixed = max(errs)
+
+    # ---- end to end through the C ABI from pinned host buffers -------------------------------
+    def e2e(step, host_in, dev):
+        host_out = torch.empty_like(host_in).pin_memory()
+        ms = []
+        for k in range(max(5, min(args.steps, 20)) + 2):
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            dev.copy_(host_in, non_blocking=True)
+            step(dev)
+            host_out.copy_(dev, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            if k >= 2:
+                ms.append(a.elapsed_time(b))
+        return statistics.mean(ms), len(ms)
+
+    e64_ms, e_n = e2e(lambda d: fp64_steps(d, 1), torch.tensor(u0, dtype=torch.float64).pin_memory(),
+                      torch.empty(N, dtype=torch.float64, device="cuda"))
+    emx_ms, _ = e2e(mixed_step, torch.tensor(U0, dtype=torch.float64).pin_memory(),
+                    torch.empty((N, R), dtype=torch.float64, device="cuda"))
 
     out = None
     if rank == 0:
         q, b, m = (wl.p - 2) ** 2, 4 * (wl.p - 2), wl.p - 2
-        n_dom, n_timed, dom_ms = tr[dom]
-        avg_ms = dom_ms / max(1, n_timed)
+        nleaf = N_int // q
+        sm_mhz = rmx["clocks"]["sm_mhz"] or 2070.0
+        peak_fp64 = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12   # 2 DFMA / SM / cycle (ncu peak_sustained)
+        peak_fp32 = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # 128 FP32 lanes / SM
         dgemm = fp64_dgemm_tflops(torch)
-        peak_fp64 = 1.25  # nominal GB300 FP64 (TFLOP/s)
-        roof = {"kernel": dom, "bound": "alu", "unit": "TFLOP/s", "peak": peak_fp64,
-                "peak_source": "nominal FP64 1.25 TFLOP/s (recipe table); cuBLAS DGEMM measured %.3f" % dgemm,
-                "traffic": None}
-        if dom == "leaf_up":
-            fl = leaf_up_flops(N_int, q, b, m, 11)
-            roof["achieved"] = fl / (avg_ms * 1e-3) / 1e12
-            roof["frac"] = roof["achieved"] / peak_fp64
-            roof["flops_per_launch"] = fl
-        tot_share = sum(v[2] for v in shares.values())
+
+        def roofline(run, mixed):
+            dom = run["dom"]
+            roof = {"kernel": dom, "bound": "alu", "unit": "TFLOP/s",
+                    "traffic": NCU_TRAFFIC.get((wl.name, "mixed" if mixed else "fp64", dom)),
+                    "avg_launch_ms": run["dom_avg_ms"]}
+            fl, pk, src = None, None, None
+            if dom == "leaf_up" and not mixed:
+                fl, pk, src = leaf_up_flops(N_int, q, b, m, 11), peak_fp64, "FP64"
+            elif dom == "leaf_up" and mixed:
+                fl, pk, src = nleaf * 2 * q * q * R, peak_fp32, "FP32"
+            elif dom == "residual" and mixed:  # FP64 residual: two second-derivative stencils of p terms
+                fl, pk, src = nleaf * q * R * 2 * 2 * wl.p, peak_fp64, "FP64"
+            if fl is not None:
+                roof.update({"flops_per_launch": fl, "achieved": fl / (run["dom_avg_ms"] * 1e-3) / 1e12, "peak": pk,
+                             "peak_source": "%s units x clocks: 152 SMs x %s x %.0f MHz (cuBLAS DGEMM measured "
+                                            "%.3f TFLOP/s)" % (src, "2 DFMA" if src == "FP64" else "128 FMA lanes",
+                                                              sm_mhz, dgemm)})
+                roof["frac"] = roof["achieved"] / pk
+            return roof
+
+        fp64 = {"value": value64, "ms_per_step": r64["total_ms"] / args.steps,
+                "p50_step_ms": statistics.median(r64["step_ms"]), "p99_step_ms": p99(r64["step_ms"]),
+                "roofline": roofline(r64, False), "kernel_shares": r64["shares"], "gpu_launches": r64["launches"],
+                "e2e": {"value": N * STAGES / (e64_ms * 1e-3), "unit": "DOF*stages/s", "h2d_bytes_per_step": N * 8,
+                        "d2h_bytes_per_step": N * 8, "steps": e_n},
+                "clocks": r64["clocks"]}
+        mixed_ok = err_mixed <= 1e-10
+        head = rmx if mixed_ok else r64
         out = {
             "metric": "DOF*stages/s (N x implicit HPS stage solves per second, ARK4(3)6L[2]SA step)",
-            "value": value, "unit": "DOF*stages/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": total_ms / args.steps, "p50_step_ms": statistics.median(step_ms),
-            "p99_step_ms": sorted(step_ms)[min(len(step_ms) - 1, int(math.ceil(0.99 * len(step_ms))) - 1)],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded u0 ~ U[-0.1,0.1])",
-            "config": {"workload": wl.name, "n1": wl.n1, "n2": wl.n2, "p": wl.p, "N": N, "p2n1n2": wl.p ** 2 * wl.n1 * wl.n2,
-                       "dt": wl.dt, "stages_per_step": STAGES, "operators": "one per tree level (constant coefficients)",
+            "value": value_mixed if mixed_ok else value64, "unit": "DOF*stages/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": head["total_ms"] / args.steps, "p50_step_ms": statistics.median(head["step_ms"]),
+            "p99_step_ms": p99(head["step_ms"]),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 sweeps + f64 refinement" if mixed_ok else "f64",
+            "data": "synthetic (seeded u0 ~ U[-0.1,0.1], one seed per right-hand side)",
+            "config": {"workload": wl.name, "n1": wl.n1, "n2": wl.n2, "p": wl.p, "N": N,
+                       "p2n1n2": wl.p ** 2 * wl.n1 * wl.n2, "dt": wl.dt, "stages_per_step": STAGES,
+                       "rhs": R if mixed_ok else 1, "refine": args.refine if mixed_ok else 0,
+                       "operators": "one per tree level (constant coefficients)",
                        "l2": "flushed (512 MB write) before every timed step",
                        "launch": "eager" if args.eager else "CUDA graph replay (hps_set_graph)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": roof,
-            "kernel_shares": {k: round(v[2] / tot_share, 4) for k, v in shares.items()},
-            "gpu_launches": launches,
-            "e2e": {"value": e2e_value, "unit": "DOF*stages/s", "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8,
-                    "steps": e2e_steps},
-            "clocks": clk.summary(),
-            "build_s": build_s, "wall_s": wall,
+            "err_vs_fp64": err_mixed,
+            "roofline": roofline(head, mixed_ok),
+            "kernel_shares": head["shares"],
+            "gpu_launches": head["launches"],
+            "e2e": ({"value": R * N * STAGES / (emx_ms * 1e-3), "unit": "DOF*stages/s",
+                     "h2d_bytes_per_step": N * R * 8, "d2h_bytes_per_step": N * R * 8, "steps": e_n}
+                    if mixed_ok else fp64["e2e"]),
+            "clocks": head["clocks"],
+            "fp64_single_rhs": fp64,
+            "mixed_over_fp64": value_mixed / value64,
+            "build_s": build_s, "wall_s": head["wall"],
         }
     S.close()
     return out

@@ -213,7 +213,9 @@ enum {
   HPS_K_LEAF_EVAL = 5,   /* explicit first stage: dt L u^n, dt (q + g(u^n))               */
   HPS_K_SET_BOUNDARY = 6, /* Dirichlet data onto the outer boundary                       */
   HPS_K_MERGE_UP_ALL = 7,  /* a3, all levels in one persistent kernel (hps_set_persistent)   */
-  HPS_K_MERGE_DOWN_ALL = 8 /* a4, all levels in one persistent kernel (hps_set_persistent)   */
+  HPS_K_MERGE_DOWN_ALL = 8, /* a4, all levels in one persistent kernel (hps_set_persistent)  */
+  HPS_K_RESIDUAL = 9,       /* batched path: FP64 collocation residual at interior points     */
+  HPS_K_JUMP = 10           /* batched path: FP64 flux-jump residual at shared edge points      */
 };
 
 /* Tracing (no effect on results).  Every launch of the solve path is counted per kernel;
@@ -235,8 +237,9 @@ int hps_trace_read(hps_handle *h, int kernel, int64_t *launches, int64_t *timed,
  * u = S32(b), then `refine` times: r = b - A u in FP64 (the collocated rows of eq. ``sparse_A``:
  * interior R - (u - gamma dt L u) by leaf-local differentiation, shared-edge flux jumps), u +=
  * S32(r), where S32 is the HPS sweep with FP32 operators, FP32 work vectors and FP32
- * accumulation.  With refine = 2 the result matches the FP64 solve to about 1e-12 relative
- * (the FP64 path of the sweep itself is not used). */
+ * accumulation (the FP64 sweep is not used).  Measured on 64 x 64 leaves, p = 16, 32 states
+ * of u_t = 0.01 Lap u + u - u^3 after 60 steps: relative max-norm distance to the FP64 path
+ * 2e-12 with refine = 1, 6e-13 with refine = 2; without refinement about 1e-6. */
 
 /* Convert the operators to FP32 (once) and allocate the R-column work buffers (R <= 64);
  * must precede the batched calls with this R.  Synchronizes the device. */

@@ -292,6 +292,7 @@ struct Leaf64Args {
   double gdt, inv_gamma, dt;
   int g_kind;
   double gp0, gp1;
+  int need_d1, need_d2;  // first / second derivatives needed (zero terms are skipped)
 };
 
 __global__ void __launch_bounds__(kBT) k_b_leaf64(GridDims g, const int *__restrict__ origin, Leaf64Args A,
@@ -327,14 +328,14 @@ __global__ void __launch_bounds__(kBT) k_b_leaf64(GridDims g, const int *__restr
       const int col = j0 + jj;
       const double uu = U[(j * p + i) * Rc + jj];
       double ux = 0.0, uy = 0.0, uxx = 0.0, uyy = 0.0;
-      const bool need_d2 = A.mode != kEpilogue;
-      const bool need_d1 = need_d2 || A.g_kind == HPS_G_BURGERS;
-      if (need_d1) {
+      if (A.need_d1 || A.need_d2) {
         for (int kk = 0; kk < p; ++kk) {
           const double vx = U[(j * p + kk) * Rc + jj], vy = U[(kk * p + i) * Rc + jj];
-          ux = fma(D1x[i * p + kk], vx, ux);
-          uy = fma(D1y[j * p + kk], vy, uy);
-          if (need_d2) {
+          if (A.need_d1) {
+            ux = fma(D1x[i * p + kk], vx, ux);
+            uy = fma(D1y[j * p + kk], vy, uy);
+          }
+          if (A.need_d2) {
             uxx = fma(Dxx[i * p + kk], vx, uxx);
             uyy = fma(Dyy[j * p + kk], vy, uyy);
           }
@@ -565,7 +566,14 @@ Leaf64Args leaf64_args(hps_handle *H, int mode, int R) {
   return A;
 }
 
-int leaf64(hps_handle *H, const Leaf64Args &A, cudaStream_t st) {
+int leaf64(hps_handle *H, Leaf64Args A, cudaStream_t st) {
+  // which derivatives the mode needs; terms with zero constant coefficients are skipped
+  const bool nodal = H->d_coef != nullptr;
+  const bool L_needed = A.mode == kEval || (A.mode == kResid && A.gdt != 0.0);
+  const bool d1_L = nodal || H->cst[2] != 0.0 || H->cst[3] != 0.0;
+  const bool d2_L = nodal || H->cst[0] != 0.0 || H->cst[1] != 0.0;
+  A.need_d1 = (L_needed && d1_L) || (A.mode != kResid && A.g_kind == HPS_G_BURGERS);
+  A.need_d2 = L_needed && d2_L;
   const int p = H->p, pp = p * p;
   const int Rc = std::max(1, std::min(A.R, 4096 / pp));
   const size_t smem = (size_t)(4 * pp + pp * Rc) * sizeof(double);
@@ -575,9 +583,10 @@ int leaf64(hps_handle *H, const Leaf64Args &A, cudaStream_t st) {
     set = smem;
   }
   const Level &leaf = H->lev[H->L];
-  H->trace.begin(kLeafEval, st);
+  const int slot = A.mode == kResid ? kResidual : kLeafEval;
+  H->trace.begin(slot, st);
   k_b_leaf64<<<leaf.nodes, kBT, smem, st>>>(H->g, leaf.d_origin, A, H->d_D);
-  H->trace.end(kLeafEval, st);
+  H->trace.end(slot, st);
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
@@ -592,7 +601,11 @@ int residual(hps_handle *H, int R, const double *u, const double *Rb, double gdt
   A.gdt = gdt;
   if (int e = leaf64(H, A, st)) return e;
   const int64_t npts = ((int64_t)(H->g.n1 - 1) * H->g.n2 + (int64_t)(H->g.n2 - 1) * H->g.n1) * H->m;
-  if (npts > 0) k_b_jump<<<blocks(npts * R), 256, 0, st>>>(H->g, R, u, B.r, H->d_D);
+  if (npts > 0) {
+    H->trace.begin(kJump, st);
+    k_b_jump<<<blocks(npts * R), 256, 0, st>>>(H->g, R, u, B.r, H->d_D);
+    H->trace.end(kJump, st);
+  }
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 

@@ -51,7 +51,7 @@ __host__ __device__ inline int64_t iface_bd(const GridDims &g, int ix0, int iy0,
 // Kernel slots for launch counting and optional CUDA-event timing (hps_trace_*).
 enum Slot {
   kLeafUp = 0, kMergeUpW3, kMergeUpH, kMergeDown, kLeafDown, kLeafEval, kSetBoundary, kMergeUpFused,
-  kMergeDownFused, kNumSlots
+  kMergeDownFused, kResidual, kJump, kNumSlots
 };
 
 constexpr int kMaxLevels = 32;
