@@ -52,13 +52,17 @@ def parse():
 
 # ---------------------------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline and the reference arm)
+SAMPLE_LEAVES = 64 * 64  # larger workloads are timed on a 32 x 32-leaf piece with the same p and coefficients
+
+
 def oracle_setup(wname):
     import numpy as np
     from oracle.grid import Grid
     from oracle.hps import HPS
     from paper_2306_02526_gb300 import workloads
     wl = workloads.WORKLOADS[wname]
-    g = Grid(wl.n1, wl.n2, wl.p)
+    n1, n2 = (wl.n1, wl.n2) if wl.n1 * wl.n2 <= SAMPLE_LEAVES else (32, 32)
+    g = Grid(n1, n2, wl.p)
     X, Y = g.coords()
     I = np.arange(g.N_int)
     coef = wl.coef(X[I], Y[I])
@@ -79,7 +83,7 @@ def cpu_sample(wname, budget):
         el = time.perf_counter() - t0
         if el >= budget:
             break
-    return {"solves": n, "seconds": el, "N": g.N, "build_s": build_s}
+    return {"solves": n, "seconds": el, "N": g.N, "build_s": build_s, "leaves": "%dx%d" % (g.n1, g.n2)}
 
 
 def run_cpu_sample_subprocess(wname, budget):
@@ -330,6 +334,43 @@ def bench_ours(args, rank, world, local_rank):
         errs.append(float((U[:, j] - ref).abs().max() / ref.abs().max()))
     err_mixed = max(errs)
 
+    # ---- per-node operators: one right-hand side through the FP32 sweep (HBM-bound) --------------
+    single = None
+    if S.nodal:
+        rhs1 = torch.tensor(np.random.default_rng(3).uniform(-0.1, 0.1, (N_int, 1)), dtype=torch.float64,
+                            device="cuda")
+        u1 = torch.empty((N, 1), dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            S.solve_batch(rhs1, u=u1, refine=args.refine)
+        S.trace_enable(("leaf_up",))
+        for _ in range(2):
+            S.solve_batch(rhs1, u=u1, refine=args.refine)
+        S.trace_enable(("leaf_up",))
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            S.solve_batch(rhs1, u=u1, refine=args.refine)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        tr1 = S.trace_read()
+        solve_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+        q_, b_ = (wl.p - 2) ** 2, 4 * (wl.p - 2)
+        nleaf_ = N_int // q_
+        ld32 = (q_ + 3) // 4 * 4
+        # algorithmic bytes of one k_b_leaf_up launch (R = 1): the leaf's FP32 A_ii^{-1} (stored
+        # transposed with rows padded to 4) + FP64 right-hand side in + FP32 w and fluxes out
+        bytes_up = nleaf_ * (q_ * ld32 * 4 + q_ * 8 + q_ * 4 + b_ * 4)
+        avg_up = tr1["leaf_up"][2] / max(1, tr1["leaf_up"][1])
+        hbm = measured_peaks().get("hbm_gbs", 6800.0)
+        single = {"solve_ms": solve_ms, "refine": args.refine,
+                  "value": N / (solve_ms * 1e-3), "unit": "DOF*solves/s",
+                  "roofline": {"kernel": "leaf_up", "bound": "hbm", "unit": "GB/s", "bytes_per_launch": bytes_up,
+                               "avg_launch_ms": avg_up, "achieved": bytes_up / (avg_up * 1e-3) / 1e9, "peak": hbm,
+                               "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                               "frac": bytes_up / (avg_up * 1e-3) / 1e9 / hbm,
+                               "traffic": NCU_TRAFFIC.get((wl.name, "single", "leaf_up"))}}
+
     # ---- end to end through the C ABI from pinned host buffers -------------------------------
     def e2e(step, host_in, dev):
         host_out = torch.empty_like(host_in).pin_memory()
@@ -371,8 +412,9 @@ def bench_ours(args, rank, world, local_rank):
                 fl, pk, src = leaf_up_flops(N_int, q, b, m, 11), peak_fp64, "FP64"
             elif dom == "leaf_up" and mixed:
                 fl, pk, src = nleaf * 2 * q * q * R, peak_fp32, "FP32"
-            elif dom == "residual" and mixed:  # FP64 residual: two second-derivative stencils of p terms
-                fl, pk, src = nleaf * q * R * 2 * 2 * wl.p, peak_fp64, "FP64"
+            elif dom == "residual" and mixed:  # FP64 residual: p-term stencils (2 second, 2 first derivatives)
+                first = S.nodal or any(float(coef.get(k_, 0.0)) != 0.0 for k_ in ("a1", "a2") if np.ndim(coef.get(k_, 0.0)) == 0)
+                fl, pk, src = nleaf * q * R * (4 if first else 2) * 2 * wl.p, peak_fp64, "FP64"
             if fl is not None:
                 roof.update({"flops_per_launch": fl, "achieved": fl / (run["dom_avg_ms"] * 1e-3) / 1e12, "peak": pk,
                              "peak_source": "%s units x clocks: 152 SMs x %s x %.0f MHz (cuBLAS DGEMM measured "
@@ -401,7 +443,8 @@ def bench_ours(args, rank, world, local_rank):
             "config": {"workload": wl.name, "n1": wl.n1, "n2": wl.n2, "p": wl.p, "N": N,
                        "p2n1n2": wl.p ** 2 * wl.n1 * wl.n2, "dt": wl.dt, "stages_per_step": STAGES,
                        "rhs": R if mixed_ok else 1, "refine": args.refine if mixed_ok else 0,
-                       "operators": "one per tree level (constant coefficients)",
+                       "operators": "one per tree node (nodal coefficients)" if S.nodal else
+                                    "one per tree level (constant coefficients)",
                        "l2": "flushed (512 MB write) before every timed step",
                        "launch": "eager" if args.eager else "CUDA graph replay (hps_set_graph)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -414,6 +457,7 @@ def bench_ours(args, rank, world, local_rank):
                     if mixed_ok else fp64["e2e"]),
             "clocks": head["clocks"],
             "fp64_single_rhs": fp64,
+            "fp32_single_rhs_solve": single,
             "mixed_over_fp64": value_mixed / value64,
             "build_s": build_s, "wall_s": head["wall"],
         }
@@ -474,9 +518,9 @@ def main():
         if cpu is not None:
             out["cpu_baseline"] = {"value": cpu["N"] * cpu["solves"] / cpu["seconds"], "unit": "DOF*stages/s",
                                    "cores": 1, "kind": "oracle",
-                                   "sample": "%d full-size oracle stage solves in %.1f s on one host thread "
-                                             "(BLAS threads = 1); oracle build %.1f s not timed"
-                                             % (cpu["solves"], cpu["seconds"], cpu["build_s"])}
+                                   "sample": "%d oracle stage solves on %s leaves (p as the workload) in %.1f s on "
+                                             "one host thread (BLAS threads = 1); oracle build %.1f s not timed"
+                                             % (cpu["solves"], cpu["leaves"], cpu["seconds"], cpu["build_s"])}
         print(json.dumps(out))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -50,12 +50,33 @@ __device__ float flux32(int e, int j, int Rp, const float *W, const float *D1x, 
 }
 
 // ---- leaf applies (FP32, R columns) ------------------------------------------------------
+// Register tile per thread: 4 consecutive rows (one 16-byte operator load per column of the
+// transposed operator) x TC columns of the right-hand sides (TC/4 16-byte shared loads).
+
+template <int TC>
+__device__ __forceinline__ void tile_fma(float (&acc)[4][TC], const float4 a, const float *x) {
+  float xv[TC];
+#pragma unroll
+  for (int t = 0; t < TC; t += 4) {
+    const float4 v = *reinterpret_cast<const float4 *>(x + t);
+    xv[t] = v.x; xv[t + 1] = v.y; xv[t + 2] = v.z; xv[t + 3] = v.w;
+  }
+#pragma unroll
+  for (int t = 0; t < TC; ++t) {
+    acc[0][t] = fmaf(a.x, xv[t], acc[0][t]);
+    acc[1][t] = fmaf(a.y, xv[t], acc[1][t]);
+    acc[2][t] = fmaf(a.z, xv[t], acc[2][t]);
+    acc[3][t] = fmaf(a.w, xv[t], acc[3][t]);
+  }
+}
+
+template <int TC>
 __global__ void __launch_bounds__(kBT) k_b_leaf_up(GridDims g, int R, const int *__restrict__ origin, Combo rhs,
                                                    double *__restrict__ Rsave, const float *__restrict__ AinvT,
                                                    int ldA, int64_t strA, int identity, const double *__restrict__ Dg,
                                                    float *__restrict__ w32, float *__restrict__ h32) {
   extern __shared__ float smf[];
-  const int p = g.p, m = g.m, q = m * m, b = 4 * m, Rp = round4(R), G = Rp / 4;
+  const int p = g.p, m = g.m, q = m * m, b = 4 * m, Rp = round4(R);
   float *D1x = smf, *D1y = smf + p * p, *Rs = smf + round4(2 * p * p), *Ws = Rs + q * Rp;
   const int k = blockIdx.x;
   const int64_t l0 = ((int64_t)origin[2 * k + 1] * g.n1 + origin[2 * k]) * q;
@@ -70,16 +91,30 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_up(GridDims g, int R, const int 
     Rs[idx] = (float)v;
   }
   __syncthreads();
-  for (int it = threadIdx.x; it < q * G; it += blockDim.x) {
-    const int r = it % q, gg = it / q;
-    float4 acc = *reinterpret_cast<const float4 *>(Rs + r * Rp + 4 * gg);
-    if (!identity) {
-      acc = make_float4(0.f, 0.f, 0.f, 0.f);
-      const float *a = AinvT + (int64_t)k * strA + r;
-#pragma unroll 4
-      for (int c = 0; c < q; ++c) fma4(acc, __ldg(a + (int64_t)c * ldA), *reinterpret_cast<const float4 *>(Rs + c * Rp + 4 * gg));
+  const int QQ = (q + 3) / 4, CG = Rp / TC;
+  for (int it = threadIdx.x; it < QQ * CG; it += blockDim.x) {
+    const int r0 = 4 * (it % QQ), j0 = TC * (it / QQ);
+    float acc[4][TC];
+    if (identity) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int t = 0; t < TC; ++t) acc[e][t] = r0 + e < q ? Rs[(r0 + e) * Rp + j0 + t] : 0.f;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int t = 0; t < TC; ++t) acc[e][t] = 0.f;
+      const float *a = AinvT + (int64_t)k * strA + r0;
+#pragma unroll 2
+      for (int c = 0; c < q; ++c)
+        tile_fma<TC>(acc, __ldg(reinterpret_cast<const float4 *>(a + (int64_t)c * ldA)), Rs + c * Rp + j0);
     }
-    *reinterpret_cast<float4 *>(Ws + r * Rp + 4 * gg) = acc;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (r0 + e < q)
+#pragma unroll
+        for (int t = 0; t < TC; ++t) Ws[(r0 + e) * Rp + j0 + t] = acc[e][t];
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < q * R; idx += blockDim.x) {
@@ -92,11 +127,12 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_up(GridDims g, int R, const int 
   }
 }
 
+template <int TC>
 __global__ void __launch_bounds__(kBT) k_b_leaf_down(GridDims g, int R, const int *__restrict__ origin,
                                                      const float *__restrict__ SlT, int ldS, int64_t strS, int identity,
                                                      const float *__restrict__ w32, float *__restrict__ g32) {
   extern __shared__ float ub[];  // [b][Rp]
-  const int m = g.m, q = m * m, b = 4 * m, Rp = round4(R), G = Rp / 4;
+  const int m = g.m, q = m * m, b = 4 * m, Rp = round4(R);
   const int k = blockIdx.x;
   const int ix = origin[2 * k], iy = origin[2 * k + 1];
   const int64_t l0 = ((int64_t)iy * g.n1 + ix) * q;
@@ -105,25 +141,129 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_down(GridDims g, int R, const in
     ub[idx] = j < R ? g32[box_bd(g, ix, iy, 1, 1, e) * R + j] : 0.f;
   }
   __syncthreads();
-  for (int it = threadIdx.x; it < q * G; it += blockDim.x) {
-    const int r = it % q, gg = it / q;
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int QQ = (q + 3) / 4, CG = Rp / TC;
+  for (int it = threadIdx.x; it < QQ * CG; it += blockDim.x) {
+    const int r0 = 4 * (it % QQ), j0 = TC * (it / QQ);
+    float acc[4][TC];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+      for (int t = 0; t < TC; ++t) acc[e][t] = 0.f;
     if (!identity) {
-      const float *a = SlT + (int64_t)k * strS + r;
-#pragma unroll 4
-      for (int c = 0; c < b; ++c) fma4(acc, __ldg(a + (int64_t)c * ldS), *reinterpret_cast<const float4 *>(ub + c * Rp + 4 * gg));
+      const float *a = SlT + (int64_t)k * strS + r0;
+#pragma unroll 2
+      for (int c = 0; c < b; ++c)
+        tile_fma<TC>(acc, __ldg(reinterpret_cast<const float4 *>(a + (int64_t)c * ldS)), ub + c * Rp + j0);
     }
+#pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const int j = 4 * gg + e;
-      if (j < R) g32[(l0 + r) * R + j] = w32[((int64_t)k * q + r) * R + j] + comp(acc, e);
+      const int r = r0 + e;
+      if (r >= q) continue;
+#pragma unroll
+      for (int t = 0; t < TC; ++t) {
+        const int j = j0 + t;
+        if (j < R) g32[(l0 + r) * R + j] = w32[((int64_t)k * q + r) * R + j] + acc[e][t];
+      }
     }
+  }
+}
+
+// Narrow variants (R <= 4) for streaming per-leaf operators: the columns of the operator are
+// split over KS thread slices per row quad so that a whole CTA keeps 16-byte loads in flight;
+// the slices are added in a fixed order through shared memory.
+__device__ __forceinline__ void quad_apply_sliced(const float *a, int ld, int K, const float *x, int Rp, int QQ,
+                                                  int KS, float *part /*[KS][4*QQ][4]*/) {
+  for (int t = threadIdx.x; t < QQ * KS; t += blockDim.x) {
+    const int rq = t % QQ, ks = t / QQ;
+    const int c0 = (int)((int64_t)K * ks / KS), c1 = (int)((int64_t)K * (ks + 1) / KS);
+    float acc[4][4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[e][u] = 0.f;
+    const float *ar = a + 4 * rq;
+#pragma unroll 8
+    for (int c = c0; c < c1; ++c) tile_fma<4>(acc, __ldg(reinterpret_cast<const float4 *>(ar + (int64_t)c * ld)), x + c * Rp);
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      *reinterpret_cast<float4 *>(part + ((int64_t)ks * 4 * QQ + 4 * rq + e) * 4) =
+          make_float4(acc[e][0], acc[e][1], acc[e][2], acc[e][3]);
+  }
+}
+
+__global__ void __launch_bounds__(kBT) k_b_leaf_up_narrow(GridDims g, int R, const int *__restrict__ origin,
+                                                          Combo rhs, double *__restrict__ Rsave,
+                                                          const float *__restrict__ AinvT, int ldA, int64_t strA,
+                                                          int identity, const double *__restrict__ Dg,
+                                                          float *__restrict__ w32, float *__restrict__ h32) {
+  extern __shared__ float smf[];
+  const int p = g.p, m = g.m, q = m * m, b = 4 * m, QQ = (q + 3) / 4, KS = max(1, kBT / QQ);
+  float *D1x = smf, *D1y = smf + p * p, *Rs = smf + round4(2 * p * p), *Ws = Rs + 4 * q, *part = Ws + 4 * q;
+  const int k = blockIdx.x;
+  const int64_t l0 = ((int64_t)origin[2 * k + 1] * g.n1 + origin[2 * k]) * q;
+  for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) smf[i] = (float)Dg[i];
+  for (int idx = threadIdx.x; idx < q * 4; idx += blockDim.x) {
+    const int r = idx / 4, j = idx % 4;
+    double v = 0.0;
+    if (j < R) {
+      for (int t = 0; t < rhs.n; ++t) v = fma(rhs.coef[t], rhs.ptr[t][(l0 + r) * R + j], v);
+      if (Rsave) Rsave[(l0 + r) * R + j] = v;
+    }
+    Rs[idx] = (float)v;
+  }
+  __syncthreads();
+  if (identity) {
+    for (int idx = threadIdx.x; idx < q * 4; idx += blockDim.x) Ws[idx] = Rs[idx];
+  } else {
+    quad_apply_sliced(AinvT + (int64_t)k * strA, ldA, q, Rs, 4, QQ, KS, part);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < q * 4; idx += blockDim.x) {
+      float s = 0.f;
+      for (int ks = 0; ks < KS; ++ks) s += part[(int64_t)ks * 16 * QQ + idx];
+      Ws[idx] = s;
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < q * R; idx += blockDim.x) {
+    const int r = idx / R, j = idx % R;
+    w32[((int64_t)k * q + r) * R + j] = Ws[r * 4 + j];
+  }
+  for (int idx = threadIdx.x; idx < b * R; idx += blockDim.x) {
+    const int e = idx / R, j = idx % R;
+    h32[((int64_t)k * b + e) * R + j] = flux32(e, j, 4, Ws, D1x, D1y, p, m);
+  }
+}
+
+__global__ void __launch_bounds__(kBT) k_b_leaf_down_narrow(GridDims g, int R, const int *__restrict__ origin,
+                                                            const float *__restrict__ SlT, int ldS, int64_t strS,
+                                                            int identity, const float *__restrict__ w32,
+                                                            float *__restrict__ g32) {
+  extern __shared__ float smf[];
+  const int m = g.m, q = m * m, b = 4 * m, QQ = (q + 3) / 4, KS = max(1, kBT / QQ);
+  float *ub = smf, *part = smf + 4 * b;
+  const int k = blockIdx.x;
+  const int ix = origin[2 * k], iy = origin[2 * k + 1];
+  const int64_t l0 = ((int64_t)iy * g.n1 + ix) * q;
+  for (int idx = threadIdx.x; idx < b * 4; idx += blockDim.x) {
+    const int e = idx / 4, j = idx % 4;
+    ub[idx] = j < R ? g32[box_bd(g, ix, iy, 1, 1, e) * R + j] : 0.f;
+  }
+  __syncthreads();
+  if (!identity) quad_apply_sliced(SlT + (int64_t)k * strS, ldS, b, ub, 4, QQ, KS, part);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < q * R; idx += blockDim.x) {
+    const int r = idx / R, j = idx % R;
+    float s = w32[((int64_t)k * q + r) * R + j];
+    if (!identity)
+      for (int ks = 0; ks < KS; ++ks) s += part[(int64_t)ks * 16 * QQ + r * 4 + j];
+    g32[(l0 + r) * R + j] = s;
   }
 }
 
 // ---- merge applies (FP32, R columns) -------------------------------------------------------
 struct BPlan {
-  int M, K, nodes, R, Rp, G;
-  int npc, rows_cta, row_tiles, node_groups, ksplit, kchunk;
+  int M, K, nodes, R, Rp, TC, MQ, CG;
+  int npc, quads_cta, row_tiles, node_groups, ksplit, kchunk;
 };
 
 BPlan plan_b(int M, int K, int nodes, int R, int target) {
@@ -133,15 +273,18 @@ BPlan plan_b(int M, int K, int nodes, int R, int target) {
   P.nodes = nodes;
   P.R = R;
   P.Rp = round4(R);
-  P.G = P.Rp / 4;
-  if (M * P.G <= kBT / 2) {
-    P.npc = std::max(1, std::min(nodes, kBT / (M * P.G)));
-    P.rows_cta = M;
+  P.TC = P.Rp % 8 == 0 ? 8 : 4;
+  P.MQ = (M + 3) / 4;
+  P.CG = P.Rp / P.TC;
+  const int per = P.MQ * P.CG;
+  if (per <= kBT / 2) {
+    P.npc = std::max(1, std::min(nodes, kBT / per));
+    P.quads_cta = P.MQ;
     P.row_tiles = 1;
   } else {
     P.npc = 1;
-    P.rows_cta = std::max(1, kBT / P.G);
-    P.row_tiles = (M + P.rows_cta - 1) / P.rows_cta;
+    P.quads_cta = std::max(1, kBT / P.CG);
+    P.row_tiles = (P.MQ + P.quads_cta - 1) / P.quads_cta;
   }
   P.node_groups = (nodes + P.npc - 1) / P.npc;
   const int base = P.node_groups * P.row_tiles;
@@ -205,7 +348,7 @@ struct BEScatter {
   }
 };
 
-template <class XL, class EP>
+template <int TC, class XL, class EP>
 __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict__ AT, int ld, int64_t str, XL xl,
                                                 EP ep, float *__restrict__ partial) {
   extern __shared__ float xs[];  // [nn][klen][Rp]
@@ -218,33 +361,45 @@ __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict
     xs[idx] = j < P.R ? xl(node0 + lo, c0 + c, j) : 0.f;
   }
   __syncthreads();
-  int lo, r, gg;
-  bool active;
+  int lo, rq, cg;
   if (P.npc > 1) {
-    const int per = P.M * P.G;
+    const int per = P.MQ * P.CG;
     lo = threadIdx.x / per;
     const int rem = threadIdx.x % per;
-    gg = rem / P.M;
-    r = rem % P.M;
-    active = lo < nn;
+    cg = rem / P.MQ;
+    rq = rem % P.MQ;
+    if (lo >= nn) return;
   } else {
     lo = 0;
-    gg = threadIdx.x / P.rows_cta;
-    r = tile * P.rows_cta + threadIdx.x % P.rows_cta;
-    active = gg < P.G && r < P.M;
+    cg = threadIdx.x / P.quads_cta;
+    rq = tile * P.quads_cta + threadIdx.x % P.quads_cta;
+    if (cg >= P.CG || rq >= P.MQ) return;
   }
-  if (!active) return;
-  const int k = node0 + lo;
-  const float *a = AT + (int64_t)k * str + (int64_t)c0 * ld + r;
-  const float *x = xs + (int64_t)lo * klen * Rp + 4 * gg;
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 8
-  for (int c = 0; c < klen; ++c) fma4(acc, __ldg(a + (int64_t)c * ld), *reinterpret_cast<const float4 *>(x + c * Rp));
-  if (P.ksplit == 1) {
-    for (int e = 0; e < 4; ++e)
-      if (4 * gg + e < P.R) ep(k, r, 4 * gg + e, comp(acc, e));
-  } else {
-    *reinterpret_cast<float4 *>(partial + (((int64_t)ks * P.nodes + k) * P.M + r) * Rp + 4 * gg) = acc;
+  const int k = node0 + lo, r0 = 4 * rq, j0 = TC * cg;
+  const float *a = AT + (int64_t)k * str + (int64_t)c0 * ld + r0;
+  const float *x = xs + (int64_t)lo * klen * Rp + j0;
+  float acc[4][TC];
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+#pragma unroll
+    for (int t = 0; t < TC; ++t) acc[e][t] = 0.f;
+#pragma unroll 4
+  for (int c = 0; c < klen; ++c)
+    tile_fma<TC>(acc, __ldg(reinterpret_cast<const float4 *>(a + (int64_t)c * ld)), x + c * Rp);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int r = r0 + e;
+    if (r >= P.M) continue;
+    if (P.ksplit == 1) {
+#pragma unroll
+      for (int t = 0; t < TC; ++t)
+        if (j0 + t < P.R) ep(k, r, j0 + t, acc[e][t]);
+    } else {
+      float *dst = partial + (((int64_t)ks * P.nodes + k) * P.M + r) * Rp + j0;
+#pragma unroll
+      for (int t = 0; t < TC; t += 4)
+        *reinterpret_cast<float4 *>(dst + t) = make_float4(acc[e][t], acc[e][t + 1], acc[e][t + 2], acc[e][t + 3]);
+    }
   }
 }
 
@@ -267,8 +422,11 @@ int launch_b(hps_handle *H, int slot, const BPlan &P, const float *AT, int ld, i
   const size_t smem = (size_t)P.npc * P.kchunk * P.Rp * sizeof(float);
   if (P.ksplit > 1 && (size_t)P.ksplit * P.nodes * P.M * P.Rp > H->batch.partial_len) return HPS_EINVAL;
   H->trace.begin(slot, st);
-  k_b_gemv<XL, EP><<<dim3(P.node_groups * P.row_tiles, P.ksplit), kBT, smem, st>>>(P, AT, ld, str, xl, ep,
-                                                                                    H->batch.partial32);
+  const dim3 grid(P.node_groups * P.row_tiles, P.ksplit);
+  if (P.TC == 8)
+    k_b_gemv<8, XL, EP><<<grid, kBT, smem, st>>>(P, AT, ld, str, xl, ep, H->batch.partial32);
+  else
+    k_b_gemv<4, XL, EP><<<grid, kBT, smem, st>>>(P, AT, ld, str, xl, ep, H->batch.partial32);
   if (P.ksplit > 1) {
     const int64_t n = (int64_t)P.nodes * P.M * P.R;
     k_b_reduce<EP><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, H->batch.partial32, ep);
@@ -341,10 +499,13 @@ __global__ void __launch_bounds__(kBT) k_b_leaf64(GridDims g, const int *__restr
           }
         }
       }
-      double c[5];
-      for (int t = 0; t < 5; ++t) c[t] = A.coef ? A.coef[t * A.N_int + gi] : A.cst[t];
-      const double Lu = c[0] * uxx + c[1] * uyy + c[2] * ux + c[3] * uy + c[4] * uu;
       const int64_t o = gi * R + col;
+      double Lu = 0.0;
+      if (A.mode != kEpilogue) {
+        double c[5];
+        for (int t = 0; t < 5; ++t) c[t] = A.coef ? A.coef[t * A.N_int + gi] : A.cst[t];
+        Lu = c[0] * uxx + c[1] * uyy + c[2] * ux + c[3] * uy + c[4] * uu;
+      }
       if (A.mode == kResid) {
         A.out0[o] = A.Rb[o] - (uu - A.gdt * Lu);
       } else {
@@ -361,6 +522,27 @@ __global__ void __launch_bounds__(kBT) k_b_leaf64(GridDims g, const int *__restr
       }
     }
   }
+}
+
+// The modes without derivatives (stage epilogue of a g without derivatives; residual of the
+// identity operator) touch interior points only, which are contiguous: one flat pass.
+__global__ void k_b_pointwise(int64_t n, Leaf64Args A) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n) return;
+  const double uu = A.u[o];
+  if (A.mode == kResid) {  // gamma dt = 0
+    A.out0[o] = A.Rb[o] - uu;
+    return;
+  }
+  double e;
+  switch (A.g_kind) {
+    case HPS_G_ALLEN_CAHN: e = A.gp0 * (uu - uu * uu * uu); break;
+    case HPS_G_FISHER: e = A.gp0 * uu * (1.0 - uu); break;
+    default: e = 0.0;
+  }
+  if (A.q) e += A.q[o];
+  A.out0[o] = (uu - A.Rb[o]) * A.inv_gamma;
+  A.out1[o] = A.dt * e;
 }
 
 // r = -(flux from the west/south leaf - flux from the east/north leaf) at every shared edge point
@@ -464,31 +646,48 @@ __global__ void k_b_copy(double *__restrict__ dst, const double *__restrict__ sr
 inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 // ---- host orchestration --------------------------------------------------------------------
-int convert_opset(hps_handle *H, const OpSet &ops, OpSet32 &o32, bool shared) {
-  auto conv = [&](const double *src, size_t n, float **dst) -> int {
-    if (!src) { *dst = nullptr; return HPS_OK; }
-    if (cudaMalloc(dst, n * sizeof(float)) != cudaSuccess) return HPS_ENOMEM;
-    H->allocs.push_back(*dst);
-    k_to_float<<<std::min<size_t>(4096, (n + 255) / 256), 256>>>(src, *dst, n);
-    return HPS_OK;
-  };
-  const int L = H->L, q = H->q, b = H->b;
-  const size_t nleaf = shared ? 1 : H->lev[L].nodes;
-  if (!ops.identity) {
-    if (int e = conv(ops.Ainv, nleaf * q * ops.ldA, &o32.Ainv)) return e;
-    if (int e = conv(ops.Sleaf, nleaf * b * ops.ldSl, &o32.Sleaf)) return e;
+__global__ void k_relayout(const double *__restrict__ src, int ld64, int64_t str64, int rows, int cols, int64_t nops,
+                           float *__restrict__ dst, int ld32) {
+  const int64_t total = nops * cols * (int64_t)ld32;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t node = i / ((int64_t)cols * ld32);
+    const int64_t rem = i % ((int64_t)cols * ld32);
+    const int c = (int)(rem / ld32), r = (int)(rem % ld32);
+    dst[i] = r < rows ? (float)src[node * str64 + (int64_t)c * ld64 + r] : 0.f;
   }
-  o32.X.assign(L, nullptr);
-  o32.S.assign(L, nullptr);
-  o32.Tcat.assign(L, nullptr);
+}
+
+// FP32 copy of a transposed operator (rows x cols per node) with rows padded to 4 floats.
+int convert_op(hps_handle *H, const double *src, int ld64, int64_t str64, int rows, int cols, int64_t nops, Op32 &o) {
+  if (!src) return HPS_OK;
+  o.ld = round4(rows);
+  o.str = nops > 1 || str64 ? (int64_t)cols * o.ld : 0;
+  const int64_t total = std::max<int64_t>(1, nops) * cols * (int64_t)o.ld;
+  if (cudaMalloc(&o.p, total * sizeof(float)) != cudaSuccess) return HPS_ENOMEM;
+  H->allocs.push_back(o.p);
+  k_relayout<<<(unsigned)std::min<int64_t>(8192, (total + 255) / 256), 256>>>(src, ld64, str64, rows, cols,
+                                                                              std::max<int64_t>(1, nops), o.p, o.ld);
+  return HPS_OK;
+}
+
+int convert_opset(hps_handle *H, const OpSet &ops, OpSet32 &o32, bool shared) {
+  const int L = H->L, q = H->q, b = H->b;
+  const int64_t nleaf = shared ? 1 : H->lev[L].nodes;
+  if (!ops.identity) {
+    if (int e = convert_op(H, ops.Ainv, ops.ldA, ops.strA, q, q, nleaf, o32.Ainv)) return e;
+    if (int e = convert_op(H, ops.Sleaf, ops.ldSl, ops.strSl, q, b, nleaf, o32.Sleaf)) return e;
+  }
+  o32.X.assign(L, Op32());
+  o32.S.assign(L, Op32());
+  o32.Tcat.assign(L, Op32());
   for (int l = 0; l < L; ++l) {
     const Level &lv = H->lev[l];
     const MergeOps &mo = ops.merge[l];
-    const size_t nops = shared ? 1 : lv.nodes;
-    if (int e = conv(mo.X, nops * lv.n3 * mo.ldX, &o32.X[l])) return e;
-    if (int e = conv(mo.S, nops * lv.nb * mo.ldS, &o32.S[l])) return e;
+    const int64_t nops = shared ? 1 : lv.nodes;
+    if (int e = convert_op(H, mo.X, mo.ldX, mo.strX, lv.n3, lv.n3, nops, o32.X[l])) return e;
+    if (int e = convert_op(H, mo.S, mo.ldS, mo.strS, lv.n3, lv.nb, nops, o32.S[l])) return e;
     if (l > 0)
-      if (int e = conv(mo.Tcat, nops * lv.n3 * mo.ldT, &o32.Tcat[l])) return e;
+      if (int e = convert_op(H, mo.Tcat, mo.ldT, mo.strT, lv.nb, lv.n3, nops, o32.Tcat[l])) return e;
   }
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
@@ -513,29 +712,48 @@ int sweep32(hps_handle *H, const OpSet &ops, const OpSet32 &o32, int R, const Co
   const int L = H->L, p = H->p, q = H->q, b = H->b, Rp = round4(R);
   const Level &leaf = H->lev[L];
   const int target = 2 * H->num_sms;
-  {
-    const size_t smem = (size_t)(round4(2 * p * p) + 2 * q * Rp) * sizeof(float);
+  const bool tc8 = Rp % 8 == 0;
+  const bool narrow = Rp == 4 && !H->shared;  // streaming per-leaf operators, one column group
+  const int QQ = (q + 3) / 4, KS = std::max(1, kBT / QQ);
+  if (narrow) {
+    const size_t smem = (size_t)(round4(2 * p * p) + 8 * q + KS * 16 * QQ) * sizeof(float);
     static size_t set = 0;
     if (smem > 48 * 1024 && smem > set) {
-      cudaFuncSetAttribute(k_b_leaf_up, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(k_b_leaf_up_narrow, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       set = smem;
     }
     H->trace.begin(kLeafUp, st);
-    k_b_leaf_up<<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, o32.Ainv, ops.ldA, ops.strA,
-                                               ops.identity ? 1 : 0, H->d_D, B.w32, B.h32[L]);
+    k_b_leaf_up_narrow<<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, o32.Ainv.p, o32.Ainv.ld,
+                                                      o32.Ainv.str, ops.identity ? 1 : 0, H->d_D, B.w32, B.h32[L]);
+    H->trace.end(kLeafUp, st);
+  } else {
+    const size_t smem = (size_t)(round4(2 * p * p) + 2 * q * Rp) * sizeof(float);
+    static size_t set = 0;
+    if (smem > 48 * 1024 && smem > set) {
+      cudaFuncSetAttribute(k_b_leaf_up<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(k_b_leaf_up<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      set = smem;
+    }
+    H->trace.begin(kLeafUp, st);
+    if (tc8)
+      k_b_leaf_up<8><<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, o32.Ainv.p, o32.Ainv.ld,
+                                                    o32.Ainv.str, ops.identity ? 1 : 0, H->d_D, B.w32, B.h32[L]);
+    else
+      k_b_leaf_up<4><<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, o32.Ainv.p, o32.Ainv.ld,
+                                                    o32.Ainv.str, ops.identity ? 1 : 0, H->d_D, B.w32, B.h32[L]);
     H->trace.end(kLeafUp, st);
   }
   for (int l = L - 1; l >= 0; --l) {
     const Level &lv = H->lev[l];
     const MergeOps &mo = ops.merge[l];
     const BPlan Pw = plan_b(lv.n3, lv.n3, lv.nodes, R, target);
-    if (int e = launch_b(H, kMergeUpW3, Pw, o32.X[l], mo.ldX, mo.strX,
+    if (int e = launch_b(H, kMergeUpW3, Pw, o32.X[l].p, o32.X[l].ld, o32.X[l].str,
                          BXDiff{B.h32[l + 1], lv.nbc, lv.j3a, lv.j3b, R, jump, H->g, lv.d_origin, lv.a, lv.c, lv.split},
                          BEStore{B.w332[l], lv.n3, R}, st))
       return e;
     if (l > 0) {
       const BPlan Ph = plan_b(lv.nb, lv.n3, lv.nodes, R, target);
-      if (int e = launch_b(H, kMergeUpH, Ph, o32.Tcat[l], mo.ldT, mo.strT, BXVec{B.w332[l], lv.n3, R},
+      if (int e = launch_b(H, kMergeUpH, Ph, o32.Tcat[l].p, o32.Tcat[l].ld, o32.Tcat[l].str, BXVec{B.w332[l], lv.n3, R},
                            BEFlux{lv.d_hsrc, B.h32[l + 1], lv.nbc, lv.nb, R, B.h32[l]}, st))
         return e;
     }
@@ -544,13 +762,20 @@ int sweep32(hps_handle *H, const OpSet &ops, const OpSet32 &o32, int R, const Co
     const Level &lv = H->lev[l];
     const MergeOps &mo = ops.merge[l];
     const BPlan Pd = plan_b(lv.n3, lv.nb, lv.nodes, R, target);
-    if (int e = launch_b(H, kMergeDown, Pd, o32.S[l], mo.ldS, mo.strS, BXBd{H->g, lv.d_origin, lv.a, lv.c, R, B.g32},
+    if (int e = launch_b(H, kMergeDown, Pd, o32.S[l].p, o32.S[l].ld, o32.S[l].str, BXBd{H->g, lv.d_origin, lv.a, lv.c, R, B.g32},
                          BEScatter{H->g, lv.d_origin, lv.a, lv.c, lv.split, lv.n3, R, B.w332[l], B.g32}, st))
       return e;
   }
   H->trace.begin(kLeafDown, st);
-  k_b_leaf_down<<<leaf.nodes, kBT, (size_t)b * Rp * sizeof(float), st>>>(H->g, R, leaf.d_origin, o32.Sleaf, ops.ldSl,
-                                                                          ops.strSl, ops.identity ? 1 : 0, B.w32, B.g32);
+  if (narrow)
+    k_b_leaf_down_narrow<<<leaf.nodes, kBT, (size_t)(4 * b + KS * 16 * QQ) * sizeof(float), st>>>(
+        H->g, R, leaf.d_origin, o32.Sleaf.p, o32.Sleaf.ld, o32.Sleaf.str, ops.identity ? 1 : 0, B.w32, B.g32);
+  else if (tc8)
+    k_b_leaf_down<8><<<leaf.nodes, kBT, (size_t)b * Rp * sizeof(float), st>>>(
+        H->g, R, leaf.d_origin, o32.Sleaf.p, o32.Sleaf.ld, o32.Sleaf.str, ops.identity ? 1 : 0, B.w32, B.g32);
+  else
+    k_b_leaf_down<4><<<leaf.nodes, kBT, (size_t)b * Rp * sizeof(float), st>>>(
+        H->g, R, leaf.d_origin, o32.Sleaf.p, o32.Sleaf.ld, o32.Sleaf.str, ops.identity ? 1 : 0, B.w32, B.g32);
   H->trace.end(kLeafDown, st);
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
@@ -574,6 +799,14 @@ int leaf64(hps_handle *H, Leaf64Args A, cudaStream_t st) {
   const bool d2_L = nodal || H->cst[0] != 0.0 || H->cst[1] != 0.0;
   A.need_d1 = (L_needed && d1_L) || (A.mode != kResid && A.g_kind == HPS_G_BURGERS);
   A.need_d2 = L_needed && d2_L;
+  const int slot = A.mode == kResid ? kResidual : kLeafEval;
+  if (!A.need_d1 && !A.need_d2 && A.mode != kEval) {
+    const int64_t n = H->g.N_int * A.R;
+    H->trace.begin(slot, st);
+    k_b_pointwise<<<blocks(n), 256, 0, st>>>(n, A);
+    H->trace.end(slot, st);
+    return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
+  }
   const int p = H->p, pp = p * p;
   const int Rc = std::max(1, std::min(A.R, 4096 / pp));
   const size_t smem = (size_t)(4 * pp + pp * Rc) * sizeof(double);
@@ -583,7 +816,6 @@ int leaf64(hps_handle *H, Leaf64Args A, cudaStream_t st) {
     set = smem;
   }
   const Level &leaf = H->lev[H->L];
-  const int slot = A.mode == kResid ? kResidual : kLeafEval;
   H->trace.begin(slot, st);
   k_b_leaf64<<<leaf.nodes, kBT, smem, st>>>(H->g, leaf.d_origin, A, H->d_D);
   H->trace.end(slot, st);
@@ -644,7 +876,7 @@ int batch_reserve(hps_handle *H, int R) {
   if (R <= 0 || R > 64) return HPS_EINVAL;
   if (R <= B.Rmax) return HPS_OK;
   cudaDeviceSynchronize();
-  if (!B.impl32.X.size()) {  // FP32 operator copies (once)
+  if (B.impl32.X.empty()) {  // FP32 operator copies (once)
     if (int e = convert_opset(H, H->impl, B.impl32, H->shared)) return e;
     if (int e = convert_opset(H, H->ident, B.ident32, true)) return e;
   }

@@ -121,9 +121,14 @@ struct OpSet {
 };
 
 // FP32 copy of an operator set (same layouts, leading dimensions and strides as the FP64 one).
+struct Op32 {
+  float *p = nullptr;
+  int ld = 0;        // rows padded to a multiple of 4 floats (16-byte column loads)
+  int64_t str = 0;   // per node, 0 when shared
+};
 struct OpSet32 {
-  float *Ainv = nullptr, *Sleaf = nullptr;
-  std::vector<float *> X, S, Tcat;  // per level
+  Op32 Ainv, Sleaf;
+  std::vector<Op32> X, S, Tcat;  // per level
 };
 
 // Work buffers of the batched mixed-precision path for up to Rmax right-hand sides.  Vectors

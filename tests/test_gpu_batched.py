@@ -25,7 +25,8 @@ def _solver(torch, n1, n2, p, coef, gdt, dom=(0.0, 1.0, 0.0, 1.0)):
 
 
 @pytest.mark.parametrize("n1,n2,p,R,nodal", [(1, 1, 5, 1, False), (2, 2, 7, 3, True), (8, 4, 9, 8, True),
-                                             (16, 16, 12, 32, False), (8, 16, 16, 5, True)])
+                                             (16, 16, 12, 32, False), (8, 16, 16, 5, True), (16, 8, 16, 1, True),
+                                             (4, 4, 13, 4, True)])
 def test_solve_batch_matches_fp64(n1, n2, p, R, nodal):
     torch = need_gpu()
     g = Grid(n1, n2, p, -0.5, 0.5, 0.0, 1.0)
