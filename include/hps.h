@@ -256,6 +256,63 @@ int hps_solve_batch(hps_handle *h, int R, const double *rhs, const double *f, do
 int ark_step_batch(hps_handle *h, int R, double *u, double t, double dt, const hps_ark_terms *terms, int refine,
                    hps_stream_t stream);
 
+/* ---- Serving: a continuous-batching request loop for time-stepping jobs -------------------
+ * Jobs arrive at given times; the loop admits a waiting job (in arrival order) as soon as an
+ * active slot is free and the device-memory budget holds its factorization -- unless one of an
+ * identical operator (tree, p, coefficients, dt) is resident, which is then shared -- plus its
+ * work buffers and state.  Every active job advances one ark_step at a time (graph replay) on
+ * its own CUDA stream with up to two steps queued, so steps of different jobs overlap on the
+ * GPU and newly admitted jobs join while others run.  A finished job copies its state to
+ * u_out and releases its memory; factorizations without users stay cached until the budget
+ * needs their memory.  Results are the same whether a job runs alone or in a mix (the same
+ * kernels on the same data; no reduction order depends on other jobs). */
+typedef struct hps_server hps_server;
+
+typedef struct hps_job_desc {
+  hps_tree tree;
+  int p;
+  double c_a11, c_a22, c_a1, c_a2, c_a0; /* constant coefficients of L */
+  double dt, t0;                          /* step and start time (gamma dt = dt / 4) */
+  int steps;
+  int g_kind;                             /* HPS_G_* preset, q = 0 and f = 0 */
+  double g_param[2];
+  const double *u0;                       /* host, N doubles; valid until hps_server_run returns */
+  double *u_out;                          /* host, N doubles, written when the job finishes */
+  double arrival_s;                       /* seconds after hps_server_run starts */
+} hps_job_desc;
+
+typedef struct hps_job_stats {
+  int state;             /* 0 waiting, 1 active, 2 done, 3 rejected */
+  int status;            /* HPS_OK or the error that ended it (HPS_ENOMEM: larger than the budget) */
+  double arrival_s, admit_s, finish_s;
+  int steps_done;
+  int shared_operators;  /* 1 if it used a factorization built for an earlier job */
+  size_t work_bytes;
+  double step_ms_mean, step_ms_p50, step_ms_p99; /* device time of its steps (CUDA events) */
+} hps_job_stats;
+
+typedef struct hps_server_stats {
+  int jobs_done, jobs_rejected;
+  double makespan_s;         /* wall time of hps_server_run */
+  double dof_stages_per_s;   /* sum over jobs of N x 5 x steps, divided by the makespan */
+  int64_t steps;
+  double step_ms_p50, step_ms_p99;
+  int max_concurrent;
+  size_t peak_bytes;
+  int factorizations_built, factorizations_shared;
+} hps_server_stats;
+
+/* A server with a device-memory budget (bytes, for factorizations + work buffers + states)
+ * and at most max_active jobs in flight. */
+int hps_server_create(size_t mem_budget_bytes, int max_active, hps_server **out);
+/* Queue a job; *job_id (may be NULL) receives its index. */
+int hps_server_submit(hps_server *s, const hps_job_desc *job, int *job_id);
+/* Run until every queued job is done or rejected (blocks; honours arrival times from now). */
+int hps_server_run(hps_server *s);
+int hps_server_job_stats(hps_server *s, int job_id, hps_job_stats *out);
+int hps_server_summary(hps_server *s, hps_server_stats *out);
+void hps_server_free(hps_server *s);
+
 /* Release the handle and all its device memory (synchronizes the device first). */
 void hps_free(hps_handle *h);
 

@@ -33,6 +33,28 @@ class hps_ark_terms(ctypes.Structure):
                 ("g_param", ctypes.c_double * 2)]
 
 
+class hps_job_desc(ctypes.Structure):
+    _fields_ = [("tree", hps_tree), ("p", ctypes.c_int), ("c_a11", ctypes.c_double), ("c_a22", ctypes.c_double),
+                ("c_a1", ctypes.c_double), ("c_a2", ctypes.c_double), ("c_a0", ctypes.c_double),
+                ("dt", ctypes.c_double), ("t0", ctypes.c_double), ("steps", ctypes.c_int), ("g_kind", ctypes.c_int),
+                ("g_param", ctypes.c_double * 2), ("u0", ctypes.c_void_p), ("u_out", ctypes.c_void_p),
+                ("arrival_s", ctypes.c_double)]
+
+
+class hps_job_stats(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("status", ctypes.c_int), ("arrival_s", ctypes.c_double),
+                ("admit_s", ctypes.c_double), ("finish_s", ctypes.c_double), ("steps_done", ctypes.c_int),
+                ("shared_operators", ctypes.c_int), ("work_bytes", ctypes.c_size_t),
+                ("step_ms_mean", ctypes.c_double), ("step_ms_p50", ctypes.c_double), ("step_ms_p99", ctypes.c_double)]
+
+
+class hps_server_stats(ctypes.Structure):
+    _fields_ = [("jobs_done", ctypes.c_int), ("jobs_rejected", ctypes.c_int), ("makespan_s", ctypes.c_double),
+                ("dof_stages_per_s", ctypes.c_double), ("steps", ctypes.c_int64), ("step_ms_p50", ctypes.c_double),
+                ("step_ms_p99", ctypes.c_double), ("max_concurrent", ctypes.c_int), ("peak_bytes", ctypes.c_size_t),
+                ("factorizations_built", ctypes.c_int), ("factorizations_shared", ctypes.c_int)]
+
+
 # name -> (restype, argtypes); the list is also the set of exported symbols include/hps.h declares
 SIGNATURES = {
     "hps_sizes": (ctypes.c_int, [ctypes.POINTER(hps_tree), ctypes.c_int, c_int64_p, c_int64_p, c_int64_p]),
@@ -61,6 +83,12 @@ SIGNATURES = {
                                        ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "ark_step_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_double,
                                       ctypes.c_double, ctypes.POINTER(hps_ark_terms), ctypes.c_int, ctypes.c_void_p]),
+    "hps_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "hps_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(hps_job_desc), ctypes.POINTER(ctypes.c_int)]),
+    "hps_server_run": (ctypes.c_int, [ctypes.c_void_p]),
+    "hps_server_job_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(hps_job_stats)]),
+    "hps_server_summary": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(hps_server_stats)]),
+    "hps_server_free": (None, [ctypes.c_void_p]),
     "hps_free": (None, [ctypes.c_void_p]),
     "hps_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }

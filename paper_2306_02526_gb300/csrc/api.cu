@@ -364,37 +364,100 @@ int hps_build(const hps_tree *tree, int p, const hps_coeffs *coeffs, double gamm
   }
   if (int e = hps::build_operators(H, H->impl, gamma_dt, false, st)) return fail(e);
   if (int e = hps::build_operators(H, H->ident, 0.0, true, st)) return fail(e);
-  // work buffers
-  const GridDims &g = H->g;
-  if (dalloc(H, &H->ustage, g.N) || dalloc(H, &H->R, g.N_int) || dalloc(H, &H->KL, 6 * (size_t)g.N_int) ||
-      dalloc(H, &H->KE, 6 * (size_t)g.N_int) || dalloc(H, &H->wleaf, g.N_int))
-    return fail(HPS_ENOMEM);
-  H->h.assign(H->L + 1, nullptr);
-  H->w3.assign(H->L, nullptr);
-  for (int l = 0; l <= H->L; ++l) {
-    const Level &lv = H->lev[l];
-    if (dalloc(H, &H->h[l], (size_t)lv.nodes * lv.nb)) return fail(HPS_ENOMEM);
-    if (l < H->L && dalloc(H, &H->w3[l], (size_t)lv.nodes * lv.n3)) return fail(HPS_ENOMEM);
-  }
-  H->partial_len = hps::partial_doubles(H);
-  if (H->partial_len && dalloc(H, &H->partial, H->partial_len)) return fail(HPS_ENOMEM);
-  // persistent merge kernel: task lists, partial sums, counters, barrier, error word
+  // persistent merge kernel: task lists (operator data, shared by clones)
   if (int e = hps::build_tasks(H, H->impl)) return fail(e);
   if (int e = hps::build_tasks(H, H->ident)) return fail(e);
-  if (dalloc(H, &H->ppartial, std::max<size_t>(1, H->ppartial_len)) ||
-      dalloc(H, &H->pcounters, std::max<size_t>(1, H->pcounter_len)) || dalloc(H, &H->pbar, 2) ||
-      dalloc(H, &H->perr, 1))
-    return fail(HPS_ENOMEM);
-  cudaMemsetAsync(H->pcounters, 0, std::max<size_t>(1, H->pcounter_len) * sizeof(unsigned), st);
-  cudaMemsetAsync(H->pbar, 0, 2 * sizeof(unsigned), st);
-  cudaMemsetAsync(H->perr, 0, sizeof(int), st);
-  cudaMemsetAsync(H->ustage, 0, g.N * sizeof(double), st);
-  if (cudaStreamSynchronize(st) != cudaSuccess) return fail(HPS_ECUDA);
+  if (int e = hps::alloc_work(H, st)) return fail(e);
   *out = H;
   return HPS_OK;
 }
 
 }  // extern "C"
+
+namespace hps {
+
+// The per-call work buffers of a handle (everything a solve writes besides the caller's vectors).
+int alloc_work(hps_handle *H, cudaStream_t st) {
+  const GridDims &g = H->g;
+  if (dalloc(H, &H->ustage, g.N) || dalloc(H, &H->R, g.N_int) || dalloc(H, &H->KL, 6 * (size_t)g.N_int) ||
+      dalloc(H, &H->KE, 6 * (size_t)g.N_int) || dalloc(H, &H->wleaf, g.N_int))
+    return HPS_ENOMEM;
+  H->h.assign(H->L + 1, nullptr);
+  H->w3.assign(H->L, nullptr);
+  for (int l = 0; l <= H->L; ++l) {
+    const Level &lv = H->lev[l];
+    if (dalloc(H, &H->h[l], (size_t)lv.nodes * lv.nb)) return HPS_ENOMEM;
+    if (l < H->L && dalloc(H, &H->w3[l], (size_t)lv.nodes * lv.n3)) return HPS_ENOMEM;
+  }
+  H->partial_len = partial_doubles(H);
+  if (H->partial_len && dalloc(H, &H->partial, H->partial_len)) return HPS_ENOMEM;
+  if (dalloc(H, &H->ppartial, std::max<size_t>(1, H->ppartial_len)) ||
+      dalloc(H, &H->pcounters, std::max<size_t>(1, H->pcounter_len)) || dalloc(H, &H->pbar, 2) ||
+      dalloc(H, &H->perr, 1))
+    return HPS_ENOMEM;
+  cudaMemsetAsync(H->pcounters, 0, std::max<size_t>(1, H->pcounter_len) * sizeof(unsigned), st);
+  cudaMemsetAsync(H->pbar, 0, 2 * sizeof(unsigned), st);
+  cudaMemsetAsync(H->perr, 0, sizeof(int), st);
+  cudaMemsetAsync(H->ustage, 0, g.N * sizeof(double), st);
+  return cudaStreamSynchronize(st) == cudaSuccess ? HPS_OK : HPS_ECUDA;
+}
+
+// A handle that shares base's operators (read only) and owns new work buffers, so that
+// several states can be advanced concurrently with one factorization.  base must outlive it.
+int clone_handle(const hps_handle *base, cudaStream_t st, hps_handle **out) {
+  if (!base || !out) return HPS_EINVAL;
+  hps_handle *H = new (std::nothrow) hps_handle();
+  if (!H) return HPS_ENOMEM;
+  H->tree = base->tree;
+  H->g = base->g;
+  H->p = base->p;
+  H->m = base->m;
+  H->q = base->q;
+  H->b = base->b;
+  H->L = base->L;
+  H->hx = base->hx;
+  H->hy = base->hy;
+  H->gamma_dt = base->gamma_dt;
+  H->shared = base->shared;
+  H->coef_kind = base->coef_kind;
+  for (int i = 0; i < 5; ++i) H->cst[i] = base->cst[i];
+  H->d_coef = base->d_coef;
+  H->d_D = base->d_D;
+  H->lev = base->lev;
+  H->impl = base->impl;
+  H->ident = base->ident;
+  H->num_sms = base->num_sms;
+  H->persistent = base->persistent;
+  H->pgrid = base->pgrid;
+  H->ppartial_len = base->ppartial_len;
+  H->pcounter_len = base->pcounter_len;
+  if (int e = alloc_work(H, st)) {
+    hps_free(H);
+    return e;
+  }
+  *out = H;
+  return HPS_OK;
+}
+
+// Device bytes of the operators (both sets) and of one handle's work buffers.
+int bytes_split(const hps_tree *tree, int p, int coeff_kind, int flags, size_t *ops, size_t *work) {
+  if (check_tree(tree, p)) return HPS_EINVAL;
+  const GridDims g = dims(tree, p);
+  std::vector<Level> lev;
+  try {
+    lev = make_levels(g);
+  } catch (...) {
+    return HPS_EINVAL;
+  }
+  const int q = g.m * g.m, b = 4 * g.m;
+  const bool shared = coeff_kind == HPS_COEF_CONST && !(flags & HPS_FLAG_PER_NODE);
+  *ops = opset_bytes(lev, q, b, shared, false) + opset_bytes(lev, q, b, true, true) +
+         (coeff_kind == HPS_COEF_NODAL ? 5 * (size_t)g.N_int * sizeof(double) : 0) + 4 * (size_t)p * p * sizeof(double);
+  *work = work_bytes(g, lev);
+  return HPS_OK;
+}
+
+}  // namespace hps
 
 namespace {
 

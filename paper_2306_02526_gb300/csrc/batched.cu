@@ -21,20 +21,6 @@ constexpr int kBSmemFloats = 8192;  // vector staging of the merge applies (32 K
 
 __host__ __device__ inline int round4(int r) { return (r + 3) & ~3; }
 
-__global__ void k_to_float(const double *__restrict__ src, float *__restrict__ dst, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    dst[i] = (float)src[i];
-}
-
-__device__ __forceinline__ void fma4(float4 &acc, float a, const float4 x) {
-  acc.x = fmaf(a, x.x, acc.x);
-  acc.y = fmaf(a, x.y, acc.y);
-  acc.z = fmaf(a, x.z, acc.z);
-  acc.w = fmaf(a, x.w, acc.w);
-}
-
-__device__ __forceinline__ float comp(const float4 &v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
-
 // flux (D_bi w)_e of column j of an interior field W[node*Rp + j] (float)
 __device__ float flux32(int e, int j, int Rp, const float *W, const float *D1x, const float *D1y, int p, int m) {
   const int side = e / m, t = e % m;
@@ -636,11 +622,6 @@ __global__ void k_b_finish(GridDims g, int R, const float *__restrict__ g32, dou
     return;
   }
   u[idx] = assign ? (double)g32[idx] : u[idx] + (double)g32[idx];
-}
-
-__global__ void k_b_copy(double *__restrict__ dst, const double *__restrict__ src, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] = src[i];
 }
 
 inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }

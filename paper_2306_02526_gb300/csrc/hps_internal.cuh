@@ -248,6 +248,11 @@ int build_tasks(hps_handle *H, OpSet &ops);
 int merge_persistent(hps_handle *H, const OpSet &ops, bool upward, double *gvec, cudaStream_t st);
 int selftest_barrier(hps_handle *H, cudaStream_t st);
 
+// ---- handle services (api.cu) ----------------------------------------------------------------
+int alloc_work(hps_handle *H, cudaStream_t st);
+int clone_handle(const hps_handle *base, cudaStream_t st, hps_handle **out);
+int bytes_split(const hps_tree *tree, int p, int coeff_kind, int flags, size_t *ops, size_t *work);
+
 // ---- batched mixed-precision path (batched.cu) ---------------------------------------------
 int batch_reserve(hps_handle *H, int R);
 int solve_batch(hps_handle *H, int R, const double *rhs, const double *f, double *u, int refine, cudaStream_t st);

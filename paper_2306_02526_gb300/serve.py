@@ -1,0 +1,71 @@
+"""Python binding of the serving loop (hps_server_* in include/hps.h).
+
+Jobs carry host arrays (numpy float64) for their initial and final states; the loop itself
+runs natively (admission by device memory, one CUDA stream per job, graph-replayed steps)."""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import check, lib
+from .hps import G_KINDS, Tree, hps_sizes
+
+
+class Server:
+    def __init__(self, mem_budget_bytes, max_active=8):
+        h = ctypes.c_void_p()
+        check(lib().hps_server_create(int(mem_budget_bytes), int(max_active), ctypes.byref(h)), "hps_server_create")
+        self._h = h
+        self._keep = []
+        self.jobs = []
+
+    def submit(self, tree: Tree, p, coef, dt, steps, u0, g=None, g_param=(1.0, 1.0), t0=0.0, arrival_s=0.0):
+        """Queue a job; returns its id.  coef: dict of constant coefficients a11, a22, a1, a2, a0."""
+        N, _, _ = hps_sizes(tree, p)
+        u0 = np.ascontiguousarray(u0, dtype=np.float64)
+        if u0.size != N:
+            raise ValueError("u0 has %d entries, expected %d" % (u0.size, N))
+        out = np.empty(N)
+        d = _lib.hps_job_desc()
+        d.tree = tree.c
+        d.p = int(p)
+        for k in ("a11", "a22", "a1", "a2", "a0"):
+            setattr(d, "c_" + k, float(coef.get(k, 0.0)))
+        d.dt, d.t0, d.steps = float(dt), float(t0), int(steps)
+        d.g_kind = G_KINDS[g]
+        d.g_param[0], d.g_param[1] = float(g_param[0]), float(g_param[1])
+        d.u0 = u0.ctypes.data_as(ctypes.c_void_p)
+        d.u_out = out.ctypes.data_as(ctypes.c_void_p)
+        d.arrival_s = float(arrival_s)
+        jid = ctypes.c_int()
+        check(lib().hps_server_submit(self._h, ctypes.byref(d), ctypes.byref(jid)), "hps_server_submit")
+        self._keep.append((u0, out))
+        self.jobs.append(out)
+        return jid.value
+
+    def run(self):
+        check(lib().hps_server_run(self._h), "hps_server_run")
+
+    def result(self, job_id):
+        return self.jobs[job_id]
+
+    def job_stats(self, job_id):
+        s = _lib.hps_job_stats()
+        check(lib().hps_server_job_stats(self._h, int(job_id), ctypes.byref(s)), "hps_server_job_stats")
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def summary(self):
+        s = _lib.hps_server_stats()
+        check(lib().hps_server_summary(self._h, ctypes.byref(s)), "hps_server_summary")
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hps_server_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
