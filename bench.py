@@ -180,6 +180,21 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------------------------------------
+def max_over_ranks(x, world, device):
+    """The largest value of x over all ranks (the job is as slow as its slowest replica)."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world, units_per_rank, max_ms):
+    """Whole-job throughput of `world` independent replicas: all ranks' units over the max time."""
+    return world * units_per_rank / (max_ms * 1e-3)
+
+
 def timed_run(S, step, args, world, local_rank, flush, torch):
     """W warm-up steps, a traced pass for per-kernel shares, then K timed steps (L2 flushed
     before each, CUDA events on the launch stream, barrier + synchronize on both sides)."""
@@ -222,11 +237,7 @@ def timed_run(S, step, args, world, local_rank, flush, torch):
         wall = time.perf_counter() - w0
     step_ms = [a.elapsed_time(b) for a, b in evs]
     tr = S.trace_read()
-    total_ms = sum(step_ms)
-    if world > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(sum(step_ms), world, "cuda")
     tot = sum(v[2] for v in shares.values()) or 1.0
     return {"total_ms": total_ms, "step_ms": step_ms, "wall": wall, "clocks": clk.summary(), "dom": dom,
             "dom_avg_ms": tr[dom][2] / max(1, tr[dom][1]), "launches": sum(v[0] for v in tr.values()),
@@ -305,12 +316,12 @@ def bench_ours(args, rank, world, local_rank):
         args_short.steps, args_short.warmup = 2, 1
         u = torch.tensor(u0, dtype=torch.float64, device="cuda")
         r64 = timed_run(S, lambda: fp64_steps(u, 1), args_short, world, local_rank, flush, torch)
-        value64 = world * N * STAGES * 2 / (r64["total_ms"] * 1e-3)
+        value64 = replica_value(world, N * STAGES * 2, r64["total_ms"])
     else:
         u = torch.tensor(u0, dtype=torch.float64, device="cuda")
         r64 = timed_run(S, lambda: fp64_steps(u, 1), args, world, local_rank, flush, torch)
         assert torch.isfinite(u).all(), "FP64 solution went non-finite"
-        value64 = world * N * STAGES * args.steps / (r64["total_ms"] * 1e-3)
+        value64 = replica_value(world, N * STAGES * args.steps, r64["total_ms"])
     if args.only == "fp64":
         args.rhs = R = 4
         args.steps, args.warmup = 2, 1
@@ -326,7 +337,7 @@ def bench_ours(args, rank, world, local_rank):
 
     rmx = timed_run(S, lambda: mixed_step(U), args, world, local_rank, flush, torch)
     assert torch.isfinite(U).all(), "mixed solution went non-finite"
-    value_mixed = world * R * N * STAGES * args.steps / (rmx["total_ms"] * 1e-3)
+    value_mixed = replica_value(world, R * N * STAGES * args.steps, rmx["total_ms"])
     # accuracy: columns 0 and R-1 against the FP64 path run for the same number of steps
     errs = []
     for j in sorted({0, R - 1}):
