@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--only", choices=["fp64", "mixed"], default=None, help="time one form only (profiling)")
     ap.add_argument("--serving-jobs", type=int, default=48, help="jobs of the serving run (0: skip)")
     ap.add_argument("--refine", type=int, default=1, help="FP64 refinement sweeps per implicit solve (mixed)")
+    ap.add_argument("--groups", type=int, default=1, help="column groups of the mixed batch (own streams each)")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-budget", type=float, default=12.0, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -328,7 +329,7 @@ def bench_ours(args, rank, world, local_rank):
         qR, fR = stage_terms(R)
 
     # ---- mixed precision, R right-hand sides (FP32 sweeps + FP64 refinement) ----------------------
-    S.batch_reserve(R)
+    S.batch_reserve(R, groups=args.groups)
     U0 = np.stack([u0] + [workloads.uniform_state(j, N, bidx) for j in range(1, R)], axis=1)
     U = torch.tensor(U0, dtype=torch.float64, device="cuda")
 
@@ -455,6 +456,7 @@ def bench_ours(args, rank, world, local_rank):
             "config": {"workload": wl.name, "n1": wl.n1, "n2": wl.n2, "p": wl.p, "N": N,
                        "p2n1n2": wl.p ** 2 * wl.n1 * wl.n2, "dt": wl.dt, "stages_per_step": STAGES,
                        "rhs": R if mixed_ok else 1, "refine": args.refine if mixed_ok else 0,
+                       "column_groups": args.groups if mixed_ok else 1,
                        "operators": "one per tree node (nodal coefficients)" if S.nodal else
                                     "one per tree level (constant coefficients)",
                        "l2": "flushed (512 MB write) before every timed step",

@@ -245,6 +245,14 @@ int hps_trace_read(hps_handle *h, int kernel, int64_t *launches, int64_t *timed,
  * must precede the batched calls with this R.  Synchronizes the device. */
 int hps_batch_reserve(hps_handle *h, int R);
 
+/* hps_batch_reserve with the columns of every later batched call split into `groups` (1..8)
+ * column groups of multiples of 4 columns, each run on its own internal stream, forked from
+ * and joined back into the caller's stream (also inside a recorded graph).  Groups overlap one
+ * group's FP64 residual kernels with another group's FP32 sweeps.  Results agree with the
+ * ungrouped call to rounding (the split of the FP32 merge sums depends on the column count).
+ * The default is one group; hps_batch_reserve keeps the handle's current count. */
+int hps_batch_reserve_groups(hps_handle *h, int R, int groups);
+
 /* R solves of hps_solve at once.  rhs: N_int x R; f: N_bd x R or NULL; u: N x R (written);
  * refine: 0..8 refinement sweeps. */
 int hps_solve_batch(hps_handle *h, int R, const double *rhs, const double *f, double *u, int refine,

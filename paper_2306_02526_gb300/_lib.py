@@ -79,6 +79,7 @@ SIGNATURES = {
     "hps_trace_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int64_p, c_int64_p,
                                       ctypes.POINTER(ctypes.c_double)]),
     "hps_batch_reserve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "hps_batch_reserve_groups": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "hps_solve_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "ark_step_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_double,

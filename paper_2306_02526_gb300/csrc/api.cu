@@ -93,6 +93,15 @@ std::vector<Level> make_levels(const GridDims &g) {
       const int64_t gi = hps::iface_bd(g, cur.origin[0], cur.origin[1], cur.a, cur.c, cur.split, r);
       if (pa.at(gi) != cur.j3a + r || pb.at(gi) != cur.j3b + r) throw std::bad_alloc();
     }
+    // child boundary position -> parent boundary position, or nb + interface position
+    cur.cmap.assign(2 * cur.nbc, -1);
+    for (int pos = 0; pos < cur.nb; ++pos) cur.cmap[cur.hsrc[pos]] = pos;
+    for (int r = 0; r < cur.n3; ++r) {
+      cur.cmap[cur.j3a + r] = cur.nb + r;
+      cur.cmap[cur.nbc + cur.j3b + r] = cur.nb + r;
+    }
+    for (int v : cur.cmap)
+      if (v < 0) throw std::bad_alloc();
   }
   return lev;
 }
@@ -261,7 +270,7 @@ size_t hps_bytes(const hps_tree *tree, int p, int coeff_kind, int flags) {
   size_t s = opset_bytes(lev, q, b, shared, false) + opset_bytes(lev, q, b, true, true) + work_bytes(g, lev);
   if (coeff_kind == HPS_COEF_NODAL) s += 5 * (size_t)g.N_int * sizeof(double);
   s += 4 * (size_t)p * p * sizeof(double);
-  for (const Level &lv : lev) s += (2 * (size_t)lv.nodes + lv.hsrc.size()) * sizeof(int);
+  for (const Level &lv : lev) s += (2 * (size_t)lv.nodes + lv.hsrc.size() + lv.cmap.size()) * sizeof(int);
   return s;
 }
 
@@ -274,6 +283,7 @@ void hps_free(hps_handle *H) {
   H->g_ark_b.destroy();
   H->g_solve_b.destroy();
   if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
+  hps::batch_release(H);
   for (void *p : H->allocs) cudaFree(p);
   delete H;
 }
@@ -329,6 +339,8 @@ int hps_build(const hps_tree *tree, int p, const hps_coeffs *coeffs, double gamm
     if (!lv.hsrc.empty()) {
       if (dalloc(H, &lv.d_hsrc, lv.hsrc.size())) return fail(HPS_ENOMEM);
       cudaMemcpyAsync(lv.d_hsrc, lv.hsrc.data(), lv.hsrc.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+      if (dalloc(H, &lv.d_cmap, lv.cmap.size())) return fail(HPS_ENOMEM);
+      cudaMemcpyAsync(lv.d_cmap, lv.cmap.data(), lv.cmap.size() * sizeof(int), cudaMemcpyHostToDevice, st);
     }
   }
   // differentiation matrices D1x, D1y, Dxx = D1x^2, Dyy = D1y^2 on this leaf size
@@ -668,9 +680,20 @@ int ark_step(hps_handle *H, double *u, double t, double dt, const hps_ark_terms 
                      (cudaStream_t)stream);
 }
 
+int hps_batch_reserve_groups(hps_handle *H, int R, int groups) {
+  if (!H) return HPS_EINVAL;
+  if (groups != H->batch.groups) {  // recorded graphs hold the old groups' buffers and streams
+    hps::drain_graph(H, H->g_ark_b);
+    hps::drain_graph(H, H->g_solve_b);
+    H->g_ark_b.destroy();
+    H->g_solve_b.destroy();
+  }
+  return hps::batch_reserve(H, R, groups);
+}
+
 int hps_batch_reserve(hps_handle *H, int R) {
   if (!H) return HPS_EINVAL;
-  return hps::batch_reserve(H, R);
+  return hps_batch_reserve_groups(H, R, H->batch.groups);
 }
 
 int hps_solve_batch(hps_handle *H, int R, const double *rhs, const double *f, double *u, int refine,

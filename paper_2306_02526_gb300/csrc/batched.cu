@@ -21,6 +21,61 @@ constexpr int kBSmemFloats = 8192;  // vector staging of the merge applies (32 K
 
 __host__ __device__ inline int round4(int r) { return (r + 3) & ~3; }
 
+// Block-wide loop over [0, n): every thread issues U independent loads before it uses any of
+// them (a warp issues in order, so a load-then-store loop would wait out one load latency per
+// element).
+template <int U, class T, class Load, class Use>
+__device__ __forceinline__ void block_gather(int n, Load ld, Use use) {
+  for (int base = threadIdx.x; base < n; base += U * blockDim.x) {
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx < n) v[u] = ld(idx);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx < n) use(idx, v[u]);
+    }
+  }
+}
+
+// The stage right-hand side of one leaf, sum_t coef_t ptr_t, over its nq = q*R contiguous
+// entries from offset `off` (FP64): saved to Rsave if non-null and staged as FP32 at
+// Rs[(f / R) * Rp + f % R]; U entries per thread and two terms per round of loads.
+template <int U>
+__device__ __forceinline__ void stage_combo(const Combo &rhs, int64_t off, int nq, int R, int Rp,
+                                            double *__restrict__ Rsave, float *Rs) {
+  for (int base = threadIdx.x; base < nq; base += U * blockDim.x) {
+    double acc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] = 0.0;
+    for (int t = 0; t < rhs.n; t += 2) {
+      const bool two = t + 1 < rhs.n;
+      const double *s0 = rhs.ptr[t] + off, *s1 = two ? rhs.ptr[t + 1] + off : s0;
+      const double c0 = rhs.coef[t], c1 = two ? rhs.coef[t + 1] : 0.0;
+      double v0[U], v1[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = base + u * blockDim.x;
+        v0[u] = idx < nq ? s0[idx] : 0.0;
+        v1[u] = idx < nq ? s1[idx] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc[u] = fma(c1, v1[u], fma(c0, v0[u], acc[u]));
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx < nq) {
+        if (Rsave) Rsave[off + idx] = acc[u];
+        Rs[(idx / R) * Rp + idx % R] = (float)acc[u];
+      }
+    }
+  }
+}
+
 // flux (D_bi w)_e of column j of an interior field W[node*Rp + j] (float)
 __device__ float flux32(int e, int j, int Rp, const float *W, const float *D1x, const float *D1y, int p, int m) {
   const int side = e / m, t = e % m;
@@ -67,15 +122,10 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_up(GridDims g, int R, const int 
   const int k = blockIdx.x;
   const int64_t l0 = ((int64_t)origin[2 * k + 1] * g.n1 + origin[2 * k]) * q;
   for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) smf[i] = (float)Dg[i];
-  for (int idx = threadIdx.x; idx < q * Rp; idx += blockDim.x) {
-    const int r = idx / Rp, j = idx % Rp;
-    double v = 0.0;
-    if (j < R) {
-      for (int t = 0; t < rhs.n; ++t) v = fma(rhs.coef[t], rhs.ptr[t][(l0 + r) * R + j], v);
-      if (Rsave) Rsave[(l0 + r) * R + j] = v;
-    }
-    Rs[idx] = (float)v;
-  }
+  if (Rp != R)  // padding columns
+    for (int idx = threadIdx.x; idx < q * Rp; idx += blockDim.x) Rs[idx] = 0.f;
+  __syncthreads();
+  stage_combo<8>(rhs, l0 * R, q * R, R, Rp, Rsave, Rs);
   __syncthreads();
   const int QQ = (q + 3) / 4, CG = Rp / TC;
   for (int it = threadIdx.x; it < QQ * CG; it += blockDim.x) {
@@ -122,10 +172,13 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_down(GridDims g, int R, const in
   const int k = blockIdx.x;
   const int ix = origin[2 * k], iy = origin[2 * k + 1];
   const int64_t l0 = ((int64_t)iy * g.n1 + ix) * q;
-  for (int idx = threadIdx.x; idx < b * Rp; idx += blockDim.x) {
-    const int e = idx / Rp, j = idx % Rp;
-    ub[idx] = j < R ? g32[box_bd(g, ix, iy, 1, 1, e) * R + j] : 0.f;
-  }
+  block_gather<8, float>(
+      b * Rp,
+      [&](int idx) {
+        const int e = idx / Rp, j = idx % Rp;
+        return j < R ? g32[box_bd(g, ix, iy, 1, 1, e) * R + j] : 0.f;
+      },
+      [&](int idx, float v) { ub[idx] = v; });
   __syncthreads();
   const int QQ = (q + 3) / 4, CG = Rp / TC;
   for (int it = threadIdx.x; it < QQ * CG; it += blockDim.x) {
@@ -188,15 +241,10 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_up_narrow(GridDims g, int R, con
   const int k = blockIdx.x;
   const int64_t l0 = ((int64_t)origin[2 * k + 1] * g.n1 + origin[2 * k]) * q;
   for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) smf[i] = (float)Dg[i];
-  for (int idx = threadIdx.x; idx < q * 4; idx += blockDim.x) {
-    const int r = idx / 4, j = idx % 4;
-    double v = 0.0;
-    if (j < R) {
-      for (int t = 0; t < rhs.n; ++t) v = fma(rhs.coef[t], rhs.ptr[t][(l0 + r) * R + j], v);
-      if (Rsave) Rsave[(l0 + r) * R + j] = v;
-    }
-    Rs[idx] = (float)v;
-  }
+  if (R != 4)
+    for (int idx = threadIdx.x; idx < q * 4; idx += blockDim.x) Rs[idx] = 0.f;
+  __syncthreads();
+  stage_combo<4>(rhs, l0 * R, q * R, R, 4, Rsave, Rs);
   __syncthreads();
   if (identity) {
     for (int idx = threadIdx.x; idx < q * 4; idx += blockDim.x) Ws[idx] = Rs[idx];
@@ -230,10 +278,13 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_down_narrow(GridDims g, int R, c
   const int k = blockIdx.x;
   const int ix = origin[2 * k], iy = origin[2 * k + 1];
   const int64_t l0 = ((int64_t)iy * g.n1 + ix) * q;
-  for (int idx = threadIdx.x; idx < b * 4; idx += blockDim.x) {
-    const int e = idx / 4, j = idx % 4;
-    ub[idx] = j < R ? g32[box_bd(g, ix, iy, 1, 1, e) * R + j] : 0.f;
-  }
+  block_gather<4, float>(
+      b * 4,
+      [&](int idx) {
+        const int e = idx / 4, j = idx % 4;
+        return j < R ? g32[box_bd(g, ix, iy, 1, 1, e) * R + j] : 0.f;
+      },
+      [&](int idx, float v) { ub[idx] = v; });
   __syncthreads();
   if (!identity) quad_apply_sliced(SlT + (int64_t)k * strS, ldS, b, ub, 4, QQ, KS, part);
   __syncthreads();
@@ -342,10 +393,13 @@ __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict
   const int node0 = ng * P.npc, nn = min(P.npc, P.nodes - node0);
   const int ks = blockIdx.y, c0 = ks * P.kchunk, klen = min(P.kchunk, P.K - c0);
   const int Rp = P.Rp;
-  for (int idx = threadIdx.x; idx < nn * klen * Rp; idx += blockDim.x) {
-    const int lo = idx / (klen * Rp), rem = idx % (klen * Rp), c = rem / Rp, j = rem % Rp;
-    xs[idx] = j < P.R ? xl(node0 + lo, c0 + c, j) : 0.f;
-  }
+  block_gather<8, float>(
+      nn * klen * Rp,
+      [&](int idx) {
+        const int lo = idx / (klen * Rp), rem = idx % (klen * Rp), c = rem / Rp, j = rem % Rp;
+        return j < P.R ? xl(node0 + lo, c0 + c, j) : 0.f;
+      },
+      [&](int idx, float v) { xs[idx] = v; });
   __syncthreads();
   int lo, rq, cg;
   if (P.npc > 1) {
@@ -403,22 +457,216 @@ __global__ void k_b_reduce(BPlan P, const float *__restrict__ partial, EP ep) {
 }
 
 template <class XL, class EP>
-int launch_b(hps_handle *H, int slot, const BPlan &P, const float *AT, int ld, int64_t str, XL xl, EP ep,
-             cudaStream_t st) {
+int launch_b(hps_handle *H, BatchWork &B, int slot, const BPlan &P, const float *AT, int ld, int64_t str, XL xl,
+             EP ep, cudaStream_t st) {
   const size_t smem = (size_t)P.npc * P.kchunk * P.Rp * sizeof(float);
-  if (P.ksplit > 1 && (size_t)P.ksplit * P.nodes * P.M * P.Rp > H->batch.partial_len) return HPS_EINVAL;
+  if (P.ksplit > 1 && (size_t)P.ksplit * P.nodes * P.M * P.Rp > B.partial_len) return HPS_EINVAL;
   H->trace.begin(slot, st);
   const dim3 grid(P.node_groups * P.row_tiles, P.ksplit);
   if (P.TC == 8)
-    k_b_gemv<8, XL, EP><<<grid, kBT, smem, st>>>(P, AT, ld, str, xl, ep, H->batch.partial32);
+    k_b_gemv<8, XL, EP><<<grid, kBT, smem, st>>>(P, AT, ld, str, xl, ep, B.partial32);
   else
-    k_b_gemv<4, XL, EP><<<grid, kBT, smem, st>>>(P, AT, ld, str, xl, ep, H->batch.partial32);
+    k_b_gemv<4, XL, EP><<<grid, kBT, smem, st>>>(P, AT, ld, str, xl, ep, B.partial32);
   if (P.ksplit > 1) {
     const int64_t n = (int64_t)P.nodes * P.M * P.R;
-    k_b_reduce<EP><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, H->batch.partial32, ep);
+    k_b_reduce<EP><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, B.partial32, ep);
   }
   H->trace.end(slot, st);
   return HPS_OK;
+}
+
+// ---- merges of the lower tree levels as one dataflow kernel per direction ------------------
+// On the lower levels a node's merge is far smaller than a kernel launch.  There, one grid of
+// resident CTAs takes node tasks in ticket order (upward: deepest level first; downward: top
+// level first) and a task waits only for its own inputs: upward the two children, downward the
+// parent (per-node flags, release/acquire).  Tickets are taken by running CTAs in an order in
+// which every dependency holds a smaller ticket, so every awaited task is already running.
+// Each wait is bounded by a time limit; on expiry the handle's error word is set (hps_status
+// reports HPS_ETIMEOUT) and the CTA stops taking tasks.
+constexpr int kFlowMaxLevels = 12;
+
+struct FlowLevel {
+  int nodes, n3, nb, nbc, j3a, j3b, a, c, split, level;
+  const int *origin, *hsrc;
+  const float *X, *T, *S;
+  int ldX, ldT, ldS;
+  int64_t strX, strT, strS;
+  float *w3, *h;
+  const float *hC;  // h of the child level
+  int flag0;        // first node flag of this level
+};
+
+struct FlowArgs {
+  int nlev, R, Rp, ntasks;
+  GridDims g;
+  FlowLevel lv[kFlowMaxLevels];  // index t = level - (top flow level)
+  int seg_t[kFlowMaxLevels], seg0[kFlowMaxLevels + 1];  // ticket segments: level index, first ticket
+  unsigned *sync;  // [0]: ticket counter, [1 ..]: node flags
+  int *err;
+  const double *jump;
+  float *g32;
+  unsigned long long limit_ns;
+};
+
+__device__ __forceinline__ unsigned long long flow_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned flow_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// thread 0: wait (bounded) until every flag in f[0..n) is set; false on timeout or error
+__device__ bool flow_wait(const unsigned *f, int n, int *err, unsigned long long limit_ns) {
+  unsigned long long t0 = 0;
+  for (int i = 0; i < n; ++i) {
+    while (!flow_acquire(f + i)) {
+      if (flow_acquire(reinterpret_cast<const unsigned *>(err))) return false;
+      if (t0 == 0) t0 = flow_ns();
+      else if (flow_ns() - t0 > limit_ns) {
+        atomicOr(err, 1);
+        return false;
+      }
+      __nanosleep(32);
+    }
+  }
+  return true;
+}
+
+// acc[0..3] = sum_c A(r, c) x[c][0..3]: A stored transposed (A(r, c) at a[c * ld]), x in shared
+// memory with row stride Rp
+__device__ __forceinline__ void flow_dot(float4 &acc, const float *__restrict__ a, int ld, int K, const float *x,
+                                         int Rp) {
+#pragma unroll 8
+  for (int c = 0; c < K; ++c) {
+    const float av = __ldg(a + (int64_t)c * ld);
+    const float4 xv = *reinterpret_cast<const float4 *>(x + c * Rp);
+    acc.x = fmaf(av, xv.x, acc.x);
+    acc.y = fmaf(av, xv.y, acc.y);
+    acc.z = fmaf(av, xv.z, acc.z);
+    acc.w = fmaf(av, xv.w, acc.w);
+  }
+}
+
+__device__ __forceinline__ bool flow_task(const FlowArgs &A, int &t, int &k) {
+  __shared__ int s_ticket;
+  __syncthreads();
+  if (threadIdx.x == 0) s_ticket = (int)atomicAdd(A.sync, 1u);
+  __syncthreads();
+  const int tk = s_ticket;
+  if (tk >= A.ntasks) return false;
+  int s = 0;
+  while (tk >= A.seg0[s + 1]) ++s;
+  t = A.seg_t[s];
+  k = tk - A.seg0[s];
+  return true;
+}
+
+__device__ __forceinline__ bool flow_wait_block(const FlowArgs &A, const unsigned *f, int n) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) s_ok = flow_wait(f, n, A.err, A.limit_ns);
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ __forceinline__ void flow_done(const FlowArgs &A, const FlowLevel &L, int k) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicExch(A.sync + 1 + L.flag0 + k, 1u);
+  }
+}
+
+__global__ void __launch_bounds__(kBT) k_b_flow_up(FlowArgs A) {
+  extern __shared__ float sm[];
+  const int R = A.R, Rp = A.Rp, CQ = Rp / 4;
+  int t, k;
+  while (flow_task(A, t, k)) {
+    const FlowLevel &L = A.lv[t];
+    if (t + 1 < A.nlev && !flow_wait_block(A, A.sync + 1 + A.lv[t + 1].flag0 + 2 * k, 2)) return;
+    float *D = sm, *Ws = sm + L.n3 * Rp;
+    // d = h^b_3 - h^a_3 (+ the interface right-hand side)
+    block_gather<4, float>(
+        L.n3 * Rp,
+        [&](int idx) {
+          const int j = idx % Rp, cc = idx / Rp;
+          if (j >= R) return 0.f;
+          float v = L.hC[((int64_t)(2 * k + 1) * L.nbc + L.j3b + cc) * R + j] -
+                    L.hC[((int64_t)(2 * k) * L.nbc + L.j3a + cc) * R + j];
+          if (A.jump)
+            v += (float)A.jump[iface_bd(A.g, L.origin[2 * k], L.origin[2 * k + 1], L.a, L.c, L.split, cc) * R + j];
+          return v;
+        },
+        [&](int idx, float v) { D[idx] = v; });
+    __syncthreads();
+    // w3 = X d
+    for (int it = threadIdx.x; it < L.n3 * CQ; it += blockDim.x) {
+      const int r = it % L.n3, j0 = 4 * (it / L.n3);
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      flow_dot(acc, L.X + (int64_t)k * L.strX + r, L.ldX, L.n3, D + j0, Rp);
+      *reinterpret_cast<float4 *>(Ws + r * Rp + j0) = acc;
+      float *w = L.w3 + ((int64_t)k * L.n3 + r) * R + j0;
+      if (j0 + 0 < R) w[0] = acc.x;
+      if (j0 + 1 < R) w[1] = acc.y;
+      if (j0 + 2 < R) w[2] = acc.z;
+      if (j0 + 3 < R) w[3] = acc.w;
+    }
+    __syncthreads();
+    // h of the parent = [h^a_1; h^b_2] + Tcat w3 (none at the root of the tree)
+    if (L.level > 0) {
+      for (int it = threadIdx.x; it < L.nb * CQ; it += blockDim.x) {
+        const int r = it % L.nb, j0 = 4 * (it / L.nb);
+        const float *hc = L.hC + ((int64_t)(2 * k) * L.nbc + L.hsrc[r]) * R + j0;
+        float4 acc = make_float4(j0 < R ? hc[0] : 0.f, j0 + 1 < R ? hc[1] : 0.f, j0 + 2 < R ? hc[2] : 0.f,
+                                 j0 + 3 < R ? hc[3] : 0.f);
+        flow_dot(acc, L.T + (int64_t)k * L.strT + r, L.ldT, L.n3, Ws + j0, Rp);
+        float *h = L.h + ((int64_t)k * L.nb + r) * R + j0;
+        if (j0 + 0 < R) h[0] = acc.x;
+        if (j0 + 1 < R) h[1] = acc.y;
+        if (j0 + 2 < R) h[2] = acc.z;
+        if (j0 + 3 < R) h[3] = acc.w;
+      }
+    }
+    flow_done(A, L, k);
+  }
+}
+
+__global__ void __launch_bounds__(kBT) k_b_flow_down(FlowArgs A) {
+  extern __shared__ float sm[];
+  const int R = A.R, Rp = A.Rp, CQ = Rp / 4;
+  int t, k;
+  while (flow_task(A, t, k)) {
+    const FlowLevel &L = A.lv[t];
+    if (t > 0 && !flow_wait_block(A, A.sync + 1 + A.lv[t - 1].flag0 + k / 2, 1)) return;
+    float *Ub = sm;
+    const int ox = L.origin[2 * k], oy = L.origin[2 * k + 1];
+    block_gather<8, float>(
+        L.nb * Rp,
+        [&](int idx) {
+          const int j = idx % Rp, pos = idx / Rp;
+          return j < R ? A.g32[box_bd(A.g, ox, oy, L.a, L.c, pos) * R + j] : 0.f;
+        },
+        [&](int idx, float v) { Ub[idx] = v; });
+    __syncthreads();
+    // u3 = S u_b + w3, scattered to the interface points
+    for (int it = threadIdx.x; it < L.n3 * CQ; it += blockDim.x) {
+      const int r = it % L.n3, j0 = 4 * (it / L.n3);
+      const float *w = L.w3 + ((int64_t)k * L.n3 + r) * R + j0;
+      float4 acc = make_float4(j0 < R ? w[0] : 0.f, j0 + 1 < R ? w[1] : 0.f, j0 + 2 < R ? w[2] : 0.f,
+                               j0 + 3 < R ? w[3] : 0.f);
+      flow_dot(acc, L.S + (int64_t)k * L.strS + r, L.ldS, L.nb, Ub + j0, Rp);
+      float *o = A.g32 + iface_bd(A.g, ox, oy, L.a, L.c, L.split, r) * R + j0;
+      if (j0 + 0 < R) o[0] = acc.x;
+      if (j0 + 1 < R) o[1] = acc.y;
+      if (j0 + 2 < R) o[2] = acc.z;
+      if (j0 + 3 < R) o[3] = acc.w;
+    }
+    flow_done(A, L, k);
+  }
 }
 
 // ---- FP64 leaf kernels: residual, stage epilogue, explicit first stage ---------------------
@@ -429,7 +677,8 @@ struct Leaf64Args {
   const double *u;      // [N][R]
   const double *Rb;     // [N_int][R] stage right-hand side (kResid, kEpilogue)
   double *out0, *out1;  // kResid: r; kEpilogue / kEval: KL, KE
-  const double *q;      // [N_int][R] or null
+  const double *q;      // [N_int][qld] (columns qoff ..) or null
+  int qld, qoff;
   const double *coef;   // 5 x N_int or null (constants in cst)
   double cst[5];
   int64_t N_int;
@@ -439,31 +688,32 @@ struct Leaf64Args {
   int need_d1, need_d2;  // first / second derivatives needed (zero terms are skipped)
 };
 
-__global__ void __launch_bounds__(kBT) k_b_leaf64(GridDims g, const int *__restrict__ origin, Leaf64Args A,
-                                                  const double *__restrict__ Dg) {
+__global__ void __launch_bounds__(kBT) k_b_leaf64(GridDims g, int nodes, const int *__restrict__ origin,
+                                                  Leaf64Args A, const double *__restrict__ Dg) {
   extern __shared__ double sd[];
   const int p = g.p, m = g.m, q = m * m, pp = p * p, R = A.R;
   const int Rc = max(1, min(R, 4096 / pp));
   double *D1x = sd, *D1y = sd + pp, *Dxx = sd + 2 * pp, *Dyy = sd + 3 * pp, *U = sd + 4 * pp;  // U [pp][Rc]
-  const int k = blockIdx.x;
+  for (int i = threadIdx.x; i < 4 * pp; i += blockDim.x) sd[i] = Dg[i];
+  for (int k = blockIdx.x; k < nodes; k += gridDim.x) {  // one leaf per CTA, or a persistent grid
   const int ix = origin[2 * k], iy = origin[2 * k + 1];
   const int64_t l0 = ((int64_t)iy * g.n1 + ix) * q;
-  for (int i = threadIdx.x; i < 4 * pp; i += blockDim.x) sd[i] = Dg[i];
   for (int j0 = 0; j0 < R; j0 += Rc) {
     const int rc = min(Rc, R - j0);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < pp * rc; idx += blockDim.x) {
-      const int node = idx / rc, jj = idx % rc;
-      const int i = node % p, j = node / p;
-      const bool ei = (i == 0 || i == p - 1), ej = (j == 0 || j == p - 1);
-      double v = 0.0;
-      int64_t gi = -1;
-      if (!ei && !ej) gi = l0 + (j - 1) * m + (i - 1);
-      else if (ei && !ej) gi = vseg(g, ix + (i == 0 ? 0 : 1), iy, j - 1);
-      else if (!ei && ej) gi = hseg(g, iy + (j == 0 ? 0 : 1), ix, i - 1);
-      if (gi >= 0) v = A.u[gi * R + j0 + jj];
-      U[node * Rc + jj] = v;
-    }
+    block_gather<4, double>(
+        pp * rc,
+        [&](int idx) {
+          const int node = idx / rc, jj = idx % rc;
+          const int i = node % p, j = node / p;
+          const bool ei = (i == 0 || i == p - 1), ej = (j == 0 || j == p - 1);
+          int64_t gi = -1;
+          if (!ei && !ej) gi = l0 + (j - 1) * m + (i - 1);
+          else if (ei && !ej) gi = vseg(g, ix + (i == 0 ? 0 : 1), iy, j - 1);
+          else if (!ei && ej) gi = hseg(g, iy + (j == 0 ? 0 : 1), ix, i - 1);
+          return gi >= 0 ? A.u[gi * R + j0 + jj] : 0.0;
+        },
+        [&](int idx, double v) { U[(idx / rc) * Rc + idx % rc] = v; });
     __syncthreads();
     for (int idx = threadIdx.x; idx < q * rc; idx += blockDim.x) {
       const int rr = idx / rc, jj = idx % rc;
@@ -502,11 +752,12 @@ __global__ void __launch_bounds__(kBT) k_b_leaf64(GridDims g, const int *__restr
           case HPS_G_BURGERS: e = -uu * (A.gp0 * ux + A.gp1 * uy); break;
           default: e = 0.0;
         }
-        if (A.q) e += A.q[o];
+        if (A.q) e += A.q[gi * A.qld + A.qoff + col];
         A.out0[o] = A.mode == kEval ? A.dt * Lu : (uu - A.Rb[o]) * A.inv_gamma;
         A.out1[o] = A.dt * e;
       }
     }
+  }
   }
 }
 
@@ -526,7 +777,7 @@ __global__ void k_b_pointwise(int64_t n, Leaf64Args A) {
     case HPS_G_FISHER: e = A.gp0 * uu * (1.0 - uu); break;
     default: e = 0.0;
   }
-  if (A.q) e += A.q[o];
+  if (A.q) e += A.q[(o / A.R) * A.qld + A.qoff + o % A.R];
   A.out0[o] = (uu - A.Rb[o]) * A.inv_gamma;
   A.out1[o] = A.dt * e;
 }
@@ -549,6 +800,7 @@ __global__ void k_b_jump(GridDims g, int R, const double *__restrict__ u, double
     const int iy = (int)(s % g.n2), L = (int)(s / g.n2) + 1;
     gi = vseg(g, L, iy, jn - 1);
     const int64_t lw = ((int64_t)iy * g.n1 + (L - 1)) * q, le = ((int64_t)iy * g.n1 + L) * q;
+#pragma unroll 4
     for (int k = 0; k < p; ++k) {
       const int64_t iw = k == 0 ? vseg(g, L - 1, iy, jn - 1) : k == p - 1 ? gi : lw + (jn - 1) * m + (k - 1);
       const int64_t ie = k == 0 ? gi : k == p - 1 ? vseg(g, L + 1, iy, jn - 1) : le + (jn - 1) * m + (k - 1);
@@ -562,6 +814,7 @@ __global__ void k_b_jump(GridDims g, int R, const double *__restrict__ u, double
     const int ix = (int)(s % g.n1), L = (int)(s / g.n1) + 1;
     gi = hseg(g, L, ix, in - 1);
     const int64_t ls = ((int64_t)(L - 1) * g.n1 + ix) * q, ln = ((int64_t)L * g.n1 + ix) * q;
+#pragma unroll 4
     for (int k = 0; k < p; ++k) {
       const int64_t is = k == 0 ? hseg(g, L - 1, ix, in - 1) : k == p - 1 ? gi : ls + (k - 1) * m + (in - 1);
       const int64_t inn = k == 0 ? gi : k == p - 1 ? hseg(g, L + 1, ix, in - 1) : ln + (k - 1) * m + (in - 1);
@@ -590,7 +843,9 @@ __device__ __forceinline__ int64_t bd_pos(const GridDims &g, int64_t gi) {
   return -1;
 }
 
-__global__ void k_b_set_boundary32(GridDims g, int R, float *__restrict__ g32, const double *__restrict__ f) {
+// f: [N_bd][fld], this call's columns from foff
+__global__ void k_b_set_boundary32(GridDims g, int R, float *__restrict__ g32, const double *__restrict__ f, int fld,
+                                   int foff) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= g.N_bd * R) return;
   const int64_t kk = idx / R;
@@ -601,13 +856,13 @@ __global__ void k_b_set_boundary32(GridDims g, int R, float *__restrict__ g32, c
   else if (kk < 2 * nv) gi = g.N_int + (int64_t)g.n1 * nv + (kk - nv);
   else if (kk < 2 * nv + nh) gi = g.N_int + g.N_v + (kk - 2 * nv);
   else gi = g.N_int + g.N_v + (int64_t)g.n2 * nh + (kk - 2 * nv - nh);
-  g32[gi * R + j] = f ? (float)f[idx] : 0.f;
+  g32[gi * R + j] = f ? (float)f[kk * fld + foff + j] : 0.f;
 }
 
 // u (FP64) from the FP32 sweep result: assign or add; interior points optionally; shared-edge
 // points always; outer-boundary points set to f exactly (assign) or left alone (add).
 __global__ void k_b_finish(GridDims g, int R, const float *__restrict__ g32, double *__restrict__ u, int assign,
-                           int interior, const double *__restrict__ f) {
+                           int interior, const double *__restrict__ f, int fld, int foff) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= g.N * R) return;
   const int64_t gi = idx / R;
@@ -618,7 +873,7 @@ __global__ void k_b_finish(GridDims g, int R, const float *__restrict__ g32, dou
   }
   const int64_t kk = bd_pos(g, gi);
   if (kk >= 0) {
-    if (assign) u[idx] = f ? f[kk * R + idx % R] : 0.0;
+    if (assign) u[idx] = f ? f[kk * fld + foff + idx % R] : 0.0;
     return;
   }
   u[idx] = assign ? (double)g32[idx] : u[idx] + (double)g32[idx];
@@ -673,8 +928,10 @@ int convert_opset(hps_handle *H, const OpSet &ops, OpSet32 &o32, bool shared) {
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
-size_t partial_floats(hps_handle *H, int R) {
+// Split-K scratch for calls with up to Rmax columns (the plan depends on the column count).
+size_t partial_floats(hps_handle *H, int Rmax) {
   size_t mx = 0;
+  for (int R = 1; R <= Rmax; ++R)
   for (int l = 0; l < H->L; ++l) {
     const Level &lv = H->lev[l];
     const BPlan P[3] = {plan_b(lv.n3, lv.n3, lv.nodes, R, 2 * H->num_sms), plan_b(lv.nb, lv.n3, lv.nodes, R, 2 * H->num_sms),
@@ -685,11 +942,30 @@ size_t partial_floats(hps_handle *H, int R) {
   return mx;
 }
 
+int flow_launch(hps_handle *H, BatchWork &B, const FlowArgs &FA, bool up, size_t smem, int nflags, cudaStream_t st) {
+  if ((size_t)nflags + 1 > B.flow_len) return HPS_EINVAL;
+  auto kern = up ? k_b_flow_up : k_b_flow_down;
+  static size_t set_up = 0, set_down = 0;
+  size_t &set = up ? set_up : set_down;
+  if (smem > 48 * 1024 && smem > set) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set = smem;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBT, smem) != cudaSuccess || per_sm < 1)
+    return HPS_ECUDA;
+  const int grid = std::min(FA.ntasks, per_sm * H->num_sms);
+  cudaMemsetAsync(B.flow_sync, 0, ((size_t)nflags + 1) * sizeof(unsigned), st);
+  H->trace.begin(up ? kMergeUpFused : kMergeDownFused, st);
+  kern<<<grid, kBT, smem, st>>>(FA);
+  H->trace.end(up ? kMergeUpFused : kMergeDownFused, st);
+  return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
+}
+
 // One FP32 sweep on R columns: leaf applies, merges up (with an optional FP64 interface
 // right-hand side), merges down into g32 (whose outer boundary the caller has set), leaf solves.
-int sweep32(hps_handle *H, const OpSet &ops, const OpSet32 &o32, int R, const Combo &rhs, double *Rsave,
-            const double *jump, cudaStream_t st) {
-  Batch &B = H->batch;
+int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, int R, const Combo &rhs,
+            double *Rsave, const double *jump, cudaStream_t st) {
   const int L = H->L, p = H->p, q = H->q, b = H->b, Rp = round4(R);
   const Level &leaf = H->lev[L];
   const int target = 2 * H->num_sms;
@@ -724,28 +1000,100 @@ int sweep32(hps_handle *H, const OpSet &ops, const OpSet32 &o32, int R, const Co
                                                     o32.Ainv.str, ops.identity ? 1 : 0, H->d_D, B.w32, B.h32[L]);
     H->trace.end(kLeafUp, st);
   }
-  for (int l = L - 1; l >= 0; --l) {
+  // lower levels (small nodes): one dataflow kernel per direction (levels lr .. L-1)
+  int lr = L;
+  while (lr > 0 && L - lr < std::min(kFlowMaxLevels, H->batch.flow_levels) &&
+         H->lev[lr - 1].n3 <= H->batch.flow_n3_max && (int64_t)H->lev[lr - 1].nb * Rp <= 16384)
+    --lr;
+  const int nflow = L - lr;
+  FlowArgs FA{};
+  size_t smem_up = 0, smem_down = 0;
+  int nflags = 0;
+  if (nflow > 0) {
+    FA.nlev = nflow;
+    FA.R = R;
+    FA.Rp = Rp;
+    FA.g = H->g;
+    int n3max = 0, nbmax = 0;
+    for (int t = 0; t < nflow; ++t) {
+      const int l = lr + t;
+      const Level &lv = H->lev[l];
+      FlowLevel &F = FA.lv[t];
+      F.nodes = lv.nodes;
+      F.n3 = lv.n3;
+      F.nb = lv.nb;
+      F.nbc = lv.nbc;
+      F.j3a = lv.j3a;
+      F.j3b = lv.j3b;
+      F.a = lv.a;
+      F.c = lv.c;
+      F.split = lv.split;
+      F.level = l;
+      F.origin = lv.d_origin;
+      F.hsrc = lv.d_hsrc;
+      F.X = o32.X[l].p;
+      F.ldX = o32.X[l].ld;
+      F.strX = o32.X[l].str;
+      F.T = o32.Tcat[l].p;
+      F.ldT = o32.Tcat[l].ld;
+      F.strT = o32.Tcat[l].str;
+      F.S = o32.S[l].p;
+      F.ldS = o32.S[l].ld;
+      F.strS = o32.S[l].str;
+      F.w3 = B.w332[l];
+      F.h = B.h32[l];
+      F.hC = B.h32[l + 1];
+      F.flag0 = nflags;
+      nflags += lv.nodes;
+      n3max = std::max(n3max, lv.n3);
+      nbmax = std::max(nbmax, lv.nb);
+    }
+    FA.ntasks = nflags;
+    FA.sync = B.flow_sync;
+    FA.err = H->perr;
+    FA.jump = jump;
+    FA.g32 = B.g32;
+    FA.limit_ns = 2000000000ull;
+    smem_up = (size_t)2 * n3max * Rp * sizeof(float);
+    smem_down = (size_t)nbmax * Rp * sizeof(float);
+    // upward ticket order: deepest level first
+    for (int s2 = 0, t = nflow - 1; t >= 0; --t, ++s2) {
+      FA.seg_t[s2] = t;
+      FA.seg0[s2] = s2 == 0 ? 0 : FA.seg0[s2 - 1] + FA.lv[FA.seg_t[s2 - 1]].nodes;
+    }
+    FA.seg0[nflow] = nflags;
+    if (int e = flow_launch(H, B, FA, true, smem_up, nflags, st)) return e;
+  }
+  for (int l = lr - 1; l >= 0; --l) {
     const Level &lv = H->lev[l];
     const MergeOps &mo = ops.merge[l];
     const BPlan Pw = plan_b(lv.n3, lv.n3, lv.nodes, R, target);
-    if (int e = launch_b(H, kMergeUpW3, Pw, o32.X[l].p, o32.X[l].ld, o32.X[l].str,
+    if (int e = launch_b(H, B, kMergeUpW3, Pw, o32.X[l].p, o32.X[l].ld, o32.X[l].str,
                          BXDiff{B.h32[l + 1], lv.nbc, lv.j3a, lv.j3b, R, jump, H->g, lv.d_origin, lv.a, lv.c, lv.split},
                          BEStore{B.w332[l], lv.n3, R}, st))
       return e;
     if (l > 0) {
       const BPlan Ph = plan_b(lv.nb, lv.n3, lv.nodes, R, target);
-      if (int e = launch_b(H, kMergeUpH, Ph, o32.Tcat[l].p, o32.Tcat[l].ld, o32.Tcat[l].str, BXVec{B.w332[l], lv.n3, R},
+      if (int e = launch_b(H, B, kMergeUpH, Ph, o32.Tcat[l].p, o32.Tcat[l].ld, o32.Tcat[l].str, BXVec{B.w332[l], lv.n3, R},
                            BEFlux{lv.d_hsrc, B.h32[l + 1], lv.nbc, lv.nb, R, B.h32[l]}, st))
         return e;
     }
   }
-  for (int l = 0; l < L; ++l) {
+  for (int l = 0; l < lr; ++l) {
     const Level &lv = H->lev[l];
-    const MergeOps &mo = ops.merge[l];
     const BPlan Pd = plan_b(lv.n3, lv.nb, lv.nodes, R, target);
-    if (int e = launch_b(H, kMergeDown, Pd, o32.S[l].p, o32.S[l].ld, o32.S[l].str, BXBd{H->g, lv.d_origin, lv.a, lv.c, R, B.g32},
+    if (int e = launch_b(H, B, kMergeDown, Pd, o32.S[l].p, o32.S[l].ld, o32.S[l].str, BXBd{H->g, lv.d_origin, lv.a, lv.c, R, B.g32},
                          BEScatter{H->g, lv.d_origin, lv.a, lv.c, lv.split, lv.n3, R, B.w332[l], B.g32}, st))
       return e;
+  }
+  if (nflow > 0) {
+    // downward ticket order: top flow level first
+    for (int t = 0; t < nflow; ++t) {
+      FA.seg_t[t] = t;
+      FA.seg0[t] = t == 0 ? 0 : FA.seg0[t - 1] + FA.lv[t - 1].nodes;
+    }
+    FA.seg0[nflow] = nflags;
+    if (int e = flow_launch(H, B, FA, false, smem_down, nflags, st)) return e;
   }
   H->trace.begin(kLeafDown, st);
   if (narrow)
@@ -760,6 +1108,7 @@ int sweep32(hps_handle *H, const OpSet &ops, const OpSet32 &o32, int R, const Co
   H->trace.end(kLeafDown, st);
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
+
 
 Leaf64Args leaf64_args(hps_handle *H, int mode, int R) {
   Leaf64Args A{};
@@ -797,16 +1146,17 @@ int leaf64(hps_handle *H, Leaf64Args A, cudaStream_t st) {
     set = smem;
   }
   const Level &leaf = H->lev[H->L];
+  const int per_sm = H->batch.fp64_ctas_per_sm;
+  const int grid = per_sm > 0 ? std::min(leaf.nodes, per_sm * H->num_sms) : leaf.nodes;
   H->trace.begin(slot, st);
-  k_b_leaf64<<<leaf.nodes, kBT, smem, st>>>(H->g, leaf.d_origin, A, H->d_D);
+  k_b_leaf64<<<grid, kBT, smem, st>>>(H->g, leaf.nodes, leaf.d_origin, A, H->d_D);
   H->trace.end(slot, st);
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
 // Residual of the stage system for u (FP64) into B.r: interior rows (gdt = the operator's
 // gamma dt; 0 for the identity) and shared-edge flux jumps.
-int residual(hps_handle *H, int R, const double *u, const double *Rb, double gdt, cudaStream_t st) {
-  Batch &B = H->batch;
+int residual(hps_handle *H, BatchWork &B, int R, const double *u, const double *Rb, double gdt, cudaStream_t st) {
   Leaf64Args A = leaf64_args(H, kResid, R);
   A.u = u;
   A.Rb = Rb;
@@ -822,23 +1172,28 @@ int residual(hps_handle *H, int R, const double *u, const double *Rb, double gdt
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
+// Boundary data of one group: f is [N_bd][fld] with the group's columns from foff.
+struct BdView {
+  const double *f;
+  int ld, off;
+};
+
 // Solve A u = [rhs (given by combination `c`, saved to Rsave if non-null); 0; f] with refinement.
-int refined_solve(hps_handle *H, const OpSet &ops, const OpSet32 &o32, int R, const Combo &c, double *Rsave,
-                  const double *Rb, const double *f, double *u, int refine, double gdt, cudaStream_t st) {
-  Batch &B = H->batch;
+int refined_solve(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, int R, const Combo &c,
+                  double *Rsave, const double *Rb, BdView f, double *u, int refine, double gdt, cudaStream_t st) {
   const GridDims &g = H->g;
-  k_b_set_boundary32<<<blocks(g.N_bd * R), 256, 0, st>>>(g, R, B.g32, f);
-  if (int e = sweep32(H, ops, o32, R, c, Rsave, nullptr, st)) return e;
-  k_b_finish<<<blocks(g.N * R), 256, 0, st>>>(g, R, B.g32, u, 1, 1, f);
+  k_b_set_boundary32<<<blocks(g.N_bd * R), 256, 0, st>>>(g, R, B.g32, f.f, f.ld, f.off);
+  if (int e = sweep32(H, B, ops, o32, R, c, Rsave, nullptr, st)) return e;
+  k_b_finish<<<blocks(g.N * R), 256, 0, st>>>(g, R, B.g32, u, 1, 1, f.f, f.ld, f.off);
   for (int it = 0; it < refine; ++it) {
-    if (int e = residual(H, R, u, Rb, gdt, st)) return e;
-    k_b_set_boundary32<<<blocks(g.N_bd * R), 256, 0, st>>>(g, R, B.g32, nullptr);
+    if (int e = residual(H, B, R, u, Rb, gdt, st)) return e;
+    k_b_set_boundary32<<<blocks(g.N_bd * R), 256, 0, st>>>(g, R, B.g32, nullptr, 0, 0);
     Combo cr{};
     cr.n = 1;
     cr.ptr[0] = B.r;
     cr.coef[0] = 1.0;
-    if (int e = sweep32(H, ops, o32, R, cr, nullptr, B.r, st)) return e;
-    k_b_finish<<<blocks(g.N * R), 256, 0, st>>>(g, R, B.g32, u, 0, 1, nullptr);
+    if (int e = sweep32(H, B, ops, o32, R, cr, nullptr, B.r, st)) return e;
+    k_b_finish<<<blocks(g.N * R), 256, 0, st>>>(g, R, B.g32, u, 0, 1, nullptr, 0, 0);
   }
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
@@ -850,58 +1205,34 @@ void add_term_b(Combo &c, const double *p, double coef) {
   ++c.n;
 }
 
-}  // namespace
-
-int batch_reserve(hps_handle *H, int R) {
-  Batch &B = H->batch;
-  if (R <= 0 || R > 64) return HPS_EINVAL;
-  if (R <= B.Rmax) return HPS_OK;
-  cudaDeviceSynchronize();
-  if (B.impl32.X.empty()) {  // FP32 operator copies (once)
-    if (int e = convert_opset(H, H->impl, B.impl32, H->shared)) return e;
-    if (int e = convert_opset(H, H->ident, B.ident32, true)) return e;
-  }
-  // (re)allocate the R-column work vectors; old ones stay in the handle's list until hps_free
-  const GridDims &g = H->g;
-  auto da = [&](auto **ptr, size_t n) -> int {
-    if (cudaMalloc((void **)ptr, std::max<size_t>(n, 1) * sizeof(**ptr)) != cudaSuccess) return HPS_ENOMEM;
-    H->allocs.push_back(*ptr);
-    return HPS_OK;
-  };
-  if (da(&B.ustage, (size_t)g.N * R) || da(&B.Rb, (size_t)g.N_int * R) || da(&B.KL, 6 * (size_t)g.N_int * R) ||
-      da(&B.KE, 6 * (size_t)g.N_int * R) || da(&B.r, (size_t)g.N * R) || da(&B.g32, (size_t)g.N * R) ||
-      da(&B.w32, (size_t)g.N_int * R))
-    return HPS_ENOMEM;
-  B.h32.assign(H->L + 1, nullptr);
-  B.w332.assign(H->L, nullptr);
-  for (int l = 0; l <= H->L; ++l) {
-    const Level &lv = H->lev[l];
-    if (da(&B.h32[l], (size_t)lv.nodes * lv.nb * R)) return HPS_ENOMEM;
-    if (l < H->L && da(&B.w332[l], (size_t)lv.nodes * lv.n3 * R)) return HPS_ENOMEM;
-  }
-  B.partial_len = partial_floats(H, R);
-  if (da(&B.partial32, std::max<size_t>(1, B.partial_len))) return HPS_ENOMEM;
-  cudaMemset(B.r, 0, (size_t)g.N * R * sizeof(double));
-  if (cudaDeviceSynchronize() != cudaSuccess) return HPS_ECUDA;
-  B.Rmax = R;
-  return HPS_OK;
+// dst[i*ldd + offd + j] = src[i*lds + offs + j] for i < rows, j < cols (column subsets of
+// RHS-fastest vectors)
+__global__ void k_cols(const double *__restrict__ src, int lds, int offs, double *__restrict__ dst, int ldd,
+                       int offd, int64_t rows, int cols) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= rows * cols) return;
+  const int64_t i = idx / cols;
+  const int j = (int)(idx % cols);
+  dst[i * ldd + offd + j] = src[i * lds + offs + j];
 }
 
-int solve_batch(hps_handle *H, int R, const double *rhs, const double *f, double *u, int refine, cudaStream_t st) {
-  if (R > H->batch.Rmax) return HPS_EINVAL;
-  Combo c{};
-  add_term_b(c, rhs, 1.0);
-  return refined_solve(H, H->impl, H->batch.impl32, R, c, nullptr, rhs, f, u, refine, H->gamma_dt, st);
+// Columns of group gi for a call with R columns: [c0, c0 + n).  Groups take multiples of 4
+// columns (the FP32 applies work on column quads), the last one the rest; n may be 0.
+void group_cols(int R, int G, int gi, int &c0, int &n) {
+  const int per = round4((R + G - 1) / G);
+  c0 = std::min(R, gi * per);
+  n = std::min(R, c0 + per) - c0;
 }
 
-int ark_batch(hps_handle *H, int R, double *u, double dt, const hps_ark_terms *terms, int refine, const ArkTable &tb,
-              cudaStream_t st) {
-  Batch &B = H->batch;
-  if (R > B.Rmax) return HPS_EINVAL;
+// One ARK step of one group: u is [N][R] (the group's own buffer or the caller's), q / f are
+// stage-major with leading dimensions qld / fld and the group's columns from qoff / foff.
+int ark_group(hps_handle *H, BatchWork &B, int R, double *u, double dt, const hps_ark_terms *terms, int qld, int qoff,
+              int fld, int foff, int refine, const ArkTable &tb, cudaStream_t st) {
   const GridDims &g = H->g;
-  const int64_t ni = g.N_int * R, nbd = g.N_bd * R;
+  const int64_t ni = g.N_int * R;
   const double *q = terms ? terms->q : nullptr;
   const double *f = terms ? terms->f : nullptr;
+  const int64_t qstage = g.N_int * (int64_t)qld, fstage = g.N_bd * (int64_t)fld;
   const int gk = terms ? terms->g_kind : HPS_G_NONE;
   const double gp0 = terms ? terms->g_param[0] : 0.0, gp1 = terms ? terms->g_param[1] : 0.0;
   // stage 1 (explicit): dt L u^n, dt (q_1 + g(u^n))
@@ -910,6 +1241,8 @@ int ark_batch(hps_handle *H, int R, double *u, double dt, const hps_ark_terms *t
   E.out0 = B.KL;
   E.out1 = B.KE;
   E.q = q;
+  E.qld = qld;
+  E.qoff = qoff;
   E.dt = dt;
   E.g_kind = gk;
   E.gp0 = gp0;
@@ -922,15 +1255,18 @@ int ark_batch(hps_handle *H, int R, double *u, double dt, const hps_ark_terms *t
       add_term_b(c, B.KL + j * ni, tb.A[i][j]);
       add_term_b(c, B.KE + j * ni, tb.Ah[i][j]);
     }
-    if (int e = refined_solve(H, H->impl, B.impl32, R, c, B.Rb, B.Rb, f ? f + i * nbd : nullptr, B.ustage, refine,
-                              H->gamma_dt, st))
+    const BdView fv{f ? f + i * fstage : nullptr, fld, foff};
+    if (int e = refined_solve(H, B, H->impl, H->batch.impl32, R, c, B.Rb, B.Rb, fv, B.ustage, refine, H->gamma_dt,
+                              st))
       return e;
     Leaf64Args P = leaf64_args(H, kEpilogue, R);
     P.u = B.ustage;
     P.Rb = B.Rb;
     P.out0 = B.KL + i * ni;
     P.out1 = B.KE + i * ni;
-    P.q = q ? q + i * ni : nullptr;
+    P.q = q ? q + i * qstage : nullptr;
+    P.qld = qld;
+    P.qoff = qoff;
     P.inv_gamma = 1.0 / tb.A[1][1];
     P.dt = dt;
     P.g_kind = gk;
@@ -946,7 +1282,142 @@ int ark_batch(hps_handle *H, int R, double *u, double dt, const hps_ark_terms *t
     add_term_b(c, B.KL + j * ni, tb.b[j]);
     add_term_b(c, B.KE + j * ni, tb.b[j]);
   }
-  return refined_solve(H, H->ident, B.ident32, R, c, B.Rb, B.Rb, f ? f + 5 * nbd : nullptr, u, refine, 0.0, st);
+  const BdView fv{f ? f + 5 * fstage : nullptr, fld, foff};
+  return refined_solve(H, B, H->ident, H->batch.ident32, R, c, B.Rb, B.Rb, fv, u, refine, 0.0, st);
+}
+
+// Run `body(group, c0, n, stream)` for every non-empty group: inline on `st` with one group,
+// else forked onto the groups' streams and joined back into `st` (capturable).
+template <class F>
+int for_groups(hps_handle *H, int R, cudaStream_t st, F body) {
+  Batch &Bt = H->batch;
+  if (Bt.groups == 1) return body(Bt.work[0], 0, R, st);
+  if (cudaEventRecord(Bt.fork, st) != cudaSuccess) return HPS_ECUDA;
+  int err = HPS_OK;
+  for (int gi = 0; gi < Bt.groups; ++gi) {
+    int c0, n;
+    group_cols(R, Bt.groups, gi, c0, n);
+    if (n == 0) continue;
+    BatchWork &W = Bt.work[gi];
+    cudaStreamWaitEvent(W.stream, Bt.fork, 0);
+    if (err == HPS_OK) err = body(W, c0, n, W.stream);
+    cudaEventRecord(W.done, W.stream);
+    cudaStreamWaitEvent(st, W.done, 0);
+  }
+  if (err == HPS_OK && cudaPeekAtLastError() != cudaSuccess) err = HPS_ECUDA;
+  return err;
+}
+
+}  // namespace
+
+void batch_release(hps_handle *H) {
+  Batch &Bt = H->batch;
+  for (BatchWork &W : Bt.work) {
+    if (W.stream) cudaStreamDestroy(W.stream);
+    if (W.done) cudaEventDestroy(W.done);
+    W.stream = nullptr;
+    W.done = nullptr;
+  }
+  if (Bt.fork) cudaEventDestroy(Bt.fork);
+  Bt.fork = nullptr;
+}
+
+int batch_reserve(hps_handle *H, int R, int groups) {
+  Batch &Bt = H->batch;
+  if (R <= 0 || R > 64 || groups < 1 || groups > 8) return HPS_EINVAL;
+  if (R <= Bt.Rmax && groups == Bt.groups) return HPS_OK;
+  cudaDeviceSynchronize();
+  if (Bt.impl32.X.empty()) {  // FP32 operator copies (once)
+    if (int e = convert_opset(H, H->impl, Bt.impl32, H->shared)) return e;
+    if (int e = convert_opset(H, H->ident, Bt.ident32, true)) return e;
+  }
+  if (const char *s = std::getenv("HPS_FP64_CTAS_PER_SM")) Bt.fp64_ctas_per_sm = std::max(0, std::atoi(s));
+  if (const char *s = std::getenv("HPS_FLOW_LEVELS")) Bt.flow_levels = std::max(0, std::atoi(s));
+  if (const char *s = std::getenv("HPS_FLOW_N3_MAX")) Bt.flow_n3_max = std::max(0, std::atoi(s));
+  // (re)allocate the work vectors; old ones stay in the handle's list until hps_free
+  const GridDims &g = H->g;
+  auto da = [&](auto **ptr, size_t n) -> int {
+    if (cudaMalloc((void **)ptr, std::max<size_t>(n, 1) * sizeof(**ptr)) != cudaSuccess) return HPS_ENOMEM;
+    H->allocs.push_back(*ptr);
+    return HPS_OK;
+  };
+  batch_release(H);
+  Bt.work.assign(groups, BatchWork{});
+  Bt.groups = groups;
+  Bt.Rmax = 0;
+  if (groups > 1 && cudaEventCreateWithFlags(&Bt.fork, cudaEventDisableTiming) != cudaSuccess) return HPS_ECUDA;
+  for (int gi = 0; gi < groups; ++gi) {
+    int c0, Rg;
+    group_cols(R, groups, gi, c0, Rg);
+    BatchWork &W = Bt.work[gi];
+    if (Rg == 0) continue;
+    if (groups > 1) {
+      if (cudaStreamCreateWithFlags(&W.stream, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&W.done, cudaEventDisableTiming) != cudaSuccess)
+        return HPS_ECUDA;
+      if (da(&W.u, (size_t)g.N * Rg)) return HPS_ENOMEM;
+    }
+    if (da(&W.ustage, (size_t)g.N * Rg) || da(&W.Rb, (size_t)g.N_int * Rg) || da(&W.KL, 6 * (size_t)g.N_int * Rg) ||
+        da(&W.KE, 6 * (size_t)g.N_int * Rg) || da(&W.r, (size_t)g.N * Rg) || da(&W.g32, (size_t)g.N * Rg) ||
+        da(&W.w32, (size_t)g.N_int * Rg))
+      return HPS_ENOMEM;
+    W.h32.assign(H->L + 1, nullptr);
+    W.w332.assign(H->L, nullptr);
+    for (int l = 0; l <= H->L; ++l) {
+      const Level &lv = H->lev[l];
+      if (da(&W.h32[l], (size_t)lv.nodes * lv.nb * Rg)) return HPS_ENOMEM;
+      if (l < H->L && da(&W.w332[l], (size_t)lv.nodes * lv.n3 * Rg)) return HPS_ENOMEM;
+    }
+    W.flow_len = 1;
+    for (const Level &lv : H->lev) W.flow_len += lv.nodes;
+    if (da(&W.flow_sync, W.flow_len)) return HPS_ENOMEM;
+    W.partial_len = partial_floats(H, Rg);
+    if (da(&W.partial32, std::max<size_t>(1, W.partial_len))) return HPS_ENOMEM;
+    cudaMemset(W.r, 0, (size_t)g.N * Rg * sizeof(double));
+    W.Rmax = Rg;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) return HPS_ECUDA;
+  Bt.Rmax = R;
+  return HPS_OK;
+}
+
+int solve_batch(hps_handle *H, int R, const double *rhs, const double *f, double *u, int refine, cudaStream_t st) {
+  if (R > H->batch.Rmax) return HPS_EINVAL;
+  const GridDims &g = H->g;
+  const bool grouped = H->batch.groups > 1;
+  return for_groups(H, R, st, [&](BatchWork &W, int c0, int n, cudaStream_t s) -> int {
+    const double *rb = rhs;
+    double *uu = u;
+    if (grouped) {  // the group's columns of rhs into its Rb buffer, u assembled in W.u
+      k_cols<<<blocks(g.N_int * n), 256, 0, s>>>(rhs, R, c0, W.Rb, n, 0, g.N_int, n);
+      rb = W.Rb;
+      uu = W.u;
+    }
+    Combo c{};
+    add_term_b(c, rb, 1.0);
+    if (int e = refined_solve(H, W, H->impl, H->batch.impl32, n, c, nullptr, rb, BdView{f, R, c0}, uu, refine,
+                              H->gamma_dt, s))
+      return e;
+    if (grouped) k_cols<<<blocks(g.N * n), 256, 0, s>>>(W.u, n, 0, u, R, c0, g.N, n);
+    return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
+  });
+}
+
+int ark_batch(hps_handle *H, int R, double *u, double dt, const hps_ark_terms *terms, int refine, const ArkTable &tb,
+              cudaStream_t st) {
+  if (R > H->batch.Rmax) return HPS_EINVAL;
+  const GridDims &g = H->g;
+  const bool grouped = H->batch.groups > 1;
+  return for_groups(H, R, st, [&](BatchWork &W, int c0, int n, cudaStream_t s) -> int {
+    double *uu = u;
+    if (grouped) {
+      k_cols<<<blocks(g.N * n), 256, 0, s>>>(u, R, c0, W.u, n, 0, g.N, n);
+      uu = W.u;
+    }
+    if (int e = ark_group(H, W, n, uu, dt, terms, R, c0, R, c0, refine, tb, s)) return e;
+    if (grouped) k_cols<<<blocks(g.N * n), 256, 0, s>>>(W.u, n, 0, u, R, c0, g.N, n);
+    return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
+  });
 }
 
 }  // namespace hps

@@ -100,7 +100,8 @@ struct Level {
   int j3a = 0, j3b = 0;  // offset of the interface in the alpha / beta child boundary
   int *d_origin = nullptr;  // nodes x (ix0, iy0)
   int *d_hsrc = nullptr;    // nb: parent boundary position -> child*nbc + position in child
-  std::vector<int> origin, hsrc;
+  int *d_cmap = nullptr;    // 2 nbc: child*nbc + position -> parent position, or nb + interface position
+  std::vector<int> origin, hsrc, cmap;
 };
 
 // Merge operators of one level, FP64, row-major, per node (stride) or shared (stride 0).
@@ -131,16 +132,34 @@ struct OpSet32 {
   std::vector<Op32> X, S, Tcat;  // per level
 };
 
-// Work buffers of the batched mixed-precision path for up to Rmax right-hand sides.  Vectors
-// with R columns are stored RHS-fastest: entry (point i, column j) at i*R + j.
-struct Batch {
+// Work buffers of one column group of the batched mixed-precision path (up to Rmax columns).
+// Vectors with R columns are stored RHS-fastest: entry (point i, column j) at i*R + j.
+struct BatchWork {
   int Rmax = 0;
-  OpSet32 impl32, ident32;
+  double *u = nullptr;  // the group's columns of the caller's u (grouped calls only)
   double *ustage = nullptr, *Rb = nullptr, *KL = nullptr, *KE = nullptr, *r = nullptr;  // FP64
   float *g32 = nullptr, *w32 = nullptr;
   std::vector<float *> h32, w332;  // per level
   float *partial32 = nullptr;
   size_t partial_len = 0;          // floats
+  unsigned *flow_sync = nullptr;   // dataflow merge kernels: ticket counter + node flags
+  size_t flow_len = 0;
+  cudaStream_t stream = nullptr;   // grouped calls: the group's own stream
+  cudaEvent_t done = nullptr;
+};
+
+// The batched path: FP32 operator copies (shared by all groups) and G column groups.  With
+// G > 1 the columns of a call are split into G groups that run on their own streams, so that
+// one group's FP64 residual kernels (bound by the FP64 pipe) overlap another group's FP32
+// sweeps (bound by the FP32 pipe and L2).
+struct Batch {
+  int Rmax = 0, groups = 1;
+  int fp64_ctas_per_sm = 0;  // 0: one CTA per leaf; else a persistent grid of that many per SM
+  int flow_levels = 12;      // lower merge levels run as one dataflow kernel (0: one launch per level)
+  int flow_n3_max = 32;      // ... those with interfaces of at most this many points
+  OpSet32 impl32, ident32;
+  std::vector<BatchWork> work;
+  cudaEvent_t fork = nullptr;
 };
 
 // A kernel sequence recorded into a CUDA graph (hps_set_graph), replayed for equal arguments.
@@ -254,7 +273,8 @@ int clone_handle(const hps_handle *base, cudaStream_t st, hps_handle **out);
 int bytes_split(const hps_tree *tree, int p, int coeff_kind, int flags, size_t *ops, size_t *work);
 
 // ---- batched mixed-precision path (batched.cu) ---------------------------------------------
-int batch_reserve(hps_handle *H, int R);
+int batch_reserve(hps_handle *H, int R, int groups);
+void batch_release(hps_handle *H);
 int solve_batch(hps_handle *H, int R, const double *rhs, const double *f, double *u, int refine, cudaStream_t st);
 struct ArkTable {
   double A[6][6], Ah[6][6], b[6];

@@ -190,9 +190,14 @@ class HPSSolver:
         return u
 
     # ---- batched mixed precision -----------------------------------------------------------
-    def batch_reserve(self, R):
-        """FP32 operator copies and R-column work buffers (hps_batch_reserve)."""
-        check(lib().hps_batch_reserve(self._h, int(R)), "hps_batch_reserve")
+    def batch_reserve(self, R, groups=None):
+        """FP32 operator copies and R-column work buffers (hps_batch_reserve); with `groups`,
+        the columns of later calls run as that many column groups on their own streams
+        (hps_batch_reserve_groups)."""
+        if groups is None:
+            check(lib().hps_batch_reserve(self._h, int(R)), "hps_batch_reserve")
+        else:
+            check(lib().hps_batch_reserve_groups(self._h, int(R), int(groups)), "hps_batch_reserve_groups")
 
     def solve_batch(self, rhs, f=None, u=None, refine=2, stream=None):
         """R solves at once: rhs (N_int, R), f (N_bd, R) or None -> u (N, R) (hps_solve_batch)."""

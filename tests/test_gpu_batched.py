@@ -88,35 +88,36 @@ def test_ark_batch_heat_matches_oracle():
     S.close()
 
 
-@pytest.mark.parametrize("gname", ["allen_cahn", "burgers"])
-def test_ark_batch_varcoef_inhomogeneous_matches_fp64(gname):
+@pytest.mark.parametrize("gname,R,groups", [("allen_cahn", 6, 1), ("burgers", 6, 1), ("burgers", 10, 3)])
+def test_ark_batch_varcoef_inhomogeneous_matches_fp64(gname, R, groups):
+    """Stage sources q and boundary data f per column; with groups the columns run as column
+    groups (4, 4, 2 of 10) on their own streams, reading q and f in place."""
     torch = need_gpu()
     from paper_2306_02526_gb300 import hps
-    n1, n2, p, dt, R = 8, 4, 10, 0.02, 6
+    n1, n2, p, dt = 8, 4, 10, 0.02
     g = Grid(n1, n2, p)
     X, Y = g.coords()
     I, bd = np.arange(g.N_int), g.boundary_indices()
     coef = workloads.VarCoef128().coef(X[I], Y[I])
     S = _solver(torch, n1, n2, p, coef, 0.25 * dt)
-    S.batch_reserve(R)
+    S.batch_reserve(R, groups=groups)
     c = hps.hps_ark_abscissae()
     gp = (0.8, -0.3)
-    qf = lambda t: np.cos(X[I] + t) * np.sin(2 * Y[I])
-    ff = lambda t: (np.sin(X + 2 * Y) * (1 + t))[bd]
+    qf = lambda t, j: np.cos(X[I] + t + 0.1 * j) * np.sin(2 * Y[I])
+    ff = lambda t, j: (np.sin(X + 2 * Y - 0.2 * j) * (1 + t))[bd]
     u0 = np.stack([0.3 * np.sin(math.pi * X) * np.cos(Y + j) for j in range(R)], axis=1)
-    u0[bd, :] = ff(0.0)[:, None]
+    for j in range(R):
+        u0[bd, j] = ff(0.0, j)
     ub = to_dev(torch, u0)
     us = [to_dev(torch, u0[:, j].copy()) for j in range(R)]
     t = 0.0
     for n in range(4):
-        qs = np.stack([qf(t + cj * dt) for cj in c])
-        fs = np.stack([ff(t + cj * dt) for cj in c])
-        qb = np.repeat(qs[:, :, None], R, axis=2)
-        fb = np.repeat(fs[:, :, None], R, axis=2)
+        qb = np.stack([np.stack([qf(t + cj * dt, j) for j in range(R)], axis=1) for cj in c])
+        fb = np.stack([np.stack([ff(t + cj * dt, j) for j in range(R)], axis=1) for cj in c])
         S.ark_step_batch(ub, t, dt, q=to_dev(torch, qb), f=to_dev(torch, fb), g=gname, g_param=gp, refine=2)
         for j in range(R):
-            S.ark_step(us[j], t, dt, q=to_dev(torch, qs.reshape(-1)), f=to_dev(torch, fs.reshape(-1)), g=gname,
-                       g_param=gp)
+            S.ark_step(us[j], t, dt, q=to_dev(torch, qb[:, :, j].reshape(-1).copy()),
+                       f=to_dev(torch, fb[:, :, j].reshape(-1).copy()), g=gname, g_param=gp)
         t += dt
     got = ub.cpu().numpy()
     for j in range(R):
@@ -148,3 +149,35 @@ def test_ark_batch_full_size_allen_cahn():
     for j in range(R):
         assert rel_max(got[:, j], us[j].cpu().numpy()) <= TOL
     S.close()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_grouped_solve_batch_matches_ungrouped(graph):
+    """Column groups on their own streams (eager, and recorded into a CUDA graph and replayed)
+    give the ungrouped result to rounding and the FP64 solve to the mixed tolerance."""
+    torch = need_gpu()
+    n1, n2, p, R = 16, 8, 12, 13
+    g = Grid(n1, n2, p, -0.5, 0.5, 0.0, 1.0)
+    coef = workloads.random_coefficients(p, g.N_int)
+    S1 = _solver(torch, n1, n2, p, coef, 0.013, (-0.5, 0.5, 0.0, 1.0))
+    SG = _solver(torch, n1, n2, p, coef, 0.013, (-0.5, 0.5, 0.0, 1.0))
+    S1.batch_reserve(R)
+    SG.batch_reserve(R, groups=2)
+    if graph:
+        SG.set_graph(True)
+    r = np.random.default_rng(7)
+    rhs = to_dev(torch, r.standard_normal((g.N_int, R)))
+    f = to_dev(torch, r.standard_normal((g.boundary_indices().size, R)))
+    want = S1.solve_batch(rhs, f, refine=2).cpu().numpy()
+    u = torch.zeros((g.N, R), dtype=torch.float64, device="cuda")
+    for _ in range(3):  # eager; recorded + replayed; replayed
+        u.zero_()
+        SG.solve_batch(rhs, f, u=u, refine=2)
+        torch.cuda.synchronize()
+        got = u.cpu().numpy()
+        assert rel_max(got, want) <= 1e-11
+        for j in (0, 7, R - 1):
+            ref = S1.solve(rhs[:, j].contiguous(), f[:, j].contiguous()).cpu().numpy()
+            assert rel_max(got[:, j], ref) <= TOL
+    S1.close()
+    SG.close()
