@@ -206,6 +206,10 @@ def timed_run(S, step, args, world, local_rank, flush, torch):
         step()
         n += 1
     S.trace_enable(_lib.KERNELS)
+    for _ in range(2):  # eager + recording: the graph now carries timing events of every kernel
+        step()
+        n += 1
+    S.trace_enable(_lib.KERNELS)  # same mask: counters reset, recorded graph kept
     for _ in range(4):
         step()
         n += 1

@@ -212,10 +212,13 @@ enum {
   HPS_K_LEAF_DOWN = 4,   /* a5: u_i = w + S u_b and the fused ARK stage epilogue          */
   HPS_K_LEAF_EVAL = 5,   /* explicit first stage: dt L u^n, dt (q + g(u^n))               */
   HPS_K_SET_BOUNDARY = 6, /* Dirichlet data onto the outer boundary                       */
-  HPS_K_MERGE_UP_ALL = 7,  /* a3, all levels in one persistent kernel (hps_set_persistent)   */
-  HPS_K_MERGE_DOWN_ALL = 8, /* a4, all levels in one persistent kernel (hps_set_persistent)  */
+  HPS_K_MERGE_UP_ALL = 7,  /* a3, all levels in one persistent kernel (hps_set_persistent);
+                              batched path: the lower levels as one dataflow kernel             */
+  HPS_K_MERGE_DOWN_ALL = 8, /* a4, likewise                                                    */
   HPS_K_RESIDUAL = 9,       /* batched path: FP64 collocation residual at interior points     */
-  HPS_K_JUMP = 10           /* batched path: FP64 flux-jump residual at shared edge points      */
+  HPS_K_JUMP = 10,          /* batched path: FP64 flux-jump residual at shared edge points      */
+  HPS_K_FINISH = 11         /* batched path: FP32 sweep result into the FP64 vector; column
+                              group copies                                                    */
 };
 
 /* Tracing (no effect on results).  Every launch of the solve path is counted per kernel;

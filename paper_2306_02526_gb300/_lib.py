@@ -13,7 +13,7 @@ HPS_COEF_CONST, HPS_COEF_NODAL = 0, 1
 HPS_FLAG_PER_NODE = 1
 HPS_G_NONE, HPS_G_ALLEN_CAHN, HPS_G_FISHER, HPS_G_BURGERS = 0, 1, 2, 3
 KERNELS = ("leaf_up", "merge_up_w3", "merge_up_h", "merge_down", "leaf_down", "leaf_eval", "set_boundary",
-           "merge_up_all", "merge_down_all", "residual", "jump")
+           "merge_up_all", "merge_down_all", "residual", "jump", "finish")
 
 
 class hps_tree(ctypes.Structure):

@@ -269,7 +269,7 @@ size_t hps_bytes(const hps_tree *tree, int p, int coeff_kind, int flags) {
   const bool shared = coeff_kind == HPS_COEF_CONST && !(flags & HPS_FLAG_PER_NODE);
   size_t s = opset_bytes(lev, q, b, shared, false) + opset_bytes(lev, q, b, true, true) + work_bytes(g, lev);
   if (coeff_kind == HPS_COEF_NODAL) s += 5 * (size_t)g.N_int * sizeof(double);
-  s += 4 * (size_t)p * p * sizeof(double);
+  s += (4 * (size_t)p * p + 2 * (size_t)p * p) * sizeof(double);  // D matrices and their even-odd halves
   for (const Level &lv : lev) s += (2 * (size_t)lv.nodes + lv.hsrc.size() + lv.cmap.size()) * sizeof(int);
   return s;
 }
@@ -362,6 +362,20 @@ int hps_build(const hps_tree *tree, int p, const hps_coeffs *coeffs, double gamm
         Dh[2 * p * p + i * p + j] = sxx;
         Dh[3 * p * p + i * p + j] = syy;
       }
+    if (p % 2 == 0) {  // even-odd halves of D1x, D1y, Dxx, Dyy: A = (D_ik + D_i,p-1-k) / 2, B = (D_ik - D_i,p-1-k) / 2
+      const int h = p / 2;
+      for (int mtx = 0; mtx < 4; ++mtx) {
+        const double *Mx = Dh.data() + (size_t)mtx * p * p;
+        std::vector<double> Ah((size_t)h * h), Bh((size_t)h * h);
+        for (int i = 0; i < h; ++i)
+          for (int k = 0; k < h; ++k) {
+            Ah[i * h + k] = 0.5 * (Mx[i * p + k] + Mx[i * p + p - 1 - k]);
+            Bh[i * h + k] = 0.5 * (Mx[i * p + k] - Mx[i * p + p - 1 - k]);
+          }
+        Dh.insert(Dh.end(), Ah.begin(), Ah.end());
+        Dh.insert(Dh.end(), Bh.begin(), Bh.end());
+      }
+    }
     if (dalloc(H, &H->d_D, Dh.size())) return fail(HPS_ENOMEM);
     cudaMemcpyAsync(H->d_D, Dh.data(), Dh.size() * sizeof(double), cudaMemcpyHostToDevice, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return fail(HPS_ECUDA);

@@ -9,6 +9,7 @@
 // Vectors with R columns are stored RHS-fastest (point i, column j at i*R + j); the FP32
 // applies compute 4 columns per thread from one operator load.
 #include <algorithm>
+#include <cooperative_groups.h>
 
 #include "hps_internal.cuh"
 
@@ -111,6 +112,23 @@ __device__ __forceinline__ void tile_fma(float (&acc)[4][TC], const float4 a, co
   }
 }
 
+// acc += A x over K columns of the transposed operator (4 rows per float4 load, column c at
+// a + c ld) with U operator loads in flight per thread: the chain of dependent L2 round trips
+// is K / U long instead of K.
+template <int TC, int U>
+__device__ __forceinline__ void stream_fma(float (&acc)[4][TC], const float *__restrict__ a, int64_t ld, int K,
+                                           const float *x, int Rp) {
+  int c = 0;
+  for (; c + U <= K; c += U) {
+    float4 av[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) av[u] = __ldg(reinterpret_cast<const float4 *>(a + (int64_t)(c + u) * ld));
+#pragma unroll
+    for (int u = 0; u < U; ++u) tile_fma<TC>(acc, av[u], x + (c + u) * Rp);
+  }
+  for (; c < K; ++c) tile_fma<TC>(acc, __ldg(reinterpret_cast<const float4 *>(a + (int64_t)c * ld)), x + c * Rp);
+}
+
 template <int TC>
 __global__ void __launch_bounds__(kBT) k_b_leaf_up(GridDims g, int R, const int *__restrict__ origin, Combo rhs,
                                                    double *__restrict__ Rsave, const float *__restrict__ AinvT,
@@ -141,10 +159,7 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_up(GridDims g, int R, const int 
       for (int e = 0; e < 4; ++e)
 #pragma unroll
         for (int t = 0; t < TC; ++t) acc[e][t] = 0.f;
-      const float *a = AinvT + (int64_t)k * strA + r0;
-#pragma unroll 2
-      for (int c = 0; c < q; ++c)
-        tile_fma<TC>(acc, __ldg(reinterpret_cast<const float4 *>(a + (int64_t)c * ldA)), Rs + c * Rp + j0);
+      stream_fma<TC, 8>(acc, AinvT + (int64_t)k * strA + r0, ldA, q, Rs + j0, Rp);
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e)
@@ -189,10 +204,7 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_down(GridDims g, int R, const in
 #pragma unroll
       for (int t = 0; t < TC; ++t) acc[e][t] = 0.f;
     if (!identity) {
-      const float *a = SlT + (int64_t)k * strS + r0;
-#pragma unroll 2
-      for (int c = 0; c < b; ++c)
-        tile_fma<TC>(acc, __ldg(reinterpret_cast<const float4 *>(a + (int64_t)c * ldS)), ub + c * Rp + j0);
+      stream_fma<TC, 8>(acc, SlT + (int64_t)k * strS + r0, ldS, b, ub + j0, Rp);
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -423,9 +435,7 @@ __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict
   for (int e = 0; e < 4; ++e)
 #pragma unroll
     for (int t = 0; t < TC; ++t) acc[e][t] = 0.f;
-#pragma unroll 4
-  for (int c = 0; c < klen; ++c)
-    tile_fma<TC>(acc, __ldg(reinterpret_cast<const float4 *>(a + (int64_t)c * ld)), x + c * Rp);
+  stream_fma<TC, 8>(acc, a, ld, klen, x, Rp);
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     const int r = r0 + e;
@@ -473,6 +483,142 @@ int launch_b(hps_handle *H, BatchWork &B, int slot, const BPlan &P, const float 
   }
   H->trace.end(slot, st);
   return HPS_OK;
+}
+
+// ---- merge applies of the upper levels: split K inside the CTA and across a cluster ---------
+// One CTA per (node, row tile) and cluster rank; 256 threads = S K-slices x Qc row quads x CG
+// column groups, each thread a 4 x TC register tile over its slice of the CTA's K chunk.  The S
+// slices are added in shared memory, the C CTAs of a cluster (its ranks: consecutive K chunks)
+// through distributed shared memory, both in a fixed order (deterministic), and the epilogue
+// runs where the sum is formed: no partial sums in global memory, no reduction launch.
+struct BPlan2 {
+  int M, K, nodes, R, Rp, TC, CG, MQ, S, Qc, RT, C, chunk, slice;
+};
+
+BPlan2 plan_b2(int M, int K, int nodes, int R) {
+  BPlan2 P{};
+  P.M = M;
+  P.K = K;
+  P.nodes = nodes;
+  P.R = R;
+  P.Rp = round4(R);
+  P.TC = P.Rp % 8 == 0 ? 8 : 4;
+  P.CG = P.Rp / P.TC;
+  P.MQ = (M + 3) / 4;
+  const int ks_total = std::max(1, (K + 31) / 32);  // about 32 operator columns per thread
+  P.S = 1;
+  while (P.S < 8 && P.S < ks_total && kBT / (2 * P.S * P.CG) >= 4) P.S *= 2;
+  P.C = 1;
+  while (P.C < 8 && P.S * P.C < ks_total) P.C *= 2;
+  P.Qc = kBT / (P.S * P.CG);
+  P.RT = (P.MQ + P.Qc - 1) / P.Qc;
+  P.chunk = (K + P.C - 1) / P.C;
+  P.slice = (P.chunk + P.S - 1) / P.S;
+  return P;
+}
+
+size_t b2_smem(const BPlan2 &P) {  // x chunk + slice partials + CTA partial
+  return ((size_t)P.chunk * P.Rp + (size_t)P.S * P.Qc * 4 * P.Rp + (size_t)P.Qc * 4 * P.Rp) * sizeof(float);
+}
+
+template <int TC, class XL, class EP>
+__global__ void __launch_bounds__(kBT) k_b_gemv2(BPlan2 P, const float *__restrict__ AT, int ld, int64_t str, XL xl,
+                                                 EP ep) {
+  extern __shared__ float sm[];
+  const int Rp = P.Rp, rows = P.Qc * 4;
+  float *xs = sm, *red = xs + (size_t)P.chunk * Rp, *cta = red + (size_t)P.S * rows * Rp;
+  namespace cgr = cooperative_groups;
+  cgr::cluster_group cl = cgr::this_cluster();
+  const int k = blockIdx.x / P.RT, rt = blockIdx.x % P.RT;
+  const int crank = (int)cl.block_rank();  // cluster dims (1, C, 1): rank = blockIdx.y = K chunk
+  const int c0 = crank * P.chunk, clen = max(0, min(P.chunk, P.K - c0));
+  block_gather<8, float>(
+      clen * Rp,
+      [&](int idx) {
+        const int c = idx / Rp, j = idx % Rp;
+        return j < P.R ? xl(k, c0 + c, j) : 0.f;
+      },
+      [&](int idx, float v) { xs[idx] = v; });
+  __syncthreads();
+  const int qi = threadIdx.x % P.Qc, cg = (threadIdx.x / P.Qc) % P.CG, sl = threadIdx.x / (P.Qc * P.CG);
+  const int r0 = 4 * (rt * P.Qc + qi), j0 = TC * cg;
+  float acc[4][TC];
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+#pragma unroll
+    for (int t = 0; t < TC; ++t) acc[e][t] = 0.f;
+  const bool live = sl < P.S;  // 256 need not be a multiple of S Qc CG
+  const int s0 = min(clen, sl * P.slice), s1 = min(clen, s0 + P.slice);
+  if (live && r0 < P.M && s1 > s0)
+    stream_fma<TC, 8>(acc, AT + (int64_t)k * str + (int64_t)(c0 + s0) * ld + r0, ld, s1 - s0, xs + s0 * Rp + j0, Rp);
+  if (live) {
+    float *mine = red + ((size_t)sl * rows + 4 * qi) * Rp + j0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+      for (int t = 0; t < TC; t += 4)
+        *reinterpret_cast<float4 *>(mine + e * Rp + t) =
+            make_float4(acc[e][t], acc[e][t + 1], acc[e][t + 2], acc[e][t + 3]);
+  }
+  __syncthreads();
+  // slices -> CTA partial (fixed order)
+  for (int idx = threadIdx.x; idx < rows * Rp; idx += blockDim.x) {
+    float v = 0.f;
+    for (int s2 = 0; s2 < P.S; ++s2) v += red[(size_t)s2 * rows * Rp + idx];
+    if (P.C == 1) {
+      const int r = 4 * rt * P.Qc + idx / Rp, j = idx % Rp;
+      if (r < P.M && j < P.R) ep(k, r, j, v);
+    } else {
+      cta[idx] = v;
+    }
+  }
+  if (P.C == 1) return;
+  cl.sync();
+  // this rank adds rows [crank * rows / C, (crank + 1) * rows / C) of the C CTA partials
+  const int ra = crank * rows / P.C, rb = (crank + 1) * rows / P.C;
+  for (int idx = ra * Rp + threadIdx.x; idx < rb * Rp; idx += blockDim.x) {
+    float v = 0.f;
+    for (int q2 = 0; q2 < P.C; ++q2) v += cl.map_shared_rank(cta, q2)[idx];
+    const int r = 4 * rt * P.Qc + idx / Rp, j = idx % Rp;
+    if (r < P.M && j < P.R) ep(k, r, j, v);
+  }
+  cl.sync();  // keep this CTA's partial alive until every rank has read it
+}
+
+constexpr size_t kB2MaxSmem = 160 * 1024;
+
+// One merge apply of a level: the cluster split-K kernel, or (handle option, or when its K chunk
+// does not fit in shared memory) the split-K kernel with partial sums in global memory.
+template <class XL, class EP>
+int launch_b2(hps_handle *H, BatchWork &B, int slot, int M, int K, int nodes, int R, const float *AT, int ld,
+              int64_t str, XL xl, EP ep, cudaStream_t st) {
+  const BPlan2 P = plan_b2(M, K, nodes, R);
+  const size_t smem = b2_smem(P);
+  if (!H->batch.gemv2 || smem > kB2MaxSmem)
+    return launch_b(H, B, slot, plan_b(M, K, nodes, R, 2 * H->num_sms), AT, ld, str, xl, ep, st);
+  auto kern = P.TC == 8 ? k_b_gemv2<8, XL, EP> : k_b_gemv2<4, XL, EP>;
+  static size_t set8 = 0, set4 = 0;
+  size_t &set = P.TC == 8 ? set8 : set4;
+  if (smem > 48 * 1024 && smem > set) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set = smem;
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(P.RT * nodes), (unsigned)P.C, 1);
+  cfg.blockDim = dim3(kBT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = (unsigned)P.C;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  H->trace.begin(slot, st);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, P, AT, ld, str, xl, ep);
+  H->trace.end(slot, st);
+  return e == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
 // ---- merges of the lower tree levels as one dataflow kernel per direction ------------------
@@ -761,6 +907,149 @@ __global__ void __launch_bounds__(kBT) k_b_leaf64(GridDims g, int nodes, const i
   }
 }
 
+// Output of one interior point for the FP64 leaf modes; terms of L with zero constant
+// coefficients are skipped (A.need_*).
+__device__ __forceinline__ void leaf64_out(const Leaf64Args &A, int64_t gi, int col, double uu, double ux, double uy,
+                                           double uxx, double uyy) {
+  const int64_t o = gi * A.R + col;
+  double Lu = 0.0;
+  if (A.mode != kEpilogue) {
+    if (A.coef) {
+      Lu = A.coef[gi] * uxx + A.coef[A.N_int + gi] * uyy + A.coef[2 * A.N_int + gi] * ux +
+           A.coef[3 * A.N_int + gi] * uy + A.coef[4 * A.N_int + gi] * uu;
+    } else {
+      if (A.need_d2) Lu = fma(A.cst[1], uyy, A.cst[0] * uxx);
+      if (A.need_d1) Lu = fma(A.cst[3], uy, fma(A.cst[2], ux, Lu));
+      if (A.cst[4] != 0.0) Lu = fma(A.cst[4], uu, Lu);
+    }
+  }
+  if (A.mode == kResid) {
+    A.out0[o] = fma(A.gdt, Lu, A.Rb[o] - uu);
+  } else {
+    double e;
+    switch (A.g_kind) {
+      case HPS_G_ALLEN_CAHN: e = A.gp0 * (uu - uu * uu * uu); break;
+      case HPS_G_FISHER: e = A.gp0 * uu * (1.0 - uu); break;
+      case HPS_G_BURGERS: e = -uu * (A.gp0 * ux + A.gp1 * uy); break;
+      default: e = 0.0;
+    }
+    if (A.q) e += A.q[gi * A.qld + A.qoff + col];
+    A.out0[o] = A.mode == kEval ? A.dt * Lu : (uu - A.Rb[o]) * A.inv_gamma;
+    A.out1[o] = A.dt * e;
+  }
+}
+
+// The FP64 leaf modes for even p by the even-odd decomposition of the differentiation
+// matrices (Solomonoff 1992): a Chebyshev matrix D is centro-symmetric (second derivative) or
+// centro-antisymmetric (first derivative), so on the symmetric and antisymmetric parts of a
+// grid line, E_k = U_k + U_{p-1-k} and O_k = U_k - U_{p-1-k} (k < p/2), the rows i and p-1-i
+// of D U are e +- o (resp. +-(e -+ o)) with e = sum_k A_ik E_k, o = sum_k B_ik O_k,
+// A = (D_ik + D_i,p-1-k)/2 and B = (D_ik - D_i,p-1-k)/2: p/2 instead of p multiply-adds per
+// output.  The FP64 pipe bounds these kernels on this GPU, so the flop count is the runtime.
+// One thread takes the four mirror images (i, j), (p-1-i, j), (i, p-1-j), (p-1-i, p-1-j).
+__global__ void __launch_bounds__(kBT) k_b_leaf64_eo(GridDims g, int nodes, const int *__restrict__ origin,
+                                                     Leaf64Args A, const double *__restrict__ Dg) {
+  extern __shared__ double sd[];
+  const int p = g.p, m = g.m, q = m * m, pp = p * p, h = p / 2, hh = h * h, R = A.R;
+  const int Rc = max(1, min(R, 2048 / pp));
+  double *Hm = sd, *U = sd + 8 * hh;  // half matrices; U [pp][Rc]
+  double *Ex = U + pp * Rc, *Ox = Ex + m * h * Rc, *Ey = Ox + m * h * Rc, *Oy = Ey + m * h * Rc;  // [m][h][Rc]
+  for (int i = threadIdx.x; i < 8 * hh; i += blockDim.x) Hm[i] = Dg[4 * pp + i];
+  const double *A1x = Hm, *B1x = Hm + hh, *A1y = Hm + 2 * hh, *B1y = Hm + 3 * hh;
+  const double *Axx = Hm + 4 * hh, *Bxx = Hm + 5 * hh, *Ayy = Hm + 6 * hh, *Byy = Hm + 7 * hh;
+  for (int k = blockIdx.x; k < nodes; k += gridDim.x) {
+    const int ix = origin[2 * k], iy = origin[2 * k + 1];
+    const int64_t l0 = ((int64_t)iy * g.n1 + ix) * q;
+    for (int j0 = 0; j0 < R; j0 += Rc) {
+      const int rc = min(Rc, R - j0);
+      __syncthreads();
+      block_gather<4, double>(
+          pp * rc,
+          [&](int idx) {
+            const int node = idx / rc, jj = idx % rc;
+            const int i = node % p, j = node / p;
+            const bool ei = (i == 0 || i == p - 1), ej = (j == 0 || j == p - 1);
+            int64_t gi = -1;
+            if (!ei && !ej) gi = l0 + (j - 1) * m + (i - 1);
+            else if (ei && !ej) gi = vseg(g, ix + (i == 0 ? 0 : 1), iy, j - 1);
+            else if (!ei && ej) gi = hseg(g, iy + (j == 0 ? 0 : 1), ix, i - 1);
+            return gi >= 0 ? A.u[gi * R + j0 + jj] : 0.0;
+          },
+          [&](int idx, double v) { U[(idx / rc) * Rc + idx % rc] = v; });
+      __syncthreads();
+      if (A.need_d1 || A.need_d2) {
+        // symmetric / antisymmetric parts of the interior rows (x lines) and columns (y lines)
+        for (int idx = threadIdx.x; idx < m * h * rc; idx += blockDim.x) {
+          const int jj = idx % rc, t = idx / rc, kk = t % h, r = t / h + 1, o = t * Rc + jj;
+          const double a = U[(r * p + kk) * Rc + jj], b = U[(r * p + p - 1 - kk) * Rc + jj];
+          Ex[o] = a + b;
+          Ox[o] = a - b;
+          const double c = U[(kk * p + r) * Rc + jj], d = U[((p - 1 - kk) * p + r) * Rc + jj];
+          Ey[o] = c + d;
+          Oy[o] = c - d;
+        }
+        __syncthreads();
+      }
+      for (int idx = threadIdx.x; idx < (h - 1) * (h - 1) * rc; idx += blockDim.x) {
+        const int jj = idx % rc, t = idx / rc, a = t % (h - 1) + 1, b = t / (h - 1) + 1;
+        const int ai = p - 1 - a, bj = p - 1 - b;
+        // points 0: (a, b)  1: (ai, b)  2: (a, bj)  3: (ai, bj)
+        double xx[4] = {0.0, 0.0, 0.0, 0.0}, yy[4] = {0.0, 0.0, 0.0, 0.0};
+        double x1[4] = {0.0, 0.0, 0.0, 0.0}, y1[4] = {0.0, 0.0, 0.0, 0.0};
+        const double *exb = Ex + (b - 1) * h * Rc + jj, *oxb = Ox + (b - 1) * h * Rc + jj;
+        const double *exj = Ex + (bj - 1) * h * Rc + jj, *oxj = Ox + (bj - 1) * h * Rc + jj;
+        const double *eya = Ey + (a - 1) * h * Rc + jj, *oya = Oy + (a - 1) * h * Rc + jj;
+        const double *eyi = Ey + (ai - 1) * h * Rc + jj, *oyi = Oy + (ai - 1) * h * Rc + jj;
+        if (A.need_d2) {
+          double e0 = 0.0, o0 = 0.0, e1 = 0.0, o1 = 0.0;
+          for (int kk = 0; kk < h; ++kk) {
+            const double ca = Axx[a * h + kk], cb = Bxx[a * h + kk];
+            e0 = fma(ca, exb[kk * Rc], e0);
+            o0 = fma(cb, oxb[kk * Rc], o0);
+            e1 = fma(ca, exj[kk * Rc], e1);
+            o1 = fma(cb, oxj[kk * Rc], o1);
+          }
+          xx[0] = e0 + o0; xx[1] = e0 - o0; xx[2] = e1 + o1; xx[3] = e1 - o1;
+          e0 = o0 = e1 = o1 = 0.0;
+          for (int kk = 0; kk < h; ++kk) {
+            const double ca = Ayy[b * h + kk], cb = Byy[b * h + kk];
+            e0 = fma(ca, eya[kk * Rc], e0);
+            o0 = fma(cb, oya[kk * Rc], o0);
+            e1 = fma(ca, eyi[kk * Rc], e1);
+            o1 = fma(cb, oyi[kk * Rc], o1);
+          }
+          yy[0] = e0 + o0; yy[2] = e0 - o0; yy[1] = e1 + o1; yy[3] = e1 - o1;
+        }
+        if (A.need_d1) {
+          double e0 = 0.0, o0 = 0.0, e1 = 0.0, o1 = 0.0;
+          for (int kk = 0; kk < h; ++kk) {
+            const double ca = A1x[a * h + kk], cb = B1x[a * h + kk];
+            e0 = fma(ca, exb[kk * Rc], e0);
+            o0 = fma(cb, oxb[kk * Rc], o0);
+            e1 = fma(ca, exj[kk * Rc], e1);
+            o1 = fma(cb, oxj[kk * Rc], o1);
+          }
+          x1[0] = e0 + o0; x1[1] = o0 - e0; x1[2] = e1 + o1; x1[3] = o1 - e1;
+          e0 = o0 = e1 = o1 = 0.0;
+          for (int kk = 0; kk < h; ++kk) {
+            const double ca = A1y[b * h + kk], cb = B1y[b * h + kk];
+            e0 = fma(ca, eya[kk * Rc], e0);
+            o0 = fma(cb, oya[kk * Rc], o0);
+            e1 = fma(ca, eyi[kk * Rc], e1);
+            o1 = fma(cb, oyi[kk * Rc], o1);
+          }
+          y1[0] = e0 + o0; y1[2] = o0 - e0; y1[1] = e1 + o1; y1[3] = o1 - e1;
+        }
+#pragma unroll
+        for (int pt = 0; pt < 4; ++pt) {
+          const int i = (pt & 1) ? ai : a, j = (pt & 2) ? bj : b;
+          leaf64_out(A, l0 + (j - 1) * m + (i - 1), j0 + jj, U[(j * p + i) * Rc + jj], x1[pt], y1[pt], xx[pt], yy[pt]);
+        }
+      }
+    }
+  }
+}
+
 // The modes without derivatives (stage epilogue of a g without derivatives; residual of the
 // identity operator) touch interior points only, which are contiguous: one flat pass.
 __global__ void k_b_pointwise(int64_t n, Leaf64Args A) {
@@ -968,7 +1257,6 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
             double *Rsave, const double *jump, cudaStream_t st) {
   const int L = H->L, p = H->p, q = H->q, b = H->b, Rp = round4(R);
   const Level &leaf = H->lev[L];
-  const int target = 2 * H->num_sms;
   const bool tc8 = Rp % 8 == 0;
   const bool narrow = Rp == 4 && !H->shared;  // streaming per-leaf operators, one column group
   const int QQ = (q + 3) / 4, KS = std::max(1, kBT / QQ);
@@ -1066,24 +1354,20 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
   }
   for (int l = lr - 1; l >= 0; --l) {
     const Level &lv = H->lev[l];
-    const MergeOps &mo = ops.merge[l];
-    const BPlan Pw = plan_b(lv.n3, lv.n3, lv.nodes, R, target);
-    if (int e = launch_b(H, B, kMergeUpW3, Pw, o32.X[l].p, o32.X[l].ld, o32.X[l].str,
-                         BXDiff{B.h32[l + 1], lv.nbc, lv.j3a, lv.j3b, R, jump, H->g, lv.d_origin, lv.a, lv.c, lv.split},
-                         BEStore{B.w332[l], lv.n3, R}, st))
+    if (int e = launch_b2(H, B, kMergeUpW3, lv.n3, lv.n3, lv.nodes, R, o32.X[l].p, o32.X[l].ld, o32.X[l].str,
+                          BXDiff{B.h32[l + 1], lv.nbc, lv.j3a, lv.j3b, R, jump, H->g, lv.d_origin, lv.a, lv.c, lv.split},
+                          BEStore{B.w332[l], lv.n3, R}, st))
       return e;
-    if (l > 0) {
-      const BPlan Ph = plan_b(lv.nb, lv.n3, lv.nodes, R, target);
-      if (int e = launch_b(H, B, kMergeUpH, Ph, o32.Tcat[l].p, o32.Tcat[l].ld, o32.Tcat[l].str, BXVec{B.w332[l], lv.n3, R},
-                           BEFlux{lv.d_hsrc, B.h32[l + 1], lv.nbc, lv.nb, R, B.h32[l]}, st))
+    if (l > 0)
+      if (int e = launch_b2(H, B, kMergeUpH, lv.nb, lv.n3, lv.nodes, R, o32.Tcat[l].p, o32.Tcat[l].ld, o32.Tcat[l].str,
+                            BXVec{B.w332[l], lv.n3, R}, BEFlux{lv.d_hsrc, B.h32[l + 1], lv.nbc, lv.nb, R, B.h32[l]}, st))
         return e;
-    }
   }
   for (int l = 0; l < lr; ++l) {
     const Level &lv = H->lev[l];
-    const BPlan Pd = plan_b(lv.n3, lv.nb, lv.nodes, R, target);
-    if (int e = launch_b(H, B, kMergeDown, Pd, o32.S[l].p, o32.S[l].ld, o32.S[l].str, BXBd{H->g, lv.d_origin, lv.a, lv.c, R, B.g32},
-                         BEScatter{H->g, lv.d_origin, lv.a, lv.c, lv.split, lv.n3, R, B.w332[l], B.g32}, st))
+    if (int e = launch_b2(H, B, kMergeDown, lv.n3, lv.nb, lv.nodes, R, o32.S[l].p, o32.S[l].ld, o32.S[l].str,
+                          BXBd{H->g, lv.d_origin, lv.a, lv.c, R, B.g32},
+                          BEScatter{H->g, lv.d_origin, lv.a, lv.c, lv.split, lv.n3, R, B.w332[l], B.g32}, st))
       return e;
   }
   if (nflow > 0) {
@@ -1138,6 +1422,23 @@ int leaf64(hps_handle *H, Leaf64Args A, cudaStream_t st) {
     return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
   }
   const int p = H->p, pp = p * p;
+  const Level &leaf = H->lev[H->L];
+  const int per_sm = H->batch.fp64_ctas_per_sm;
+  const int grid = per_sm > 0 ? std::min(leaf.nodes, per_sm * H->num_sms) : leaf.nodes;
+  if (p % 2 == 0 && H->batch.even_odd) {
+    const int h = p / 2, m = H->m;
+    const int Rc = std::max(1, std::min(A.R, 2048 / pp));
+    const size_t smem = (size_t)(8 * h * h + pp * Rc + 4 * m * h * Rc) * sizeof(double);
+    static size_t set = 0;
+    if (smem > 48 * 1024 && smem > set) {
+      cudaFuncSetAttribute(k_b_leaf64_eo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      set = smem;
+    }
+    H->trace.begin(slot, st);
+    k_b_leaf64_eo<<<grid, kBT, smem, st>>>(H->g, leaf.nodes, leaf.d_origin, A, H->d_D);
+    H->trace.end(slot, st);
+    return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
+  }
   const int Rc = std::max(1, std::min(A.R, 4096 / pp));
   const size_t smem = (size_t)(4 * pp + pp * Rc) * sizeof(double);
   static size_t set = 0;
@@ -1145,9 +1446,6 @@ int leaf64(hps_handle *H, Leaf64Args A, cudaStream_t st) {
     cudaFuncSetAttribute(k_b_leaf64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     set = smem;
   }
-  const Level &leaf = H->lev[H->L];
-  const int per_sm = H->batch.fp64_ctas_per_sm;
-  const int grid = per_sm > 0 ? std::min(leaf.nodes, per_sm * H->num_sms) : leaf.nodes;
   H->trace.begin(slot, st);
   k_b_leaf64<<<grid, kBT, smem, st>>>(H->g, leaf.nodes, leaf.d_origin, A, H->d_D);
   H->trace.end(slot, st);
@@ -1182,18 +1480,26 @@ struct BdView {
 int refined_solve(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, int R, const Combo &c,
                   double *Rsave, const double *Rb, BdView f, double *u, int refine, double gdt, cudaStream_t st) {
   const GridDims &g = H->g;
+  H->trace.begin(kSetBoundary, st);
   k_b_set_boundary32<<<blocks(g.N_bd * R), 256, 0, st>>>(g, R, B.g32, f.f, f.ld, f.off);
+  H->trace.end(kSetBoundary, st);
   if (int e = sweep32(H, B, ops, o32, R, c, Rsave, nullptr, st)) return e;
+  H->trace.begin(kFinish, st);
   k_b_finish<<<blocks(g.N * R), 256, 0, st>>>(g, R, B.g32, u, 1, 1, f.f, f.ld, f.off);
+  H->trace.end(kFinish, st);
   for (int it = 0; it < refine; ++it) {
     if (int e = residual(H, B, R, u, Rb, gdt, st)) return e;
+    H->trace.begin(kSetBoundary, st);
     k_b_set_boundary32<<<blocks(g.N_bd * R), 256, 0, st>>>(g, R, B.g32, nullptr, 0, 0);
+    H->trace.end(kSetBoundary, st);
     Combo cr{};
     cr.n = 1;
     cr.ptr[0] = B.r;
     cr.coef[0] = 1.0;
     if (int e = sweep32(H, B, ops, o32, R, cr, nullptr, B.r, st)) return e;
+    H->trace.begin(kFinish, st);
     k_b_finish<<<blocks(g.N * R), 256, 0, st>>>(g, R, B.g32, u, 0, 1, nullptr, 0, 0);
+    H->trace.end(kFinish, st);
   }
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
@@ -1333,6 +1639,8 @@ int batch_reserve(hps_handle *H, int R, int groups) {
   }
   if (const char *s = std::getenv("HPS_FP64_CTAS_PER_SM")) Bt.fp64_ctas_per_sm = std::max(0, std::atoi(s));
   if (const char *s = std::getenv("HPS_FLOW_LEVELS")) Bt.flow_levels = std::max(0, std::atoi(s));
+  if (const char *s = std::getenv("HPS_GEMV2")) Bt.gemv2 = std::atoi(s) != 0;
+  if (const char *s = std::getenv("HPS_EVEN_ODD")) Bt.even_odd = std::atoi(s) != 0;
   if (const char *s = std::getenv("HPS_FLOW_N3_MAX")) Bt.flow_n3_max = std::max(0, std::atoi(s));
   // (re)allocate the work vectors; old ones stay in the handle's list until hps_free
   const GridDims &g = H->g;
@@ -1389,7 +1697,9 @@ int solve_batch(hps_handle *H, int R, const double *rhs, const double *f, double
     const double *rb = rhs;
     double *uu = u;
     if (grouped) {  // the group's columns of rhs into its Rb buffer, u assembled in W.u
+      H->trace.begin(kFinish, s);
       k_cols<<<blocks(g.N_int * n), 256, 0, s>>>(rhs, R, c0, W.Rb, n, 0, g.N_int, n);
+      H->trace.end(kFinish, s);
       rb = W.Rb;
       uu = W.u;
     }
@@ -1398,7 +1708,11 @@ int solve_batch(hps_handle *H, int R, const double *rhs, const double *f, double
     if (int e = refined_solve(H, W, H->impl, H->batch.impl32, n, c, nullptr, rb, BdView{f, R, c0}, uu, refine,
                               H->gamma_dt, s))
       return e;
-    if (grouped) k_cols<<<blocks(g.N * n), 256, 0, s>>>(W.u, n, 0, u, R, c0, g.N, n);
+    if (grouped) {
+      H->trace.begin(kFinish, s);
+      k_cols<<<blocks(g.N * n), 256, 0, s>>>(W.u, n, 0, u, R, c0, g.N, n);
+      H->trace.end(kFinish, s);
+    }
     return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
   });
 }
@@ -1411,11 +1725,17 @@ int ark_batch(hps_handle *H, int R, double *u, double dt, const hps_ark_terms *t
   return for_groups(H, R, st, [&](BatchWork &W, int c0, int n, cudaStream_t s) -> int {
     double *uu = u;
     if (grouped) {
+      H->trace.begin(kFinish, s);
       k_cols<<<blocks(g.N * n), 256, 0, s>>>(u, R, c0, W.u, n, 0, g.N, n);
+      H->trace.end(kFinish, s);
       uu = W.u;
     }
     if (int e = ark_group(H, W, n, uu, dt, terms, R, c0, R, c0, refine, tb, s)) return e;
-    if (grouped) k_cols<<<blocks(g.N * n), 256, 0, s>>>(W.u, n, 0, u, R, c0, g.N, n);
+    if (grouped) {
+      H->trace.begin(kFinish, s);
+      k_cols<<<blocks(g.N * n), 256, 0, s>>>(W.u, n, 0, u, R, c0, g.N, n);
+      H->trace.end(kFinish, s);
+    }
     return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
   });
 }

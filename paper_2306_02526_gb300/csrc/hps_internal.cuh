@@ -51,7 +51,7 @@ __host__ __device__ inline int64_t iface_bd(const GridDims &g, int ix0, int iy0,
 // Kernel slots for launch counting and optional CUDA-event timing (hps_trace_*).
 enum Slot {
   kLeafUp = 0, kMergeUpW3, kMergeUpH, kMergeDown, kLeafDown, kLeafEval, kSetBoundary, kMergeUpFused,
-  kMergeDownFused, kResidual, kJump, kNumSlots
+  kMergeDownFused, kResidual, kJump, kFinish, kNumSlots
 };
 
 constexpr int kMaxLevels = 32;
@@ -157,6 +157,8 @@ struct Batch {
   int fp64_ctas_per_sm = 0;  // 0: one CTA per leaf; else a persistent grid of that many per SM
   int flow_levels = 12;      // lower merge levels run as one dataflow kernel (0: one launch per level)
   int flow_n3_max = 32;      // ... those with interfaces of at most this many points
+  bool gemv2 = false;        // upper merge levels: in-CTA + cluster split-K (else split-K partials)
+  bool even_odd = true;      // FP64 leaf kernels by the even-odd decomposition (even p)
   OpSet32 impl32, ident32;
   std::vector<BatchWork> work;
   cudaEvent_t fork = nullptr;
