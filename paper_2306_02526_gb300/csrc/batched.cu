@@ -10,6 +10,7 @@
 // applies compute 4 columns per thread from one operator load.
 #include <algorithm>
 #include <cooperative_groups.h>
+#include <cstdlib>
 
 #include "hps_internal.cuh"
 
@@ -41,6 +42,14 @@ __device__ __forceinline__ void block_gather(int n, Load ld, Use use) {
     }
   }
 }
+
+// 16-byte asynchronous global -> shared copies (cp.async): a CTA issues all copies of a tile,
+// then waits once, so the tile costs one memory round trip instead of one per dependent load.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // The stage right-hand side of one leaf, sum_t coef_t ptr_t, over its nq = q*R contiguous
 // entries from offset `off` (FP64): saved to Rsave if non-null and staged as FP32 at
@@ -129,6 +138,13 @@ __device__ __forceinline__ void stream_fma(float (&acc)[4][TC], const float *__r
   for (; c < K; ++c) tile_fma<TC>(acc, __ldg(reinterpret_cast<const float4 *>(a + (int64_t)c * ld)), x + c * Rp);
 }
 
+// acc += A x with the operator tile in shared memory (4 rows per float4, column c at a + c lda)
+template <int TC>
+__device__ __forceinline__ void smem_fma(float (&acc)[4][TC], const float *a, int lda, int K, const float *x, int Rp) {
+#pragma unroll 4
+  for (int c = 0; c < K; ++c) tile_fma<TC>(acc, *reinterpret_cast<const float4 *>(a + c * lda), x + c * Rp);
+}
+
 template <int TC>
 __global__ void __launch_bounds__(kBT) k_b_leaf_up(GridDims g, int R, const int *__restrict__ origin, Combo rhs,
                                                    double *__restrict__ Rsave, const float *__restrict__ AinvT,
@@ -181,41 +197,102 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_up(GridDims g, int R, const int 
 template <int TC>
 __global__ void __launch_bounds__(kBT) k_b_leaf_down(GridDims g, int R, const int *__restrict__ origin,
                                                      const float *__restrict__ SlT, int ldS, int64_t strS, int identity,
-                                                     const float *__restrict__ w32, float *__restrict__ g32) {
-  extern __shared__ float ub[];  // [b][Rp]
+                                                     int staged, const float *__restrict__ w32,
+                                                     float *__restrict__ g32) {
+  extern __shared__ __align__(16) float ub[];  // [b][Rp], then (staged) the output tile [q][Rp]
   const int m = g.m, q = m * m, b = 4 * m, Rp = round4(R);
   const int k = blockIdx.x;
   const int ix = origin[2 * k], iy = origin[2 * k + 1];
   const int64_t l0 = ((int64_t)iy * g.n1 + ix) * q;
-  block_gather<8, float>(
-      b * Rp,
-      [&](int idx) {
-        const int e = idx / Rp, j = idx % Rp;
-        return j < R ? g32[box_bd(g, ix, iy, 1, 1, e) * R + j] : 0.f;
-      },
-      [&](int idx, float v) { ub[idx] = v; });
-  __syncthreads();
-  const int QQ = (q + 3) / 4, CG = Rp / TC;
-  for (int it = threadIdx.x; it < QQ * CG; it += blockDim.x) {
-    const int r0 = 4 * (it % QQ), j0 = TC * (it / QQ);
-    float acc[4][TC];
+  float *Os = ub + b * Rp;
+  if (!identity) {
+    block_gather<8, float>(
+        b * Rp,
+        [&](int idx) {
+          const int e = idx / Rp, j = idx % Rp;
+          return j < R ? g32[box_bd(g, ix, iy, 1, 1, e) * R + j] : 0.f;
+        },
+        [&](int idx, float v) { ub[idx] = v; });
+    __syncthreads();
+    const int QQ = (q + 3) / 4, CG = Rp / TC;
+    for (int it = threadIdx.x; it < QQ * CG; it += blockDim.x) {
+      const int r0 = 4 * (it % QQ), j0 = TC * (it / QQ);
+      float acc[4][TC];
 #pragma unroll
-    for (int e = 0; e < 4; ++e)
+      for (int e = 0; e < 4; ++e)
 #pragma unroll
-      for (int t = 0; t < TC; ++t) acc[e][t] = 0.f;
-    if (!identity) {
+        for (int t = 0; t < TC; ++t) acc[e][t] = 0.f;
       stream_fma<TC, 8>(acc, SlT + (int64_t)k * strS + r0, ldS, b, ub + j0, Rp);
-    }
+      if (staged) {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int r = r0 + e;
-      if (r >= q) continue;
+        for (int e = 0; e < 4; ++e)
+          if (r0 + e < q)
 #pragma unroll
-      for (int t = 0; t < TC; ++t) {
-        const int j = j0 + t;
-        if (j < R) g32[(l0 + r) * R + j] = w32[((int64_t)k * q + r) * R + j] + acc[e][t];
+            for (int t = 0; t < TC; t += 4)
+              *reinterpret_cast<float4 *>(Os + (r0 + e) * Rp + j0 + t) =
+                  make_float4(acc[e][t], acc[e][t + 1], acc[e][t + 2], acc[e][t + 3]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (r0 + e < q)
+#pragma unroll
+            for (int t = 0; t < TC; ++t)
+              if (j0 + t < R)
+                g32[(l0 + r0 + e) * R + j0 + t] = w32[((int64_t)k * q + r0 + e) * R + j0 + t] + acc[e][t];
       }
     }
+    if (!staged) return;
+    __syncthreads();
+  }
+  // u_i = w + S u_b: the leaf's interior block is contiguous in both vectors
+  for (int idx = threadIdx.x; idx < q * R; idx += blockDim.x)
+    g32[l0 * R + idx] = w32[(int64_t)k * q * R + idx] + (identity ? 0.f : Os[(idx / R) * Rp + idx % R]);
+}
+
+// Shared leaf operator, persistent CTAs: S_leaf^T is copied to shared memory once per CTA and
+// every leaf the CTA takes is applied from there (a per-leaf CTA re-reads it from L1/L2).
+template <int TC>
+__global__ void __launch_bounds__(kBT) k_b_leaf_down_res(GridDims g, int nodes, int R, const int *__restrict__ origin,
+                                                         const float *__restrict__ SlT, int ldS,
+                                                         const float *__restrict__ w32, float *__restrict__ g32) {
+  extern __shared__ __align__(16) float sres[];
+  const int m = g.m, q = m * m, b = 4 * m, Rp = round4(R);
+  float *Ss = sres, *ub = sres + (size_t)b * ldS, *Os = ub + b * Rp;  // [b][ldS], [b][Rp], [q][Rp]
+  for (int i = threadIdx.x; i < b * ldS / 4; i += blockDim.x) cp_async16(Ss + 4 * i, SlT + 4 * i);
+  cp_async_wait_all();
+  const int QQ = (q + 3) / 4, CG = Rp / TC;
+  for (int k = blockIdx.x; k < nodes; k += gridDim.x) {
+    const int ix = origin[2 * k], iy = origin[2 * k + 1];
+    const int64_t l0 = ((int64_t)iy * g.n1 + ix) * q;
+    __syncthreads();  // previous leaf done with ub; operator copy visible
+    block_gather<8, float>(
+        b * Rp,
+        [&](int idx) {
+          const int e = idx / Rp, j = idx % Rp;
+          return j < R ? g32[box_bd(g, ix, iy, 1, 1, e) * R + j] : 0.f;
+        },
+        [&](int idx, float v) { ub[idx] = v; });
+    __syncthreads();
+    for (int it = threadIdx.x; it < QQ * CG; it += blockDim.x) {
+      const int r0 = 4 * (it % QQ), j0 = TC * (it / QQ);
+      float acc[4][TC];
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int t = 0; t < TC; ++t) acc[e][t] = 0.f;
+      smem_fma<TC>(acc, Ss + r0, ldS, b, ub + j0, Rp);
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (r0 + e < q)
+#pragma unroll
+          for (int t = 0; t < TC; t += 4)
+            *reinterpret_cast<float4 *>(Os + (r0 + e) * Rp + j0 + t) =
+                make_float4(acc[e][t], acc[e][t + 1], acc[e][t + 2], acc[e][t + 3]);
+    }
+    __syncthreads();
+    // u_i = w + S u_b: the leaf's interior block is contiguous in both vectors
+    for (int idx = threadIdx.x; idx < q * R; idx += blockDim.x)
+      g32[l0 * R + idx] = w32[(int64_t)k * q * R + idx] + Os[(idx / R) * Rp + idx % R];
   }
 }
 
@@ -313,10 +390,35 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_down_narrow(GridDims g, int R, c
 struct BPlan {
   int M, K, nodes, R, Rp, TC, MQ, CG;
   int npc, quads_cta, row_tiles, node_groups, ksplit, kchunk;
+  int shared_op;  // operator shared by all nodes (stride 0)
+  int trows;      // rows of the operator tile a CTA stages (multiple of 4)
 };
 
-BPlan plan_b(int M, int K, int nodes, int R, int target) {
+constexpr int kBOpFloats = 16384;  // operator tile staged in shared memory (64 KB)
+
+__host__ __device__ inline int b_tiles(const BPlan &P) { return P.shared_op ? 1 : P.npc; }
+size_t b_smem_floats(const BPlan &P) {  // operator tile(s) + vector chunk
+  return (size_t)b_tiles(P) * P.kchunk * P.trows + (size_t)P.npc * P.kchunk * P.Rp;
+}
+
+// Tuning of the split-K plan (process-wide; HPS_PLAN_KMIN, HPS_PLAN_NPC_MAX override): the
+// smallest K chunk of a split, and the most nodes one CTA takes.
+struct PlanTune {
+  int kmin = 32, npc_max = 1 << 30;
+  PlanTune() {
+    if (const char *s = std::getenv("HPS_PLAN_KMIN")) kmin = std::max(1, std::atoi(s));
+    if (const char *s = std::getenv("HPS_PLAN_NPC_MAX")) npc_max = std::max(1, std::atoi(s));
+  }
+};
+const PlanTune &plan_tune() {
+  static const PlanTune t;
+  return t;
+}
+
+BPlan plan_b(int M, int K, int nodes, int R, int target, bool shared_op) {
+  const PlanTune &tune = plan_tune();
   BPlan P;
+  P.shared_op = shared_op ? 1 : 0;
   P.M = M;
   P.K = K;
   P.nodes = nodes;
@@ -327,7 +429,7 @@ BPlan plan_b(int M, int K, int nodes, int R, int target) {
   P.CG = P.Rp / P.TC;
   const int per = P.MQ * P.CG;
   if (per <= kBT / 2) {
-    P.npc = std::max(1, std::min(nodes, kBT / per));
+    P.npc = std::max(1, std::min({nodes, kBT / per, tune.npc_max}));
     P.quads_cta = P.MQ;
     P.row_tiles = 1;
   } else {
@@ -338,11 +440,22 @@ BPlan plan_b(int M, int K, int nodes, int R, int target) {
   P.node_groups = (nodes + P.npc - 1) / P.npc;
   const int base = P.node_groups * P.row_tiles;
   int ks = 1;
-  if (base < target) ks = std::min({(target + base - 1) / base, std::max(1, K / 32), kMaxSplit});
+  if (base < target) ks = std::min({(target + base - 1) / base, std::max(1, K / tune.kmin), kMaxSplit});
   P.kchunk = (K + ks - 1) / ks;
-  while ((int64_t)P.npc * P.kchunk * P.Rp > kBSmemFloats) P.kchunk = (P.kchunk + 1) / 2;
+  P.trows = P.npc > 1 ? 4 * P.MQ : 4 * std::min(P.quads_cta, P.MQ);
+  while ((int64_t)P.npc * P.kchunk * P.Rp > kBSmemFloats ||
+         (int64_t)b_tiles(P) * P.kchunk * P.trows > kBOpFloats)
+    P.kchunk = (P.kchunk + 1) / 2;
   P.ksplit = (K + P.kchunk - 1) / P.kchunk;
   return P;
+}
+
+int plan_target(const hps_handle *H) {  // CTAs a split-K plan aims for (HPS_PLAN_TARGET per SM)
+  static const int per_sm = [] {
+    const char *s = std::getenv("HPS_PLAN_TARGET");
+    return s ? std::max(1, std::atoi(s)) : 2;
+  }();
+  return per_sm * H->num_sms;
 }
 
 struct BXDiff {  // d = h^b_3 - h^a_3 (+ interface right-hand side)
@@ -400,11 +513,24 @@ struct BEScatter {
 template <int TC, class XL, class EP>
 __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict__ AT, int ld, int64_t str, XL xl,
                                                 EP ep, float *__restrict__ partial) {
-  extern __shared__ float xs[];  // [nn][klen][Rp]
+  extern __shared__ __align__(16) float smb[];
   const int ng = blockIdx.x / P.row_tiles, tile = blockIdx.x % P.row_tiles;
   const int node0 = ng * P.npc, nn = min(P.npc, P.nodes - node0);
   const int ks = blockIdx.y, c0 = ks * P.kchunk, klen = min(P.kchunk, P.K - c0);
   const int Rp = P.Rp;
+  // operator tile(s) [tile][klen][trows] by asynchronous copies, overlapping the vector staging
+  const int trows = P.trows, rlo = P.npc > 1 ? 0 : 4 * tile * P.quads_cta;
+  const int trow = min(trows, 4 * P.MQ - rlo);  // rows of this CTA's tile (ragged last tile)
+  const int ntile = P.shared_op ? 1 : nn;
+  float *As = smb, *xs = smb + (size_t)b_tiles(P) * P.kchunk * trows;
+  {
+    const int q4 = trow / 4, n16 = ntile * klen * q4;
+    for (int i = threadIdx.x; i < n16; i += blockDim.x) {
+      const int t = i / (klen * q4), rem = i % (klen * q4), c = rem / q4, qq = rem % q4;
+      cp_async16(As + ((size_t)t * klen + c) * trows + 4 * qq,
+                 AT + (int64_t)(node0 + t) * str + (int64_t)(c0 + c) * ld + rlo + 4 * qq);
+    }
+  }
   block_gather<8, float>(
       nn * klen * Rp,
       [&](int idx) {
@@ -412,6 +538,7 @@ __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict
         return j < P.R ? xl(node0 + lo, c0 + c, j) : 0.f;
       },
       [&](int idx, float v) { xs[idx] = v; });
+  cp_async_wait_all();
   __syncthreads();
   int lo, rq, cg;
   if (P.npc > 1) {
@@ -420,22 +547,23 @@ __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict
     const int rem = threadIdx.x % per;
     cg = rem / P.MQ;
     rq = rem % P.MQ;
-    if (lo >= nn) return;
   } else {
     lo = 0;
     cg = threadIdx.x / P.quads_cta;
     rq = tile * P.quads_cta + threadIdx.x % P.quads_cta;
-    if (cg >= P.CG || rq >= P.MQ) return;
   }
-  const int k = node0 + lo, r0 = 4 * rq, j0 = TC * cg;
-  const float *a = AT + (int64_t)k * str + (int64_t)c0 * ld + r0;
-  const float *x = xs + (int64_t)lo * klen * Rp + j0;
+  const bool live = lo < nn && cg < P.CG && rq < P.MQ;
+  const int r0 = 4 * rq, j0 = TC * cg;
   float acc[4][TC];
 #pragma unroll
   for (int e = 0; e < 4; ++e)
 #pragma unroll
     for (int t = 0; t < TC; ++t) acc[e][t] = 0.f;
-  stream_fma<TC, 8>(acc, a, ld, klen, x, Rp);
+  if (live)
+    smem_fma<TC>(acc, As + (size_t)(P.shared_op ? 0 : lo) * klen * trows + (r0 - rlo), trows, klen,
+                 xs + (int64_t)lo * klen * Rp + j0, Rp);
+  if (!live) return;
+  const int k = node0 + lo;
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
     const int r = r0 + e;
@@ -469,8 +597,14 @@ __global__ void k_b_reduce(BPlan P, const float *__restrict__ partial, EP ep) {
 template <class XL, class EP>
 int launch_b(hps_handle *H, BatchWork &B, int slot, const BPlan &P, const float *AT, int ld, int64_t str, XL xl,
              EP ep, cudaStream_t st) {
-  const size_t smem = (size_t)P.npc * P.kchunk * P.Rp * sizeof(float);
+  const size_t smem = b_smem_floats(P) * sizeof(float);
   if (P.ksplit > 1 && (size_t)P.ksplit * P.nodes * P.M * P.Rp > B.partial_len) return HPS_EINVAL;
+  static size_t set = 0;
+  if (smem > 48 * 1024 && smem > set) {
+    cudaFuncSetAttribute(k_b_gemv<8, XL, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_b_gemv<4, XL, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set = smem;
+  }
   H->trace.begin(slot, st);
   const dim3 grid(P.node_groups * P.row_tiles, P.ksplit);
   if (P.TC == 8)
@@ -595,7 +729,7 @@ int launch_b2(hps_handle *H, BatchWork &B, int slot, int M, int K, int nodes, in
   const BPlan2 P = plan_b2(M, K, nodes, R);
   const size_t smem = b2_smem(P);
   if (!H->batch.gemv2 || smem > kB2MaxSmem)
-    return launch_b(H, B, slot, plan_b(M, K, nodes, R, 2 * H->num_sms), AT, ld, str, xl, ep, st);
+    return launch_b(H, B, slot, plan_b(M, K, nodes, R, plan_target(H), str == 0), AT, ld, str, xl, ep, st);
   auto kern = P.TC == 8 ? k_b_gemv2<8, XL, EP> : k_b_gemv2<4, XL, EP>;
   static size_t set8 = 0, set4 = 0;
   size_t &set = P.TC == 8 ? set8 : set4;
@@ -1223,10 +1357,13 @@ size_t partial_floats(hps_handle *H, int Rmax) {
   for (int R = 1; R <= Rmax; ++R)
   for (int l = 0; l < H->L; ++l) {
     const Level &lv = H->lev[l];
-    const BPlan P[3] = {plan_b(lv.n3, lv.n3, lv.nodes, R, 2 * H->num_sms), plan_b(lv.nb, lv.n3, lv.nodes, R, 2 * H->num_sms),
-                        plan_b(lv.n3, lv.nb, lv.nodes, R, 2 * H->num_sms)};
-    for (const BPlan &pl : P)
-      if (pl.ksplit > 1) mx = std::max(mx, (size_t)pl.ksplit * pl.nodes * pl.M * pl.Rp);
+    for (int sh = 0; sh < 2; ++sh) {  // the identity operators are shared even when the others are not
+      const BPlan P[3] = {plan_b(lv.n3, lv.n3, lv.nodes, R, plan_target(H), sh),
+                          plan_b(lv.nb, lv.n3, lv.nodes, R, plan_target(H), sh),
+                          plan_b(lv.n3, lv.nb, lv.nodes, R, plan_target(H), sh)};
+      for (const BPlan &pl : P)
+        if (pl.ksplit > 1) mx = std::max(mx, (size_t)pl.ksplit * pl.nodes * pl.M * pl.Rp);
+    }
   }
   return mx;
 }
@@ -1383,12 +1520,33 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
   if (narrow)
     k_b_leaf_down_narrow<<<leaf.nodes, kBT, (size_t)(4 * b + KS * 16 * QQ) * sizeof(float), st>>>(
         H->g, R, leaf.d_origin, o32.Sleaf.p, o32.Sleaf.ld, o32.Sleaf.str, ops.identity ? 1 : 0, B.w32, B.g32);
-  else if (tc8)
-    k_b_leaf_down<8><<<leaf.nodes, kBT, (size_t)b * Rp * sizeof(float), st>>>(
-        H->g, R, leaf.d_origin, o32.Sleaf.p, o32.Sleaf.ld, o32.Sleaf.str, ops.identity ? 1 : 0, B.w32, B.g32);
-  else
-    k_b_leaf_down<4><<<leaf.nodes, kBT, (size_t)b * Rp * sizeof(float), st>>>(
-        H->g, R, leaf.d_origin, o32.Sleaf.p, o32.Sleaf.ld, o32.Sleaf.str, ops.identity ? 1 : 0, B.w32, B.g32);
+  else if (H->shared && !ops.identity && (size_t)(b * o32.Sleaf.ld + (b + q) * Rp) * sizeof(float) <= 110 * 1024) {
+    const size_t smem = (size_t)(b * o32.Sleaf.ld + (b + q) * Rp) * sizeof(float);
+    auto kern = tc8 ? k_b_leaf_down_res<8> : k_b_leaf_down_res<4>;
+    static size_t set8 = 0, set4 = 0;
+    size_t &set = tc8 ? set8 : set4;
+    if (smem > 48 * 1024 && smem > set) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      set = smem;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBT, smem) != cudaSuccess || per_sm < 1)
+      return HPS_ECUDA;
+    kern<<<std::min(leaf.nodes, per_sm * H->num_sms), kBT, smem, st>>>(H->g, leaf.nodes, R, leaf.d_origin,
+                                                                      o32.Sleaf.p, o32.Sleaf.ld, B.w32, B.g32);
+  } else {
+    const int staged = (size_t)(b + q) * Rp * sizeof(float) <= 96 * 1024;  // coalesced output through smem
+    const size_t smem = (size_t)(staged ? b + q : b) * Rp * sizeof(float);
+    auto kern = tc8 ? k_b_leaf_down<8> : k_b_leaf_down<4>;
+    static size_t set8 = 0, set4 = 0;
+    size_t &set = tc8 ? set8 : set4;
+    if (smem > 48 * 1024 && smem > set) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      set = smem;
+    }
+    kern<<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, o32.Sleaf.p, o32.Sleaf.ld, o32.Sleaf.str,
+                                        ops.identity ? 1 : 0, staged, B.w32, B.g32);
+  }
   H->trace.end(kLeafDown, st);
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
