@@ -23,6 +23,15 @@ constexpr int kBSmemFloats = 8192;  // vector staging of the merge applies (32 K
 
 __host__ __device__ inline int round4(int r) { return (r + 3) & ~3; }
 
+// Where a sweep's FP32 result goes in the FP64 solution: u = v (assign) or u += v (a correction).
+struct UOut {
+  double *u;
+  int assign;
+};
+__device__ __forceinline__ void u_out(const UOut &U, int64_t i, float v) {
+  U.u[i] = U.assign ? (double)v : U.u[i] + (double)v;
+}
+
 // Block-wide loop over [0, n): every thread issues U independent loads before it uses any of
 // them (a warp issues in order, so a load-then-store loop would wait out one load latency per
 // element).
@@ -39,6 +48,38 @@ __device__ __forceinline__ void block_gather(int n, Load ld, Use use) {
     for (int u = 0; u < U; ++u) {
       const int idx = base + u * blockDim.x;
       if (idx < n) use(idx, v[u]);
+    }
+  }
+}
+
+// The stage right-hand sides of all leaves at once (interior points are contiguous): FP64 sum
+// to Rsave (if non-null) and its FP32 copy to r32, four entries per thread.
+__global__ void k_b_combo(int64_t n, Combo rhs, double *__restrict__ Rsave, float *__restrict__ r32) {
+  constexpr int U = 4;
+  const int64_t base = (int64_t)blockIdx.x * blockDim.x * U + threadIdx.x;
+  double acc[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) acc[u] = 0.0;
+  for (int t = 0; t < rhs.n; t += 2) {
+    const bool two = t + 1 < rhs.n;
+    const double *s0 = rhs.ptr[t], *s1 = two ? rhs.ptr[t + 1] : s0;
+    const double c0 = rhs.coef[t], c1 = two ? rhs.coef[t + 1] : 0.0;
+    double v0[U], v1[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + (int64_t)u * blockDim.x;
+      v0[u] = i < n ? s0[i] : 0.0;
+      v1[u] = i < n ? s1[i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] = fma(c1, v1[u], fma(c0, v0[u], acc[u]));
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t i = base + (int64_t)u * blockDim.x;
+    if (i < n) {
+      if (Rsave) Rsave[i] = acc[u];
+      r32[i] = (float)acc[u];
     }
   }
 }
@@ -147,19 +188,33 @@ __device__ __forceinline__ void smem_fma(float (&acc)[4][TC], const float *a, in
 
 template <int TC>
 __global__ void __launch_bounds__(kBT) k_b_leaf_up(GridDims g, int R, const int *__restrict__ origin, Combo rhs,
-                                                   double *__restrict__ Rsave, const float *__restrict__ AinvT,
-                                                   int ldA, int64_t strA, int identity, const double *__restrict__ Dg,
+                                                   double *__restrict__ Rsave, const float *__restrict__ r32,
+                                                   const float *__restrict__ AinvT, int ldA, int64_t strA,
+                                                   int identity, const double *__restrict__ Dg,
                                                    float *__restrict__ w32, float *__restrict__ h32) {
-  extern __shared__ float smf[];
+  extern __shared__ __align__(16) float smf[];
   const int p = g.p, m = g.m, q = m * m, b = 4 * m, Rp = round4(R);
   float *D1x = smf, *D1y = smf + p * p, *Rs = smf + round4(2 * p * p), *Ws = Rs + q * Rp;
   const int k = blockIdx.x;
   const int64_t l0 = ((int64_t)origin[2 * k + 1] * g.n1 + origin[2 * k]) * q;
   for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) smf[i] = (float)Dg[i];
-  if (Rp != R)  // padding columns
-    for (int idx = threadIdx.x; idx < q * Rp; idx += blockDim.x) Rs[idx] = 0.f;
-  __syncthreads();
-  stage_combo<8>(rhs, l0 * R, q * R, R, Rp, Rsave, Rs);
+  if (r32 && Rp == R) {  // right-hand side formed by k_b_combo: one asynchronous copy
+    for (int i = threadIdx.x; i < q * R / 4; i += blockDim.x) cp_async16(Rs + 4 * i, r32 + l0 * R + 4 * i);
+    cp_async_wait_all();
+  } else if (r32) {
+    block_gather<8, float>(
+        q * Rp,
+        [&](int idx) {
+          const int r = idx / Rp, j = idx % Rp;
+          return j < R ? r32[(l0 + r) * R + j] : 0.f;
+        },
+        [&](int idx, float v) { Rs[idx] = v; });
+  } else {
+    if (Rp != R)  // padding columns
+      for (int idx = threadIdx.x; idx < q * Rp; idx += blockDim.x) Rs[idx] = 0.f;
+    __syncthreads();
+    stage_combo<8>(rhs, l0 * R, q * R, R, Rp, Rsave, Rs);
+  }
   __syncthreads();
   const int QQ = (q + 3) / 4, CG = Rp / TC;
   for (int it = threadIdx.x; it < QQ * CG; it += blockDim.x) {
@@ -198,7 +253,7 @@ template <int TC>
 __global__ void __launch_bounds__(kBT) k_b_leaf_down(GridDims g, int R, const int *__restrict__ origin,
                                                      const float *__restrict__ SlT, int ldS, int64_t strS, int identity,
                                                      int staged, const float *__restrict__ w32,
-                                                     float *__restrict__ g32) {
+                                                     const float *__restrict__ g32, UOut uo) {
   extern __shared__ __align__(16) float ub[];  // [b][Rp], then (staged) the output tile [q][Rp]
   const int m = g.m, q = m * m, b = 4 * m, Rp = round4(R);
   const int k = blockIdx.x;
@@ -238,7 +293,7 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_down(GridDims g, int R, const in
 #pragma unroll
             for (int t = 0; t < TC; ++t)
               if (j0 + t < R)
-                g32[(l0 + r0 + e) * R + j0 + t] = w32[((int64_t)k * q + r0 + e) * R + j0 + t] + acc[e][t];
+                u_out(uo, (l0 + r0 + e) * R + j0 + t, w32[((int64_t)k * q + r0 + e) * R + j0 + t] + acc[e][t]);
       }
     }
     if (!staged) return;
@@ -246,7 +301,7 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_down(GridDims g, int R, const in
   }
   // u_i = w + S u_b: the leaf's interior block is contiguous in both vectors
   for (int idx = threadIdx.x; idx < q * R; idx += blockDim.x)
-    g32[l0 * R + idx] = w32[(int64_t)k * q * R + idx] + (identity ? 0.f : Os[(idx / R) * Rp + idx % R]);
+    u_out(uo, l0 * R + idx, w32[(int64_t)k * q * R + idx] + (identity ? 0.f : Os[(idx / R) * Rp + idx % R]));
 }
 
 // Shared leaf operator, persistent CTAs: S_leaf^T is copied to shared memory once per CTA and
@@ -254,7 +309,8 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_down(GridDims g, int R, const in
 template <int TC>
 __global__ void __launch_bounds__(kBT) k_b_leaf_down_res(GridDims g, int nodes, int R, const int *__restrict__ origin,
                                                          const float *__restrict__ SlT, int ldS,
-                                                         const float *__restrict__ w32, float *__restrict__ g32) {
+                                                         const float *__restrict__ w32, const float *__restrict__ g32,
+                                                         UOut uo) {
   extern __shared__ __align__(16) float sres[];
   const int m = g.m, q = m * m, b = 4 * m, Rp = round4(R);
   float *Ss = sres, *ub = sres + (size_t)b * ldS, *Os = ub + b * Rp;  // [b][ldS], [b][Rp], [q][Rp]
@@ -292,7 +348,7 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_down_res(GridDims g, int nodes, 
     __syncthreads();
     // u_i = w + S u_b: the leaf's interior block is contiguous in both vectors
     for (int idx = threadIdx.x; idx < q * R; idx += blockDim.x)
-      g32[l0 * R + idx] = w32[(int64_t)k * q * R + idx] + Os[(idx / R) * Rp + idx % R];
+      u_out(uo, l0 * R + idx, w32[(int64_t)k * q * R + idx] + Os[(idx / R) * Rp + idx % R]);
   }
 }
 
@@ -360,7 +416,7 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_up_narrow(GridDims g, int R, con
 __global__ void __launch_bounds__(kBT) k_b_leaf_down_narrow(GridDims g, int R, const int *__restrict__ origin,
                                                             const float *__restrict__ SlT, int ldS, int64_t strS,
                                                             int identity, const float *__restrict__ w32,
-                                                            float *__restrict__ g32) {
+                                                            const float *__restrict__ g32, UOut uo) {
   extern __shared__ float smf[];
   const int m = g.m, q = m * m, b = 4 * m, QQ = (q + 3) / 4, KS = max(1, kBT / QQ);
   float *ub = smf, *part = smf + 4 * b;
@@ -382,7 +438,7 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_down_narrow(GridDims g, int R, c
     float s = w32[((int64_t)k * q + r) * R + j];
     if (!identity)
       for (int ks = 0; ks < KS; ++ks) s += part[(int64_t)ks * 16 * QQ + r * 4 + j];
-    g32[(l0 + r) * R + j] = s;
+    u_out(uo, (l0 + r) * R + j, s);
   }
 }
 
@@ -499,14 +555,18 @@ struct BEFlux {
     h[((int64_t)k * nb + r) * R + j] = hC[((int64_t)(2 * k) * nbc + hsrc[r]) * R + j] + v;
   }
 };
-struct BEScatter {
+struct BEScatter {  // interface values: FP32 for the levels below, and into the FP64 solution
   GridDims g;
   const int *origin;
   int a, c, split, n3, R;
   const float *w3;
   float *gv;
+  UOut uo;
   __device__ void operator()(int k, int r, int j, float v) const {
-    gv[iface_bd(g, origin[2 * k], origin[2 * k + 1], a, c, split, r) * R + j] = v + w3[((int64_t)k * n3 + r) * R + j];
+    const int64_t i = iface_bd(g, origin[2 * k], origin[2 * k + 1], a, c, split, r) * R + j;
+    const float x = v + w3[((int64_t)k * n3 + r) * R + j];
+    gv[i] = x;
+    u_out(uo, i, x);
   }
 };
 
@@ -785,6 +845,7 @@ struct FlowArgs {
   int *err;
   const double *jump;
   float *g32;
+  UOut uo;
   unsigned long long limit_ns;
 };
 
@@ -939,11 +1000,15 @@ __global__ void __launch_bounds__(kBT) k_b_flow_down(FlowArgs A) {
       float4 acc = make_float4(j0 < R ? w[0] : 0.f, j0 + 1 < R ? w[1] : 0.f, j0 + 2 < R ? w[2] : 0.f,
                                j0 + 3 < R ? w[3] : 0.f);
       flow_dot(acc, L.S + (int64_t)k * L.strS + r, L.ldS, L.nb, Ub + j0, Rp);
-      float *o = A.g32 + iface_bd(A.g, ox, oy, L.a, L.c, L.split, r) * R + j0;
-      if (j0 + 0 < R) o[0] = acc.x;
-      if (j0 + 1 < R) o[1] = acc.y;
-      if (j0 + 2 < R) o[2] = acc.z;
-      if (j0 + 3 < R) o[3] = acc.w;
+      const int64_t i0 = iface_bd(A.g, ox, oy, L.a, L.c, L.split, r) * R + j0;
+      float *o = A.g32 + i0;
+      const float v4[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (j0 + t < R) {
+          o[t] = v4[t];
+          u_out(A.uo, i0 + t, v4[t]);
+        }
     }
     flow_done(A, L, k);
   }
@@ -1248,27 +1313,10 @@ __global__ void k_b_jump(GridDims g, int R, const double *__restrict__ u, double
   r[gi * R + col] = -(fa - fb);
 }
 
-// compact boundary position of global point gi, or -1 if gi is not on the outer boundary
-__device__ __forceinline__ int64_t bd_pos(const GridDims &g, int64_t gi) {
-  const int64_t nv = (int64_t)g.n2 * g.m, nh = (int64_t)g.n1 * g.m;
-  if (gi < g.N_int) return -1;
-  if (gi < g.N_int + g.N_v) {
-    const int64_t off = gi - g.N_int;
-    const int64_t line = off / nv;
-    if (line == 0) return off;
-    if (line == g.n1) return nv + (off - (int64_t)g.n1 * nv);
-    return -1;
-  }
-  const int64_t off = gi - g.N_int - g.N_v;
-  const int64_t line = off / nh;
-  if (line == 0) return 2 * nv + off;
-  if (line == g.n2) return 2 * nv + nh + (off - (int64_t)g.n2 * nh);
-  return -1;
-}
 
-// f: [N_bd][fld], this call's columns from foff
+// f: [N_bd][fld], this call's columns from foff; u (if non-null) gets the FP64 values
 __global__ void k_b_set_boundary32(GridDims g, int R, float *__restrict__ g32, const double *__restrict__ f, int fld,
-                                   int foff) {
+                                   int foff, double *__restrict__ u) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= g.N_bd * R) return;
   const int64_t kk = idx / R;
@@ -1279,28 +1327,11 @@ __global__ void k_b_set_boundary32(GridDims g, int R, float *__restrict__ g32, c
   else if (kk < 2 * nv) gi = g.N_int + (int64_t)g.n1 * nv + (kk - nv);
   else if (kk < 2 * nv + nh) gi = g.N_int + g.N_v + (kk - 2 * nv);
   else gi = g.N_int + g.N_v + (int64_t)g.n2 * nh + (kk - 2 * nv - nh);
-  g32[gi * R + j] = f ? (float)f[kk * fld + foff + j] : 0.f;
+  const double v = f ? f[kk * fld + foff + j] : 0.0;
+  g32[gi * R + j] = (float)v;
+  if (u) u[gi * R + j] = v;
 }
 
-// u (FP64) from the FP32 sweep result: assign or add; interior points optionally; shared-edge
-// points always; outer-boundary points set to f exactly (assign) or left alone (add).
-__global__ void k_b_finish(GridDims g, int R, const float *__restrict__ g32, double *__restrict__ u, int assign,
-                           int interior, const double *__restrict__ f, int fld, int foff) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= g.N * R) return;
-  const int64_t gi = idx / R;
-  if (gi < g.N_int) {
-    if (!interior) return;
-    u[idx] = assign ? (double)g32[idx] : u[idx] + (double)g32[idx];
-    return;
-  }
-  const int64_t kk = bd_pos(g, gi);
-  if (kk >= 0) {
-    if (assign) u[idx] = f ? f[kk * fld + foff + idx % R] : 0.0;
-    return;
-  }
-  u[idx] = assign ? (double)g32[idx] : u[idx] + (double)g32[idx];
-}
 
 inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
@@ -1391,7 +1422,7 @@ int flow_launch(hps_handle *H, BatchWork &B, const FlowArgs &FA, bool up, size_t
 // One FP32 sweep on R columns: leaf applies, merges up (with an optional FP64 interface
 // right-hand side), merges down into g32 (whose outer boundary the caller has set), leaf solves.
 int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, int R, const Combo &rhs,
-            double *Rsave, const double *jump, cudaStream_t st) {
+            double *Rsave, const double *jump, UOut uo, cudaStream_t st) {
   const int L = H->L, p = H->p, q = H->q, b = H->b, Rp = round4(R);
   const Level &leaf = H->lev[L];
   const bool tc8 = Rp % 8 == 0;
@@ -1417,11 +1448,17 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
       set = smem;
     }
     H->trace.begin(kLeafUp, st);
+    const float *r32 = nullptr;
+    if (H->batch.leaf_split) {  // stage right-hand side as its own streaming pass
+      const int64_t n = H->g.N_int * R;
+      k_b_combo<<<(unsigned)((n + 4 * 256 - 1) / (4 * 256)), 256, 0, st>>>(n, rhs, Rsave, B.r32);
+      r32 = B.r32;
+    }
     if (tc8)
-      k_b_leaf_up<8><<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, o32.Ainv.p, o32.Ainv.ld,
+      k_b_leaf_up<8><<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, r32, o32.Ainv.p, o32.Ainv.ld,
                                                     o32.Ainv.str, ops.identity ? 1 : 0, H->d_D, B.w32, B.h32[L]);
     else
-      k_b_leaf_up<4><<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, o32.Ainv.p, o32.Ainv.ld,
+      k_b_leaf_up<4><<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, r32, o32.Ainv.p, o32.Ainv.ld,
                                                     o32.Ainv.str, ops.identity ? 1 : 0, H->d_D, B.w32, B.h32[L]);
     H->trace.end(kLeafUp, st);
   }
@@ -1478,6 +1515,7 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
     FA.err = H->perr;
     FA.jump = jump;
     FA.g32 = B.g32;
+    FA.uo = uo;
     FA.limit_ns = 2000000000ull;
     smem_up = (size_t)2 * n3max * Rp * sizeof(float);
     smem_down = (size_t)nbmax * Rp * sizeof(float);
@@ -1504,7 +1542,7 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
     const Level &lv = H->lev[l];
     if (int e = launch_b2(H, B, kMergeDown, lv.n3, lv.nb, lv.nodes, R, o32.S[l].p, o32.S[l].ld, o32.S[l].str,
                           BXBd{H->g, lv.d_origin, lv.a, lv.c, R, B.g32},
-                          BEScatter{H->g, lv.d_origin, lv.a, lv.c, lv.split, lv.n3, R, B.w332[l], B.g32}, st))
+                          BEScatter{H->g, lv.d_origin, lv.a, lv.c, lv.split, lv.n3, R, B.w332[l], B.g32, uo}, st))
       return e;
   }
   if (nflow > 0) {
@@ -1519,7 +1557,7 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
   H->trace.begin(kLeafDown, st);
   if (narrow)
     k_b_leaf_down_narrow<<<leaf.nodes, kBT, (size_t)(4 * b + KS * 16 * QQ) * sizeof(float), st>>>(
-        H->g, R, leaf.d_origin, o32.Sleaf.p, o32.Sleaf.ld, o32.Sleaf.str, ops.identity ? 1 : 0, B.w32, B.g32);
+        H->g, R, leaf.d_origin, o32.Sleaf.p, o32.Sleaf.ld, o32.Sleaf.str, ops.identity ? 1 : 0, B.w32, B.g32, uo);
   else if (H->shared && !ops.identity && (size_t)(b * o32.Sleaf.ld + (b + q) * Rp) * sizeof(float) <= 110 * 1024) {
     const size_t smem = (size_t)(b * o32.Sleaf.ld + (b + q) * Rp) * sizeof(float);
     auto kern = tc8 ? k_b_leaf_down_res<8> : k_b_leaf_down_res<4>;
@@ -1533,7 +1571,7 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBT, smem) != cudaSuccess || per_sm < 1)
       return HPS_ECUDA;
     kern<<<std::min(leaf.nodes, per_sm * H->num_sms), kBT, smem, st>>>(H->g, leaf.nodes, R, leaf.d_origin,
-                                                                      o32.Sleaf.p, o32.Sleaf.ld, B.w32, B.g32);
+                                                                      o32.Sleaf.p, o32.Sleaf.ld, B.w32, B.g32, uo);
   } else {
     const int staged = (size_t)(b + q) * Rp * sizeof(float) <= 96 * 1024;  // coalesced output through smem
     const size_t smem = (size_t)(staged ? b + q : b) * Rp * sizeof(float);
@@ -1545,7 +1583,7 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
       set = smem;
     }
     kern<<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, o32.Sleaf.p, o32.Sleaf.ld, o32.Sleaf.str,
-                                        ops.identity ? 1 : 0, staged, B.w32, B.g32);
+                                        ops.identity ? 1 : 0, staged, B.w32, B.g32, uo);
   }
   H->trace.end(kLeafDown, st);
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
@@ -1639,25 +1677,21 @@ int refined_solve(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &
                   double *Rsave, const double *Rb, BdView f, double *u, int refine, double gdt, cudaStream_t st) {
   const GridDims &g = H->g;
   H->trace.begin(kSetBoundary, st);
-  k_b_set_boundary32<<<blocks(g.N_bd * R), 256, 0, st>>>(g, R, B.g32, f.f, f.ld, f.off);
+  k_b_set_boundary32<<<blocks(g.N_bd * R), 256, 0, st>>>(g, R, B.g32, f.f, f.ld, f.off, u);
   H->trace.end(kSetBoundary, st);
-  if (int e = sweep32(H, B, ops, o32, R, c, Rsave, nullptr, st)) return e;
-  H->trace.begin(kFinish, st);
-  k_b_finish<<<blocks(g.N * R), 256, 0, st>>>(g, R, B.g32, u, 1, 1, f.f, f.ld, f.off);
-  H->trace.end(kFinish, st);
+  // the sweeps write their FP32 results straight into u (interior points from the leaf solve,
+  // shared-edge points from the merges; the outer boundary is f, set above)
+  if (int e = sweep32(H, B, ops, o32, R, c, Rsave, nullptr, UOut{u, 1}, st)) return e;
   for (int it = 0; it < refine; ++it) {
     if (int e = residual(H, B, R, u, Rb, gdt, st)) return e;
     H->trace.begin(kSetBoundary, st);
-    k_b_set_boundary32<<<blocks(g.N_bd * R), 256, 0, st>>>(g, R, B.g32, nullptr, 0, 0);
+    k_b_set_boundary32<<<blocks(g.N_bd * R), 256, 0, st>>>(g, R, B.g32, nullptr, 0, 0, nullptr);
     H->trace.end(kSetBoundary, st);
     Combo cr{};
     cr.n = 1;
     cr.ptr[0] = B.r;
     cr.coef[0] = 1.0;
-    if (int e = sweep32(H, B, ops, o32, R, cr, nullptr, B.r, st)) return e;
-    H->trace.begin(kFinish, st);
-    k_b_finish<<<blocks(g.N * R), 256, 0, st>>>(g, R, B.g32, u, 0, 1, nullptr, 0, 0);
-    H->trace.end(kFinish, st);
+    if (int e = sweep32(H, B, ops, o32, R, cr, nullptr, B.r, UOut{u, 0}, st)) return e;
   }
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
@@ -1691,7 +1725,7 @@ void group_cols(int R, int G, int gi, int &c0, int &n) {
 // One ARK step of one group: u is [N][R] (the group's own buffer or the caller's), q / f are
 // stage-major with leading dimensions qld / fld and the group's columns from qoff / foff.
 int ark_group(hps_handle *H, BatchWork &B, int R, double *u, double dt, const hps_ark_terms *terms, int qld, int qoff,
-              int fld, int foff, int refine, const ArkTable &tb, cudaStream_t st) {
+              int fld, int foff, int refine, const ArkTable &tb, cudaStream_t st, cudaEvent_t after_first = nullptr) {
   const GridDims &g = H->g;
   const int64_t ni = g.N_int * R;
   const double *q = terms ? terms->q : nullptr;
@@ -1712,6 +1746,7 @@ int ark_group(hps_handle *H, BatchWork &B, int R, double *u, double dt, const hp
   E.gp0 = gp0;
   E.gp1 = gp1;
   if (int e = leaf64(H, E, st)) return e;
+  if (after_first) cudaEventRecord(after_first, st);
   for (int i = 1; i < 6; ++i) {
     Combo c{};
     add_term_b(c, u, 1.0);
@@ -1779,8 +1814,10 @@ void batch_release(hps_handle *H) {
   for (BatchWork &W : Bt.work) {
     if (W.stream) cudaStreamDestroy(W.stream);
     if (W.done) cudaEventDestroy(W.done);
+    if (W.first) cudaEventDestroy(W.first);
     W.stream = nullptr;
     W.done = nullptr;
+    W.first = nullptr;
   }
   if (Bt.fork) cudaEventDestroy(Bt.fork);
   Bt.fork = nullptr;
@@ -1799,6 +1836,8 @@ int batch_reserve(hps_handle *H, int R, int groups) {
   if (const char *s = std::getenv("HPS_FLOW_LEVELS")) Bt.flow_levels = std::max(0, std::atoi(s));
   if (const char *s = std::getenv("HPS_GEMV2")) Bt.gemv2 = std::atoi(s) != 0;
   if (const char *s = std::getenv("HPS_EVEN_ODD")) Bt.even_odd = std::atoi(s) != 0;
+  if (const char *s = std::getenv("HPS_LEAF_SPLIT")) Bt.leaf_split = std::atoi(s) != 0;
+  if (const char *s = std::getenv("HPS_OFFSET_GROUPS")) Bt.offset_groups = std::atoi(s) != 0;
   if (const char *s = std::getenv("HPS_FLOW_N3_MAX")) Bt.flow_n3_max = std::max(0, std::atoi(s));
   // (re)allocate the work vectors; old ones stay in the handle's list until hps_free
   const GridDims &g = H->g;
@@ -1819,13 +1858,14 @@ int batch_reserve(hps_handle *H, int R, int groups) {
     if (Rg == 0) continue;
     if (groups > 1) {
       if (cudaStreamCreateWithFlags(&W.stream, cudaStreamNonBlocking) != cudaSuccess ||
-          cudaEventCreateWithFlags(&W.done, cudaEventDisableTiming) != cudaSuccess)
+          cudaEventCreateWithFlags(&W.done, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&W.first, cudaEventDisableTiming) != cudaSuccess)
         return HPS_ECUDA;
       if (da(&W.u, (size_t)g.N * Rg)) return HPS_ENOMEM;
     }
     if (da(&W.ustage, (size_t)g.N * Rg) || da(&W.Rb, (size_t)g.N_int * Rg) || da(&W.KL, 6 * (size_t)g.N_int * Rg) ||
         da(&W.KE, 6 * (size_t)g.N_int * Rg) || da(&W.r, (size_t)g.N * Rg) || da(&W.g32, (size_t)g.N * Rg) ||
-        da(&W.w32, (size_t)g.N_int * Rg))
+        da(&W.w32, (size_t)g.N_int * Rg) || da(&W.r32, (size_t)g.N_int * Rg))
       return HPS_ENOMEM;
     W.h32.assign(H->L + 1, nullptr);
     W.w332.assign(H->L, nullptr);
@@ -1880,15 +1920,20 @@ int ark_batch(hps_handle *H, int R, double *u, double dt, const hps_ark_terms *t
   if (R > H->batch.Rmax) return HPS_EINVAL;
   const GridDims &g = H->g;
   const bool grouped = H->batch.groups > 1;
+  BatchWork *prev = nullptr;
   return for_groups(H, R, st, [&](BatchWork &W, int c0, int n, cudaStream_t s) -> int {
     double *uu = u;
     if (grouped) {
+      // offset the groups by one phase: this group starts when the previous one has finished its
+      // explicit first stage (FP64-bound), so FP64 and FP32 phases of different groups overlap
+      if (prev && H->batch.offset_groups) cudaStreamWaitEvent(s, prev->first, 0);
       H->trace.begin(kFinish, s);
       k_cols<<<blocks(g.N * n), 256, 0, s>>>(u, R, c0, W.u, n, 0, g.N, n);
       H->trace.end(kFinish, s);
       uu = W.u;
     }
-    if (int e = ark_group(H, W, n, uu, dt, terms, R, c0, R, c0, refine, tb, s)) return e;
+    if (int e = ark_group(H, W, n, uu, dt, terms, R, c0, R, c0, refine, tb, s, grouped ? W.first : nullptr)) return e;
+    prev = &W;
     if (grouped) {
       H->trace.begin(kFinish, s);
       k_cols<<<blocks(g.N * n), 256, 0, s>>>(W.u, n, 0, u, R, c0, g.N, n);

@@ -138,7 +138,7 @@ struct BatchWork {
   int Rmax = 0;
   double *u = nullptr;  // the group's columns of the caller's u (grouped calls only)
   double *ustage = nullptr, *Rb = nullptr, *KL = nullptr, *KE = nullptr, *r = nullptr;  // FP64
-  float *g32 = nullptr, *w32 = nullptr;
+  float *g32 = nullptr, *w32 = nullptr, *r32 = nullptr;
   std::vector<float *> h32, w332;  // per level
   float *partial32 = nullptr;
   size_t partial_len = 0;          // floats
@@ -146,6 +146,7 @@ struct BatchWork {
   size_t flow_len = 0;
   cudaStream_t stream = nullptr;   // grouped calls: the group's own stream
   cudaEvent_t done = nullptr;
+  cudaEvent_t first = nullptr;     // grouped ARK steps: the explicit first stage is done
 };
 
 // The batched path: FP32 operator copies (shared by all groups) and G column groups.  With
@@ -159,6 +160,8 @@ struct Batch {
   int flow_n3_max = 32;      // ... those with interfaces of at most this many points
   bool gemv2 = false;        // upper merge levels: in-CTA + cluster split-K (else split-K partials)
   bool even_odd = true;      // FP64 leaf kernels by the even-odd decomposition (even p)
+  bool leaf_split = false;   // stage right-hand side as its own streaming pass before the leaf apply
+  bool offset_groups = true; // grouped ARK steps: each group starts one phase after the previous
   OpSet32 impl32, ident32;
   std::vector<BatchWork> work;
   cudaEvent_t fork = nullptr;
