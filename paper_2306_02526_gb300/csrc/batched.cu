@@ -304,6 +304,167 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_down(GridDims g, int R, const in
     u_out(uo, l0 * R + idx, w32[(int64_t)k * q * R + idx] + (identity ? 0.f : Os[(idx / R) * Rp + idx % R]));
 }
 
+// ---- leaf apply on the tensor cores: 3xTF32 warp MMA (m16n8k8) -----------------------------
+// W = A_ii^{-1} R with the shared operator: each FP32 operand x is split into two TF32 numbers
+// x = hi + lo (hi = x rounded to TF32, lo = x - hi rounded to TF32) and the product is formed as
+// A_lo B_hi + A_hi B_lo + A_hi B_hi with FP32 accumulation (the dropped A_lo B_lo is below FP32
+// rounding), i.e. FP32 accuracy at tensor-core rate.  The operator's hi / lo fragments are laid
+// out once in lane order (k_frag_a); the right-hand side is split while it is staged.
+// Fragment layouts of mma.m16n8k8 with .tf32 operands (g = lane / 4, t = lane % 4):
+//   A 16x8 row-major: a0 (g, t), a1 (g + 8, t), a2 (g, t + 4), a3 (g + 8, t + 4)
+//   B 8x8:            b0 (k = t, n = g), b1 (k = t + 4, n = g)
+//   C 16x8 FP32:      c0 (g, 2t), c1 (g, 2t + 1), c2 (g + 8, 2t), c3 (g + 8, 2t + 1)
+constexpr int kTcMaxMT = 16;  // row tiles of 16 (q <= 256)
+constexpr int kTcMaxNT = 4;   // column tiles of 8 (R <= 32)
+__host__ __device__ inline int tc_rs(int Rp) { return Rp + (Rp % 16 == 0 ? 8 : 0); }
+
+__device__ __forceinline__ unsigned tf32_rna(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint4 &a, unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
+}
+
+// hi / lo TF32 fragments of the q x q operator (stored transposed: A(r, c) at AT[c ld + r]),
+// tile (mt, kt), lane l, register i at ((mt KT + kt) 32 + l) 4 + i; zero outside q x q.
+__global__ void k_frag_a(const float *__restrict__ AT, int ld, int q, int MT, int KT, unsigned *__restrict__ hi,
+                         unsigned *__restrict__ lo) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)MT * KT * 128) return;
+  const int i = (int)(idx % 4), lane = (int)(idx / 4 % 32);
+  const int64_t tile = idx / 128;
+  const int mt = (int)(tile / KT), kt = (int)(tile % KT);
+  const int g = lane / 4, t = lane % 4;
+  const int r = mt * 16 + g + (i & 1) * 8, c = kt * 8 + t + (i >> 1) * 4;
+  const float v = (r < q && c < q) ? AT[(int64_t)c * ld + r] : 0.f;
+  const unsigned h = tf32_rna(v);
+  hi[idx] = h;
+  lo[idx] = tf32_rna(v - __uint_as_float(h));
+}
+
+// One leaf per CTA (8 warps; warp w takes row tiles w, w + 8).  Shared memory: the right-hand
+// side as TF32 hi / lo [KT*8][RS] (RS = 8 or 24 mod 32 keeps the B-fragment reads conflict-free), then
+// W [q][Rp] in the hi buffer, and the differentiation rows for the fluxes.
+template <int NT>
+__global__ void __launch_bounds__(kBT) k_b_leaf_up_tc(GridDims g, int R, const int *__restrict__ origin, Combo rhs,
+                                                      double *__restrict__ Rsave, const uint4 *__restrict__ Ahi,
+                                                      const uint4 *__restrict__ Alo, int MT, int KT,
+                                                      const double *__restrict__ Dg, float *__restrict__ w32,
+                                                      float *__restrict__ h32) {
+  extern __shared__ __align__(16) float smt[];
+  const int p = g.p, m = g.m, q = m * m, b = 4 * m, Rp = NT * 8, RS = tc_rs(Rp);
+  float *D1x = smt, *D1y = smt + p * p;
+  unsigned *Bh = reinterpret_cast<unsigned *>(smt + round4(2 * p * p)), *Bl = Bh + KT * 8 * RS;
+  float *Ws = reinterpret_cast<float *>(Bh);  // [q][Rp] after the products
+  const int k = blockIdx.x;
+  const int64_t l0 = ((int64_t)origin[2 * k + 1] * g.n1 + origin[2 * k]) * q;
+  for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) smt[i] = (float)Dg[i];
+  for (int i = threadIdx.x; i < (KT * 8 - q) * RS; i += blockDim.x) {  // padding rows of K
+    Bh[q * RS + i] = 0u;
+    Bl[q * RS + i] = 0u;
+  }
+  if (R != Rp)  // padding columns
+    for (int i = threadIdx.x; i < q * RS; i += blockDim.x) {
+      Bh[i] = 0u;
+      Bl[i] = 0u;
+    }
+  __syncthreads();
+  // stage right-hand side (FP64 combination, saved if requested), split into TF32 hi / lo
+  constexpr int U = 8;
+  const int nq = q * R;
+  for (int base = threadIdx.x; base < nq; base += U * blockDim.x) {
+    double acc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] = 0.0;
+    for (int t = 0; t < rhs.n; t += 2) {
+      const bool two = t + 1 < rhs.n;
+      const double *s0 = rhs.ptr[t] + l0 * R, *s1 = two ? rhs.ptr[t + 1] + l0 * R : s0;
+      const double c0 = rhs.coef[t], c1 = two ? rhs.coef[t + 1] : 0.0;
+      double v0[U], v1[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = base + u * blockDim.x;
+        v0[u] = idx < nq ? s0[idx] : 0.0;
+        v1[u] = idx < nq ? s1[idx] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc[u] = fma(c1, v1[u], fma(c0, v0[u], acc[u]));
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx < nq) {
+        if (Rsave) Rsave[l0 * R + idx] = acc[u];
+        const float v = (float)acc[u];
+        const unsigned h = tf32_rna(v);
+        const int o = (idx / R) * RS + idx % R;
+        Bh[o] = h;
+        Bl[o] = tf32_rna(v - __uint_as_float(h));
+      }
+    }
+  }
+  __syncthreads();
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, gq = lane / 4, tq = lane % 4;
+  float acc[2][NT][4];
+#pragma unroll
+  for (int s = 0; s < 2; ++s)
+#pragma unroll
+    for (int n = 0; n < NT; ++n)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[s][n][e] = 0.f;
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int mt = warp + 8 * s;
+    if (mt >= MT) break;
+    for (int kt = 0; kt < KT; ++kt) {
+      const uint4 ah = __ldg(Ahi + ((int64_t)mt * KT + kt) * 32 + lane);
+      const uint4 al = __ldg(Alo + ((int64_t)mt * KT + kt) * 32 + lane);
+      const int r0 = (kt * 8 + tq) * RS + gq, r1 = r0 + 4 * RS;
+#pragma unroll
+      for (int n = 0; n < NT; ++n) {
+        const unsigned bh0 = Bh[r0 + 8 * n], bh1 = Bh[r1 + 8 * n], bl0 = Bl[r0 + 8 * n], bl1 = Bl[r1 + 8 * n];
+        mma_tf32(acc[s][n], al, bh0, bh1);
+        mma_tf32(acc[s][n], ah, bl0, bl1);
+        mma_tf32(acc[s][n], ah, bh0, bh1);
+      }
+    }
+  }
+  __syncthreads();  // every warp is done with the staged right-hand side
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int mt = warp + 8 * s;
+    if (mt >= MT) break;
+#pragma unroll
+    for (int n = 0; n < NT; ++n) {
+      const int r = mt * 16 + gq, c = n * 8 + 2 * tq;
+      if (r < q) {
+        Ws[r * Rp + c] = acc[s][n][0];
+        Ws[r * Rp + c + 1] = acc[s][n][1];
+      }
+      if (r + 8 < q) {
+        Ws[(r + 8) * Rp + c] = acc[s][n][2];
+        Ws[(r + 8) * Rp + c + 1] = acc[s][n][3];
+      }
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < q * R; idx += blockDim.x) {
+    const int r = idx / R, j = idx % R;
+    w32[((int64_t)k * q + r) * R + j] = Ws[r * Rp + j];
+  }
+  for (int idx = threadIdx.x; idx < b * R; idx += blockDim.x) {
+    const int e = idx / R, j = idx % R;
+    h32[((int64_t)k * b + e) * R + j] = flux32(e, j, Rp, Ws, D1x, D1y, p, m);
+  }
+}
+
 // Shared leaf operator, persistent CTAs: S_leaf^T is copied to shared memory once per CTA and
 // every leaf the CTA takes is applied from there (a per-leaf CTA re-reads it from L1/L2).
 template <int TC>
@@ -1422,7 +1583,7 @@ int flow_launch(hps_handle *H, BatchWork &B, const FlowArgs &FA, bool up, size_t
 // One FP32 sweep on R columns: leaf applies, merges up (with an optional FP64 interface
 // right-hand side), merges down into g32 (whose outer boundary the caller has set), leaf solves.
 int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, int R, const Combo &rhs,
-            double *Rsave, const double *jump, UOut uo, cudaStream_t st) {
+            double *Rsave, const double *jump, UOut uo, bool allow_tc, cudaStream_t st) {
   const int L = H->L, p = H->p, q = H->q, b = H->b, Rp = round4(R);
   const Level &leaf = H->lev[L];
   const bool tc8 = Rp % 8 == 0;
@@ -1438,6 +1599,23 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
     H->trace.begin(kLeafUp, st);
     k_b_leaf_up_narrow<<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, o32.Ainv.p, o32.Ainv.ld,
                                                       o32.Ainv.str, ops.identity ? 1 : 0, H->d_D, B.w32, B.h32[L]);
+    H->trace.end(kLeafUp, st);
+  } else if (allow_tc && H->batch.afrag_hi && H->batch.tensor_leaf && H->shared && !ops.identity && Rp % 8 == 0 &&
+             Rp / 8 <= kTcMaxNT &&
+             !H->batch.leaf_split) {
+    const int MT = (q + 15) / 16, KT = (q + 7) / 8, NT = Rp / 8;
+    const size_t smem = (size_t)(round4(2 * p * p) + 2 * KT * 8 * tc_rs(Rp)) * sizeof(float);
+    auto kern = NT == 4 ? k_b_leaf_up_tc<4> : NT == 3 ? k_b_leaf_up_tc<3> : NT == 2 ? k_b_leaf_up_tc<2>
+                                                                                   : k_b_leaf_up_tc<1>;
+    static size_t set[5] = {0, 0, 0, 0, 0};
+    if (smem > 48 * 1024 && smem > set[NT]) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      set[NT] = smem;
+    }
+    H->trace.begin(kLeafUp, st);
+    kern<<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, reinterpret_cast<const uint4 *>(H->batch.afrag_hi),
+                                        reinterpret_cast<const uint4 *>(H->batch.afrag_lo), MT, KT, H->d_D, B.w32,
+                                        B.h32[L]);
     H->trace.end(kLeafUp, st);
   } else {
     const size_t smem = (size_t)(round4(2 * p * p) + 2 * q * Rp) * sizeof(float);
@@ -1681,7 +1859,10 @@ int refined_solve(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &
   H->trace.end(kSetBoundary, st);
   // the sweeps write their FP32 results straight into u (interior points from the leaf solve,
   // shared-edge points from the merges; the outer boundary is f, set above)
-  if (int e = sweep32(H, B, ops, o32, R, c, Rsave, nullptr, UOut{u, 1}, st)) return e;
+  // the first sweep may take the 3xTF32 tensor-core leaf apply (its rounding is slightly coarser
+  // than FP32 and biased); corrections use the FP32 FMA path, so the refined result keeps FP32
+  // times FP32 accuracy
+  if (int e = sweep32(H, B, ops, o32, R, c, Rsave, nullptr, UOut{u, 1}, true, st)) return e;
   for (int it = 0; it < refine; ++it) {
     if (int e = residual(H, B, R, u, Rb, gdt, st)) return e;
     H->trace.begin(kSetBoundary, st);
@@ -1691,7 +1872,7 @@ int refined_solve(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &
     cr.n = 1;
     cr.ptr[0] = B.r;
     cr.coef[0] = 1.0;
-    if (int e = sweep32(H, B, ops, o32, R, cr, nullptr, B.r, UOut{u, 0}, st)) return e;
+    if (int e = sweep32(H, B, ops, o32, R, cr, nullptr, B.r, UOut{u, 0}, false, st)) return e;
   }
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
@@ -1831,6 +2012,16 @@ int batch_reserve(hps_handle *H, int R, int groups) {
   if (Bt.impl32.X.empty()) {  // FP32 operator copies (once)
     if (int e = convert_opset(H, H->impl, Bt.impl32, H->shared)) return e;
     if (int e = convert_opset(H, H->ident, Bt.ident32, true)) return e;
+    const int q = H->q, MT = (q + 15) / 16, KT = (q + 7) / 8;
+    if (H->shared && MT <= kTcMaxMT && Bt.impl32.Ainv.p) {  // TF32 hi / lo fragments of the leaf operator
+      const size_t n = (size_t)MT * KT * 128;
+      if (cudaMalloc(&Bt.afrag_hi, n * sizeof(unsigned)) != cudaSuccess ||
+          cudaMalloc(&Bt.afrag_lo, n * sizeof(unsigned)) != cudaSuccess)
+        return HPS_ENOMEM;
+      H->allocs.push_back(Bt.afrag_hi);
+      H->allocs.push_back(Bt.afrag_lo);
+      k_frag_a<<<blocks((int64_t)n), 256>>>(Bt.impl32.Ainv.p, Bt.impl32.Ainv.ld, q, MT, KT, Bt.afrag_hi, Bt.afrag_lo);
+    }
   }
   if (const char *s = std::getenv("HPS_FP64_CTAS_PER_SM")) Bt.fp64_ctas_per_sm = std::max(0, std::atoi(s));
   if (const char *s = std::getenv("HPS_FLOW_LEVELS")) Bt.flow_levels = std::max(0, std::atoi(s));
@@ -1838,6 +2029,7 @@ int batch_reserve(hps_handle *H, int R, int groups) {
   if (const char *s = std::getenv("HPS_EVEN_ODD")) Bt.even_odd = std::atoi(s) != 0;
   if (const char *s = std::getenv("HPS_LEAF_SPLIT")) Bt.leaf_split = std::atoi(s) != 0;
   if (const char *s = std::getenv("HPS_OFFSET_GROUPS")) Bt.offset_groups = std::atoi(s) != 0;
+  if (const char *s = std::getenv("HPS_TENSOR_LEAF")) Bt.tensor_leaf = std::atoi(s) != 0;
   if (const char *s = std::getenv("HPS_FLOW_N3_MAX")) Bt.flow_n3_max = std::max(0, std::atoi(s));
   // (re)allocate the work vectors; old ones stay in the handle's list until hps_free
   const GridDims &g = H->g;

@@ -162,6 +162,8 @@ struct Batch {
   bool even_odd = true;      // FP64 leaf kernels by the even-odd decomposition (even p)
   bool leaf_split = false;   // stage right-hand side as its own streaming pass before the leaf apply
   bool offset_groups = true; // grouped ARK steps: each group starts one phase after the previous
+  bool tensor_leaf = true;   // shared leaf operator applied by 3xTF32 warp MMA (else FP32 FFMA)
+  unsigned *afrag_hi = nullptr, *afrag_lo = nullptr;  // its TF32 fragments
   OpSet32 impl32, ident32;
   std::vector<BatchWork> work;
   cudaEvent_t fork = nullptr;
