@@ -127,18 +127,76 @@ __device__ __forceinline__ void stage_combo(const Combo &rhs, int64_t off, int n
   }
 }
 
-// flux (D_bi w)_e of column j of an interior field W[node*Rp + j] (float)
-__device__ float flux32(int e, int j, int Rp, const float *W, const float *D1x, const float *D1y, int p, int m) {
-  const int side = e / m, t = e % m;
-  float s = 0.f;
-  if (side == 0 || side == 2) {
-    const float *d = D1y + (side == 0 ? 0 : (p - 1) * p);
-    for (int jj = 1; jj <= m; ++jj) s = fmaf(d[jj], W[((jj - 1) * m + t) * Rp + j], s);
-  } else {
-    const float *d = D1x + (side == 1 ? (p - 1) * p : 0);
-    for (int ii = 1; ii <= m; ++ii) s = fmaf(d[ii], W[(t * m + ii - 1) * Rp + j], s);
+
+// 4 columns (j0 .. j0+3) of the flux of edge point e: float4 reads of the interior field.
+__device__ __forceinline__ float4 flux4(int e, int j0, int Rp, const float *W, const float *D1x, const float *D1y,
+                                        int p, int m) {
+  const int side = e / m, t = e - side * m;
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+  const float *d;
+  int base, step;
+  if (side == 0 || side == 2) {  // horizontal edge: d/dy along column t
+    d = D1y + (side == 0 ? 0 : (p - 1) * p);
+    base = t;
+    step = m;
+  } else {  // vertical edge: d/dx along row t
+    d = D1x + (side == 1 ? (p - 1) * p : 0);
+    base = t * m;
+    step = 1;
+  }
+  for (int jj = 1; jj <= m; ++jj) {
+    const float dv = d[jj];
+    const float4 w = *reinterpret_cast<const float4 *>(W + (base + (jj - 1) * step) * Rp + j0);
+    s.x = fmaf(dv, w.x, s.x);
+    s.y = fmaf(dv, w.y, s.y);
+    s.z = fmaf(dv, w.z, s.z);
+    s.w = fmaf(dv, w.w, s.w);
   }
   return s;
+}
+
+// Outputs of a leaf apply from the interior field W [q][Rp] in shared memory: w32 (the field)
+// and h32 (its fluxes on the b edge points), four columns per thread step.
+__device__ __forceinline__ void leaf_up_out(int64_t k, int q, int b, int R, int Rp, const float *Ws, const float *D1x,
+                                            const float *D1y, int p, int m, float *__restrict__ w32,
+                                            float *__restrict__ h32) {
+  const int Rq = Rp / 4;
+  if (R == Rp) {
+    float4 *wo = reinterpret_cast<float4 *>(w32 + k * q * R);
+    for (int i = threadIdx.x; i < q * Rq; i += blockDim.x) wo[i] = reinterpret_cast<const float4 *>(Ws)[i];
+  } else {
+    for (int idx = threadIdx.x; idx < q * R; idx += blockDim.x) {
+      const int r = idx / R, j = idx - r * R;
+      w32[(k * q + r) * R + j] = Ws[r * Rp + j];
+    }
+  }
+  for (int i = threadIdx.x; i < b * Rq; i += blockDim.x) {
+    const int e = i / Rq, j0 = 4 * (i - e * Rq);
+    const float4 f = flux4(e, j0, Rp, Ws, D1x, D1y, p, m);
+    float *o = h32 + (k * b + e) * R + j0;
+    if (R == Rp) {
+      *reinterpret_cast<float4 *>(o) = f;
+    } else {
+      const float fv[4] = {f.x, f.y, f.z, f.w};
+      for (int t = 0; t < 4 && j0 + t < R; ++t) o[t] = fv[t];
+    }
+  }
+}
+
+// The boundary values of box (ix, iy, a x c) for R columns into ub [nb][Rp] (zero padding):
+// the global index of each boundary position is computed once per four columns.
+template <int U = 4>
+__device__ __forceinline__ void gather_box(const GridDims &g, int ix, int iy, int a, int c, int nb, int R, int Rp,
+                                           const float *__restrict__ src, float *ub) {
+  const int Rq = Rp / 4;
+  block_gather<U, float4>(
+      nb * Rq,
+      [&](int i) {
+        const int pos = i / Rq, j0 = 4 * (i - pos * Rq);
+        const float *p = src + box_bd(g, ix, iy, a, c, pos) * R + j0;
+        return make_float4(p[0], j0 + 1 < R ? p[1] : 0.f, j0 + 2 < R ? p[2] : 0.f, j0 + 3 < R ? p[3] : 0.f);
+      },
+      [&](int i, float4 v) { reinterpret_cast<float4 *>(ub)[i] = v; });
 }
 
 // ---- leaf applies (FP32, R columns) ------------------------------------------------------
@@ -239,14 +297,7 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_up(GridDims g, int R, const int 
         for (int t = 0; t < TC; ++t) Ws[(r0 + e) * Rp + j0 + t] = acc[e][t];
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < q * R; idx += blockDim.x) {
-    const int r = idx / R, j = idx % R;
-    w32[((int64_t)k * q + r) * R + j] = Ws[r * Rp + j];
-  }
-  for (int idx = threadIdx.x; idx < b * R; idx += blockDim.x) {
-    const int e = idx / R, j = idx % R;
-    h32[((int64_t)k * b + e) * R + j] = flux32(e, j, Rp, Ws, D1x, D1y, p, m);
-  }
+  leaf_up_out(k, q, b, R, Rp, Ws, D1x, D1y, p, m, w32, h32);
 }
 
 template <int TC>
@@ -261,13 +312,7 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_down(GridDims g, int R, const in
   const int64_t l0 = ((int64_t)iy * g.n1 + ix) * q;
   float *Os = ub + b * Rp;
   if (!identity) {
-    block_gather<8, float>(
-        b * Rp,
-        [&](int idx) {
-          const int e = idx / Rp, j = idx % Rp;
-          return j < R ? g32[box_bd(g, ix, iy, 1, 1, e) * R + j] : 0.f;
-        },
-        [&](int idx, float v) { ub[idx] = v; });
+    gather_box<2>(g, ix, iy, 1, 1, b, R, Rp, g32, ub);
     __syncthreads();
     const int QQ = (q + 3) / 4, CG = Rp / TC;
     for (int it = threadIdx.x; it < QQ * CG; it += blockDim.x) {
@@ -455,14 +500,7 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_up_tc(GridDims g, int R, const i
     }
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < q * R; idx += blockDim.x) {
-    const int r = idx / R, j = idx % R;
-    w32[((int64_t)k * q + r) * R + j] = Ws[r * Rp + j];
-  }
-  for (int idx = threadIdx.x; idx < b * R; idx += blockDim.x) {
-    const int e = idx / R, j = idx % R;
-    h32[((int64_t)k * b + e) * R + j] = flux32(e, j, Rp, Ws, D1x, D1y, p, m);
-  }
+  leaf_up_out(k, q, b, R, Rp, Ws, D1x, D1y, p, m, w32, h32);
 }
 
 // Shared leaf operator, persistent CTAs: S_leaf^T is copied to shared memory once per CTA and
@@ -482,13 +520,7 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_down_res(GridDims g, int nodes, 
     const int ix = origin[2 * k], iy = origin[2 * k + 1];
     const int64_t l0 = ((int64_t)iy * g.n1 + ix) * q;
     __syncthreads();  // previous leaf done with ub; operator copy visible
-    block_gather<8, float>(
-        b * Rp,
-        [&](int idx) {
-          const int e = idx / Rp, j = idx % Rp;
-          return j < R ? g32[box_bd(g, ix, iy, 1, 1, e) * R + j] : 0.f;
-        },
-        [&](int idx, float v) { ub[idx] = v; });
+    gather_box<2>(g, ix, iy, 1, 1, b, R, Rp, g32, ub);
     __syncthreads();
     for (int it = threadIdx.x; it < QQ * CG; it += blockDim.x) {
       const int r0 = 4 * (it % QQ), j0 = TC * (it / QQ);
@@ -564,14 +596,7 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_up_narrow(GridDims g, int R, con
     }
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < q * R; idx += blockDim.x) {
-    const int r = idx / R, j = idx % R;
-    w32[((int64_t)k * q + r) * R + j] = Ws[r * 4 + j];
-  }
-  for (int idx = threadIdx.x; idx < b * R; idx += blockDim.x) {
-    const int e = idx / R, j = idx % R;
-    h32[((int64_t)k * b + e) * R + j] = flux32(e, j, 4, Ws, D1x, D1y, p, m);
-  }
+  leaf_up_out(k, q, b, R, 4, Ws, D1x, D1y, p, m, w32, h32);
 }
 
 __global__ void __launch_bounds__(kBT) k_b_leaf_down_narrow(GridDims g, int R, const int *__restrict__ origin,
@@ -584,13 +609,7 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_down_narrow(GridDims g, int R, c
   const int k = blockIdx.x;
   const int ix = origin[2 * k], iy = origin[2 * k + 1];
   const int64_t l0 = ((int64_t)iy * g.n1 + ix) * q;
-  block_gather<4, float>(
-      b * 4,
-      [&](int idx) {
-        const int e = idx / 4, j = idx % 4;
-        return j < R ? g32[box_bd(g, ix, iy, 1, 1, e) * R + j] : 0.f;
-      },
-      [&](int idx, float v) { ub[idx] = v; });
+  gather_box(g, ix, iy, 1, 1, b, R, 4, g32, ub);
   __syncthreads();
   if (!identity) quad_apply_sliced(SlT + (int64_t)k * strS, ldS, b, ub, 4, QQ, KS, part);
   __syncthreads();
@@ -687,11 +706,29 @@ struct BXDiff {  // d = h^b_3 - h^a_3 (+ interface right-hand side)
     if (jump) v += (float)jump[iface_bd(g, origin[2 * k], origin[2 * k + 1], a, c, split, cc) * R + j];
     return v;
   }
+  __device__ float4 load4(int k, int cc, int j0) const {  // row addresses once per 4 columns
+    const float *pb = hC + ((int64_t)(2 * k + 1) * nbc + j3b + cc) * R + j0;
+    const float *pa = hC + ((int64_t)(2 * k) * nbc + j3a + cc) * R + j0;
+    float v[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) v[t] = j0 + t < R ? pb[t] - pa[t] : 0.f;
+    if (jump) {
+      const double *pj = jump + iface_bd(g, origin[2 * k], origin[2 * k + 1], a, c, split, cc) * R + j0;
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (j0 + t < R) v[t] += (float)pj[t];
+    }
+    return make_float4(v[0], v[1], v[2], v[3]);
+  }
 };
 struct BXVec {
   const float *v;
   int n, R;
   __device__ float operator()(int k, int c, int j) const { return v[((int64_t)k * n + c) * R + j]; }
+  __device__ float4 load4(int k, int c, int j0) const {
+    const float *p = v + ((int64_t)k * n + c) * R + j0;
+    return make_float4(p[0], j0 + 1 < R ? p[1] : 0.f, j0 + 2 < R ? p[2] : 0.f, j0 + 3 < R ? p[3] : 0.f);
+  }
 };
 struct BXBd {
   GridDims g;
@@ -701,11 +738,22 @@ struct BXBd {
   __device__ float operator()(int k, int pos, int j) const {
     return gv[box_bd(g, origin[2 * k], origin[2 * k + 1], a, c, pos) * R + j];
   }
+  __device__ float4 load4(int k, int pos, int j0) const {
+    const float *p = gv + box_bd(g, origin[2 * k], origin[2 * k + 1], a, c, pos) * R + j0;
+    return make_float4(p[0], j0 + 1 < R ? p[1] : 0.f, j0 + 2 < R ? p[2] : 0.f, j0 + 3 < R ? p[3] : 0.f);
+  }
 };
 struct BEStore {
   float *out;
   int n, R;
   __device__ void operator()(int k, int r, int j, float v) const { out[((int64_t)k * n + r) * R + j] = v; }
+  template <int TC>
+  __device__ void row(int k, int r, int j0, const float (&v)[TC]) const {
+    float *o = out + ((int64_t)k * n + r) * R + j0;
+#pragma unroll
+    for (int t = 0; t < TC; ++t)
+      if (j0 + t < R) o[t] = v[t];
+  }
 };
 struct BEFlux {
   const int *hsrc;
@@ -714,6 +762,14 @@ struct BEFlux {
   float *h;
   __device__ void operator()(int k, int r, int j, float v) const {
     h[((int64_t)k * nb + r) * R + j] = hC[((int64_t)(2 * k) * nbc + hsrc[r]) * R + j] + v;
+  }
+  template <int TC>
+  __device__ void row(int k, int r, int j0, const float (&v)[TC]) const {
+    const float *src = hC + ((int64_t)(2 * k) * nbc + hsrc[r]) * R + j0;
+    float *o = h + ((int64_t)k * nb + r) * R + j0;
+#pragma unroll
+    for (int t = 0; t < TC; ++t)
+      if (j0 + t < R) o[t] = src[t] + v[t];
   }
 };
 struct BEScatter {  // interface values: FP32 for the levels below, and into the FP64 solution
@@ -728,6 +784,18 @@ struct BEScatter {  // interface values: FP32 for the levels below, and into the
     const float x = v + w3[((int64_t)k * n3 + r) * R + j];
     gv[i] = x;
     u_out(uo, i, x);
+  }
+  template <int TC>
+  __device__ void row(int k, int r, int j0, const float (&v)[TC]) const {
+    const int64_t i0 = iface_bd(g, origin[2 * k], origin[2 * k + 1], a, c, split, r) * R + j0;
+    const float *w = w3 + ((int64_t)k * n3 + r) * R + j0;
+#pragma unroll
+    for (int t = 0; t < TC; ++t)
+      if (j0 + t < R) {
+        const float x = v[t] + w[t];
+        gv[i0 + t] = x;
+        u_out(uo, i0 + t, x);
+      }
   }
 };
 
@@ -752,13 +820,19 @@ __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict
                  AT + (int64_t)(node0 + t) * str + (int64_t)(c0 + c) * ld + rlo + 4 * qq);
     }
   }
-  block_gather<8, float>(
-      nn * klen * Rp,
-      [&](int idx) {
-        const int lo = idx / (klen * Rp), rem = idx % (klen * Rp), c = rem / Rp, j = rem % Rp;
-        return j < P.R ? xl(node0 + lo, c0 + c, j) : 0.f;
-      },
-      [&](int idx, float v) { xs[idx] = v; });
+  {  // vector chunk [nn][klen][Rp], four columns per load (row addresses once per 4 columns)
+    const int Rq = Rp / 4, n4 = nn * klen * Rq;
+    const bool pow2 = (Rq & (Rq - 1)) == 0;
+    const int sh = __ffs(Rq) - 1;
+    block_gather<4, float4>(
+        n4,
+        [&](int t) {
+          const int row = pow2 ? t >> sh : t / Rq, j0 = 4 * (pow2 ? t & (Rq - 1) : t % Rq);
+          const int lo = row / klen, c = row - lo * klen;
+          return xl.load4(node0 + lo, c0 + c, j0);
+        },
+        [&](int t, float4 v) { reinterpret_cast<float4 *>(xs)[t] = v; });
+  }
   cp_async_wait_all();
   __syncthreads();
   int lo, rq, cg;
@@ -790,9 +864,7 @@ __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict
     const int r = r0 + e;
     if (r >= P.M) continue;
     if (P.ksplit == 1) {
-#pragma unroll
-      for (int t = 0; t < TC; ++t)
-        if (j0 + t < P.R) ep(k, r, j0 + t, acc[e][t]);
+      ep.template row<TC>(k, r, j0, acc[e]);
     } else {
       float *dst = partial + (((int64_t)ks * P.nodes + k) * P.M + r) * Rp + j0;
 #pragma unroll
@@ -802,17 +874,25 @@ __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict
   }
 }
 
+// Sum of the split-K partials in chunk order, four columns per thread.
 template <class EP>
 __global__ void k_b_reduce(BPlan P, const float *__restrict__ partial, EP ep) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)P.nodes * P.M * P.R) return;
-  const int j = (int)(idx % P.R);
-  const int64_t kr = idx / P.R;
-  const int r = (int)(kr % P.M), k = (int)(kr / P.M);
-  float s = 0.f;
+  const int Rq = P.Rp / 4;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.nodes * P.M * Rq) return;
+  const int row = i / Rq, j0 = 4 * (i - row * Rq), k = row / P.M, r = row - k * P.M;
+  float v[4] = {0.f, 0.f, 0.f, 0.f};
+  const int64_t stride = (int64_t)P.nodes * P.M * P.Rp;
+  const float *src = partial + (int64_t)row * P.Rp + j0;
 #pragma unroll 8
-  for (int ks = 0; ks < P.ksplit; ++ks) s += partial[(((int64_t)ks * P.nodes + k) * P.M + r) * P.Rp + j];
-  ep(k, r, j, s);
+  for (int ks = 0; ks < P.ksplit; ++ks) {
+    const float4 x = *reinterpret_cast<const float4 *>(src + ks * stride);
+    v[0] += x.x;
+    v[1] += x.y;
+    v[2] += x.z;
+    v[3] += x.w;
+  }
+  ep.template row<4>(k, r, j0, v);
 }
 
 template <class XL, class EP>
@@ -833,7 +913,7 @@ int launch_b(hps_handle *H, BatchWork &B, int slot, const BPlan &P, const float 
   else
     k_b_gemv<4, XL, EP><<<grid, kBT, smem, st>>>(P, AT, ld, str, xl, ep, B.partial32);
   if (P.ksplit > 1) {
-    const int64_t n = (int64_t)P.nodes * P.M * P.R;
+    const int64_t n = (int64_t)P.nodes * P.M * (P.Rp / 4);
     k_b_reduce<EP><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, B.partial32, ep);
   }
   H->trace.end(slot, st);
@@ -1092,18 +1172,25 @@ __global__ void __launch_bounds__(kBT) k_b_flow_up(FlowArgs A) {
     if (t + 1 < A.nlev && !flow_wait_block(A, A.sync + 1 + A.lv[t + 1].flag0 + 2 * k, 2)) return;
     float *D = sm, *Ws = sm + L.n3 * Rp;
     // d = h^b_3 - h^a_3 (+ the interface right-hand side)
-    block_gather<4, float>(
-        L.n3 * Rp,
-        [&](int idx) {
-          const int j = idx % Rp, cc = idx / Rp;
-          if (j >= R) return 0.f;
-          float v = L.hC[((int64_t)(2 * k + 1) * L.nbc + L.j3b + cc) * R + j] -
-                    L.hC[((int64_t)(2 * k) * L.nbc + L.j3a + cc) * R + j];
-          if (A.jump)
-            v += (float)A.jump[iface_bd(A.g, L.origin[2 * k], L.origin[2 * k + 1], L.a, L.c, L.split, cc) * R + j];
-          return v;
+    block_gather<4, float4>(
+        L.n3 * CQ,
+        [&](int i) {
+          const int cc = i / CQ, j0 = 4 * (i - cc * CQ);
+          const float *pb = L.hC + ((int64_t)(2 * k + 1) * L.nbc + L.j3b + cc) * R + j0;
+          const float *pa = L.hC + ((int64_t)(2 * k) * L.nbc + L.j3a + cc) * R + j0;
+          float v[4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) v[t] = j0 + t < R ? pb[t] - pa[t] : 0.f;
+          if (A.jump) {
+            const double *pj =
+                A.jump + iface_bd(A.g, L.origin[2 * k], L.origin[2 * k + 1], L.a, L.c, L.split, cc) * R + j0;
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+              if (j0 + t < R) v[t] += (float)pj[t];
+          }
+          return make_float4(v[0], v[1], v[2], v[3]);
         },
-        [&](int idx, float v) { D[idx] = v; });
+        [&](int i, float4 v) { reinterpret_cast<float4 *>(D)[i] = v; });
     __syncthreads();
     // w3 = X d
     for (int it = threadIdx.x; it < L.n3 * CQ; it += blockDim.x) {
@@ -1146,13 +1233,7 @@ __global__ void __launch_bounds__(kBT) k_b_flow_down(FlowArgs A) {
     if (t > 0 && !flow_wait_block(A, A.sync + 1 + A.lv[t - 1].flag0 + k / 2, 1)) return;
     float *Ub = sm;
     const int ox = L.origin[2 * k], oy = L.origin[2 * k + 1];
-    block_gather<8, float>(
-        L.nb * Rp,
-        [&](int idx) {
-          const int j = idx % Rp, pos = idx / Rp;
-          return j < R ? A.g32[box_bd(A.g, ox, oy, L.a, L.c, pos) * R + j] : 0.f;
-        },
-        [&](int idx, float v) { Ub[idx] = v; });
+    gather_box(A.g, ox, oy, L.a, L.c, L.nb, R, Rp, A.g32, Ub);
     __syncthreads();
     // u3 = S u_b + w3, scattered to the interface points
     for (int it = threadIdx.x; it < L.n3 * CQ; it += blockDim.x) {
