@@ -172,7 +172,7 @@ struct Batch {
 // A kernel sequence recorded into a CUDA graph (hps_set_graph), replayed for equal arguments.
 struct GraphEntry {
   static constexpr int kKey = 8;
-  static constexpr int kEventPairs = 64;
+  static constexpr int kEventPairs = 1024;  // enough for every kernel of one batched ARK step
   bool seen = false;   // the key ran once eagerly (kernels loaded, attributes set)
   bool valid = false;  // exec holds the graph of this key
   uint64_t key[kKey] = {};
