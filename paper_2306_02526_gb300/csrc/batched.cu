@@ -1170,14 +1170,25 @@ __global__ void __launch_bounds__(kBT) k_b_flow_up(FlowArgs A) {
   while (flow_task(A, t, k)) {
     const FlowLevel &L = A.lv[t];
     if (t + 1 < A.nlev && !flow_wait_block(A, A.sync + 1 + A.lv[t + 1].flag0 + 2 * k, 2)) return;
-    float *D = sm, *Ws = sm + L.n3 * Rp;
+    // both children's h (contiguous: nodes 2k, 2k+1) in one asynchronous copy; every later read
+    // of this task is from shared memory
+    const int nch = 2 * L.nbc * R;
+    float *Hs = sm, *D = sm + round4(nch), *Ws = D + L.n3 * Rp;
+    {
+      const float *src = L.hC + (int64_t)(2 * k) * L.nbc * R;
+      if (R % 4 == 0)
+        for (int i = threadIdx.x; i < nch / 4; i += blockDim.x) cp_async16(Hs + 4 * i, src + 4 * i);
+      else
+        for (int i = threadIdx.x; i < nch; i += blockDim.x) Hs[i] = src[i];
+      cp_async_wait_all();
+    }
+    __syncthreads();
     // d = h^b_3 - h^a_3 (+ the interface right-hand side)
     block_gather<4, float4>(
         L.n3 * CQ,
         [&](int i) {
           const int cc = i / CQ, j0 = 4 * (i - cc * CQ);
-          const float *pb = L.hC + ((int64_t)(2 * k + 1) * L.nbc + L.j3b + cc) * R + j0;
-          const float *pa = L.hC + ((int64_t)(2 * k) * L.nbc + L.j3a + cc) * R + j0;
+          const float *pb = Hs + (L.nbc + L.j3b + cc) * R + j0, *pa = Hs + (L.j3a + cc) * R + j0;
           float v[4];
 #pragma unroll
           for (int t = 0; t < 4; ++t) v[t] = j0 + t < R ? pb[t] - pa[t] : 0.f;
@@ -1209,7 +1220,7 @@ __global__ void __launch_bounds__(kBT) k_b_flow_up(FlowArgs A) {
     if (L.level > 0) {
       for (int it = threadIdx.x; it < L.nb * CQ; it += blockDim.x) {
         const int r = it % L.nb, j0 = 4 * (it / L.nb);
-        const float *hc = L.hC + ((int64_t)(2 * k) * L.nbc + L.hsrc[r]) * R + j0;
+        const float *hc = Hs + L.hsrc[r] * R + j0;  // hsrc = child * nbc + position
         float4 acc = make_float4(j0 < R ? hc[0] : 0.f, j0 + 1 < R ? hc[1] : 0.f, j0 + 2 < R ? hc[2] : 0.f,
                                  j0 + 3 < R ? hc[3] : 0.f);
         flow_dot(acc, L.T + (int64_t)k * L.strT + r, L.ldT, L.n3, Ws + j0, Rp);
@@ -1231,14 +1242,22 @@ __global__ void __launch_bounds__(kBT) k_b_flow_down(FlowArgs A) {
   while (flow_task(A, t, k)) {
     const FlowLevel &L = A.lv[t];
     if (t > 0 && !flow_wait_block(A, A.sync + 1 + A.lv[t - 1].flag0 + k / 2, 1)) return;
-    float *Ub = sm;
+    float *Ub = sm, *W3 = sm + L.nb * Rp;
     const int ox = L.origin[2 * k], oy = L.origin[2 * k + 1];
+    {  // this node's w3 rows (contiguous) by asynchronous copies, overlapping the boundary gather
+      const float *src = L.w3 + (int64_t)k * L.n3 * R;
+      if (R % 4 == 0)
+        for (int i = threadIdx.x; i < L.n3 * R / 4; i += blockDim.x) cp_async16(W3 + 4 * i, src + 4 * i);
+      else
+        for (int i = threadIdx.x; i < L.n3 * R; i += blockDim.x) W3[i] = src[i];
+    }
     gather_box(A.g, ox, oy, L.a, L.c, L.nb, R, Rp, A.g32, Ub);
+    cp_async_wait_all();
     __syncthreads();
     // u3 = S u_b + w3, scattered to the interface points
     for (int it = threadIdx.x; it < L.n3 * CQ; it += blockDim.x) {
       const int r = it % L.n3, j0 = 4 * (it / L.n3);
-      const float *w = L.w3 + ((int64_t)k * L.n3 + r) * R + j0;
+      const float *w = W3 + r * R + j0;
       float4 acc = make_float4(j0 < R ? w[0] : 0.f, j0 + 1 < R ? w[1] : 0.f, j0 + 2 < R ? w[2] : 0.f,
                                j0 + 3 < R ? w[3] : 0.f);
       flow_dot(acc, L.S + (int64_t)k * L.strS + r, L.ldS, L.nb, Ub + j0, Rp);
@@ -1776,8 +1795,10 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
     FA.g32 = B.g32;
     FA.uo = uo;
     FA.limit_ns = 2000000000ull;
-    smem_up = (size_t)2 * n3max * Rp * sizeof(float);
-    smem_down = (size_t)nbmax * Rp * sizeof(float);
+    int nbcmax = 0;
+    for (int t = 0; t < nflow; ++t) nbcmax = std::max(nbcmax, FA.lv[t].nbc);
+    smem_up = ((size_t)round4(2 * nbcmax * R) + 2 * (size_t)n3max * Rp) * sizeof(float);
+    smem_down = ((size_t)nbmax * Rp + (size_t)n3max * R) * sizeof(float);
     // upward ticket order: deepest level first
     for (int s2 = 0, t = nflow - 1; t >= 0; --t, ++s2) {
       FA.seg_t[s2] = t;

@@ -156,7 +156,7 @@ struct BatchWork {
 struct Batch {
   int Rmax = 0, groups = 1;
   int fp64_ctas_per_sm = 0;  // 0: one CTA per leaf; else a persistent grid of that many per SM
-  int flow_levels = 12;      // lower merge levels run as one dataflow kernel (0: one launch per level)
+  int flow_levels = 0;       // lower merge levels run as one dataflow kernel (0: one launch per level)
   int flow_n3_max = 32;      // ... those with interfaces of at most this many points
   bool gemv2 = false;        // upper merge levels: in-CTA + cluster split-K (else split-K partials)
   bool even_odd = true;      // FP64 leaf kernels by the even-odd decomposition (even p)
