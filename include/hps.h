@@ -267,6 +267,43 @@ int hps_solve_batch(hps_handle *h, int R, const double *rhs, const double *f, do
 int ark_step_batch(hps_handle *h, int R, double *u, double t, double dt, const hps_ark_terms *terms, int refine,
                    hps_stream_t stream);
 
+/* ---- Batched-path kernel variants and their autotuner ------------------------------------
+ * Options select among kernel variants of the batched path (all compute the same result to
+ * the mixed-precision tolerance).  Setting one drops the recorded graphs of the batched calls
+ * and, for the split-K plan options, re-sizes the split-K scratch (synchronizes the device). */
+enum {
+  HPS_OPT_TENSOR_LEAF = 0,      /* 1: first sweep of a solve applies the shared leaf operator by
+                                   3xTF32 warp MMA on the tensor cores (default 1)                */
+  HPS_OPT_EVEN_ODD = 1,         /* 1: FP64 leaf kernels by the even-odd decomposition (default 1) */
+  HPS_OPT_FLOW_LEVELS = 2,      /* lowest merge levels run as one dataflow kernel (default 0)     */
+  HPS_OPT_FLOW_N3_MAX = 3,      /* ... levels whose interface has at most this many points (32)  */
+  HPS_OPT_CLUSTER_SPLITK = 4,   /* 1: upper merge levels split K over a thread-block cluster and
+                                   add the parts in distributed shared memory (default 0)        */
+  HPS_OPT_PLAN_TARGET = 5,      /* split-K plans: CTAs per SM aimed at (default 2)                */
+  HPS_OPT_PLAN_KMIN = 6,        /* split-K plans: smallest K chunk (default 32)                   */
+  HPS_OPT_PLAN_NPC_MAX = 7,     /* split-K plans: most tree nodes per CTA (default unlimited)     */
+  HPS_OPT_SPLIT_RHS = 8,        /* 1: stage right-hand side as its own pass (default 0)           */
+  HPS_OPT_FP64_CTAS_PER_SM = 9, /* FP64 leaf kernels: persistent CTAs per SM, 0: one CTA per leaf  */
+  HPS_OPT_GROUP_OFFSET = 10,    /* 1: column groups of an ARK step start one phase apart (1)     */
+  HPS_OPT_COUNT = 11
+};
+int hps_batch_set_option(hps_handle *h, int opt, int value);
+int hps_batch_get_option(hps_handle *h, int opt, int *value);
+
+/* One configuration tried by hps_batch_autotune and its time. */
+typedef struct hps_tune_result {
+  int tensor_leaf, flow_levels, plan_target, plan_kmin;
+  float ms; /* device time of one hps_solve_batch with this configuration (mean of 3) */
+} hps_tune_result;
+
+/* Times hps_solve_batch (R columns, `refine` sweeps, synthetic right-hand sides) under each
+ * candidate configuration of the options above on this handle's own operators, keeps the
+ * fastest and reports every candidate in `results` (up to max_results, count in *n_results;
+ * either may be NULL).  Needs hps_batch_reserve(R) first; allocates and frees its own test
+ * vectors; synchronizes the device. */
+int hps_batch_autotune(hps_handle *h, int R, int refine, hps_stream_t stream, hps_tune_result *results,
+                       int max_results, int *n_results);
+
 /* ---- Serving: a continuous-batching request loop for time-stepping jobs -------------------
  * Jobs arrive at given times; the loop admits a waiting job (in arrival order) as soon as an
  * active slot is free and the device-memory budget holds its factorization -- unless one of an

@@ -48,6 +48,15 @@ class hps_job_stats(ctypes.Structure):
                 ("step_ms_mean", ctypes.c_double), ("step_ms_p50", ctypes.c_double), ("step_ms_p99", ctypes.c_double)]
 
 
+class hps_tune_result(ctypes.Structure):
+    _fields_ = [("tensor_leaf", ctypes.c_int), ("flow_levels", ctypes.c_int), ("plan_target", ctypes.c_int),
+                ("plan_kmin", ctypes.c_int), ("ms", ctypes.c_float)]
+
+
+BATCH_OPTIONS = ("tensor_leaf", "even_odd", "flow_levels", "flow_n3_max", "cluster_splitk", "plan_target",
+                 "plan_kmin", "plan_npc_max", "split_rhs", "fp64_ctas_per_sm", "group_offset")
+
+
 class hps_server_stats(ctypes.Structure):
     _fields_ = [("jobs_done", ctypes.c_int), ("jobs_rejected", ctypes.c_int), ("makespan_s", ctypes.c_double),
                 ("dof_stages_per_s", ctypes.c_double), ("steps", ctypes.c_int64), ("step_ms_p50", ctypes.c_double),
@@ -80,6 +89,11 @@ SIGNATURES = {
                                       ctypes.POINTER(ctypes.c_double)]),
     "hps_batch_reserve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "hps_batch_reserve_groups": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "hps_batch_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "hps_batch_get_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "hps_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.POINTER(hps_tune_result), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int)]),
     "hps_solve_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "ark_step_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_double,

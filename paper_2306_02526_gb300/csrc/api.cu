@@ -705,6 +705,36 @@ int hps_batch_reserve_groups(hps_handle *H, int R, int groups) {
   return hps::batch_reserve(H, R, groups);
 }
 
+static void drop_batch_graphs(hps_handle *H) {
+  hps::drain_graph(H, H->g_ark_b);
+  hps::drain_graph(H, H->g_solve_b);
+  H->g_ark_b.destroy();
+  H->g_solve_b.destroy();
+}
+
+int hps_batch_set_option(hps_handle *H, int opt, int value) {
+  if (!H) return HPS_EINVAL;
+  drop_batch_graphs(H);
+  return hps::batch_option(H, opt, &value, nullptr);
+}
+
+int hps_batch_get_option(hps_handle *H, int opt, int *value) {
+  if (!H || !value) return HPS_EINVAL;
+  return hps::batch_option(H, opt, nullptr, value);
+}
+
+int hps_batch_autotune(hps_handle *H, int R, int refine, hps_stream_t stream, hps_tune_result *results,
+                       int max_results, int *n_results) {
+  if (!H || max_results < 0) return HPS_EINVAL;
+  drop_batch_graphs(H);
+  const bool graph = H->graph_mode;
+  H->graph_mode = false;  // time the kernels, not graph recording
+  const int e = hps::batch_autotune(H, R, refine, (cudaStream_t)stream, results, max_results, n_results);
+  H->graph_mode = graph;
+  drop_batch_graphs(H);
+  return e;
+}
+
 int hps_batch_reserve(hps_handle *H, int R) {
   if (!H) return HPS_EINVAL;
   return hps_batch_reserve_groups(H, R, H->batch.groups);

@@ -637,22 +637,13 @@ size_t b_smem_floats(const BPlan &P) {  // operator tile(s) + vector chunk
   return (size_t)b_tiles(P) * P.kchunk * P.trows + (size_t)P.npc * P.kchunk * P.Rp;
 }
 
-// Tuning of the split-K plan (process-wide; HPS_PLAN_KMIN, HPS_PLAN_NPC_MAX override): the
-// smallest K chunk of a split, and the most nodes one CTA takes.
+// Split-K plan of one level apply.  Tunables (handle options): the CTAs aimed at (target), the
+// smallest K chunk of a split (kmin) and the most nodes one CTA takes (npc_max).
 struct PlanTune {
-  int kmin = 32, npc_max = 1 << 30;
-  PlanTune() {
-    if (const char *s = std::getenv("HPS_PLAN_KMIN")) kmin = std::max(1, std::atoi(s));
-    if (const char *s = std::getenv("HPS_PLAN_NPC_MAX")) npc_max = std::max(1, std::atoi(s));
-  }
+  int kmin, npc_max;
 };
-const PlanTune &plan_tune() {
-  static const PlanTune t;
-  return t;
-}
 
-BPlan plan_b(int M, int K, int nodes, int R, int target, bool shared_op) {
-  const PlanTune &tune = plan_tune();
+BPlan plan_b(int M, int K, int nodes, int R, int target, bool shared_op, PlanTune tune) {
   BPlan P;
   P.shared_op = shared_op ? 1 : 0;
   P.M = M;
@@ -686,13 +677,8 @@ BPlan plan_b(int M, int K, int nodes, int R, int target, bool shared_op) {
   return P;
 }
 
-int plan_target(const hps_handle *H) {  // CTAs a split-K plan aims for (HPS_PLAN_TARGET per SM)
-  static const int per_sm = [] {
-    const char *s = std::getenv("HPS_PLAN_TARGET");
-    return s ? std::max(1, std::atoi(s)) : 2;
-  }();
-  return per_sm * H->num_sms;
-}
+int plan_target(const hps_handle *H) { return H->batch.plan_target * H->num_sms; }
+PlanTune plan_tune(const hps_handle *H) { return PlanTune{H->batch.plan_kmin, H->batch.plan_npc_max}; }
 
 struct BXDiff {  // d = h^b_3 - h^a_3 (+ interface right-hand side)
   const float *hC;
@@ -1030,7 +1016,8 @@ int launch_b2(hps_handle *H, BatchWork &B, int slot, int M, int K, int nodes, in
   const BPlan2 P = plan_b2(M, K, nodes, R);
   const size_t smem = b2_smem(P);
   if (!H->batch.gemv2 || smem > kB2MaxSmem)
-    return launch_b(H, B, slot, plan_b(M, K, nodes, R, plan_target(H), str == 0), AT, ld, str, xl, ep, st);
+    return launch_b(H, B, slot, plan_b(M, K, nodes, R, plan_target(H), str == 0, plan_tune(H)), AT, ld, str, xl, ep,
+                    st);
   auto kern = P.TC == 8 ? k_b_gemv2<8, XL, EP> : k_b_gemv2<4, XL, EP>;
   static size_t set8 = 0, set4 = 0;
   size_t &set = P.TC == 8 ? set8 : set4;
@@ -1650,9 +1637,9 @@ size_t partial_floats(hps_handle *H, int Rmax) {
   for (int l = 0; l < H->L; ++l) {
     const Level &lv = H->lev[l];
     for (int sh = 0; sh < 2; ++sh) {  // the identity operators are shared even when the others are not
-      const BPlan P[3] = {plan_b(lv.n3, lv.n3, lv.nodes, R, plan_target(H), sh),
-                          plan_b(lv.nb, lv.n3, lv.nodes, R, plan_target(H), sh),
-                          plan_b(lv.n3, lv.nb, lv.nodes, R, plan_target(H), sh)};
+      const BPlan P[3] = {plan_b(lv.n3, lv.n3, lv.nodes, R, plan_target(H), sh, plan_tune(H)),
+                          plan_b(lv.nb, lv.n3, lv.nodes, R, plan_target(H), sh, plan_tune(H)),
+                          plan_b(lv.n3, lv.nb, lv.nodes, R, plan_target(H), sh, plan_tune(H))};
       for (const BPlan &pl : P)
         if (pl.ksplit > 1) mx = std::max(mx, (size_t)pl.ksplit * pl.nodes * pl.M * pl.Rp);
     }
@@ -2125,14 +2112,6 @@ int batch_reserve(hps_handle *H, int R, int groups) {
       k_frag_a<<<blocks((int64_t)n), 256>>>(Bt.impl32.Ainv.p, Bt.impl32.Ainv.ld, q, MT, KT, Bt.afrag_hi, Bt.afrag_lo);
     }
   }
-  if (const char *s = std::getenv("HPS_FP64_CTAS_PER_SM")) Bt.fp64_ctas_per_sm = std::max(0, std::atoi(s));
-  if (const char *s = std::getenv("HPS_FLOW_LEVELS")) Bt.flow_levels = std::max(0, std::atoi(s));
-  if (const char *s = std::getenv("HPS_GEMV2")) Bt.gemv2 = std::atoi(s) != 0;
-  if (const char *s = std::getenv("HPS_EVEN_ODD")) Bt.even_odd = std::atoi(s) != 0;
-  if (const char *s = std::getenv("HPS_LEAF_SPLIT")) Bt.leaf_split = std::atoi(s) != 0;
-  if (const char *s = std::getenv("HPS_OFFSET_GROUPS")) Bt.offset_groups = std::atoi(s) != 0;
-  if (const char *s = std::getenv("HPS_TENSOR_LEAF")) Bt.tensor_leaf = std::atoi(s) != 0;
-  if (const char *s = std::getenv("HPS_FLOW_N3_MAX")) Bt.flow_n3_max = std::max(0, std::atoi(s));
   // (re)allocate the work vectors; old ones stay in the handle's list until hps_free
   const GridDims &g = H->g;
   auto da = [&](auto **ptr, size_t n) -> int {
@@ -2179,6 +2158,119 @@ int batch_reserve(hps_handle *H, int R, int groups) {
   if (cudaDeviceSynchronize() != cudaSuccess) return HPS_ECUDA;
   Bt.Rmax = R;
   return HPS_OK;
+}
+
+int batch_option(hps_handle *H, int opt, const int *set, int *get) {
+  Batch &Bt = H->batch;
+  int *field = nullptr;
+  bool *flag = nullptr;
+  switch (opt) {
+    case HPS_OPT_TENSOR_LEAF: flag = &Bt.tensor_leaf; break;
+    case HPS_OPT_EVEN_ODD: flag = &Bt.even_odd; break;
+    case HPS_OPT_FLOW_LEVELS: field = &Bt.flow_levels; break;
+    case HPS_OPT_FLOW_N3_MAX: field = &Bt.flow_n3_max; break;
+    case HPS_OPT_CLUSTER_SPLITK: flag = &Bt.gemv2; break;
+    case HPS_OPT_PLAN_TARGET: field = &Bt.plan_target; break;
+    case HPS_OPT_PLAN_KMIN: field = &Bt.plan_kmin; break;
+    case HPS_OPT_PLAN_NPC_MAX: field = &Bt.plan_npc_max; break;
+    case HPS_OPT_SPLIT_RHS: flag = &Bt.leaf_split; break;
+    case HPS_OPT_FP64_CTAS_PER_SM: field = &Bt.fp64_ctas_per_sm; break;
+    case HPS_OPT_GROUP_OFFSET: flag = &Bt.offset_groups; break;
+    default: return HPS_EINVAL;
+  }
+  if (get) *get = field ? *field : (*flag ? 1 : 0);
+  if (!set) return HPS_OK;
+  const int v = *set;
+  const bool plan = opt == HPS_OPT_PLAN_TARGET || opt == HPS_OPT_PLAN_KMIN || opt == HPS_OPT_PLAN_NPC_MAX;
+  if (v < 0 || (plan && v < 1) || (opt == HPS_OPT_FLOW_LEVELS && v > kFlowMaxLevels)) return HPS_EINVAL;
+  if (field) *field = v;
+  else *flag = v != 0;
+  if (plan) {  // split-K scratch for the new plans
+    cudaDeviceSynchronize();
+    for (BatchWork &W : Bt.work) {
+      if (W.Rmax == 0) continue;
+      const size_t need = partial_floats(H, W.Rmax);
+      if (need > W.partial_len) {
+        float *p = nullptr;
+        if (cudaMalloc(&p, need * sizeof(float)) != cudaSuccess) return HPS_ENOMEM;
+        H->allocs.push_back(p);
+        W.partial32 = p;
+        W.partial_len = need;
+      }
+    }
+  }
+  return HPS_OK;
+}
+
+namespace {
+__global__ void k_tune_fill(double *x, int64_t n) {  // deterministic right-hand side in [-0.1, 0.1]
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = 0.1 * sin(0.37 * (double)(i % 100003) + 0.001 * (double)(i / 100003));
+}
+}  // namespace
+
+int batch_autotune(hps_handle *H, int R, int refine, cudaStream_t st, hps_tune_result *res, int max_res, int *n_res) {
+  Batch &Bt = H->batch;
+  if (R <= 0 || R > Bt.Rmax || refine < 0 || refine > 8) return HPS_EINVAL;
+  const GridDims &g = H->g;
+  double *rhs = nullptr, *f = nullptr, *u = nullptr;
+  auto cleanup = [&](int e) {
+    cudaDeviceSynchronize();
+    cudaFree(rhs);
+    cudaFree(f);
+    cudaFree(u);
+    return e;
+  };
+  if (cudaMalloc(&rhs, (size_t)g.N_int * R * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&f, (size_t)g.N_bd * R * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&u, (size_t)g.N * R * sizeof(double)) != cudaSuccess)
+    return cleanup(HPS_ENOMEM);
+  k_tune_fill<<<blocks(g.N_int * R), 256, 0, st>>>(rhs, g.N_int * R);
+  cudaMemsetAsync(f, 0, (size_t)g.N_bd * R * sizeof(double), st);
+  struct Cand { int tensor, flow, target, kmin; };
+  std::vector<Cand> cands;
+  for (int tensor : {1, 0})
+    for (int flow : {0, 3})
+      for (const auto &tk : {std::pair<int, int>{2, 32}, std::pair<int, int>{4, 16}})
+        cands.push_back({tensor, flow, tk.first, tk.second});
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int nres = 0, ibest = -1;
+  for (size_t i = 0; i < cands.size(); ++i) {
+    const Cand &c = cands[i];
+    const int vals[4] = {c.tensor, c.flow, c.target, c.kmin};
+    const int opts[4] = {HPS_OPT_TENSOR_LEAF, HPS_OPT_FLOW_LEVELS, HPS_OPT_PLAN_TARGET, HPS_OPT_PLAN_KMIN};
+    int e = HPS_OK;
+    for (int k = 0; k < 4 && e == HPS_OK; ++k) e = batch_option(H, opts[k], &vals[k], nullptr);
+    for (int w = 0; w < 2 && e == HPS_OK; ++w) e = solve_batch(H, R, rhs, f, u, refine, st);
+    cudaEventRecord(e0, st);
+    for (int w = 0; w < 3 && e == HPS_OK; ++w) e = solve_batch(H, R, rhs, f, u, refine, st);
+    cudaEventRecord(e1, st);
+    if (e != HPS_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return cleanup(e != HPS_OK ? e : HPS_ECUDA);
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= 3.f;
+    if (res && nres < max_res) res[nres] = hps_tune_result{c.tensor, c.flow, c.target, c.kmin, ms};
+    if (res && nres < max_res) ++nres;
+    if (ms < best) {
+      best = ms;
+      ibest = (int)i;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const Cand &c = cands[ibest];
+  const int vals[4] = {c.tensor, c.flow, c.target, c.kmin};
+  const int opts[4] = {HPS_OPT_TENSOR_LEAF, HPS_OPT_FLOW_LEVELS, HPS_OPT_PLAN_TARGET, HPS_OPT_PLAN_KMIN};
+  for (int k = 0; k < 4; ++k) batch_option(H, opts[k], &vals[k], nullptr);
+  if (n_res) *n_res = nres;
+  return cleanup(HPS_OK);
 }
 
 int solve_batch(hps_handle *H, int R, const double *rhs, const double *f, double *u, int refine, cudaStream_t st) {

@@ -162,6 +162,9 @@ struct Batch {
   bool even_odd = true;      // FP64 leaf kernels by the even-odd decomposition (even p)
   bool leaf_split = false;   // stage right-hand side as its own streaming pass before the leaf apply
   bool offset_groups = true; // grouped ARK steps: each group starts one phase after the previous
+  int plan_target = 2;       // split-K plans: CTAs per SM aimed at
+  int plan_kmin = 32;        // split-K plans: smallest K chunk
+  int plan_npc_max = 1 << 30;  // split-K plans: most nodes per CTA
   bool tensor_leaf = true;   // shared leaf operator applied by 3xTF32 warp MMA (else FP32 FFMA)
   unsigned *afrag_hi = nullptr, *afrag_lo = nullptr;  // its TF32 fragments
   OpSet32 impl32, ident32;
@@ -281,6 +284,8 @@ int bytes_split(const hps_tree *tree, int p, int coeff_kind, int flags, size_t *
 
 // ---- batched mixed-precision path (batched.cu) ---------------------------------------------
 int batch_reserve(hps_handle *H, int R, int groups);
+int batch_option(hps_handle *H, int opt, const int *set, int *get);
+int batch_autotune(hps_handle *H, int R, int refine, cudaStream_t st, hps_tune_result *res, int max_res, int *n_res);
 void batch_release(hps_handle *H);
 int solve_batch(hps_handle *H, int R, const double *rhs, const double *f, double *u, int refine, cudaStream_t st);
 struct ArkTable {

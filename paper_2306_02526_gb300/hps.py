@@ -199,6 +199,26 @@ class HPSSolver:
         else:
             check(lib().hps_batch_reserve_groups(self._h, int(R), int(groups)), "hps_batch_reserve_groups")
 
+    def batch_option(self, name, value=None):
+        """Get (value None) or set a batched-path kernel option (hps_batch_get/set_option); names
+        in _lib.BATCH_OPTIONS."""
+        opt = _lib.BATCH_OPTIONS.index(name)
+        if value is not None:
+            check(lib().hps_batch_set_option(self._h, opt, int(value)), "hps_batch_set_option")
+        out = ctypes.c_int()
+        check(lib().hps_batch_get_option(self._h, opt, ctypes.byref(out)), "hps_batch_get_option")
+        return out.value
+
+    def batch_autotune(self, R, refine=1, stream=None):
+        """Time the candidate kernel configurations on this operator, keep the fastest
+        (hps_batch_autotune); returns one dict per candidate."""
+        res = (_lib.hps_tune_result * 32)()
+        n = ctypes.c_int()
+        check(lib().hps_batch_autotune(self._h, int(R), int(refine), _stream_ptr(stream), res, 32, ctypes.byref(n)),
+              "hps_batch_autotune")
+        return [{"tensor_leaf": r.tensor_leaf, "flow_levels": r.flow_levels, "plan_target": r.plan_target,
+                 "plan_kmin": r.plan_kmin, "ms": r.ms} for r in res[:n.value]]
+
     def solve_batch(self, rhs, f=None, u=None, refine=2, stream=None):
         """R solves at once: rhs (N_int, R), f (N_bd, R) or None -> u (N, R) (hps_solve_batch)."""
         import torch

@@ -181,3 +181,51 @@ def test_grouped_solve_batch_matches_ungrouped(graph):
             assert rel_max(got[:, j], ref) <= TOL
     S1.close()
     SG.close()
+
+
+def _ark_pair(torch, n1, n2, p, R, dt, opt=None, val=None, autotune=False):
+    """Two batched ARK steps (Allen-Cahn, constant coefficients: the shared-operator kernels)
+    against the FP64 single-column path, column by column."""
+    from paper_2306_02526_gb300 import hps
+    g = Grid(n1, n2, p)
+    X, Y = g.coords()
+    bd = g.boundary_indices()
+    S = _solver(torch, n1, n2, p, {"a11": 0.02, "a22": 0.02}, 0.25 * dt)
+    S.batch_reserve(R)
+    tuned = None
+    if opt is not None:
+        S.batch_option(opt, val)
+        assert S.batch_option(opt) == val
+    if autotune:
+        tuned = S.batch_autotune(R, refine=1)
+    u0 = np.stack([0.3 * np.sin(math.pi * (j + 1) * X) * np.sin(math.pi * Y) for j in range(R)], axis=1)
+    u0[bd, :] = 0.0
+    ub = to_dev(torch, u0)
+    us = [to_dev(torch, u0[:, j].copy()) for j in range(R)]
+    for n in range(2):
+        S.ark_step_batch(ub, n * dt, dt, g="allen_cahn", g_param=(1.0, 0.0), refine=1)
+        for j in range(R):
+            S.ark_step(us[j], n * dt, dt, g="allen_cahn", g_param=(1.0, 0.0))
+    got = ub.cpu().numpy()
+    err = max(rel_max(got[:, j], us[j].cpu().numpy()) for j in range(R))
+    S.close()
+    return err, tuned
+
+
+@pytest.mark.parametrize("opt,val", [("tensor_leaf", 0), ("even_odd", 0), ("flow_levels", 3), ("flow_levels", 8),
+                                     ("cluster_splitk", 1), ("plan_target", 4), ("plan_kmin", 8),
+                                     ("plan_npc_max", 1), ("split_rhs", 1), ("fp64_ctas_per_sm", 2)])
+def test_batch_option_variants_match_fp64(opt, val):
+    """Every kernel variant of the batched path (handle options) gives the FP64 result to the
+    mixed-precision tolerance; flow_levels = 8 puts every level of the 16 x 8 tree, root
+    included, into the dataflow kernels."""
+    torch = need_gpu()
+    err, _ = _ark_pair(torch, 16, 8, 12, 16, 0.01, opt, val)
+    assert err <= TOL, (opt, val, err)
+
+
+def test_batch_autotune_keeps_a_correct_configuration():
+    torch = need_gpu()
+    err, tuned = _ark_pair(torch, 16, 16, 12, 16, 0.01, autotune=True)
+    assert len(tuned) == 8 and all(t["ms"] > 0 for t in tuned)
+    assert err <= TOL
