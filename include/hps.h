@@ -285,7 +285,10 @@ enum {
   HPS_OPT_SPLIT_RHS = 8,        /* 1: stage right-hand side as its own pass (default 0)           */
   HPS_OPT_FP64_CTAS_PER_SM = 9, /* FP64 leaf kernels: persistent CTAs per SM, 0: one CTA per leaf  */
   HPS_OPT_GROUP_OFFSET = 10,    /* 1: column groups of an ARK step start one phase apart (1)     */
-  HPS_OPT_COUNT = 11
+  HPS_OPT_LAST_CTA_SUM = 11,    /* split-K merge applies with at most this many chunks are summed
+                                   by the last CTA of each tile, deeper ones by a reduction
+                                   kernel (default 0: always the reduction kernel)                */
+  HPS_OPT_COUNT = 12
 };
 int hps_batch_set_option(hps_handle *h, int opt, int value);
 int hps_batch_get_option(hps_handle *h, int opt, int *value);

@@ -787,7 +787,7 @@ struct BEScatter {  // interface values: FP32 for the levels below, and into the
 
 template <int TC, class XL, class EP>
 __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict__ AT, int ld, int64_t str, XL xl,
-                                                EP ep, float *__restrict__ partial) {
+                                                EP ep, float *__restrict__ partial, unsigned *__restrict__ tile_count) {
   extern __shared__ __align__(16) float smb[];
   const int ng = blockIdx.x / P.row_tiles, tile = blockIdx.x % P.row_tiles;
   const int node0 = ng * P.npc, nn = min(P.npc, P.nodes - node0);
@@ -843,21 +843,47 @@ __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict
   if (live)
     smem_fma<TC>(acc, As + (size_t)(P.shared_op ? 0 : lo) * klen * trows + (r0 - rlo), trows, klen,
                  xs + (int64_t)lo * klen * Rp + j0, Rp);
-  if (!live) return;
   const int k = node0 + lo;
+  if (live)
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const int r = r0 + e;
-    if (r >= P.M) continue;
-    if (P.ksplit == 1) {
-      ep.template row<TC>(k, r, j0, acc[e]);
-    } else {
-      float *dst = partial + (((int64_t)ks * P.nodes + k) * P.M + r) * Rp + j0;
+    for (int e = 0; e < 4; ++e) {
+      const int r = r0 + e;
+      if (r >= P.M) continue;
+      if (P.ksplit == 1) {
+        ep.template row<TC>(k, r, j0, acc[e]);
+      } else {
+        float *dst = partial + (((int64_t)ks * P.nodes + k) * P.M + r) * Rp + j0;
 #pragma unroll
-      for (int t = 0; t < TC; t += 4)
-        *reinterpret_cast<float4 *>(dst + t) = make_float4(acc[e][t], acc[e][t + 1], acc[e][t + 2], acc[e][t + 3]);
+        for (int t = 0; t < TC; t += 4)
+          *reinterpret_cast<float4 *>(dst + t) = make_float4(acc[e][t], acc[e][t + 1], acc[e][t + 2], acc[e][t + 3]);
+      }
     }
+  if (P.ksplit == 1 || !tile_count) return;
+  // split K, summed here: the CTA that finishes a tile last adds its ksplit partials in chunk
+  // order (deterministic) and runs the epilogue; it also re-arms the tile's counter
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(tile_count + blockIdx.x, 1u) == (unsigned)(P.ksplit - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int Rq = Rp / 4, rows = P.npc > 1 ? P.M : min(trow, P.M - rlo);
+  const int64_t kstride = (int64_t)P.nodes * P.M * Rp;
+  for (int i = threadIdx.x; i < nn * rows * Rq; i += blockDim.x) {
+    const int q4 = i % Rq, row = i / Rq, l2 = row / rows, r = rlo + row - l2 * rows, j0q = 4 * q4;
+    const float *src = partial + ((int64_t)(node0 + l2) * P.M + r) * Rp + j0q;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int ks2 = 0; ks2 < P.ksplit; ++ks2) {
+      const float4 x = __ldcg(reinterpret_cast<const float4 *>(src + ks2 * kstride));
+      v[0] += x.x;
+      v[1] += x.y;
+      v[2] += x.z;
+      v[3] += x.w;
+    }
+    ep.template row<4>(node0 + l2, r, j0q, v);
   }
+  if (threadIdx.x == 0) tile_count[blockIdx.x] = 0u;
 }
 
 // Sum of the split-K partials in chunk order, four columns per thread.
@@ -894,11 +920,15 @@ int launch_b(hps_handle *H, BatchWork &B, int slot, const BPlan &P, const float 
   }
   H->trace.begin(slot, st);
   const dim3 grid(P.node_groups * P.row_tiles, P.ksplit);
+  // split-K sums: in the kernel (last CTA of a tile) unless the tiles are too many or too deep
+  const bool in_kernel = P.ksplit <= H->batch.last_cta_max_split &&
+                         (size_t)P.node_groups * P.row_tiles <= B.tile_count_len;
+  unsigned *tc = in_kernel ? B.tile_count : nullptr;
   if (P.TC == 8)
-    k_b_gemv<8, XL, EP><<<grid, kBT, smem, st>>>(P, AT, ld, str, xl, ep, B.partial32);
+    k_b_gemv<8, XL, EP><<<grid, kBT, smem, st>>>(P, AT, ld, str, xl, ep, B.partial32, tc);
   else
-    k_b_gemv<4, XL, EP><<<grid, kBT, smem, st>>>(P, AT, ld, str, xl, ep, B.partial32);
-  if (P.ksplit > 1) {
+    k_b_gemv<4, XL, EP><<<grid, kBT, smem, st>>>(P, AT, ld, str, xl, ep, B.partial32, tc);
+  if (P.ksplit > 1 && !in_kernel) {
     const int64_t n = (int64_t)P.nodes * P.M * (P.Rp / 4);
     k_b_reduce<EP><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, B.partial32, ep);
   }
@@ -2147,6 +2177,9 @@ int batch_reserve(hps_handle *H, int R, int groups) {
       if (da(&W.h32[l], (size_t)lv.nodes * lv.nb * Rg)) return HPS_ENOMEM;
       if (l < H->L && da(&W.w332[l], (size_t)lv.nodes * lv.n3 * Rg)) return HPS_ENOMEM;
     }
+    W.tile_count_len = 65536;
+    if (da(&W.tile_count, W.tile_count_len)) return HPS_ENOMEM;
+    cudaMemset(W.tile_count, 0, W.tile_count_len * sizeof(unsigned));
     W.flow_len = 1;
     for (const Level &lv : H->lev) W.flow_len += lv.nodes;
     if (da(&W.flow_sync, W.flow_len)) return HPS_ENOMEM;
@@ -2176,6 +2209,7 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
     case HPS_OPT_SPLIT_RHS: flag = &Bt.leaf_split; break;
     case HPS_OPT_FP64_CTAS_PER_SM: field = &Bt.fp64_ctas_per_sm; break;
     case HPS_OPT_GROUP_OFFSET: flag = &Bt.offset_groups; break;
+    case HPS_OPT_LAST_CTA_SUM: field = &Bt.last_cta_max_split; break;
     default: return HPS_EINVAL;
   }
   if (get) *get = field ? *field : (*flag ? 1 : 0);

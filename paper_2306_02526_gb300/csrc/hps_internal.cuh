@@ -142,6 +142,8 @@ struct BatchWork {
   std::vector<float *> h32, w332;  // per level
   float *partial32 = nullptr;
   size_t partial_len = 0;          // floats
+  unsigned *tile_count = nullptr;  // split-K tiles: CTAs done (re-armed by the last one)
+  size_t tile_count_len = 0;
   unsigned *flow_sync = nullptr;   // dataflow merge kernels: ticket counter + node flags
   size_t flow_len = 0;
   cudaStream_t stream = nullptr;   // grouped calls: the group's own stream
@@ -162,6 +164,7 @@ struct Batch {
   bool even_odd = true;      // FP64 leaf kernels by the even-odd decomposition (even p)
   bool leaf_split = false;   // stage right-hand side as its own streaming pass before the leaf apply
   bool offset_groups = true; // grouped ARK steps: each group starts one phase after the previous
+  int last_cta_max_split = 0;   // split-K sums by the last CTA of each tile up to this split depth (0: never)
   int plan_target = 2;       // split-K plans: CTAs per SM aimed at
   int plan_kmin = 32;        // split-K plans: smallest K chunk
   int plan_npc_max = 1 << 30;  // split-K plans: most nodes per CTA
