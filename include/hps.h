@@ -288,9 +288,20 @@ enum {
   HPS_OPT_LAST_CTA_SUM = 11,    /* split-K merge applies with at most this many chunks are summed
                                    by the last CTA of each tile, deeper ones by a reduction
                                    kernel (default 0: always the reduction kernel)                */
-  HPS_OPT_COUNT = 12
+  HPS_OPT_FAST_DIAG = 12,       /* 1: constant-coefficient leaf solves by fast diagonalization
+                                   (when the handle's 1-D operators have a real, well-conditioned
+                                   eigen-decomposition; default 1)                                */
+  HPS_OPT_COUNT = 13
 };
 int hps_batch_set_option(hps_handle *h, int opt, int value);
+
+/* Host-only check of the fast diagonalization for constant coefficients coef = (a11, a22, a1,
+ * a2, a0), gamma dt and leaf widths hx, hy (Sec. 4.2: the leaf interior operator is a Kronecker
+ * sum of 1-D Chebyshev operators): factors A_ii^-1 = (V_y (x) V_x) Lam (V_y^-1 (x) V_x^-1) and
+ * reports *max_err = max over all unit vectors e of |A_ii F e - e|.  HPS_OK when the factors
+ * exist and max_err <= 1e-12 (then hps_build uses them), HPS_EINVAL when a 1-D operator has no
+ * real, well-conditioned eigen-decomposition.  Needs no GPU. */
+int hps_fastdiag_check(int p, const double *coef, double gamma_dt, double hx, double hy, double *max_err);
 int hps_batch_get_option(hps_handle *h, int opt, int *value);
 
 /* One configuration tried by hps_batch_autotune and its time. */

@@ -54,7 +54,8 @@ class hps_tune_result(ctypes.Structure):
 
 
 BATCH_OPTIONS = ("tensor_leaf", "even_odd", "flow_levels", "flow_n3_max", "cluster_splitk", "plan_target",
-                 "plan_kmin", "plan_npc_max", "split_rhs", "fp64_ctas_per_sm", "group_offset", "last_cta_sum")
+                 "plan_kmin", "plan_npc_max", "split_rhs", "fp64_ctas_per_sm", "group_offset", "last_cta_sum",
+                 "fast_diag")
 
 
 class hps_server_stats(ctypes.Structure):
@@ -90,6 +91,8 @@ SIGNATURES = {
     "hps_batch_reserve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "hps_batch_reserve_groups": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "hps_batch_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "hps_fastdiag_check": (ctypes.c_int, [ctypes.c_int, c_double_p, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, c_double_p]),
     "hps_batch_get_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "hps_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                           ctypes.POINTER(hps_tune_result), ctypes.c_int,

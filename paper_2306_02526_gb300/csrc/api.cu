@@ -136,6 +136,28 @@ int dalloc(hps_handle *H, T **ptr, size_t count) {
   return HPS_OK;
 }
 
+// D1x, D1y (Chebyshev differentiation scaled to leaves of width hx, hy), Dxx = D1x^2, Dyy = D1y^2
+std::vector<double> scaled_D(int p, double hx, double hy) {
+  const std::vector<double> D = cheb_D(p);
+  std::vector<double> Dh((size_t)4 * p * p);
+  const double sx = 2.0 / hx, sy = 2.0 / hy;
+  for (int i = 0; i < p * p; ++i) {
+    Dh[i] = sx * D[i];
+    Dh[p * p + i] = sy * D[i];
+  }
+  for (int i = 0; i < p; ++i)
+    for (int j = 0; j < p; ++j) {
+      double sxx = 0.0, syy = 0.0;
+      for (int k = 0; k < p; ++k) {
+        sxx += Dh[i * p + k] * Dh[k * p + j];
+        syy += Dh[p * p + i * p + k] * Dh[p * p + k * p + j];
+      }
+      Dh[2 * p * p + i * p + j] = sxx;
+      Dh[3 * p * p + i * p + j] = syy;
+    }
+  return Dh;
+}
+
 size_t opset_bytes(const std::vector<Level> &lev, int q, int b, bool shared, bool identity) {
   auto pad = [](int n) { return (size_t)((n + 1) & ~1); };
   size_t s = 0;
@@ -345,23 +367,7 @@ int hps_build(const hps_tree *tree, int p, const hps_coeffs *coeffs, double gamm
   }
   // differentiation matrices D1x, D1y, Dxx = D1x^2, Dyy = D1y^2 on this leaf size
   {
-    const std::vector<double> D = cheb_D(p);
-    std::vector<double> Dh((size_t)4 * p * p);
-    const double sx = 2.0 / H->hx, sy = 2.0 / H->hy;
-    for (int i = 0; i < p * p; ++i) {
-      Dh[i] = sx * D[i];
-      Dh[p * p + i] = sy * D[i];
-    }
-    for (int i = 0; i < p; ++i)
-      for (int j = 0; j < p; ++j) {
-        double sxx = 0.0, syy = 0.0;
-        for (int k = 0; k < p; ++k) {
-          sxx += Dh[i * p + k] * Dh[k * p + j];
-          syy += Dh[p * p + i * p + k] * Dh[p * p + k * p + j];
-        }
-        Dh[2 * p * p + i * p + j] = sxx;
-        Dh[3 * p * p + i * p + j] = syy;
-      }
+    std::vector<double> Dh = scaled_D(p, H->hx, H->hy);
     if (p % 2 == 0) {  // even-odd halves of D1x, D1y, Dxx, Dyy: A = (D_ik + D_i,p-1-k) / 2, B = (D_ik - D_i,p-1-k) / 2
       const int h = p / 2;
       for (int mtx = 0; mtx < 4; ++mtx) {
@@ -379,6 +385,7 @@ int hps_build(const hps_tree *tree, int p, const hps_coeffs *coeffs, double gamm
     if (dalloc(H, &H->d_D, Dh.size())) return fail(HPS_ENOMEM);
     cudaMemcpyAsync(H->d_D, Dh.data(), Dh.size() * sizeof(double), cudaMemcpyHostToDevice, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return fail(HPS_ECUDA);
+    if (int e = hps::fastdiag_build(H, Dh, st)) return fail(e);
   }
   if (coeffs->kind == HPS_COEF_NODAL) {
     const int64_t n = H->g.N_int;
@@ -449,6 +456,7 @@ int clone_handle(const hps_handle *base, cudaStream_t st, hps_handle **out) {
   for (int i = 0; i < 5; ++i) H->cst[i] = base->cst[i];
   H->d_coef = base->d_coef;
   H->d_D = base->d_D;
+  H->fd = base->fd;
   H->lev = base->lev;
   H->impl = base->impl;
   H->ident = base->ident;
@@ -710,6 +718,16 @@ static void drop_batch_graphs(hps_handle *H) {
   hps::drain_graph(H, H->g_solve_b);
   H->g_ark_b.destroy();
   H->g_solve_b.destroy();
+}
+
+int hps_fastdiag_check(int p, const double *coef, double gamma_dt, double hx, double hy, double *max_err) {
+  if (p < 4 || p > 32 || !coef || !(gamma_dt > 0.0) || !(hx > 0.0) || !(hy > 0.0)) return HPS_EINVAL;
+  const std::vector<double> Dh = scaled_D(p, hx, hy);
+  std::vector<double> F[5];
+  double err = 0.0;
+  const bool ok = hps::fastdiag_factor(p, Dh.data(), coef, gamma_dt, true, F, &err);
+  if (max_err) *max_err = err;
+  return ok ? HPS_OK : HPS_EINVAL;
 }
 
 int hps_batch_set_option(hps_handle *H, int opt, int value) {

@@ -349,6 +349,125 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_down(GridDims g, int R, const in
     u_out(uo, l0 * R + idx, w32[(int64_t)k * q * R + idx] + (identity ? 0.f : Os[(idx / R) * Rp + idx % R]));
 }
 
+// ---- leaf apply by fast diagonalization (constant coefficients) -----------------------------
+// W = A_ii^-1 R = (V_y (x) V_x) Lam (V_y^-1 (x) V_x^-1) R as four passes of m x m products along
+// grid lines (x lines: the m interior points of a row; y lines: of a column), 4 m^3 R
+// multiply-adds per leaf instead of m^4 R.  Each thread forms 4 outputs x 4 columns per pass
+// (an outer product of a float4 of the transposed line operator and a float4 of the field).
+
+// x pass: out[(j, i)][c] = sum_k M(i, k) in[(j, k)][c] (times Lam(j, i) if lam); MT = M^T [k][mp]
+__device__ __forceinline__ void fd_pass_x(const float *in, float *out, const float *MT, int m, int mp, int Rp,
+                                          const float *lam) {
+  const int IQ = mp / 4, Rq = Rp / 4;
+  for (int it = threadIdx.x; it < m * IQ * Rq; it += blockDim.x) {
+    const int c4 = it % Rq, t = it / Rq, iq = t % IQ, j = t / IQ;
+    float4 acc[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) acc[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float *inr = in + j * m * Rp + 4 * c4;
+    for (int k = 0; k < m; ++k) {
+      const float4 x = *reinterpret_cast<const float4 *>(inr + k * Rp);
+      const float4 mv = *reinterpret_cast<const float4 *>(MT + k * mp + 4 * iq);
+      const float mm[4] = {mv.x, mv.y, mv.z, mv.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        acc[a].x = fmaf(mm[a], x.x, acc[a].x);
+        acc[a].y = fmaf(mm[a], x.y, acc[a].y);
+        acc[a].z = fmaf(mm[a], x.z, acc[a].z);
+        acc[a].w = fmaf(mm[a], x.w, acc[a].w);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int i = 4 * iq + a;
+      if (i >= m) break;
+      float4 v = acc[a];
+      if (lam) {
+        const float l = lam[j * mp + i];
+        v.x *= l;
+        v.y *= l;
+        v.z *= l;
+        v.w *= l;
+      }
+      *reinterpret_cast<float4 *>(out + (j * m + i) * Rp + 4 * c4) = v;
+    }
+  }
+}
+
+// y pass: out[(j, i)][c] = sum_k M(j, k) in[(k, i)][c] (times Lam(j, i) if lam)
+__device__ __forceinline__ void fd_pass_y(const float *in, float *out, const float *MT, int m, int mp, int Rp,
+                                          const float *lam) {
+  const int JQ = mp / 4, Rq = Rp / 4;
+  for (int it = threadIdx.x; it < m * JQ * Rq; it += blockDim.x) {
+    const int c4 = it % Rq, t = it / Rq, jq = t % JQ, i = t / JQ;
+    float4 acc[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) acc[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float *inc = in + i * Rp + 4 * c4;
+    for (int k = 0; k < m; ++k) {
+      const float4 x = *reinterpret_cast<const float4 *>(inc + k * m * Rp);
+      const float4 mv = *reinterpret_cast<const float4 *>(MT + k * mp + 4 * jq);
+      const float mm[4] = {mv.x, mv.y, mv.z, mv.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        acc[a].x = fmaf(mm[a], x.x, acc[a].x);
+        acc[a].y = fmaf(mm[a], x.y, acc[a].y);
+        acc[a].z = fmaf(mm[a], x.z, acc[a].z);
+        acc[a].w = fmaf(mm[a], x.w, acc[a].w);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int j = 4 * jq + a;
+      if (j >= m) break;
+      float4 v = acc[a];
+      if (lam) {
+        const float l = lam[j * mp + i];
+        v.x *= l;
+        v.y *= l;
+        v.z *= l;
+        v.w *= l;
+      }
+      *reinterpret_cast<float4 *>(out + (j * m + i) * Rp + 4 * c4) = v;
+    }
+  }
+}
+
+// One leaf per CTA: stage right-hand side (FP64 combination, saved if requested), the four
+// passes between two shared-memory buffers, then w and the fluxes.  fd32 holds [V_x, V_x^-1,
+// V_y, V_y^-1, Lam], each m x mp.
+__global__ void __launch_bounds__(kBT) k_b_leaf_up_fd(GridDims g, int R, const int *__restrict__ origin, Combo rhs,
+                                                      double *__restrict__ Rsave, const float *__restrict__ fd32,
+                                                      int mp, const double *__restrict__ Dg, float *__restrict__ w32,
+                                                      float *__restrict__ h32) {
+  extern __shared__ __align__(16) float sfd[];
+  const int p = g.p, m = g.m, q = m * m, b = 4 * m, Rp = round4(R), mm = m * mp;
+  float *MT = sfd, *Lam = MT + 4 * mm, *D1x = Lam + mm, *D1y = D1x + p * p;
+  float *Rs = D1x + round4(2 * p * p), *Ts = Rs + q * Rp;
+  const int k = blockIdx.x;
+  const int64_t l0 = ((int64_t)origin[2 * k + 1] * g.n1 + origin[2 * k]) * q;
+  for (int idx = threadIdx.x; idx < 4 * mm; idx += blockDim.x) {  // transposed line operators
+    const int a = idx / mm, r = idx % mm, kk = r / mp, i = r % mp;
+    MT[idx] = i < m ? fd32[((size_t)a * m + i) * mp + kk] : 0.f;
+  }
+  for (int idx = threadIdx.x; idx < mm; idx += blockDim.x) Lam[idx] = fd32[4 * (size_t)mm + idx];
+  for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) D1x[i] = (float)Dg[i];
+  if (Rp != R)
+    for (int idx = threadIdx.x; idx < q * Rp; idx += blockDim.x) Rs[idx] = 0.f;
+  __syncthreads();
+  stage_combo<8>(rhs, l0 * R, q * R, R, Rp, Rsave, Rs);
+  __syncthreads();
+  fd_pass_x(Rs, Ts, MT + 1 * mm, m, mp, Rp, nullptr);  // V_x^-1 along x
+  __syncthreads();
+  fd_pass_y(Ts, Rs, MT + 3 * mm, m, mp, Rp, Lam);      // V_y^-1 along y, then Lam
+  __syncthreads();
+  fd_pass_y(Rs, Ts, MT + 2 * mm, m, mp, Rp, nullptr);  // V_y along y
+  __syncthreads();
+  fd_pass_x(Ts, Rs, MT + 0 * mm, m, mp, Rp, nullptr);  // V_x along x
+  __syncthreads();
+  leaf_up_out(k, q, b, R, Rp, Rs, D1x, D1y, p, m, w32, h32);
+}
+
 // ---- leaf apply on the tensor cores: 3xTF32 warp MMA (m16n8k8) -----------------------------
 // W = A_ii^{-1} R with the shared operator: each FP32 operand x is split into two TF32 numbers
 // x = hi + lo (hi = x rounded to TF32, lo = x - hi rounded to TF32) and the product is formed as
@@ -1677,6 +1796,8 @@ size_t partial_floats(hps_handle *H, int Rmax) {
   return mx;
 }
 
+inline int m_of(const hps_handle *H) { return H->m; }
+
 int flow_launch(hps_handle *H, BatchWork &B, const FlowArgs &FA, bool up, size_t smem, int nflags, cudaStream_t st) {
   if ((size_t)nflags + 1 > B.flow_len) return HPS_EINVAL;
   auto kern = up ? k_b_flow_up : k_b_flow_down;
@@ -1716,6 +1837,18 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
     H->trace.begin(kLeafUp, st);
     k_b_leaf_up_narrow<<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, o32.Ainv.p, o32.Ainv.ld,
                                                       o32.Ainv.str, ops.identity ? 1 : 0, H->d_D, B.w32, B.h32[L]);
+    H->trace.end(kLeafUp, st);
+  } else if (H->fd.on && H->batch.fast_diag && !ops.identity) {
+    const int mp = H->fd.mp;
+    const size_t smem = (size_t)(5 * m_of(H) * mp + round4(2 * p * p) + 2 * q * Rp) * sizeof(float);
+    static size_t set = 0;
+    if (smem > 48 * 1024 && smem > set) {
+      cudaFuncSetAttribute(k_b_leaf_up_fd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      set = smem;
+    }
+    H->trace.begin(kLeafUp, st);
+    k_b_leaf_up_fd<<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, H->fd.d32, mp, H->d_D, B.w32,
+                                                  B.h32[L]);
     H->trace.end(kLeafUp, st);
   } else if (allow_tc && H->batch.afrag_hi && H->batch.tensor_leaf && H->shared && !ops.identity && Rp % 8 == 0 &&
              Rp / 8 <= kTcMaxNT &&
@@ -2210,6 +2343,7 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
     case HPS_OPT_FP64_CTAS_PER_SM: field = &Bt.fp64_ctas_per_sm; break;
     case HPS_OPT_GROUP_OFFSET: flag = &Bt.offset_groups; break;
     case HPS_OPT_LAST_CTA_SUM: field = &Bt.last_cta_max_split; break;
+    case HPS_OPT_FAST_DIAG: flag = &Bt.fast_diag; break;
     default: return HPS_EINVAL;
   }
   if (get) *get = field ? *field : (*flag ? 1 : 0);

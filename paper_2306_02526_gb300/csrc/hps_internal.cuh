@@ -165,6 +165,7 @@ struct Batch {
   bool leaf_split = false;   // stage right-hand side as its own streaming pass before the leaf apply
   bool offset_groups = true; // grouped ARK steps: each group starts one phase after the previous
   int last_cta_max_split = 0;   // split-K sums by the last CTA of each tile up to this split depth (0: never)
+  bool fast_diag = true;     // leaf apply by fast diagonalization where the handle has it
   int plan_target = 2;       // split-K plans: CTAs per SM aimed at
   int plan_kmin = 32;        // split-K plans: smallest K chunk
   int plan_npc_max = 1 << 30;  // split-K plans: most nodes per CTA
@@ -207,6 +208,15 @@ struct Trace {
   void release();
 };
 
+// Factored inverse of the constant-coefficient leaf operator (fastdiag.cu): V_x, V_x^-1, V_y,
+// V_y^-1 and 1 / (c - gamma dt (lam_y + lam_x)), each m x mp (rows padded to a multiple of 4).
+struct FastDiag {
+  bool on = false;
+  int mp = 0;
+  double *d64 = nullptr;
+  float *d32 = nullptr;
+};
+
 struct Combo {
   const double *ptr[kCombo];
   double coef[kCombo];
@@ -225,6 +235,7 @@ struct hps_handle {
   double cst[5];
   double *d_coef = nullptr;   // 5 x N_int (NODAL)
   double *d_D = nullptr;      // D1x, D1y, Dxx, Dyy: 4 p*p doubles, row-major
+  hps::FastDiag fd;           // factored A_ii^-1 (constant coefficients)
   std::vector<hps::Level> lev;  // 0 (root) .. L (leaves)
   hps::OpSet impl, ident;
   // work buffers
@@ -286,6 +297,9 @@ int clone_handle(const hps_handle *base, cudaStream_t st, hps_handle **out);
 int bytes_split(const hps_tree *tree, int p, int coeff_kind, int flags, size_t *ops, size_t *work);
 
 // ---- batched mixed-precision path (batched.cu) ---------------------------------------------
+int fastdiag_build(hps_handle *H, const std::vector<double> &Dh, cudaStream_t st);
+bool fastdiag_factor(int p, const double *Dh, const double *cst, double gdt, bool check_all,
+                     std::vector<double> (&F)[5], double *max_err);
 int batch_reserve(hps_handle *H, int R, int groups);
 int batch_option(hps_handle *H, int opt, const int *set, int *get);
 int batch_autotune(hps_handle *H, int R, int refine, cudaStream_t st, hps_tune_result *res, int max_res, int *n_res);
