@@ -124,6 +124,68 @@ __global__ void __launch_bounds__(512) k_leaf_up(GridDims g, int nleaf, const in
   }
 }
 
+// Leaf apply by fast diagonalization (constant coefficients): W = (V_y (x) V_x) Lam
+// (V_y^-1 (x) V_x^-1) R as four passes of m-point products along grid lines, 4 m^3 instead of
+// m^4 multiply-adds per leaf.  fd holds [V_x, V_x^-1, V_y, V_y^-1, Lam], each m x mp; the x
+// passes read their operator transposed (consecutive threads = consecutive output points).
+__global__ void __launch_bounds__(512) k_leaf_up_fd(GridDims g, int nleaf, const int *__restrict__ origin, Combo rhs,
+                                                    double *__restrict__ Rsave, const double *__restrict__ fd, int mp,
+                                                    const double *__restrict__ Dg, double *__restrict__ wleaf,
+                                                    double *__restrict__ hleaf) {
+  extern __shared__ double sm[];
+  const int p = g.p, m = g.m, q = m * m, b = 4 * m, lpc = leaf_lpc(q), mm = m * m;
+  double *D1x = sm, *D1y = sm + p * p, *Ms = sm + 2 * p * p, *Rs = Ms + 5 * mm, *Ts = Rs + lpc * q;
+  const int k0 = blockIdx.x * lpc;
+  const int nl = min(lpc, nleaf - k0);
+  for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) sm[i] = Dg[i];
+  for (int idx = threadIdx.x; idx < 5 * mm; idx += blockDim.x) {  // x operators transposed: [k][i]
+    const int a = idx / mm, r = idx % mm, x = r / m, y = r % m;
+    const bool tr = a == 0 || a == 1;
+    Ms[idx] = tr ? fd[((size_t)a * m + y) * mp + x] : fd[((size_t)a * m + x) * mp + y];
+  }
+  for (int idx = threadIdx.x; idx < nl * q; idx += blockDim.x) {
+    const int lo = idx / q, r = idx % q, k = k0 + lo;
+    const int64_t l0 = ((int64_t)origin[2 * k + 1] * g.n1 + origin[2 * k]) * q;
+    double v = 0.0;
+    for (int t = 0; t < rhs.n; ++t) v = fma(rhs.coef[t], rhs.ptr[t][l0 + r], v);
+    Rs[idx] = v;
+    if (Rsave) Rsave[l0 + r] = v;
+  }
+  const double *VxT = Ms, *VxiT = Ms + mm, *Vy = Ms + 2 * mm, *Vyi = Ms + 3 * mm, *Lam = Ms + 4 * mm;
+  auto pass_x = [&](const double *in, double *out, const double *MT) {  // out(j,i) = sum_k M(i,k) in(j,k)
+    for (int idx = threadIdx.x; idx < nl * q; idx += blockDim.x) {
+      const int lo = idx / q, r = idx % q, j = r / m, i = r % m;
+      const double *x = in + lo * q + j * m;
+      double s = 0.0;
+      for (int k = 0; k < m; ++k) s = fma(MT[k * m + i], x[k], s);
+      out[idx] = s;
+    }
+  };
+  auto pass_y = [&](const double *in, double *out, const double *M, const double *lam) {  // out(j,i) = sum_k M(j,k) in(k,i)
+    for (int idx = threadIdx.x; idx < nl * q; idx += blockDim.x) {
+      const int lo = idx / q, r = idx % q, j = r / m, i = r % m;
+      const double *x = in + lo * q + i;
+      double s = 0.0;
+      for (int k = 0; k < m; ++k) s = fma(M[j * m + k], x[k * m], s);
+      out[idx] = lam ? s * lam[r] : s;
+    }
+  };
+  __syncthreads();
+  pass_x(Rs, Ts, VxiT);
+  __syncthreads();
+  pass_y(Ts, Rs, Vyi, Lam);
+  __syncthreads();
+  pass_y(Rs, Ts, Vy, nullptr);
+  __syncthreads();
+  pass_x(Ts, Rs, VxT);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nl * q; idx += blockDim.x) wleaf[(int64_t)k0 * q + idx] = Rs[idx];
+  for (int idx = threadIdx.x; idx < nl * b; idx += blockDim.x) {
+    const int lo = idx / b, e = idx % b;
+    hleaf[(int64_t)k0 * b + idx] = flux_interior(e, Rs + lo * q, D1x, D1y, p, m);
+  }
+}
+
 __global__ void __launch_bounds__(512) k_leaf_down(GridDims g, int nleaf, const int *__restrict__ origin,
                                                    const double *__restrict__ SlT, int ldS, int64_t strS,
                                                    int identity, const double *__restrict__ wleaf,
@@ -515,7 +577,18 @@ int sweep(hps_handle *H, const OpSet &ops, const Combo &rhs, double *Rsave, doub
   const int lpc = leaf_lpc(q);
   const int lthreads = std::min(512, ((lpc * q + 31) / 32) * 32);
   const unsigned lgrid = (unsigned)((leaf.nodes + lpc - 1) / lpc);
-  {
+  if (H->fd.on && H->batch.fast_diag && !ops.identity) {
+    const size_t smem = (size_t)(2 * p * p + 5 * H->m * H->m + 2 * lpc * q) * sizeof(double);
+    static size_t set = 0;
+    if (smem > 48 * 1024 && smem > set) {
+      cudaFuncSetAttribute(k_leaf_up_fd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      set = smem;
+    }
+    H->trace.begin(kLeafUp, st);
+    k_leaf_up_fd<<<lgrid, lthreads, smem, st>>>(H->g, leaf.nodes, leaf.d_origin, rhs, Rsave, H->fd.d64, H->fd.mp,
+                                                H->d_D, H->wleaf, H->h[L]);
+    H->trace.end(kLeafUp, st);
+  } else {
     const size_t smem = (size_t)(2 * p * p + 2 * lpc * q) * sizeof(double);
     H->trace.begin(kLeafUp, st);
     k_leaf_up<<<lgrid, lthreads, smem, st>>>(H->g, leaf.nodes, leaf.d_origin, rhs, Rsave, ops.Ainv, ops.ldA, ops.strA,
