@@ -172,6 +172,41 @@ def leaf_up_flops(N_int, q, b, m, nterms):
     return nleaf * (2 * q * q + 2 * q * nterms + 2 * b * m)
 
 
+def tree_levels(n1, n2, m):
+    """(nodes, n3, nb) of every merge level, root first: boxes split across the longer side
+    (ties: a vertical cut), interface n3 = short side x m, box boundary nb = 2 (a + c) m."""
+    out, a, c, nodes = [], n1, n2, 1
+    while a * c > 1:
+        if a >= c:
+            out.append((nodes, c * m, 2 * (a + c) * m))
+            a //= 2
+        else:
+            out.append((nodes, a * m, 2 * (a + c) * m))
+            c //= 2
+        nodes *= 2
+    return out
+
+
+def merge_flops_per_launch(slot, n1, n2, m, cols):
+    """Average flops of one launch of a merge apply (one launch per level): w3 = X d (2 n3^2),
+    h = hcat + Tcat w3 (2 nb n3, not at the root), u3 = S u_b + w3 (2 n3 nb), per node and column."""
+    lv = tree_levels(n1, n2, m)
+    if slot == "merge_up_w3":
+        per = [nodes * 2 * n3 * n3 for nodes, n3, nb in lv]
+    elif slot == "merge_up_h":
+        per = [nodes * 2 * nb * n3 for nodes, n3, nb in lv[1:]]
+    else:
+        per = [nodes * 2 * n3 * nb for nodes, n3, nb in lv]
+    return cols * sum(per) / max(1, len(per))
+
+
+def fd_leaf_flops(N_int, q, b, m, nterms):
+    """FP64 flops of one fast-diagonalization leaf apply: the right-hand-side combination
+    (2 q nterms), four m-point line passes (8 m^3), the eigenvalue scaling (q) and the edge
+    fluxes (2 b m), per leaf."""
+    return N_int // q * (2 * q * nterms + 8 * m ** 3 + q + 2 * b * m)
+
+
 def residual_flops(p, first):
     """FP64 flops of the collocation residual R - (u - gamma dt L u) on one leaf and column, as the
     even-odd kernel evaluates it (p even): the symmetric / antisymmetric line sums (2 m p), per
@@ -436,7 +471,12 @@ def bench_ours(args, rank, world, local_rank):
                     "avg_launch_ms": run["dom_avg_ms"]}
             fl, pk, src = None, None, None
             if dom == "leaf_up" and not mixed:
-                fl, pk, src = leaf_up_flops(N_int, q, b, m, 11), peak_fp64, "FP64"
+                fl = (fd_leaf_flops(N_int, q, b, m, 11) if S.batch_option("fast_diag") and not S.nodal
+                      else leaf_up_flops(N_int, q, b, m, 11))
+                pk, src = peak_fp64, "FP64"
+            elif dom in ("merge_up_w3", "merge_up_h", "merge_down"):  # latency-bound applies, average launch
+                fl = merge_flops_per_launch(dom, wl.n1, wl.n2, m, R if mixed else 1)
+                pk, src = (peak_fp32, "FP32") if mixed else (peak_fp64, "FP64")
             elif dom == "leaf_up" and mixed:
                 fl, pk, src = nleaf * 2 * q * q * R, peak_fp32, "FP32"
             elif dom == "residual" and mixed:  # FP64 residual by the even-odd evaluation of L u
