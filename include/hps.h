@@ -291,7 +291,9 @@ enum {
   HPS_OPT_FAST_DIAG = 12,       /* 1: constant-coefficient leaf solves by fast diagonalization
                                    (when the handle's 1-D operators have a real, well-conditioned
                                    eigen-decomposition; default 1)                                */
-  HPS_OPT_COUNT = 13
+  HPS_OPT_PLAN_TILE_COLS = 13,  /* merge applies: columns per thread register tile, 8, 4 or 2 (2:
+                                   more threads per level, the chain is latency-bound)            */
+  HPS_OPT_COUNT = 14
 };
 int hps_batch_set_option(hps_handle *h, int opt, int value);
 
@@ -306,13 +308,13 @@ int hps_batch_get_option(hps_handle *h, int opt, int *value);
 
 /* One configuration tried by hps_batch_autotune and its time. */
 typedef struct hps_tune_result {
-  int tensor_leaf, flow_levels, plan_target, plan_kmin;
+  int tile_cols, flow_levels, plan_target, plan_kmin;
   float ms; /* device time of one hps_solve_batch with this configuration (mean of 3) */
 } hps_tune_result;
 
 /* Times hps_solve_batch (R columns, `refine` sweeps, synthetic right-hand sides) under each
- * candidate configuration of the options above on this handle's own operators, keeps the
- * fastest and reports every candidate in `results` (up to max_results, count in *n_results;
+ * candidate configuration (merge tile columns x dataflow levels x split-K plan) of the options
+ * above on this handle's own operators, keeps the fastest and reports every candidate in `results` (up to max_results, count in *n_results;
  * either may be NULL).  Needs hps_batch_reserve(R) first; allocates and frees its own test
  * vectors; synchronizes the device. */
 int hps_batch_autotune(hps_handle *h, int R, int refine, hps_stream_t stream, hps_tune_result *results,

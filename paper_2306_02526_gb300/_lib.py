@@ -49,13 +49,13 @@ class hps_job_stats(ctypes.Structure):
 
 
 class hps_tune_result(ctypes.Structure):
-    _fields_ = [("tensor_leaf", ctypes.c_int), ("flow_levels", ctypes.c_int), ("plan_target", ctypes.c_int),
+    _fields_ = [("tile_cols", ctypes.c_int), ("flow_levels", ctypes.c_int), ("plan_target", ctypes.c_int),
                 ("plan_kmin", ctypes.c_int), ("ms", ctypes.c_float)]
 
 
 BATCH_OPTIONS = ("tensor_leaf", "even_odd", "flow_levels", "flow_n3_max", "cluster_splitk", "plan_target",
                  "plan_kmin", "plan_npc_max", "split_rhs", "fp64_ctas_per_sm", "group_offset", "last_cta_sum",
-                 "fast_diag")
+                 "fast_diag", "plan_tile_cols")
 
 
 class hps_server_stats(ctypes.Structure):

@@ -206,10 +206,18 @@ __device__ __forceinline__ void gather_box(const GridDims &g, int ix, int iy, in
 template <int TC>
 __device__ __forceinline__ void tile_fma(float (&acc)[4][TC], const float4 a, const float *x) {
   float xv[TC];
+  if constexpr (TC % 4 == 0) {
 #pragma unroll
-  for (int t = 0; t < TC; t += 4) {
-    const float4 v = *reinterpret_cast<const float4 *>(x + t);
-    xv[t] = v.x; xv[t + 1] = v.y; xv[t + 2] = v.z; xv[t + 3] = v.w;
+    for (int t = 0; t < TC; t += 4) {
+      const float4 v = *reinterpret_cast<const float4 *>(x + t);
+      xv[t] = v.x; xv[t + 1] = v.y; xv[t + 2] = v.z; xv[t + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < TC; t += 2) {
+      const float2 v = *reinterpret_cast<const float2 *>(x + t);
+      xv[t] = v.x; xv[t + 1] = v.y;
+    }
   }
 #pragma unroll
   for (int t = 0; t < TC; ++t) {
@@ -759,7 +767,7 @@ size_t b_smem_floats(const BPlan &P) {  // operator tile(s) + vector chunk
 // Split-K plan of one level apply.  Tunables (handle options): the CTAs aimed at (target), the
 // smallest K chunk of a split (kmin) and the most nodes one CTA takes (npc_max).
 struct PlanTune {
-  int kmin, npc_max;
+  int kmin, npc_max, tc;  // tc: register-tile columns (8 or 4)
 };
 
 BPlan plan_b(int M, int K, int nodes, int R, int target, bool shared_op, PlanTune tune) {
@@ -770,7 +778,7 @@ BPlan plan_b(int M, int K, int nodes, int R, int target, bool shared_op, PlanTun
   P.nodes = nodes;
   P.R = R;
   P.Rp = round4(R);
-  P.TC = P.Rp % 8 == 0 ? 8 : 4;
+  P.TC = tune.tc == 2 ? 2 : P.Rp % 8 == 0 && tune.tc == 8 ? 8 : 4;
   P.MQ = (M + 3) / 4;
   P.CG = P.Rp / P.TC;
   const int per = P.MQ * P.CG;
@@ -797,7 +805,9 @@ BPlan plan_b(int M, int K, int nodes, int R, int target, bool shared_op, PlanTun
 }
 
 int plan_target(const hps_handle *H) { return H->batch.plan_target * H->num_sms; }
-PlanTune plan_tune(const hps_handle *H) { return PlanTune{H->batch.plan_kmin, H->batch.plan_npc_max}; }
+PlanTune plan_tune(const hps_handle *H) {
+  return PlanTune{H->batch.plan_kmin, H->batch.plan_npc_max, H->batch.plan_tile_cols};
+}
 
 struct BXDiff {  // d = h^b_3 - h^a_3 (+ interface right-hand side)
   const float *hC;
@@ -859,6 +869,17 @@ struct BEStore {
     for (int t = 0; t < TC; ++t)
       if (j0 + t < R) o[t] = v[t];
   }
+  // unsplit applies: the additive part is loaded into the accumulators before the product
+  // (its latency hides behind the arithmetic) and `store` writes the finished row
+  template <int TC>
+  __device__ void init(int, int, int, float (&a)[TC]) const {
+#pragma unroll
+    for (int t = 0; t < TC; ++t) a[t] = 0.f;
+  }
+  template <int TC>
+  __device__ void store(int k, int r, int j0, const float (&v)[TC]) const {
+    row<TC>(k, r, j0, v);
+  }
 };
 struct BEFlux {
   const int *hsrc;
@@ -875,6 +896,19 @@ struct BEFlux {
 #pragma unroll
     for (int t = 0; t < TC; ++t)
       if (j0 + t < R) o[t] = src[t] + v[t];
+  }
+  template <int TC>
+  __device__ void init(int k, int r, int j0, float (&a)[TC]) const {
+    const float *src = hC + ((int64_t)(2 * k) * nbc + hsrc[r]) * R + j0;
+#pragma unroll
+    for (int t = 0; t < TC; ++t) a[t] = j0 + t < R ? src[t] : 0.f;
+  }
+  template <int TC>
+  __device__ void store(int k, int r, int j0, const float (&v)[TC]) const {
+    float *o = h + ((int64_t)k * nb + r) * R + j0;
+#pragma unroll
+    for (int t = 0; t < TC; ++t)
+      if (j0 + t < R) o[t] = v[t];
   }
 };
 struct BEScatter {  // interface values: FP32 for the levels below, and into the FP64 solution
@@ -900,6 +934,22 @@ struct BEScatter {  // interface values: FP32 for the levels below, and into the
         const float x = v[t] + w[t];
         gv[i0 + t] = x;
         u_out(uo, i0 + t, x);
+      }
+  }
+  template <int TC>
+  __device__ void init(int k, int r, int j0, float (&acc)[TC]) const {
+    const float *w = w3 + ((int64_t)k * n3 + r) * R + j0;
+#pragma unroll
+    for (int t = 0; t < TC; ++t) acc[t] = j0 + t < R ? w[t] : 0.f;
+  }
+  template <int TC>
+  __device__ void store(int k, int r, int j0, const float (&v)[TC]) const {
+    const int64_t i0 = iface_bd(g, origin[2 * k], origin[2 * k + 1], a, c, split, r) * R + j0;
+#pragma unroll
+    for (int t = 0; t < TC; ++t)
+      if (j0 + t < R) {
+        gv[i0 + t] = v[t];
+        u_out(uo, i0 + t, v[t]);
       }
   }
 };
@@ -959,6 +1009,10 @@ __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict
   for (int e = 0; e < 4; ++e)
 #pragma unroll
     for (int t = 0; t < TC; ++t) acc[e][t] = 0.f;
+  if (live && P.ksplit == 1)
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (r0 + e < P.M) ep.template init<TC>(node0 + lo, r0 + e, j0, acc[e]);
   if (live)
     smem_fma<TC>(acc, As + (size_t)(P.shared_op ? 0 : lo) * klen * trows + (r0 - rlo), trows, klen,
                  xs + (int64_t)lo * klen * Rp + j0, Rp);
@@ -969,12 +1023,12 @@ __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict
       const int r = r0 + e;
       if (r >= P.M) continue;
       if (P.ksplit == 1) {
-        ep.template row<TC>(k, r, j0, acc[e]);
+        ep.template store<TC>(k, r, j0, acc[e]);
       } else {
         float *dst = partial + (((int64_t)ks * P.nodes + k) * P.M + r) * Rp + j0;
 #pragma unroll
-        for (int t = 0; t < TC; t += 4)
-          *reinterpret_cast<float4 *>(dst + t) = make_float4(acc[e][t], acc[e][t + 1], acc[e][t + 2], acc[e][t + 3]);
+        for (int t = 0; t < TC; t += 2)
+          *reinterpret_cast<float2 *>(dst + t) = make_float2(acc[e][t], acc[e][t + 1]);
       }
     }
   if (P.ksplit == 1 || !tile_count) return;
@@ -1035,6 +1089,7 @@ int launch_b(hps_handle *H, BatchWork &B, int slot, const BPlan &P, const float 
   if (smem > 48 * 1024 && smem > set) {
     cudaFuncSetAttribute(k_b_gemv<8, XL, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(k_b_gemv<4, XL, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_b_gemv<2, XL, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     set = smem;
   }
   H->trace.begin(slot, st);
@@ -1045,8 +1100,10 @@ int launch_b(hps_handle *H, BatchWork &B, int slot, const BPlan &P, const float 
   unsigned *tc = in_kernel ? B.tile_count : nullptr;
   if (P.TC == 8)
     k_b_gemv<8, XL, EP><<<grid, kBT, smem, st>>>(P, AT, ld, str, xl, ep, B.partial32, tc);
-  else
+  else if (P.TC == 4)
     k_b_gemv<4, XL, EP><<<grid, kBT, smem, st>>>(P, AT, ld, str, xl, ep, B.partial32, tc);
+  else
+    k_b_gemv<2, XL, EP><<<grid, kBT, smem, st>>>(P, AT, ld, str, xl, ep, B.partial32, tc);
   if (P.ksplit > 1 && !in_kernel) {
     const int64_t n = (int64_t)P.nodes * P.M * (P.Rp / 4);
     k_b_reduce<EP><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, B.partial32, ep);
@@ -2344,12 +2401,15 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
     case HPS_OPT_GROUP_OFFSET: flag = &Bt.offset_groups; break;
     case HPS_OPT_LAST_CTA_SUM: field = &Bt.last_cta_max_split; break;
     case HPS_OPT_FAST_DIAG: flag = &Bt.fast_diag; break;
+    case HPS_OPT_PLAN_TILE_COLS: field = &Bt.plan_tile_cols; break;
     default: return HPS_EINVAL;
   }
   if (get) *get = field ? *field : (*flag ? 1 : 0);
   if (!set) return HPS_OK;
   const int v = *set;
-  const bool plan = opt == HPS_OPT_PLAN_TARGET || opt == HPS_OPT_PLAN_KMIN || opt == HPS_OPT_PLAN_NPC_MAX;
+  const bool plan = opt == HPS_OPT_PLAN_TARGET || opt == HPS_OPT_PLAN_KMIN || opt == HPS_OPT_PLAN_NPC_MAX ||
+                    opt == HPS_OPT_PLAN_TILE_COLS;
+  if (opt == HPS_OPT_PLAN_TILE_COLS && *set != 2 && *set != 4 && *set != 8) return HPS_EINVAL;
   if (v < 0 || (plan && v < 1) || (opt == HPS_OPT_FLOW_LEVELS && v > kFlowMaxLevels)) return HPS_EINVAL;
   if (field) *field = v;
   else *flag = v != 0;
@@ -2395,12 +2455,12 @@ int batch_autotune(hps_handle *H, int R, int refine, cudaStream_t st, hps_tune_r
     return cleanup(HPS_ENOMEM);
   k_tune_fill<<<blocks(g.N_int * R), 256, 0, st>>>(rhs, g.N_int * R);
   cudaMemsetAsync(f, 0, (size_t)g.N_bd * R * sizeof(double), st);
-  struct Cand { int tensor, flow, target, kmin; };
+  struct Cand { int tile, flow, target, kmin; };
   std::vector<Cand> cands;
-  for (int tensor : {1, 0})
+  for (int tile : {2, 8})
     for (int flow : {0, 3})
       for (const auto &tk : {std::pair<int, int>{2, 32}, std::pair<int, int>{4, 16}})
-        cands.push_back({tensor, flow, tk.first, tk.second});
+        cands.push_back({tile, flow, tk.first, tk.second});
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -2408,8 +2468,8 @@ int batch_autotune(hps_handle *H, int R, int refine, cudaStream_t st, hps_tune_r
   int nres = 0, ibest = -1;
   for (size_t i = 0; i < cands.size(); ++i) {
     const Cand &c = cands[i];
-    const int vals[4] = {c.tensor, c.flow, c.target, c.kmin};
-    const int opts[4] = {HPS_OPT_TENSOR_LEAF, HPS_OPT_FLOW_LEVELS, HPS_OPT_PLAN_TARGET, HPS_OPT_PLAN_KMIN};
+    const int vals[4] = {c.tile, c.flow, c.target, c.kmin};
+    const int opts[4] = {HPS_OPT_PLAN_TILE_COLS, HPS_OPT_FLOW_LEVELS, HPS_OPT_PLAN_TARGET, HPS_OPT_PLAN_KMIN};
     int e = HPS_OK;
     for (int k = 0; k < 4 && e == HPS_OK; ++k) e = batch_option(H, opts[k], &vals[k], nullptr);
     for (int w = 0; w < 2 && e == HPS_OK; ++w) e = solve_batch(H, R, rhs, f, u, refine, st);
@@ -2424,7 +2484,7 @@ int batch_autotune(hps_handle *H, int R, int refine, cudaStream_t st, hps_tune_r
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     ms /= 3.f;
-    if (res && nres < max_res) res[nres] = hps_tune_result{c.tensor, c.flow, c.target, c.kmin, ms};
+    if (res && nres < max_res) res[nres] = hps_tune_result{c.tile, c.flow, c.target, c.kmin, ms};
     if (res && nres < max_res) ++nres;
     if (ms < best) {
       best = ms;
@@ -2434,8 +2494,8 @@ int batch_autotune(hps_handle *H, int R, int refine, cudaStream_t st, hps_tune_r
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   const Cand &c = cands[ibest];
-  const int vals[4] = {c.tensor, c.flow, c.target, c.kmin};
-  const int opts[4] = {HPS_OPT_TENSOR_LEAF, HPS_OPT_FLOW_LEVELS, HPS_OPT_PLAN_TARGET, HPS_OPT_PLAN_KMIN};
+  const int vals[4] = {c.tile, c.flow, c.target, c.kmin};
+  const int opts[4] = {HPS_OPT_PLAN_TILE_COLS, HPS_OPT_FLOW_LEVELS, HPS_OPT_PLAN_TARGET, HPS_OPT_PLAN_KMIN};
   for (int k = 0; k < 4; ++k) batch_option(H, opts[k], &vals[k], nullptr);
   if (n_res) *n_res = nres;
   return cleanup(HPS_OK);

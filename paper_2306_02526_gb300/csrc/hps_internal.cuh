@@ -169,6 +169,7 @@ struct Batch {
   int plan_target = 2;       // split-K plans: CTAs per SM aimed at
   int plan_kmin = 32;        // split-K plans: smallest K chunk
   int plan_npc_max = 1 << 30;  // split-K plans: most nodes per CTA
+  int plan_tile_cols = 2;    // merge applies: register-tile columns per thread (8, 4 or 2)
   bool tensor_leaf = true;   // shared leaf operator applied by 3xTF32 warp MMA (else FP32 FFMA)
   unsigned *afrag_hi = nullptr, *afrag_lo = nullptr;  // its TF32 fragments
   OpSet32 impl32, ident32;

@@ -216,7 +216,7 @@ class HPSSolver:
         n = ctypes.c_int()
         check(lib().hps_batch_autotune(self._h, int(R), int(refine), _stream_ptr(stream), res, 32, ctypes.byref(n)),
               "hps_batch_autotune")
-        return [{"tensor_leaf": r.tensor_leaf, "flow_levels": r.flow_levels, "plan_target": r.plan_target,
+        return [{"tile_cols": r.tile_cols, "flow_levels": r.flow_levels, "plan_target": r.plan_target,
                  "plan_kmin": r.plan_kmin, "ms": r.ms} for r in res[:n.value]]
 
     def solve_batch(self, rhs, f=None, u=None, refine=2, stream=None):
