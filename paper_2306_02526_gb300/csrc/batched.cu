@@ -2047,9 +2047,10 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
         H->g, R, leaf.d_origin, o32.Sleaf.p, o32.Sleaf.ld, o32.Sleaf.str, ops.identity ? 1 : 0, B.w32, B.g32, uo);
   else if (H->shared && !ops.identity && (size_t)(b * o32.Sleaf.ld + (b + q) * Rp) * sizeof(float) <= 110 * 1024) {
     const size_t smem = (size_t)(b * o32.Sleaf.ld + (b + q) * Rp) * sizeof(float);
-    auto kern = tc8 ? k_b_leaf_down_res<8> : k_b_leaf_down_res<4>;
+    const bool t8 = tc8;
+    auto kern = t8 ? k_b_leaf_down_res<8> : k_b_leaf_down_res<4>;
     static size_t set8 = 0, set4 = 0;
-    size_t &set = tc8 ? set8 : set4;
+    size_t &set = t8 ? set8 : set4;
     if (smem > 48 * 1024 && smem > set) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       set = smem;
