@@ -872,12 +872,12 @@ struct BEStore {
   // unsplit applies: the additive part is loaded into the accumulators before the product
   // (its latency hides behind the arithmetic) and `store` writes the finished row
   template <int TC>
-  __device__ void init(int, int, int, float (&a)[TC]) const {
+  __device__ void init(int, int, int, float (&a)[TC], double (&)[TC]) const {
 #pragma unroll
     for (int t = 0; t < TC; ++t) a[t] = 0.f;
   }
   template <int TC>
-  __device__ void store(int k, int r, int j0, const float (&v)[TC]) const {
+  __device__ void store(int k, int r, int j0, const float (&v)[TC], const double (&)[TC]) const {
     row<TC>(k, r, j0, v);
   }
 };
@@ -898,13 +898,13 @@ struct BEFlux {
       if (j0 + t < R) o[t] = src[t] + v[t];
   }
   template <int TC>
-  __device__ void init(int k, int r, int j0, float (&a)[TC]) const {
+  __device__ void init(int k, int r, int j0, float (&a)[TC], double (&)[TC]) const {
     const float *src = hC + ((int64_t)(2 * k) * nbc + hsrc[r]) * R + j0;
 #pragma unroll
     for (int t = 0; t < TC; ++t) a[t] = j0 + t < R ? src[t] : 0.f;
   }
   template <int TC>
-  __device__ void store(int k, int r, int j0, const float (&v)[TC]) const {
+  __device__ void store(int k, int r, int j0, const float (&v)[TC], const double (&)[TC]) const {
     float *o = h + ((int64_t)k * nb + r) * R + j0;
 #pragma unroll
     for (int t = 0; t < TC; ++t)
@@ -937,19 +937,24 @@ struct BEScatter {  // interface values: FP32 for the levels below, and into the
       }
   }
   template <int TC>
-  __device__ void init(int k, int r, int j0, float (&acc)[TC]) const {
+  __device__ void init(int k, int r, int j0, float (&acc)[TC], double (&old)[TC]) const {
     const float *w = w3 + ((int64_t)k * n3 + r) * R + j0;
 #pragma unroll
     for (int t = 0; t < TC; ++t) acc[t] = j0 + t < R ? w[t] : 0.f;
+    if (!uo.assign) {  // the correction adds to u: fetch the old values now
+      const double *u0 = uo.u + iface_bd(g, origin[2 * k], origin[2 * k + 1], a, c, split, r) * R + j0;
+#pragma unroll
+      for (int t = 0; t < TC; ++t) old[t] = j0 + t < R ? u0[t] : 0.0;
+    }
   }
   template <int TC>
-  __device__ void store(int k, int r, int j0, const float (&v)[TC]) const {
+  __device__ void store(int k, int r, int j0, const float (&v)[TC], const double (&old)[TC]) const {
     const int64_t i0 = iface_bd(g, origin[2 * k], origin[2 * k + 1], a, c, split, r) * R + j0;
 #pragma unroll
     for (int t = 0; t < TC; ++t)
       if (j0 + t < R) {
         gv[i0 + t] = v[t];
-        u_out(uo, i0 + t, v[t]);
+        uo.u[i0 + t] = uo.assign ? (double)v[t] : old[t] + (double)v[t];
       }
   }
 };
@@ -1009,10 +1014,11 @@ __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict
   for (int e = 0; e < 4; ++e)
 #pragma unroll
     for (int t = 0; t < TC; ++t) acc[e][t] = 0.f;
+  double aux[4][TC];
   if (live && P.ksplit == 1)
 #pragma unroll
     for (int e = 0; e < 4; ++e)
-      if (r0 + e < P.M) ep.template init<TC>(node0 + lo, r0 + e, j0, acc[e]);
+      if (r0 + e < P.M) ep.template init<TC>(node0 + lo, r0 + e, j0, acc[e], aux[e]);
   if (live)
     smem_fma<TC>(acc, As + (size_t)(P.shared_op ? 0 : lo) * klen * trows + (r0 - rlo), trows, klen,
                  xs + (int64_t)lo * klen * Rp + j0, Rp);
@@ -1023,7 +1029,7 @@ __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict
       const int r = r0 + e;
       if (r >= P.M) continue;
       if (P.ksplit == 1) {
-        ep.template store<TC>(k, r, j0, acc[e]);
+        ep.template store<TC>(k, r, j0, acc[e], aux[e]);
       } else {
         float *dst = partial + (((int64_t)ks * P.nodes + k) * P.M + r) * Rp + j0;
 #pragma unroll
