@@ -438,6 +438,7 @@ def bench_ours(args, rank, world, local_rank):
         host_out = torch.empty_like(host_in).pin_memory()
         ms = []
         for k in range(max(5, min(args.steps, 20)) + 2):
+            flush.fill_(float(k))  # L2 flushed before every step, as in the device-timed runs
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)

@@ -293,7 +293,10 @@ enum {
                                    eigen-decomposition; default 1)                                */
   HPS_OPT_PLAN_TILE_COLS = 13,  /* merge applies: columns per thread register tile, 8, 4 or 2 (2:
                                    more threads per level, the chain is latency-bound)            */
-  HPS_OPT_COUNT = 14
+  HPS_OPT_FUSE_EPILOGUE = 14,   /* 1: the stage epilogue of a pointwise g (dt L U_i from the stage
+                                   equation, dt (q_i + g(U_i))) is written by the last leaf kernel
+                                   of the stage solve instead of its own pass (default 1)          */
+  HPS_OPT_COUNT = 15
 };
 int hps_batch_set_option(hps_handle *h, int opt, int value);
 

@@ -32,6 +32,30 @@ __device__ __forceinline__ void u_out(const UOut &U, int64_t i, float v) {
   U.u[i] = U.assign ? (double)v : U.u[i] + (double)v;
 }
 
+// Stage epilogue of an implicit ARK stage (Eq. 2.3-2.4 split): from the solved stage value
+// U_i (interior point o of an [N][R] vector) the implicit derivative dt L U_i is recovered
+// from the stage equation U_i - gamma dt L U_i = Rb_i as (U_i - Rb_i) / gamma, and the
+// explicit one is dt (q_i + g(U_i)); only g without derivatives (pointwise) takes this form.
+struct StageEpi {
+  int on;
+  const double *Rb;     // [N_int][R] stage right-hand side
+  double *KL, *KE;      // [N_int][R] outputs
+  const double *q;      // [N_int][qld] (columns qoff ..) or null
+  int qld, qoff, g_kind;
+  double inv_gamma, dt, gp0;
+};
+__device__ __forceinline__ void stage_epi_point(const StageEpi &E, int R, int64_t o, double uu) {
+  double e;
+  switch (E.g_kind) {
+    case HPS_G_ALLEN_CAHN: e = E.gp0 * (uu - uu * uu * uu); break;
+    case HPS_G_FISHER: e = E.gp0 * uu * (1.0 - uu); break;
+    default: e = 0.0;
+  }
+  if (E.q) e += E.q[(o / R) * E.qld + E.qoff + o % R];
+  E.KL[o] = (uu - E.Rb[o]) * E.inv_gamma;
+  E.KE[o] = E.dt * e;
+}
+
 // Block-wide loop over [0, n): every thread issues U independent loads before it uses any of
 // them (a warp issues in order, so a load-then-store loop would wait out one load latency per
 // element).
@@ -636,7 +660,7 @@ template <int TC>
 __global__ void __launch_bounds__(kBT) k_b_leaf_down_res(GridDims g, int nodes, int R, const int *__restrict__ origin,
                                                          const float *__restrict__ SlT, int ldS,
                                                          const float *__restrict__ w32, const float *__restrict__ g32,
-                                                         UOut uo) {
+                                                         UOut uo, StageEpi ep) {
   extern __shared__ __align__(16) float sres[];
   const int m = g.m, q = m * m, b = 4 * m, Rp = round4(R);
   float *Ss = sres, *ub = sres + (size_t)b * ldS, *Os = ub + b * Rp;  // [b][ldS], [b][Rp], [q][Rp]
@@ -666,9 +690,15 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_down_res(GridDims g, int nodes, 
                 make_float4(acc[e][t], acc[e][t + 1], acc[e][t + 2], acc[e][t + 3]);
     }
     __syncthreads();
-    // u_i = w + S u_b: the leaf's interior block is contiguous in both vectors
-    for (int idx = threadIdx.x; idx < q * R; idx += blockDim.x)
-      u_out(uo, l0 * R + idx, w32[(int64_t)k * q * R + idx] + Os[(idx / R) * Rp + idx % R]);
+    // u_i = w + S u_b: the leaf's interior block is contiguous in both vectors; the last sweep of
+    // a stage solve also writes the stage epilogue from the finished value
+    for (int idx = threadIdx.x; idx < q * R; idx += blockDim.x) {
+      const int64_t o = l0 * R + idx;
+      const float v = w32[(int64_t)k * q * R + idx] + Os[(idx / R) * Rp + idx % R];
+      const double un = uo.assign ? (double)v : uo.u[o] + (double)v;
+      uo.u[o] = un;
+      if (ep.on) stage_epi_point(ep, R, o, un);
+    }
   }
 }
 
@@ -1719,15 +1749,8 @@ __global__ void k_b_pointwise(int64_t n, Leaf64Args A) {
     A.out0[o] = A.Rb[o] - uu;
     return;
   }
-  double e;
-  switch (A.g_kind) {
-    case HPS_G_ALLEN_CAHN: e = A.gp0 * (uu - uu * uu * uu); break;
-    case HPS_G_FISHER: e = A.gp0 * uu * (1.0 - uu); break;
-    default: e = 0.0;
-  }
-  if (A.q) e += A.q[(o / A.R) * A.qld + A.qoff + o % A.R];
-  A.out0[o] = (uu - A.Rb[o]) * A.inv_gamma;
-  A.out1[o] = A.dt * e;
+  const StageEpi E{1, A.Rb, A.out0, A.out1, A.q, A.qld, A.qoff, A.g_kind, A.inv_gamma, A.dt, A.gp0};
+  stage_epi_point(E, A.R, o, uu);
 }
 
 // r = -(flux from the west/south leaf - flux from the east/north leaf) at every shared edge point
@@ -1884,7 +1907,8 @@ int flow_launch(hps_handle *H, BatchWork &B, const FlowArgs &FA, bool up, size_t
 // One FP32 sweep on R columns: leaf applies, merges up (with an optional FP64 interface
 // right-hand side), merges down into g32 (whose outer boundary the caller has set), leaf solves.
 int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, int R, const Combo &rhs,
-            double *Rsave, const double *jump, UOut uo, bool allow_tc, cudaStream_t st) {
+            double *Rsave, const double *jump, UOut uo, bool allow_tc, cudaStream_t st, const StageEpi &ep,
+            bool &epi_done) {
   const int L = H->L, p = H->p, q = H->q, b = H->b, Rp = round4(R);
   const Level &leaf = H->lev[L];
   const bool tc8 = Rp % 8 == 0;
@@ -2065,7 +2089,8 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBT, smem) != cudaSuccess || per_sm < 1)
       return HPS_ECUDA;
     kern<<<std::min(leaf.nodes, per_sm * H->num_sms), kBT, smem, st>>>(H->g, leaf.nodes, R, leaf.d_origin,
-                                                                      o32.Sleaf.p, o32.Sleaf.ld, B.w32, B.g32, uo);
+                                                                      o32.Sleaf.p, o32.Sleaf.ld, B.w32, B.g32, uo, ep);
+    epi_done = ep.on != 0;
   } else {
     const int staged = (size_t)(b + q) * Rp * sizeof(float) <= 96 * 1024;  // coalesced output through smem
     const size_t smem = (size_t)(staged ? b + q : b) * Rp * sizeof(float);
@@ -2167,8 +2192,12 @@ struct BdView {
 };
 
 // Solve A u = [rhs (given by combination `c`, saved to Rsave if non-null); 0; f] with refinement.
+// The last sweep writes the stage epilogue `ep` too where its leaf kernel can (epi_done).
 int refined_solve(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, int R, const Combo &c,
-                  double *Rsave, const double *Rb, BdView f, double *u, int refine, double gdt, cudaStream_t st) {
+                  double *Rsave, const double *Rb, BdView f, double *u, int refine, double gdt, cudaStream_t st,
+                  const StageEpi &ep, bool &epi_done) {
+  const StageEpi none{};
+  epi_done = false;
   const GridDims &g = H->g;
   H->trace.begin(kSetBoundary, st);
   k_b_set_boundary32<<<blocks(g.N_bd * R), 256, 0, st>>>(g, R, B.g32, f.f, f.ld, f.off, u);
@@ -2178,7 +2207,9 @@ int refined_solve(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &
   // the first sweep may take the 3xTF32 tensor-core leaf apply (its rounding is slightly coarser
   // than FP32 and biased); corrections use the FP32 FMA path, so the refined result keeps FP32
   // times FP32 accuracy
-  if (int e = sweep32(H, B, ops, o32, R, c, Rsave, nullptr, UOut{u, 1}, true, st)) return e;
+  if (int e = sweep32(H, B, ops, o32, R, c, Rsave, nullptr, UOut{u, 1}, true, st, refine == 0 ? ep : none,
+                      epi_done))
+    return e;
   for (int it = 0; it < refine; ++it) {
     if (int e = residual(H, B, R, u, Rb, gdt, st)) return e;
     H->trace.begin(kSetBoundary, st);
@@ -2188,7 +2219,9 @@ int refined_solve(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &
     cr.n = 1;
     cr.ptr[0] = B.r;
     cr.coef[0] = 1.0;
-    if (int e = sweep32(H, B, ops, o32, R, cr, nullptr, B.r, UOut{u, 0}, false, st)) return e;
+    if (int e = sweep32(H, B, ops, o32, R, cr, nullptr, B.r, UOut{u, 0}, false, st, it == refine - 1 ? ep : none,
+                        epi_done))
+      return e;
   }
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
@@ -2252,15 +2285,21 @@ int ark_group(hps_handle *H, BatchWork &B, int R, double *u, double dt, const hp
       add_term_b(c, B.KE + j * ni, tb.Ah[i][j]);
     }
     const BdView fv{f ? f + i * fstage : nullptr, fld, foff};
+    const double *qi = q ? q + i * qstage : nullptr;
+    // a pointwise g lets the last leaf kernel of the solve write the epilogue
+    const bool fuse = H->batch.fuse_epilogue && gk != HPS_G_BURGERS;
+    const StageEpi ep{fuse ? 1 : 0, B.Rb, B.KL + i * ni, B.KE + i * ni, qi, qld, qoff, gk, 1.0 / tb.A[1][1], dt, gp0};
+    bool done = false;
     if (int e = refined_solve(H, B, H->impl, H->batch.impl32, R, c, B.Rb, B.Rb, fv, B.ustage, refine, H->gamma_dt,
-                              st))
+                              st, ep, done))
       return e;
+    if (done) continue;
     Leaf64Args P = leaf64_args(H, kEpilogue, R);
     P.u = B.ustage;
     P.Rb = B.Rb;
     P.out0 = B.KL + i * ni;
     P.out1 = B.KE + i * ni;
-    P.q = q ? q + i * qstage : nullptr;
+    P.q = qi;
     P.qld = qld;
     P.qoff = qoff;
     P.inv_gamma = 1.0 / tb.A[1][1];
@@ -2279,7 +2318,8 @@ int ark_group(hps_handle *H, BatchWork &B, int R, double *u, double dt, const hp
     add_term_b(c, B.KE + j * ni, tb.b[j]);
   }
   const BdView fv{f ? f + 5 * fstage : nullptr, fld, foff};
-  return refined_solve(H, B, H->ident, H->batch.ident32, R, c, B.Rb, B.Rb, fv, u, refine, 0.0, st);
+  bool done = false;
+  return refined_solve(H, B, H->ident, H->batch.ident32, R, c, B.Rb, B.Rb, fv, u, refine, 0.0, st, StageEpi{}, done);
 }
 
 // Run `body(group, c0, n, stream)` for every non-empty group: inline on `st` with one group,
@@ -2409,6 +2449,7 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
     case HPS_OPT_LAST_CTA_SUM: field = &Bt.last_cta_max_split; break;
     case HPS_OPT_FAST_DIAG: flag = &Bt.fast_diag; break;
     case HPS_OPT_PLAN_TILE_COLS: field = &Bt.plan_tile_cols; break;
+    case HPS_OPT_FUSE_EPILOGUE: flag = &Bt.fuse_epilogue; break;
     default: return HPS_EINVAL;
   }
   if (get) *get = field ? *field : (*flag ? 1 : 0);
@@ -2524,8 +2565,9 @@ int solve_batch(hps_handle *H, int R, const double *rhs, const double *f, double
     }
     Combo c{};
     add_term_b(c, rb, 1.0);
+    bool done = false;
     if (int e = refined_solve(H, W, H->impl, H->batch.impl32, n, c, nullptr, rb, BdView{f, R, c0}, uu, refine,
-                              H->gamma_dt, s))
+                              H->gamma_dt, s, StageEpi{}, done))
       return e;
     if (grouped) {
       H->trace.begin(kFinish, s);

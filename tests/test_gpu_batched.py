@@ -125,6 +125,52 @@ def test_ark_batch_varcoef_inhomogeneous_matches_fp64(gname, R, groups):
     S.close()
 
 
+@pytest.mark.parametrize("gname,groups", [("allen_cahn", 1), ("allen_cahn", 3), ("fisher", 2)])
+def test_fused_stage_epilogue_with_sources(gname, groups):
+    """Constant coefficients (the persistent leaf solve that writes the stage epilogue), stage
+    sources q and boundary data f per column, column groups reading q at their column offset:
+    the fused epilogue against the separate pass (to rounding) and against the FP64 path."""
+    torch = need_gpu()
+    from paper_2306_02526_gb300 import hps
+    n1, n2, p, dt, R = 8, 4, 10, 0.02, 10
+    g = Grid(n1, n2, p)
+    X, Y = g.coords()
+    I, bd = np.arange(g.N_int), g.boundary_indices()
+    c = hps.hps_ark_abscissae()
+    gp = (0.8, 0.0)
+    qf = lambda t, j: np.cos(X[I] + t + 0.1 * j) * np.sin(2 * Y[I])
+    ff = lambda t, j: (np.sin(X + 2 * Y - 0.2 * j) * (1 + t))[bd]
+    u0 = np.stack([0.3 * np.sin(math.pi * X) * np.cos(Y + j) for j in range(R)], axis=1)
+    for j in range(R):
+        u0[bd, j] = ff(0.0, j)
+    outs = []
+    for fuse in (1, 0):
+        S = _solver(torch, n1, n2, p, {"a11": 0.03, "a22": 0.02}, 0.25 * dt)
+        S.batch_reserve(R, groups=groups)
+        S.batch_option("fuse_epilogue", fuse)
+        ub = to_dev(torch, u0)
+        t = 0.0
+        for n in range(3):
+            qb = np.stack([np.stack([qf(t + cj * dt, j) for j in range(R)], axis=1) for cj in c])
+            fb = np.stack([np.stack([ff(t + cj * dt, j) for j in range(R)], axis=1) for cj in c])
+            S.ark_step_batch(ub, t, dt, q=to_dev(torch, qb), f=to_dev(torch, fb), g=gname, g_param=gp, refine=1)
+            t += dt
+        outs.append(ub.cpu().numpy())
+        if fuse:
+            us = [to_dev(torch, u0[:, j].copy()) for j in range(R)]
+            t = 0.0
+            for n in range(3):
+                for j in range(R):
+                    qj = np.stack([qf(t + cj * dt, j) for cj in c]).reshape(-1)
+                    fj = np.stack([ff(t + cj * dt, j) for cj in c]).reshape(-1)
+                    S.ark_step(us[j], t, dt, q=to_dev(torch, qj), f=to_dev(torch, fj), g=gname, g_param=gp)
+                t += dt
+            for j in range(R):
+                assert rel_max(outs[0][:, j], us[j].cpu().numpy()) <= TOL
+        S.close()
+    assert rel_max(outs[0], outs[1]) <= 1e-13
+
+
 def test_ark_batch_full_size_allen_cahn():
     """The bench workload (64x64 leaves, p = 16) with 8 seeded states: 2 batched mixed steps
     against the FP64 path column by column."""
@@ -216,7 +262,7 @@ def _ark_pair(torch, n1, n2, p, R, dt, opt=None, val=None, autotune=False):
                                      ("cluster_splitk", 1), ("plan_target", 4), ("plan_kmin", 8),
                                      ("plan_npc_max", 1), ("split_rhs", 1), ("fp64_ctas_per_sm", 2),
                                      ("fast_diag", 0), ("last_cta_sum", 16), ("plan_tile_cols", 8),
-                                     ("plan_tile_cols", 4), ("plan_tile_cols", 2)])
+                                     ("plan_tile_cols", 4), ("plan_tile_cols", 2), ("fuse_epilogue", 0)])
 def test_batch_option_variants_match_fp64(opt, val):
     """Every kernel variant of the batched path (handle options) gives the FP64 result to the
     mixed-precision tolerance; flow_levels = 8 puts every level of the 16 x 8 tree, root
