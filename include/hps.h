@@ -296,7 +296,11 @@ enum {
   HPS_OPT_FUSE_EPILOGUE = 14,   /* 1: the stage epilogue of a pointwise g (dt L U_i from the stage
                                    equation, dt (q_i + g(U_i))) is written by the last leaf kernel
                                    of the stage solve instead of its own pass (default 1)          */
-  HPS_OPT_COUNT = 15
+  HPS_OPT_FUSE_JUMP = 15,       /* 1: the FP64 residual's flux jumps at shared edges come from the
+                                   even-odd leaf kernel (side fluxes added into r) (default 1)     */
+  HPS_OPT_FOLD_SCALE = 16,      /* 1: constant coefficients times gamma dt (or dt) folded into the
+                                   even-odd half matrices (default 1)                              */
+  HPS_OPT_COUNT = 17
 };
 int hps_batch_set_option(hps_handle *h, int opt, int value);
 

@@ -1521,6 +1521,12 @@ struct Leaf64Args {
   int g_kind;
   double gp0, gp1;
   int need_d1, need_d2;  // first / second derivatives needed (zero terms are skipped)
+  // fold: the even-odd kernel takes the mode's scale (gamma dt or dt) times the constant
+  // coefficients into its half matrices (s1x, s1y: first, s2x, s2y: second derivatives, s0:
+  // the zeroth-order term), so its line sums are the scaled terms of L u
+  int fold;
+  double s1x, s1y, s2x, s2y, s0;
+  double *flux_r;  // kResid, even-odd kernel: the leaf adds its side fluxes into r at shared edges
 };
 
 __global__ void __launch_bounds__(kBT) k_b_leaf64(GridDims g, int nodes, const int *__restrict__ origin,
@@ -1601,6 +1607,26 @@ __global__ void __launch_bounds__(kBT) k_b_leaf64(GridDims g, int nodes, const i
 __device__ __forceinline__ void leaf64_out(const Leaf64Args &A, int64_t gi, int col, double uu, double ux, double uy,
                                            double uxx, double uyy) {
   const int64_t o = gi * A.R + col;
+  if (A.fold) {  // the derivative terms arrive scaled: their sum is gamma dt L u (kResid) or dt L u (kEval)
+    double Ls = 0.0;
+    if (A.need_d2) Ls = uxx + uyy;
+    if (A.need_d1) Ls += ux + uy;
+    if (A.s0 != 0.0) Ls = fma(A.s0, uu, Ls);
+    if (A.mode == kResid) {
+      A.out0[o] = (A.Rb[o] - uu) + Ls;
+    } else {
+      double e;
+      switch (A.g_kind) {
+        case HPS_G_ALLEN_CAHN: e = A.gp0 * (uu - uu * uu * uu); break;
+        case HPS_G_FISHER: e = A.gp0 * uu * (1.0 - uu); break;
+        default: e = 0.0;
+      }
+      if (A.q) e += A.q[gi * A.qld + A.qoff + col];
+      A.out0[o] = Ls;
+      A.out1[o] = A.dt * e;
+    }
+    return;
+  }
   double Lu = 0.0;
   if (A.mode != kEpilogue) {
     if (A.coef) {
@@ -1636,14 +1662,22 @@ __device__ __forceinline__ void leaf64_out(const Leaf64Args &A, int64_t gi, int 
 // A = (D_ik + D_i,p-1-k)/2 and B = (D_ik - D_i,p-1-k)/2: p/2 instead of p multiply-adds per
 // output.  The FP64 pipe bounds these kernels on this GPU, so the flop count is the runtime.
 // One thread takes the four mirror images (i, j), (p-1-i, j), (i, p-1-j), (p-1-i, p-1-j).
-__global__ void __launch_bounds__(kBT) k_b_leaf64_eo(GridDims g, int nodes, const int *__restrict__ origin,
+__global__ void __launch_bounds__(kBT, 3) k_b_leaf64_eo(GridDims g, int nodes, const int *__restrict__ origin,
                                                      Leaf64Args A, const double *__restrict__ Dg) {
   extern __shared__ double sd[];
   const int p = g.p, m = g.m, q = m * m, pp = p * p, h = p / 2, hh = h * h, R = A.R;
   const int Rc = max(1, min(R, 2048 / pp));
-  double *Hm = sd, *U = sd + 8 * hh;  // half matrices; U [pp][Rc]
+  double *Hm = sd, *F0 = sd + 8 * hh, *U = F0 + 4 * h;  // half matrices; unscaled row 0 of the D1 halves; U [pp][Rc]
   double *Ex = U + pp * Rc, *Ox = Ex + m * h * Rc, *Ey = Ox + m * h * Rc, *Oy = Ey + m * h * Rc;  // [m][h][Rc]
-  for (int i = threadIdx.x; i < 8 * hh; i += blockDim.x) Hm[i] = Dg[4 * pp + i];
+  for (int i = threadIdx.x; i < 8 * hh; i += blockDim.x) {
+    double v = Dg[4 * pp + i];
+    if (A.fold) {
+      const int mtx = i / (2 * hh);  // D1x, D1y, Dxx, Dyy halves in this order
+      v *= mtx == 0 ? A.s1x : mtx == 1 ? A.s1y : mtx == 2 ? A.s2x : A.s2y;
+    }
+    Hm[i] = v;
+  }
+  for (int i = threadIdx.x; i < 4 * h; i += blockDim.x) F0[i] = Dg[4 * pp + (i / h) * hh + i % h];
   const double *A1x = Hm, *B1x = Hm + hh, *A1y = Hm + 2 * hh, *B1y = Hm + 3 * hh;
   const double *Axx = Hm + 4 * hh, *Bxx = Hm + 5 * hh, *Ayy = Hm + 6 * hh, *Byy = Hm + 7 * hh;
   for (int k = blockIdx.x; k < nodes; k += gridDim.x) {
@@ -1666,7 +1700,7 @@ __global__ void __launch_bounds__(kBT) k_b_leaf64_eo(GridDims g, int nodes, cons
           },
           [&](int idx, double v) { U[(idx / rc) * Rc + idx % rc] = v; });
       __syncthreads();
-      if (A.need_d1 || A.need_d2) {
+      if (A.need_d1 || A.need_d2 || A.flux_r) {
         // symmetric / antisymmetric parts of the interior rows (x lines) and columns (y lines)
         for (int idx = threadIdx.x; idx < m * h * rc; idx += blockDim.x) {
           const int jj = idx % rc, t = idx / rc, kk = t % h, r = t / h + 1, o = t * Rc + jj;
@@ -1733,6 +1767,32 @@ __global__ void __launch_bounds__(kBT) k_b_leaf64_eo(GridDims g, int nodes, cons
         for (int pt = 0; pt < 4; ++pt) {
           const int i = (pt & 1) ? ai : a, j = (pt & 2) ? bj : b;
           leaf64_out(A, l0 + (j - 1) * m + (i - 1), j0 + jj, U[(j * p + i) * Rc + jj], x1[pt], y1[pt], xx[pt], yy[pt]);
+        }
+      }
+      if (A.flux_r) {
+        // Flux jumps at the shared edges (the interface conditions of the collocation system):
+        // the normal derivatives on this leaf's four sides are row 0 / row p-1 of D1 on the
+        // boundary lines, e + o and o - e from row 0 of the halves (D1 is centro-antisymmetric).
+        // r at a shared edge is the second leaf's (east / north) row-0 flux minus the first
+        // leaf's row-(p-1) flux; each leaf adds its signed term into r, zeroed beforehand: a sum
+        // of two terms onto zero, the same whichever leaf comes first.
+        for (int idx = threadIdx.x; idx < 2 * m * rc; idx += blockDim.x) {
+          const int jj = idx % rc, t = idx / rc, r = t % m + 1, dir = t / m;
+          const double *E = (dir ? Ey : Ex) + (r - 1) * h * Rc + jj, *O = (dir ? Oy : Ox) + (r - 1) * h * Rc + jj;
+          const double *a0 = F0 + 2 * dir * h, *b0 = a0 + h;
+          double e = 0.0, o = 0.0;
+          for (int kk = 0; kk < h; ++kk) {
+            e = fma(a0[kk], E[kk * Rc], e);
+            o = fma(b0[kk], O[kk * Rc], o);
+          }
+          const int col = j0 + jj;
+          if (dir == 0) {
+            if (ix > 0) atomicAdd(A.flux_r + vseg(g, ix, iy, r - 1) * R + col, e + o);
+            if (ix + 1 < g.n1) atomicAdd(A.flux_r + vseg(g, ix + 1, iy, r - 1) * R + col, -(o - e));
+          } else {
+            if (iy > 0) atomicAdd(A.flux_r + hseg(g, iy, ix, r - 1) * R + col, e + o);
+            if (iy + 1 < g.n2) atomicAdd(A.flux_r + hseg(g, iy + 1, ix, r - 1) * R + col, -(o - e));
+          }
         }
       }
     }
@@ -2120,7 +2180,10 @@ Leaf64Args leaf64_args(hps_handle *H, int mode, int R) {
   return A;
 }
 
-int leaf64(hps_handle *H, Leaf64Args A, cudaStream_t st) {
+// FP64 leaf pass of mode A.mode.  A.flux_r (kResid) asks the even-odd kernel for the shared-edge
+// flux jumps as well; flux_done tells whether it took them (else the caller runs k_b_jump).
+int leaf64(hps_handle *H, Leaf64Args A, cudaStream_t st, bool *flux_done = nullptr) {
+  if (flux_done) *flux_done = false;
   // which derivatives the mode needs; terms with zero constant coefficients are skipped
   const bool nodal = H->d_coef != nullptr;
   const bool L_needed = A.mode == kEval || (A.mode == kResid && A.gdt != 0.0);
@@ -2131,6 +2194,7 @@ int leaf64(hps_handle *H, Leaf64Args A, cudaStream_t st) {
   const int slot = A.mode == kResid ? kResidual : kLeafEval;
   if (!A.need_d1 && !A.need_d2 && A.mode != kEval) {
     const int64_t n = H->g.N_int * A.R;
+    A.flux_r = nullptr;
     H->trace.begin(slot, st);
     k_b_pointwise<<<blocks(n), 256, 0, st>>>(n, A);
     H->trace.end(slot, st);
@@ -2143,7 +2207,28 @@ int leaf64(hps_handle *H, Leaf64Args A, cudaStream_t st) {
   if (p % 2 == 0 && H->batch.even_odd) {
     const int h = p / 2, m = H->m;
     const int Rc = std::max(1, std::min(A.R, 2048 / pp));
-    const size_t smem = (size_t)(8 * h * h + pp * Rc + 4 * m * h * Rc) * sizeof(double);
+    const size_t smem = (size_t)(8 * h * h + 4 * h + pp * Rc + 4 * m * h * Rc) * sizeof(double);
+    // constant coefficients: scales folded into the half matrices (not for a g that needs the
+    // plain first derivatives)
+    if (!nodal && A.mode != kEpilogue && !(A.mode == kEval && A.g_kind == HPS_G_BURGERS) && H->batch.fold_scale) {
+      const double sc = A.mode == kResid ? A.gdt : A.dt;
+      A.fold = 1;
+      A.s1x = sc * H->cst[2];
+      A.s1y = sc * H->cst[3];
+      A.s2x = sc * H->cst[0];
+      A.s2y = sc * H->cst[1];
+      A.s0 = sc * H->cst[4];
+    }
+    const bool flux = A.flux_r && A.mode == kResid && H->batch.fuse_jump;
+    if (flux) {
+      const GridDims &g = H->g;
+      if (cudaMemsetAsync(A.flux_r + g.N_int * A.R, 0, (size_t)(g.N - g.N_int) * A.R * sizeof(double), st) !=
+          cudaSuccess)
+        return HPS_ECUDA;
+      if (flux_done) *flux_done = true;
+    } else {
+      A.flux_r = nullptr;
+    }
     static size_t set = 0;
     if (smem > 48 * 1024 && smem > set) {
       cudaFuncSetAttribute(k_b_leaf64_eo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -2156,6 +2241,7 @@ int leaf64(hps_handle *H, Leaf64Args A, cudaStream_t st) {
   }
   const int Rc = std::max(1, std::min(A.R, 4096 / pp));
   const size_t smem = (size_t)(4 * pp + pp * Rc) * sizeof(double);
+  A.flux_r = nullptr;
   static size_t set = 0;
   if (smem > 48 * 1024 && smem > set) {
     cudaFuncSetAttribute(k_b_leaf64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -2175,9 +2261,11 @@ int residual(hps_handle *H, BatchWork &B, int R, const double *u, const double *
   A.Rb = Rb;
   A.out0 = B.r;
   A.gdt = gdt;
-  if (int e = leaf64(H, A, st)) return e;
+  A.flux_r = B.r;
+  bool flux_done = false;
+  if (int e = leaf64(H, A, st, &flux_done)) return e;
   const int64_t npts = ((int64_t)(H->g.n1 - 1) * H->g.n2 + (int64_t)(H->g.n2 - 1) * H->g.n1) * H->m;
-  if (npts > 0) {
+  if (npts > 0 && !flux_done) {
     H->trace.begin(kJump, st);
     k_b_jump<<<blocks(npts * R), 256, 0, st>>>(H->g, R, u, B.r, H->d_D);
     H->trace.end(kJump, st);
@@ -2450,6 +2538,8 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
     case HPS_OPT_FAST_DIAG: flag = &Bt.fast_diag; break;
     case HPS_OPT_PLAN_TILE_COLS: field = &Bt.plan_tile_cols; break;
     case HPS_OPT_FUSE_EPILOGUE: flag = &Bt.fuse_epilogue; break;
+    case HPS_OPT_FUSE_JUMP: flag = &Bt.fuse_jump; break;
+    case HPS_OPT_FOLD_SCALE: flag = &Bt.fold_scale; break;
     default: return HPS_EINVAL;
   }
   if (get) *get = field ? *field : (*flag ? 1 : 0);

@@ -167,6 +167,8 @@ struct Batch {
   int last_cta_max_split = 0;   // split-K sums by the last CTA of each tile up to this split depth (0: never)
   bool fast_diag = true;     // leaf apply by fast diagonalization where the handle has it
   bool fuse_epilogue = true;  // stage epilogue written by the last leaf kernel of the stage solve
+  bool fuse_jump = true;      // residual: flux jumps from the even-odd leaf kernel (no k_b_jump)
+  bool fold_scale = true;     // even-odd leaf kernels: scales folded into the half matrices
   int plan_target = 2;       // split-K plans: CTAs per SM aimed at
   int plan_kmin = 32;        // split-K plans: smallest K chunk
   int plan_npc_max = 1 << 30;  // split-K plans: most nodes per CTA
