@@ -300,7 +300,10 @@ enum {
                                    even-odd leaf kernel (side fluxes added into r) (default 1)     */
   HPS_OPT_FOLD_SCALE = 16,      /* 1: constant coefficients times gamma dt (or dt) folded into the
                                    even-odd half matrices (default 1)                              */
-  HPS_OPT_COUNT = 17
+  HPS_OPT_SA_CLOSE = 17,        /* 1: the step close of the batched ARK step combines the last stage
+                                   value and the explicit terms (b = last row of the implicit
+                                   table), 7 instead of 13 terms (default 1)                       */
+  HPS_OPT_COUNT = 18
 };
 int hps_batch_set_option(hps_handle *h, int opt, int value);
 

@@ -52,7 +52,7 @@ __device__ __forceinline__ void stage_epi_point(const StageEpi &E, int R, int64_
     default: e = 0.0;
   }
   if (E.q) e += E.q[(o / R) * E.qld + E.qoff + o % R];
-  E.KL[o] = (uu - E.Rb[o]) * E.inv_gamma;
+  if (E.KL) E.KL[o] = (uu - E.Rb[o]) * E.inv_gamma;
   E.KE[o] = E.dt * e;
 }
 
@@ -2365,6 +2365,8 @@ int ark_group(hps_handle *H, BatchWork &B, int R, double *u, double dt, const hp
   E.gp1 = gp1;
   if (int e = leaf64(H, E, st)) return e;
   if (after_first) cudaEventRecord(after_first, st);
+  bool sa_close = H->batch.sa_close;
+  for (int j = 0; j < 6; ++j) sa_close = sa_close && tb.A[5][j] == tb.b[j];
   for (int i = 1; i < 6; ++i) {
     Combo c{};
     add_term_b(c, u, 1.0);
@@ -2376,7 +2378,9 @@ int ark_group(hps_handle *H, BatchWork &B, int R, double *u, double dt, const hp
     const double *qi = q ? q + i * qstage : nullptr;
     // a pointwise g lets the last leaf kernel of the solve write the epilogue
     const bool fuse = H->batch.fuse_epilogue && gk != HPS_G_BURGERS;
-    const StageEpi ep{fuse ? 1 : 0, B.Rb, B.KL + i * ni, B.KE + i * ni, qi, qld, qoff, gk, 1.0 / tb.A[1][1], dt, gp0};
+    // the last stage's dt L U_6 is not needed by a stiffly accurate close
+    double *kl = sa_close && i == 5 ? nullptr : B.KL + i * ni;
+    const StageEpi ep{fuse ? 1 : 0, B.Rb, kl, B.KE + i * ni, qi, qld, qoff, gk, 1.0 / tb.A[1][1], dt, gp0};
     bool done = false;
     if (int e = refined_solve(H, B, H->impl, H->batch.impl32, R, c, B.Rb, B.Rb, fv, B.ustage, refine, H->gamma_dt,
                               st, ep, done))
@@ -2400,10 +2404,18 @@ int ark_group(hps_handle *H, BatchWork &B, int R, double *u, double dt, const hp
   // step close: ARK combination at interior points, shared-edge values from the identity
   // operator solve (refined against its residual: interior R - u and the flux jumps)
   Combo c{};
-  add_term_b(c, u, 1.0);
-  for (int j = 0; j < 6; ++j) {
-    add_term_b(c, B.KL + j * ni, tb.b[j]);
-    add_term_b(c, B.KE + j * ni, tb.b[j]);
+  if (sa_close) {
+    // stiffly accurate implicit table (b = last row of A) and dt L U_6 taken from the stage
+    // equation: u + sum_j b_j dt L U_j = U_6 - sum_j Ah_6j dt (q_j + g(U_j)), so the close needs
+    // U_6 and the explicit terms only
+    add_term_b(c, B.ustage, 1.0);
+    for (int j = 0; j < 6; ++j) add_term_b(c, B.KE + j * ni, tb.b[j] - tb.Ah[5][j]);
+  } else {
+    add_term_b(c, u, 1.0);
+    for (int j = 0; j < 6; ++j) {
+      add_term_b(c, B.KL + j * ni, tb.b[j]);
+      add_term_b(c, B.KE + j * ni, tb.b[j]);
+    }
   }
   const BdView fv{f ? f + 5 * fstage : nullptr, fld, foff};
   bool done = false;
@@ -2540,6 +2552,7 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
     case HPS_OPT_FUSE_EPILOGUE: flag = &Bt.fuse_epilogue; break;
     case HPS_OPT_FUSE_JUMP: flag = &Bt.fuse_jump; break;
     case HPS_OPT_FOLD_SCALE: flag = &Bt.fold_scale; break;
+    case HPS_OPT_SA_CLOSE: flag = &Bt.sa_close; break;
     default: return HPS_EINVAL;
   }
   if (get) *get = field ? *field : (*flag ? 1 : 0);

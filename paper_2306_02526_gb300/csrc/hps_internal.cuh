@@ -169,6 +169,7 @@ struct Batch {
   bool fuse_epilogue = true;  // stage epilogue written by the last leaf kernel of the stage solve
   bool fuse_jump = true;      // residual: flux jumps from the even-odd leaf kernel (no k_b_jump)
   bool fold_scale = true;     // even-odd leaf kernels: scales folded into the half matrices
+  bool sa_close = true;       // step close from the last stage value (stiffly accurate table)
   int plan_target = 2;       // split-K plans: CTAs per SM aimed at
   int plan_kmin = 32;        // split-K plans: smallest K chunk
   int plan_npc_max = 1 << 30;  // split-K plans: most nodes per CTA
