@@ -33,27 +33,28 @@ __device__ __forceinline__ void u_out(const UOut &U, int64_t i, float v) {
 }
 
 // Stage epilogue of an implicit ARK stage (Eq. 2.3-2.4 split): from the solved stage value
-// U_i (interior point o of an [N][R] vector) the implicit derivative dt L U_i is recovered
-// from the stage equation U_i - gamma dt L U_i = Rb_i as (U_i - Rb_i) / gamma, and the
-// explicit one is dt (q_i + g(U_i)); only g without derivatives (pointwise) takes this form.
+// U_i (interior point o of an [N][R] vector) the implicit term is recovered from the stage
+// equation U_i - gamma dt L U_i = Rb_i: the batched path keeps it as gamma dt L U_i = U_i - Rb_i
+// (the stage combinations take A_ij / gamma, exact for gamma = 1/4); the explicit term is
+// dt (q_i + g(U_i)).  Only g without derivatives (pointwise) takes this form.
 struct StageEpi {
   int on;
   const double *Rb;     // [N_int][R] stage right-hand side
-  double *KL, *KE;      // [N_int][R] outputs
+  double *KL, *KE;      // [N_int][R] outputs (KL: gamma dt L U_i; may be null)
   const double *q;      // [N_int][qld] (columns qoff ..) or null
   int qld, qoff, g_kind;
-  double inv_gamma, dt, gp0;
+  double dt, dtg;       // dt, dt * g_param[0]
 };
 __device__ __forceinline__ void stage_epi_point(const StageEpi &E, int R, int64_t o, double uu) {
   double e;
   switch (E.g_kind) {
-    case HPS_G_ALLEN_CAHN: e = E.gp0 * (uu - uu * uu * uu); break;
-    case HPS_G_FISHER: e = E.gp0 * uu * (1.0 - uu); break;
+    case HPS_G_ALLEN_CAHN: e = E.dtg * (uu - uu * uu * uu); break;
+    case HPS_G_FISHER: e = E.dtg * uu * (1.0 - uu); break;
     default: e = 0.0;
   }
-  if (E.q) e += E.q[(o / R) * E.qld + E.qoff + o % R];
-  if (E.KL) E.KL[o] = (uu - E.Rb[o]) * E.inv_gamma;
-  E.KE[o] = E.dt * e;
+  if (E.q) e = fma(E.dt, E.q[(o / R) * E.qld + E.qoff + o % R], e);
+  if (E.KL) E.KL[o] = uu - E.Rb[o];
+  E.KE[o] = e;
 }
 
 // Block-wide loop over [0, n): every thread issues U independent loads before it uses any of
@@ -1517,7 +1518,7 @@ struct Leaf64Args {
   const double *coef;   // 5 x N_int or null (constants in cst)
   double cst[5];
   int64_t N_int;
-  double gdt, inv_gamma, dt;
+  double gdt, dtL, dt;  // dtL: scale of L u in kEval (gamma dt in the batched ARK step)
   int g_kind;
   double gp0, gp1;
   int need_d1, need_d2;  // first / second derivatives needed (zero terms are skipped)
@@ -1594,7 +1595,7 @@ __global__ void __launch_bounds__(kBT) k_b_leaf64(GridDims g, int nodes, const i
           default: e = 0.0;
         }
         if (A.q) e += A.q[gi * A.qld + A.qoff + col];
-        A.out0[o] = A.mode == kEval ? A.dt * Lu : (uu - A.Rb[o]) * A.inv_gamma;
+        A.out0[o] = A.mode == kEval ? A.dtL * Lu : uu - A.Rb[o];
         A.out1[o] = A.dt * e;
       }
     }
@@ -1649,7 +1650,7 @@ __device__ __forceinline__ void leaf64_out(const Leaf64Args &A, int64_t gi, int 
       default: e = 0.0;
     }
     if (A.q) e += A.q[gi * A.qld + A.qoff + col];
-    A.out0[o] = A.mode == kEval ? A.dt * Lu : (uu - A.Rb[o]) * A.inv_gamma;
+    A.out0[o] = A.mode == kEval ? A.dtL * Lu : uu - A.Rb[o];
     A.out1[o] = A.dt * e;
   }
 }
@@ -1809,7 +1810,7 @@ __global__ void k_b_pointwise(int64_t n, Leaf64Args A) {
     A.out0[o] = A.Rb[o] - uu;
     return;
   }
-  const StageEpi E{1, A.Rb, A.out0, A.out1, A.q, A.qld, A.qoff, A.g_kind, A.inv_gamma, A.dt, A.gp0};
+  const StageEpi E{1, A.Rb, A.out0, A.out1, A.q, A.qld, A.qoff, A.g_kind, A.dt, A.dt * A.gp0};
   stage_epi_point(E, A.R, o, uu);
 }
 
@@ -2211,7 +2212,7 @@ int leaf64(hps_handle *H, Leaf64Args A, cudaStream_t st, bool *flux_done = nullp
     // constant coefficients: scales folded into the half matrices (not for a g that needs the
     // plain first derivatives)
     if (!nodal && A.mode != kEpilogue && !(A.mode == kEval && A.g_kind == HPS_G_BURGERS) && H->batch.fold_scale) {
-      const double sc = A.mode == kResid ? A.gdt : A.dt;
+      const double sc = A.mode == kResid ? A.gdt : A.dtL;
       A.fold = 1;
       A.s1x = sc * H->cst[2];
       A.s1y = sc * H->cst[3];
@@ -2351,7 +2352,9 @@ int ark_group(hps_handle *H, BatchWork &B, int R, double *u, double dt, const hp
   const int64_t qstage = g.N_int * (int64_t)qld, fstage = g.N_bd * (int64_t)fld;
   const int gk = terms ? terms->g_kind : HPS_G_NONE;
   const double gp0 = terms ? terms->g_param[0] : 0.0, gp1 = terms ? terms->g_param[1] : 0.0;
-  // stage 1 (explicit): dt L u^n, dt (q_1 + g(u^n))
+  // stage 1 (explicit): gamma dt L u^n, dt (q_1 + g(u^n)); the implicit terms are kept times
+  // gamma (KL_j = gamma dt L U_j) and their coefficients divided by it
+  const double gam = tb.A[1][1];
   Leaf64Args E = leaf64_args(H, kEval, R);
   E.u = u;
   E.out0 = B.KL;
@@ -2360,6 +2363,7 @@ int ark_group(hps_handle *H, BatchWork &B, int R, double *u, double dt, const hp
   E.qld = qld;
   E.qoff = qoff;
   E.dt = dt;
+  E.dtL = gam * dt;
   E.g_kind = gk;
   E.gp0 = gp0;
   E.gp1 = gp1;
@@ -2371,7 +2375,7 @@ int ark_group(hps_handle *H, BatchWork &B, int R, double *u, double dt, const hp
     Combo c{};
     add_term_b(c, u, 1.0);
     for (int j = 0; j < i; ++j) {
-      add_term_b(c, B.KL + j * ni, tb.A[i][j]);
+      add_term_b(c, B.KL + j * ni, tb.A[i][j] / gam);
       add_term_b(c, B.KE + j * ni, tb.Ah[i][j]);
     }
     const BdView fv{f ? f + i * fstage : nullptr, fld, foff};
@@ -2380,7 +2384,7 @@ int ark_group(hps_handle *H, BatchWork &B, int R, double *u, double dt, const hp
     const bool fuse = H->batch.fuse_epilogue && gk != HPS_G_BURGERS;
     // the last stage's dt L U_6 is not needed by a stiffly accurate close
     double *kl = sa_close && i == 5 ? nullptr : B.KL + i * ni;
-    const StageEpi ep{fuse ? 1 : 0, B.Rb, kl, B.KE + i * ni, qi, qld, qoff, gk, 1.0 / tb.A[1][1], dt, gp0};
+    const StageEpi ep{fuse ? 1 : 0, B.Rb, kl, B.KE + i * ni, qi, qld, qoff, gk, dt, dt * gp0};
     bool done = false;
     if (int e = refined_solve(H, B, H->impl, H->batch.impl32, R, c, B.Rb, B.Rb, fv, B.ustage, refine, H->gamma_dt,
                               st, ep, done))
@@ -2394,7 +2398,6 @@ int ark_group(hps_handle *H, BatchWork &B, int R, double *u, double dt, const hp
     P.q = qi;
     P.qld = qld;
     P.qoff = qoff;
-    P.inv_gamma = 1.0 / tb.A[1][1];
     P.dt = dt;
     P.g_kind = gk;
     P.gp0 = gp0;
@@ -2413,7 +2416,7 @@ int ark_group(hps_handle *H, BatchWork &B, int R, double *u, double dt, const hp
   } else {
     add_term_b(c, u, 1.0);
     for (int j = 0; j < 6; ++j) {
-      add_term_b(c, B.KL + j * ni, tb.b[j]);
+      add_term_b(c, B.KL + j * ni, tb.b[j] / gam);
       add_term_b(c, B.KE + j * ni, tb.b[j]);
     }
   }
