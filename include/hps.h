@@ -217,8 +217,10 @@ enum {
   HPS_K_MERGE_DOWN_ALL = 8, /* a4, likewise                                                    */
   HPS_K_RESIDUAL = 9,       /* batched path: FP64 collocation residual at interior points     */
   HPS_K_JUMP = 10,          /* batched path: FP64 flux-jump residual at shared edge points      */
-  HPS_K_FINISH = 11         /* batched path: FP32 sweep result into the FP64 vector; column
+  HPS_K_FINISH = 11,        /* batched path: FP32 sweep result into the FP64 vector; column
                               group copies                                                    */
+  HPS_K_CLOSE = 12          /* step close by the edge projection: interior combination with the
+                              leaves' flux sums, then one tridiagonal solve per grid line      */
 };
 
 /* Tracing (no effect on results).  Every launch of the solve path is counted per kernel;
@@ -303,7 +305,12 @@ enum {
   HPS_OPT_SA_CLOSE = 17,        /* 1: the step close of the batched ARK step combines the last stage
                                    value and the explicit terms (b = last row of the implicit
                                    table), 7 instead of 13 terms (default 1)                       */
-  HPS_OPT_COUNT = 18
+  HPS_OPT_EDGE_PROJECTION = 18, /* 1: the step close (identity operator, Sec. 3.1.1) solves for the
+                                   shared-edge values directly: flux continuity with the given
+                                   interior values is one tridiagonal system per grid line of
+                                   shared edges (uniform leaves), in FP64; 0: identity-operator
+                                   HPS solve with refinement (default 1)                          */
+  HPS_OPT_COUNT = 19
 };
 int hps_batch_set_option(hps_handle *h, int opt, int value);
 

@@ -13,7 +13,7 @@ HPS_COEF_CONST, HPS_COEF_NODAL = 0, 1
 HPS_FLAG_PER_NODE = 1
 HPS_G_NONE, HPS_G_ALLEN_CAHN, HPS_G_FISHER, HPS_G_BURGERS = 0, 1, 2, 3
 KERNELS = ("leaf_up", "merge_up_w3", "merge_up_h", "merge_down", "leaf_down", "leaf_eval", "set_boundary",
-           "merge_up_all", "merge_down_all", "residual", "jump", "finish")
+           "merge_up_all", "merge_down_all", "residual", "jump", "finish", "close")
 
 
 class hps_tree(ctypes.Structure):
@@ -56,7 +56,7 @@ class hps_tune_result(ctypes.Structure):
 BATCH_OPTIONS = ("tensor_leaf", "even_odd", "flow_levels", "flow_n3_max", "cluster_splitk", "plan_target",
                  "plan_kmin", "plan_npc_max", "split_rhs", "fp64_ctas_per_sm", "group_offset", "last_cta_sum",
                  "fast_diag", "plan_tile_cols", "fuse_epilogue",
-                 "fuse_jump", "fold_scale", "sa_close")
+                 "fuse_jump", "fold_scale", "sa_close", "edge_projection")
 
 
 class hps_server_stats(ctypes.Structure):

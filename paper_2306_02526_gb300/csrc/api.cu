@@ -292,6 +292,7 @@ size_t hps_bytes(const hps_tree *tree, int p, int coeff_kind, int flags) {
   size_t s = opset_bytes(lev, q, b, shared, false) + opset_bytes(lev, q, b, true, true) + work_bytes(g, lev);
   if (coeff_kind == HPS_COEF_NODAL) s += 5 * (size_t)g.N_int * sizeof(double);
   s += (4 * (size_t)p * p + 2 * (size_t)p * p) * sizeof(double);  // D matrices and their even-odd halves
+  s += 2 * (size_t)(g.n1 - 1 + g.n2 - 1) * sizeof(double);         // edge-projection factors
   for (const Level &lv : lev) s += (2 * (size_t)lv.nodes + lv.hsrc.size() + lv.cmap.size()) * sizeof(int);
   return s;
 }
@@ -368,6 +369,32 @@ int hps_build(const hps_tree *tree, int p, const hps_coeffs *coeffs, double gamm
   // differentiation matrices D1x, D1y, Dxx = D1x^2, Dyy = D1y^2 on this leaf size
   {
     std::vector<double> Dh = scaled_D(p, H->hx, H->hy);
+    {  // Thomas factors of the edge-projection systems (one per grid line of shared edges)
+      std::vector<double> pr;
+      for (int dir = 0; dir < 2; ++dir) {
+        const double *D1 = Dh.data() + (size_t)dir * p * p;
+        const int n = (dir ? H->g.n2 : H->g.n1) - 1;
+        const double lo = D1[(p - 1) * p], d = D1[(p - 1) * p + p - 1] - D1[0], up = -D1[p - 1];
+        H->proj_lo[dir] = lo;
+        H->proj_up[dir] = up;
+        std::vector<double> w(n, 0.0), ib(n);
+        double b = d;
+        for (int L = 0; L < n; ++L) {
+          if (L > 0) {
+            w[L] = lo / b;
+            b = d - w[L] * up;
+          }
+          if (!(std::fabs(b) > 0.0)) return fail(HPS_EINVAL);
+          ib[L] = 1.0 / b;
+        }
+        pr.insert(pr.end(), w.begin(), w.end());
+        pr.insert(pr.end(), ib.begin(), ib.end());
+      }
+      if (!pr.empty()) {
+        if (dalloc(H, &H->d_proj, pr.size())) return fail(HPS_ENOMEM);
+        cudaMemcpyAsync(H->d_proj, pr.data(), pr.size() * sizeof(double), cudaMemcpyHostToDevice, st);
+      }
+    }
     if (p % 2 == 0) {  // even-odd halves of D1x, D1y, Dxx, Dyy: A = (D_ik + D_i,p-1-k) / 2, B = (D_ik - D_i,p-1-k) / 2
       const int h = p / 2;
       for (int mtx = 0; mtx < 4; ++mtx) {
@@ -457,6 +484,11 @@ int clone_handle(const hps_handle *base, cudaStream_t st, hps_handle **out) {
   H->d_coef = base->d_coef;
   H->d_D = base->d_D;
   H->fd = base->fd;
+  H->d_proj = base->d_proj;
+  for (int d = 0; d < 2; ++d) {
+    H->proj_lo[d] = base->proj_lo[d];
+    H->proj_up[d] = base->proj_up[d];
+  }
   H->lev = base->lev;
   H->impl = base->impl;
   H->ident = base->ident;

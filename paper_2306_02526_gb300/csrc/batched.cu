@@ -1858,6 +1858,99 @@ __global__ void k_b_jump(GridDims g, int R, const double *__restrict__ u, double
 }
 
 
+// Step close by the edge projection (the identity-operator system of Sec. 3.1.1 solved
+// directly).  With the interior values fixed, flux continuity at a shared-edge point involves
+// only the grid line through it normal to the edge: the two leaves' interior points on that line
+// and the edge values at the line's three leaf boundaries.  So on a uniform leaf grid the
+// shared-edge values of one grid line (leaf row iy and node j for vertical edges, leaf column ix
+// and node i for horizontal ones) solve a tridiagonal system
+//   lo v_{L-1} + d v_L + up v_{L+1} = F0_E - Fl_W,  L = 1 .. n-1,  v_0 and v_n boundary data,
+// lo = D1[p-1][0], d = D1[p-1][p-1] - D1[0][0], up = -D1[0][p-1], F0_E / Fl_W the east (north)
+// leaf's row-0 and the west (south) leaf's row-(p-1) derivative sums over their interior points.
+//
+// k_b_close_leaf: one CTA per leaf; interior values = the combination `c` (written into u),
+// then the leaf adds +F0 into the right-hand side of its west / south edge and -Fl into that of
+// its east / north edge (rhs zeroed beforehand; two terms onto zero, so the order of the two
+// leaves does not change the sum).
+constexpr int kCloseRc = 16;
+__global__ void __launch_bounds__(kBT) k_b_close_leaf(GridDims g, const int *__restrict__ origin, int R, Combo c,
+                                                     double *__restrict__ u, double *__restrict__ rhs,
+                                                     const double *__restrict__ Dg) {
+  extern __shared__ double scl[];
+  const int p = g.p, m = g.m, q = m * m, Rc = min(R, kCloseRc);
+  double *Dr = scl, *Us = scl + 4 * p;  // rows 0 and p-1 of D1x, then of D1y; Us [q][Rc]
+  for (int i = threadIdx.x; i < 4 * p; i += blockDim.x) {
+    const int mtx = i / (2 * p), row = (i / p) % 2 ? p - 1 : 0;
+    Dr[i] = Dg[mtx * p * p + row * p + i % p];
+  }
+  const int k = blockIdx.x, ix = origin[2 * k], iy = origin[2 * k + 1];
+  const int64_t l0 = ((int64_t)iy * g.n1 + ix) * q;
+  for (int j0 = 0; j0 < R; j0 += Rc) {
+    const int rc = min(Rc, R - j0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < q * rc; idx += blockDim.x) {
+      const int pt = idx / rc, jj = idx % rc;
+      const int64_t o = (l0 + pt) * R + j0 + jj;
+      double acc = 0.0;
+      for (int t = 0; t < c.n; ++t) acc = fma(c.coef[t], c.ptr[t][o], acc);
+      u[o] = acc;
+      Us[pt * Rc + jj] = acc;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 2 * m * rc; idx += blockDim.x) {
+      const int jj = idx % rc, t = idx / rc, r = t % m, dir = t / m;
+      const double *d0 = Dr + 2 * dir * p, *dl = d0 + p;
+      double f0 = 0.0, fl = 0.0;
+      for (int kk = 1; kk <= m; ++kk) {  // x line j = r + 1 (dir 0) or y line i = r + 1 (dir 1)
+        const double v = Us[(dir ? (kk - 1) * m + r : r * m + kk - 1) * Rc + jj];
+        f0 = fma(d0[kk], v, f0);
+        fl = fma(dl[kk], v, fl);
+      }
+      const int col = j0 + jj;
+      if (dir == 0) {
+        if (ix > 0) atomicAdd(rhs + vseg(g, ix, iy, r) * R + col, f0);
+        if (ix + 1 < g.n1) atomicAdd(rhs + vseg(g, ix + 1, iy, r) * R + col, -fl);
+      } else {
+        if (iy > 0) atomicAdd(rhs + hseg(g, iy, ix, r) * R + col, f0);
+        if (iy + 1 < g.n2) atomicAdd(rhs + hseg(g, iy + 1, ix, r) * R + col, -fl);
+      }
+    }
+  }
+}
+
+// k_b_edge_tridiag: one thread per grid line of shared edges and column; forward elimination
+// with the host's Thomas factors (w_L, 1/b_L) into rhs, back substitution into u.
+__global__ void k_b_edge_tridiag(GridDims g, int R, double *__restrict__ rhs, double *__restrict__ u,
+                                 const double *__restrict__ proj, double lox, double upx, double loy, double upy) {
+  const int64_t nvl = (int64_t)g.n2 * g.m, nhl = (int64_t)g.n1 * g.m;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (nvl + nhl) * R) return;
+  const int col = (int)(idx % R);
+  int64_t s = idx / R;
+  const bool vert = s < nvl;
+  if (!vert) s -= nvl;
+  const int n = vert ? g.n1 : g.n2;  // lines 0 .. n; shared ones 1 .. n-1
+  if (n < 2) return;
+  const int a = (int)(s / g.m), node = (int)(s % g.m);  // leaf row (vertical) or column, node
+  const double *w = vert ? proj : proj + 2 * (g.n1 - 1), *ib = w + (n - 1);
+  const double lo = vert ? lox : loy, up = vert ? upx : upy;
+  auto at = [&](int L) { return (vert ? vseg(g, L, a, node) : hseg(g, L, a, node)) * R + col; };
+  const double v0 = u[at(0)], vn = u[at(n)];
+  double rp = 0.0;
+  for (int L = 1; L < n; ++L) {
+    double r = rhs[at(L)];
+    if (L == 1) r -= lo * v0;
+    if (L == n - 1) r -= up * vn;
+    rp = L == 1 ? r : fma(-w[L - 1], rp, r);
+    rhs[at(L)] = rp;
+  }
+  double v = 0.0;
+  for (int L = n - 1; L >= 1; --L) {
+    v = L == n - 1 ? rhs[at(L)] * ib[L - 1] : (rhs[at(L)] - up * v) * ib[L - 1];
+    u[at(L)] = v;
+  }
+}
+
 // f: [N_bd][fld], this call's columns from foff; u (if non-null) gets the FP64 values
 __global__ void k_b_set_boundary32(GridDims g, int R, float *__restrict__ g32, const double *__restrict__ f, int fld,
                                    int foff, double *__restrict__ u) {
@@ -2274,6 +2367,21 @@ int residual(hps_handle *H, BatchWork &B, int R, const double *u, const double *
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
+int edge_projection_impl(hps_handle *H, int R, const Combo &c, double *u, double *rhs, cudaStream_t st) {
+  const GridDims &g = H->g;
+  const Level &leaf = H->lev[H->L];
+  if (cudaMemsetAsync(rhs + g.N_int * R, 0, (size_t)(g.N - g.N_int) * R * sizeof(double), st) != cudaSuccess)
+    return HPS_ECUDA;
+  const size_t smem = (size_t)(4 * H->p + H->q * std::min(R, kCloseRc)) * sizeof(double);
+  H->trace.begin(kClose, st);
+  k_b_close_leaf<<<leaf.nodes, kBT, smem, st>>>(g, leaf.d_origin, R, c, u, rhs, H->d_D);
+  const int64_t nsys = ((int64_t)g.n2 * g.m + (int64_t)g.n1 * g.m) * R;
+  k_b_edge_tridiag<<<blocks(nsys, 128), 128, 0, st>>>(g, R, rhs, u, H->d_proj, H->proj_lo[0], H->proj_up[0],
+                                                       H->proj_lo[1], H->proj_up[1]);
+  H->trace.end(kClose, st);
+  return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
+}
+
 // Boundary data of one group: f is [N_bd][fld] with the group's columns from foff.
 struct BdView {
   const double *f;
@@ -2421,6 +2529,12 @@ int ark_group(hps_handle *H, BatchWork &B, int R, double *u, double dt, const hp
     }
   }
   const BdView fv{f ? f + 5 * fstage : nullptr, fld, foff};
+  if (H->batch.edge_projection && H->d_proj) {
+    H->trace.begin(kSetBoundary, st);
+    k_b_set_boundary32<<<blocks(g.N_bd * R), 256, 0, st>>>(g, R, B.g32, fv.f, fv.ld, fv.off, u);
+    H->trace.end(kSetBoundary, st);
+    return edge_projection_impl(H, R, c, u, B.r, st);
+  }
   bool done = false;
   return refined_solve(H, B, H->ident, H->batch.ident32, R, c, B.Rb, B.Rb, fv, u, refine, 0.0, st, StageEpi{}, done);
 }
@@ -2461,6 +2575,10 @@ void batch_release(hps_handle *H) {
   }
   if (Bt.fork) cudaEventDestroy(Bt.fork);
   Bt.fork = nullptr;
+}
+
+int edge_projection(hps_handle *H, int R, const Combo &c, double *u, double *rhs, cudaStream_t st) {
+  return edge_projection_impl(H, R, c, u, rhs, st);
 }
 
 int batch_reserve(hps_handle *H, int R, int groups) {
@@ -2556,6 +2674,7 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
     case HPS_OPT_FUSE_JUMP: flag = &Bt.fuse_jump; break;
     case HPS_OPT_FOLD_SCALE: flag = &Bt.fold_scale; break;
     case HPS_OPT_SA_CLOSE: flag = &Bt.sa_close; break;
+    case HPS_OPT_EDGE_PROJECTION: flag = &Bt.edge_projection; break;
     default: return HPS_EINVAL;
   }
   if (get) *get = field ? *field : (*flag ? 1 : 0);

@@ -51,7 +51,7 @@ __host__ __device__ inline int64_t iface_bd(const GridDims &g, int ix0, int iy0,
 // Kernel slots for launch counting and optional CUDA-event timing (hps_trace_*).
 enum Slot {
   kLeafUp = 0, kMergeUpW3, kMergeUpH, kMergeDown, kLeafDown, kLeafEval, kSetBoundary, kMergeUpFused,
-  kMergeDownFused, kResidual, kJump, kFinish, kNumSlots
+  kMergeDownFused, kResidual, kJump, kFinish, kClose, kNumSlots
 };
 
 constexpr int kMaxLevels = 32;
@@ -170,6 +170,7 @@ struct Batch {
   bool fuse_jump = true;      // residual: flux jumps from the even-odd leaf kernel (no k_b_jump)
   bool fold_scale = true;     // even-odd leaf kernels: scales folded into the half matrices
   bool sa_close = true;       // step close from the last stage value (stiffly accurate table)
+  bool edge_projection = true;  // step close by per-line tridiagonal solves for the edge values
   int plan_target = 2;       // split-K plans: CTAs per SM aimed at
   int plan_kmin = 32;        // split-K plans: smallest K chunk
   int plan_npc_max = 1 << 30;  // split-K plans: most nodes per CTA
@@ -240,6 +241,10 @@ struct hps_handle {
   double cst[5];
   double *d_coef = nullptr;   // 5 x N_int (NODAL)
   double *d_D = nullptr;      // D1x, D1y, Dxx, Dyy: 4 p*p doubles, row-major
+  // edge projection (step close): Thomas factors of the per-line tridiagonal systems,
+  // [w_x, 1/b_x] (n1 - 1 each) then [w_y, 1/b_y] (n2 - 1 each); off-diagonals lo (v_{L-1}), up (v_{L+1})
+  double *d_proj = nullptr;
+  double proj_lo[2] = {0.0, 0.0}, proj_up[2] = {0.0, 0.0};
   hps::FastDiag fd;           // factored A_ii^-1 (constant coefficients)
   std::vector<hps::Level> lev;  // 0 (root) .. L (leaves)
   hps::OpSet impl, ident;
@@ -307,6 +312,9 @@ bool fastdiag_factor(int p, const double *Dh, const double *cst, double gdt, boo
                      std::vector<double> (&F)[5], double *max_err);
 int batch_reserve(hps_handle *H, int R, int groups);
 int batch_option(hps_handle *H, int opt, const int *set, int *get);
+// edge projection of the step close (batched.cu): u interior = combination `c`, u boundary as
+// given, shared-edge values from flux continuity; rhs: [N][R] scratch
+int edge_projection(hps_handle *H, int R, const Combo &c, double *u, double *rhs, cudaStream_t st);
 int batch_autotune(hps_handle *H, int R, int refine, cudaStream_t st, hps_tune_result *res, int max_res, int *n_res);
 void batch_release(hps_handle *H);
 int solve_batch(hps_handle *H, int R, const double *rhs, const double *f, double *u, int refine, cudaStream_t st);
