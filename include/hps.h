@@ -305,7 +305,8 @@ enum {
   HPS_OPT_SA_CLOSE = 17,        /* 1: the step close of the batched ARK step combines the last stage
                                    value and the explicit terms (b = last row of the implicit
                                    table), 7 instead of 13 terms (default 1)                       */
-  HPS_OPT_EDGE_PROJECTION = 18, /* 1: the step close (identity operator, Sec. 3.1.1) solves for the
+  HPS_OPT_EDGE_PROJECTION = 18, /* 1: the step close (batched and FP64 ARK steps; the identity
+                                   operator of Sec. 3.1.1) solves for the
                                    shared-edge values directly: flux continuity with the given
                                    interior values is one tridiagonal system per grid line of
                                    shared edges (uniform leaves), in FP64; 0: identity-operator

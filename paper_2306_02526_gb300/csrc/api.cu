@@ -624,7 +624,10 @@ int ark_enqueue(hps_handle *H, double *u, double dt, const hps_ark_terms *terms,
     ep.gp1 = gp1;
     if (int e = hps::sweep(H, H->impl, c, H->R, H->ustage, nullptr, &ep, st)) return e;
   }
-  // step close: ARK combination at interior points, shared-edge values from the identity solve
+  // step close: ARK combination at interior points, shared-edge values from the identity-operator
+  // system (flux continuity), by the edge projection or by an identity-operator sweep
+  // (the stage sweeps leave the interior of ustage unwritten: the epilogue takes the stage
+  // values in the leaf kernel, so the close keeps the full 13-term combination)
   hps::Combo c{};
   add_term(c, u, 1.0);
   for (int j = 0; j < 6; ++j) {
@@ -632,6 +635,8 @@ int ark_enqueue(hps_handle *H, double *u, double dt, const hps_ark_terms *terms,
     add_term(c, H->KE + j * ni, tb.b[j]);
   }
   if (int e = hps::set_boundary(H, u, f ? f + 5 * nbd : nullptr, st)) return e;
+  // (the projection's edge right-hand side goes into the edge range of ustage, free here)
+  if (H->batch.edge_projection && H->d_proj) return hps::edge_projection(H, 1, c, u, H->ustage, st);
   return hps::sweep(H, H->ident, c, nullptr, u, u, nullptr, st);
 }
 
@@ -745,11 +750,13 @@ int hps_batch_reserve_groups(hps_handle *H, int R, int groups) {
   return hps::batch_reserve(H, R, groups);
 }
 
-static void drop_batch_graphs(hps_handle *H) {
+static void drop_batch_graphs(hps_handle *H) {  // (the step-close options reach the FP64 step too)
   hps::drain_graph(H, H->g_ark_b);
   hps::drain_graph(H, H->g_solve_b);
+  hps::drain_graph(H, H->g_ark);
   H->g_ark_b.destroy();
   H->g_solve_b.destroy();
+  H->g_ark.destroy();
 }
 
 int hps_fastdiag_check(int p, const double *coef, double gamma_dt, double hx, double hy, double *max_err) {

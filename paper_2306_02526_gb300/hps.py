@@ -200,7 +200,8 @@ class HPSSolver:
             check(lib().hps_batch_reserve_groups(self._h, int(R), int(groups)), "hps_batch_reserve_groups")
 
     def batch_option(self, name, value=None):
-        """Get (value None) or set a batched-path kernel option (hps_batch_get/set_option); names
+        """Get (value None) or set a kernel option of the batched path (hps_batch_get/set_option;
+        the step-close option edge_projection applies to the FP64 ark_step too); names
         in _lib.BATCH_OPTIONS."""
         opt = _lib.BATCH_OPTIONS.index(name)
         if value is not None:

@@ -114,9 +114,11 @@ def test_ark_heat_trajectory_matches_oracle():
     assert np.abs(u_gpu.cpu().numpy() - wl.exact(X, Y, t)).max() < 1e-5
 
 
-@pytest.mark.parametrize("gname", ["allen_cahn", "fisher", "burgers"])
-def test_ark_nonlinear_and_inhomogeneous_match_oracle(gname):
-    """Variable coefficients, time-dependent boundary data, a source and each g preset."""
+@pytest.mark.parametrize("gname,close", [("allen_cahn", "projection"), ("fisher", "projection"),
+                                         ("burgers", "projection"), ("allen_cahn", "sweep")])
+def test_ark_nonlinear_and_inhomogeneous_match_oracle(gname, close):
+    """Variable coefficients, time-dependent boundary data, a source and each g preset; the step
+    close by the edge projection (default) and by the identity-operator sweep."""
     torch = need_gpu()
     from paper_2306_02526_gb300 import hps
     n1, n2, p, dt = 4, 8, 9, 0.02
@@ -132,6 +134,8 @@ def test_ark_nonlinear_and_inhomogeneous_match_oracle(gname):
     prob = oark.Problem(g, coef, q=qf, f=ff, g=gfun)
     Hi, Hid = HPS(g, coef, 0.25 * dt), HPS(g, coef, 0.0)
     S = _gpu_solver(torch, n1, n2, p, coef, 0.25 * dt)
+    if close == "sweep":
+        S.batch_option("edge_projection", 0)
     c = hps.hps_ark_abscissae()
     u_or = 0.3 * np.sin(math.pi * X) * np.cos(Y)
     u_or[bd] = ff(0.0)
