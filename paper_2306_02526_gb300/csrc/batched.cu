@@ -1936,18 +1936,40 @@ __global__ void k_b_edge_tridiag(GridDims g, int R, double *__restrict__ rhs, do
   const double lo = vert ? lox : loy, up = vert ? upx : upy;
   auto at = [&](int L) { return (vert ? vseg(g, L, a, node) : hseg(g, L, a, node)) * R + col; };
   const double v0 = u[at(0)], vn = u[at(n)];
+  // blocks of kTB lines: the loads of a block are issued before its recurrence steps
+  constexpr int kTB = 8;
   double rp = 0.0;
-  for (int L = 1; L < n; ++L) {
-    double r = rhs[at(L)];
-    if (L == 1) r -= lo * v0;
-    if (L == n - 1) r -= up * vn;
-    rp = L == 1 ? r : fma(-w[L - 1], rp, r);
-    rhs[at(L)] = rp;
+  for (int L0 = 1; L0 < n; L0 += kTB) {
+    double r[kTB];
+#pragma unroll
+    for (int t = 0; t < kTB; ++t)
+      if (L0 + t < n) r[t] = rhs[at(L0 + t)];
+#pragma unroll
+    for (int t = 0; t < kTB; ++t) {
+      const int L = L0 + t;
+      if (L < n) {
+        double x = r[t];
+        if (L == 1) x -= lo * v0;
+        if (L == n - 1) x -= up * vn;
+        rp = L == 1 ? x : fma(-w[L - 1], rp, x);
+        rhs[at(L)] = rp;
+      }
+    }
   }
   double v = 0.0;
-  for (int L = n - 1; L >= 1; --L) {
-    v = L == n - 1 ? rhs[at(L)] * ib[L - 1] : (rhs[at(L)] - up * v) * ib[L - 1];
-    u[at(L)] = v;
+  for (int L1 = n - 1; L1 >= 1; L1 -= kTB) {
+    double r[kTB];
+#pragma unroll
+    for (int t = 0; t < kTB; ++t)
+      if (L1 - t >= 1) r[t] = rhs[at(L1 - t)];
+#pragma unroll
+    for (int t = 0; t < kTB; ++t) {
+      const int L = L1 - t;
+      if (L >= 1) {
+        v = L == n - 1 ? r[t] * ib[L - 1] : (r[t] - up * v) * ib[L - 1];
+        u[at(L)] = v;
+      }
+    }
   }
 }
 
