@@ -675,7 +675,8 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_down_res(GridDims g, int nodes, 
     gather_box<2>(g, ix, iy, 1, 1, b, R, Rp, g32, ub);
     __syncthreads();
     for (int it = threadIdx.x; it < QQ * CG; it += blockDim.x) {
-      const int r0 = 4 * (it % QQ), j0 = TC * (it / QQ);
+      // column groups fastest: the staged output rows are written without bank conflicts
+      const int r0 = 4 * (it / CG), j0 = TC * (it % CG);
       float acc[4][TC];
 #pragma unroll
       for (int e = 0; e < 4; ++e)
@@ -1026,17 +1027,20 @@ __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict
   }
   cp_async_wait_all();
   __syncthreads();
+  // column groups fastest across the threads: a warp's epilogue loads and stores cover whole
+  // row segments (coalesced); its operator reads are broadcasts of a few row quads
   int lo, rq, cg;
   if (P.npc > 1) {
     const int per = P.MQ * P.CG;
     lo = threadIdx.x / per;
     const int rem = threadIdx.x % per;
-    cg = rem / P.MQ;
-    rq = rem % P.MQ;
+    rq = rem / P.CG;
+    cg = rem % P.CG;
   } else {
     lo = 0;
-    cg = threadIdx.x / P.quads_cta;
-    rq = tile * P.quads_cta + threadIdx.x % P.quads_cta;
+    cg = threadIdx.x % P.CG;
+    const int lq = threadIdx.x / P.CG;
+    rq = lq < P.quads_cta ? tile * P.quads_cta + lq : P.MQ;  // past the tile: idle
   }
   const bool live = lo < nn && cg < P.CG && rq < P.MQ;
   const int r0 = 4 * rq, j0 = TC * cg;
@@ -1525,7 +1529,7 @@ struct Leaf64Args {
   // fold: the even-odd kernel takes the mode's scale (gamma dt or dt) times the constant
   // coefficients into its half matrices (s1x, s1y: first, s2x, s2y: second derivatives, s0:
   // the zeroth-order term), so its line sums are the scaled terms of L u
-  int fold;
+  int fold, has_s0;
   double s1x, s1y, s2x, s2y, s0;
   double *flux_r;  // kResid, even-odd kernel: the leaf adds its side fluxes into r at shared edges
 };
@@ -1612,7 +1616,7 @@ __device__ __forceinline__ void leaf64_out(const Leaf64Args &A, int64_t gi, int 
     double Ls = 0.0;
     if (A.need_d2) Ls = uxx + uyy;
     if (A.need_d1) Ls += ux + uy;
-    if (A.s0 != 0.0) Ls = fma(A.s0, uu, Ls);
+    if (A.has_s0) Ls = fma(A.s0, uu, Ls);
     if (A.mode == kResid) {
       A.out0[o] = (A.Rb[o] - uu) + Ls;
     } else {
@@ -2334,6 +2338,7 @@ int leaf64(hps_handle *H, Leaf64Args A, cudaStream_t st, bool *flux_done = nullp
       A.s2x = sc * H->cst[0];
       A.s2y = sc * H->cst[1];
       A.s0 = sc * H->cst[4];
+      A.has_s0 = A.s0 != 0.0;
     }
     const bool flux = A.flux_r && A.mode == kResid && H->batch.fuse_jump;
     if (flux) {
