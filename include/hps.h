@@ -311,7 +311,9 @@ enum {
                                    interior values is one tridiagonal system per grid line of
                                    shared edges (uniform leaves), in FP64; 0: identity-operator
                                    HPS solve with refinement (default 1)                          */
-  HPS_OPT_COUNT = 19
+  HPS_OPT_EO_COLS = 19,         /* even-odd FP64 leaf kernels: columns per pass (default 12; shared
+                                   memory grows with it)                                          */
+  HPS_OPT_COUNT = 20
 };
 int hps_batch_set_option(hps_handle *h, int opt, int value);
 

@@ -56,7 +56,8 @@ class hps_tune_result(ctypes.Structure):
 BATCH_OPTIONS = ("tensor_leaf", "even_odd", "flow_levels", "flow_n3_max", "cluster_splitk", "plan_target",
                  "plan_kmin", "plan_npc_max", "split_rhs", "fp64_ctas_per_sm", "group_offset", "last_cta_sum",
                  "fast_diag", "plan_tile_cols", "fuse_epilogue",
-                 "fuse_jump", "fold_scale", "sa_close", "edge_projection")
+                 "fuse_jump", "fold_scale", "sa_close", "edge_projection",
+                 "eo_cols")
 
 
 class hps_server_stats(ctypes.Structure):

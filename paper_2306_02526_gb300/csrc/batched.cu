@@ -1530,6 +1530,7 @@ struct Leaf64Args {
   // coefficients into its half matrices (s1x, s1y: first, s2x, s2y: second derivatives, s0:
   // the zeroth-order term), so its line sums are the scaled terms of L u
   int fold, has_s0;
+  int rc;  // even-odd kernel: columns per pass
   double s1x, s1y, s2x, s2y, s0;
   double *flux_r;  // kResid, even-odd kernel: the leaf adds its side fluxes into r at shared edges
 };
@@ -1671,7 +1672,7 @@ __global__ void __launch_bounds__(kBT, 3) k_b_leaf64_eo(GridDims g, int nodes, c
                                                      Leaf64Args A, const double *__restrict__ Dg) {
   extern __shared__ double sd[];
   const int p = g.p, m = g.m, q = m * m, pp = p * p, h = p / 2, hh = h * h, R = A.R;
-  const int Rc = max(1, min(R, 2048 / pp));
+  const int Rc = A.rc;  // columns per pass
   double *Hm = sd, *F0 = sd + 8 * hh, *U = F0 + 4 * h;  // half matrices; unscaled row 0 of the D1 halves; U [pp][Rc]
   double *Ex = U + pp * Rc, *Ox = Ex + m * h * Rc, *Ey = Ox + m * h * Rc, *Oy = Ey + m * h * Rc;  // [m][h][Rc]
   for (int i = threadIdx.x; i < 8 * hh; i += blockDim.x) {
@@ -2326,8 +2327,11 @@ int leaf64(hps_handle *H, Leaf64Args A, cudaStream_t st, bool *flux_done = nullp
   const int grid = per_sm > 0 ? std::min(leaf.nodes, per_sm * H->num_sms) : leaf.nodes;
   if (p % 2 == 0 && H->batch.even_odd) {
     const int h = p / 2, m = H->m;
-    const int Rc = std::max(1, std::min(A.R, 2048 / pp));
-    const size_t smem = (size_t)(8 * h * h + 4 * h + pp * Rc + 4 * m * h * Rc) * sizeof(double);
+    int Rc = std::max(1, std::min(A.R, H->batch.eo_cols));
+    auto eo_smem = [&](int rc) { return (size_t)(8 * h * h + 4 * h + pp * rc + 4 * m * h * rc) * sizeof(double); };
+    while (Rc > 1 && eo_smem(Rc) > 227 * 1024) Rc = (Rc + 1) / 2;
+    A.rc = Rc;
+    const size_t smem = eo_smem(Rc);
     // constant coefficients: scales folded into the half matrices (not for a g that needs the
     // plain first derivatives)
     if (!nodal && A.mode != kEpilogue && !(A.mode == kEval && A.g_kind == HPS_G_BURGERS) && H->batch.fold_scale) {
@@ -2702,6 +2706,7 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
     case HPS_OPT_FOLD_SCALE: flag = &Bt.fold_scale; break;
     case HPS_OPT_SA_CLOSE: flag = &Bt.sa_close; break;
     case HPS_OPT_EDGE_PROJECTION: flag = &Bt.edge_projection; break;
+    case HPS_OPT_EO_COLS: field = &Bt.eo_cols; break;
     default: return HPS_EINVAL;
   }
   if (get) *get = field ? *field : (*flag ? 1 : 0);
@@ -2711,6 +2716,7 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
                     opt == HPS_OPT_PLAN_TILE_COLS;
   if (opt == HPS_OPT_PLAN_TILE_COLS && *set != 2 && *set != 4 && *set != 8) return HPS_EINVAL;
   if (v < 0 || (plan && v < 1) || (opt == HPS_OPT_FLOW_LEVELS && v > kFlowMaxLevels)) return HPS_EINVAL;
+  if (opt == HPS_OPT_EO_COLS && (v < 1 || v > 32)) return HPS_EINVAL;
   if (field) *field = v;
   else *flag = v != 0;
   if (plan) {  // split-K scratch for the new plans

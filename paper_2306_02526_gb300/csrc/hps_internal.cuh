@@ -171,6 +171,7 @@ struct Batch {
   bool fold_scale = true;     // even-odd leaf kernels: scales folded into the half matrices
   bool sa_close = true;       // step close from the last stage value (stiffly accurate table)
   bool edge_projection = true;  // step close by per-line tridiagonal solves for the edge values
+  int eo_cols = 12;           // even-odd FP64 leaf kernels: columns per pass (3 CTAs per SM at p = 16)
   int plan_target = 2;       // split-K plans: CTAs per SM aimed at
   int plan_kmin = 32;        // split-K plans: smallest K chunk
   int plan_npc_max = 1 << 30;  // split-K plans: most nodes per CTA
