@@ -171,6 +171,46 @@ def test_fused_stage_epilogue_with_sources(gname, groups):
     assert rel_max(outs[0], outs[1]) <= 1e-13
 
 
+@pytest.mark.parametrize("n1,n2,p,R", [(1, 1, 6, 3), (1, 4, 7, 5), (8, 2, 9, 6), (2, 2, 16, 33)])
+def test_ark_batch_close_on_degenerate_trees_matches_oracle(n1, n2, p, R):
+    """Batched step (constant coefficients, a source, boundary data) on a single leaf, a column
+    of leaves, odd p and a rectangle, R not a multiple of 4 (and > 32): 2 steps against the
+    oracle, column by column."""
+    torch = need_gpu()
+    from paper_2306_02526_gb300 import hps
+    dt = 0.02
+    g = Grid(n1, n2, p)
+    X, Y = g.coords()
+    I, bd = np.arange(g.N_int), g.boundary_indices()
+    coef = {"a11": 0.5, "a22": 0.8}
+    S = _solver(torch, n1, n2, p, coef, 0.25 * dt)
+    S.batch_reserve(R)
+    c = hps.hps_ark_abscissae()
+    qf = lambda t, j: np.cos(X[I] - t + 0.1 * j) * np.sin(3 * Y[I])
+    ff = lambda t, j: (np.sin(2 * X + Y - 0.05 * j) * (1 - t))[bd]
+    u0 = np.stack([0.2 * np.cos(2 * X + 0.1 * j) * np.sin(5 * Y) for j in range(R)], axis=1)
+    for j in range(R):
+        u0[bd, j] = ff(0.0, j)
+    ug = to_dev(torch, u0)
+    Hi, Hid = HPS(g, coef, 0.25 * dt), HPS(g, coef, 0.0)
+    uo = [u0[:, j].copy() for j in range(R)]
+    t = 0.0
+    for n in range(2):
+        qb = np.stack([np.stack([qf(t + cj * dt, j) for j in range(R)], axis=1) for cj in c])
+        fb = np.stack([np.stack([ff(t + cj * dt, j) for j in range(R)], axis=1) for cj in c])
+        S.ark_step_batch(ug, t, dt, q=to_dev(torch, qb), f=to_dev(torch, fb), g="fisher", g_param=(0.7, 0.0),
+                         refine=2)
+        for j in range(R):
+            prob = oark.Problem(g, coef, q=lambda tt, j=j: qf(tt, j), f=lambda tt, j=j: ff(tt, j),
+                                g=nonlinear.fisher(0.7))
+            uo[j], _ = oark.ark_step(prob, Hi, Hid, uo[j], t, dt)
+        t += dt
+    got = ug.cpu().numpy()
+    for j in range(R):
+        assert rel_max(got[:, j], uo[j]) <= TOL
+    S.close()
+
+
 def test_ark_batch_full_size_allen_cahn():
     """The bench workload (64x64 leaves, p = 16) with 8 seeded states: 2 batched mixed steps
     against the FP64 path column by column."""

@@ -150,6 +150,37 @@ def test_ark_nonlinear_and_inhomogeneous_match_oracle(gname, close):
         assert rel_max(u_gpu.cpu().numpy(), u_or) <= TOL
 
 
+@pytest.mark.parametrize("n1,n2,p", [(1, 1, 5), (2, 1, 6), (1, 4, 7), (8, 2, 9), (4, 4, 16)])
+def test_ark_close_on_degenerate_trees_matches_oracle(n1, n2, p):
+    """Step close (edge projection: one tridiagonal system per grid line of shared edges) on a
+    single leaf, single rows / columns of leaves, odd p and a rectangle: 3 ARK steps with a
+    source and time-dependent boundary data against the oracle."""
+    torch = need_gpu()
+    from paper_2306_02526_gb300 import hps
+    dt = 0.02
+    g = Grid(n1, n2, p, 0.0, 1.0, 0.0, 0.5)
+    X, Y = g.coords()
+    I, bd = np.arange(g.N_int), g.boundary_indices()
+    coef = {"a11": 0.5, "a22": 0.8, "a1": 0.3, "a0": -0.2}
+    qf = lambda t: np.cos(X[I] - t) * np.sin(3 * Y[I])
+    ff = lambda t: (np.sin(2 * X + Y) * (1 - t))[bd]
+    prob = oark.Problem(g, coef, q=qf, f=ff, g=nonlinear.allen_cahn(0.5))
+    Hi, Hid = HPS(g, coef, 0.25 * dt), HPS(g, coef, 0.0)
+    S = _gpu_solver(torch, n1, n2, p, coef, 0.25 * dt, dom=(0.0, 1.0, 0.0, 0.5))
+    c = hps.hps_ark_abscissae()
+    u_or = 0.2 * np.cos(2 * X) * np.sin(5 * Y)
+    u_or[bd] = ff(0.0)
+    u_gpu = to_dev(torch, u_or)
+    t = 0.0
+    for n in range(3):
+        q = to_dev(torch, np.stack([qf(t + cj * dt) for cj in c]).reshape(-1))
+        f = to_dev(torch, np.stack([ff(t + cj * dt) for cj in c]).reshape(-1))
+        S.ark_step(u_gpu, t, dt, q=q, f=f, g="allen_cahn", g_param=(0.5, 0.0))
+        u_or, _ = oark.ark_step(prob, Hi, Hid, u_or, t, dt)
+        t += dt
+        assert rel_max(u_gpu.cpu().numpy(), u_or) <= TOL
+
+
 def test_ark_rejects_wrong_dt():
     torch = need_gpu()
     from paper_2306_02526_gb300 import _lib
