@@ -193,6 +193,14 @@ int hps_trace_tasks(hps_handle *h, int enable, int upward, double *us, int max_t
  * HPS_OK if the barrier completed (a fault in the barrier), or an error code. */
 int hps_selftest_barrier_timeout(hps_handle *h, hps_stream_t stream);
 
+/* Self-test of the integer-pipe FP32 <-> FP64 conversions the batched kernels use in place of
+ * the hardware conversions (which issue to the FP64 pipe on this GPU): n bit patterns from a
+ * counter hash seeded by `seed` (zeros, subnormals, normals, infinities, NaN; doubles near the
+ * float range; rounding ties), each converted both ways by both methods.  *mismatches (host)
+ * receives the number of patterns whose results differ (any NaN matches any NaN).  Synchronous
+ * on `stream`; allocates 8 bytes of device memory.  HPS_EINVAL for n < 1 or a null output. */
+int hps_selftest_conversions(int64_t n, uint64_t seed, hps_stream_t stream, int64_t *mismatches);
+
 /* Graph replay.  With enable != 0, ark_step and hps_solve record their kernel sequence
  * (about 380 launches per ARK step at 64 x 64 leaves) into a CUDA graph and replay it, so
  * the launch cost is paid once: the first call with a given set of pointers and arguments

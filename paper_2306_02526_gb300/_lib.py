@@ -87,6 +87,7 @@ SIGNATURES = {
     "hps_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "hps_trace_tasks": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, c_double_p, ctypes.c_int]),
     "hps_selftest_barrier_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "hps_selftest_conversions": (ctypes.c_int, [ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p, c_int64_p]),
     "hps_trace_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint]),
     "hps_trace_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_int64_p, c_int64_p,
                                       ctypes.POINTER(ctypes.c_double)]),

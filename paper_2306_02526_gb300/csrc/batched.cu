@@ -23,13 +23,70 @@ constexpr int kBSmemFloats = 8192;  // vector staging of the merge applies (32 K
 
 __host__ __device__ inline int round4(int r) { return (r + 3) & ~3; }
 
+}  // namespace
+
+// FP32 <-> FP64 conversions on the integer pipe.  On this GPU the hardware conversions issue
+// to the FP64 pipe (2 per SM per cycle, the rate of DFMA), which bounds the FP64 vector kernels;
+// the IEEE-754 binary32 / binary64 layouts make the common cases a few integer operations.
+// float -> double is exact: sign, exponent rebiased (+1023 - 127), mantissa shifted by 29;
+// zeros are built directly, subnormal / infinite / NaN inputs take the hardware conversion.
+__device__ __forceinline__ double f2d_int(float x) {
+  const unsigned b = __float_as_uint(x), e = (b >> 23) & 0xffu, man = b & 0x7fffffu;
+  if (e == 0xffu || (e == 0u && man != 0u)) return (double)x;
+  const unsigned hi = (b & 0x80000000u) | (e == 0u ? 0u : ((e + 896u) << 20) | (man >> 3));
+  return __hiloint2double((int)hi, (int)(man << 29));
+}
+// double -> float, rounded to nearest (ties to even): the top 23 of the 52 mantissa bits plus
+// the rounding of the other 29 (a carry out of the mantissa increments the exponent, up to
+// infinity, as IEEE rounding does); zeros directly; results below the normal float range,
+// infinities and NaN take the hardware conversion.
+__device__ __forceinline__ float d2f_int(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int e = (int)((hi >> 20) & 0x7ffu) - 896;  // binary32 biased exponent
+  if (((hi & 0x7fffffffu) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
+  if (e <= 0 || e >= 255) return (float)x;
+  unsigned r = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;
+  r += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;
+  return __uint_as_float((hi & 0x80000000u) + ((unsigned)e << 23) + r);
+}
+
+// Self-check of the two conversions against the hardware ones over n bit patterns from a
+// counter hash (all classes: zeros, subnormals, normals, infinities, NaN payloads) plus the
+// float range edges; mismatches counted (NaN: any NaN result matches).
+__global__ void k_conv_check(int64_t n, unsigned long long seed, unsigned long long *bad) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  unsigned long long z = seed + 0x9e3779b97f4a7c15ull * (unsigned long long)(i + 1);  // splitmix64
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  z ^= z >> 31;
+  double d = __longlong_as_double((long long)z);
+  if ((i & 3) == 1) {  // doubles near the float range: exponent within +-40 of float's
+    const unsigned long long ex = 896ull + (z >> 56) % 300ull - 20ull;
+    d = __longlong_as_double((long long)((z & 0x800fffffffffffffull) | (ex << 52)));
+  }
+  if ((i & 3) == 2) {  // ties: the low 29 bits exactly half
+    d = __longlong_as_double((long long)((z & ~0x1fffffffull) | 0x10000000ull));
+  }
+  const float fh = (float)d, fs = d2f_int(d);
+  const bool okf = (fh != fh) ? (fs != fs) : __float_as_uint(fh) == __float_as_uint(fs);
+  const float f = __uint_as_float((unsigned)z);
+  const double dh = (double)f, ds = f2d_int(f);
+  const bool okd = (dh != dh) ? (ds != ds) : __double_as_longlong(dh) == __double_as_longlong(ds);
+  if (!okf || !okd) atomicAdd(bad, 1ull);
+}
+
+namespace {
+
 // Where a sweep's FP32 result goes in the FP64 solution: u = v (assign) or u += v (a correction).
 struct UOut {
   double *u;
   int assign;
 };
 __device__ __forceinline__ void u_out(const UOut &U, int64_t i, float v) {
-  U.u[i] = U.assign ? (double)v : U.u[i] + (double)v;
+  const double d = f2d_int(v);
+  U.u[i] = U.assign ? d : U.u[i] + d;
 }
 
 // Stage epilogue of an implicit ARK stage (Eq. 2.3-2.4 split): from the solved stage value
@@ -104,7 +161,7 @@ __global__ void k_b_combo(int64_t n, Combo rhs, double *__restrict__ Rsave, floa
     const int64_t i = base + (int64_t)u * blockDim.x;
     if (i < n) {
       if (Rsave) Rsave[i] = acc[u];
-      r32[i] = (float)acc[u];
+      r32[i] = d2f_int(acc[u]);
     }
   }
 }
@@ -146,7 +203,7 @@ __device__ __forceinline__ void stage_combo(const Combo &rhs, int64_t off, int n
       const int idx = base + u * blockDim.x;
       if (idx < nq) {
         if (Rsave) Rsave[off + idx] = acc[u];
-        Rs[(idx / R) * Rp + idx % R] = (float)acc[u];
+        Rs[(idx / R) * Rp + idx % R] = d2f_int(acc[u]);
       }
     }
   }
@@ -484,7 +541,7 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_up_fd(GridDims g, int R, const i
     MT[idx] = i < m ? fd32[((size_t)a * m + i) * mp + kk] : 0.f;
   }
   for (int idx = threadIdx.x; idx < mm; idx += blockDim.x) Lam[idx] = fd32[4 * (size_t)mm + idx];
-  for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) D1x[i] = (float)Dg[i];
+  for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) D1x[i] = d2f_int(Dg[i]);
   if (Rp != R)
     for (int idx = threadIdx.x; idx < q * Rp; idx += blockDim.x) Rs[idx] = 0.f;
   __syncthreads();
@@ -599,7 +656,7 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_up_tc(GridDims g, int R, const i
       const int idx = base + u * blockDim.x;
       if (idx < nq) {
         if (Rsave) Rsave[l0 * R + idx] = acc[u];
-        const float v = (float)acc[u];
+        const float v = d2f_int(acc[u]);
         const unsigned h = tf32_rna(v);
         const int o = (idx / R) * RS + idx % R;
         Bh[o] = h;
@@ -863,7 +920,7 @@ struct BXDiff {  // d = h^b_3 - h^a_3 (+ interface right-hand side)
       const double *pj = jump + iface_bd(g, origin[2 * k], origin[2 * k + 1], a, c, split, cc) * R + j0;
 #pragma unroll
       for (int t = 0; t < 4; ++t)
-        if (j0 + t < R) v[t] += (float)pj[t];
+        if (j0 + t < R) v[t] += d2f_int(pj[t]);
     }
     return make_float4(v[0], v[1], v[2], v[3]);
   }
@@ -986,7 +1043,7 @@ struct BEScatter {  // interface values: FP32 for the levels below, and into the
     for (int t = 0; t < TC; ++t)
       if (j0 + t < R) {
         gv[i0 + t] = v[t];
-        uo.u[i0 + t] = uo.assign ? (double)v[t] : old[t] + (double)v[t];
+        uo.u[i0 + t] = uo.assign ? f2d_int(v[t]) : old[t] + f2d_int(v[t]);
       }
   }
 };
@@ -1992,7 +2049,7 @@ __global__ void k_b_set_boundary32(GridDims g, int R, float *__restrict__ g32, c
   else if (kk < 2 * nv + nh) gi = g.N_int + g.N_v + (kk - 2 * nv);
   else gi = g.N_int + g.N_v + (int64_t)g.n2 * nh + (kk - 2 * nv - nh);
   const double v = f ? f[kk * fld + foff + j] : 0.0;
-  g32[gi * R + j] = (float)v;
+  g32[gi * R + j] = d2f_int(v);
   if (u) u[gi * R + j] = v;
 }
 
@@ -2865,3 +2922,23 @@ int ark_batch(hps_handle *H, int R, double *u, double dt, const hps_ark_terms *t
 }
 
 }  // namespace hps
+
+extern "C" int hps_selftest_conversions(int64_t n, uint64_t seed, hps_stream_t stream, int64_t *mismatches) {
+  if (n < 1 || !mismatches) return HPS_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long *bad = nullptr;
+  if (cudaMalloc(&bad, sizeof(unsigned long long)) != cudaSuccess) return HPS_ENOMEM;
+  unsigned long long h = 0;
+  int e = HPS_OK;
+  if (cudaMemsetAsync(bad, 0, sizeof(unsigned long long), st) != cudaSuccess) e = HPS_ECUDA;
+  if (e == HPS_OK) {
+    hps::k_conv_check<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, (unsigned long long)seed, bad);
+    if (cudaPeekAtLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&h, bad, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      e = HPS_ECUDA;
+  }
+  cudaFree(bad);
+  *mismatches = (int64_t)h;
+  return e;
+}
