@@ -180,14 +180,25 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <int U>
 __device__ __forceinline__ void stage_combo(const Combo &rhs, int64_t off, int nq, int R, int Rp,
                                             double *__restrict__ Rsave, float *Rs) {
+  // FP64 operations per point: one per term, none for a leading term with coefficient 1 (the
+  // FP64 pipe bounds this loop on this GPU)
+  const bool unit0 = rhs.n > 0 && rhs.coef[0] == 1.0;
   for (int base = threadIdx.x; base < nq; base += U * blockDim.x) {
     double acc[U];
+    {
+      const double *s0 = rhs.ptr[0] + off;
+      const double c0 = rhs.n > 0 ? rhs.coef[0] : 0.0;
 #pragma unroll
-    for (int u = 0; u < U; ++u) acc[u] = 0.0;
-    for (int t = 0; t < rhs.n; t += 2) {
-      const bool two = t + 1 < rhs.n;
-      const double *s0 = rhs.ptr[t] + off, *s1 = two ? rhs.ptr[t + 1] + off : s0;
-      const double c0 = rhs.coef[t], c1 = two ? rhs.coef[t + 1] : 0.0;
+      for (int u = 0; u < U; ++u) {
+        const int idx = base + u * blockDim.x;
+        const double v = idx < nq && rhs.n > 0 ? s0[idx] : 0.0;
+        acc[u] = unit0 ? v : c0 * v;
+      }
+    }
+    int t = 1;
+    for (; t + 1 < rhs.n; t += 2) {
+      const double *s0 = rhs.ptr[t] + off, *s1 = rhs.ptr[t + 1] + off;
+      const double c0 = rhs.coef[t], c1 = rhs.coef[t + 1];
       double v0[U], v1[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -197,6 +208,18 @@ __device__ __forceinline__ void stage_combo(const Combo &rhs, int64_t off, int n
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) acc[u] = fma(c1, v1[u], fma(c0, v0[u], acc[u]));
+    }
+    if (t < rhs.n) {
+      const double *s0 = rhs.ptr[t] + off;
+      const double c0 = rhs.coef[t];
+      double v0[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int idx = base + u * blockDim.x;
+        v0[u] = idx < nq ? s0[idx] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc[u] = fma(c0, v0[u], acc[u]);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -1954,7 +1977,12 @@ __global__ void __launch_bounds__(kBT) k_b_close_leaf(GridDims g, const int *__r
       const int pt = idx / rc, jj = idx % rc;
       const int64_t o = (l0 + pt) * R + j0 + jj;
       double acc = 0.0;
-      for (int t = 0; t < c.n; ++t) acc = fma(c.coef[t], c.ptr[t][o], acc);
+      int t = 0;
+      if (c.n > 0 && c.coef[0] == 1.0) {  // a leading unit term costs no FP64 operation
+        acc = c.ptr[0][o];
+        t = 1;
+      }
+      for (; t < c.n; ++t) acc = fma(c.coef[t], c.ptr[t][o], acc);
       u[o] = acc;
       Us[pt * Rc + jj] = acc;
     }
