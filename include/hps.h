@@ -321,7 +321,10 @@ enum {
                                    HPS solve with refinement (default 1)                          */
   HPS_OPT_EO_COLS = 19,         /* even-odd FP64 leaf kernels: columns per pass (default 12; shared
                                    memory grows with it)                                          */
-  HPS_OPT_COUNT = 20
+  HPS_OPT_TILE_COLS_W3 = 20,    /* register-tile columns of the w3 applies (2, 4, 8; 0: PLAN_TILE_COLS) */
+  HPS_OPT_TILE_COLS_H = 21,     /* ... of the h applies                                              */
+  HPS_OPT_TILE_COLS_DOWN = 22,  /* ... of the u3 (downward) applies                                  */
+  HPS_OPT_COUNT = 23
 };
 int hps_batch_set_option(hps_handle *h, int opt, int value);
 

@@ -917,8 +917,10 @@ BPlan plan_b(int M, int K, int nodes, int R, int target, bool shared_op, PlanTun
 }
 
 int plan_target(const hps_handle *H) { return H->batch.plan_target * H->num_sms; }
-PlanTune plan_tune(const hps_handle *H) {
-  return PlanTune{H->batch.plan_kmin, H->batch.plan_npc_max, H->batch.plan_tile_cols};
+PlanTune plan_tune(const hps_handle *H, int slot) {  // slot: kMergeUpW3, kMergeUpH or kMergeDown
+  const int i = slot == kMergeUpW3 ? 0 : slot == kMergeUpH ? 1 : 2;
+  const int tc = H->batch.tile_cols_apply[i] ? H->batch.tile_cols_apply[i] : H->batch.plan_tile_cols;
+  return PlanTune{H->batch.plan_kmin, H->batch.plan_npc_max, tc};
 }
 
 struct BXDiff {  // d = h^b_3 - h^a_3 (+ interface right-hand side)
@@ -1343,8 +1345,8 @@ int launch_b2(hps_handle *H, BatchWork &B, int slot, int M, int K, int nodes, in
   const BPlan2 P = plan_b2(M, K, nodes, R);
   const size_t smem = b2_smem(P);
   if (!H->batch.gemv2 || smem > kB2MaxSmem)
-    return launch_b(H, B, slot, plan_b(M, K, nodes, R, plan_target(H), str == 0, plan_tune(H)), AT, ld, str, xl, ep,
-                    st);
+    return launch_b(H, B, slot, plan_b(M, K, nodes, R, plan_target(H), str == 0, plan_tune(H, slot)), AT, ld, str,
+                    xl, ep, st);
   auto kern = P.TC == 8 ? k_b_gemv2<8, XL, EP> : k_b_gemv2<4, XL, EP>;
   static size_t set8 = 0, set4 = 0;
   size_t &set = P.TC == 8 ? set8 : set4;
@@ -2138,9 +2140,9 @@ size_t partial_floats(hps_handle *H, int Rmax) {
   for (int l = 0; l < H->L; ++l) {
     const Level &lv = H->lev[l];
     for (int sh = 0; sh < 2; ++sh) {  // the identity operators are shared even when the others are not
-      const BPlan P[3] = {plan_b(lv.n3, lv.n3, lv.nodes, R, plan_target(H), sh, plan_tune(H)),
-                          plan_b(lv.nb, lv.n3, lv.nodes, R, plan_target(H), sh, plan_tune(H)),
-                          plan_b(lv.n3, lv.nb, lv.nodes, R, plan_target(H), sh, plan_tune(H))};
+      const BPlan P[3] = {plan_b(lv.n3, lv.n3, lv.nodes, R, plan_target(H), sh, plan_tune(H, kMergeUpW3)),
+                          plan_b(lv.nb, lv.n3, lv.nodes, R, plan_target(H), sh, plan_tune(H, kMergeUpH)),
+                          plan_b(lv.n3, lv.nb, lv.nodes, R, plan_target(H), sh, plan_tune(H, kMergeDown))};
       for (const BPlan &pl : P)
         if (pl.ksplit > 1) mx = std::max(mx, (size_t)pl.ksplit * pl.nodes * pl.M * pl.Rp);
     }
@@ -2792,15 +2794,20 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
     case HPS_OPT_SA_CLOSE: flag = &Bt.sa_close; break;
     case HPS_OPT_EDGE_PROJECTION: flag = &Bt.edge_projection; break;
     case HPS_OPT_EO_COLS: field = &Bt.eo_cols; break;
+    case HPS_OPT_TILE_COLS_W3: field = &Bt.tile_cols_apply[0]; break;
+    case HPS_OPT_TILE_COLS_H: field = &Bt.tile_cols_apply[1]; break;
+    case HPS_OPT_TILE_COLS_DOWN: field = &Bt.tile_cols_apply[2]; break;
     default: return HPS_EINVAL;
   }
   if (get) *get = field ? *field : (*flag ? 1 : 0);
   if (!set) return HPS_OK;
   const int v = *set;
+  const bool per_apply = opt == HPS_OPT_TILE_COLS_W3 || opt == HPS_OPT_TILE_COLS_H || opt == HPS_OPT_TILE_COLS_DOWN;
   const bool plan = opt == HPS_OPT_PLAN_TARGET || opt == HPS_OPT_PLAN_KMIN || opt == HPS_OPT_PLAN_NPC_MAX ||
-                    opt == HPS_OPT_PLAN_TILE_COLS;
+                    opt == HPS_OPT_PLAN_TILE_COLS || per_apply;
   if (opt == HPS_OPT_PLAN_TILE_COLS && *set != 2 && *set != 4 && *set != 8) return HPS_EINVAL;
-  if (v < 0 || (plan && v < 1) || (opt == HPS_OPT_FLOW_LEVELS && v > kFlowMaxLevels)) return HPS_EINVAL;
+  if (per_apply && *set != 0 && *set != 2 && *set != 4 && *set != 8) return HPS_EINVAL;
+  if (v < 0 || (plan && !per_apply && v < 1) || (opt == HPS_OPT_FLOW_LEVELS && v > kFlowMaxLevels)) return HPS_EINVAL;
   if (opt == HPS_OPT_EO_COLS && (v < 1 || v > 32)) return HPS_EINVAL;
   if (field) *field = v;
   else *flag = v != 0;

@@ -171,6 +171,7 @@ struct Batch {
   bool fold_scale = true;     // even-odd leaf kernels: scales folded into the half matrices
   bool sa_close = true;       // step close from the last stage value (stiffly accurate table)
   bool edge_projection = true;  // step close by per-line tridiagonal solves for the edge values
+  int tile_cols_apply[3] = {0, 0, 0};  // w3, h, down applies: register-tile columns (0: plan_tile_cols)
   int eo_cols = 12;           // even-odd FP64 leaf kernels: columns per pass (3 CTAs per SM at p = 16)
   int plan_target = 2;       // split-K plans: CTAs per SM aimed at
   int plan_kmin = 32;        // split-K plans: smallest K chunk
