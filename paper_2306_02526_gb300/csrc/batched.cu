@@ -549,14 +549,15 @@ __device__ __forceinline__ void fd_pass_y(const float *in, float *out, const flo
 // One leaf per CTA: stage right-hand side (FP64 combination, saved if requested), the four
 // passes between two shared-memory buffers, then w and the fluxes.  fd32 holds [V_x, V_x^-1,
 // V_y, V_y^-1, Lam], each m x mp.
-__global__ void __launch_bounds__(kBT) k_b_leaf_up_fd(GridDims g, int R, const int *__restrict__ origin, Combo rhs,
+__global__ void __launch_bounds__(kBT, 4) k_b_leaf_up_fd(GridDims g, int R, const int *__restrict__ origin, Combo rhs,
                                                       double *__restrict__ Rsave, const float *__restrict__ fd32,
                                                       int mp, const double *__restrict__ Dg, float *__restrict__ w32,
                                                       float *__restrict__ h32) {
   extern __shared__ __align__(16) float sfd[];
   const int p = g.p, m = g.m, q = m * m, b = 4 * m, Rp = round4(R), mm = m * mp;
-  float *MT = sfd, *Lam = MT + 4 * mm, *D1x = Lam + mm, *D1y = D1x + p * p;
-  float *Rs = D1x + round4(2 * p * p), *Ts = Rs + q * Rp;
+  float *MT = sfd, *Lam = MT + 4 * mm;
+  const float *D1x = fd32 + 5 * mm, *D1y = D1x + p * p;  // FP32 copies after the factors (L1-cached)
+  float *Rs = Lam + mm, *Ts = Rs + q * Rp;
   const int k = blockIdx.x;
   const int64_t l0 = ((int64_t)origin[2 * k + 1] * g.n1 + origin[2 * k]) * q;
   for (int idx = threadIdx.x; idx < 4 * mm; idx += blockDim.x) {  // transposed line operators
@@ -564,7 +565,6 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_up_fd(GridDims g, int R, const i
     MT[idx] = i < m ? fd32[((size_t)a * m + i) * mp + kk] : 0.f;
   }
   for (int idx = threadIdx.x; idx < mm; idx += blockDim.x) Lam[idx] = fd32[4 * (size_t)mm + idx];
-  for (int i = threadIdx.x; i < 2 * p * p; i += blockDim.x) D1x[i] = d2f_int(Dg[i]);
   if (Rp != R)
     for (int idx = threadIdx.x; idx < q * Rp; idx += blockDim.x) Rs[idx] = 0.f;
   __syncthreads();
@@ -2195,7 +2195,7 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
     H->trace.end(kLeafUp, st);
   } else if (H->fd.on && H->batch.fast_diag && !ops.identity) {
     const int mp = H->fd.mp;
-    const size_t smem = (size_t)(5 * m_of(H) * mp + round4(2 * p * p) + 2 * q * Rp) * sizeof(float);
+    const size_t smem = (size_t)(5 * m_of(H) * mp + 2 * q * Rp) * sizeof(float);
     static size_t set = 0;
     if (smem > 48 * 1024 && smem > set) {
       cudaFuncSetAttribute(k_b_leaf_up_fd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

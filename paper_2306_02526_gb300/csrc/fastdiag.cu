@@ -259,13 +259,17 @@ int fastdiag_build(hps_handle *H, const std::vector<double> &Dh, cudaStream_t st
   const int m = H->m;
   std::vector<double> F[5];
   if (!fastdiag_factor(H->p, Dh.data(), H->cst, H->gamma_dt, false, F, nullptr)) return HPS_OK;
-  // device copies: [Vx, Vx^-1, Vy, Vy^-1, Lam], each m x mp (rows padded to 4 for float4 loads)
+  // device copies: [Vx, Vx^-1, Vy, Vy^-1, Lam], each m x mp (rows padded to 4 for float4 loads);
+  // the FP32 copy is followed by D1x, D1y (p x p each)
   const int mp = (m + 3) & ~3;
   std::vector<double> h64(5 * (size_t)m * mp, 0.0);
   for (int a = 0; a < 5; ++a)
     for (int i = 0; i < m; ++i)
       for (int k = 0; k < m; ++k) h64[((size_t)a * m + i) * mp + k] = F[a][i * m + k];
   std::vector<float> h32(h64.begin(), h64.end());
+  // the batched leaf apply also reads the scaled D1x, D1y in FP32 from here (after the factors)
+  const size_t pp = (size_t)H->p * H->p;
+  for (size_t i = 0; i < 2 * pp; ++i) h32.push_back((float)Dh[i]);
   if (cudaMalloc(&H->fd.d64, h64.size() * sizeof(double)) != cudaSuccess) return HPS_ENOMEM;
   H->allocs.push_back(H->fd.d64);
   if (cudaMalloc(&H->fd.d32, h32.size() * sizeof(float)) != cudaSuccess) return HPS_ENOMEM;
