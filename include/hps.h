@@ -324,7 +324,10 @@ enum {
   HPS_OPT_TILE_COLS_W3 = 20,    /* register-tile columns of the w3 applies (2, 4, 8; 0: PLAN_TILE_COLS) */
   HPS_OPT_TILE_COLS_H = 21,     /* ... of the h applies                                              */
   HPS_OPT_TILE_COLS_DOWN = 22,  /* ... of the u3 (downward) applies                                  */
-  HPS_OPT_COUNT = 23
+  HPS_OPT_FP64_PLAN_TARGET = 23, /* FP64 path (hps_solve, ark_step): merge applies split their columns
+                                   until this many CTAs per SM (1..8, default 3; not while the
+                                   persistent merge kernel is on)                                  */
+  HPS_OPT_COUNT = 24
 };
 int hps_batch_set_option(hps_handle *h, int opt, int value);
 

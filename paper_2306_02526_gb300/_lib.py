@@ -57,7 +57,8 @@ BATCH_OPTIONS = ("tensor_leaf", "even_odd", "flow_levels", "flow_n3_max", "clust
                  "plan_kmin", "plan_npc_max", "split_rhs", "fp64_ctas_per_sm", "group_offset", "last_cta_sum",
                  "fast_diag", "plan_tile_cols", "fuse_epilogue",
                  "fuse_jump", "fold_scale", "sa_close", "edge_projection",
-                 "eo_cols", "tile_cols_w3", "tile_cols_h", "tile_cols_down")
+                 "eo_cols", "tile_cols_w3", "tile_cols_h", "tile_cols_down",
+                 "fp64_plan_target")
 
 
 class hps_server_stats(ctypes.Structure):

@@ -754,9 +754,11 @@ static void drop_batch_graphs(hps_handle *H) {  // (the step-close options reach
   hps::drain_graph(H, H->g_ark_b);
   hps::drain_graph(H, H->g_solve_b);
   hps::drain_graph(H, H->g_ark);
+  hps::drain_graph(H, H->g_solve);
   H->g_ark_b.destroy();
   H->g_solve_b.destroy();
   H->g_ark.destroy();
+  H->g_solve.destroy();
 }
 
 int hps_fastdiag_check(int p, const double *coef, double gamma_dt, double hx, double hy, double *max_err) {

@@ -2797,6 +2797,7 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
     case HPS_OPT_TILE_COLS_W3: field = &Bt.tile_cols_apply[0]; break;
     case HPS_OPT_TILE_COLS_H: field = &Bt.tile_cols_apply[1]; break;
     case HPS_OPT_TILE_COLS_DOWN: field = &Bt.tile_cols_apply[2]; break;
+    case HPS_OPT_FP64_PLAN_TARGET: field = &H->fp64_plan_target; break;
     default: return HPS_EINVAL;
   }
   if (get) *get = field ? *field : (*flag ? 1 : 0);
@@ -2809,6 +2810,20 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
   if (per_apply && *set != 0 && *set != 2 && *set != 4 && *set != 8) return HPS_EINVAL;
   if (v < 0 || (plan && !per_apply && v < 1) || (opt == HPS_OPT_FLOW_LEVELS && v > kFlowMaxLevels)) return HPS_EINVAL;
   if (opt == HPS_OPT_EO_COLS && (v < 1 || v > 32)) return HPS_EINVAL;
+  if (opt == HPS_OPT_FP64_PLAN_TARGET) {  // FP64 split plans: not while the persistent kernel holds tasks
+    if (v < 1 || v > 8 || H->persistent) return HPS_EINVAL;
+    H->fp64_plan_target = v;
+    const size_t need = partial_doubles(H);
+    if (need > H->partial_len) {
+      cudaDeviceSynchronize();
+      double *p = nullptr;
+      if (cudaMalloc(&p, need * sizeof(double)) != cudaSuccess) return HPS_ENOMEM;
+      H->allocs.push_back(p);
+      H->partial = p;
+      H->partial_len = need;
+    }
+    return HPS_OK;
+  }
   if (field) *field = v;
   else *flag = v != 0;
   if (plan) {  // split-K scratch for the new plans

@@ -260,6 +260,7 @@ struct hps_handle {
   std::vector<void *> allocs;
   hps::Trace trace;
   bool persistent = false;    // merge levels by the persistent kernel (else one launch per task)
+  int fp64_plan_target = 3;   // FP64 merge applies: split columns until this many CTAs per SM
   int pgrid = 0;              // its CTA count (co-resident)
   double *ppartial = nullptr; // its split-column partial sums
   size_t ppartial_len = 0;

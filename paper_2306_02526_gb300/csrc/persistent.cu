@@ -197,7 +197,7 @@ int persistent_grid(hps_handle *H) {
 // Task lists of one operator set: upward (w3, h per level, leaves to root) and downward.
 int build_tasks(hps_handle *H, OpSet &ops) {
   if (!persistent_grid(H)) return HPS_ECUDA;
-  const int target = 2 * H->num_sms;  // the same split plan as the per-level path
+  const int target = H->fp64_plan_target * H->num_sms;  // the same split plan as the per-level path
   std::vector<MTask> up, down;
   for (int l = H->L - 1; l >= 0; --l) {
     const Level &lv = H->lev[l];

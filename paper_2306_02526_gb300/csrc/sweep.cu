@@ -562,8 +562,9 @@ size_t partial_doubles(const hps_handle *H) {
   size_t mx = 0;
   for (int l = 0; l < H->L; ++l) {
     const Level &lv = H->lev[l];
-    const GemvPlan P[3] = {plan_gemv(lv.n3, lv.n3, lv.nodes, 2 * H->num_sms), plan_gemv(lv.nb, lv.n3, lv.nodes, 2 * H->num_sms),
-                           plan_gemv(lv.n3, lv.nb, lv.nodes, 2 * H->num_sms)};
+    const int tgt = H->fp64_plan_target * H->num_sms;
+    const GemvPlan P[3] = {plan_gemv(lv.n3, lv.n3, lv.nodes, tgt), plan_gemv(lv.nb, lv.n3, lv.nodes, tgt),
+                           plan_gemv(lv.n3, lv.nb, lv.nodes, tgt)};
     for (const GemvPlan &p : P)
       if (p.ksplit > 1) mx = std::max(mx, (size_t)p.ksplit * p.nodes * p.M);
   }
@@ -602,12 +603,12 @@ int sweep(hps_handle *H, const OpSet &ops, const Combo &rhs, double *Rsave, doub
   for (int l = L - 1; l >= 0 && !H->persistent; --l) {
     const Level &lv = H->lev[l];
     const MergeOps &mo = ops.merge[l];
-    const GemvPlan Pw = plan_gemv(lv.n3, lv.n3, lv.nodes, 2 * H->num_sms);
+    const GemvPlan Pw = plan_gemv(lv.n3, lv.n3, lv.nodes, H->fp64_plan_target * H->num_sms);
     if (int e = launch_gemv(H, kMergeUpW3, Pw, mo.X, mo.ldX, mo.strX, XDiff{H->h[l + 1], lv.nbc, lv.j3a, lv.j3b},
                             EStore{H->w3[l], lv.n3}, st))
       return e;
     if (l > 0) {
-      const GemvPlan Ph = plan_gemv(lv.nb, lv.n3, lv.nodes, 2 * H->num_sms);
+      const GemvPlan Ph = plan_gemv(lv.nb, lv.n3, lv.nodes, H->fp64_plan_target * H->num_sms);
       if (int e = launch_gemv(H, kMergeUpH, Ph, mo.Tcat, mo.ldT, mo.strT, XVec{H->w3[l], lv.n3},
                               EFlux{lv.d_hsrc, H->h[l + 1], lv.nbc, lv.nb, H->h[l]}, st))
         return e;
@@ -616,7 +617,7 @@ int sweep(hps_handle *H, const OpSet &ops, const Combo &rhs, double *Rsave, doub
   for (int l = 0; l < L && !H->persistent; ++l) {
     const Level &lv = H->lev[l];
     const MergeOps &mo = ops.merge[l];
-    const GemvPlan Pd = plan_gemv(lv.n3, lv.nb, lv.nodes, 2 * H->num_sms);
+    const GemvPlan Pd = plan_gemv(lv.n3, lv.nb, lv.nodes, H->fp64_plan_target * H->num_sms);
     if (int e = launch_gemv(H, kMergeDown, Pd, mo.S, mo.ldS, mo.strS, XBoundary{H->g, lv.d_origin, lv.a, lv.c, gvec},
                             EScatter{H->g, lv.d_origin, lv.a, lv.c, lv.split, lv.n3, H->w3[l], gvec}, st))
       return e;

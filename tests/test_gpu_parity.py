@@ -136,6 +136,7 @@ def test_ark_nonlinear_and_inhomogeneous_match_oracle(gname, close):
     S = _gpu_solver(torch, n1, n2, p, coef, 0.25 * dt)
     if close == "sweep":
         S.batch_option("edge_projection", 0)
+        S.batch_option("fp64_plan_target", 1)  # and another split plan of the FP64 merge applies
     c = hps.hps_ark_abscissae()
     u_or = 0.3 * np.sin(math.pi * X) * np.cos(Y)
     u_or[bd] = ff(0.0)
