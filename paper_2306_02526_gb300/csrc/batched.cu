@@ -548,11 +548,11 @@ __device__ __forceinline__ void fd_pass_y(const float *in, float *out, const flo
 
 // One leaf per CTA: stage right-hand side (FP64 combination, saved if requested), the four
 // passes between two shared-memory buffers, then w and the fluxes.  fd32 holds [V_x, V_x^-1,
-// V_y, V_y^-1, Lam], each m x mp.
+// V_y, V_y^-1, Lam], each m x mp, then D1x, D1y (p x p each, read through L1: with 54.7 KB of
+// shared memory and 64 registers four CTAs fit on an SM).
 __global__ void __launch_bounds__(kBT, 4) k_b_leaf_up_fd(GridDims g, int R, const int *__restrict__ origin, Combo rhs,
                                                       double *__restrict__ Rsave, const float *__restrict__ fd32,
-                                                      int mp, const double *__restrict__ Dg, float *__restrict__ w32,
-                                                      float *__restrict__ h32) {
+                                                      int mp, float *__restrict__ w32, float *__restrict__ h32) {
   extern __shared__ __align__(16) float sfd[];
   const int p = g.p, m = g.m, q = m * m, b = 4 * m, Rp = round4(R), mm = m * mp;
   float *MT = sfd, *Lam = MT + 4 * mm;
@@ -2202,7 +2202,7 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
       set = smem;
     }
     H->trace.begin(kLeafUp, st);
-    k_b_leaf_up_fd<<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, H->fd.d32, mp, H->d_D, B.w32,
+    k_b_leaf_up_fd<<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, H->fd.d32, mp, B.w32,
                                                   B.h32[L]);
     H->trace.end(kLeafUp, st);
   } else if (allow_tc && H->batch.afrag_hi && H->batch.tensor_leaf && H->shared && !ops.identity && Rp % 8 == 0 &&
