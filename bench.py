@@ -452,28 +452,27 @@ def bench_ours(args, rank, world, local_rank):
                                "frac": bytes_up / (avg_up * 1e-3) / 1e9 / hbm,
                                "traffic": NCU_TRAFFIC.get((wl.name, "single", "leaf_up"))}}
 
-    # ---- end to end through the C ABI from pinned host buffers -------------------------------
-    def e2e(step, host_in, dev):
-        host_out = torch.empty_like(host_in).pin_memory()
+    # ---- end to end through the C ABI with HOST buffers (ark_step_host / ark_step_batch_host:
+    # host -> device copy of the states, the step, device -> host copy, all inside the call) ----
+    def e2e(step_host, host_u):
         ms = []
         for k in range(max(5, min(args.steps, 20)) + 2):
             flush.fill_(float(k))  # L2 flushed before every step, as in the device-timed runs
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            dev.copy_(host_in, non_blocking=True)
-            step(dev)
-            host_out.copy_(dev, non_blocking=True)
+            step_host(host_u)
             b.record(stream)
             b.synchronize()
             if k >= 2:
                 ms.append(a.elapsed_time(b))
         return statistics.mean(ms), len(ms)
 
-    e64_ms, e_n = e2e(lambda d: fp64_steps(d, 1), torch.tensor(u0, dtype=torch.float64).pin_memory(),
-                      torch.empty(N, dtype=torch.float64, device="cuda"))
-    emx_ms, _ = e2e(mixed_step, torch.tensor(U0, dtype=torch.float64).pin_memory(),
-                    torch.empty((N, R), dtype=torch.float64, device="cuda"))
+    e64_ms, e_n = e2e(lambda hu: S.ark_step_host(hu, 0.0, wl.dt, q=q1, f=f1, g=wl.g, g_param=wl.g_param),
+                      torch.tensor(u0, dtype=torch.float64).pin_memory())
+    emx_ms, _ = e2e(lambda hu: S.ark_step_batch_host(hu, 0.0, wl.dt, q=qR, f=fR, g=wl.g, g_param=wl.g_param,
+                                                     refine=args.refine),
+                    torch.tensor(U0, dtype=torch.float64).pin_memory())
 
     out = None
     if rank == 0:

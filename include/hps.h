@@ -272,10 +272,21 @@ int hps_solve_batch(hps_handle *h, int R, const double *rhs, const double *f, do
                     hps_stream_t stream);
 
 /* ark_step on R states at once (u: N x R in place; terms->q: 6 x N_int x R, terms->f:
- * 6 x N_bd x R, both stage-major, or NULL).  Each implicit stage and the closing identity
- * solve use `refine` FP64 refinement sweeps. */
+ * 6 x N_bd x R, both stage-major, or NULL).  Each implicit stage uses `refine` FP64 refinement
+ * sweeps; the step close solves its identity-operator system directly (HPS_OPT_EDGE_PROJECTION)
+ * or, with that option off, by a sweep with `refine` refinement sweeps. */
 int ark_step_batch(hps_handle *h, int R, double *u, double t, double dt, const hps_ark_terms *terms, int refine,
                    hps_stream_t stream);
+
+/* ark_step / ark_step_batch on states held in HOST memory: u_host (N, resp. N x R doubles,
+ * page-locked for asynchronous copies) is copied into a device buffer the handle keeps, stepped
+ * and copied back, all in order on `stream`; terms are device pointers as above.  The first call
+ * allocates the device buffer (N x Rmax doubles for the batched form, Rmax from
+ * hps_batch_reserve); u_host holds the new states once `stream` has reached the end of the call. */
+int ark_step_host(hps_handle *h, double *u_host, double t, double dt, const hps_ark_terms *terms,
+                  hps_stream_t stream);
+int ark_step_batch_host(hps_handle *h, int R, double *u_host, double t, double dt, const hps_ark_terms *terms,
+                        int refine, hps_stream_t stream);
 
 /* ---- Batched-path kernel variants and their autotuner ------------------------------------
  * Options select among kernel variants of the batched path (all compute the same result to

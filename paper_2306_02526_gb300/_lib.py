@@ -105,6 +105,11 @@ SIGNATURES = {
                                        ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "ark_step_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_double,
                                       ctypes.c_double, ctypes.POINTER(hps_ark_terms), ctypes.c_int, ctypes.c_void_p]),
+    "ark_step_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                     ctypes.POINTER(hps_ark_terms), ctypes.c_void_p]),
+    "ark_step_batch_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_double,
+                                           ctypes.c_double, ctypes.POINTER(hps_ark_terms), ctypes.c_int,
+                                           ctypes.c_void_p]),
     "hps_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "hps_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(hps_job_desc), ctypes.POINTER(ctypes.c_int)]),
     "hps_server_run": (ctypes.c_int, [ctypes.c_void_p]),

@@ -739,6 +739,50 @@ int ark_step(hps_handle *H, double *u, double t, double dt, const hps_ark_terms 
                      (cudaStream_t)stream);
 }
 
+// Device buffer of at least n doubles for the host-buffer steps (kept by the handle).
+static int host_stage(hps_handle *H, size_t n) {
+  if (H->host_stage_len >= n) return HPS_OK;
+  if (H->host_stage) {
+    cudaDeviceSynchronize();  // the old buffer may still be read by queued work
+    cudaFree(H->host_stage);
+    H->allocs.erase(std::remove(H->allocs.begin(), H->allocs.end(), (void *)H->host_stage), H->allocs.end());
+    H->host_stage = nullptr;
+    H->host_stage_len = 0;
+  }
+  if (cudaMalloc(&H->host_stage, n * sizeof(double)) != cudaSuccess) return HPS_ENOMEM;
+  H->allocs.push_back(H->host_stage);
+  H->host_stage_len = n;
+  return HPS_OK;
+}
+
+int ark_step_host(hps_handle *H, double *u_host, double t, double dt, const hps_ark_terms *terms,
+                  hps_stream_t stream) {
+  if (!H || !u_host) return HPS_EINVAL;
+  const size_t n = (size_t)H->g.N;
+  if (int e = host_stage(H, n)) return e;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(H->host_stage, u_host, n * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return HPS_ECUDA;
+  if (int e = ark_step(H, H->host_stage, t, dt, terms, stream)) return e;
+  return cudaMemcpyAsync(u_host, H->host_stage, n * sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess
+             ? HPS_OK
+             : HPS_ECUDA;
+}
+
+int ark_step_batch_host(hps_handle *H, int R, double *u_host, double t, double dt, const hps_ark_terms *terms,
+                        int refine, hps_stream_t stream) {
+  if (!H || !u_host || R <= 0 || R > H->batch.Rmax) return HPS_EINVAL;
+  const size_t n = (size_t)H->g.N * R;
+  if (int e = host_stage(H, (size_t)H->g.N * H->batch.Rmax)) return e;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(H->host_stage, u_host, n * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return HPS_ECUDA;
+  if (int e = ark_step_batch(H, R, H->host_stage, t, dt, terms, refine, stream)) return e;
+  return cudaMemcpyAsync(u_host, H->host_stage, n * sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess
+             ? HPS_OK
+             : HPS_ECUDA;
+}
+
 int hps_batch_reserve_groups(hps_handle *H, int R, int groups) {
   if (!H) return HPS_EINVAL;
   if (groups != H->batch.groups) {  // recorded graphs hold the old groups' buffers and streams

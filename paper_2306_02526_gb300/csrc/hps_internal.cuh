@@ -261,6 +261,8 @@ struct hps_handle {
   hps::Trace trace;
   bool persistent = false;    // merge levels by the persistent kernel (else one launch per task)
   int fp64_plan_target = 3;   // FP64 merge applies: split columns until this many CTAs per SM
+  double *host_stage = nullptr;  // device copy of the states of ark_step(_batch)_host
+  size_t host_stage_len = 0;
   int pgrid = 0;              // its CTA count (co-resident)
   double *ppartial = nullptr; // its split-column partial sums
   size_t ppartial_len = 0;

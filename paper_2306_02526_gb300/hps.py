@@ -79,6 +79,16 @@ def _dptr(t, n, name):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _hptr(t, n, name):
+    """Host pointer of a contiguous float64 CPU tensor (page-locked for asynchronous copies)."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and not t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("%s must be a contiguous float64 CPU tensor" % name)
+    if t.numel() != n:
+        raise ValueError("%s has %d entries, expected %d" % (name, t.numel(), n))
+    return ctypes.c_void_p(t.data_ptr())
+
+
 class HPSSolver:
     """A built handle: the HPS operators of I - gamma_dt L (plus the identity set).
 
@@ -189,6 +199,19 @@ class HPSSolver:
                              _stream_ptr(stream)), "ark_step")
         return u
 
+    def ark_step_host(self, u_host, t, dt, q=None, f=None, g=None, g_param=(1.0, 1.0), stream=None):
+        """ark_step on a state in host memory (ark_step_host): u_host is a float64 CPU tensor of
+        N entries (pin_memory() for asynchronous copies), updated once the stream is done; q, f
+        on the device as for ark_step."""
+        terms = _lib.hps_ark_terms()
+        terms.q = _dptr(q, 6 * self.N_int, "q")
+        terms.f = _dptr(f, 6 * self.N_bd, "f")
+        terms.g_kind = G_KINDS[g]
+        terms.g_param[0], terms.g_param[1] = float(g_param[0]), float(g_param[1])
+        check(lib().ark_step_host(self._h, _hptr(u_host, self.N, "u_host"), float(t), float(dt), ctypes.byref(terms),
+                                  _stream_ptr(stream)), "ark_step_host")
+        return u_host
+
     # ---- batched mixed precision -----------------------------------------------------------
     def batch_reserve(self, R, groups=None):
         """FP32 operator copies and R-column work buffers (hps_batch_reserve); with `groups`,
@@ -241,3 +264,16 @@ class HPSSolver:
         check(lib().ark_step_batch(self._h, R, _dptr(u, self.N * R, "u"), float(t), float(dt), ctypes.byref(terms),
                                    int(refine), _stream_ptr(stream)), "ark_step_batch")
         return u
+
+    def ark_step_batch_host(self, u_host, t, dt, q=None, f=None, g=None, g_param=(1.0, 1.0), refine=2, stream=None):
+        """ark_step_batch on R states in host memory (ark_step_batch_host): u_host (N, R) float64
+        CPU tensor (pin_memory() for asynchronous copies), updated once the stream is done."""
+        R = u_host.shape[1]
+        terms = _lib.hps_ark_terms()
+        terms.q = _dptr(q, 6 * self.N_int * R, "q")
+        terms.f = _dptr(f, 6 * self.N_bd * R, "f")
+        terms.g_kind = G_KINDS[g]
+        terms.g_param[0], terms.g_param[1] = float(g_param[0]), float(g_param[1])
+        check(lib().ark_step_batch_host(self._h, R, _hptr(u_host, self.N * R, "u_host"), float(t), float(dt),
+                                        ctypes.byref(terms), int(refine), _stream_ptr(stream)), "ark_step_batch_host")
+        return u_host

@@ -320,3 +320,30 @@ def test_batch_autotune_keeps_a_correct_configuration():
     err, tuned = _ark_pair(torch, 16, 16, 12, 16, 0.01, autotune=True)
     assert len(tuned) == 8 and all(t["ms"] > 0 for t in tuned)
     assert err <= TOL
+
+
+def test_host_buffer_steps_equal_device_steps():
+    """ark_step_host / ark_step_batch_host (states in page-locked host memory, copies inside the
+    call) give bit for bit the states of ark_step / ark_step_batch on device buffers."""
+    torch = need_gpu()
+    n1, n2, p, dt, R = 4, 2, 10, 0.02, 6
+    g = Grid(n1, n2, p)
+    X, Y = g.coords()
+    bd = g.boundary_indices()
+    S = _solver(torch, n1, n2, p, {"a11": 0.3, "a22": 0.5}, 0.25 * dt)
+    S.batch_reserve(R)
+    u0 = np.stack([0.2 * np.cos(2 * X + 0.3 * j) * np.sin(4 * Y) for j in range(R)], axis=1)
+    u0[bd, :] = 0.0
+    ud = to_dev(torch, u0)
+    uh = torch.tensor(u0, dtype=torch.float64).pin_memory()
+    vd = to_dev(torch, u0[:, 0].copy())
+    vh = torch.tensor(u0[:, 0].copy(), dtype=torch.float64).pin_memory()
+    for n in range(3):
+        S.ark_step_batch(ud, n * dt, dt, g="allen_cahn", g_param=(1.0, 0.0), refine=1)
+        S.ark_step_batch_host(uh, n * dt, dt, g="allen_cahn", g_param=(1.0, 0.0), refine=1)
+        S.ark_step(vd, n * dt, dt, g="allen_cahn", g_param=(1.0, 0.0))
+        S.ark_step_host(vh, n * dt, dt, g="allen_cahn", g_param=(1.0, 0.0))
+    torch.cuda.synchronize()
+    assert torch.equal(ud.cpu(), uh)
+    assert torch.equal(vd.cpu(), vh)
+    S.close()
