@@ -288,10 +288,12 @@ int ark_step_host(hps_handle *h, double *u_host, double t, double dt, const hps_
 int ark_step_batch_host(hps_handle *h, int R, double *u_host, double t, double dt, const hps_ark_terms *terms,
                         int refine, hps_stream_t stream);
 
-/* ---- Batched-path kernel variants and their autotuner ------------------------------------
- * Options select among kernel variants of the batched path (all compute the same result to
- * the mixed-precision tolerance).  Setting one drops the recorded graphs of the batched calls
- * and, for the split-K plan options, re-sizes the split-K scratch (synchronizes the device). */
+/* ---- Kernel variants and their autotuner --------------------------------------------------
+ * Options select among kernel variants (all compute the same result to the path's tolerance:
+ * 1e-10 for the batched mixed-precision path, 1e-12 for FP64).  Most belong to the batched path;
+ * HPS_OPT_EDGE_PROJECTION and HPS_OPT_FP64_PLAN_TARGET also reach ark_step / hps_solve.  Setting
+ * one drops the recorded graphs of the batched and FP64 calls and, for the split-K plan options
+ * (HPS_OPT_FP64_PLAN_TARGET included), re-sizes the split-K scratch (synchronizes the device). */
 enum {
   HPS_OPT_TENSOR_LEAF = 0,      /* 1: first sweep of a solve applies the shared leaf operator by
                                    3xTF32 warp MMA on the tensor cores (default 1)                */
