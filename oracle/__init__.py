@@ -18,6 +18,8 @@ Modules (each function cites the passage of the paper it follows):
                    densely (brute force for tiny trees).
 * ``tableau``   -- ARK4(3)6L[2]SA Butcher tables in exact rational arithmetic (Table ``tbl:butcher``).
 * ``ark``       -- the additive Runge-Kutta step in stage form (eq. ``stage2``).
+* ``ark_slope`` -- the step in slope form for g = 0 (eq. ``slope0``) with penalized interface
+                   conditions (Sec. 3.1, penalization in the slope formulation).
 * ``nonlinear`` -- the nonlinear terms g(u) used by the tests (leaf-local differentiation).
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test in ``tests/test_oracle_*.py``.
