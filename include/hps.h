@@ -278,6 +278,17 @@ int hps_solve_batch(hps_handle *h, int R, const double *rhs, const double *f, do
 int ark_step_batch(hps_handle *h, int R, double *u, double t, double dt, const hps_ark_terms *terms, int refine,
                    hps_stream_t stream);
 
+/* One ARK4(3)6L[2]SA step in slope form (Sec. 3.1, eq. slope0) for g = 0, FP64, on u (N, in
+ * place): slopes k_1 = L u^n + q_1 (explicit; its shared-edge values from the identity-operator
+ * system), (I - gamma dt L) k_i = L u^n + dt sum_{j<i} a_ij L k_j + q_i (one HPS solve each),
+ * u^{n+1} = u^n + dt sum_j b_j k_j at every point.  Every slope system's interface rows carry
+ * -1/dt times the flux jump of u^n (the penalization of Sec. 3.1), so u^{n+1} has no flux jump.
+ * terms->q: 6 x N_int stage sources or NULL; terms->f: 6 x N_bd slope boundary data, i.e. u_t at
+ * t + c_i dt on the boundary, or NULL for zero (time-independent Dirichlet data); terms->g_kind
+ * must be HPS_G_NONE.  Needs at least two leaves and the per-level merge kernels (not
+ * hps_set_persistent); the first call allocates 7 N doubles of work memory. */
+int ark_slope_step(hps_handle *h, double *u, double t, double dt, const hps_ark_terms *terms, hps_stream_t stream);
+
 /* ark_step / ark_step_batch on states held in HOST memory: u_host (N, resp. N x R doubles,
  * page-locked for asynchronous copies) is copied into a device buffer the handle keeps, stepped
  * and copied back, all in order on `stream`; terms are device pointers as above.  The first call

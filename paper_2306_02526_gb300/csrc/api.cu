@@ -739,6 +739,18 @@ int ark_step(hps_handle *H, double *u, double t, double dt, const hps_ark_terms 
                      (cudaStream_t)stream);
 }
 
+int ark_slope_step(hps_handle *H, double *u, double t, double dt, const hps_ark_terms *terms, hps_stream_t stream) {
+  if (!H || !u || !(dt > 0.0) || !std::isfinite(t)) return HPS_EINVAL;
+  if (std::fabs(0.25 * dt - H->gamma_dt) > 1e-12 * H->gamma_dt) return HPS_EDT;
+  if ((terms && terms->g_kind != HPS_G_NONE) || H->persistent) return HPS_EINVAL;
+  hps::ArkTable tab;
+  const Tableau &tb = tableau();
+  std::memcpy(tab.A, tb.A, sizeof(tab.A));
+  std::memcpy(tab.Ah, tb.Ah, sizeof(tab.Ah));
+  std::memcpy(tab.b, tb.b, sizeof(tab.b));
+  return hps::ark_slope(H, u, dt, terms, tab, (cudaStream_t)stream);
+}
+
 // Device buffer of at least n doubles for the host-buffer steps (kept by the handle).
 static int host_stage(hps_handle *H, size_t n) {
   if (H->host_stage_len >= n) return HPS_OK;

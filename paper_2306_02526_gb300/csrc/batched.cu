@@ -2013,7 +2013,8 @@ __global__ void __launch_bounds__(kBT) k_b_close_leaf(GridDims g, const int *__r
 // k_b_edge_tridiag: one thread per grid line of shared edges and column; forward elimination
 // with the host's Thomas factors (w_L, 1/b_L) into rhs, back substitution into u.
 __global__ void k_b_edge_tridiag(GridDims g, int R, double *__restrict__ rhs, double *__restrict__ u,
-                                 const double *__restrict__ proj, double lox, double upx, double loy, double upy) {
+                                 const double *__restrict__ proj, double lox, double upx, double loy, double upy,
+                                 const double *__restrict__ J) {
   const int64_t nvl = (int64_t)g.n2 * g.m, nhl = (int64_t)g.n1 * g.m;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (nvl + nhl) * R) return;
@@ -2035,7 +2036,7 @@ __global__ void k_b_edge_tridiag(GridDims g, int R, double *__restrict__ rhs, do
     double r[kTB];
 #pragma unroll
     for (int t = 0; t < kTB; ++t)
-      if (L0 + t < n) r[t] = rhs[at(L0 + t)];
+      if (L0 + t < n) r[t] = J ? rhs[at(L0 + t)] + J[at(L0 + t)] : rhs[at(L0 + t)];
 #pragma unroll
     for (int t = 0; t < kTB; ++t) {
       const int L = L0 + t;
@@ -2485,7 +2486,10 @@ int residual(hps_handle *H, BatchWork &B, int R, const double *u, const double *
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
-int edge_projection_impl(hps_handle *H, int R, const Combo &c, double *u, double *rhs, cudaStream_t st) {
+// J (or null): interface right-hand side, A_if u = J instead of 0 (added to each line's
+// right-hand side in the tridiagonal kernel, after the two leaves' flux sums).
+int edge_projection_impl(hps_handle *H, int R, const Combo &c, double *u, double *rhs, cudaStream_t st,
+                         const double *J = nullptr) {
   const GridDims &g = H->g;
   const Level &leaf = H->lev[H->L];
   if (cudaMemsetAsync(rhs + g.N_int * R, 0, (size_t)(g.N - g.N_int) * R * sizeof(double), st) != cudaSuccess)
@@ -2495,7 +2499,7 @@ int edge_projection_impl(hps_handle *H, int R, const Combo &c, double *u, double
   k_b_close_leaf<<<leaf.nodes, kBT, smem, st>>>(g, leaf.d_origin, R, c, u, rhs, H->d_D);
   const int64_t nsys = ((int64_t)g.n2 * g.m + (int64_t)g.n1 * g.m) * R;
   k_b_edge_tridiag<<<blocks(nsys, 128), 128, 0, st>>>(g, R, rhs, u, H->d_proj, H->proj_lo[0], H->proj_up[0],
-                                                       H->proj_lo[1], H->proj_up[1]);
+                                                       H->proj_lo[1], H->proj_up[1], J);
   H->trace.end(kClose, st);
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
@@ -2695,8 +2699,17 @@ void batch_release(hps_handle *H) {
   Bt.fork = nullptr;
 }
 
-int edge_projection(hps_handle *H, int R, const Combo &c, double *u, double *rhs, cudaStream_t st) {
-  return edge_projection_impl(H, R, c, u, rhs, st);
+int edge_projection(hps_handle *H, int R, const Combo &c, double *u, double *rhs, cudaStream_t st, const double *J) {
+  return edge_projection_impl(H, R, c, u, rhs, st, J);
+}
+
+int flux_jump_rhs(hps_handle *H, int R, const double *u, double *r, cudaStream_t st) {
+  const int64_t npts = ((int64_t)(H->g.n1 - 1) * H->g.n2 + (int64_t)(H->g.n2 - 1) * H->g.n1) * H->m;
+  if (npts == 0) return HPS_OK;
+  H->trace.begin(kJump, st);
+  k_b_jump<<<blocks(npts * R), 256, 0, st>>>(H->g, R, u, r, H->d_D);
+  H->trace.end(kJump, st);
+  return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
 int batch_reserve(hps_handle *H, int R, int groups) {

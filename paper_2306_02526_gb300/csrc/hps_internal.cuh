@@ -263,6 +263,7 @@ struct hps_handle {
   int fp64_plan_target = 3;   // FP64 merge applies: split columns until this many CTAs per SM
   double *host_stage = nullptr;  // device copy of the states of ark_step(_batch)_host
   size_t host_stage_len = 0;
+  double *slope_k = nullptr;     // slope form: 6 scaled slopes (N each) and the interface right-hand side
   int pgrid = 0;              // its CTA count (co-resident)
   double *ppartial = nullptr; // its split-column partial sums
   size_t ppartial_len = 0;
@@ -295,7 +296,7 @@ struct Epilogue {          // fused ARK stage epilogue at the leaves (a5)
 };
 
 int sweep(hps_handle *H, const OpSet &ops, const Combo &rhs, double *Rsave, double *gvec,
-          double *out_interior, const Epilogue *ep, cudaStream_t st);
+          double *out_interior, const Epilogue *ep, cudaStream_t st, const double *jump = nullptr);
 int set_boundary(hps_handle *H, double *gvec, const double *f, cudaStream_t st);
 size_t partial_doubles(const hps_handle *H);  // split-K scratch the merge applies need
 void drain_graph(hps_handle *H, GraphEntry &e);  // read the timing events of the last replay
@@ -319,13 +320,19 @@ int batch_reserve(hps_handle *H, int R, int groups);
 int batch_option(hps_handle *H, int opt, const int *set, int *get);
 // edge projection of the step close (batched.cu): u interior = combination `c`, u boundary as
 // given, shared-edge values from flux continuity; rhs: [N][R] scratch
-int edge_projection(hps_handle *H, int R, const Combo &c, double *u, double *rhs, cudaStream_t st);
+int edge_projection(hps_handle *H, int R, const Combo &c, double *u, double *rhs, cudaStream_t st,
+                    const double *J = nullptr);  // J: interface right-hand side (global vector) or null
+// r = -(flux jump of u) at every shared-edge point, (west/south flux) - (east/north flux) negated
+int flux_jump_rhs(hps_handle *H, int R, const double *u, double *r, cudaStream_t st);
+
 int batch_autotune(hps_handle *H, int R, int refine, cudaStream_t st, hps_tune_result *res, int max_res, int *n_res);
 void batch_release(hps_handle *H);
 int solve_batch(hps_handle *H, int R, const double *rhs, const double *f, double *u, int refine, cudaStream_t st);
 struct ArkTable {
   double A[6][6], Ah[6][6], b[6];
 };
+// one ARK step in slope form (g = 0), FP64, single state (slope.cu)
+int ark_slope(hps_handle *H, double *u, double dt, const hps_ark_terms *terms, const ArkTable &tb, cudaStream_t st);
 int ark_batch(hps_handle *H, int R, double *u, double dt, const hps_ark_terms *terms, int refine, const ArkTable &tb,
               cudaStream_t st);
 int leaf_eval(hps_handle *H, const double *u, double *KL, double *KE, const double *q, double dt,

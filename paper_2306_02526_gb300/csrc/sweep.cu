@@ -285,11 +285,17 @@ GemvPlan plan_gemv(int M, int K, int nodes, int target_ctas) {
 }
 
 // x loaders
-struct XDiff {  // d = h^b_3 - h^a_3 from the children's fluxes
+struct XDiff {  // d = h^b_3 - h^a_3 from the children's fluxes (+ the interface right-hand side)
   const double *hC;
   int nbc, j3a, j3b;
-  __device__ double operator()(int k, int c) const {
-    return hC[(int64_t)(2 * k + 1) * nbc + j3b + c] - hC[(int64_t)(2 * k) * nbc + j3a + c];
+  const double *jump;  // global vector read at interface points, or null
+  GridDims g;
+  const int *origin;
+  int a, c, split;
+  __device__ double operator()(int k, int cc) const {
+    double d = hC[(int64_t)(2 * k + 1) * nbc + j3b + cc] - hC[(int64_t)(2 * k) * nbc + j3a + cc];
+    if (jump) d += jump[iface_bd(g, origin[2 * k], origin[2 * k + 1], a, c, split, cc)];
+    return d;
   }
 };
 struct XVec {
@@ -572,8 +578,9 @@ size_t partial_doubles(const hps_handle *H) {
 }
 
 int sweep(hps_handle *H, const OpSet &ops, const Combo &rhs, double *Rsave, double *gvec, double *out_interior,
-          const Epilogue *ep, cudaStream_t st) {
+          const Epilogue *ep, cudaStream_t st, const double *jump) {
   const int L = H->L, p = H->p, q = H->q, b = H->b;
+  if (jump && H->persistent) return HPS_EINVAL;  // the persistent merge kernel has no interface input
   const Level &leaf = H->lev[L];
   const int lpc = leaf_lpc(q);
   const int lthreads = std::min(512, ((lpc * q + 31) / 32) * 32);
@@ -604,7 +611,8 @@ int sweep(hps_handle *H, const OpSet &ops, const Combo &rhs, double *Rsave, doub
     const Level &lv = H->lev[l];
     const MergeOps &mo = ops.merge[l];
     const GemvPlan Pw = plan_gemv(lv.n3, lv.n3, lv.nodes, H->fp64_plan_target * H->num_sms);
-    if (int e = launch_gemv(H, kMergeUpW3, Pw, mo.X, mo.ldX, mo.strX, XDiff{H->h[l + 1], lv.nbc, lv.j3a, lv.j3b},
+    if (int e = launch_gemv(H, kMergeUpW3, Pw, mo.X, mo.ldX, mo.strX,
+                            XDiff{H->h[l + 1], lv.nbc, lv.j3a, lv.j3b, jump, H->g, lv.d_origin, lv.a, lv.c, lv.split},
                             EStore{H->w3[l], lv.n3}, st))
       return e;
     if (l > 0) {

@@ -199,6 +199,17 @@ class HPSSolver:
                              _stream_ptr(stream)), "ark_step")
         return u
 
+    def ark_slope_step(self, u, t, dt, q=None, kbc=None, stream=None):
+        """One ARK step in slope form for g = 0 (ark_slope_step) in place on u: q (6, N_int) stage
+        sources or None; kbc (6, N_bd) slope boundary data (u_t at the stage times) or None (zero)."""
+        terms = _lib.hps_ark_terms()
+        terms.q = _dptr(q, 6 * self.N_int, "q")
+        terms.f = _dptr(kbc, 6 * self.N_bd, "kbc")
+        terms.g_kind = G_KINDS[None]
+        check(lib().ark_slope_step(self._h, _dptr(u, self.N, "u"), float(t), float(dt), ctypes.byref(terms),
+                                   _stream_ptr(stream)), "ark_slope_step")
+        return u
+
     def ark_step_host(self, u_host, t, dt, q=None, f=None, g=None, g_param=(1.0, 1.0), stream=None):
         """ark_step on a state in host memory (ark_step_host): u_host is a float64 CPU tensor of
         N entries (pin_memory() for asynchronous copies), updated once the stream is done; q, f
