@@ -396,6 +396,27 @@ def bench_ours(args, rank, world, local_rank):
         args.steps, args.warmup = 2, 1
         qR, fR = stage_terms(R)
 
+    # ---- slope form (g = 0 only): the workload's linear part on the same operators, FP64 ----------
+    slope = None
+    if args.only is None:
+        us = torch.tensor(u0, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            S.ark_slope_step(us, 0.0, wl.dt)
+        torch.cuda.synchronize()
+        se = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+        for k in range(10):
+            flush.fill_(float(k))
+            se[k][0].record(stream)
+            S.ark_slope_step(us, 0.0, wl.dt)
+            se[k][1].record(stream)
+        torch.cuda.synchronize()
+        sms = [a.elapsed_time(b) for a, b in se]
+        assert torch.isfinite(us).all(), "slope-form state went non-finite"
+        slope = {"value": N * STAGES * len(sms) / (sum(sms) * 1e-3), "unit": "DOF*stages/s",
+                 "ms_per_step": sum(sms) / len(sms), "steps": len(sms), "launch": "eager",
+                 "note": "slope form with penalized interface rows (g = 0): u_t = L u of the workload, "
+                         "same grid and operators, FP64, L2 flushed before every step"}
+
     # ---- mixed precision, R right-hand sides (FP32 sweeps + FP64 refinement) ----------------------
     S.batch_reserve(R, groups=args.groups)
     U0 = np.stack([u0] + [workloads.uniform_state(j, N, bidx) for j in range(1, R)], axis=1)
@@ -544,6 +565,7 @@ def bench_ours(args, rank, world, local_rank):
                     if mixed_ok else fp64["e2e"]),
             "clocks": head["clocks"],
             "fp64_single_rhs": fp64,
+            "fp64_slope_form": slope,
             "fp32_single_rhs_solve": single,
             "mixed_over_fp64": value_mixed / value64,
             "build_s": build_s, "wall_s": head["wall"],
