@@ -160,7 +160,9 @@ int hps_ark_abscissae(double *c);
  * + dt sum_j ahat_ij (q_j + g_j) with u_i = f(t_i) on the boundary; L u^n by leaf-local
  * differentiation, dt L u_j = (u_j - R_j)/gamma for j >= 2; then
  * u^{n+1} = u^n + dt sum_j b_j L u_j + dt sum_j bhat_j (q_j + g_j) at interior points,
- * f(t + dt) on the boundary and shared-edge values from the identity-operator solve.
+ * f(t + dt) on the boundary and shared-edge values from the identity-operator system (flux
+ * continuity with those interior values), solved directly as one tridiagonal system per grid
+ * line of shared edges (HPS_OPT_EDGE_PROJECTION, default) or by an identity-operator sweep.
  * The handle must have been built with gamma_dt == dt/4 (else HPS_EDT).  No allocation,
  * no host synchronization: the call can be captured in a CUDA graph. */
 int ark_step(hps_handle *h, double *u, double t, double dt, const hps_ark_terms *terms,
