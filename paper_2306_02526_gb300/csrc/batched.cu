@@ -2494,7 +2494,12 @@ int edge_projection_impl(hps_handle *H, int R, const Combo &c, double *u, double
   const Level &leaf = H->lev[H->L];
   if (cudaMemsetAsync(rhs + g.N_int * R, 0, (size_t)(g.N - g.N_int) * R * sizeof(double), st) != cudaSuccess)
     return HPS_ECUDA;
-  const size_t smem = (size_t)(4 * H->p + H->q * std::min(R, kCloseRc)) * sizeof(double);
+  const size_t smem = (size_t)(4 * H->p + H->q * std::min(R, kCloseRc)) * sizeof(double);  // <= 116 KB (p <= 32)
+  static size_t set = 0;
+  if (smem > 48 * 1024 && smem > set) {
+    cudaFuncSetAttribute(k_b_close_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set = smem;
+  }
   H->trace.begin(kClose, st);
   k_b_close_leaf<<<leaf.nodes, kBT, smem, st>>>(g, leaf.d_origin, R, c, u, rhs, H->d_D);
   const int64_t nsys = ((int64_t)g.n2 * g.m + (int64_t)g.n1 * g.m) * R;

@@ -171,7 +171,7 @@ def test_fused_stage_epilogue_with_sources(gname, groups):
     assert rel_max(outs[0], outs[1]) <= 1e-13
 
 
-@pytest.mark.parametrize("n1,n2,p,R", [(1, 1, 6, 3), (1, 4, 7, 5), (8, 2, 9, 6), (2, 2, 16, 33)])
+@pytest.mark.parametrize("n1,n2,p,R", [(1, 1, 6, 3), (1, 4, 7, 5), (8, 2, 9, 6), (2, 2, 16, 33), (2, 1, 26, 16)])
 def test_ark_batch_close_on_degenerate_trees_matches_oracle(n1, n2, p, R):
     """Batched step (constant coefficients, a source, boundary data) on a single leaf, a column
     of leaves, odd p and a rectangle, R not a multiple of 4 (and > 32): 2 steps against the
