@@ -71,6 +71,56 @@ def test_burgers_type_nonlinearity_fourth_order():
     assert rates[-1] > 3.6, (errs, rates)
 
 
+def _reaction_mms(g_fn, g_closed, kappa):
+    """Manufactured solution u = 0.8 sin(pi x) sin(pi y) e^{-t} of u_t = eps Lap u + g(u) + q with
+    q = u_t - eps Lap u - g_closed(u): the oracle's g must cancel the source's reaction term exactly,
+    so a dropped factor or a wrong sign in g leaves an O(1) error instead of 4th-order convergence."""
+    g = Grid(2, 2, 12)
+    X, Y = g.coords()
+    I, bd = np.arange(g.N_int), g.boundary_indices()
+    eps = 0.1
+    cf = {"a11": eps, "a22": eps}
+    ue = lambda t: 0.8 * np.sin(np.pi * X) * np.sin(np.pi * Y) * np.exp(-t)
+
+    def q(t):
+        u = ue(t)
+        return (-u + eps * 2 * np.pi ** 2 * u - g_closed(u))[I]
+
+    prob = ark.Problem(g, cf, q=q, f=lambda t: ue(t)[bd], g=g_fn(kappa))
+    errs = [np.abs(run(prob, cf, ue(0.0), 1.0, n) - ue(1.0)).max() for n in (8, 16, 32)]
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    return errs, rates
+
+
+def test_allen_cahn_manufactured_fourth_order():
+    """g = kappa (u - u^3) (Sec. 5: Allen-Cahn reaction), kappa = 2.5: 4th order in dt with the
+    manufactured source written from the equation, and small absolute error."""
+    k = 2.5
+    errs, rates = _reaction_mms(nonlinear.allen_cahn, lambda u: k * (u - u ** 3), k)
+    assert rates[-1] > 3.6 and rates[-1] < 4.6, (errs, rates)
+    assert errs[-1] < 1e-6, errs
+
+
+def test_fisher_manufactured_fourth_order():
+    """g = kappa u (1 - u) (Fisher-KPP reaction), kappa = 2.5: 4th order in dt with the manufactured
+    source written from the equation, and small absolute error."""
+    k = 2.5
+    errs, rates = _reaction_mms(nonlinear.fisher, lambda u: k * u * (1.0 - u), k)
+    assert rates[-1] > 3.6 and rates[-1] < 4.6, (errs, rates)
+    assert errs[-1] < 1e-6, errs
+
+
+def test_reaction_mms_detects_planted_errors():
+    """The manufactured test above fails for a g with a dropped kappa or a flipped sign (mistakes
+    planted in a copy of the oracle's g, on the CPU)."""
+    k = 2.5
+    dropped = lambda kappa: nonlinear.fisher(1.0)
+    flipped = lambda kappa: (lambda grid, u: -nonlinear.allen_cahn(kappa)(grid, u))
+    for bad, closed in ((dropped, lambda u: k * u * (1.0 - u)), (flipped, lambda u: k * (u - u ** 3))):
+        errs, rates = _reaction_mms(bad, closed, k)
+        assert errs[-1] > 1e-3, errs
+
+
 def test_inhomogeneous_bc_converges_with_order_reduction():
     """Sec. 3.1.2 / Sec. 5.3: time-dependent Dirichlet data in the stage form loses order."""
     g = Grid(2, 2, 12)
