@@ -47,8 +47,13 @@ def parse():
     ap.add_argument("--serving-jobs", type=int, default=48, help="jobs of the serving run (0: skip)")
     ap.add_argument("--refine", type=int, default=1, help="FP64 refinement sweeps per implicit solve (mixed)")
     ap.add_argument("--groups", type=int, default=1, help="column groups of the mixed batch (own streams each)")
+    ap.add_argument("--per-node-workload", default="varcoef_128x128_p16",
+                    help="workload of the per-node-operator section (single-RHS HBM-bound solve, mixed vs FP64); "
+                         "'none' skips it")
+    ap.add_argument("--per-node-refine", type=int, default=2, help="refinement sweeps of its mixed ARK step")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-budget", type=float, default=12.0, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-steps", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -75,29 +80,48 @@ def oracle_setup(wname):
     return g, H, rhs, build_s
 
 
-def cpu_sample(wname, budget):
-    """Time full-size oracle stage solves until `budget` seconds have passed (at least one)."""
+def cpu_sample(wname, budget, steps=0, warmup=0):
+    """Time full-size oracle stage solves: `warmup` untimed, then `steps` timed (steps = 0: until
+    `budget` seconds have passed, at least one)."""
     g, H, rhs, build_s = oracle_setup(wname)
+    for _ in range(warmup):
+        H.solve(rhs)
     n, t0 = 0, time.perf_counter()
     while True:
         H.solve(rhs)
         n += 1
         el = time.perf_counter() - t0
-        if el >= budget:
+        if (steps and n >= steps) or (not steps and el >= budget):
             break
     return {"solves": n, "seconds": el, "N": g.N, "build_s": build_s, "leaves": "%dx%d" % (g.n1, g.n2)}
 
 
-def run_cpu_sample_subprocess(wname, budget):
+def run_cpu_sample_subprocess(wname, budget, threads=1, steps=0, warmup=0):
+    """The oracle in a child process whose BLAS / OpenMP pools have `threads` threads."""
     env = dict(os.environ)
-    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[k] = "1"
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = str(threads)
     env["CUDA_VISIBLE_DEVICES"] = ""
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", wname, "--cpu-budget", str(budget)],
-                       capture_output=True, text=True, env=env, timeout=900)
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", wname, "--cpu-budget", str(budget),
+           "--cpu-steps", str(steps), "--warmup", str(warmup)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1200)
     if r.returncode != 0:
         raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    out["threads"] = threads
+    return out
+
+
+def best_oracle_threads(wname, budget):
+    """Short oracle samples with 1, 4 and all host threads in the BLAS pool; the fastest setting
+    and every sample's rate (DOF x stage solves / s)."""
+    cores = os.cpu_count() or 1
+    rates = {}
+    for th in sorted({1, min(4, cores), cores}):
+        smp = run_cpu_sample_subprocess(wname, budget, th)
+        rates[th] = smp["N"] * smp["solves"] / smp["seconds"]
+    best = max(rates, key=rates.get)
+    return best, rates
 
 
 # ---------------------------------------------------------------------------------------------
@@ -185,6 +209,18 @@ def tree_levels(n1, n2, m):
             c //= 2
         nodes *= 2
     return out
+
+
+def solve_operator_elems(n1, n2, p):
+    """Operator elements one single-RHS HPS solve with per-node operators reads (each once): per leaf
+    A_ii^{-1} (q x q) and S (q x b); per merge node X (n3 x n3), S^t (n3 x nb) and [T^a_13; T^b_23]
+    (nb x n3), the root without the last."""
+    m = p - 2
+    q, b = m * m, 4 * m
+    lv = tree_levels(n1, n2, m)
+    leaves = n1 * n2 * (q * q + q * b)
+    merges = sum(nodes * (n3 * n3 + 2 * n3 * nb) for nodes, n3, nb in lv) - lv[0][1] * lv[0][2]
+    return leaves, merges
 
 
 def merge_flops_per_launch(slot, n1, n2, m, cols):
@@ -436,43 +472,6 @@ def bench_ours(args, rank, world, local_rank):
         errs.append(float((U[:, j] - ref).abs().max() / ref.abs().max()))
     err_mixed = max(errs)
 
-    # ---- per-node operators: one right-hand side through the FP32 sweep (HBM-bound) --------------
-    single = None
-    if S.nodal:
-        rhs1 = torch.tensor(np.random.default_rng(3).uniform(-0.1, 0.1, (N_int, 1)), dtype=torch.float64,
-                            device="cuda")
-        u1 = torch.empty((N, 1), dtype=torch.float64, device="cuda")
-        for _ in range(3):
-            S.solve_batch(rhs1, u=u1, refine=args.refine)
-        S.trace_enable(("leaf_up",))
-        for _ in range(2):
-            S.solve_batch(rhs1, u=u1, refine=args.refine)
-        S.trace_enable(("leaf_up",))
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        for k in range(args.steps):
-            flush.fill_(float(k))
-            ev[k][0].record(stream)
-            S.solve_batch(rhs1, u=u1, refine=args.refine)
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
-        tr1 = S.trace_read()
-        solve_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
-        q_, b_ = (wl.p - 2) ** 2, 4 * (wl.p - 2)
-        nleaf_ = N_int // q_
-        ld32 = (q_ + 3) // 4 * 4
-        # algorithmic bytes of one k_b_leaf_up launch (R = 1): the leaf's FP32 A_ii^{-1} (stored
-        # transposed with rows padded to 4) + FP64 right-hand side in + FP32 w and fluxes out
-        bytes_up = nleaf_ * (q_ * ld32 * 4 + q_ * 8 + q_ * 4 + b_ * 4)
-        avg_up = tr1["leaf_up"][2] / max(1, tr1["leaf_up"][1])
-        hbm = measured_peaks().get("hbm_gbs", 6800.0)
-        single = {"solve_ms": solve_ms, "refine": args.refine,
-                  "value": N / (solve_ms * 1e-3), "unit": "DOF*solves/s",
-                  "roofline": {"kernel": "leaf_up", "bound": "hbm", "unit": "GB/s", "bytes_per_launch": bytes_up,
-                               "avg_launch_ms": avg_up, "achieved": bytes_up / (avg_up * 1e-3) / 1e9, "peak": hbm,
-                               "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
-                               "frac": bytes_up / (avg_up * 1e-3) / 1e9 / hbm,
-                               "traffic": NCU_TRAFFIC.get((wl.name, "single", "leaf_up"))}}
-
     # ---- end to end through the C ABI with HOST buffers (ark_step_host / ark_step_batch_host:
     # host -> device copy of the states, the step, device -> host copy, all inside the call) ----
     def e2e(step_host, host_u):
@@ -566,13 +565,156 @@ def bench_ours(args, rank, world, local_rank):
             "clocks": head["clocks"],
             "fp64_single_rhs": fp64,
             "fp64_slope_form": slope,
-            "fp32_single_rhs_solve": single,
+            "fp32_single_rhs_solve": None,
             "mixed_over_fp64": value_mixed / value64,
             "build_s": build_s, "wall_s": head["wall"],
         }
     S.close()
+    if rank == 0 and out is not None and args.only is None and args.per_node_workload != "none":
+        out["per_node"] = bench_per_node(args, flush)
+        pn = out["per_node"]
+        out["fp32_single_rhs_solve"] = pn["fp32_sweep_solve"]
     if rank == 0 and out is not None and args.serving_jobs > 0 and args.only is None:
         out["serving"] = bench_serving(args)
+    return out
+
+
+def bench_per_node(args, flush):
+    """Per-node operators (variable coefficients, 128 x 128 leaves, p = 16 by default), one GPU:
+      * single-RHS solves, each with the L2 flushed before it: the FP64 HPS solve; one FP32 sweep
+        (hps_solve_batch, R = 1, no refinement); the refined FP32 solve (1 FP64 refinement sweep);
+        whole-solve rooflines from the algorithmic bytes (operators read once + 6 N vector words),
+        the FP64 one against min(HBM, FP64 pipe) time;
+      * the ARK step: FP64 with one state against the batched mixed-precision step with --rhs states
+        and --per-node-refine refinement sweeps, error of columns 0 and R-1 against the FP64 path."""
+    import numpy as np
+    import torch
+    from paper_2306_02526_gb300 import hps, workloads
+    wl = workloads.WORKLOADS[args.per_node_workload]
+    tree = hps.Tree(wl.n1, wl.n2)
+    N, N_int, N_bd = hps.hps_sizes(tree, wl.p)
+    x, y = hps.hps_coords(tree, wl.p)
+    bidx = hps.hps_boundary_index(tree, wl.p)
+    I = np.arange(N_int)
+    coef = wl.coef(x[I], y[I])
+    cdev = {k: torch.tensor(np.broadcast_to(v, (N_int,)).copy(), dtype=torch.float64, device="cuda")
+            for k, v in coef.items()}
+    t0 = time.perf_counter()
+    S = hps.HPSSolver(tree, wl.p, cdev, 0.25 * wl.dt)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    S.set_graph(True)
+    stream = torch.cuda.current_stream()
+    hbm = measured_peaks().get("hbm_gbs", 6800.0)
+    peak_src = "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in measured_peaks() else "fallback 6800 GB/s"
+    leaves, merges = solve_operator_elems(wl.n1, wl.n2, wl.p)
+
+    def timed(fn, n, trace=()):
+        for _ in range(3):
+            fn()
+        S.trace_enable(trace)
+        for _ in range(2):  # eager + recording (the graph then carries the trace events)
+            fn()
+        S.trace_enable(trace)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for k in range(n):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            fn()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev], S.trace_read()
+
+    def shares(fn, n=3):
+        from paper_2306_02526_gb300 import _lib
+        _, tr = timed(fn, n, _lib.KERNELS)
+        tot = sum(v[2] for v in tr.values()) or 1.0
+        return {k: {"launches": v[0] // n, "ms": round(v[2] / n, 4), "share": round(v[2] / tot, 4)}
+                for k, v in tr.items() if v[0]}
+
+    out = {"workload": wl.name, "n1": wl.n1, "n2": wl.n2, "p": wl.p, "N": N, "build_s": build_s,
+           "operators": "one per tree node (nodal coefficients)",
+           "operator_elements": {"leaves": leaves, "merges": merges, "leaf_share": leaves / (leaves + merges)}}
+    rhs = torch.tensor(np.random.default_rng(3).uniform(-0.1, 0.1, N_int), dtype=torch.float64, device="cuda")
+    u64 = torch.empty(N, dtype=torch.float64, device="cuda")
+    # ---- FP64 single-RHS solve ----
+    ms64, _ = timed(lambda: S.solve(rhs, u=u64), 10)
+    t64 = statistics.mean(ms64)
+    flops = 2.0 * (leaves + merges)
+    sm_mhz = 2070.0
+    peak_fp64 = 152 * 2 * 2 * sm_mhz * 1e6
+    bytes64 = (leaves + merges + 6 * N) * 8
+    t_ideal = max(bytes64 / (hbm * 1e9), flops / peak_fp64)
+    out["fp64_solve"] = {
+        "ms": t64, "value": N / (t64 * 1e-3), "unit": "DOF*solves/s",
+        "roofline": {"bound": "alu" if flops / peak_fp64 > bytes64 / (hbm * 1e9) else "hbm",
+                     "bytes": bytes64, "flops": flops, "ideal_ms": t_ideal * 1e3, "frac": t_ideal * 1e3 / t64,
+                     "achieved_gbs": bytes64 / (t64 * 1e-3) / 1e9, "achieved_tflops": flops / (t64 * 1e-3) / 1e12,
+                     "peak_gbs": hbm, "peak_tflops": peak_fp64 / 1e12,
+                     "peak_source": "%s; FP64 152 SMs x 2 DFMA x 2 flop x %.0f MHz" % (peak_src, sm_mhz),
+                     "note": "ideal time = max(bytes / HBM, flops / FP64 pipe); frac = ideal / measured"},
+        "kernel_shares": shares(lambda: S.solve(rhs, u=u64))}
+    # ---- FP32 sweeps, one right-hand side (the HBM-bound form) ----
+    S.batch_reserve(1)
+    r1 = rhs.reshape(N_int, 1).contiguous()
+    ub = torch.empty((N, 1), dtype=torch.float64, device="cuda")
+    bytes32 = (leaves + merges) * 4 + 6 * N * 4
+    for refine in (0, 1):
+        ms32, tr = timed(lambda: S.solve_batch(r1, u=ub, refine=refine), 10, ("leaf_up",))
+        t32 = statistics.mean(ms32)
+        err = float((ub[:, 0] - u64).abs().max() / u64.abs().max())
+        alg = bytes32 * (refine + 1) + refine * (N_int * 5 + 3 * N) * 8  # + the FP64 residual's vectors
+        up_ms = tr["leaf_up"][2] / max(1, tr["leaf_up"][1])
+        q_, b_ = (wl.p - 2) ** 2, 4 * (wl.p - 2)
+        up_bytes = wl.n1 * wl.n2 * (q_ * ((q_ + 3) // 4 * 4) * 4 + q_ * 8 + q_ * 4 + b_ * 4)
+        out["fp32_sweep_solve" if refine == 0 else "fp32_refined_solve"] = {
+            "ms": t32, "refine": refine, "err_vs_fp64": err, "value": N / (t32 * 1e-3), "unit": "DOF*solves/s",
+            "roofline": {"bound": "hbm", "unit": "GB/s", "bytes": alg, "achieved": alg / (t32 * 1e-3) / 1e9,
+                         "peak": hbm, "peak_source": peak_src, "frac": alg / (t32 * 1e-3) / 1e9 / hbm,
+                         "note": "bytes = %d sweep(s) x (FP32 operators read once + 6 N FP32 vector words)%s"
+                                 % (refine + 1, " + the FP64 residual's vectors" if refine else "")},
+            "leaf_up": {"avg_launch_ms": up_ms, "bytes_per_launch": up_bytes,
+                        "achieved": up_bytes / (up_ms * 1e-3) / 1e9, "frac": up_bytes / (up_ms * 1e-3) / 1e9 / hbm},
+            "kernel_shares": shares(lambda: S.solve_batch(r1, u=ub, refine=refine))}
+    # ---- ARK step: FP64 (1 state) vs batched mixed precision (R states) ----
+    c = hps.hps_ark_abscissae()
+    qs = None
+    if wl.q(x[:1], y[:1], 0.0) is not None:
+        qs = np.stack([wl.q(x[I], y[I], cj * wl.dt) for cj in c])
+    q1 = None if qs is None else torch.tensor(qs.reshape(-1), dtype=torch.float64, device="cuda")
+    u0 = wl.u0(x, y, bidx)
+    u = torch.tensor(u0, dtype=torch.float64, device="cuda")
+    step64 = lambda uu: S.ark_step(uu, 0.0, wl.dt, q=q1, g=wl.g, g_param=wl.g_param)
+    ms_s64, _ = timed(lambda: step64(u), 5)
+    R = args.rhs
+    S.batch_reserve(R)
+    qR = None if qs is None else torch.tensor(np.repeat(qs[:, :, None], R, axis=2), dtype=torch.float64,
+                                              device="cuda")
+    U0 = np.stack([u0] + [workloads.uniform_state(j, N, bidx) for j in range(1, R)], axis=1)
+    U = torch.tensor(U0, dtype=torch.float64, device="cuda")
+    stepmx = lambda: S.ark_step_batch(U, 0.0, wl.dt, q=qR, g=wl.g, g_param=wl.g_param, refine=args.per_node_refine)
+    ms_mx, _ = timed(stepmx, 5)
+    nsteps = 3 + 2 + 5
+    errs = []
+    ref = torch.empty(N, dtype=torch.float64, device="cuda")
+    for j in sorted({0, R - 1}):
+        ref.copy_(torch.from_numpy(U0[:, j].copy()))
+        for _ in range(nsteps):
+            step64(ref)
+        errs.append(float((U[:, j] - ref).abs().max() / ref.abs().max()))
+    v64 = N * STAGES / (statistics.mean(ms_s64) * 1e-3)
+    vmx = R * N * STAGES / (statistics.mean(ms_mx) * 1e-3)
+    out["ark_step"] = {"fp64": {"value": v64, "unit": "DOF*stages/s", "ms_per_step": statistics.mean(ms_s64),
+                                "p50_step_ms": statistics.median(ms_s64), "steps": len(ms_s64)},
+                       "mixed": {"value": vmx, "unit": "DOF*stages/s", "ms_per_step": statistics.mean(ms_mx),
+                                 "p50_step_ms": statistics.median(ms_mx), "steps": len(ms_mx), "rhs": R,
+                                 "refine": args.per_node_refine, "err_vs_fp64": max(errs),
+                                 "err_columns": sorted({0, R - 1}), "steps_compared": nsteps},
+                       "mixed_over_fp64": vmx / v64,
+                       "mixed_kernel_shares": shares(stepmx, 2)}
+    out["l2"] = "flushed (512 MB write) before every timed solve / step"
+    out["launch"] = "CUDA graph replay (hps_set_graph)"
+    S.close()
     return out
 
 
@@ -612,30 +754,25 @@ def bench_serving(args):
 
 
 def bench_reference(args, rank, world):
+    """The oracle (the reference arm of this measurement) on the host cores: the BLAS thread count
+    is chosen by short probes (1, 4, all threads), then W untimed and K timed full-size stage
+    solves run in a child process with that many threads."""
     if rank != 0:
         return None
-    import numpy as np  # noqa: F401
-    g, H, rhs, build_s = oracle_setup(args.workload)
-    t0 = time.perf_counter()
-    H.solve(rhs)
-    est = time.perf_counter() - t0
-    steps = max(1, min(args.steps, int(150.0 / max(est, 1e-3))))
-    for _ in range(min(args.warmup, 1)):
-        H.solve(rhs)
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        H.solve(rhs)
-    el = time.perf_counter() - t0
-    value = g.N * steps / el
-    cores = os.cpu_count()
+    th, rates = best_oracle_threads(args.workload, 4.0)
+    smp = run_cpu_sample_subprocess(args.workload, 0.0, th, steps=args.steps, warmup=min(args.warmup, 1))
+    value = smp["N"] * smp["solves"] / smp["seconds"]
     return {
         "impl": "reference", "metric": "DOF*stages/s (N x implicit HPS stage solves per second, ARK4(3)6L[2]SA step)",
-        "value": value, "unit": "DOF*stages/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup,
-        "ms_per_step": el / steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic", "config": {"workload": args.workload, "N": g.N},
-        "cpu_baseline": {"value": value, "unit": "DOF*stages/s", "cores": cores, "kind": "oracle",
-                         "sample": "%d full-size oracle stage solves (one step = one stage solve); oracle build %.1f s "
-                                   "not timed" % (steps, build_s)},
+        "value": value, "unit": "DOF*stages/s", "n_gpus": 1, "steps": smp["solves"], "warmup": args.warmup,
+        "ms_per_step": smp["seconds"] / smp["solves"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": args.workload, "N": smp["N"]},
+        "cpu_baseline": {"value": value, "unit": "DOF*stages/s", "cores": th, "kind": "oracle",
+                         "sample": "%d full-size oracle stage solves (one step = one stage solve) with %d BLAS/OpenMP "
+                                   "threads, the fastest of %s (probe rates %s; host has %d cores); oracle build "
+                                   "%.1f s not timed" % (smp["solves"], th, sorted(rates),
+                                                         {k: "%.3g" % v for k, v in rates.items()}, os.cpu_count(),
+                                                         smp["build_s"])},
         "e2e": {"value": value, "unit": "DOF*stages/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -643,7 +780,7 @@ def bench_reference(args, rank, world):
 def main():
     args = parse()
     if args.cpu_sample:
-        print(json.dumps(cpu_sample(args.cpu_sample, args.cpu_budget)))
+        print(json.dumps(cpu_sample(args.cpu_sample, args.cpu_budget, args.cpu_steps, args.warmup)))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -657,16 +794,22 @@ def main():
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        cpu = run_cpu_sample_subprocess(args.workload, args.cpu_budget)  # before any GPU work in this process
+    if rank == 0 and not args.no_cpu_baseline:  # before any GPU work in this process
+        th, rates = best_oracle_threads(args.workload, 4.0)
+        cpu = run_cpu_sample_subprocess(args.workload, args.cpu_budget, th)
+        cpu["probe_rates"] = rates
     out = bench_ours(args, rank, world, local_rank)
     if rank == 0 and out is not None:
         if cpu is not None:
             out["cpu_baseline"] = {"value": cpu["N"] * cpu["solves"] / cpu["seconds"], "unit": "DOF*stages/s",
-                                   "cores": 1, "kind": "oracle",
-                                   "sample": "%d oracle stage solves on %s leaves (p as the workload) in %.1f s on "
-                                             "one host thread (BLAS threads = 1); oracle build %.1f s not timed"
-                                             % (cpu["solves"], cpu["leaves"], cpu["seconds"], cpu["build_s"])}
+                                   "cores": cpu["threads"], "kind": "oracle",
+                                   "sample": "%d oracle stage solves on %s leaves (p as the workload) in %.1f s with "
+                                             "%d BLAS/OpenMP threads, the fastest of %s threads (probe rates %s); "
+                                             "oracle build %.1f s not timed"
+                                             % (cpu["solves"], cpu["leaves"], cpu["seconds"], cpu["threads"],
+                                                sorted(cpu["probe_rates"]),
+                                                {k: "%.3g" % v for k, v in cpu["probe_rates"].items()},
+                                                cpu["build_s"])}
         print(json.dumps(out))
     if world > 1:
         torch.distributed.destroy_process_group()

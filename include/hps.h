@@ -126,9 +126,8 @@ int hps_solve(hps_handle *h, const double *rhs, const double *f, double *u, hps_
  * the one array and it keeps the last call's contents (every entry a call reads it writes
  * first, except the few counters of the merge kernel, which each call clears): calls that
  * overlap on the GPU -- on different streams or different handles -- race and must be
- * serialized by the caller.  A bounded wait that runs out in this call is reported by the
- * call's own error word inside the array, which is not read back: check results with
- * hps_solve when in doubt. */
+ * serialized by the caller.  With hps_set_persistent on, a bounded wait that runs out in this
+ * call is recorded in the handle's error word as for hps_solve (hps_status reports it). */
 int hps_solve_static(hps_handle *h, const double *rhs, const double *f, double *u, hps_stream_t stream);
 
 /* Nonlinear term presets g(u) (Sec. 1: at most first derivatives), evaluated at interior

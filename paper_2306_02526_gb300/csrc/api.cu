@@ -3,6 +3,8 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <map>
+#include <mutex>
 #include <unordered_map>
 
 #include "hps_internal.cuh"
@@ -435,6 +437,23 @@ int hps_build(const hps_tree *tree, int p, const hps_coeffs *coeffs, double gamm
 }  // extern "C"
 
 namespace hps {
+
+int smem_optin(const void *kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return HPS_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HPS_ECUDA;
+  static std::mutex mu;
+  static std::map<std::pair<const void *, int>, size_t> done;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t &have = done[{kernel, dev}];
+  if (bytes <= have) return HPS_OK;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return HPS_ECUDA;
+  }
+  have = bytes;
+  return HPS_OK;
+}
 
 // The per-call work buffers of a handle (everything a solve writes besides the caller's vectors).
 int alloc_work(hps_handle *H, cudaStream_t st) {

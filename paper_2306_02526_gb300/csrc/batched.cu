@@ -1208,13 +1208,9 @@ int launch_b(hps_handle *H, BatchWork &B, int slot, const BPlan &P, const float 
              EP ep, cudaStream_t st) {
   const size_t smem = b_smem_floats(P) * sizeof(float);
   if (P.ksplit > 1 && (size_t)P.ksplit * P.nodes * P.M * P.Rp > B.partial_len) return HPS_EINVAL;
-  static size_t set = 0;
-  if (smem > 48 * 1024 && smem > set) {
-    cudaFuncSetAttribute(k_b_gemv<8, XL, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_b_gemv<4, XL, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_b_gemv<2, XL, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    set = smem;
-  }
+  if (int e_ = smem_optin((const void *)k_b_gemv<8, XL, EP>, smem)) return e_;
+  if (int e_ = smem_optin((const void *)k_b_gemv<4, XL, EP>, smem)) return e_;
+  if (int e_ = smem_optin((const void *)k_b_gemv<2, XL, EP>, smem)) return e_;
   H->trace.begin(slot, st);
   const dim3 grid(P.node_groups * P.row_tiles, P.ksplit);
   // split-K sums: in the kernel (last CTA of a tile) unless the tiles are too many or too deep
@@ -1348,12 +1344,7 @@ int launch_b2(hps_handle *H, BatchWork &B, int slot, int M, int K, int nodes, in
     return launch_b(H, B, slot, plan_b(M, K, nodes, R, plan_target(H), str == 0, plan_tune(H, slot)), AT, ld, str,
                     xl, ep, st);
   auto kern = P.TC == 8 ? k_b_gemv2<8, XL, EP> : k_b_gemv2<4, XL, EP>;
-  static size_t set8 = 0, set4 = 0;
-  size_t &set = P.TC == 8 ? set8 : set4;
-  if (smem > 48 * 1024 && smem > set) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    set = smem;
-  }
+  if (int e_ = smem_optin((const void *)kern, smem)) return e_;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)(P.RT * nodes), (unsigned)P.C, 1);
   cfg.blockDim = dim3(kBT, 1, 1);
@@ -2156,12 +2147,7 @@ inline int m_of(const hps_handle *H) { return H->m; }
 int flow_launch(hps_handle *H, BatchWork &B, const FlowArgs &FA, bool up, size_t smem, int nflags, cudaStream_t st) {
   if ((size_t)nflags + 1 > B.flow_len) return HPS_EINVAL;
   auto kern = up ? k_b_flow_up : k_b_flow_down;
-  static size_t set_up = 0, set_down = 0;
-  size_t &set = up ? set_up : set_down;
-  if (smem > 48 * 1024 && smem > set) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    set = smem;
-  }
+  if (int e_ = smem_optin((const void *)kern, smem)) return e_;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBT, smem) != cudaSuccess || per_sm < 1)
     return HPS_ECUDA;
@@ -2185,11 +2171,7 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
   const int QQ = (q + 3) / 4, KS = std::max(1, kBT / QQ);
   if (narrow) {
     const size_t smem = (size_t)(round4(2 * p * p) + 8 * q + KS * 16 * QQ) * sizeof(float);
-    static size_t set = 0;
-    if (smem > 48 * 1024 && smem > set) {
-      cudaFuncSetAttribute(k_b_leaf_up_narrow, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      set = smem;
-    }
+    if (int e_ = smem_optin((const void *)k_b_leaf_up_narrow, smem)) return e_;
     H->trace.begin(kLeafUp, st);
     k_b_leaf_up_narrow<<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, o32.Ainv.p, o32.Ainv.ld,
                                                       o32.Ainv.str, ops.identity ? 1 : 0, H->d_D, B.w32, B.h32[L]);
@@ -2197,11 +2179,7 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
   } else if (H->fd.on && H->batch.fast_diag && !ops.identity) {
     const int mp = H->fd.mp;
     const size_t smem = (size_t)(5 * m_of(H) * mp + 2 * q * Rp) * sizeof(float);
-    static size_t set = 0;
-    if (smem > 48 * 1024 && smem > set) {
-      cudaFuncSetAttribute(k_b_leaf_up_fd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      set = smem;
-    }
+    if (int e_ = smem_optin((const void *)k_b_leaf_up_fd, smem)) return e_;
     H->trace.begin(kLeafUp, st);
     k_b_leaf_up_fd<<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, H->fd.d32, mp, B.w32,
                                                   B.h32[L]);
@@ -2213,11 +2191,7 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
     const size_t smem = (size_t)(round4(2 * p * p) + 2 * KT * 8 * tc_rs(Rp)) * sizeof(float);
     auto kern = NT == 4 ? k_b_leaf_up_tc<4> : NT == 3 ? k_b_leaf_up_tc<3> : NT == 2 ? k_b_leaf_up_tc<2>
                                                                                    : k_b_leaf_up_tc<1>;
-    static size_t set[5] = {0, 0, 0, 0, 0};
-    if (smem > 48 * 1024 && smem > set[NT]) {
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      set[NT] = smem;
-    }
+    if (int e_ = smem_optin((const void *)kern, smem)) return e_;
     H->trace.begin(kLeafUp, st);
     kern<<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, reinterpret_cast<const uint4 *>(H->batch.afrag_hi),
                                         reinterpret_cast<const uint4 *>(H->batch.afrag_lo), MT, KT, H->d_D, B.w32,
@@ -2225,12 +2199,8 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
     H->trace.end(kLeafUp, st);
   } else {
     const size_t smem = (size_t)(round4(2 * p * p) + 2 * q * Rp) * sizeof(float);
-    static size_t set = 0;
-    if (smem > 48 * 1024 && smem > set) {
-      cudaFuncSetAttribute(k_b_leaf_up<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      cudaFuncSetAttribute(k_b_leaf_up<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      set = smem;
-    }
+    if (int e_ = smem_optin((const void *)k_b_leaf_up<8>, smem)) return e_;
+    if (int e_ = smem_optin((const void *)k_b_leaf_up<4>, smem)) return e_;
     H->trace.begin(kLeafUp, st);
     const float *r32 = nullptr;
     if (H->batch.leaf_split) {  // stage right-hand side as its own streaming pass
@@ -2348,12 +2318,7 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
     const size_t smem = (size_t)(b * o32.Sleaf.ld + (b + q) * Rp) * sizeof(float);
     const bool t8 = tc8;
     auto kern = t8 ? k_b_leaf_down_res<8> : k_b_leaf_down_res<4>;
-    static size_t set8 = 0, set4 = 0;
-    size_t &set = t8 ? set8 : set4;
-    if (smem > 48 * 1024 && smem > set) {
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      set = smem;
-    }
+    if (int e_ = smem_optin((const void *)kern, smem)) return e_;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBT, smem) != cudaSuccess || per_sm < 1)
       return HPS_ECUDA;
@@ -2364,12 +2329,7 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
     const int staged = (size_t)(b + q) * Rp * sizeof(float) <= 96 * 1024;  // coalesced output through smem
     const size_t smem = (size_t)(staged ? b + q : b) * Rp * sizeof(float);
     auto kern = tc8 ? k_b_leaf_down<8> : k_b_leaf_down<4>;
-    static size_t set8 = 0, set4 = 0;
-    size_t &set = tc8 ? set8 : set4;
-    if (smem > 48 * 1024 && smem > set) {
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      set = smem;
-    }
+    if (int e_ = smem_optin((const void *)kern, smem)) return e_;
     kern<<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, o32.Sleaf.p, o32.Sleaf.ld, o32.Sleaf.str,
                                         ops.identity ? 1 : 0, staged, B.w32, B.g32, uo);
   }
@@ -2442,11 +2402,7 @@ int leaf64(hps_handle *H, Leaf64Args A, cudaStream_t st, bool *flux_done = nullp
     } else {
       A.flux_r = nullptr;
     }
-    static size_t set = 0;
-    if (smem > 48 * 1024 && smem > set) {
-      cudaFuncSetAttribute(k_b_leaf64_eo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      set = smem;
-    }
+    if (int e_ = smem_optin((const void *)k_b_leaf64_eo, smem)) return e_;
     H->trace.begin(slot, st);
     k_b_leaf64_eo<<<grid, kBT, smem, st>>>(H->g, leaf.nodes, leaf.d_origin, A, H->d_D);
     H->trace.end(slot, st);
@@ -2455,11 +2411,7 @@ int leaf64(hps_handle *H, Leaf64Args A, cudaStream_t st, bool *flux_done = nullp
   const int Rc = std::max(1, std::min(A.R, 4096 / pp));
   const size_t smem = (size_t)(4 * pp + pp * Rc) * sizeof(double);
   A.flux_r = nullptr;
-  static size_t set = 0;
-  if (smem > 48 * 1024 && smem > set) {
-    cudaFuncSetAttribute(k_b_leaf64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    set = smem;
-  }
+  if (int e_ = smem_optin((const void *)k_b_leaf64, smem)) return e_;
   H->trace.begin(slot, st);
   k_b_leaf64<<<grid, kBT, smem, st>>>(H->g, leaf.nodes, leaf.d_origin, A, H->d_D);
   H->trace.end(slot, st);
@@ -2495,11 +2447,7 @@ int edge_projection_impl(hps_handle *H, int R, const Combo &c, double *u, double
   if (cudaMemsetAsync(rhs + g.N_int * R, 0, (size_t)(g.N - g.N_int) * R * sizeof(double), st) != cudaSuccess)
     return HPS_ECUDA;
   const size_t smem = (size_t)(4 * H->p + H->q * std::min(R, kCloseRc)) * sizeof(double);  // <= 116 KB (p <= 32)
-  static size_t set = 0;
-  if (smem > 48 * 1024 && smem > set) {
-    cudaFuncSetAttribute(k_b_close_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    set = smem;
-  }
+  if (int e_ = smem_optin((const void *)k_b_close_leaf, smem)) return e_;
   H->trace.begin(kClose, st);
   k_b_close_leaf<<<leaf.nodes, kBT, smem, st>>>(g, leaf.d_origin, R, c, u, rhs, H->d_D);
   const int64_t nsys = ((int64_t)g.n2 * g.m + (int64_t)g.n1 * g.m) * R;

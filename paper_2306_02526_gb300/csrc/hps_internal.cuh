@@ -308,6 +308,11 @@ int merge_persistent(hps_handle *H, const OpSet &ops, bool upward, double *gvec,
 int selftest_barrier(hps_handle *H, cudaStream_t st);
 
 // ---- handle services (api.cu) ----------------------------------------------------------------
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` on the CURRENT device (the
+// attribute is per device).  Remembers the largest value set per (kernel, device) under a lock,
+// so every host thread and every device gets the attribute before its first large launch.
+// HPS_OK, or HPS_ECUDA when the runtime refuses the value.
+int smem_optin(const void *kernel, size_t bytes);
 int alloc_work(hps_handle *H, cudaStream_t st);
 int clone_handle(const hps_handle *base, cudaStream_t st, hps_handle **out);
 int bytes_split(const hps_tree *tree, int p, int coeff_kind, int flags, size_t *ops, size_t *work);

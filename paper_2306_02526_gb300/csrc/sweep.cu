@@ -435,11 +435,7 @@ template <class XL, class EP>
 int launch_gemv(hps_handle *H, int slot, const GemvPlan &P, const double *AT, int ld, int64_t str, XL xl, EP ep,
                 cudaStream_t st) {
   const size_t smem = (size_t)P.npc * P.kchunk * sizeof(double);
-  static size_t smem_set = 0;  // per instantiation
-  if (smem > 48 * 1024 && smem > smem_set) {
-    cudaFuncSetAttribute(k_gemv_t<XL, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    smem_set = smem;
-  }
+  if (int e_ = smem_optin((const void *)k_gemv_t<XL, EP>, smem)) return e_;
   if (P.ksplit > 1 && (size_t)P.ksplit * P.nodes * P.M > H->partial_len) return HPS_EINVAL;
   H->trace.begin(slot, st);
   dim3 grid(P.node_groups * P.row_tiles, P.ksplit);
@@ -587,11 +583,7 @@ int sweep(hps_handle *H, const OpSet &ops, const Combo &rhs, double *Rsave, doub
   const unsigned lgrid = (unsigned)((leaf.nodes + lpc - 1) / lpc);
   if (H->fd.on && H->batch.fast_diag && !ops.identity) {
     const size_t smem = (size_t)(2 * p * p + 5 * H->m * H->m + 2 * lpc * q) * sizeof(double);
-    static size_t set = 0;
-    if (smem > 48 * 1024 && smem > set) {
-      cudaFuncSetAttribute(k_leaf_up_fd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      set = smem;
-    }
+    if (int e_ = smem_optin((const void *)k_leaf_up_fd, smem)) return e_;
     H->trace.begin(kLeafUp, st);
     k_leaf_up_fd<<<lgrid, lthreads, smem, st>>>(H->g, leaf.nodes, leaf.d_origin, rhs, Rsave, H->fd.d64, H->fd.mp,
                                                 H->d_D, H->wleaf, H->h[L]);
