@@ -21,6 +21,12 @@ double *g_scratch_addr[kMaxDevices] = {};
 
 inline size_t round256(size_t n) { return (n + 31) & ~size_t(31); }  // 32 doubles = 256 bytes
 
+// Carries a timeout recorded in this call's error word (inside the static array) into the
+// handle's own error word, which hps_status reads; an earlier unreported timeout is kept.
+__global__ void k_fold_error(const int *__restrict__ call_err, int *__restrict__ handle_err) {
+  if (threadIdx.x == 0 && *call_err != 0) *handle_err = *call_err;
+}
+
 }  // namespace
 
 extern "C" int hps_solve_static(hps_handle *H, const double *rhs, const double *f, double *u, hps_stream_t stream) {
@@ -85,6 +91,10 @@ extern "C" int hps_solve_static(hps_handle *H, const double *rhs, const double *
     c.coef[0] = 1.0;
     c.n = 1;
     e = hps::sweep(H, H->impl, c, nullptr, u, u, nullptr, st);
+  }
+  if (e == HPS_OK && H->persistent) {  // the bounded waits of the persistent merge kernel report here
+    k_fold_error<<<1, 32, 0, st>>>(H->perr, saved_err);
+    if (cudaPeekAtLastError() != cudaSuccess) e = HPS_ECUDA;
   }
   H->wleaf = saved_w;
   H->partial = saved_partial;

@@ -24,14 +24,25 @@ def _static_solve(S, rhs, f, u):
                                        ctypes.c_void_p(u.data_ptr()), stream)
 
 
-def test_static_solve_matches_hps_solve_twice():
+@pytest.mark.parametrize("case", ["nodal", "nodal_persistent", "const_fast_diag"])
+def test_static_solve_matches_hps_solve_twice(case):
+    """Per-level merge launches on per-node operators; the persistent merge kernel (its partial
+    sums, tile counters, barrier and error word then also sit in the static array); constant
+    coefficients with the fast-diagonalization leaf apply."""
     torch = need_gpu()
     from paper_2306_02526_gb300 import _lib, hps, workloads
     n1, n2, p = 8, 4, 10
     tree = hps.Tree(n1, n2, -0.2, 1.3, 0.0, 0.75)
     N, N_int, N_bd = hps.hps_sizes(tree, p)
-    coef = {k: to_dev(torch, v) for k, v in workloads.random_coefficients(11, N_int).items()}
+    if case == "const_fast_diag":
+        coef = {"a11": 0.8, "a22": 1.1, "a1": 0.2, "a2": -0.1, "a0": -0.4}
+    else:
+        coef = {k: to_dev(torch, v) for k, v in workloads.random_coefficients(11, N_int).items()}
     S = hps.HPSSolver(tree, p, coef, 0.017)
+    if case == "nodal_persistent":
+        S.set_persistent(True)
+    if case == "const_fast_diag":
+        assert S.batch_option("fast_diag") == 1
     r = np.random.default_rng(5)
     for call in range(2):  # two calls in a row: the array keeps the previous call's contents
         rhs = to_dev(torch, r.standard_normal(N_int))
@@ -41,6 +52,7 @@ def test_static_solve_matches_hps_solve_twice():
         assert _static_solve(S, rhs, f, u) == _lib.HPS_OK
         got = u.cpu().numpy()
         assert rel_max(got, want) <= 1e-12
+    S.status()  # no bounded wait ran out (the static call's error word was folded into the handle's)
     S.close()
 
 
