@@ -51,6 +51,8 @@ def parse():
                     help="workload of the per-node-operator section (single-RHS HBM-bound solve, mixed vs FP64); "
                          "'none' skips it")
     ap.add_argument("--per-node-refine", type=int, default=2, help="refinement sweeps of its mixed ARK step")
+    ap.add_argument("--per-node-umma", type=int, default=2, choices=[0, 1, 2],
+                    help="its leaf applies on the tcgen05 tensor cores: 0 none, 1 first sweeps, 2 every sweep")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-budget", type=float, default=12.0, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-steps", type=int, default=0, help=argparse.SUPPRESS)
@@ -688,6 +690,7 @@ def bench_per_node(args, flush):
     ms_s64, _ = timed(lambda: step64(u), 5)
     R = args.rhs
     S.batch_reserve(R)
+    S.batch_option("umma_leaf", args.per_node_umma)  # tensor-core leaf applies (per-node operators)
     qR = None if qs is None else torch.tensor(np.repeat(qs[:, :, None], R, axis=2), dtype=torch.float64,
                                               device="cuda")
     U0 = np.stack([u0] + [workloads.uniform_state(j, N, bidx) for j in range(1, R)], axis=1)
@@ -709,6 +712,7 @@ def bench_per_node(args, flush):
                        "mixed": {"value": vmx, "unit": "DOF*stages/s", "ms_per_step": statistics.mean(ms_mx),
                                  "p50_step_ms": statistics.median(ms_mx), "steps": len(ms_mx), "rhs": R,
                                  "refine": args.per_node_refine, "err_vs_fp64": max(errs),
+                                 "umma_leaf": args.per_node_umma,
                                  "err_columns": sorted({0, R - 1}), "steps_compared": nsteps},
                        "mixed_over_fp64": vmx / v64,
                        "mixed_kernel_shares": shares(stepmx, 2)}

@@ -352,7 +352,13 @@ enum {
   HPS_OPT_FP64_PLAN_TARGET = 23, /* FP64 path (hps_solve, ark_step): merge applies split their columns
                                    until this many CTAs per SM (1..8, default 3; not while the
                                    persistent merge kernel is on)                                  */
-  HPS_OPT_COUNT = 24
+  HPS_OPT_UMMA_LEAF = 24,       /* 1: the first sweep of a solve applies PER-NODE leaf operators (variable
+                                   coefficients, q <= 256, 16 or 32 columns) on the 5th-generation
+                                   tensor cores: tcgen05.mma kind::tf32 with 3xTF32 products and the
+                                   accumulator in tensor memory, operator boxes streamed by TMA
+                                   (default 1); 2: every sweep, the refinement sweeps included;
+                                   0: FP32 FFMA                                                     */
+  HPS_OPT_COUNT = 25
 };
 int hps_batch_set_option(hps_handle *h, int opt, int value);
 

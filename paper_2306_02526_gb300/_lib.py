@@ -58,7 +58,7 @@ BATCH_OPTIONS = ("tensor_leaf", "even_odd", "flow_levels", "flow_n3_max", "clust
                  "fast_diag", "plan_tile_cols", "fuse_epilogue",
                  "fuse_jump", "fold_scale", "sa_close", "edge_projection",
                  "eo_cols", "tile_cols_w3", "tile_cols_h", "tile_cols_down",
-                 "fp64_plan_target")
+                 "fp64_plan_target", "umma_leaf")
 
 
 class hps_server_stats(ctypes.Structure):

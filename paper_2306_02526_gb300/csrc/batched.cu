@@ -13,6 +13,7 @@
 #include <cstdlib>
 
 #include "hps_internal.cuh"
+#include "tc5.cuh"
 
 namespace hps {
 
@@ -264,18 +265,18 @@ __device__ __forceinline__ float4 flux4(int e, int j0, int Rp, const float *W, c
 // and h32 (its fluxes on the b edge points), four columns per thread step.
 __device__ __forceinline__ void leaf_up_out(int64_t k, int q, int b, int R, int Rp, const float *Ws, const float *D1x,
                                             const float *D1y, int p, int m, float *__restrict__ w32,
-                                            float *__restrict__ h32) {
+                                            float *__restrict__ h32, int t0, int nt) {
   const int Rq = Rp / 4;
   if (R == Rp) {
     float4 *wo = reinterpret_cast<float4 *>(w32 + k * q * R);
-    for (int i = threadIdx.x; i < q * Rq; i += blockDim.x) wo[i] = reinterpret_cast<const float4 *>(Ws)[i];
+    for (int i = t0; i < q * Rq; i += nt) wo[i] = reinterpret_cast<const float4 *>(Ws)[i];
   } else {
-    for (int idx = threadIdx.x; idx < q * R; idx += blockDim.x) {
+    for (int idx = t0; idx < q * R; idx += nt) {
       const int r = idx / R, j = idx - r * R;
       w32[(k * q + r) * R + j] = Ws[r * Rp + j];
     }
   }
-  for (int i = threadIdx.x; i < b * Rq; i += blockDim.x) {
+  for (int i = t0; i < b * Rq; i += nt) {
     const int e = i / Rq, j0 = 4 * (i - e * Rq);
     const float4 f = flux4(e, j0, Rp, Ws, D1x, D1y, p, m);
     float *o = h32 + (k * b + e) * R + j0;
@@ -286,6 +287,11 @@ __device__ __forceinline__ void leaf_up_out(int64_t k, int q, int b, int R, int 
       for (int t = 0; t < 4 && j0 + t < R; ++t) o[t] = fv[t];
     }
   }
+}
+__device__ __forceinline__ void leaf_up_out(int64_t k, int q, int b, int R, int Rp, const float *Ws, const float *D1x,
+                                            const float *D1y, int p, int m, float *__restrict__ w32,
+                                            float *__restrict__ h32) {
+  leaf_up_out(k, q, b, R, Rp, Ws, D1x, D1y, p, m, w32, h32, (int)threadIdx.x, (int)blockDim.x);
 }
 
 // The boundary values of box (ix, iy, a x c) for R columns into ub [nb][Rp] (zero padding):
@@ -733,6 +739,309 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_up_tc(GridDims g, int R, const i
   }
   __syncthreads();
   leaf_up_out(k, q, b, R, Rp, Ws, D1x, D1y, p, m, w32, h32);
+}
+
+// ---- leaf apply with per-node operators on the 5th-generation tensor cores -----------------
+// W = A_ii^{-1} Rs on every leaf from the per-node FP32 operators split once, at reserve time,
+// into TF32 hi and lo parts (A = Ah + Al exactly in FP32; both stored K-major, [leaf][hi|lo][row]
+// [ldk]), as 3xTF32 products W ~ Ah Bh + Ah Bl + Al Bh (Rs = Bh + Bl) accumulated in FP32 in
+// tensor memory: an M = 128 x N = RP accumulator per 128-row tile of the leaf, two accumulator
+// sets so that one leaf's products run while the previous leaf's are read back.  Storing the
+// split costs twice the operator bytes but leaves the operands exactly as the TMA writes them, so
+// no thread touches them: the kernel streams HBM -> shared memory -> tensor cores.
+// Persistent CTAs (one per SM) with three warp roles that meet only at mbarriers:
+//   warp 0   TMA producer: per box the hi and lo boxes of 128 rows x 32 columns (128-byte swizzle;
+//            rows and columns beyond q read as zeros) into one of kUmmaStages stages;
+//   warp 1   MMA issuer: per box 4 K steps x 3 tcgen05.mma kind::tf32, committed to the stage's
+//            "free" barrier, and per leaf to its accumulator set's barrier;
+//   warps 2+ math: the leaf's right-hand side (FP32, formed in FP64 by the streaming combination
+//            pass k_b_combo, which also saves the FP64 sum; prefetched into registers one leaf
+//            ahead) into hi / lo operand tiles (two buffers, by leaf parity), and the epilogue of
+//            the previous leaf (tcgen05.ld into shared memory over that leaf's operand tiles,
+//            then w and its edge fluxes like every other leaf apply).
+// Every wait is bounded: one that runs out raises the CTA's abort flag, the roles leave their
+// loops, the copies and products still in flight are waited for, *err is set and the CTA returns.
+constexpr int kUmmaStages = 3;
+constexpr int kUmmaMathWarps = 8;
+constexpr int kUmmaThreads = 64 + 32 * kUmmaMathWarps;
+constexpr unsigned kUmmaBoxBytes = 128u * 32u * 4u;  // one box: 128 rows x 32 FP32
+constexpr uint64_t kUmmaWaitNs = 2000000000ull;
+constexpr int kUmmaPre = 8;  // float4 registers per math thread for the next leaf's right-hand side
+
+__host__ __device__ inline int umma_kc(int q) { return (q + 31) / 32; }
+__host__ __device__ inline int umma_mt(int q) { return (q + 127) / 128; }
+// W staging row stride (floats): RP + 4 keeps the accumulator read-back from piling onto a bank
+__host__ __device__ constexpr int umma_ldw(int RP) { return RP + 4; }
+// barriers: full and free per stage; operand tiles ready; per accumulator set done and free;
+// W staged, W read; drain
+constexpr int kUmmaBars = 2 * kUmmaStages + 1 + 4 + 2 + 1;
+// dynamic shared memory of k_b_leaf_up_umma<RP> (bytes, with the 1024-byte alignment slack)
+inline size_t umma_smem_bytes(int p, int RP) {
+  const int q = (p - 2) * (p - 2);
+  return 1024 + (size_t)kUmmaStages * 2 * kUmmaBoxBytes + 2 * 2 * (size_t)umma_kc(q) * RP * 128 +
+         (size_t)2 * p * p * 4 + kUmmaBars * 8 + 16;
+}
+// the leaf's q x R right-hand side block must fit the prefetch registers and be float4-aligned,
+// and W (q x ldw) must fit over one operand-tile buffer
+inline bool umma_fits(int p, int R, int RP) {
+  const int q = (p - 2) * (p - 2);
+  return (q * R) % 4 == 0 && q * R <= 4 * kUmmaPre * 32 * kUmmaMathWarps && q <= 256 &&
+         (size_t)q * umma_ldw(RP) * 4 <= 2 * (size_t)umma_kc(q) * RP * 128 && umma_smem_bytes(p, RP) <= 232448;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc5::smem_u32(bar)) : "memory");
+}
+// Bounded wait that also gives up as soon as another role has raised the abort flag.
+__device__ __forceinline__ bool umma_wait(uint64_t *bar, unsigned parity, volatile int *abort_flag) {
+  if (tc5::mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = tc5::global_ns();
+  while (!tc5::mbar_try_wait(bar, parity)) {
+    if (*abort_flag || tc5::global_ns() - t0 > kUmmaWaitNs) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+  return true;
+}
+// RP/2 accumulator columns of the calling warp's 32 TMEM lanes
+template <int NC>
+__device__ __forceinline__ void tmem_ld_half(unsigned taddr, float *v) {
+  if constexpr (NC == 16) {
+    float t[16];
+    tc5::tmem_ld16(taddr, t);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = t[i];
+  } else {
+    unsigned r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+  }
+}
+// One operand element of B (K index r, column n) as TF32 hi / lo at its swizzled position.
+template <int RP>
+__device__ __forceinline__ void umma_put_b(uint8_t *Bh, uint8_t *Bl, int r, int n, float v) {
+  const float h = tc5::tf32_hi(v);
+  const unsigned off = (unsigned)(r >> 5) * (RP * 128) + tc5::sw128_off(n, r & 31);
+  *reinterpret_cast<float *>(Bh + off) = h;
+  *reinterpret_cast<float *>(Bl + off) = v - h;
+}
+
+template <int RP>
+__global__ void __launch_bounds__(kUmmaThreads, 1)
+    k_b_leaf_up_umma(GridDims g, int nodes, int R, const int *__restrict__ origin, const float *__restrict__ r32,
+                     const __grid_constant__ CUtensorMap tmA, const double *__restrict__ Dg,
+                     float *__restrict__ w32, float *__restrict__ h32, int *__restrict__ err) {
+  namespace t5 = tc5;
+  constexpr int kSet = 2 * RP;     // TMEM columns of one accumulator set (up to 2 row tiles)
+  constexpr int kCols = 2 * kSet;  // two sets: 64 or 128 columns
+  constexpr int NTM = 32 * kUmmaMathWarps, RQ = RP / 4, LDW = umma_ldw(RP);
+  extern __shared__ uint8_t sm_raw[];
+  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(sm_raw) + 1023) & ~uintptr_t(1023));
+  const int p = g.p, m = g.m, q = m * m, b = 4 * m;
+  const int KC = umma_kc(q), MT = umma_mt(q), KSTEPS = (q + 7) / 8, NCH = MT * KC;
+  const int BT = KC * RP * 128;                                // one operand-tile set (hi or lo)
+  uint8_t *Stg = sm;                                           // stages: hi box, lo box
+  uint8_t *Bbuf = sm + kUmmaStages * 2 * kUmmaBoxBytes;        // two buffers of (Bh, Bl)
+  float *D1x = reinterpret_cast<float *>(Bbuf + 4 * BT), *D1y = D1x + p * p;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(D1y + p * p);
+  uint64_t *full = bars, *sfree = full + kUmmaStages, *bready = sfree + kUmmaStages;
+  uint64_t *accum = bready + 1, *tfree = accum + 2, *wsready = tfree + 2, *wsdone = wsready + 1;
+  uint64_t *drain = wsdone + 1;
+  unsigned *tslot = reinterpret_cast<unsigned *>(drain + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < kUmmaStages; ++s) {
+      t5::mbar_init(&full[s], 1);
+      t5::mbar_init(&sfree[s], 1);
+    }
+    t5::mbar_init(bready, NTM);
+    for (int h = 0; h < 2; ++h) {
+      t5::mbar_init(&accum[h], 1);
+      t5::mbar_init(&tfree[h], NTM);
+    }
+    t5::mbar_init(wsready, NTM);
+    t5::mbar_init(wsdone, NTM);
+    t5::mbar_init(drain, 1);
+    *abort_flag = 0;
+    t5::fence_barrier_init();
+    t5::tma_prefetch_desc(&tmA);
+  }
+  for (int i = tid; i < 2 * p * p; i += blockDim.x) D1x[i] = (float)Dg[i];
+  if (warp == 1) t5::tmem_alloc(tslot, kCols);
+  t5::tc_fence_before();
+  __syncthreads();
+  t5::tc_fence_after();
+  const unsigned tmem = *tslot;
+  // this CTA's leaves k = blockIdx.x + j gridDim.x; box c = j NCH + i, i = t KC + kc (row tile t,
+  // column box kc), in stage c % kUmmaStages
+  const int nl = (int)blockIdx.x < nodes ? (nodes - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int total = nl * NCH;
+  int last_box[kUmmaStages];  // producer: last box loaded into each stage (-1: none)
+  if (warp == 0 && lane == 0) {
+    // ---------------- producer ----------------
+    for (int s = 0; s < kUmmaStages; ++s) last_box[s] = -1;
+    for (int c = 0; c < total; ++c) {
+      const int j = c / NCH, i = c - j * NCH, s = c % kUmmaStages;
+      const int k = (int)blockIdx.x + j * (int)gridDim.x;
+      if (c >= kUmmaStages && !umma_wait(&sfree[s], (unsigned)((c - kUmmaStages) / kUmmaStages) & 1u, abort_flag))
+        break;
+      t5::mbar_expect_tx(&full[s], 2 * kUmmaBoxBytes);
+      uint8_t *dst = Stg + s * 2 * kUmmaBoxBytes;
+      t5::tma_load_3d(dst, &tmA, (i % KC) * 32, (i / KC) * 128, 2 * k, &full[s]);
+      t5::tma_load_3d(dst + kUmmaBoxBytes, &tmA, (i % KC) * 32, (i / KC) * 128, 2 * k + 1, &full[s]);
+      last_box[s] = c;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    const unsigned idesc = t5::idesc_tf32(128, RP);
+    for (int j = 0; j < nl; ++j) {
+      const int hs = j & 1;
+      if (j >= 2 && !umma_wait(&tfree[hs], (unsigned)((j - 2) >> 1) & 1u, abort_flag)) break;
+      if (!umma_wait(bready, (unsigned)j & 1u, abort_flag)) break;
+      t5::tc_fence_after();
+      const uint8_t *Bh = Bbuf + hs * 2 * BT, *Bl = Bh + BT;
+      bool ok = true;
+      for (int i = 0; i < NCH; ++i) {
+        const int c = j * NCH + i, s = c % kUmmaStages, t = i / KC, kc = i - t * KC;
+        if (!umma_wait(&full[s], (unsigned)(c / kUmmaStages) & 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        t5::tc_fence_after();
+        const unsigned a_h = t5::smem_u32(Stg + s * 2 * kUmmaBoxBytes), a_l = a_h + kUmmaBoxBytes;
+        const unsigned b_h = t5::smem_u32(Bh + kc * RP * 128), b_l = t5::smem_u32(Bl + kc * RP * 128);
+        const unsigned d = tmem + (unsigned)(hs * kSet + t * RP);
+        for (int ks = 0; ks < 4 && kc * 4 + ks < KSTEPS; ++ks) {
+          const unsigned o = 32u * ks;  // 8 TF32 values further along K inside the 128-byte line
+          t5::mma_tf32(d, t5::desc_sw128_kmajor(a_h + o), t5::desc_sw128_kmajor(b_h + o), idesc,
+                       (kc > 0 || ks > 0) ? 1u : 0u);
+          t5::mma_tf32(d, t5::desc_sw128_kmajor(a_h + o), t5::desc_sw128_kmajor(b_l + o), idesc, 1u);
+          t5::mma_tf32(d, t5::desc_sw128_kmajor(a_l + o), t5::desc_sw128_kmajor(b_h + o), idesc, 1u);
+        }
+        t5::mma_commit(&sfree[s]);
+      }
+      if (!ok) break;
+      t5::mma_commit(&accum[hs]);
+    }
+    t5::mma_commit(drain);  // completes once every product this thread issued has completed
+  } else if (warp >= 2) {
+    // ---------------- math warps ----------------
+    const int mt = tid - 64, mw = warp - 2;
+    const int quarter = warp & 3, chalf = mw / 4;  // TMEM lanes 32 quarter .. +31, column half chalf
+    const int nf4 = q * R / 4;
+    float4 pre[kUmmaPre];  // the next leaf's right-hand side block (q x R FP32, contiguous)
+    auto prefetch = [&](int jj) {
+      const int k = (int)blockIdx.x + jj * (int)gridDim.x;
+      const int64_t l0 = ((int64_t)origin[2 * k + 1] * g.n1 + origin[2 * k]) * q;
+      const float4 *src = reinterpret_cast<const float4 *>(r32 + l0 * R);
+#pragma unroll
+      for (int u = 0; u < kUmmaPre; ++u) {
+        const int e = mt + u * NTM;
+        if (e < nf4) pre[u] = __ldg(src + e);
+      }
+    };
+    // epilogue of leaf jj: accumulators -> W [q][LDW] over the leaf's operand tiles -> w, fluxes
+    auto epilogue = [&](int jj) -> bool {
+      const int hs = jj & 1, k = (int)blockIdx.x + jj * (int)gridDim.x;
+      float *Ws = reinterpret_cast<float *>(Bbuf + hs * 2 * BT);
+      bool ok = umma_wait(&accum[hs], (unsigned)(jj >> 1) & 1u, abort_flag);
+      if (!__all_sync(0xffffffffu, ok)) return false;
+      t5::tc_fence_after();
+      for (int t = 0; t < MT; ++t) {
+        const int r = t * 128 + quarter * 32 + lane;
+        const unsigned ta = tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)(hs * kSet + t * RP + chalf * (RP / 2));
+        float v[RP / 2];
+        tmem_ld_half<RP / 2>(ta, v);
+        if (r < q)
+#pragma unroll
+          for (int n = 0; n < RP / 2; n += 4)
+            *reinterpret_cast<float4 *>(Ws + r * LDW + chalf * (RP / 2) + n) =
+                make_float4(v[n], v[n + 1], v[n + 2], v[n + 3]);
+      }
+      t5::tc_fence_before();
+      mbar_arrive(&tfree[hs]);  // this accumulator set may take the leaf after next
+      mbar_arrive(wsready);
+      ok = umma_wait(wsready, (unsigned)jj & 1u, abort_flag);
+      if (!__all_sync(0xffffffffu, ok)) return false;
+      for (int i = mt; i < q * RQ; i += NTM) {  // w
+        const int r = i / RQ, j0 = 4 * (i - r * RQ);
+        const float4 v = *reinterpret_cast<const float4 *>(Ws + r * LDW + j0);
+        float *o = w32 + ((int64_t)k * q + r) * R + j0;
+        if (R == RP) {
+          *reinterpret_cast<float4 *>(o) = v;
+        } else {
+          const float vv[4] = {v.x, v.y, v.z, v.w};
+          for (int t = 0; t < 4 && j0 + t < R; ++t) o[t] = vv[t];
+        }
+      }
+      for (int i = mt; i < b * RQ; i += NTM) {  // its fluxes on the b edge points
+        const int e = i / RQ, j0 = 4 * (i - e * RQ);
+        const float4 f = flux4(e, j0, LDW, Ws, D1x, D1y, p, m);
+        float *o = h32 + ((int64_t)k * b + e) * R + j0;
+        if (R == RP) {
+          *reinterpret_cast<float4 *>(o) = f;
+        } else {
+          const float fv[4] = {f.x, f.y, f.z, f.w};
+          for (int t = 0; t < 4 && j0 + t < R; ++t) o[t] = fv[t];
+        }
+      }
+      mbar_arrive(wsdone);
+      ok = umma_wait(wsdone, (unsigned)jj & 1u, abort_flag);  // W read: the region takes operand tiles
+      return __all_sync(0xffffffffu, ok);
+    };
+    if (nl > 0) prefetch(0);
+    bool run = true;
+    for (int j = 0; j < nl; ++j) {
+      // the leaf's right-hand side as hi / lo operand tiles in buffer j & 1 (N = RP lines, K = KC*32;
+      // zero beyond q and R); the buffer's last use, leaf j - 2 and its epilogue, is over
+      uint8_t *Bh = Bbuf + (j & 1) * 2 * BT, *Bl = Bh + BT;
+#pragma unroll
+      for (int u = 0; u < kUmmaPre; ++u) {
+        const int e = mt + u * NTM;
+        if (e < nf4) {
+          const float vv[4] = {pre[u].x, pre[u].y, pre[u].z, pre[u].w};
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {
+            const int f = 4 * e + cc, r = f / R;
+            umma_put_b<RP>(Bh, Bl, r, f - r * R, vv[cc]);
+          }
+        }
+      }
+      for (int idx = mt; idx < (KC * 32 - q) * RP; idx += NTM) umma_put_b<RP>(Bh, Bl, q + idx / RP, idx % RP, 0.f);
+      if (R < RP)
+        for (int idx = mt; idx < q * (RP - R); idx += NTM)
+          umma_put_b<RP>(Bh, Bl, idx / (RP - R), R + idx % (RP - R), 0.f);
+      t5::fence_async_smem();
+      mbar_arrive(bready);
+      if (j + 1 < nl) prefetch(j + 1);
+      if (j >= 1 && !epilogue(j - 1)) {
+        run = false;
+        break;
+      }
+    }
+    if (run && nl > 0 && !*abort_flag) epilogue(nl - 1);
+  }
+  // wind down: every role has left its loop
+  __syncthreads();
+  if (warp == 0 && lane == 0 && *abort_flag) {  // copies still in flight (only a stage's last one can be)
+    for (int s = 0; s < kUmmaStages; ++s)
+      if (last_box[s] >= 0) t5::mbar_wait(&full[s], (unsigned)(last_box[s] / kUmmaStages) & 1u, kUmmaWaitNs);
+    atomicExch(err, 1);
+  }
+  if (warp == 1 && lane == 0) t5::mbar_wait(drain, 0u, kUmmaWaitNs);  // products still running
+  t5::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    t5::tc_fence_after();
+    t5::tmem_dealloc(tmem, kCols);
+  }
 }
 
 // Shared leaf operator, persistent CTAs: S_leaf^T is copied to shared memory once per CTA and
@@ -2090,6 +2399,48 @@ __global__ void k_relayout(const double *__restrict__ src, int ld64, int64_t str
   }
 }
 
+// TF32 split of the per-node leaf operators for the tensor-core leaf apply, K-major:
+// dst[node][0][r][c] = hi and dst[node][1][r][c] = lo of (float) A(r, c), A(r, c) at c ld + r of
+// the transposed FP64 operator; hi keeps the top 10 mantissa bits (exactly TF32), lo = value - hi.
+__global__ void k_kmajor_split(const double *__restrict__ src, int ld64, int64_t str64, int q, int64_t nops,
+                               float *__restrict__ dst, int ldk) {
+  const int64_t per = (int64_t)q * ldk, total = nops * per;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t node = i / per, rem = i % per;
+    const int r = (int)(rem / ldk), c = (int)(rem % ldk);
+    const float v = c < q ? (float)src[node * str64 + (int64_t)c * ld64 + r] : 0.f;
+    const float h = tc5::tf32_hi(v);
+    dst[node * 2 * per + rem] = h;
+    dst[node * 2 * per + per + rem] = v - h;
+  }
+}
+
+// Tensor map of the split K-major leaf operators: 3-D (column, row, 2 leaf + part) FP32, boxes of
+// 32 columns x 128 rows x 1 in the 128-byte swizzle; out-of-range rows and columns read as zeros.
+int umma_map(hps_handle *H) {
+  Batch &Bt = H->batch;
+  using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult qr{};
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr) != cudaSuccess ||
+      qr != cudaDriverEntryPointSuccess || !fn)
+    return HPS_ECUDA;
+  const int q = H->q;
+  const cuuint64_t dims[3] = {(cuuint64_t)q, (cuuint64_t)q, 2 * (cuuint64_t)H->lev[H->L].nodes};
+  const cuuint64_t strides[2] = {(cuuint64_t)Bt.ainv_ldk * 4, (cuuint64_t)q * Bt.ainv_ldk * 4};
+  const cuuint32_t box[3] = {32, 128, 1}, estr[3] = {1, 1, 1};
+  CUtensorMap map;
+  if (reinterpret_cast<EncodeFn>(fn)(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, Bt.ainv_k, dims, strides, box, estr,
+                                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return HPS_ECUDA;
+  static_assert(sizeof(map) == sizeof(Bt.ainv_map), "tensor map size");
+  memcpy(Bt.ainv_map, &map, sizeof map);
+  return HPS_OK;
+}
+
 // FP32 copy of a transposed operator (rows x cols per node) with rows padded to 4 floats.
 int convert_op(hps_handle *H, const double *src, int ld64, int64_t str64, int rows, int cols, int64_t nops, Op32 &o) {
   if (!src) return HPS_OK;
@@ -2196,6 +2547,22 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
     kern<<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, reinterpret_cast<const uint4 *>(H->batch.afrag_hi),
                                         reinterpret_cast<const uint4 *>(H->batch.afrag_lo), MT, KT, H->d_D, B.w32,
                                         B.h32[L]);
+    H->trace.end(kLeafUp, st);
+  } else if ((allow_tc || H->batch.umma_leaf == 2) && H->batch.umma_leaf && H->batch.ainv_k && !H->shared &&
+             !ops.identity &&
+             (Rp == 16 || Rp == 32) && umma_fits(p, R, Rp)) {
+    // per-node leaf operators on the tcgen05 tensor cores (3xTF32), persistent CTAs, after the
+    // stage right-hand side as its own streaming pass (FP64 sum saved, FP32 copy for the products)
+    const size_t smem = umma_smem_bytes(p, Rp);
+    auto kern = Rp == 32 ? k_b_leaf_up_umma<32> : k_b_leaf_up_umma<16>;
+    if (int e_ = smem_optin((const void *)kern, smem)) return e_;
+    CUtensorMap map;
+    memcpy(&map, H->batch.ainv_map, sizeof map);
+    H->trace.begin(kLeafUp, st);
+    const int64_t n = H->g.N_int * R;
+    k_b_combo<<<(unsigned)((n + 4 * 256 - 1) / (4 * 256)), 256, 0, st>>>(n, rhs, Rsave, B.r32);
+    kern<<<std::min(leaf.nodes, H->num_sms), kUmmaThreads, smem, st>>>(H->g, leaf.nodes, R, leaf.d_origin, B.r32,
+                                                                      map, H->d_D, B.w32, B.h32[L], H->perr);
     H->trace.end(kLeafUp, st);
   } else {
     const size_t smem = (size_t)(round4(2 * p * p) + 2 * q * Rp) * sizeof(float);
@@ -2683,6 +3050,17 @@ int batch_reserve(hps_handle *H, int R, int groups) {
       H->allocs.push_back(Bt.afrag_lo);
       k_frag_a<<<blocks((int64_t)n), 256>>>(Bt.impl32.Ainv.p, Bt.impl32.Ainv.ld, q, MT, KT, Bt.afrag_hi, Bt.afrag_lo);
     }
+    if (!H->shared && H->impl.Ainv && H->impl.strA && q <= 256 && umma_smem_bytes(H->p, 16) <= 232448) {
+      // TF32 hi / lo split of the per-node leaf operators, K-major, and its tensor map (tensor-core leaf apply)
+      const int64_t nops = H->lev[H->L].nodes;
+      Bt.ainv_ldk = round4(q);
+      if (cudaMalloc(&Bt.ainv_k, 2 * (size_t)nops * q * Bt.ainv_ldk * sizeof(float)) != cudaSuccess)
+        return HPS_ENOMEM;
+      H->allocs.push_back(Bt.ainv_k);
+      k_kmajor_split<<<4 * H->num_sms, 256>>>(H->impl.Ainv, H->impl.ldA, H->impl.strA, q, nops, Bt.ainv_k,
+                                              Bt.ainv_ldk);
+      if (int e = umma_map(H)) return e;
+    }
   }
   // (re)allocate the work vectors; old ones stay in the handle's list until hps_free
   const GridDims &g = H->g;
@@ -2741,6 +3119,7 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
   bool *flag = nullptr;
   switch (opt) {
     case HPS_OPT_TENSOR_LEAF: flag = &Bt.tensor_leaf; break;
+    case HPS_OPT_UMMA_LEAF: field = &Bt.umma_leaf; break;
     case HPS_OPT_EVEN_ODD: flag = &Bt.even_odd; break;
     case HPS_OPT_FLOW_LEVELS: field = &Bt.flow_levels; break;
     case HPS_OPT_FLOW_N3_MAX: field = &Bt.flow_n3_max; break;
@@ -2776,6 +3155,7 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
   if (per_apply && *set != 0 && *set != 2 && *set != 4 && *set != 8) return HPS_EINVAL;
   if (v < 0 || (plan && !per_apply && v < 1) || (opt == HPS_OPT_FLOW_LEVELS && v > kFlowMaxLevels)) return HPS_EINVAL;
   if (opt == HPS_OPT_EO_COLS && (v < 1 || v > 32)) return HPS_EINVAL;
+  if (opt == HPS_OPT_UMMA_LEAF && v > 2) return HPS_EINVAL;
   if (opt == HPS_OPT_FP64_PLAN_TARGET) {  // FP64 split plans: not while the persistent kernel holds tasks
     if (v < 1 || v > 8 || H->persistent) return HPS_EINVAL;
     H->fp64_plan_target = v;

@@ -179,6 +179,10 @@ struct Batch {
   int plan_tile_cols = 2;    // merge applies: register-tile columns per thread (8, 4 or 2)
   bool tensor_leaf = true;   // shared leaf operator applied by 3xTF32 warp MMA (else FP32 FFMA)
   unsigned *afrag_hi = nullptr, *afrag_lo = nullptr;  // its TF32 fragments
+  int umma_leaf = 1;         // per-node leaf operators on the tcgen05 tensor cores (3xTF32): 1 first sweep, 2 all
+  float *ainv_k = nullptr;   // their TF32 hi / lo split, K-major: [leaf][hi, lo][row][ainv_ldk]
+  int ainv_ldk = 0;
+  uint64_t ainv_map[16] = {};  // its TMA tensor map (CUtensorMap, 128 bytes)
   OpSet32 impl32, ident32;
   std::vector<BatchWork> work;
   cudaEvent_t fork = nullptr;
