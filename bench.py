@@ -43,7 +43,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eager", action="store_true", help="launch every kernel from the host (no CUDA graph)")
     ap.add_argument("--rhs", type=int, default=32, help="right-hand sides of the mixed-precision batch")
-    ap.add_argument("--only", choices=["fp64", "mixed"], default=None, help="time one form only (profiling)")
+    ap.add_argument("--only", choices=["fp64", "mixed", "serving"], default=None,
+                    help="time one form only (profiling); serving: only the serving run, its JSON")
     ap.add_argument("--serving-jobs", type=int, default=48, help="jobs of the serving run (0: skip)")
     ap.add_argument("--refine", type=int, default=1, help="FP64 refinement sweeps per implicit solve (mixed)")
     ap.add_argument("--groups", type=int, default=1, help="column groups of the mixed batch (own streams each)")
@@ -578,6 +579,8 @@ def bench_ours(args, rank, world, local_rank):
         out["fp32_single_rhs_solve"] = pn["fp32_sweep_solve"]
     if rank == 0 and out is not None and args.serving_jobs > 0 and args.only is None:
         out["serving"] = bench_serving(args)
+        out["serving"]["batched_over_plain_fp64_sweep"] = (out["serving"]["batched_mixed"]["dof_stages_per_s"] /
+                                                           out["fp64_single_rhs"]["value"])
     return out
 
 
@@ -722,38 +725,69 @@ def bench_per_node(args, flush):
     return out
 
 
-def bench_serving(args):
-    """A Poisson-arrival stream (200 jobs/s, seeded) of heat and Allen-Cahn jobs with leaf grids
-    8x8..64x64, p in {8, 12, 16}, 10..100 steps, through the native serving loop."""
+# operations the serving stream draws from (leaf grid, p, kind): heat u_t = Lap u (dt = 0.01) or
+# Allen-Cahn u_t = 0.01 Lap u + u - u^3 (dt = 1e-3), spanning leaf grids 8x8 .. 128x128 and p 8 .. 16
+SERVING_CATALOG = ((8, 8, "heat"), (16, 12, "ac"), (32, 16, "heat"), (64, 16, "ac"), (128, 8, "heat"),
+                   (64, 12, "ac"))
+
+
+def serving_jobs(n_jobs, seed=2026):
+    """A seeded Poisson-arrival stream (200 jobs/s) of jobs drawn uniformly from SERVING_CATALOG,
+    10..500 steps each, initial states U[-0.1, 0.1] (zero on the boundary)."""
     import numpy as np
     from paper_2306_02526_gb300 import hps
-    from paper_2306_02526_gb300.serve import Server
-    r = np.random.default_rng(2026)
-    S = Server(64 << 30, max_active=16)
-    t, total_dof = 0.0, 0
-    for _ in range(args.serving_jobs):
+    r = np.random.default_rng(seed)
+    t, jobs = 0.0, []
+    for _ in range(n_jobs):
         t += r.exponential(1.0 / 200.0)
-        n = int(r.choice([8, 16, 32, 64]))
-        p = int(r.choice([8, 12, 16]))
-        heat = bool(r.random() < 0.5)
+        n, p, kind = SERVING_CATALOG[int(r.integers(len(SERVING_CATALOG)))]
         tree = hps.Tree(n, n)
         N, _, _ = hps.hps_sizes(tree, p)
         bd = hps.hps_boundary_index(tree, p)
         u0 = r.uniform(-0.1, 0.1, N)
         u0[bd] = 0.0
-        steps = int(r.integers(10, 101))
-        if heat:
-            S.submit(tree, p, {"a11": 1.0, "a22": 1.0}, 0.01, steps, u0, arrival_s=t)
+        steps = int(r.integers(10, 501))
+        if kind == "heat":
+            jobs.append(dict(tree=tree, p=p, coef={"a11": 1.0, "a22": 1.0}, dt=0.01, steps=steps, u0=u0,
+                             arrival_s=t))
         else:
-            S.submit(tree, p, {"a11": 0.01, "a22": 0.01}, 1e-3, steps, u0, g="allen_cahn", g_param=(1.0, 0.0),
-                     arrival_s=t)
-        total_dof += N * steps
-    S.run()
-    out = S.summary()
-    out["arrival_rate_per_s"] = 200.0
-    out["jobs"] = args.serving_jobs
-    out["note"] = "factorization builds happen inside the run (cache misses) and count in the makespan"
-    S.close()
+            jobs.append(dict(tree=tree, p=p, coef={"a11": 0.01, "a22": 0.01}, dt=1e-3, steps=steps, u0=u0,
+                             g="allen_cahn", g_param=(1.0, 0.0), arrival_s=t))
+    return jobs
+
+
+def bench_serving(args):
+    """The serving stream through the native loop twice: every job stepping alone in FP64, and
+    jobs of the same operation coalesced into batched mixed-precision steps (up to 32 columns,
+    refinement sweeps chosen per operation by the server from its stiffness).  The batched results are compared with the FP64 ones job by job."""
+    import numpy as np
+    from paper_2306_02526_gb300.serve import Server
+    jobs = serving_jobs(args.serving_jobs)
+    out = {"arrival_rate_per_s": 200.0, "jobs": len(jobs), "catalog": [list(c) for c in SERVING_CATALOG],
+           "steps_range": [10, 500],
+           "note": "factorization builds happen inside the run (cache misses) and count in the makespan; "
+                   "DOF*stages/s = sum over jobs of N x 5 x steps / makespan"}
+    results = {}
+    for name, cols in (("fp64", 0), ("batched_mixed", 32)):
+        S = Server(64 << 30, max_active=64 if cols else 16, batch_cols=cols, refine=-1)
+        ids = [S.submit(**j) for j in jobs]
+        S.run()
+        results[name] = [S.result(i).copy() for i in ids]
+        summ = S.summary()
+        summ["form"] = ("every job alone, FP64 ark_step, one stream per job" if not cols else
+                        "jobs of one operation as columns of ark_step_batch (FP32 sweeps + FP64 refinement, sweeps "
+                        "chosen per operation by its stiffness), "
+                        "at most 32 per batch, joining at step boundaries")
+        out[name] = summ
+        S.close()
+    err = 0.0
+    for j, a, b in zip(jobs, results["fp64"], results["batched_mixed"]):
+        # relative to the larger of the initial and the final state (heat jobs decay by many orders)
+        scale = max(np.abs(a).max(), np.abs(j["u0"]).max())
+        err = max(err, float(np.abs(a - b).max() / scale))
+    out["batched_err_vs_fp64"] = err
+    out["batched_err_note"] = "max over jobs of |u_batched - u_fp64|_inf / max(|u_fp64|_inf, |u0|_inf)"
+    out["batched_over_fp64_served"] = out["batched_mixed"]["dof_stages_per_s"] / out["fp64"]["dof_stages_per_s"]
     return out
 
 
@@ -795,6 +829,11 @@ def main():
             print(json.dumps(out))
         return
     import torch
+    if args.only == "serving":
+        from paper_2306_02526_gb300 import build as _b
+        _b.build()
+        print(json.dumps(bench_serving(args)))
+        return
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     cpu = None

@@ -429,11 +429,27 @@ typedef struct hps_server_stats {
   int max_concurrent;
   size_t peak_bytes;
   int factorizations_built, factorizations_shared;
+  int batches_formed;        /* batching on: batches created */
+  double mean_batch_cols;    /* batching on: members per batched step, averaged over the steps */
 } hps_server_stats;
 
 /* A server with a device-memory budget (bytes, for factorizations + work buffers + states)
  * and at most max_active jobs in flight. */
 int hps_server_create(size_t mem_budget_bytes, int max_active, hps_server **out);
+/* Batching (continuous batching at the kernel level): with max_cols >= 1 (<= 64), jobs whose
+ * steps are the same operation -- identical operator (tree, p, coefficients, dt) and identical
+ * g -- advance as the columns of one state by ark_step_batch (FP32 sweeps + `refine` FP64
+ * refinement sweeps per implicit solve; refine = -1: chosen per operation from its stiffness
+ * gamma dt max(a11/hx^2, a22/hy^2) 4 * 0.047 (p-1)^4 -- 1 up to 1e5, one more per factor 100)
+ * on a stream of their own, at most max_cols jobs per batch;
+ * R = the member count rounded up to 4.  An arriving job joins a running batch of its operation
+ * with a free column at that batch's next step boundary (the batch lets its queued steps finish,
+ * then repacks its columns), else starts a new batch (its memory -- handle reserved for max_cols
+ * columns, two N x max_cols states -- measured against the budget).  A job's result then agrees
+ * with its FP64 ark_step result to the mixed-precision tolerance (1e-10) and with its result in
+ * another mix to rounding (the split of the FP32 merge sums follows R).  max_cols = 0 (default):
+ * every job steps on its own with the FP64 ark_step, results bit-identical alone and in a mix. */
+int hps_server_set_batching(hps_server *s, int max_cols, int refine);
 /* Queue a job; *job_id (may be NULL) receives its index. */
 int hps_server_submit(hps_server *s, const hps_job_desc *job, int *job_id);
 /* Run until every queued job is done or rejected (blocks; honours arrival times from now). */

@@ -65,7 +65,8 @@ class hps_server_stats(ctypes.Structure):
     _fields_ = [("jobs_done", ctypes.c_int), ("jobs_rejected", ctypes.c_int), ("makespan_s", ctypes.c_double),
                 ("dof_stages_per_s", ctypes.c_double), ("steps", ctypes.c_int64), ("step_ms_p50", ctypes.c_double),
                 ("step_ms_p99", ctypes.c_double), ("max_concurrent", ctypes.c_int), ("peak_bytes", ctypes.c_size_t),
-                ("factorizations_built", ctypes.c_int), ("factorizations_shared", ctypes.c_int)]
+                ("factorizations_built", ctypes.c_int), ("factorizations_shared", ctypes.c_int), ("batches_formed", ctypes.c_int),
+                ("mean_batch_cols", ctypes.c_double)]
 
 
 # name -> (restype, argtypes); the list is also the set of exported symbols include/hps.h declares
@@ -115,6 +116,7 @@ SIGNATURES = {
     "hps_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "hps_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(hps_job_desc), ctypes.POINTER(ctypes.c_int)]),
     "hps_server_run": (ctypes.c_int, [ctypes.c_void_p]),
+    "hps_server_set_batching": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "hps_server_job_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(hps_job_stats)]),
     "hps_server_summary": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(hps_server_stats)]),
     "hps_server_free": (None, [ctypes.c_void_p]),

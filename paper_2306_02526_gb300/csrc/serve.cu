@@ -9,6 +9,7 @@
 // back and release their memory; factorizations without users stay cached until memory is
 // needed.  Every step is bracketed by CUDA events for the latency statistics.
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <cstring>
 #include <memory>
@@ -58,6 +59,28 @@ struct Job {
   std::vector<float> step_ms;
   double admit_s = 0.0, finish_s = 0.0;
   bool shared_ops = false;
+  struct Group *grp = nullptr;  // batched serving: the batch it is (or will be) a column of
+};
+
+// Batched serving: jobs of one operation advanced together as the columns of one state.
+struct Group {
+  OpKey key;
+  int g_kind = 0;
+  double g_param[2] = {0.0, 0.0};
+  CacheEntry *ce = nullptr;
+  hps_handle *h = nullptr;
+  cudaStream_t st = nullptr;
+  double *U = nullptr, *U2 = nullptr;  // N x cap each: the state (R columns) and the repack target
+  double *col = nullptr;               // N: one job's state on its way in or out
+  int *d_map = nullptr;                // cap: repack map (new column -> old column or -1)
+  int cap = 0, R = 0;
+  int refine = 1;                      // FP64 refinement sweeps per implicit solve of this batch
+  int64_t N = 0;
+  size_t bytes = 0;
+  std::vector<Job *> members, pending;
+  int enq = 0, done = 0;
+  cudaEvent_t ev[2 * kRing] = {};
+  int64_t col_steps = 0, steps = 0;    // sum over steps of the member count; steps run
 };
 
 }  // namespace
@@ -70,6 +93,10 @@ struct hps_server {
   double makespan_s = 0.0;
   int max_concurrent = 0;
   int builds = 0, cache_hits = 0;
+  int batch_cols = 0, refine = 1;  // batching on when batch_cols > 0
+  std::vector<std::unique_ptr<Group>> groups;
+  int groups_formed = 0;
+  int64_t batch_col_steps = 0, batch_step_count = 0;  // batched steps run and their member counts
 };
 
 namespace {
@@ -194,6 +221,339 @@ bool admit(hps_server *S, Job &J, double t) {
   return true;
 }
 
+
+// ---- batched serving -----------------------------------------------------------------------
+// dst[i Rd + j] = src[i Rs + map[j]] (map[j] < 0: zero), the columns of a batch after members
+// joined or left
+__global__ void k_repack(int64_t N, const double *__restrict__ src, int Rs, double *__restrict__ dst, int Rd,
+                         const int *__restrict__ map) {
+  const int64_t n = N * Rd;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pt = i / Rd;
+    const int j = (int)(i - pt * Rd), s = map[j];
+    dst[i] = s >= 0 ? src[pt * Rs + s] : 0.0;
+  }
+}
+// one column of an N x R state from / to a contiguous vector
+__global__ void k_col(int64_t N, double *__restrict__ U, int R, int j, double *__restrict__ v, int to_state) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    if (to_state) U[i * R + j] = v[i];
+    else v[i] = U[i * R + j];
+  }
+}
+
+// Refinement sweeps for the mixed-precision step of an operation when the caller leaves the choice
+// to the server: by the stiffness sigma = gamma dt max(a11 / hx^2, a22 / hy^2) 4 lambda(p), lambda(p)
+// = 0.047 (p - 1)^4 the spectral radius of the 1-D Chebyshev second-derivative matrix on [-1, 1]
+// with Dirichlet ends; the FP32 sweep's error, and with it the number of sweeps that bring the
+// solve to FP64 accuracy, grows with sigma: 1 sweep up to sigma = 1e5 (measured: heat on 32 x 32
+// leaves with p = 16 and dt = 0.01, sigma = 2.4e4, stays within 2e-11 of the FP64 step over ten
+// steps with one sweep), then one more per factor 100.
+int auto_refine(const hps_job_desc &d) {
+  const double hx = (d.tree.x1 - d.tree.x0) / d.tree.n1, hy = (d.tree.y1 - d.tree.y0) / d.tree.n2;
+  const double lam = 0.047 * std::pow((double)(d.p - 1), 4.0);
+  const double sigma = 0.25 * d.dt * std::max(std::fabs(d.c_a11) / (hx * hx), std::fabs(d.c_a22) / (hy * hy)) * 4.0 * lam;
+  int r = 1;
+  for (double s = 1e5; sigma > s && r < 4; s *= 100.0) ++r;
+  return r;
+}
+
+OpKey job_key(const hps_job_desc &d) {
+  OpKey key{};
+  key.tree = d.tree;
+  key.p = d.p;
+  key.c[0] = d.c_a11; key.c[1] = d.c_a22; key.c[2] = d.c_a1; key.c[3] = d.c_a2; key.c[4] = d.c_a0;
+  key.gdt = 0.25 * d.dt;
+  return key;
+}
+
+bool same_op(const Group &G, const hps_job_desc &d) {
+  return G.key == job_key(d) && G.g_kind == d.g_kind && G.g_param[0] == d.g_param[0] && G.g_param[1] == d.g_param[1];
+}
+
+void release_group(hps_server *S, Group &G) {
+  if (G.st) cudaStreamSynchronize(G.st);
+  if (G.h) hps_free(G.h);
+  for (double *p : {G.U, G.U2, G.col})
+    if (p) cudaFree(p);
+  if (G.d_map) cudaFree(G.d_map);
+  for (auto &e : G.ev)
+    if (e) cudaEventDestroy(e);
+  if (G.st) cudaStreamDestroy(G.st);
+  if (G.ce) --G.ce->users;
+  S->used -= G.bytes;
+  S->batch_col_steps += G.col_steps;
+  S->batch_step_count += G.steps;
+  G = Group{};
+}
+
+// A new (empty) batch for job J's operation: its factorization (shared through the cache), a
+// handle reserved for `cap` columns and the state buffers.  The batch's bytes are measured as the
+// device memory its allocations took.  Returns false when the budget does not hold it (J waits).
+bool create_group(hps_server *S, const Job &J, double t, Group **out, int *reject) {
+  const hps_job_desc &d = J.d;
+  const OpKey key = job_key(d);
+  *reject = HPS_OK;
+  size_t ops = 0, work = 0;
+  if (hps::bytes_split(&d.tree, d.p, HPS_COEF_CONST, 0, &ops, &work)) {
+    *reject = HPS_EINVAL;
+    return false;
+  }
+  int64_t N = 0;
+  hps_sizes(&d.tree, d.p, &N, nullptr, nullptr);
+  const int cap = S->batch_cols;
+  // estimate before allocating: FP64 operators if not cached + about 160 bytes per point and
+  // column of batched work vectors and states + the single-column work of the handle
+  CacheEntry *ce = find_entry(S, key);
+  const size_t est = (ce ? 0 : ops) + work + (size_t)N * cap * 160 + (size_t)N * 8;
+  if (est > S->budget) {
+    *reject = HPS_ENOMEM;
+    return false;
+  }
+  if (S->used + est > S->budget) {
+    if (ce) ++ce->users;
+    evict(S, est);
+    for (auto &g : S->groups)  // idle batches hold memory too
+      if (S->used + est > S->budget && g->h && g->members.empty() && g->pending.empty()) release_group(S, *g);
+    if (ce) --ce->users;
+  }
+  if (S->used + est > S->budget) return false;
+  auto G = std::make_unique<Group>();
+  G->key = key;
+  G->g_kind = d.g_kind;
+  G->g_param[0] = d.g_param[0];
+  G->g_param[1] = d.g_param[1];
+  G->cap = cap;
+  G->N = N;
+  G->refine = S->refine >= 0 ? S->refine : auto_refine(d);
+  auto fail = [&](int e) -> bool {
+    *reject = e;
+    release_group(S, *G);
+    return false;
+  };
+  if (cudaStreamCreateWithFlags(&G->st, cudaStreamNonBlocking) != cudaSuccess) return fail(HPS_ECUDA);
+  if (!ce) {
+    hps_coeffs c{};
+    c.kind = HPS_COEF_CONST;
+    c.c_a11 = d.c_a11; c.c_a22 = d.c_a22; c.c_a1 = d.c_a1; c.c_a2 = d.c_a2; c.c_a0 = d.c_a0;
+    hps_handle *base = nullptr;
+    if (int e = hps_build(&d.tree, d.p, &c, key.gdt, 0, (hps_stream_t)G->st, &base)) return fail(e);
+    auto entry = std::make_unique<CacheEntry>();
+    entry->key = key;
+    entry->base = base;
+    entry->bytes = ops;
+    ce = entry.get();
+    S->cache.push_back(std::move(entry));
+    S->used += ops;
+    ++S->builds;
+  } else {
+    ++S->cache_hits;
+  }
+  ce->last_use = t;
+  ++ce->users;
+  G->ce = ce;
+  size_t free0 = 0, free1 = 0, total = 0;
+  cudaDeviceSynchronize();
+  cudaMemGetInfo(&free0, &total);
+  if (int e = hps::clone_handle(ce->base, G->st, &G->h)) return fail(e);
+  if (int e = hps_batch_reserve(G->h, cap)) return fail(e);
+  G->h->graph_mode = true;
+  if (cudaMalloc(&G->U, (size_t)N * cap * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&G->U2, (size_t)N * cap * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&G->col, (size_t)N * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&G->d_map, (size_t)cap * sizeof(int)) != cudaSuccess)
+    return fail(HPS_ENOMEM);
+  for (auto &e : G->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return fail(HPS_ECUDA);
+  cudaDeviceSynchronize();
+  cudaMemGetInfo(&free1, &total);
+  G->bytes = free0 > free1 ? free0 - free1 : est;
+  if (S->used + G->bytes > S->budget) {  // the measured size breaks the budget: give it back, wait
+    release_group(S, *G);
+    return false;
+  }
+  S->used += G->bytes;
+  S->peak_used = std::max(S->peak_used, S->used);
+  ++S->groups_formed;
+  S->groups.push_back(std::move(G));
+  *out = S->groups.back().get();
+  return true;
+}
+
+inline int round4i(int n) { return (n + 3) & ~3; }
+
+// A step boundary of G (none of its steps in flight): members that have run all their steps copy
+// their column out and leave, waiting members join, and the columns are repacked into R = the
+// member count rounded up to 4 (at most cap).
+int group_boundary(Group &G, std::chrono::steady_clock::time_point t0) {
+  std::vector<Job *> stay;
+  std::vector<int> from;  // old column of each member of the new layout (-1: a joining job)
+  bool changed = false;
+  const unsigned nb = (unsigned)std::min<int64_t>((G.N + 255) / 256, 4096);
+  for (int j = 0; j < (int)G.members.size(); ++j) {
+    Job &J = *G.members[j];
+    if (J.done >= J.d.steps) {
+      k_col<<<nb, 256, 0, G.st>>>(G.N, G.U, G.R, j, G.col, 0);
+      cudaMemcpyAsync(J.d.u_out, G.col, (size_t)G.N * sizeof(double), cudaMemcpyDeviceToHost, G.st);
+      if (cudaStreamSynchronize(G.st) != cudaSuccess && !J.status) J.status = HPS_ECUDA;
+      const int st = hps_status(G.h, (hps_stream_t)G.st);
+      if (st && !J.status) J.status = st;
+      J.finish_s = now_s(t0);
+      J.state = kDone;
+      J.grp = nullptr;
+      changed = true;
+    } else {
+      stay.push_back(&J);
+      from.push_back(j);
+    }
+  }
+  while (!G.pending.empty() && (int)stay.size() < G.cap) {
+    stay.push_back(G.pending.front());
+    from.push_back(-1);
+    G.pending.erase(G.pending.begin());
+    changed = true;
+  }
+  if (!changed) return HPS_OK;
+  const int Rn = stay.empty() ? 0 : std::min(G.cap, round4i((int)stay.size()));
+  if (Rn > 0) {
+    std::vector<int> map(Rn, -1);
+    for (size_t i = 0; i < stay.size(); ++i) map[i] = from[i];
+    if (cudaMemcpyAsync(G.d_map, map.data(), Rn * sizeof(int), cudaMemcpyHostToDevice, G.st) != cudaSuccess)
+      return HPS_ECUDA;
+    if (G.R > 0) {
+      k_repack<<<(unsigned)std::min<int64_t>((G.N * Rn + 255) / 256, 8192), 256, 0, G.st>>>(G.N, G.U, G.R, G.U2, Rn,
+                                                                                            G.d_map);
+    } else {
+      cudaMemsetAsync(G.U2, 0, (size_t)G.N * Rn * sizeof(double), G.st);
+    }
+    std::swap(G.U, G.U2);
+    const double now = now_s(t0);
+    for (size_t i = 0; i < stay.size(); ++i) {
+      if (from[i] >= 0) continue;
+      Job &J = *stay[i];
+      cudaMemcpyAsync(G.col, J.d.u0, (size_t)G.N * sizeof(double), cudaMemcpyHostToDevice, G.st);
+      k_col<<<nb, 256, 0, G.st>>>(G.N, G.U, Rn, (int)i, G.col, 1);
+      J.admit_s = now;
+      J.step_ms.reserve(J.d.steps);
+    }
+  }
+  G.members = stay;
+  G.R = Rn;
+  return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
+}
+
+int run_batched(hps_server *S) {
+  std::vector<Job *> order;
+  for (auto &j : S->jobs)
+    if (j->state == kWaiting) order.push_back(j.get());
+  std::stable_sort(order.begin(), order.end(), [](Job *a, Job *b) { return a->d.arrival_s < b->d.arrival_s; });
+  const auto t0 = std::chrono::steady_clock::now();
+  size_t next = 0;
+  int err = HPS_OK;
+  auto in_flight_jobs = [&]() {
+    int n = 0;
+    for (auto &g : S->groups) n += (int)(g->members.size() + g->pending.size());
+    return n;
+  };
+  for (;;) {
+    const int busy = in_flight_jobs();
+    if (next >= order.size() && busy == 0) break;
+    bool progressed = false;
+    const double t = now_s(t0);
+    // 1. completed steps
+    for (auto &gp : S->groups) {
+      Group &G = *gp;
+      while (G.done < G.enq && cudaEventQuery(G.ev[2 * (G.done % kRing) + 1]) == cudaSuccess) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, G.ev[2 * (G.done % kRing)], G.ev[2 * (G.done % kRing) + 1]);
+        for (Job *J : G.members) {
+          J->step_ms.push_back(ms);
+          ++J->done;
+        }
+        G.col_steps += (int64_t)G.members.size();
+        ++G.steps;
+        ++G.done;
+        progressed = true;
+      }
+    }
+    // 2. admissions in arrival order: into a batch of the same operation with a free column, else a
+    // new batch (memory permitting; a job that must wait for memory holds the queue)
+    while (next < order.size() && order[next]->d.arrival_s <= t && in_flight_jobs() < S->max_active) {
+      Job &J = *order[next];
+      Group *G = nullptr;
+      for (auto &g : S->groups)
+        if (g->h && same_op(*g, J.d) && (int)(g->members.size() + g->pending.size()) < g->cap) {
+          G = g.get();
+          J.shared_ops = true;
+          break;
+        }
+      if (!G) {
+        int rej = HPS_OK;
+        const int builds = S->builds;
+        if (!create_group(S, J, t, &G, &rej)) {
+          if (rej || in_flight_jobs() == 0) {  // it never fits: reject, the rest still runs
+            J.state = kRejected;
+            J.status = rej ? rej : HPS_ENOMEM;
+            ++next;
+            progressed = true;
+            continue;
+          }
+          break;
+        }
+        J.shared_ops = false;
+        if (S->builds == builds) J.shared_ops = true, --S->cache_hits;  // (create_group counted the cache hit)
+      }
+      if (J.shared_ops) ++S->cache_hits;  // a running batch of its operation: operators shared
+      G->pending.push_back(&J);
+      J.grp = G;
+      J.state = kActive;
+      J.N = G->N;
+      J.bytes = G->bytes / G->cap;
+      ++next;
+      progressed = true;
+    }
+    S->max_concurrent = std::max(S->max_concurrent, in_flight_jobs());
+    // 3. step boundaries and steps
+    for (auto &gp : S->groups) {
+      Group &G = *gp;
+      if (!G.h) continue;
+      bool leaving = false;
+      for (Job *J : G.members) leaving |= J->done >= J->d.steps;
+      if (G.done == G.enq && (leaving || !G.pending.empty())) {
+        if (int e = group_boundary(G, t0)) err = e;
+        progressed = true;
+      }
+      if (G.members.empty() || !G.pending.empty()) continue;  // joiners get in once the queue drains
+      int room = 1 << 30;
+      for (Job *J : G.members) room = std::min(room, J->d.steps - J->done);
+      room -= G.enq - G.done;
+      while (G.enq - G.done < kInFlight && room > 0) {
+        const int slot = G.enq % kRing;
+        hps_ark_terms terms{};
+        terms.g_kind = G.g_kind;
+        terms.g_param[0] = G.g_param[0];
+        terms.g_param[1] = G.g_param[1];
+        cudaEventRecord(G.ev[2 * slot], G.st);
+        const int e = ark_step_batch(G.h, G.R, G.U, 0.0, 4.0 * G.key.gdt, &terms, G.refine, (hps_stream_t)G.st);
+        cudaEventRecord(G.ev[2 * slot + 1], G.st);
+        if (e) {
+          err = e;
+          for (Job *J : G.members) J->status = e;
+        }
+        ++G.enq;
+        --room;
+        progressed = true;
+      }
+    }
+    if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+  S->makespan_s = now_s(t0);
+  for (auto &g : S->groups)
+    if (g->h) release_group(S, *g);
+  S->groups.clear();
+  return err;
+}
+
 }  // namespace
 
 extern "C" {
@@ -219,8 +579,16 @@ int hps_server_submit(hps_server *S, const hps_job_desc *d, int *job_id) {
   return HPS_OK;
 }
 
+int hps_server_set_batching(hps_server *S, int max_cols, int refine) {
+  if (!S || max_cols < 0 || max_cols > 64 || refine < -1 || refine > 8) return HPS_EINVAL;
+  S->batch_cols = max_cols;
+  S->refine = refine;
+  return HPS_OK;
+}
+
 int hps_server_run(hps_server *S) {
   if (!S) return HPS_EINVAL;
+  if (S->batch_cols > 0) return run_batched(S);
   std::vector<Job *> order;
   for (auto &j : S->jobs)
     if (j->state == kWaiting) order.push_back(j.get());
@@ -345,14 +713,18 @@ int hps_server_summary(hps_server *S, hps_server_stats *out) {
   out->peak_bytes = S->peak_used;
   out->factorizations_built = S->builds;
   out->factorizations_shared = S->cache_hits;
+  out->batches_formed = S->groups_formed;
+  out->mean_batch_cols = S->batch_step_count > 0 ? (double)S->batch_col_steps / S->batch_step_count : 0.0;
   return HPS_OK;
 }
 
 void hps_server_free(hps_server *S) {
   if (!S) return;
   cudaDeviceSynchronize();
+  for (auto &g : S->groups)
+    if (g->h) release_group(S, *g);
   for (auto &j : S->jobs)
-    if (j->state == kActive) release_job(S, *j);
+    if (j->state == kActive && !j->grp) release_job(S, *j);
   for (auto &c : S->cache)
     if (c->base) hps_free(c->base);
   delete S;

@@ -1,7 +1,9 @@
 """Python binding of the serving loop (hps_server_* in include/hps.h).
 
 Jobs carry host arrays (numpy float64) for their initial and final states; the loop itself
-runs natively (admission by device memory, one CUDA stream per job, graph-replayed steps)."""
+runs natively (admission by device memory, one CUDA stream per job or per batch, graph-replayed
+steps).  batch_cols > 0 coalesces jobs of the same operation into batched mixed-precision steps
+(hps_server_set_batching)."""
 import ctypes
 
 import numpy as np
@@ -12,10 +14,12 @@ from .hps import G_KINDS, Tree, hps_sizes
 
 
 class Server:
-    def __init__(self, mem_budget_bytes, max_active=8):
+    def __init__(self, mem_budget_bytes, max_active=8, batch_cols=0, refine=-1):
         h = ctypes.c_void_p()
         check(lib().hps_server_create(int(mem_budget_bytes), int(max_active), ctypes.byref(h)), "hps_server_create")
         self._h = h
+        if batch_cols:
+            check(lib().hps_server_set_batching(h, int(batch_cols), int(refine)), "hps_server_set_batching")
         self._keep = []
         self.jobs = []
 
