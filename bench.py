@@ -43,8 +43,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eager", action="store_true", help="launch every kernel from the host (no CUDA graph)")
     ap.add_argument("--rhs", type=int, default=32, help="right-hand sides of the mixed-precision batch")
-    ap.add_argument("--only", choices=["fp64", "mixed", "serving"], default=None,
-                    help="time one form only (profiling); serving: only the serving run, its JSON")
+    ap.add_argument("--only", choices=["fp64", "mixed", "serving", "per-node-fp32", "many-instances"], default=None,
+                    help="time one form only (profiling); serving: only the serving run; per-node-fp32: "
+                         "--steps FP32 single-right-hand-side sweeps on the --per-node-workload handle")
     ap.add_argument("--serving-jobs", type=int, default=48, help="jobs of the serving run (0: skip)")
     ap.add_argument("--refine", type=int, default=1, help="FP64 refinement sweeps per implicit solve (mixed)")
     ap.add_argument("--groups", type=int, default=1, help="column groups of the mixed batch (own streams each)")
@@ -52,6 +53,7 @@ def parse():
                     help="workload of the per-node-operator section (single-RHS HBM-bound solve, mixed vs FP64); "
                          "'none' skips it")
     ap.add_argument("--per-node-refine", type=int, default=2, help="refinement sweeps of its mixed ARK step")
+    ap.add_argument("--instances", type=int, default=64, help="instances of the many-instance run (0: skip)")
     ap.add_argument("--per-node-umma", type=int, default=2, choices=[0, 1, 2],
                     help="its leaf applies on the tcgen05 tensor cores: 0 none, 1 first sweeps, 2 every sweep")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
@@ -575,6 +577,8 @@ def bench_ours(args, rank, world, local_rank):
     S.close()
     if rank == 0 and out is not None and args.only is None and args.per_node_workload != "none":
         out["per_node"] = bench_per_node(args, flush)
+    if rank == 0 and out is not None and args.only is None and args.instances > 0:
+        out["many_instances"] = bench_multi(args, flush)
         pn = out["per_node"]
         out["fp32_single_rhs_solve"] = pn["fp32_sweep_solve"]
     if rank == 0 and out is not None and args.serving_jobs > 0 and args.only is None:
@@ -582,6 +586,37 @@ def bench_ours(args, rank, world, local_rank):
         out["serving"]["batched_over_plain_fp64_sweep"] = (out["serving"]["batched_mixed"]["dof_stages_per_s"] /
                                                            out["fp64_single_rhs"]["value"])
     return out
+
+
+def per_node_fp32_sweeps(args):
+    """Profiling form: --warmup + --steps FP32 sweeps with one right-hand side (hps_solve_batch,
+    R = 1, no refinement) on the per-node-operator handle of --per-node-workload, eager launches."""
+    import numpy as np
+    import torch
+    from paper_2306_02526_gb300 import build as _b
+    from paper_2306_02526_gb300 import hps, workloads
+    _b.build()
+    wl = workloads.WORKLOADS[args.per_node_workload]
+    tree = hps.Tree(wl.n1, wl.n2)
+    N, N_int, N_bd = hps.hps_sizes(tree, wl.p)
+    x, y = hps.hps_coords(tree, wl.p)
+    I = np.arange(N_int)
+    coef = {k: torch.tensor(np.broadcast_to(v, (N_int,)).copy(), dtype=torch.float64, device="cuda")
+            for k, v in wl.coef(x[I], y[I]).items()}
+    S = hps.HPSSolver(tree, wl.p, coef, 0.25 * wl.dt)
+    S.batch_reserve(1)
+    rhs = torch.tensor(np.random.default_rng(3).uniform(-0.1, 0.1, (N_int, 1)), dtype=torch.float64, device="cuda")
+    u = torch.empty((N, 1), dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        S.solve_batch(rhs, u=u, refine=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        S.solve_batch(rhs, u=u, refine=0)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / max(1, args.steps)
+    S.close()
+    return {"workload": wl.name, "N": N, "sweeps": args.steps, "ms_per_sweep_wall": ms}
 
 
 def bench_per_node(args, flush):
@@ -725,6 +760,94 @@ def bench_per_node(args, flush):
     return out
 
 
+def bench_multi(args, flush):
+    """Many independent instances of uneven sizes (workloads.instances: 64 seeded reaction-diffusion
+    instances, leaf grids 16^2..64^2, p in {8, 12, 16}, per-node operators), --rhs states each,
+    advanced together by hps_multi_ark_step (every instance's batched mixed-precision step on its
+    own stream, the whole step one CUDA graph), tensor-core leaf applies in every sweep and
+    --per-node-refine refinement sweeps; the same steps with the instances one after another on
+    one stream for comparison; columns 0 and R-1 of four instances against the FP64 path."""
+    import numpy as np
+    import torch
+    from paper_2306_02526_gb300 import hps, workloads
+    ins = workloads.instances(count=args.instances)
+    R = args.rhs
+    t0 = time.perf_counter()
+    solvers, states, U0s, Ns = [], [], [], []
+    op_bytes = 0
+    for w in ins:
+        tree = hps.Tree(w.n1, w.n2)
+        N, N_int, _ = hps.hps_sizes(tree, w.p)
+        x, y = hps.hps_coords(tree, w.p)
+        bd = hps.hps_boundary_index(tree, w.p)
+        coef = {k: torch.tensor(v, dtype=torch.float64, device="cuda") for k, v in w.coef(x[:N_int], y[:N_int]).items()}
+        S = hps.HPSSolver(tree, w.p, coef, 0.25 * w.dt)
+        S.batch_reserve(R)
+        S.batch_option("umma_leaf", args.per_node_umma)
+        op_bytes += hps.hps_bytes(tree, w.p, nodal=True)
+        U0 = np.stack([workloads.uniform_state(1000 * len(solvers) + j, N, bd) for j in range(R)], axis=1)
+        solvers.append(S)
+        U0s.append(U0)
+        states.append(torch.tensor(U0, dtype=torch.float64, device="cuda"))
+        Ns.append(N)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    M = hps.MultiStep(solvers)
+    M.set_graph(True)
+    stream = torch.cuda.current_stream()
+    dt, gk = ins[0].dt, dict(g="allen_cahn", g_param=(1.0, 0.0))
+    step = lambda: M.ark_step(states, dt, refine=args.per_node_refine, **gk)
+    nwarm, ntimed = 3, max(3, min(args.steps, 5))
+    for _ in range(nwarm):
+        step()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ntimed)]
+    for k in range(ntimed):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    # the same step with the instances one after another on the caller's stream (no graph)
+    M.set_graph(False)
+    seq = []
+    for k in range(2):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(float(k))
+        a.record(stream)
+        for S, u in zip(solvers, states):
+            S.ark_step_batch(u, 0.0, dt, refine=args.per_node_refine, **gk)
+        b.record(stream)
+        b.synchronize()
+        seq.append(a.elapsed_time(b))
+    nsteps = nwarm + ntimed + 2
+    errs = []
+    for i in range(0, len(solvers), max(1, len(solvers) // 4)):
+        S = solvers[i]
+        ref = torch.empty(Ns[i], dtype=torch.float64, device="cuda")
+        for j in sorted({0, R - 1}):
+            ref.copy_(torch.from_numpy(U0s[i][:, j].copy()))
+            for n in range(nsteps):
+                S.ark_step(ref, n * dt, dt, **gk)
+            errs.append(float((states[i][:, j] - ref).abs().max() / ref.abs().max()))
+    M.close()
+    for S in solvers:
+        S.close()
+    units = sum(Ns) * R * STAGES
+    return {"instances": len(ins), "rhs_each": R, "sum_N": sum(Ns), "leaf_grids": sorted({w.n1 for w in ins}),
+            "orders": sorted({w.p for w in ins}), "operators": "one per tree node (seeded coefficients)",
+            "operator_bytes_fp64": op_bytes, "build_s": build_s,
+            "value": units / (statistics.mean(ms) * 1e-3), "unit": "DOF*stages/s",
+            "ms_per_step": statistics.mean(ms), "steps": ntimed,
+            "launch": "one CUDA graph per step for all instances (hps_multi_set_graph)",
+            "sequential_ms_per_step": statistics.mean(seq),
+            "concurrent_over_sequential": statistics.mean(seq) / statistics.mean(ms),
+            "refine": args.per_node_refine, "umma_leaf": args.per_node_umma,
+            "err_vs_fp64": max(errs), "err_sample": "columns 0 and R-1 of every %d-th instance after %d steps"
+                                                    % (max(1, len(solvers) // 4), nsteps),
+            "l2": "flushed before every timed step"}
+
+
 # operations the serving stream draws from (leaf grid, p, kind): heat u_t = Lap u (dt = 0.01) or
 # Allen-Cahn u_t = 0.01 Lap u + u - u^3 (dt = 1e-3), spanning leaf grids 8x8 .. 128x128 and p 8 .. 16
 SERVING_CATALOG = ((8, 8, "heat"), (16, 12, "ac"), (32, 16, "heat"), (64, 16, "ac"), (128, 8, "heat"),
@@ -833,6 +956,15 @@ def main():
         from paper_2306_02526_gb300 import build as _b
         _b.build()
         print(json.dumps(bench_serving(args)))
+        return
+    if args.only == "per-node-fp32":
+        print(json.dumps(per_node_fp32_sweeps(args)))
+        return
+    if args.only == "many-instances":
+        from paper_2306_02526_gb300 import build as _b
+        _b.build()
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        print(json.dumps(bench_multi(args, flush)))
         return
     if world > 1:
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))

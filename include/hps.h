@@ -300,6 +300,25 @@ int ark_step_host(hps_handle *h, double *u_host, double t, double dt, const hps_
 int ark_step_batch_host(hps_handle *h, int R, double *u_host, double t, double dt, const hps_ark_terms *terms,
                         int refine, hps_stream_t stream);
 
+/* ---- Many instances ------------------------------------------------------------------------
+ * n independent instances (handles with their own trees, p and coefficients, each reserved with
+ * hps_batch_reserve for its column count) advanced together: one call runs every instance's
+ * batched mixed-precision ARK step (ark_step_batch) on an internal stream forked from `stream`
+ * and joined back into it, so the per-level kernels of different instances share the GPU.  With
+ * hps_multi_set_graph(m, 1) the whole multi-instance step is recorded into one CUDA graph on the
+ * second call with equal arguments (every instance a branch) and replayed: one graph launch per
+ * step for all instances (the instances' own graph replay is switched off).  u[i]: device state of
+ * instance i, N_i x R[i] RHS-fastest; terms: n entries (or NULL: no q, f, g); dt must match every
+ * handle's gamma_dt (dt = 4 gamma_dt).  The handles must outlive the object and must not be used
+ * on other streams while a step runs.  The instances' launches run concurrently inside one graph;
+ * they are not fused into one kernel per tree level. */
+typedef struct hps_multi hps_multi;
+int hps_multi_create(hps_handle *const *handles, int n, hps_multi **out);
+int hps_multi_set_graph(hps_multi *m, int enable);
+int hps_multi_ark_step(hps_multi *m, double *const *u, const int *R, const hps_ark_terms *terms, double dt, int refine,
+                       hps_stream_t stream);
+void hps_multi_free(hps_multi *m);
+
 /* ---- Kernel variants and their autotuner --------------------------------------------------
  * Options select among kernel variants (all compute the same result to the path's tolerance:
  * 1e-10 for the batched mixed-precision path, 1e-12 for FP64).  Most belong to the batched path;
@@ -353,11 +372,13 @@ enum {
                                    until this many CTAs per SM (1..8, default 3; not while the
                                    persistent merge kernel is on)                                  */
   HPS_OPT_UMMA_LEAF = 24,       /* 1: the first sweep of a solve applies PER-NODE leaf operators (variable
-                                   coefficients, q <= 256, 16 or 32 columns) on the 5th-generation
+                                   coefficients, 32 <= q <= 256, 16 or 32 columns) on the 5th-generation
                                    tensor cores: tcgen05.mma kind::tf32 with 3xTF32 products and the
                                    accumulator in tensor memory, operator boxes streamed by TMA
                                    (default 1); 2: every sweep, the refinement sweeps included;
-                                   0: FP32 FFMA                                                     */
+                                   3: BF16 trial -- the first sweep's leaf applies as ONE BF16
+                                   product (kind::f16, BF16 operator copy made when set; q >= 64),
+                                   refinement sweeps FP32 FFMA; 0: FP32 FFMA                        */
   HPS_OPT_COUNT = 25
 };
 int hps_batch_set_option(hps_handle *h, int opt, int value);

@@ -117,6 +117,11 @@ SIGNATURES = {
     "hps_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(hps_job_desc), ctypes.POINTER(ctypes.c_int)]),
     "hps_server_run": (ctypes.c_int, [ctypes.c_void_p]),
     "hps_server_set_batching": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "hps_multi_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "hps_multi_set_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "hps_multi_ark_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int),
+                                          ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p]),
+    "hps_multi_free": (None, [ctypes.c_void_p]),
     "hps_server_job_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(hps_job_stats)]),
     "hps_server_summary": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(hps_server_stats)]),
     "hps_server_free": (None, [ctypes.c_void_p]),

@@ -439,7 +439,9 @@ int hps_build(const hps_tree *tree, int p, const hps_coeffs *coeffs, double gamm
 namespace hps {
 
 int smem_optin(const void *kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return HPS_OK;
+  // the 48 KB default covers dynamic AND static shared memory: opt in well below it, so that a
+  // kernel with a few static bytes (a flag, a counter) and 48 KB of dynamic memory still launches
+  if (bytes <= 32 * 1024) return HPS_OK;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return HPS_ECUDA;
   static std::mutex mu;

@@ -14,6 +14,7 @@
 
 #include "hps_internal.cuh"
 #include "tc5.cuh"
+#include <cuda_bf16.h>
 
 namespace hps {
 
@@ -782,10 +783,11 @@ inline size_t umma_smem_bytes(int p, int RP) {
          (size_t)2 * p * p * 4 + kUmmaBars * 8 + 16;
 }
 // the leaf's q x R right-hand side block must fit the prefetch registers and be float4-aligned,
-// and W (q x ldw) must fit over one operand-tile buffer
+// W (q x ldw) must fit over one operand-tile buffer, and a 32-column operator box must not be
+// wider than the operator (q >= 32, i.e. p >= 8)
 inline bool umma_fits(int p, int R, int RP) {
   const int q = (p - 2) * (p - 2);
-  return (q * R) % 4 == 0 && q * R <= 4 * kUmmaPre * 32 * kUmmaMathWarps && q <= 256 &&
+  return (q * R) % 4 == 0 && q * R <= 4 * kUmmaPre * 32 * kUmmaMathWarps && q >= 32 && q <= 256 &&
          (size_t)q * umma_ldw(RP) * 4 <= 2 * (size_t)umma_kc(q) * RP * 128 && umma_smem_bytes(p, RP) <= 232448;
 }
 
@@ -824,15 +826,22 @@ __device__ __forceinline__ void tmem_ld_half(unsigned taddr, float *v) {
   }
 }
 // One operand element of B (K index r, column n) as TF32 hi / lo at its swizzled position.
-template <int RP>
+// (BF: the value rounded to BF16 at its position in the 64-per-line BF16 layout, no lo part)
+template <int RP, bool BF>
 __device__ __forceinline__ void umma_put_b(uint8_t *Bh, uint8_t *Bl, int r, int n, float v) {
-  const float h = tc5::tf32_hi(v);
-  const unsigned off = (unsigned)(r >> 5) * (RP * 128) + tc5::sw128_off(n, r & 31);
-  *reinterpret_cast<float *>(Bh + off) = h;
-  *reinterpret_cast<float *>(Bl + off) = v - h;
+  if constexpr (BF) {
+    const int k = r & 63;
+    const unsigned off = (unsigned)(r >> 6) * (RP * 128) + (unsigned)(n * 128 + ((((k >> 3) ^ (n & 7)) & 7) << 4) + (k & 7) * 2);
+    *reinterpret_cast<__nv_bfloat16 *>(Bh + off) = __float2bfloat16_rn(v);
+  } else {
+    const float h = tc5::tf32_hi(v);
+    const unsigned off = (unsigned)(r >> 5) * (RP * 128) + tc5::sw128_off(n, r & 31);
+    *reinterpret_cast<float *>(Bh + off) = h;
+    *reinterpret_cast<float *>(Bl + off) = v - h;
+  }
 }
 
-template <int RP>
+template <int RP, bool BF>
 __global__ void __launch_bounds__(kUmmaThreads, 1)
     k_b_leaf_up_umma(GridDims g, int nodes, int R, const int *__restrict__ origin, const float *__restrict__ r32,
                      const __grid_constant__ CUtensorMap tmA, const double *__restrict__ Dg,
@@ -844,8 +853,10 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
   extern __shared__ uint8_t sm_raw[];
   uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(sm_raw) + 1023) & ~uintptr_t(1023));
   const int p = g.p, m = g.m, q = m * m, b = 4 * m;
-  const int KC = umma_kc(q), MT = umma_mt(q), KSTEPS = (q + 7) / 8, NCH = MT * KC;
-  const int BT = KC * RP * 128;                                // one operand-tile set (hi or lo)
+  // BF (the BF16 trial): one BF16 product per K step of 16, 64 K values per 128-byte line
+  constexpr int KL = BF ? 64 : 32;
+  const int KC = (q + KL - 1) / KL, MT = umma_mt(q), KSTEPS = BF ? (q + 15) / 16 : (q + 7) / 8, NCH = MT * KC;
+  const int BT = umma_kc(q) * RP * 128;                        // one operand-tile set (hi or lo)
   uint8_t *Stg = sm;                                           // stages: hi box, lo box
   uint8_t *Bbuf = sm + kUmmaStages * 2 * kUmmaBoxBytes;        // two buffers of (Bh, Bl)
   float *D1x = reinterpret_cast<float *>(Bbuf + 4 * BT), *D1y = D1x + p * p;
@@ -892,15 +903,20 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
       const int k = (int)blockIdx.x + j * (int)gridDim.x;
       if (c >= kUmmaStages && !umma_wait(&sfree[s], (unsigned)((c - kUmmaStages) / kUmmaStages) & 1u, abort_flag))
         break;
-      t5::mbar_expect_tx(&full[s], 2 * kUmmaBoxBytes);
       uint8_t *dst = Stg + s * 2 * kUmmaBoxBytes;
-      t5::tma_load_3d(dst, &tmA, (i % KC) * 32, (i / KC) * 128, 2 * k, &full[s]);
-      t5::tma_load_3d(dst + kUmmaBoxBytes, &tmA, (i % KC) * 32, (i / KC) * 128, 2 * k + 1, &full[s]);
+      if constexpr (BF) {  // one BF16 box of 128 rows x 64 columns
+        t5::mbar_expect_tx(&full[s], kUmmaBoxBytes);
+        t5::tma_load_3d(dst, &tmA, (i % KC) * 64, (i / KC) * 128, k, &full[s]);
+      } else {
+        t5::mbar_expect_tx(&full[s], 2 * kUmmaBoxBytes);
+        t5::tma_load_3d(dst, &tmA, (i % KC) * 32, (i / KC) * 128, 2 * k, &full[s]);
+        t5::tma_load_3d(dst + kUmmaBoxBytes, &tmA, (i % KC) * 32, (i / KC) * 128, 2 * k + 1, &full[s]);
+      }
       last_box[s] = c;
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
-    const unsigned idesc = t5::idesc_tf32(128, RP);
+    const unsigned idesc = BF ? t5::idesc_bf16(128, RP) : t5::idesc_tf32(128, RP);
     for (int j = 0; j < nl; ++j) {
       const int hs = j & 1;
       if (j >= 2 && !umma_wait(&tfree[hs], (unsigned)((j - 2) >> 1) & 1u, abort_flag)) break;
@@ -919,11 +935,16 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
         const unsigned b_h = t5::smem_u32(Bh + kc * RP * 128), b_l = t5::smem_u32(Bl + kc * RP * 128);
         const unsigned d = tmem + (unsigned)(hs * kSet + t * RP);
         for (int ks = 0; ks < 4 && kc * 4 + ks < KSTEPS; ++ks) {
-          const unsigned o = 32u * ks;  // 8 TF32 values further along K inside the 128-byte line
-          t5::mma_tf32(d, t5::desc_sw128_kmajor(a_h + o), t5::desc_sw128_kmajor(b_h + o), idesc,
-                       (kc > 0 || ks > 0) ? 1u : 0u);
-          t5::mma_tf32(d, t5::desc_sw128_kmajor(a_h + o), t5::desc_sw128_kmajor(b_l + o), idesc, 1u);
-          t5::mma_tf32(d, t5::desc_sw128_kmajor(a_l + o), t5::desc_sw128_kmajor(b_h + o), idesc, 1u);
+          const unsigned o = 32u * ks;  // 8 TF32 (16 BF16) values further along K in the 128-byte line
+          if constexpr (BF) {
+            t5::mma_bf16(d, t5::desc_sw128_kmajor(a_h + o), t5::desc_sw128_kmajor(b_h + o), idesc,
+                         (kc > 0 || ks > 0) ? 1u : 0u);
+          } else {
+            t5::mma_tf32(d, t5::desc_sw128_kmajor(a_h + o), t5::desc_sw128_kmajor(b_h + o), idesc,
+                         (kc > 0 || ks > 0) ? 1u : 0u);
+            t5::mma_tf32(d, t5::desc_sw128_kmajor(a_h + o), t5::desc_sw128_kmajor(b_l + o), idesc, 1u);
+            t5::mma_tf32(d, t5::desc_sw128_kmajor(a_l + o), t5::desc_sw128_kmajor(b_h + o), idesc, 1u);
+          }
         }
         t5::mma_commit(&sfree[s]);
       }
@@ -1010,14 +1031,15 @@ __global__ void __launch_bounds__(kUmmaThreads, 1)
 #pragma unroll
           for (int cc = 0; cc < 4; ++cc) {
             const int f = 4 * e + cc, r = f / R;
-            umma_put_b<RP>(Bh, Bl, r, f - r * R, vv[cc]);
+            umma_put_b<RP, BF>(Bh, Bl, r, f - r * R, vv[cc]);
           }
         }
       }
-      for (int idx = mt; idx < (KC * 32 - q) * RP; idx += NTM) umma_put_b<RP>(Bh, Bl, q + idx / RP, idx % RP, 0.f);
+      for (int idx = mt; idx < (KC * KL - q) * RP; idx += NTM)
+        umma_put_b<RP, BF>(Bh, Bl, q + idx / RP, idx % RP, 0.f);
       if (R < RP)
         for (int idx = mt; idx < q * (RP - R); idx += NTM)
-          umma_put_b<RP>(Bh, Bl, idx / (RP - R), R + idx % (RP - R), 0.f);
+          umma_put_b<RP, BF>(Bh, Bl, idx / (RP - R), R + idx % (RP - R), 0.f);
       t5::fence_async_smem();
       mbar_arrive(bready);
       if (j + 1 < nl) prefetch(j + 1);
@@ -1537,7 +1559,7 @@ int launch_b(hps_handle *H, BatchWork &B, int slot, const BPlan &P, const float 
     k_b_reduce<EP><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, B.partial32, ep);
   }
   H->trace.end(slot, st);
-  return HPS_OK;
+  return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
 // ---- merge applies of the upper levels: split K inside the CTA and across a cluster ---------
@@ -2415,6 +2437,18 @@ __global__ void k_kmajor_split(const double *__restrict__ src, int ld64, int64_t
   }
 }
 
+// BF16 copy of the per-node leaf operators for the BF16 trial, K-major: dst[node][r][c] (row stride
+// ldk, a multiple of 8) = A(r, c) rounded to BF16.
+__global__ void k_kmajor_bf16(const double *__restrict__ src, int ld64, int64_t str64, int q, int64_t nops,
+                              __nv_bfloat16 *__restrict__ dst, int ldk) {
+  const int64_t per = (int64_t)q * ldk, total = nops * per;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t node = i / per, rem = i % per;
+    const int r = (int)(rem / ldk), c = (int)(rem % ldk);
+    dst[i] = __float2bfloat16_rn(c < q ? (float)src[node * str64 + (int64_t)c * ld64 + r] : 0.f);
+  }
+}
+
 // Tensor map of the split K-major leaf operators: 3-D (column, row, 2 leaf + part) FP32, boxes of
 // 32 columns x 128 rows x 1 in the 128-byte swizzle; out-of-range rows and columns read as zeros.
 int umma_map(hps_handle *H) {
@@ -2439,6 +2473,41 @@ int umma_map(hps_handle *H) {
   static_assert(sizeof(map) == sizeof(Bt.ainv_map), "tensor map size");
   memcpy(Bt.ainv_map, &map, sizeof map);
   return HPS_OK;
+}
+
+// The BF16 copy of the per-node leaf operators and its tensor map (boxes of 64 columns x 128 rows),
+// made when the BF16 trial is switched on.
+int umma_bf16_reserve(hps_handle *H) {
+  Batch &Bt = H->batch;
+  if (Bt.ainv_bf) return HPS_OK;
+  const int q = H->q;
+  if (H->shared || !H->impl.Ainv || !H->impl.strA || q < 64 || q > 256) return HPS_EINVAL;
+  using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult qr{};
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &qr) != cudaSuccess ||
+      qr != cudaDriverEntryPointSuccess || !fn)
+    return HPS_ECUDA;
+  cudaDeviceSynchronize();
+  const int64_t nops = H->lev[H->L].nodes;
+  const int ldk = (q + 7) & ~7;
+  __nv_bfloat16 *p = nullptr;
+  if (cudaMalloc(&p, (size_t)nops * q * ldk * sizeof(__nv_bfloat16)) != cudaSuccess) return HPS_ENOMEM;
+  H->allocs.push_back(p);
+  k_kmajor_bf16<<<4 * H->num_sms, 256>>>(H->impl.Ainv, H->impl.ldA, H->impl.strA, q, nops, p, ldk);
+  const cuuint64_t dims[3] = {(cuuint64_t)q, (cuuint64_t)q, (cuuint64_t)nops};
+  const cuuint64_t strides[2] = {(cuuint64_t)ldk * 2, (cuuint64_t)q * ldk * 2};
+  const cuuint32_t box[3] = {64, 128, 1}, estr[3] = {1, 1, 1};
+  CUtensorMap map;
+  if (reinterpret_cast<EncodeFn>(fn)(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, p, dims, strides, box, estr,
+                                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return HPS_ECUDA;
+  memcpy(Bt.ainv_map_bf, &map, sizeof map);
+  Bt.ainv_bf = p;
+  return cudaDeviceSynchronize() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
 // FP32 copy of a transposed operator (rows x cols per node) with rows padded to 4 floats.
@@ -2548,13 +2617,27 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
                                         reinterpret_cast<const uint4 *>(H->batch.afrag_lo), MT, KT, H->d_D, B.w32,
                                         B.h32[L]);
     H->trace.end(kLeafUp, st);
-  } else if ((allow_tc || H->batch.umma_leaf == 2) && H->batch.umma_leaf && H->batch.ainv_k && !H->shared &&
-             !ops.identity &&
+  } else if (allow_tc && H->batch.umma_leaf == 3 && H->batch.ainv_bf && !H->shared && !ops.identity &&
+             (Rp == 16 || Rp == 32) && umma_fits(p, R, Rp)) {
+    // BF16 trial: the first sweep's leaf applies as one BF16 product on the tensor cores
+    const size_t smem = umma_smem_bytes(p, Rp);
+    auto kern = Rp == 32 ? k_b_leaf_up_umma<32, true> : k_b_leaf_up_umma<16, true>;
+    if (int e_ = smem_optin((const void *)kern, smem)) return e_;
+    CUtensorMap map;
+    memcpy(&map, H->batch.ainv_map_bf, sizeof map);
+    H->trace.begin(kLeafUp, st);
+    const int64_t n = H->g.N_int * R;
+    k_b_combo<<<(unsigned)((n + 4 * 256 - 1) / (4 * 256)), 256, 0, st>>>(n, rhs, Rsave, B.r32);
+    kern<<<std::min(leaf.nodes, H->num_sms), kUmmaThreads, smem, st>>>(H->g, leaf.nodes, R, leaf.d_origin, B.r32,
+                                                                      map, H->d_D, B.w32, B.h32[L], H->perr);
+    H->trace.end(kLeafUp, st);
+  } else if ((allow_tc || H->batch.umma_leaf == 2) && (H->batch.umma_leaf == 1 || H->batch.umma_leaf == 2) &&
+             H->batch.ainv_k && !H->shared && !ops.identity &&
              (Rp == 16 || Rp == 32) && umma_fits(p, R, Rp)) {
     // per-node leaf operators on the tcgen05 tensor cores (3xTF32), persistent CTAs, after the
     // stage right-hand side as its own streaming pass (FP64 sum saved, FP32 copy for the products)
     const size_t smem = umma_smem_bytes(p, Rp);
-    auto kern = Rp == 32 ? k_b_leaf_up_umma<32> : k_b_leaf_up_umma<16>;
+    auto kern = Rp == 32 ? k_b_leaf_up_umma<32, false> : k_b_leaf_up_umma<16, false>;
     if (int e_ = smem_optin((const void *)kern, smem)) return e_;
     CUtensorMap map;
     memcpy(&map, H->batch.ainv_map, sizeof map);
@@ -3050,7 +3133,7 @@ int batch_reserve(hps_handle *H, int R, int groups) {
       H->allocs.push_back(Bt.afrag_lo);
       k_frag_a<<<blocks((int64_t)n), 256>>>(Bt.impl32.Ainv.p, Bt.impl32.Ainv.ld, q, MT, KT, Bt.afrag_hi, Bt.afrag_lo);
     }
-    if (!H->shared && H->impl.Ainv && H->impl.strA && q <= 256 && umma_smem_bytes(H->p, 16) <= 232448) {
+    if (!H->shared && H->impl.Ainv && H->impl.strA && q >= 32 && q <= 256 && umma_smem_bytes(H->p, 16) <= 232448) {
       // TF32 hi / lo split of the per-node leaf operators, K-major, and its tensor map (tensor-core leaf apply)
       const int64_t nops = H->lev[H->L].nodes;
       Bt.ainv_ldk = round4(q);
@@ -3155,7 +3238,9 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
   if (per_apply && *set != 0 && *set != 2 && *set != 4 && *set != 8) return HPS_EINVAL;
   if (v < 0 || (plan && !per_apply && v < 1) || (opt == HPS_OPT_FLOW_LEVELS && v > kFlowMaxLevels)) return HPS_EINVAL;
   if (opt == HPS_OPT_EO_COLS && (v < 1 || v > 32)) return HPS_EINVAL;
-  if (opt == HPS_OPT_UMMA_LEAF && v > 2) return HPS_EINVAL;
+  if (opt == HPS_OPT_UMMA_LEAF && v > 3) return HPS_EINVAL;
+  if (opt == HPS_OPT_UMMA_LEAF && v == 3)
+    if (int e = umma_bf16_reserve(H)) return e;
   if (opt == HPS_OPT_FP64_PLAN_TARGET) {  // FP64 split plans: not while the persistent kernel holds tasks
     if (v < 1 || v > 8 || H->persistent) return HPS_EINVAL;
     H->fp64_plan_target = v;

@@ -179,10 +179,13 @@ struct Batch {
   int plan_tile_cols = 2;    // merge applies: register-tile columns per thread (8, 4 or 2)
   bool tensor_leaf = true;   // shared leaf operator applied by 3xTF32 warp MMA (else FP32 FFMA)
   unsigned *afrag_hi = nullptr, *afrag_lo = nullptr;  // its TF32 fragments
-  int umma_leaf = 1;         // per-node leaf operators on the tcgen05 tensor cores (3xTF32): 1 first sweep, 2 all
+  int umma_leaf = 1;         // per-node leaf operators on the tcgen05 tensor cores (3xTF32): 1 first sweep, 2 all;
+                             // 3: BF16 trial (first sweep one BF16 product, refinement sweeps FP32 FFMA)
   float *ainv_k = nullptr;   // their TF32 hi / lo split, K-major: [leaf][hi, lo][row][ainv_ldk]
   int ainv_ldk = 0;
   uint64_t ainv_map[16] = {};  // its TMA tensor map (CUtensorMap, 128 bytes)
+  void *ainv_bf = nullptr;       // BF16 trial: their BF16 copy, K-major [leaf][row][round8(q)]
+  uint64_t ainv_map_bf[16] = {}; // its TMA tensor map
   OpSet32 impl32, ident32;
   std::vector<BatchWork> work;
   cudaEvent_t fork = nullptr;
@@ -313,7 +316,8 @@ int selftest_barrier(hps_handle *H, cudaStream_t st);
 
 // ---- handle services (api.cu) ----------------------------------------------------------------
 // Raises a kernel's dynamic shared-memory limit to at least `bytes` on the CURRENT device (the
-// attribute is per device).  Remembers the largest value set per (kernel, device) under a lock,
+// attribute is per device; requests above 32 KB are raised explicitly, since the 48 KB default
+// also has to hold the kernel's static shared memory).  Remembers the largest value set per (kernel, device) under a lock,
 // so every host thread and every device gets the attribute before its first large launch.
 // HPS_OK, or HPS_ECUDA when the runtime refuses the value.
 int smem_optin(const void *kernel, size_t bytes);

@@ -133,6 +133,22 @@ __host__ __device__ constexpr unsigned idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
 }
 
+// Instruction descriptor of tcgen05.mma kind::f16 with BF16 A and B (bits [7,10) and [10,13) = 1),
+// FP32 accumulator, both K-major.
+__host__ __device__ constexpr unsigned idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
+}
+
+// D (TMEM) = A B + (accumulate ? D : 0) with BF16 operands (K = 16 per instruction).
+__device__ __forceinline__ void mma_bf16(unsigned d_tmem, uint64_t adesc, uint64_t bdesc, unsigned idesc,
+                                         unsigned accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // D (TMEM) = A B + (accumulate ? D : 0), one elected thread issues it.
 __device__ __forceinline__ void mma_tf32(unsigned d_tmem, uint64_t adesc, uint64_t bdesc, unsigned idesc,
                                          unsigned accumulate) {

@@ -288,3 +288,46 @@ class HPSSolver:
         check(lib().ark_step_batch_host(self._h, R, _hptr(u_host, self.N * R, "u_host"), float(t), float(dt),
                                         ctypes.byref(terms), int(refine), _stream_ptr(stream)), "ark_step_batch_host")
         return u_host
+
+
+class MultiStep:
+    """Several independent instances (HPSSolver objects, each reserved for its column count)
+    advanced together by one batched ARK step each per call, concurrently (hps_multi_*)."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        arr = (ctypes.c_void_p * len(self.solvers))(*[s._h.value for s in self.solvers])
+        h = ctypes.c_void_p()
+        check(lib().hps_multi_create(arr, len(self.solvers), ctypes.byref(h)), "hps_multi_create")
+        self._h = h
+
+    def set_graph(self, enable=True):
+        check(lib().hps_multi_set_graph(self._h, 1 if enable else 0), "hps_multi_set_graph")
+
+    def ark_step(self, us, dt, g=None, g_param=(1.0, 1.0), refine=1, stream=None):
+        """us: one (N_i, R_i) float64 CUDA tensor per instance, advanced in place."""
+        n = len(self.solvers)
+        if len(us) != n:
+            raise ValueError("expected %d states" % n)
+        up = (ctypes.c_void_p * n)(*[_dptr(u, s.N * u.shape[1], "u").value for u, s in zip(us, self.solvers)])
+        R = (ctypes.c_int * n)(*[int(u.shape[1]) for u in us])
+        terms = (_lib.hps_ark_terms * n)()
+        for t in terms:
+            t.q = None
+            t.f = None
+            t.g_kind = G_KINDS[g]
+            t.g_param[0], t.g_param[1] = float(g_param[0]), float(g_param[1])
+        check(lib().hps_multi_ark_step(self._h, up, R, ctypes.cast(terms, ctypes.c_void_p), float(dt), int(refine),
+                                       _stream_ptr(stream)), "hps_multi_ark_step")
+        return us
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hps_multi_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -11,6 +11,10 @@ Both the CUDA path and the CPU oracle take their inputs from this module.
   varcoef_128   u_t = div(a grad u) + b.grad u + c u + q, a = 1 + 0.5 sin(2 pi x) cos(2 pi y),
                 b = (0.5, -0.25), c = -1, 128x128 leaves, p = 16, dt = 1e-3,
                 exact u = sin(pi x) sin(pi y) e^{-t}
+  varcoef_64    the same on 64x64 leaves (profiling captures)
+  instances     many independent reaction-diffusion instances of uneven sizes (leaf grids 16^2 .. 64^2,
+                p in {8, 12, 16}), seeded coefficients a = 1 + alpha sin(2 pi k1 x) cos(2 pi k2 y),
+                c ~ U[-2, 0], g = u - u^3, dt = 1e-3, seeded states U[-0.1, 0.1]
 """
 import math
 
@@ -129,4 +133,47 @@ class VarCoef128(Workload):
         return self.exact(x, y, 0.0)
 
 
-WORKLOADS = {w.name: w for w in (Heat4x4(), AllenCahn64(), VarCoef128())}
+class VarCoef64(VarCoef128):
+    """The variable-coefficient problem on 64 x 64 leaves (p = 16): a smaller case of the same
+    operator for profiling captures that must stay within a few GB of device memory."""
+    name = "varcoef_64x64_p16"
+    n1 = n2 = 64
+
+
+WORKLOADS = {w.name: w for w in (Heat4x4(), AllenCahn64(), VarCoef128(), VarCoef64())}
+
+
+class Instance(Workload):
+    """One instance of the many-instance workload: u_t = div(a grad u) + c u + u - u^3 on [0,1]^2,
+    a = 1 + alpha sin(2 pi k1 x) cos(2 pi k2 y), written as a11 = a22 = a, a1 = a_x, a2 = a_y, a0 = c."""
+    dt = 1e-3
+    g = "allen_cahn"
+    g_param = (1.0, 0.0)
+
+    def __init__(self, n, p, alpha, k1, k2, c0, index):
+        self.n1 = self.n2 = int(n)
+        self.p = int(p)
+        self.alpha, self.k1, self.k2, self.c0 = float(alpha), int(k1), int(k2), float(c0)
+        self.name = "instance_%d_%dx%d_p%d" % (index, n, n, p)
+
+    def coef(self, x, y):
+        s1, c1 = np.sin(2 * math.pi * self.k1 * x), np.cos(2 * math.pi * self.k1 * x)
+        s2, c2 = np.sin(2 * math.pi * self.k2 * y), np.cos(2 * math.pi * self.k2 * y)
+        a = 1.0 + self.alpha * s1 * c2
+        ax = self.alpha * 2 * math.pi * self.k1 * c1 * c2
+        ay = -self.alpha * 2 * math.pi * self.k2 * s1 * s2
+        return {"a11": a, "a22": a, "a1": ax, "a2": ay, "a0": self.c0 + 0 * x}
+
+    def u0(self, x, y, boundary_index):
+        return uniform_state(0, x.size, boundary_index)
+
+
+def instances(count=64, seed=0, grids=(16, 32, 64), orders=(8, 12, 16)):
+    """`count` seeded instances: leaf grid n x n with n from `grids`, p from `orders`,
+    alpha ~ U[0.1, 0.5], k1, k2 in {1, 2, 3}, c ~ U[-2, 0]."""
+    r = rng(seed)
+    out = []
+    for i in range(count):
+        out.append(Instance(int(r.choice(grids)), int(r.choice(orders)), r.uniform(0.1, 0.5), int(r.integers(1, 4)),
+                            int(r.integers(1, 4)), r.uniform(-2.0, 0.0), i))
+    return out

@@ -77,3 +77,24 @@ def test_umma_ark_batch_matches_fp64(mode, refine):
     err = max(rel_max(got[:, j], us[j].cpu().numpy()) for j in range(R))
     S.close()
     assert err <= TOL, err
+
+
+@pytest.mark.parametrize("n1,n2,p,R", [(8, 4, 16, 32), (16, 16, 12, 16)])
+def test_bf16_trial_first_sweep_is_coarse_and_refines(n1, n2, p, R):
+    """BF16 trial (option umma_leaf = 3): the first sweep's per-node leaf applies as one BF16
+    product on the tensor cores.  Its unrefined error sits at BF16 level (well above the FP32
+    sweep's), and FP32 refinement sweeps still bring the solve to the mixed-precision tolerance."""
+    torch = need_gpu()
+    S, N, N_int, N_bd = _nodal_solver(torch, n1, n2, p, 0.013, 7 * p + R)
+    S.batch_reserve(R)
+    r = np.random.default_rng(R + p)
+    rhs = to_dev(torch, r.standard_normal((N_int, R)))
+    f = to_dev(torch, r.standard_normal((N_bd, R)))
+    want = np.stack([S.solve(rhs[:, j].contiguous(), f[:, j].contiguous()).cpu().numpy() for j in range(R)], axis=1)
+    e_tf = rel_max(S.solve_batch(rhs, f, refine=0).cpu().numpy(), want)
+    S.batch_option("umma_leaf", 3)
+    e_bf = [rel_max(S.solve_batch(rhs, f, refine=k).cpu().numpy(), want) for k in (0, 1, 2, 3)]
+    S.status()
+    S.close()
+    assert 10 * e_tf < e_bf[0] < 5e-2, (e_tf, e_bf)
+    assert e_bf[1] < e_bf[0] and min(e_bf[2], e_bf[3]) <= TOL, e_bf
