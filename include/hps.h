@@ -439,6 +439,7 @@ typedef struct hps_job_stats {
   int shared_operators;  /* 1 if it used a factorization built for an earlier job */
   size_t work_bytes;
   double step_ms_mean, step_ms_p50, step_ms_p99; /* device time of its steps (CUDA events) */
+  int evictions;         /* times it was checkpointed to host memory and queued again */
 } hps_job_stats;
 
 typedef struct hps_server_stats {
@@ -473,6 +474,14 @@ int hps_server_create(size_t mem_budget_bytes, int max_active, hps_server **out)
 int hps_server_set_batching(hps_server *s, int max_cols, int refine);
 /* Queue a job; *job_id (may be NULL) receives its index. */
 int hps_server_submit(hps_server *s, const hps_job_desc *job, int *job_id);
+/* Eviction with checkpoint / resume: once job `job_id` has run `steps` steps (none in flight) its
+ * state u and step count -- hence its time t0 + steps dt -- are copied to host memory, its device
+ * memory and slot (or batch column) are released and it queues again behind the jobs waiting at
+ * that moment; re-admitted, it continues from the checkpoint.  Set before hps_server_run; at most
+ * one eviction per job.  Without batching the resumed job's result is bit-identical to an
+ * uninterrupted run (the same kernels on the same data); with batching it agrees to the
+ * mixed-precision tolerance. */
+int hps_server_evict_after(hps_server *s, int job_id, int steps);
 /* Run until every queued job is done or rejected (blocks; honours arrival times from now). */
 int hps_server_run(hps_server *s);
 int hps_server_job_stats(hps_server *s, int job_id, hps_job_stats *out);

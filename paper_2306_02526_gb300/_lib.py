@@ -45,7 +45,8 @@ class hps_job_stats(ctypes.Structure):
     _fields_ = [("state", ctypes.c_int), ("status", ctypes.c_int), ("arrival_s", ctypes.c_double),
                 ("admit_s", ctypes.c_double), ("finish_s", ctypes.c_double), ("steps_done", ctypes.c_int),
                 ("shared_operators", ctypes.c_int), ("work_bytes", ctypes.c_size_t),
-                ("step_ms_mean", ctypes.c_double), ("step_ms_p50", ctypes.c_double), ("step_ms_p99", ctypes.c_double)]
+                ("step_ms_mean", ctypes.c_double), ("step_ms_p50", ctypes.c_double), ("step_ms_p99", ctypes.c_double),
+                ("evictions", ctypes.c_int)]
 
 
 class hps_tune_result(ctypes.Structure):
@@ -117,6 +118,7 @@ SIGNATURES = {
     "hps_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(hps_job_desc), ctypes.POINTER(ctypes.c_int)]),
     "hps_server_run": (ctypes.c_int, [ctypes.c_void_p]),
     "hps_server_set_batching": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "hps_server_evict_after": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "hps_multi_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "hps_multi_set_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "hps_multi_ark_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int),

@@ -60,6 +60,14 @@ struct Job {
   double admit_s = 0.0, finish_s = 0.0;
   bool shared_ops = false;
   struct Group *grp = nullptr;  // batched serving: the batch it is (or will be) a column of
+  // eviction with checkpoint / resume: after `evict_after` steps the job's state u and its step
+  // count (hence t = t0 + steps dt) go to host memory, its device memory and slot are released,
+  // and it queues again; re-admitted, it resumes from the checkpoint
+  int evict_after = -1;
+  int evictions = 0;
+  std::vector<double> ckpt;
+  bool pending_evict() const { return evict_after >= 0 && evictions == 0; }
+  const double *state_in() const { return evictions > 0 ? ckpt.data() : d.u0; }
 };
 
 // Batched serving: jobs of one operation advanced together as the columns of one state.
@@ -214,8 +222,9 @@ bool admit(hps_server *S, Job &J, double t) {
   J.N = N;
   for (auto &e : J.ev)
     if (cudaEventCreate(&e) != cudaSuccess) return reject(HPS_ECUDA);
-  cudaMemcpyAsync(J.du, d.u0, (size_t)N * sizeof(double), cudaMemcpyHostToDevice, J.st);
+  cudaMemcpyAsync(J.du, J.state_in(), (size_t)N * sizeof(double), cudaMemcpyHostToDevice, J.st);
   J.state = kActive;
+  J.enq = J.done;  // a resumed job continues with its next step
   J.admit_s = t;
   J.step_ms.reserve(d.steps);
   return true;
@@ -385,13 +394,25 @@ inline int round4i(int n) { return (n + 3) & ~3; }
 // A step boundary of G (none of its steps in flight): members that have run all their steps copy
 // their column out and leave, waiting members join, and the columns are repacked into R = the
 // member count rounded up to 4 (at most cap).
-int group_boundary(Group &G, std::chrono::steady_clock::time_point t0) {
+int group_boundary(Group &G, std::chrono::steady_clock::time_point t0, std::vector<Job *> &evicted) {
   std::vector<Job *> stay;
   std::vector<int> from;  // old column of each member of the new layout (-1: a joining job)
   bool changed = false;
   const unsigned nb = (unsigned)std::min<int64_t>((G.N + 255) / 256, 4096);
   for (int j = 0; j < (int)G.members.size(); ++j) {
     Job &J = *G.members[j];
+    if (J.pending_evict() && J.done >= J.evict_after && J.done < J.d.steps) {  // checkpoint and queue again
+      k_col<<<nb, 256, 0, G.st>>>(G.N, G.U, G.R, j, G.col, 0);
+      J.ckpt.resize((size_t)G.N);
+      cudaMemcpyAsync(J.ckpt.data(), G.col, (size_t)G.N * sizeof(double), cudaMemcpyDeviceToHost, G.st);
+      if (cudaStreamSynchronize(G.st) != cudaSuccess && !J.status) J.status = HPS_ECUDA;
+      ++J.evictions;
+      J.state = kWaiting;
+      J.grp = nullptr;
+      evicted.push_back(&J);
+      changed = true;
+      continue;
+    }
     if (J.done >= J.d.steps) {
       k_col<<<nb, 256, 0, G.st>>>(G.N, G.U, G.R, j, G.col, 0);
       cudaMemcpyAsync(J.d.u_out, G.col, (size_t)G.N * sizeof(double), cudaMemcpyDeviceToHost, G.st);
@@ -431,7 +452,7 @@ int group_boundary(Group &G, std::chrono::steady_clock::time_point t0) {
     for (size_t i = 0; i < stay.size(); ++i) {
       if (from[i] >= 0) continue;
       Job &J = *stay[i];
-      cudaMemcpyAsync(G.col, J.d.u0, (size_t)G.N * sizeof(double), cudaMemcpyHostToDevice, G.st);
+      cudaMemcpyAsync(G.col, J.state_in(), (size_t)G.N * sizeof(double), cudaMemcpyHostToDevice, G.st);
       k_col<<<nb, 256, 0, G.st>>>(G.N, G.U, Rn, (int)i, G.col, 1);
       J.admit_s = now;
       J.step_ms.reserve(J.d.steps);
@@ -518,14 +539,17 @@ int run_batched(hps_server *S) {
       Group &G = *gp;
       if (!G.h) continue;
       bool leaving = false;
-      for (Job *J : G.members) leaving |= J->done >= J->d.steps;
+      for (Job *J : G.members) leaving |= J->done >= J->d.steps || (J->pending_evict() && J->done >= J->evict_after);
       if (G.done == G.enq && (leaving || !G.pending.empty())) {
-        if (int e = group_boundary(G, t0)) err = e;
+        std::vector<Job *> evicted;
+        if (int e = group_boundary(G, t0, evicted)) err = e;
+        for (Job *J : evicted) order.push_back(J);  // queued again (admissible at once)
         progressed = true;
       }
       if (G.members.empty() || !G.pending.empty()) continue;  // joiners get in once the queue drains
       int room = 1 << 30;
-      for (Job *J : G.members) room = std::min(room, J->d.steps - J->done);
+      for (Job *J : G.members)
+        room = std::min(room, (J->pending_evict() ? std::min(J->evict_after, J->d.steps) : J->d.steps) - J->done);
       room -= G.enq - G.done;
       while (G.enq - G.done < kInFlight && room > 0) {
         const int slot = G.enq % kRing;
@@ -579,6 +603,12 @@ int hps_server_submit(hps_server *S, const hps_job_desc *d, int *job_id) {
   return HPS_OK;
 }
 
+int hps_server_evict_after(hps_server *S, int job_id, int steps) {
+  if (!S || job_id < 0 || job_id >= (int)S->jobs.size() || steps < 0) return HPS_EINVAL;
+  S->jobs[job_id]->evict_after = steps;
+  return HPS_OK;
+}
+
 int hps_server_set_batching(hps_server *S, int max_cols, int refine) {
   if (!S || max_cols < 0 || max_cols > 64 || refine < -1 || refine > 8) return HPS_EINVAL;
   S->batch_cols = max_cols;
@@ -609,6 +639,19 @@ int hps_server_run(hps_server *S) {
         J.step_ms.push_back(ms);
         ++J.done;
         progressed = true;
+      }
+      if (J.pending_evict() && J.done >= J.evict_after && J.done == J.enq && J.done < J.d.steps) {
+        // checkpoint (u, steps done) to host memory, release the job's memory and slot, queue again
+        J.ckpt.resize((size_t)J.N);
+        cudaMemcpyAsync(J.ckpt.data(), J.du, (size_t)J.N * sizeof(double), cudaMemcpyDeviceToHost, J.st);
+        if (cudaStreamSynchronize(J.st) != cudaSuccess) J.status = HPS_ECUDA;
+        ++J.evictions;
+        J.state = kWaiting;
+        release_job(S, J);
+        order.push_back(&J);
+        active.erase(active.begin() + i);
+        progressed = true;
+        continue;
       }
       if (J.done == J.d.steps) {
         cudaMemcpyAsync(J.d.u_out, J.du, (size_t)J.N * sizeof(double), cudaMemcpyDeviceToHost, J.st);
@@ -642,7 +685,7 @@ int hps_server_run(hps_server *S) {
     // 3. keep up to kInFlight steps queued per job
     for (Job *Jp : active) {
       Job &J = *Jp;
-      while (J.enq < J.d.steps && J.enq - J.done < kInFlight) {
+      while (J.enq < J.d.steps && J.enq - J.done < kInFlight && !(J.pending_evict() && J.enq >= J.evict_after)) {
         const int slot = J.enq % kRing;
         hps_ark_terms terms{};
         terms.g_kind = J.d.g_kind;
@@ -677,6 +720,7 @@ int hps_server_job_stats(hps_server *S, int job_id, hps_job_stats *out) {
   out->steps_done = (int)J.step_ms.size();
   out->shared_operators = J.shared_ops ? 1 : 0;
   out->work_bytes = J.bytes;
+  out->evictions = J.evictions;
   if (!J.step_ms.empty()) {
     std::vector<float> v = J.step_ms;
     std::sort(v.begin(), v.end());

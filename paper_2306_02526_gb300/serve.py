@@ -47,6 +47,10 @@ class Server:
         self.jobs.append(out)
         return jid.value
 
+    def evict_after(self, job_id, steps):
+        """Checkpoint job `job_id` to host memory after `steps` steps, release it, queue it again."""
+        check(lib().hps_server_evict_after(self._h, int(job_id), int(steps)), "hps_server_evict_after")
+
     def run(self):
         check(lib().hps_server_run(self._h), "hps_server_run")
 

@@ -102,3 +102,22 @@ def test_memory_budget_admission():
     small = min(hps.hps_bytes(j["tree"], j["p"]) for j in jobs)
     res, stats, summ = _serve([jobs[0], jobs[3]], budget=int(small * 1.5))
     assert [s["state"] for s in stats].count(3) >= 1 and summ["jobs_done"] >= 1
+
+
+def test_evicted_job_resumes_bit_identical():
+    """Eviction with checkpoint / resume (hps_server_evict_after): a job checkpointed to host memory
+    after 5 steps, released and re-admitted behind the other jobs ends bit-identical to an
+    uninterrupted run."""
+    need_gpu()
+    from paper_2306_02526_gb300.serve import Server
+    jobs = _jobs()
+    ref, _, _ = _serve([dict(jobs[1], arrival_s=0.0)])
+    S = Server(8 << 30, 2)  # two slots: the evicted job waits for one
+    ids = [S.submit(**j) for j in jobs]
+    S.evict_after(ids[1], 5)
+    S.run()
+    st = S.job_stats(ids[1])
+    got = S.result(ids[1]).copy()
+    S.close()
+    assert st["state"] == 2 and st["status"] == 0 and st["evictions"] == 1 and st["steps_done"] == jobs[1]["steps"]
+    assert np.array_equal(got, ref[0])

@@ -116,3 +116,22 @@ def test_batched_serving_memory_budget():
     # a job that can never fit is rejected
     res, stats, summ = _serve(jobs[:1], budget=hps.hps_bytes(jobs[0]["tree"], jobs[0]["p"]) // 2)
     assert stats[0]["state"] == 3
+
+
+def test_batched_evicted_job_resumes():
+    """A batch member checkpointed after 4 steps leaves its batch, queues again, rejoins a batch and
+    ends within the mixed-precision tolerance of its uninterrupted result and of the FP64 path."""
+    torch = need_gpu()
+    from paper_2306_02526_gb300.serve import Server
+    jobs = _jobs()[:6]
+    ref, _, _ = _serve(jobs)
+    S = Server(16 << 30, 16, batch_cols=8, refine=-1)
+    ids = [S.submit(**j) for j in jobs]
+    S.evict_after(ids[2], 4)
+    S.run()
+    st = S.job_stats(ids[2])
+    got = S.result(ids[2]).copy()
+    S.close()
+    assert st["state"] == 2 and st["evictions"] == 1 and st["steps_done"] == jobs[2]["steps"]
+    assert rel_max(got, ref[2]) <= TOL
+    assert rel_max(got, _fp64(torch, jobs[2])) <= TOL
