@@ -359,7 +359,7 @@ def timed_run(S, step, args, world, local_rank, flush, torch, events_in_region=T
 # from the ncu captures summarised under profiles/; an entry is removed when its kernel changes.
 NCU_TRAFFIC = {
     ("allen_cahn_64x64_p16", "fp64", "leaf_up"): 45.56e6,
-    ("allen_cahn_64x64_p16", "mixed", "residual"): 677.0e6,
+    ("allen_cahn_64x64_p16", "mixed", "residual"): 694.1e6,
 }
 
 
