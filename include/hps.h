@@ -379,7 +379,10 @@ enum {
                                    3: BF16 trial -- the first sweep's leaf applies as ONE BF16
                                    product (kind::f16, BF16 operator copy made when set; q >= 64),
                                    refinement sweeps FP32 FFMA; 0: FP32 FFMA                        */
-  HPS_OPT_COUNT = 25
+  HPS_OPT_ONE_COLUMN_MERGE = 25, /* 1: merge applies with ONE column and per-node operators stream the
+                                   operator without shared-memory staging, K split over the warps
+                                   of a CTA (default 1; 0: the general tiled applies)              */
+  HPS_OPT_COUNT = 26
 };
 int hps_batch_set_option(hps_handle *h, int opt, int value);
 

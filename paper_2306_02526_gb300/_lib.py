@@ -59,7 +59,7 @@ BATCH_OPTIONS = ("tensor_leaf", "even_odd", "flow_levels", "flow_n3_max", "clust
                  "fast_diag", "plan_tile_cols", "fuse_epilogue",
                  "fuse_jump", "fold_scale", "sa_close", "edge_projection",
                  "eo_cols", "tile_cols_w3", "tile_cols_h", "tile_cols_down",
-                 "fp64_plan_target", "umma_leaf")
+                 "fp64_plan_target", "umma_leaf", "one_column_merge")
 
 
 class hps_server_stats(ctypes.Structure):

@@ -1562,6 +1562,145 @@ int launch_b(hps_handle *H, BatchWork &B, int slot, const BPlan &P, const float 
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
+// ---- merge applies with one column and per-node operators (the HBM-bound single-RHS sweep) ----
+// y_k = A_k x_k for every node k of a level, A_k (M x K, stored transposed: column c at
+// AT + k str + c ld) streamed straight from global memory: a thread owns a quad of 4 rows of one
+// node (one 16-byte load per column), the kw warps of a quad group split K inside the CTA and add
+// their partial sums through shared memory in warp order, and levels with too few quads for the
+// GPU split K over CTAs as well (summed by k_b_reduce in chunk order).  No operator staging: each
+// element is used once.
+struct BPlan1 {
+  int M, K, nodes, QN;   // rows, columns, nodes, row quads per node
+  int kw, qcta;          // warps per quad group (in-CTA split of K), quads per CTA
+  int ks, kchunk;        // split of K over CTAs
+  int64_t quads;
+};
+
+BPlan1 plan_b1(int M, int K, int nodes, int target) {
+  BPlan1 P{};
+  P.M = M;
+  P.K = K;
+  P.nodes = nodes;
+  P.QN = (M + 3) / 4;
+  P.quads = (int64_t)nodes * P.QN;
+  P.kw = 8;
+  while (P.kw > 1 && K / P.kw < 16) P.kw /= 2;  // at least 16 columns per warp
+  P.qcta = 32 * (8 / P.kw);
+  const int64_t gx = (P.quads + P.qcta - 1) / P.qcta;
+  int ks = 1;
+  if (gx < target) ks = (int)std::min<int64_t>({(target + gx - 1) / gx, std::max(1, K / (16 * P.kw)), kMaxSplit});
+  P.kchunk = (K + ks - 1) / ks;
+  P.ks = (K + P.kchunk - 1) / P.kchunk;
+  return P;
+}
+
+// The vector entries a CTA needs (its nodes x its K range) are staged in shared memory once
+// (every thread of a node would otherwise rebuild the same entry; the correction sweeps' interface
+// right-hand side is an FP64 gather per entry).
+__host__ __device__ inline int64_t b1_node_span(const BPlan1 &P) { return P.qcta / P.QN + 2; }
+
+template <class XL, class EP>
+__global__ void __launch_bounds__(kBT) k_b_gemv1(BPlan1 P, const float *__restrict__ AT, int ld, int64_t str, XL xl,
+                                                 EP ep, float *__restrict__ partial) {
+  __shared__ float4 red[kBT / 32][32];
+  extern __shared__ float xs1[];  // [node - n0][c - c0]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = warp / P.kw, wk = warp - grp * P.kw;
+  const int64_t q0 = (int64_t)blockIdx.x * P.qcta, quad = q0 + grp * 32 + lane;
+  const int ks = blockIdx.y, c0 = ks * P.kchunk, c1 = min(P.K, c0 + P.kchunk), klen = c1 - c0;
+  const int n0 = (int)(q0 / P.QN), n1 = (int)(min(P.quads, q0 + P.qcta) - 1) / P.QN;  // nodes of this CTA
+  const bool live = quad < P.quads;
+  const int node = live ? (int)(quad / P.QN) : 0, r0 = live ? 4 * (int)(quad - (int64_t)node * P.QN) : 0;
+  const float *a = AT + (int64_t)node * str + r0;
+  const int step = P.kw;
+  constexpr int kU = 8;  // operator loads in flight per thread
+  float4 av[kU];
+  int c = c0 + wk;
+  // the first operator loads go out before the vector staging, so their latency overlaps it
+#pragma unroll
+  for (int u = 0; u < kU; ++u)
+    if (live && c + u * step < c1) av[u] = __ldg(reinterpret_cast<const float4 *>(a + (int64_t)(c + u * step) * ld));
+  for (int i = threadIdx.x; i < (n1 - n0 + 1) * klen; i += blockDim.x) {
+    const int nn = i / klen, cc = i - nn * klen;
+    xs1[i] = xl(n0 + nn, c0 + cc, 0);
+  }
+  __syncthreads();
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (live) {
+    const float *x = xs1 + (int64_t)(node - n0) * klen - c0;
+    for (;;) {
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int cu = c + u * step;
+        if (cu < c1) {
+          const float xv = x[cu];
+          acc.x = fmaf(av[u].x, xv, acc.x);
+          acc.y = fmaf(av[u].y, xv, acc.y);
+          acc.z = fmaf(av[u].z, xv, acc.z);
+          acc.w = fmaf(av[u].w, xv, acc.w);
+        }
+      }
+      c += kU * step;
+      if (c >= c1) break;
+#pragma unroll
+      for (int u = 0; u < kU; ++u)
+        if (c + u * step < c1) av[u] = __ldg(reinterpret_cast<const float4 *>(a + (int64_t)(c + u * step) * ld));
+    }
+  }
+  red[warp][lane] = acc;
+  __syncthreads();
+  if (wk != 0 || !live) return;
+  float4 s = red[warp][lane];
+  for (int w = 1; w < P.kw; ++w) {  // in warp order: deterministic
+    const float4 t = red[warp + w][lane];
+    s.x += t.x;
+    s.y += t.y;
+    s.z += t.z;
+    s.w += t.w;
+  }
+  const float v[4] = {s.x, s.y, s.z, s.w};
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int r = r0 + e;
+    if (r >= P.M) continue;
+    if (P.ks == 1) {
+      const float vv[4] = {v[e], 0.f, 0.f, 0.f};
+      ep.template row<4>(node, r, 0, vv);
+    } else {  // the k_b_reduce layout of a 4-column (padded) plan
+      *reinterpret_cast<float4 *>(partial + (((int64_t)ks * P.nodes + node) * P.M + r) * 4) =
+          make_float4(v[e], 0.f, 0.f, 0.f);
+    }
+  }
+}
+
+template <class XL, class EP>
+int launch_b1(hps_handle *H, BatchWork &B, int slot, int M, int K, int nodes, const float *AT, int ld, int64_t str,
+              XL xl, EP ep, cudaStream_t st, bool *done) {
+  *done = false;
+  const BPlan1 P = plan_b1(M, K, nodes, 4 * H->num_sms);
+  if (P.ks > 1 && (size_t)P.ks * nodes * M * 4 > B.partial_len) return HPS_OK;  // not enough scratch: the general path
+  const size_t smem = (size_t)b1_node_span(P) * P.kchunk * sizeof(float);
+  if (smem > 96 * 1024) return HPS_OK;
+  if (int e_ = smem_optin((const void *)k_b_gemv1<XL, EP>, smem)) return e_;
+  *done = true;
+  H->trace.begin(slot, st);
+  k_b_gemv1<XL, EP><<<dim3((unsigned)((P.quads + P.qcta - 1) / P.qcta), (unsigned)P.ks), kBT, smem, st>>>(
+      P, AT, ld, str, xl, ep, B.partial32);
+  if (P.ks > 1) {
+    BPlan R4{};
+    R4.M = M;
+    R4.K = K;
+    R4.nodes = nodes;
+    R4.R = 1;
+    R4.Rp = 4;
+    R4.ksplit = P.ks;
+    const int64_t n = (int64_t)nodes * M;
+    k_b_reduce<EP><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(R4, B.partial32, ep);
+  }
+  H->trace.end(slot, st);
+  return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
+}
+
 // ---- merge applies of the upper levels: split K inside the CTA and across a cluster ---------
 // One CTA per (node, row tile) and cluster rank; 256 threads = S K-slices x Qc row quads x CG
 // column groups, each thread a 4 x TC register tile over its slice of the CTA's K chunk.  The S
@@ -1669,6 +1808,13 @@ constexpr size_t kB2MaxSmem = 160 * 1024;
 template <class XL, class EP>
 int launch_b2(hps_handle *H, BatchWork &B, int slot, int M, int K, int nodes, int R, const float *AT, int ld,
               int64_t str, XL xl, EP ep, cudaStream_t st) {
+  // per-node operators, one column: streaming applies (the small interface solves w3 = X d of the
+  // lower levels stay on the tiled kernel, which measured faster there)
+  if (R == 1 && str != 0 && H->batch.one_column_merge && !(slot == kMergeUpW3 && M < 128)) {
+    bool done = false;
+    if (int e = launch_b1(H, B, slot, M, K, nodes, AT, ld, str, xl, ep, st, &done)) return e;
+    if (done) return HPS_OK;
+  }
   const BPlan2 P = plan_b2(M, K, nodes, R);
   const size_t smem = b2_smem(P);
   if (!H->batch.gemv2 || smem > kB2MaxSmem)
@@ -3203,6 +3349,7 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
   switch (opt) {
     case HPS_OPT_TENSOR_LEAF: flag = &Bt.tensor_leaf; break;
     case HPS_OPT_UMMA_LEAF: field = &Bt.umma_leaf; break;
+    case HPS_OPT_ONE_COLUMN_MERGE: flag = &Bt.one_column_merge; break;
     case HPS_OPT_EVEN_ODD: flag = &Bt.even_odd; break;
     case HPS_OPT_FLOW_LEVELS: field = &Bt.flow_levels; break;
     case HPS_OPT_FLOW_N3_MAX: field = &Bt.flow_n3_max; break;

@@ -184,6 +184,7 @@ struct Batch {
   float *ainv_k = nullptr;   // their TF32 hi / lo split, K-major: [leaf][hi, lo][row][ainv_ldk]
   int ainv_ldk = 0;
   uint64_t ainv_map[16] = {};  // its TMA tensor map (CUtensorMap, 128 bytes)
+  bool one_column_merge = true; // per-node merge applies with one column streamed without staging
   void *ainv_bf = nullptr;       // BF16 trial: their BF16 copy, K-major [leaf][row][round8(q)]
   uint64_t ainv_map_bf[16] = {}; // its TMA tensor map
   OpSet32 impl32, ident32;
