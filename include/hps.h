@@ -382,7 +382,16 @@ enum {
   HPS_OPT_ONE_COLUMN_MERGE = 25, /* 1: merge applies with ONE column and per-node operators stream the
                                    operator without shared-memory staging, K split over the warps
                                    of a CTA (default 1; 0: the general tiled applies)              */
-  HPS_OPT_COUNT = 26
+  HPS_OPT_ONE_COLUMN_SUM = 26,   /* 1: their split-K partial sums added by the CTA that finishes a
+                                   row block last, in chunk order (default 1; 0: a reduction
+                                   launch)                                                          */
+  HPS_OPT_STREAM_LEAF = 27,      /* c = 1..4: with one to four columns, the per-leaf operators of the
+                                   leaf applies streamed through shared memory by 1-D bulk copies,
+                                   c persistent CTAs per SM, fewer where c rings do not fit in shared
+                                   memory (default 3; 0: one CTA per leaf)                          */
+  HPS_OPT_STREAM_CHUNK_KB = 28,  /* their copies: whole operator columns of about this many KB
+                                   (2..64, default 24)                                              */
+  HPS_OPT_COUNT = 29
 };
 int hps_batch_set_option(hps_handle *h, int opt, int value);
 
@@ -421,17 +430,34 @@ int hps_batch_autotune(hps_handle *h, int R, int refine, hps_stream_t stream, hp
  * kernels on the same data; no reduction order depends on other jobs). */
 typedef struct hps_server hps_server;
 
+/* Sources and boundary data of a served job's next step (eq. stage2: q and f at the stage times
+ * t_j = t + c_j dt, c_j from hps_ark_abscissae): the callback fills q (device, 6 x N_int doubles,
+ * stage-major, q(t_j) at the interior points in global interior order) and f (device, 6 x N_bd
+ * doubles, stage-major, f(t_j) in boundary order; entry 6, c_6 = 1, is also the boundary value of
+ * u^{n+1}) for the step that starts at t.  Every write must be ordered on `stream` (kernels or
+ * asynchronous copies enqueued there): the server enqueues the step after the callback returns,
+ * and the next fill of the same buffers only after that step.  It runs on the thread of
+ * hps_server_run and returns 0, or an error code that ends the job (its status). */
+typedef int (*hps_terms_fn)(void *user, double t, double dt, double *q, double *f, hps_stream_t stream);
+
 typedef struct hps_job_desc {
   hps_tree tree;
   int p;
-  double c_a11, c_a22, c_a1, c_a2, c_a0; /* constant coefficients of L */
+  double c_a11, c_a22, c_a1, c_a2, c_a0; /* constant coefficients of L (when a11 .. a0 are all NULL) */
   double dt, t0;                          /* step and start time (gamma dt = dt / 4) */
   int steps;
-  int g_kind;                             /* HPS_G_* preset, q = 0 and f = 0 */
+  int g_kind;                             /* HPS_G_* preset */
   double g_param[2];
   const double *u0;                       /* host, N doubles; valid until hps_server_run returns */
   double *u_out;                          /* host, N doubles, written when the job finishes */
   double arrival_s;                       /* seconds after hps_server_run starts */
+  /* Nodal coefficients: host arrays of N_int values at the interior points (global interior
+   * order), NULL for a coefficient that is zero; when any is non-NULL they replace c_a11 .. c_a0.
+   * Valid until hps_server_run returns.  Jobs whose arrays hold the same values (compared entry
+   * by entry) share one factorization. */
+  const double *a11, *a22, *a1, *a2, *a0;
+  hps_terms_fn terms;                     /* NULL: q = 0 and f = 0 */
+  void *terms_user;                       /* passed to terms */
 } hps_job_desc;
 
 typedef struct hps_job_stats {
@@ -473,7 +499,11 @@ int hps_server_create(size_t mem_budget_bytes, int max_active, hps_server **out)
  * columns, two N x max_cols states -- measured against the budget).  A job's result then agrees
  * with its FP64 ark_step result to the mixed-precision tolerance (1e-10) and with its result in
  * another mix to rounding (the split of the FP32 merge sums follows R).  max_cols = 0 (default):
- * every job steps on its own with the FP64 ark_step, results bit-identical alone and in a mix. */
+ * every job steps on its own with the FP64 ark_step, results bit-identical alone and in a mix.
+ * Jobs with a terms callback share batches only with other jobs that have one: before each
+ * batched step every member's callback fills a staging pair, copied into its column of the
+ * batch's 6 x N_int x R and 6 x N_bd x R arrays.  For nodal coefficients the stiffness takes the
+ * largest |a11|, |a22| over the points. */
 int hps_server_set_batching(hps_server *s, int max_cols, int refine);
 /* Queue a job; *job_id (may be NULL) receives its index. */
 int hps_server_submit(hps_server *s, const hps_job_desc *job, int *job_id);

@@ -38,7 +38,14 @@ class hps_job_desc(ctypes.Structure):
                 ("c_a1", ctypes.c_double), ("c_a2", ctypes.c_double), ("c_a0", ctypes.c_double),
                 ("dt", ctypes.c_double), ("t0", ctypes.c_double), ("steps", ctypes.c_int), ("g_kind", ctypes.c_int),
                 ("g_param", ctypes.c_double * 2), ("u0", ctypes.c_void_p), ("u_out", ctypes.c_void_p),
-                ("arrival_s", ctypes.c_double)]
+                ("arrival_s", ctypes.c_double), ("a11", ctypes.c_void_p), ("a22", ctypes.c_void_p),
+                ("a1", ctypes.c_void_p), ("a2", ctypes.c_void_p), ("a0", ctypes.c_void_p),
+                ("terms", ctypes.c_void_p), ("terms_user", ctypes.c_void_p)]
+
+
+# int (*)(void *user, double t, double dt, double *q, double *f, hps_stream_t stream)
+TERMS_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
+                            ctypes.c_void_p, ctypes.c_void_p)
 
 
 class hps_job_stats(ctypes.Structure):
@@ -59,7 +66,9 @@ BATCH_OPTIONS = ("tensor_leaf", "even_odd", "flow_levels", "flow_n3_max", "clust
                  "fast_diag", "plan_tile_cols", "fuse_epilogue",
                  "fuse_jump", "fold_scale", "sa_close", "edge_projection",
                  "eo_cols", "tile_cols_w3", "tile_cols_h", "tile_cols_down",
-                 "fp64_plan_target", "umma_leaf", "one_column_merge")
+                 "fp64_plan_target", "umma_leaf", "one_column_merge",
+                 "one_column_sum", "stream_leaf",
+                 "stream_chunk_kb")
 
 
 class hps_server_stats(ctypes.Structure):

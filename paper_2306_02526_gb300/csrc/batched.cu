@@ -179,20 +179,25 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // The stage right-hand side of one leaf, sum_t coef_t ptr_t, over its nq = q*R contiguous
 // entries from offset `off` (FP64): saved to Rsave if non-null and staged as FP32 at
 // Rs[(f / R) * Rp + f % R]; U entries per thread and two terms per round of loads.
+// (threads t0, t0 + nt, ... of the CTA take part; default: all of them)
 template <int U>
 __device__ __forceinline__ void stage_combo(const Combo &rhs, int64_t off, int nq, int R, int Rp,
-                                            double *__restrict__ Rsave, float *Rs) {
+                                            double *__restrict__ Rsave, float *Rs, int t0 = -1, int nt = 0) {
   // FP64 operations per point: one per term, none for a leading term with coefficient 1 (the
   // FP64 pipe bounds this loop on this GPU)
   const bool unit0 = rhs.n > 0 && rhs.coef[0] == 1.0;
-  for (int base = threadIdx.x; base < nq; base += U * blockDim.x) {
+  if (t0 < 0) {
+    t0 = (int)threadIdx.x;
+    nt = (int)blockDim.x;
+  }
+  for (int base = t0; base < nq; base += U * nt) {
     double acc[U];
     {
       const double *s0 = rhs.ptr[0] + off;
       const double c0 = rhs.n > 0 ? rhs.coef[0] : 0.0;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int idx = base + u * blockDim.x;
+        const int idx = base + u * nt;
         const double v = idx < nq && rhs.n > 0 ? s0[idx] : 0.0;
         acc[u] = unit0 ? v : c0 * v;
       }
@@ -204,7 +209,7 @@ __device__ __forceinline__ void stage_combo(const Combo &rhs, int64_t off, int n
       double v0[U], v1[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int idx = base + u * blockDim.x;
+        const int idx = base + u * nt;
         v0[u] = idx < nq ? s0[idx] : 0.0;
         v1[u] = idx < nq ? s1[idx] : 0.0;
       }
@@ -217,7 +222,7 @@ __device__ __forceinline__ void stage_combo(const Combo &rhs, int64_t off, int n
       double v0[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int idx = base + u * blockDim.x;
+        const int idx = base + u * nt;
         v0[u] = idx < nq ? s0[idx] : 0.0;
       }
 #pragma unroll
@@ -225,7 +230,7 @@ __device__ __forceinline__ void stage_combo(const Combo &rhs, int64_t off, int n
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int idx = base + u * blockDim.x;
+      const int idx = base + u * nt;
       if (idx < nq) {
         if (Rsave) Rsave[off + idx] = acc[u];
         Rs[(idx / R) * Rp + idx % R] = d2f_int(acc[u]);
@@ -1192,6 +1197,245 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_down_narrow(GridDims g, int R, c
   }
 }
 
+// ---- streaming leaf applies for one to four columns (per-leaf operators) ------------------
+// The per-leaf operators (A_ii^-1 for the particular solve, S for the interior solve) are read
+// once per sweep and, leaf after leaf, lie contiguously in memory: one persistent CTA per SM
+// streams its leaves' operators through a ring of shared-memory stages with 1-D bulk copies
+// (cp.async.bulk, completion counted on an mbarrier per stage) issued by one producer thread,
+// while 8 consumer warps apply each chunk of columns from shared memory.  The producer runs up to
+// a ring ahead of the consumers, so the loads of the next leaf keep flowing through a leaf's
+// right-hand side gather and output phases.  Every wait is bounded (a timeout sets the error word).
+constexpr int kStreamConsumers = 256;                 // 8 consumer warps
+constexpr int kStreamThreads = 32 + kStreamConsumers;  // + the producer warp
+constexpr int kStreamMaxStages = 16;
+
+struct StreamPlan {
+  int nodes, M, K, ld;  // leaves, operator rows and columns, column stride (floats)
+  int64_t str;          // floats from one leaf's operator to the next
+  int C, NCH, S;        // columns per chunk, chunks per leaf, ring stages
+  int QQ, KS;           // row quads, K slices of the consumer threads
+  int hint;             // L2 evict-first hint on the operator copies
+};
+
+inline size_t stream_smem(const StreamPlan &P, int role_floats);
+// cps: CTAs per SM (1 to 4), each with its own ring: while one CTA gathers a leaf's right-hand
+// side or writes its outputs, the others keep streaming
+inline StreamPlan stream_plan(int nodes, int M, int K, int ld, int64_t str, int cps = 2, int role_floats = 0,
+                              int chunk_kb = 16) {
+  StreamPlan P{};
+  P.nodes = nodes;
+  P.M = M;
+  P.K = K;
+  P.ld = ld;
+  P.str = str;
+  P.C = std::max(1, std::min(K, chunk_kb * 1024 / (ld * 4)));
+  P.NCH = (K + P.C - 1) / P.C;
+  P.QQ = (M + 3) / 4;
+  P.KS = std::max(1, kStreamConsumers / P.QQ);
+  P.hint = 1;
+  P.S = 0;
+  const size_t rest = stream_smem(P, role_floats), budget = (size_t)(227 * 1024) / std::max(1, cps);
+  if (budget > rest) P.S = (int)std::min<size_t>(kStreamMaxStages, (budget - rest) / ((size_t)P.C * ld * 4));
+  return P;
+}
+// shared memory (bytes): ring, right-hand side xs [K][4], slice partials, output ys [4 QQ][4],
+// the role's own floats, barriers and the abort flag
+inline size_t stream_smem(const StreamPlan &P, int role_floats) {
+  const size_t f = (size_t)P.S * P.C * P.ld + 4 * (size_t)P.K + (size_t)P.KS * 16 * P.QQ + 16 * (size_t)P.QQ +
+                   round4(role_floats);
+  return f * sizeof(float) + 2 * kStreamMaxStages * sizeof(uint64_t) + 16;
+}
+inline bool stream_fits(const StreamPlan &P, int role_floats) {
+  return P.QQ <= kStreamConsumers && P.S >= 2 && (P.ld * 4) % 16 == 0 && (P.str * 4) % 16 == 0 &&
+         stream_smem(P, role_floats) <= 227 * 1024;
+}
+
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kStreamConsumers) : "memory"); }
+// consumer barrier that also ORs a predicate over the consumer threads (a uniform decision)
+__device__ __forceinline__ bool consumer_sync_or(bool v) {
+  unsigned r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((unsigned)v), "n"(kStreamConsumers)
+      : "memory");
+  return r != 0;
+}
+
+// Particular solve: xs = the leaf's stage right-hand side, ys = A_ii^-1 xs -> w and its fluxes.
+struct StreamUp {
+  GridDims g;
+  int R;
+  const int *origin;
+  Combo rhs;
+  double *Rsave;
+  const double *Dg;
+  float *w32, *h32;
+  __host__ __device__ int role_floats() const { return 2 * g.p * g.p; }
+  __device__ void setup(float *rs, int t0, int nt) const {
+    for (int i = t0; i < 2 * g.p * g.p; i += nt) rs[i] = (float)Dg[i];
+  }
+  __device__ void prologue(int k, float *xs, float *, int t0, int nt) const {
+    const int q = g.m * g.m;
+    const int64_t l0 = ((int64_t)origin[2 * k + 1] * g.n1 + origin[2 * k]) * q;
+    for (int i = t0; i < q * (4 - R); i += nt) xs[(i / (4 - R)) * 4 + R + i % (4 - R)] = 0.f;
+    stage_combo<4>(rhs, l0 * R, q * R, R, 4, Rsave, xs, t0, nt);
+  }
+  __device__ void epilogue(int k, const float *ys, const float *rs, int t0, int nt) const {
+    const int p = g.p, m = g.m;
+    leaf_up_out(k, m * m, 4 * m, R, 4, ys, rs, rs + p * p, p, m, w32, h32, t0, nt);
+  }
+};
+
+// Interior solve: xs = the leaf's boundary values, u_i = w + S xs.
+struct StreamDown {
+  GridDims g;
+  int R;
+  const int *origin;
+  const float *w32, *g32;
+  UOut uo;
+  __host__ __device__ int role_floats() const { return 0; }
+  __device__ void setup(float *, int, int) const {}
+  __device__ void prologue(int k, float *xs, float *, int t0, int nt) const {
+    const int b = 4 * g.m, ix = origin[2 * k], iy = origin[2 * k + 1];
+    for (int i = t0; i < b * 4; i += nt) {
+      const int pos = i >> 2, j = i & 3;
+      xs[i] = j < R ? g32[box_bd(g, ix, iy, 1, 1, pos) * R + j] : 0.f;
+    }
+  }
+  __device__ void epilogue(int k, const float *ys, const float *, int t0, int nt) const {
+    const int q = g.m * g.m;
+    const int64_t l0 = ((int64_t)origin[2 * k + 1] * g.n1 + origin[2 * k]) * q;
+    for (int idx = t0; idx < q * R; idx += nt) {
+      const int r = idx / R, j = idx - r * R;
+      u_out(uo, (l0 + r) * R + j, w32[((int64_t)k * q + r) * R + j] + ys[r * 4 + j]);
+    }
+  }
+};
+
+// RC: right-hand-side columns computed (1: one column, scalar right-hand side per operator column;
+// 4: up to four columns padded to four)
+template <class Role, int RC>
+__global__ void __launch_bounds__(kStreamThreads, 4)
+    k_b_leaf_stream(StreamPlan P, const float *__restrict__ A, Role role, int *__restrict__ err) {
+  extern __shared__ __align__(16) float sms[];
+  const int S = P.S, stage_f = P.C * P.ld;
+  float *ring = sms, *xs = ring + (size_t)S * stage_f, *part = xs + 4 * P.K, *ys = part + (size_t)P.KS * 16 * P.QQ;
+  float *rs = ys + 16 * P.QQ;
+  uint64_t *full = reinterpret_cast<uint64_t *>(rs + round4(role.role_floats()));
+  uint64_t *empty = full + kStreamMaxStages;
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + kStreamMaxStages);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc5::mbar_init(&full[s], 1);
+      tc5::mbar_init(&empty[s], kStreamConsumers / 32);
+    }
+    *abort_flag = 0;
+    tc5::fence_barrier_init();
+  }
+  __syncthreads();
+  const int nl = (int)blockIdx.x < P.nodes ? (P.nodes - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int total = nl * P.NCH;
+  int last_box[kStreamMaxStages];  // producer: last chunk copied into each stage (-1: none)
+  if (warp == 0) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      const uint64_t pol = tc5::policy_evict_first();
+      for (int s = 0; s < kStreamMaxStages; ++s) last_box[s] = -1;
+      for (int c = 0; c < total; ++c) {
+        const int j = c / P.NCH, i = c - j * P.NCH, s = c % S;
+        const int k = (int)blockIdx.x + j * (int)gridDim.x;
+        if (c >= S && !umma_wait(&empty[s], (unsigned)((c - S) / S) & 1u, abort_flag)) break;
+        const int cols = min(P.C, P.K - i * P.C);
+        const unsigned bytes = (unsigned)(cols * P.ld * 4);
+        const float *src = A + (int64_t)k * P.str + (int64_t)i * P.C * P.ld;
+        tc5::mbar_expect_tx(&full[s], bytes);
+        if (P.hint)
+          tc5::bulk_load_hint(ring + (size_t)s * stage_f, src, bytes, &full[s], pol);
+        else
+          tc5::bulk_load(ring + (size_t)s * stage_f, src, bytes, &full[s]);
+        last_box[s] = c;
+      }
+    }
+  } else {
+    // ---------------- consumers ----------------
+    const int ct = tid - 32;
+    role.setup(rs, ct, kStreamConsumers);
+    const int rq = ct % P.QQ, ks = ct / P.QQ;
+    const bool live = ks < P.KS;
+    bool failed = false;
+    for (int j = 0; j < nl; ++j) {
+      const int k = (int)blockIdx.x + j * (int)gridDim.x;
+      role.prologue(k, xs, rs, ct, kStreamConsumers);
+      consumer_sync();
+      float acc[4][RC];
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int u = 0; u < RC; ++u) acc[e][u] = 0.f;
+      for (int i = 0; i < P.NCH; ++i) {
+        const int c = j * P.NCH + i, s = c % S;
+        if (!failed && !umma_wait(&full[s], (unsigned)(c / S) & 1u, abort_flag)) failed = true;
+        if (!failed && live) {
+          const float *a = ring + (size_t)s * stage_f + 4 * rq;
+          const float *x = xs + 4 * i * P.C;
+          const int cols = min(P.C, P.K - i * P.C);
+          if constexpr (RC == 1) {
+#pragma unroll 4
+            for (int cc = ks; cc < cols; cc += P.KS) {
+              const float4 av = *reinterpret_cast<const float4 *>(a + cc * P.ld);
+              const float xv = x[4 * cc];
+              acc[0][0] = fmaf(av.x, xv, acc[0][0]);
+              acc[1][0] = fmaf(av.y, xv, acc[1][0]);
+              acc[2][0] = fmaf(av.z, xv, acc[2][0]);
+              acc[3][0] = fmaf(av.w, xv, acc[3][0]);
+            }
+          } else {
+#pragma unroll 4
+            for (int cc = ks; cc < cols; cc += P.KS)
+              tile_fma<4>(acc, *reinterpret_cast<const float4 *>(a + cc * P.ld), x + 4 * cc);
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+      }
+      if (live) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          *reinterpret_cast<float4 *>(part + ((size_t)ks * 4 * P.QQ + 4 * rq + e) * 4) =
+              RC == 1 ? make_float4(acc[e][0], 0.f, 0.f, 0.f)
+                      : make_float4(acc[e][0], acc[e][RC > 1 ? 1 : 0], acc[e][RC > 2 ? 2 : 0], acc[e][RC > 3 ? 3 : 0]);
+      }
+      consumer_sync();
+      for (int idx = ct; idx < 16 * P.QQ; idx += kStreamConsumers) {  // slices in order: deterministic
+        float v = 0.f;
+        for (int k2 = 0; k2 < P.KS; ++k2) v += part[(size_t)k2 * 16 * P.QQ + idx];
+        ys[idx] = v;
+      }
+      consumer_sync();
+      role.epilogue(k, ys, rs, ct, kStreamConsumers);
+      if (consumer_sync_or(failed || *abort_flag)) break;  // uniform: every consumer leaves together
+    }
+  }
+  // wind down: every role has left its loop
+  __syncthreads();
+  if (warp == 0 && lane == 0 && *abort_flag) {  // copies still in flight (only a stage's last one can be)
+    for (int s = 0; s < S; ++s)
+      if (last_box[s] >= 0) tc5::mbar_wait(&full[s], (unsigned)(last_box[s] / S) & 1u, kUmmaWaitNs);
+    atomicExch(err, 1);
+  }
+}
+
+template <class Role>
+int launch_stream(hps_handle *H, const StreamPlan &P, int cps, const float *A, const Role &role, cudaStream_t st) {
+  const size_t smem = stream_smem(P, role.role_floats());
+  auto kern = role.R == 1 ? k_b_leaf_stream<Role, 1> : k_b_leaf_stream<Role, 4>;
+  if (int e_ = smem_optin((const void *)kern, smem)) return e_;
+  kern<<<std::min(P.nodes, H->num_sms * cps), kStreamThreads, smem, st>>>(P, A, role, H->perr);
+  return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
+}
+
 // ---- merge applies (FP32, R columns) -------------------------------------------------------
 struct BPlan {
   int M, K, nodes, R, Rp, TC, MQ, CG;
@@ -1601,7 +1845,7 @@ __host__ __device__ inline int64_t b1_node_span(const BPlan1 &P) { return P.qcta
 
 template <class XL, class EP>
 __global__ void __launch_bounds__(kBT) k_b_gemv1(BPlan1 P, const float *__restrict__ AT, int ld, int64_t str, XL xl,
-                                                 EP ep, float *__restrict__ partial) {
+                                                 EP ep, float *__restrict__ partial, unsigned *__restrict__ tile_count) {
   __shared__ float4 red[kBT / 32][32];
   extern __shared__ float xs1[];  // [node - n0][c - c0]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1649,28 +1893,54 @@ __global__ void __launch_bounds__(kBT) k_b_gemv1(BPlan1 P, const float *__restri
   }
   red[warp][lane] = acc;
   __syncthreads();
-  if (wk != 0 || !live) return;
-  float4 s = red[warp][lane];
-  for (int w = 1; w < P.kw; ++w) {  // in warp order: deterministic
-    const float4 t = red[warp + w][lane];
-    s.x += t.x;
-    s.y += t.y;
-    s.z += t.z;
-    s.w += t.w;
-  }
-  const float v[4] = {s.x, s.y, s.z, s.w};
+  if (wk == 0 && live) {
+    float4 s = red[warp][lane];
+    for (int w = 1; w < P.kw; ++w) {  // in warp order: deterministic
+      const float4 t = red[warp + w][lane];
+      s.x += t.x;
+      s.y += t.y;
+      s.z += t.z;
+      s.w += t.w;
+    }
+    const float v[4] = {s.x, s.y, s.z, s.w};
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const int r = r0 + e;
-    if (r >= P.M) continue;
-    if (P.ks == 1) {
-      const float vv[4] = {v[e], 0.f, 0.f, 0.f};
-      ep.template row<4>(node, r, 0, vv);
-    } else {  // the k_b_reduce layout of a 4-column (padded) plan
-      *reinterpret_cast<float4 *>(partial + (((int64_t)ks * P.nodes + node) * P.M + r) * 4) =
-          make_float4(v[e], 0.f, 0.f, 0.f);
+    for (int e = 0; e < 4; ++e) {
+      const int r = r0 + e;
+      if (r >= P.M) continue;
+      if (P.ks == 1) {
+        const float vv[4] = {v[e], 0.f, 0.f, 0.f};
+        ep.template row<4>(node, r, 0, vv);
+      } else if (tile_count) {  // one float per (K chunk, node, row)
+        partial[((int64_t)ks * P.nodes + node) * P.M + r] = v[e];
+      } else {  // the k_b_reduce layout of a 4-column (padded) plan
+        *reinterpret_cast<float4 *>(partial + (((int64_t)ks * P.nodes + node) * P.M + r) * 4) =
+            make_float4(v[e], 0.f, 0.f, 0.f);
+      }
     }
   }
+  if (P.ks == 1 || !tile_count) return;
+  // split K, summed here: the CTA of a quad block that finishes last adds the ks partials of its
+  // rows in chunk order (deterministic), runs the epilogue and re-arms the block's counter
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(tile_count + blockIdx.x, 1u) == (unsigned)(P.ks - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int i = threadIdx.x; i < 4 * P.qcta; i += blockDim.x) {
+    const int64_t qd = q0 + i / 4;
+    if (qd >= P.quads) break;
+    const int nd = (int)(qd / P.QN), r = 4 * (int)(qd - (int64_t)nd * P.QN) + (i & 3);
+    if (r >= P.M) continue;
+    const float *src = partial + (int64_t)nd * P.M + r;
+    const int64_t kstride = (int64_t)P.nodes * P.M;
+    float v = 0.f;
+    for (int k2 = 0; k2 < P.ks; ++k2) v += __ldcg(src + k2 * kstride);
+    const float vv[4] = {v, 0.f, 0.f, 0.f};
+    ep.template row<4>(nd, r, 0, vv);
+  }
+  if (threadIdx.x == 0) tile_count[blockIdx.x] = 0u;
 }
 
 template <class XL, class EP>
@@ -1678,15 +1948,17 @@ int launch_b1(hps_handle *H, BatchWork &B, int slot, int M, int K, int nodes, co
               XL xl, EP ep, cudaStream_t st, bool *done) {
   *done = false;
   const BPlan1 P = plan_b1(M, K, nodes, 4 * H->num_sms);
-  if (P.ks > 1 && (size_t)P.ks * nodes * M * 4 > B.partial_len) return HPS_OK;  // not enough scratch: the general path
+  const int64_t gx = (P.quads + P.qcta - 1) / P.qcta;
+  // split-K sums inside the kernel (last CTA of a quad block) where the counters reach
+  unsigned *tc = H->batch.one_column_merge_sum && gx <= (int64_t)B.tile_count_len ? B.tile_count : nullptr;
+  if (P.ks > 1 && (size_t)P.ks * nodes * M * (tc ? 1 : 4) > B.partial_len) return HPS_OK;  // the general path
   const size_t smem = (size_t)b1_node_span(P) * P.kchunk * sizeof(float);
   if (smem > 96 * 1024) return HPS_OK;
   if (int e_ = smem_optin((const void *)k_b_gemv1<XL, EP>, smem)) return e_;
   *done = true;
   H->trace.begin(slot, st);
-  k_b_gemv1<XL, EP><<<dim3((unsigned)((P.quads + P.qcta - 1) / P.qcta), (unsigned)P.ks), kBT, smem, st>>>(
-      P, AT, ld, str, xl, ep, B.partial32);
-  if (P.ks > 1) {
+  k_b_gemv1<XL, EP><<<dim3((unsigned)gx, (unsigned)P.ks), kBT, smem, st>>>(P, AT, ld, str, xl, ep, B.partial32, tc);
+  if (P.ks > 1 && !tc) {
     BPlan R4{};
     R4.M = M;
     R4.K = K;
@@ -2735,7 +3007,20 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
   const bool tc8 = Rp % 8 == 0;
   const bool narrow = Rp == 4 && !H->shared;  // streaming per-leaf operators, one column group
   const int QQ = (q + 3) / 4, KS = std::max(1, kBT / QQ);
-  if (narrow) {
+  int cps = H->batch.stream_leaf;  // CTAs per SM: fewer where the rings of that many do not fit
+  StreamPlan SPu{};
+  for (; cps > 0; --cps) {
+    SPu = stream_plan(leaf.nodes, q, q, o32.Ainv.ld, o32.Ainv.str, cps, 2 * p * p, H->batch.stream_chunk_kb);
+    if (stream_fits(SPu, 2 * p * p)) break;
+  }
+  const bool stream_up = narrow && cps > 0 && !ops.identity && o32.Ainv.p;
+  if (stream_up) {
+    H->trace.begin(kLeafUp, st);
+    if (int e = launch_stream(H, SPu, cps, o32.Ainv.p,
+                              StreamUp{H->g, R, leaf.d_origin, rhs, Rsave, H->d_D, B.w32, B.h32[L]}, st))
+      return e;
+    H->trace.end(kLeafUp, st);
+  } else if (narrow) {
     const size_t smem = (size_t)(round4(2 * p * p) + 8 * q + KS * 16 * QQ) * sizeof(float);
     if (int e_ = smem_optin((const void *)k_b_leaf_up_narrow, smem)) return e_;
     H->trace.begin(kLeafUp, st);
@@ -2907,7 +3192,17 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
     if (int e = flow_launch(H, B, FA, false, smem_down, nflags, st)) return e;
   }
   H->trace.begin(kLeafDown, st);
-  if (narrow)
+  int cpd = H->batch.stream_leaf;
+  StreamPlan SPd{};
+  for (; cpd > 0; --cpd) {
+    SPd = stream_plan(leaf.nodes, q, b, o32.Sleaf.ld, o32.Sleaf.str, cpd, 0, H->batch.stream_chunk_kb);
+    if (stream_fits(SPd, 0)) break;
+  }
+  const bool stream_down = narrow && cpd > 0 && !ops.identity && o32.Sleaf.p;
+  if (stream_down) {
+    if (int e = launch_stream(H, SPd, cpd, o32.Sleaf.p, StreamDown{H->g, R, leaf.d_origin, B.w32, B.g32, uo}, st))
+      return e;
+  } else if (narrow)
     k_b_leaf_down_narrow<<<leaf.nodes, kBT, (size_t)(4 * b + KS * 16 * QQ) * sizeof(float), st>>>(
         H->g, R, leaf.d_origin, o32.Sleaf.p, o32.Sleaf.ld, o32.Sleaf.str, ops.identity ? 1 : 0, B.w32, B.g32, uo);
   else if (H->shared && !ops.identity && (size_t)(b * o32.Sleaf.ld + (b + q) * Rp) * sizeof(float) <= 110 * 1024) {
@@ -3350,6 +3645,9 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
     case HPS_OPT_TENSOR_LEAF: flag = &Bt.tensor_leaf; break;
     case HPS_OPT_UMMA_LEAF: field = &Bt.umma_leaf; break;
     case HPS_OPT_ONE_COLUMN_MERGE: flag = &Bt.one_column_merge; break;
+    case HPS_OPT_ONE_COLUMN_SUM: flag = &Bt.one_column_merge_sum; break;
+    case HPS_OPT_STREAM_LEAF: field = &Bt.stream_leaf; break;
+    case HPS_OPT_STREAM_CHUNK_KB: field = &Bt.stream_chunk_kb; break;
     case HPS_OPT_EVEN_ODD: flag = &Bt.even_odd; break;
     case HPS_OPT_FLOW_LEVELS: field = &Bt.flow_levels; break;
     case HPS_OPT_FLOW_N3_MAX: field = &Bt.flow_n3_max; break;
@@ -3386,6 +3684,8 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
   if (v < 0 || (plan && !per_apply && v < 1) || (opt == HPS_OPT_FLOW_LEVELS && v > kFlowMaxLevels)) return HPS_EINVAL;
   if (opt == HPS_OPT_EO_COLS && (v < 1 || v > 32)) return HPS_EINVAL;
   if (opt == HPS_OPT_UMMA_LEAF && v > 3) return HPS_EINVAL;
+  if (opt == HPS_OPT_STREAM_LEAF && v > 4) return HPS_EINVAL;
+  if (opt == HPS_OPT_STREAM_CHUNK_KB && (v < 2 || v > 64)) return HPS_EINVAL;
   if (opt == HPS_OPT_UMMA_LEAF && v == 3)
     if (int e = umma_bf16_reserve(H)) return e;
   if (opt == HPS_OPT_FP64_PLAN_TARGET) {  // FP64 split plans: not while the persistent kernel holds tasks
