@@ -1,6 +1,7 @@
 // Continuous-batching server for time-stepping jobs (a native request loop around ark_step).
 //
-// Jobs (tree, p, constant coefficients, dt, steps, g, initial state) arrive at given times.
+// Jobs (tree, p, constant or nodal coefficients, dt, steps, g, sources and boundary data through a
+// per-step callback, initial state) arrive at given times.
 // The loop admits a waiting job as soon as an active slot is free and the device-memory
 // budget allows its operators (unless a resident factorization of an identical operator can
 // be shared) plus its work buffers and state; admitted jobs advance one ARK step at a time,
@@ -23,19 +24,24 @@ namespace {
 constexpr int kRing = 4;      // event pairs per job (steps in flight <= kInFlight < kRing)
 constexpr int kInFlight = 2;
 
+// The operator of a job: tree, p, gamma dt and its coefficients -- five constants, or (nodal) a
+// hash of the five arrays, equal keys then compared entry by entry against the stored arrays.
 struct OpKey {
   hps_tree tree;
   int p;
   double c[5];
   double gdt;
+  int nodal;
+  uint64_t chash;
   bool operator==(const OpKey &o) const {
     return std::memcmp(&tree, &o.tree, sizeof(tree)) == 0 && p == o.p && std::memcmp(c, o.c, sizeof(c)) == 0 &&
-           gdt == o.gdt;
+           gdt == o.gdt && nodal == o.nodal && chash == o.chash;
   }
 };
 
 struct CacheEntry {
   OpKey key;
+  std::vector<double> coef;  // nodal: the five coefficient arrays (5 x N_int, zeros for NULL)
   hps_handle *base = nullptr;
   int users = 0;
   size_t bytes = 0;
@@ -46,12 +52,16 @@ enum JobState { kWaiting = 0, kActive = 1, kDone = 2, kRejected = 3 };
 
 struct Job {
   hps_job_desc d;
+  OpKey key{};
+  int64_t N_int = 0, N_bd = 0;
+  double a11max = 0.0, a22max = 0.0;  // largest |a11|, |a22| over the points (stiffness)
   int state = kWaiting;
   int status = HPS_OK;
   CacheEntry *ce = nullptr;
   hps_handle *h = nullptr;
   cudaStream_t st = nullptr;
   double *du = nullptr;
+  double *dq = nullptr, *df = nullptr;  // terms callback: the step's q (6 x N_int) and f (6 x N_bd)
   int64_t N = 0;
   size_t bytes = 0;
   int enq = 0, done = 0;
@@ -73,6 +83,10 @@ struct Job {
 // Batched serving: jobs of one operation advanced together as the columns of one state.
 struct Group {
   OpKey key;
+  bool with_terms = false;             // members fill q and f before every step
+  double *Q = nullptr, *F = nullptr;   // 6 x N_int x cap, 6 x N_bd x cap (stage-major, columns fastest)
+  double *qs = nullptr, *fs = nullptr; // one member's fill (6 x N_int, 6 x N_bd)
+  int64_t N_int = 0, N_bd = 0;
   int g_kind = 0;
   double g_param[2] = {0.0, 0.0};
   CacheEntry *ce = nullptr;
@@ -116,8 +130,11 @@ double now_s(std::chrono::steady_clock::time_point t0) {
 void release_job(hps_server *S, Job &J) {
   if (J.h) hps_free(J.h);
   J.h = nullptr;
-  if (J.du) cudaFree(J.du);
-  J.du = nullptr;
+  for (double **p : {&J.du, &J.dq, &J.df})
+    if (*p) {
+      cudaFree(*p);
+      *p = nullptr;
+    }
   for (auto &e : J.ev)
     if (e) {
       cudaEventDestroy(e);
@@ -144,31 +161,123 @@ void evict(hps_server *S, size_t need) {
   }
 }
 
-CacheEntry *find_entry(hps_server *S, const OpKey &k) {
+const double *coef_array(const hps_job_desc &d, int c) {
+  const double *a[5] = {d.a11, d.a22, d.a1, d.a2, d.a0};
+  return a[c];
+}
+bool job_nodal(const hps_job_desc &d) { return d.a11 || d.a22 || d.a1 || d.a2 || d.a0; }
+
+// FNV-1a over the bit patterns of the five arrays (a NULL array as zeros)
+uint64_t coef_hash(const hps_job_desc &d, int64_t n) {
+  uint64_t h = 1469598103934665603ull;
+  for (int c = 0; c < 5; ++c) {
+    const double *a = coef_array(d, c);
+    for (int64_t i = 0; i < n; ++i) {
+      uint64_t b = 0;
+      if (a) std::memcpy(&b, a + i, sizeof b);
+      for (int k = 0; k < 8; ++k) {
+        h ^= (b >> (8 * k)) & 0xffu;
+        h *= 1099511628211ull;
+      }
+    }
+  }
+  return h;
+}
+
+// the job's arrays hold exactly the stored values (bit patterns; NULL = zeros)
+bool coef_same(const std::vector<double> &stored, const hps_job_desc &d, int64_t n) {
+  if ((int64_t)stored.size() != 5 * n) return false;
+  for (int c = 0; c < 5; ++c) {
+    const double *a = coef_array(d, c);
+    const double *s = stored.data() + c * n;
+    if (a) {
+      if (std::memcmp(a, s, (size_t)n * sizeof(double)) != 0) return false;
+    } else {
+      for (int64_t i = 0; i < n; ++i)
+        if (std::signbit(s[i]) || s[i] != 0.0) return false;
+    }
+  }
+  return true;
+}
+
+// the operator of J is that of cache entry c
+bool same_operator(const CacheEntry &c, const Job &J) {
+  return c.key == J.key && (!J.key.nodal || coef_same(c.coef, J.d, J.N_int));
+}
+
+CacheEntry *find_entry(hps_server *S, const Job &J) {
   for (auto &c : S->cache)
-    if (c->base && c->key == k) return c.get();
+    if (c->base && same_operator(*c, J)) return c.get();
   return nullptr;
 }
+
+// Builds J's factorization on `st` (nodal coefficients staged to the device for the build) and
+// caches it with `ops` bytes.
+int build_entry(hps_server *S, const Job &J, cudaStream_t st, size_t ops, CacheEntry **out) {
+  const hps_job_desc &d = J.d;
+  hps_coeffs c{};
+  double *dc = nullptr;
+  if (J.key.nodal) {
+    const int64_t n = J.N_int;
+    if (cudaMalloc(&dc, 5 * (size_t)n * sizeof(double)) != cudaSuccess) return HPS_ENOMEM;
+    for (int k = 0; k < 5; ++k) {
+      const double *a = coef_array(d, k);
+      if (a)
+        cudaMemcpyAsync(dc + k * n, a, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st);
+      else
+        cudaMemsetAsync(dc + k * n, 0, (size_t)n * sizeof(double), st);
+    }
+    c.kind = HPS_COEF_NODAL;
+    c.a11 = dc; c.a22 = dc + n; c.a1 = dc + 2 * n; c.a2 = dc + 3 * n; c.a0 = dc + 4 * n;
+  } else {
+    c.kind = HPS_COEF_CONST;
+    c.c_a11 = d.c_a11; c.c_a22 = d.c_a22; c.c_a1 = d.c_a1; c.c_a2 = d.c_a2; c.c_a0 = d.c_a0;
+  }
+  hps_handle *base = nullptr;
+  int e = hps_build(&d.tree, d.p, &c, J.key.gdt, 0, (hps_stream_t)st, &base);
+  if (dc) {
+    if (cudaStreamSynchronize(st) != cudaSuccess && !e) e = HPS_ECUDA;
+    cudaFree(dc);
+  }
+  if (e) {
+    if (base) hps_free(base);
+    return e;
+  }
+  auto entry = std::make_unique<CacheEntry>();
+  entry->key = J.key;
+  if (J.key.nodal) {
+    entry->coef.assign(5 * (size_t)J.N_int, 0.0);
+    for (int k = 0; k < 5; ++k)
+      if (const double *a = coef_array(d, k)) std::memcpy(entry->coef.data() + k * J.N_int, a, (size_t)J.N_int * 8);
+  }
+  entry->base = base;
+  entry->bytes = ops;
+  *out = entry.get();
+  S->cache.push_back(std::move(entry));
+  S->used += ops;
+  ++S->builds;
+  return HPS_OK;
+}
+
+// extra device bytes of a nodal build (the staged coefficient arrays, freed after it)
+size_t build_extra(const Job &J) { return J.key.nodal ? 5 * (size_t)J.N_int * sizeof(double) : 0; }
+// device bytes of one (q, f) pair of a step
+size_t terms_bytes(const Job &J) { return 6 * (size_t)(J.N_int + J.N_bd) * sizeof(double); }
 
 // tries to admit J; returns false when it has to wait for memory or a slot
 bool admit(hps_server *S, Job &J, double t) {
   const hps_job_desc &d = J.d;
-  OpKey key{};
-  key.tree = d.tree;
-  key.p = d.p;
-  key.c[0] = d.c_a11; key.c[1] = d.c_a22; key.c[2] = d.c_a1; key.c[3] = d.c_a2; key.c[4] = d.c_a0;
-  key.gdt = 0.25 * d.dt;
   size_t ops = 0, work = 0;
-  if (hps::bytes_split(&d.tree, d.p, HPS_COEF_CONST, 0, &ops, &work)) {
+  if (hps::bytes_split(&d.tree, d.p, J.key.nodal ? HPS_COEF_NODAL : HPS_COEF_CONST, 0, &ops, &work)) {
     J.state = kRejected;
     J.status = HPS_EINVAL;
     return true;
   }
   int64_t N = 0;
   hps_sizes(&d.tree, d.p, &N, nullptr, nullptr);
-  CacheEntry *ce = find_entry(S, key);
-  const size_t need_job = work + (size_t)N * sizeof(double);
-  const size_t need = need_job + (ce ? 0 : ops);
+  CacheEntry *ce = find_entry(S, J);
+  const size_t need_job = work + (size_t)N * sizeof(double) + (d.terms ? terms_bytes(J) : 0);
+  const size_t need = need_job + (ce ? 0 : ops + build_extra(J));
   if (need > S->budget) {  // can never fit
     J.state = kRejected;
     J.status = HPS_ENOMEM;
@@ -192,20 +301,7 @@ bool admit(hps_server *S, Job &J, double t) {
     return true;
   };
   if (!ce) {  // build and cache the factorization of this operator
-    hps_coeffs c{};
-    c.kind = HPS_COEF_CONST;
-    c.c_a11 = d.c_a11; c.c_a22 = d.c_a22; c.c_a1 = d.c_a1; c.c_a2 = d.c_a2; c.c_a0 = d.c_a0;
-    hps_handle *base = nullptr;
-    const int e = hps_build(&d.tree, d.p, &c, key.gdt, 0, (hps_stream_t)J.st, &base);
-    if (e) return reject(e);
-    auto entry = std::make_unique<CacheEntry>();
-    entry->key = key;
-    entry->base = base;
-    entry->bytes = ops;
-    ce = entry.get();
-    S->cache.push_back(std::move(entry));
-    S->used += ops;
-    ++S->builds;
+    if (int e = build_entry(S, J, J.st, ops, &ce)) return reject(e);
   } else {
     ++S->cache_hits;
     J.shared_ops = true;
@@ -219,6 +315,9 @@ bool admit(hps_server *S, Job &J, double t) {
   if (int e = hps::clone_handle(ce->base, J.st, &J.h)) return reject(e);
   J.h->graph_mode = true;  // a fresh handle: no recorded graphs to discard
   if (cudaMalloc(&J.du, (size_t)N * sizeof(double)) != cudaSuccess) return reject(HPS_ENOMEM);
+  if (d.terms && (cudaMalloc(&J.dq, 6 * (size_t)J.N_int * sizeof(double)) != cudaSuccess ||
+                  cudaMalloc(&J.df, 6 * (size_t)std::max<int64_t>(1, J.N_bd) * sizeof(double)) != cudaSuccess))
+    return reject(HPS_ENOMEM);
   J.N = N;
   for (auto &e : J.ev)
     if (cudaEventCreate(&e) != cudaSuccess) return reject(HPS_ECUDA);
@@ -251,39 +350,63 @@ __global__ void k_col(int64_t N, double *__restrict__ U, int R, int j, double *_
   }
 }
 
+// one member's fill into column j of a batch's stage-major term array: dst[r R + j] = src[r]
+__global__ void k_put_col(int64_t rows, const double *__restrict__ src, double *__restrict__ dst, int R, int j) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x)
+    dst[r * R + j] = src[r];
+}
+
 // Refinement sweeps for the mixed-precision step of an operation when the caller leaves the choice
 // to the server: by the stiffness sigma = gamma dt max(a11 / hx^2, a22 / hy^2) 4 lambda(p), lambda(p)
 // = 0.047 (p - 1)^4 the spectral radius of the 1-D Chebyshev second-derivative matrix on [-1, 1]
 // with Dirichlet ends; the FP32 sweep's error, and with it the number of sweeps that bring the
 // solve to FP64 accuracy, grows with sigma: 1 sweep up to sigma = 1e5 (measured: heat on 32 x 32
 // leaves with p = 16 and dt = 0.01, sigma = 2.4e4, stays within 2e-11 of the FP64 step over ten
-// steps with one sweep), then one more per factor 100.
-int auto_refine(const hps_job_desc &d) {
+// steps with one sweep), then one more per factor 100.  Nodal coefficients: the largest |a11|, |a22|.
+int auto_refine(const Job &J) {
+  const hps_job_desc &d = J.d;
   const double hx = (d.tree.x1 - d.tree.x0) / d.tree.n1, hy = (d.tree.y1 - d.tree.y0) / d.tree.n2;
   const double lam = 0.047 * std::pow((double)(d.p - 1), 4.0);
-  const double sigma = 0.25 * d.dt * std::max(std::fabs(d.c_a11) / (hx * hx), std::fabs(d.c_a22) / (hy * hy)) * 4.0 * lam;
+  const double sigma = 0.25 * d.dt * std::max(J.a11max / (hx * hx), J.a22max / (hy * hy)) * 4.0 * lam;
   int r = 1;
   for (double s = 1e5; sigma > s && r < 4; s *= 100.0) ++r;
   return r;
 }
 
-OpKey job_key(const hps_job_desc &d) {
+// The key of a submitted job (the hash and maxima of nodal coefficients read once, at submission).
+void job_key(Job &J) {
+  const hps_job_desc &d = J.d;
   OpKey key{};
   key.tree = d.tree;
   key.p = d.p;
-  key.c[0] = d.c_a11; key.c[1] = d.c_a22; key.c[2] = d.c_a1; key.c[3] = d.c_a2; key.c[4] = d.c_a0;
   key.gdt = 0.25 * d.dt;
-  return key;
+  if (job_nodal(d)) {
+    key.nodal = 1;
+    key.chash = coef_hash(d, J.N_int);
+    J.a11max = J.a22max = 0.0;
+    for (int64_t i = 0; i < J.N_int; ++i) {
+      if (d.a11) J.a11max = std::max(J.a11max, std::fabs(d.a11[i]));
+      if (d.a22) J.a22max = std::max(J.a22max, std::fabs(d.a22[i]));
+    }
+  } else {
+    key.c[0] = d.c_a11; key.c[1] = d.c_a22; key.c[2] = d.c_a1; key.c[3] = d.c_a2; key.c[4] = d.c_a0;
+    J.a11max = std::fabs(d.c_a11);
+    J.a22max = std::fabs(d.c_a22);
+  }
+  J.key = key;
 }
 
-bool same_op(const Group &G, const hps_job_desc &d) {
-  return G.key == job_key(d) && G.g_kind == d.g_kind && G.g_param[0] == d.g_param[0] && G.g_param[1] == d.g_param[1];
+// J's steps are the operation of batch G: its operator, its g, and terms on both or neither
+bool same_op(const Group &G, const Job &J) {
+  const hps_job_desc &d = J.d;
+  return G.ce && same_operator(*G.ce, J) && G.g_kind == d.g_kind && G.g_param[0] == d.g_param[0] &&
+         G.g_param[1] == d.g_param[1] && G.with_terms == (d.terms != nullptr);
 }
 
 void release_group(hps_server *S, Group &G) {
   if (G.st) cudaStreamSynchronize(G.st);
   if (G.h) hps_free(G.h);
-  for (double *p : {G.U, G.U2, G.col})
+  for (double *p : {G.U, G.U2, G.col, G.Q, G.F, G.qs, G.fs})
     if (p) cudaFree(p);
   if (G.d_map) cudaFree(G.d_map);
   for (auto &e : G.ev)
@@ -301,10 +424,10 @@ void release_group(hps_server *S, Group &G) {
 // device memory its allocations took.  Returns false when the budget does not hold it (J waits).
 bool create_group(hps_server *S, const Job &J, double t, Group **out, int *reject) {
   const hps_job_desc &d = J.d;
-  const OpKey key = job_key(d);
+  const OpKey key = J.key;
   *reject = HPS_OK;
   size_t ops = 0, work = 0;
-  if (hps::bytes_split(&d.tree, d.p, HPS_COEF_CONST, 0, &ops, &work)) {
+  if (hps::bytes_split(&d.tree, d.p, key.nodal ? HPS_COEF_NODAL : HPS_COEF_CONST, 0, &ops, &work)) {
     *reject = HPS_EINVAL;
     return false;
   }
@@ -313,8 +436,9 @@ bool create_group(hps_server *S, const Job &J, double t, Group **out, int *rejec
   const int cap = S->batch_cols;
   // estimate before allocating: FP64 operators if not cached + about 160 bytes per point and
   // column of batched work vectors and states + the single-column work of the handle
-  CacheEntry *ce = find_entry(S, key);
-  const size_t est = (ce ? 0 : ops) + work + (size_t)N * cap * 160 + (size_t)N * 8;
+  CacheEntry *ce = find_entry(S, J);
+  const size_t est = (ce ? 0 : ops + build_extra(J)) + work + (size_t)N * cap * 160 + (size_t)N * 8 +
+                     (d.terms ? terms_bytes(J) * (cap + 1) : 0);
   if (est > S->budget) {
     *reject = HPS_ENOMEM;
     return false;
@@ -334,7 +458,10 @@ bool create_group(hps_server *S, const Job &J, double t, Group **out, int *rejec
   G->g_param[1] = d.g_param[1];
   G->cap = cap;
   G->N = N;
-  G->refine = S->refine >= 0 ? S->refine : auto_refine(d);
+  G->N_int = J.N_int;
+  G->N_bd = J.N_bd;
+  G->with_terms = d.terms != nullptr;
+  G->refine = S->refine >= 0 ? S->refine : auto_refine(J);
   auto fail = [&](int e) -> bool {
     *reject = e;
     release_group(S, *G);
@@ -342,19 +469,7 @@ bool create_group(hps_server *S, const Job &J, double t, Group **out, int *rejec
   };
   if (cudaStreamCreateWithFlags(&G->st, cudaStreamNonBlocking) != cudaSuccess) return fail(HPS_ECUDA);
   if (!ce) {
-    hps_coeffs c{};
-    c.kind = HPS_COEF_CONST;
-    c.c_a11 = d.c_a11; c.c_a22 = d.c_a22; c.c_a1 = d.c_a1; c.c_a2 = d.c_a2; c.c_a0 = d.c_a0;
-    hps_handle *base = nullptr;
-    if (int e = hps_build(&d.tree, d.p, &c, key.gdt, 0, (hps_stream_t)G->st, &base)) return fail(e);
-    auto entry = std::make_unique<CacheEntry>();
-    entry->key = key;
-    entry->base = base;
-    entry->bytes = ops;
-    ce = entry.get();
-    S->cache.push_back(std::move(entry));
-    S->used += ops;
-    ++S->builds;
+    if (int e = build_entry(S, J, G->st, ops, &ce)) return fail(e);
   } else {
     ++S->cache_hits;
   }
@@ -372,6 +487,14 @@ bool create_group(hps_server *S, const Job &J, double t, Group **out, int *rejec
       cudaMalloc(&G->col, (size_t)N * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&G->d_map, (size_t)cap * sizeof(int)) != cudaSuccess)
     return fail(HPS_ENOMEM);
+  if (G->with_terms) {
+    const size_t nb = (size_t)std::max<int64_t>(1, J.N_bd);
+    if (cudaMalloc(&G->Q, 6 * (size_t)J.N_int * cap * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&G->F, 6 * nb * cap * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&G->qs, 6 * (size_t)J.N_int * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&G->fs, 6 * nb * sizeof(double)) != cudaSuccess)
+      return fail(HPS_ENOMEM);
+  }
   for (auto &e : G->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return fail(HPS_ECUDA);
   cudaDeviceSynchronize();
@@ -448,6 +571,10 @@ int group_boundary(Group &G, std::chrono::steady_clock::time_point t0, std::vect
       cudaMemsetAsync(G.U2, 0, (size_t)G.N * Rn * sizeof(double), G.st);
     }
     std::swap(G.U, G.U2);
+    if (G.with_terms) {  // columns moved: every member fills its own before the next step
+      cudaMemsetAsync(G.Q, 0, 6 * (size_t)G.N_int * Rn * sizeof(double), G.st);
+      cudaMemsetAsync(G.F, 0, 6 * (size_t)G.N_bd * Rn * sizeof(double), G.st);
+    }
     const double now = now_s(t0);
     for (size_t i = 0; i < stay.size(); ++i) {
       if (from[i] >= 0) continue;
@@ -503,7 +630,7 @@ int run_batched(hps_server *S) {
       Job &J = *order[next];
       Group *G = nullptr;
       for (auto &g : S->groups)
-        if (g->h && same_op(*g, J.d) && (int)(g->members.size() + g->pending.size()) < g->cap) {
+        if (g->h && same_op(*g, J) && (int)(g->members.size() + g->pending.size()) < g->cap) {
           G = g.get();
           J.shared_ops = true;
           break;
@@ -558,6 +685,21 @@ int run_batched(hps_server *S) {
         terms.g_param[0] = G.g_param[0];
         terms.g_param[1] = G.g_param[1];
         cudaEventRecord(G.ev[2 * slot], G.st);
+        if (G.with_terms) {  // each member's q and f at its own time, into its column
+          const int64_t ahead = G.enq - G.done;
+          const unsigned nbq = (unsigned)std::min<int64_t>((6 * G.N_int + 255) / 256, 4096);
+          const unsigned nbf = (unsigned)std::min<int64_t>((6 * G.N_bd + 255) / 256, 4096);
+          for (size_t j = 0; j < G.members.size(); ++j) {
+            Job &J = *G.members[j];
+            const double tj = J.d.t0 + (double)(J.done + ahead) * J.d.dt;
+            const int e = J.d.terms(J.d.terms_user, tj, J.d.dt, G.qs, G.fs, (hps_stream_t)G.st);
+            if (e && !J.status) J.status = e;
+            k_put_col<<<nbq, 256, 0, G.st>>>(6 * G.N_int, G.qs, G.Q, G.R, (int)j);
+            if (G.N_bd > 0) k_put_col<<<nbf, 256, 0, G.st>>>(6 * G.N_bd, G.fs, G.F, G.R, (int)j);
+          }
+          terms.q = G.Q;
+          terms.f = G.F;
+        }
         const int e = ark_step_batch(G.h, G.R, G.U, 0.0, 4.0 * G.key.gdt, &terms, G.refine, (hps_stream_t)G.st);
         cudaEventRecord(G.ev[2 * slot + 1], G.st);
         if (e) {
@@ -596,8 +738,13 @@ int hps_server_submit(hps_server *S, const hps_job_desc *d, int *job_id) {
   if (!S || !d || !d->u0 || !d->u_out || d->steps < 0 || !(d->dt > 0.0) || d->g_kind < HPS_G_NONE ||
       d->g_kind > HPS_G_BURGERS || !(d->arrival_s >= 0.0))
     return HPS_EINVAL;
+  int64_t N = 0, N_int = 0, N_bd = 0;
+  if (hps_sizes(&d->tree, d->p, &N, &N_int, &N_bd)) return HPS_EINVAL;
   auto J = std::make_unique<Job>();
   J->d = *d;
+  J->N_int = N_int;
+  J->N_bd = N_bd;
+  job_key(*J);
   if (job_id) *job_id = (int)S->jobs.size();
   S->jobs.push_back(std::move(J));
   return HPS_OK;
@@ -691,8 +838,19 @@ int hps_server_run(hps_server *S) {
         terms.g_kind = J.d.g_kind;
         terms.g_param[0] = J.d.g_param[0];
         terms.g_param[1] = J.d.g_param[1];
+        const double tn = J.d.t0 + J.enq * J.d.dt;
+        if (J.d.terms) {  // q and f of this step, ordered on the job's stream before it
+          if (const int e = J.d.terms(J.d.terms_user, tn, J.d.dt, J.dq, J.df, (hps_stream_t)J.st)) {
+            err = e;
+            J.status = e;
+            J.d.steps = J.enq;  // no further steps: the job ends with its steps in flight
+            break;
+          }
+          terms.q = J.dq;
+          terms.f = J.df;
+        }
         cudaEventRecord(J.ev[2 * slot], J.st);
-        const int e = ark_step(J.h, J.du, J.d.t0 + J.enq * J.d.dt, J.d.dt, &terms, (hps_stream_t)J.st);
+        const int e = ark_step(J.h, J.du, tn, J.d.dt, &terms, (hps_stream_t)J.st);
         cudaEventRecord(J.ev[2 * slot + 1], J.st);
         if (e) {
           err = e;
