@@ -851,12 +851,28 @@ def bench_multi(args, flush):
 # operations the serving stream draws from (leaf grid, p, kind): heat u_t = Lap u (dt = 0.01) or
 # Allen-Cahn u_t = 0.01 Lap u + u - u^3 (dt = 1e-3), spanning leaf grids 8x8 .. 128x128 and p 8 .. 16
 SERVING_CATALOG = ((8, 8, "heat"), (16, 12, "ac"), (32, 16, "heat"), (64, 16, "ac"), (128, 8, "heat"),
-                   (64, 12, "ac"))
+                   (64, 12, "ac"), (32, 12, "varcoef_src"))
+
+
+class _SeparableSource:
+    """q(x, t) = Q(x) cos(t) (Q resident on the device), f = 0: the per-step fill of a served job
+    with variable coefficients, six scaled copies on the job's stream."""
+
+    def __init__(self, Q, c):
+        self.Q, self.c = Q, c
+
+    def __call__(self, t, dt, q, f):
+        import math
+        import torch
+        w = torch.tensor([math.cos(t + cj * dt) for cj in self.c], dtype=torch.float64).to(q.device, non_blocking=True)
+        torch.mul(w[:, None], self.Q[None, :], out=q)
+        f.zero_()
 
 
 def serving_jobs(n_jobs, seed=2026):
     """A seeded Poisson-arrival stream (200 jobs/s) of jobs drawn uniformly from SERVING_CATALOG,
-    10..500 steps each, initial states U[-0.1, 0.1] (zero on the boundary)."""
+    10..500 steps each, initial states U[-0.1, 0.1] (zero on the boundary); 'varcoef_src' jobs have
+    nodal coefficients and a source q = sin(pi x) sin(pi y) cos(t) filled on the device per step."""
     import numpy as np
     from paper_2306_02526_gb300 import hps
     r = np.random.default_rng(seed)
@@ -873,6 +889,16 @@ def serving_jobs(n_jobs, seed=2026):
         if kind == "heat":
             jobs.append(dict(tree=tree, p=p, coef={"a11": 1.0, "a22": 1.0}, dt=0.01, steps=steps, u0=u0,
                              arrival_s=t))
+        elif kind == "varcoef_src":  # nodal coefficients (one seeded field for all such jobs) and a source
+            import torch
+            x, y = hps.hps_coords(tree, p)
+            N_int = hps.hps_sizes(tree, p)[1]
+            xi, yi = x[:N_int], y[:N_int]
+            coef = {"a11": 0.02 * (1.0 + 0.5 * np.sin(3 * xi) * np.cos(2 * yi)), "a22": 0.02 * (1.0 + 0.3 * xi * yi),
+                    "a1": 0.05 * np.cos(yi), "a0": -0.1 + 0.0 * xi}
+            Q = torch.tensor(np.sin(np.pi * xi) * np.sin(np.pi * yi), dtype=torch.float64, device="cuda")
+            jobs.append(dict(tree=tree, p=p, coef=coef, dt=1e-3, steps=steps, u0=u0, g="fisher", g_param=(0.5, 0.0),
+                             arrival_s=t, terms=_SeparableSource(Q, hps.hps_ark_abscissae())))
         else:
             jobs.append(dict(tree=tree, p=p, coef={"a11": 0.01, "a22": 0.01}, dt=1e-3, steps=steps, u0=u0,
                              g="allen_cahn", g_param=(1.0, 0.0), arrival_s=t))

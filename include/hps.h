@@ -136,8 +136,19 @@ enum {
   HPS_G_NONE = 0,
   HPS_G_ALLEN_CAHN = 1, /* g = k0 (u - u^3) */
   HPS_G_FISHER = 2,     /* g = k0 u (1 - u) */
-  HPS_G_BURGERS = 3     /* g = -u (k0 u_x + k1 u_y) */
+  HPS_G_BURGERS = 3,    /* g = -u (k0 u_x + k1 u_y) */
+  HPS_G_USER = 4        /* g from the caller's hook hps_ark_terms.g_fn (ark_step, ark_step_host) */
 };
+
+/* A caller-supplied g (g_kind = HPS_G_USER).  For the value u_j of every stage (device, N doubles
+ * in global order, complete: interior points, shared edges, boundary) the library calls
+ * g_fn(g_user, u_j, g_out, stream) while it enqueues the step; the hook fills g_out (device, N_int
+ * doubles) with g(u_j) at the interior points by work of its own ordered on `stream` (its kernels
+ * or copies), and the step adds dt g_out to the stage's explicit term.  In graph mode the step,
+ * the hook's work included, is recorded on the second call with the same arguments and then
+ * replayed without calling the hook, so the hook must enqueue the same work at every call: g = g(u)
+ * (Sec. 1), no explicit time dependence.  Returns 0, or an error code that the step returns. */
+typedef int (*hps_g_fn)(void *user, const double *u, double *g_out, hps_stream_t stream);
 
 /* Explicit terms of one ARK step.  Stage times t_j = t + c_j dt, j = 1..6 (hps_ark_abscissae).
  *   q: device, 6 * N_int doubles, q(t_j) at interior points, stage-major; NULL means q = 0.
@@ -149,6 +160,8 @@ typedef struct hps_ark_terms {
   const double *f;
   int g_kind;
   double g_param[2];
+  hps_g_fn g_fn;  /* g_kind == HPS_G_USER: the hook (else unused) */
+  void *g_user;   /* passed to g_fn */
 } hps_ark_terms;
 
 /* Abscissae c_1..c_6 of ARK4(3)6L[2]SA (host output, 6 doubles); gamma = 1/4. */
@@ -273,7 +286,7 @@ int hps_solve_batch(hps_handle *h, int R, const double *rhs, const double *f, do
                     hps_stream_t stream);
 
 /* ark_step on R states at once (u: N x R in place; terms->q: 6 x N_int x R, terms->f:
- * 6 x N_bd x R, both stage-major, or NULL).  Each implicit stage uses `refine` FP64 refinement
+ * 6 x N_bd x R, both stage-major, or NULL; g a preset, HPS_G_USER is rejected with HPS_EINVAL).  Each implicit stage uses `refine` FP64 refinement
  * sweeps; the step close solves its identity-operator system directly (HPS_OPT_EDGE_PROJECTION)
  * or, with that option off, by a sweep with `refine` refinement sweeps. */
 int ark_step_batch(hps_handle *h, int R, double *u, double t, double dt, const hps_ark_terms *terms, int refine,

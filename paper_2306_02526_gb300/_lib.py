@@ -11,7 +11,7 @@ c_int64_p = ctypes.POINTER(ctypes.c_int64)
 HPS_OK, HPS_EINVAL, HPS_ENOMEM, HPS_ESINGULAR, HPS_ETIMEOUT, HPS_ECUDA, HPS_EDT, HPS_ESCRATCH = 0, -1, -2, -3, -4, -5, -6, -7
 HPS_COEF_CONST, HPS_COEF_NODAL = 0, 1
 HPS_FLAG_PER_NODE = 1
-HPS_G_NONE, HPS_G_ALLEN_CAHN, HPS_G_FISHER, HPS_G_BURGERS = 0, 1, 2, 3
+HPS_G_NONE, HPS_G_ALLEN_CAHN, HPS_G_FISHER, HPS_G_BURGERS, HPS_G_USER = 0, 1, 2, 3, 4
 KERNELS = ("leaf_up", "merge_up_w3", "merge_up_h", "merge_down", "leaf_down", "leaf_eval", "set_boundary",
            "merge_up_all", "merge_down_all", "residual", "jump", "finish", "close")
 
@@ -30,7 +30,11 @@ class hps_coeffs(ctypes.Structure):
 
 class hps_ark_terms(ctypes.Structure):
     _fields_ = [("q", ctypes.c_void_p), ("f", ctypes.c_void_p), ("g_kind", ctypes.c_int),
-                ("g_param", ctypes.c_double * 2)]
+                ("g_param", ctypes.c_double * 2), ("g_fn", ctypes.c_void_p), ("g_user", ctypes.c_void_p)]
+
+
+# int (*)(void *user, const double *u, double *g_out, hps_stream_t stream)
+G_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 
 
 class hps_job_desc(ctypes.Structure):

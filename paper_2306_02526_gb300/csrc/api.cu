@@ -616,15 +616,33 @@ int solve_enqueue(hps_handle *H, const double *rhs, const double *f, double *u, 
   return hps::sweep(H, H->impl, c, nullptr, u, u, nullptr, st);
 }
 
+// KE += dt G: the caller's g (HPS_G_USER) added to a stage's explicit term
+__global__ void k_add_user_g(int64_t n, double *__restrict__ KE, double dt, const double *__restrict__ G) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    KE[i] = fma(dt, G[i], KE[i]);
+}
+
+// g(u_j) by the caller's hook into H->gbuf (ordered on st), then KE_j += dt g(u_j)
+int user_g_term(hps_handle *H, const hps_ark_terms *terms, const double *uj, double *KE, double dt, cudaStream_t st) {
+  if (int e = terms->g_fn(terms->g_user, uj, H->gbuf, (hps_stream_t)st)) return e;
+  const int64_t n = H->g.N_int;
+  k_add_user_g<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(n, KE, dt, H->gbuf);
+  return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
+}
+
 int ark_enqueue(hps_handle *H, double *u, double dt, const hps_ark_terms *terms, cudaStream_t st) {
   const Tableau &tb = tableau();
-  const int gk = terms ? terms->g_kind : HPS_G_NONE;
+  const bool user_g = terms && terms->g_kind == HPS_G_USER;
+  // the kernels evaluate the presets; the caller's g is added after them
+  const int gk = terms && !user_g ? terms->g_kind : HPS_G_NONE;
   const int64_t ni = H->g.N_int, nbd = H->g.N_bd;
   const double *q = terms ? terms->q : nullptr;
   const double *f = terms ? terms->f : nullptr;
   const double gp0 = terms ? terms->g_param[0] : 0.0, gp1 = terms ? terms->g_param[1] : 0.0;
   // stage 1 (explicit): dt L u^n and dt (q_1 + g(u^n))
   if (int e = hps::leaf_eval(H, u, H->KL, H->KE, q, dt, gk, gp0, gp1, st)) return e;
+  if (user_g)
+    if (int e = user_g_term(H, terms, u, H->KE, dt, st)) return e;
   for (int i = 1; i < 6; ++i) {
     hps::Combo c{};
     add_term(c, u, 1.0);
@@ -643,7 +661,10 @@ int ark_enqueue(hps_handle *H, double *u, double dt, const hps_ark_terms *terms,
     ep.g_kind = gk;
     ep.gp0 = gp0;
     ep.gp1 = gp1;
-    if (int e = hps::sweep(H, H->impl, c, H->R, H->ustage, nullptr, &ep, st)) return e;
+    // (with the caller's g the stage value is completed in ustage -- interior points too -- for the hook)
+    if (int e = hps::sweep(H, H->impl, c, H->R, H->ustage, user_g ? H->ustage : nullptr, &ep, st)) return e;
+    if (user_g)
+      if (int e = user_g_term(H, terms, H->ustage, H->KE + i * ni, dt, st)) return e;
   }
   // step close: ARK combination at interior points, shared-edge values from the identity-operator
   // system (flux continuity), by the edge projection or by an identity-operator sweep
@@ -752,10 +773,14 @@ int ark_step(hps_handle *H, double *u, double t, double dt, const hps_ark_terms 
   if (!H || !u || !(dt > 0.0) || !std::isfinite(t)) return HPS_EINVAL;
   if (std::fabs(0.25 * dt - H->gamma_dt) > 1e-12 * H->gamma_dt) return HPS_EDT;
   const int gk = terms ? terms->g_kind : HPS_G_NONE;
-  if (gk < HPS_G_NONE || gk > HPS_G_BURGERS) return HPS_EINVAL;
+  if (gk < HPS_G_NONE || gk > HPS_G_USER || (gk == HPS_G_USER && !terms->g_fn)) return HPS_EINVAL;
+  if (gk == HPS_G_USER && !H->gbuf && dalloc(H, &H->gbuf, (size_t)H->g.N_int)) return HPS_ENOMEM;
+  // (the hook and its argument stand in the key where a preset's parameters would)
+  const bool user = gk == HPS_G_USER;
   const uint64_t key[hps::GraphEntry::kKey] = {
       (uint64_t)u, (uint64_t)(terms ? terms->q : nullptr), (uint64_t)(terms ? terms->f : nullptr), (uint64_t)gk,
-      bits(terms ? terms->g_param[0] : 0.0), bits(terms ? terms->g_param[1] : 0.0), bits(dt), 1};
+      user ? (uint64_t)terms->g_fn : bits(terms ? terms->g_param[0] : 0.0),
+      user ? (uint64_t)terms->g_user : bits(terms ? terms->g_param[1] : 0.0), bits(dt), 1};
   return run_graphed(H, H->g_ark, key, [&](cudaStream_t s) { return ark_enqueue(H, u, dt, terms, s); },
                      (cudaStream_t)stream);
 }
@@ -892,7 +917,7 @@ int ark_step_batch(hps_handle *H, int R, double *u, double t, double dt, const h
     return HPS_EINVAL;
   if (std::fabs(0.25 * dt - H->gamma_dt) > 1e-12 * H->gamma_dt) return HPS_EDT;
   const int gk = terms ? terms->g_kind : HPS_G_NONE;
-  if (gk < HPS_G_NONE || gk > HPS_G_BURGERS) return HPS_EINVAL;
+  if (gk < HPS_G_NONE || gk > HPS_G_BURGERS) return HPS_EINVAL;  // (no HPS_G_USER on the batched path)
   hps::ArkTable tab;
   const Tableau &tb = tableau();
   std::memcpy(tab.A, tb.A, sizeof(tab.A));

@@ -263,6 +263,7 @@ struct hps_handle {
   hps::OpSet impl, ident;
   // work buffers
   double *ustage = nullptr, *R = nullptr, *KL = nullptr, *KE = nullptr, *wleaf = nullptr;
+  double *gbuf = nullptr;  // N_int: the caller's g of one stage (HPS_G_USER), allocated at first use
   std::vector<double *> h;    // per level: nodes x nb
   std::vector<double *> w3;   // per merge level: nodes x n3
   double *partial = nullptr;  // split-K partial sums of the merge applies

@@ -189,15 +189,50 @@ class HPSSolver:
 
     def ark_step(self, u, t, dt, q=None, f=None, g=None, g_param=(1.0, 1.0), stream=None):
         """One ARK4(3)6L[2]SA step in place on u (ark_step).  q: (6, N_int) stage sources or
-        None; f: (6, N_bd) stage boundary data or None; g: None, 'allen_cahn', 'fisher', 'burgers'."""
+        None; f: (6, N_bd) stage boundary data or None; g: None, 'allen_cahn', 'fisher', 'burgers',
+        or a callable g(u_j, g_out) (HPS_G_USER) on CUDA tensors -- the stage value (N,) and
+        g(u_j) at the interior points (N_int,), to be written in place -- that runs with the
+        step's stream as torch's current stream.  With graphs on (set_graph) the step is recorded
+        with the callable's work and replayed without calling it again: it must then do the same
+        work each time and allocate nothing (out= forms into tensors made beforehand)."""
         terms = _lib.hps_ark_terms()
         terms.q = _dptr(q, 6 * self.N_int, "q")
         terms.f = _dptr(f, 6 * self.N_bd, "f")
-        terms.g_kind = G_KINDS[g]
-        terms.g_param[0], terms.g_param[1] = float(g_param[0]), float(g_param[1])
-        check(lib().ark_step(self._h, _dptr(u, self.N, "u"), float(t), float(dt), ctypes.byref(terms),
-                             _stream_ptr(stream)), "ark_step")
+        if callable(g):
+            terms.g_kind = _lib.HPS_G_USER
+            terms.g_fn = ctypes.cast(self._g_hook(g), ctypes.c_void_p)
+        else:
+            terms.g_kind = G_KINDS[g]
+            terms.g_param[0], terms.g_param[1] = float(g_param[0]), float(g_param[1])
+        rc = lib().ark_step(self._h, _dptr(u, self.N, "u"), float(t), float(dt), ctypes.byref(terms),
+                            _stream_ptr(stream))
+        errs = self.__dict__.setdefault("_hook_errors", [])
+        if errs:
+            e = errs[0]
+            errs.clear()
+            raise e
+        check(rc, "ark_step")
         return u
+
+    def _g_hook(self, fn):
+        """The C hook of a Python g, one per callable (a stable pointer: graph replays match it)."""
+        hooks = self.__dict__.setdefault("_g_hooks", {})
+        if id(fn) not in hooks:
+            N, Ni, errs = self.N, self.N_int, self.__dict__.setdefault("_hook_errors", [])
+
+            def call(user, u, gout, stream):
+                try:
+                    import torch
+                    ut = torch.as_tensor(DeviceArray(u, (N,)), device="cuda")
+                    gt = torch.as_tensor(DeviceArray(gout, (Ni,)), device="cuda")
+                    with torch.cuda.stream(_torch_stream(stream)):
+                        fn(ut, gt)
+                    return 0
+                except Exception as e:  # the step returns an error; ark_step raises this
+                    errs.append(e)
+                    return _lib.HPS_EINVAL
+            hooks[id(fn)] = (fn, _lib.G_FN(call))
+        return hooks[id(fn)][1]
 
     def ark_slope_step(self, u, t, dt, q=None, kbc=None, stream=None):
         """One ARK step in slope form for g = 0 (ark_slope_step) in place on u: q (6, N_int) stage
@@ -331,3 +366,17 @@ class MultiStep:
             self.close()
         except Exception:
             pass
+
+
+def _torch_stream(ptr):
+    """torch's view of a CUDA stream handed over by the library (NULL: the legacy default stream)."""
+    import torch
+    return torch.cuda.ExternalStream(ptr) if ptr else torch.cuda.default_stream()
+
+
+class DeviceArray:
+    """A device buffer of float64 seen through the CUDA array interface (no copy)."""
+
+    def __init__(self, ptr, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8", "data": (int(ptr), False),
+                                         "version": 3, "strides": None}

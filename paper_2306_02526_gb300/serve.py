@@ -15,7 +15,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import check, lib
-from .hps import G_KINDS, Tree, hps_sizes
+from .hps import G_KINDS, DeviceArray, Tree, _torch_stream, hps_sizes
 
 
 class Server:
@@ -73,9 +73,9 @@ class Server:
         def call(user, t, dt, q, f, stream):
             try:
                 import torch
-                qt = torch.as_tensor(_DeviceArray(q, (6, N_int)), device="cuda")
-                ft = torch.as_tensor(_DeviceArray(f, (6, N_bd)), device="cuda")
-                with torch.cuda.stream(torch.cuda.ExternalStream(stream)):
+                qt = torch.as_tensor(DeviceArray(q, (6, N_int)), device="cuda")
+                ft = torch.as_tensor(DeviceArray(f, (6, N_bd)), device="cuda")
+                with torch.cuda.stream(_torch_stream(stream)):
                     fn(t, dt, qt, ft)
                 return 0
             except Exception as e:  # the job ends with this status; the exception is raised by run()
@@ -118,10 +118,3 @@ class Server:
         except Exception:
             pass
 
-
-class _DeviceArray:
-    """A device buffer of float64 seen through the CUDA array interface (no copy)."""
-
-    def __init__(self, ptr, shape):
-        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f8", "data": (int(ptr), False),
-                                         "version": 3, "strides": None}
