@@ -468,6 +468,39 @@ def bench_ours(args, rank, world, local_rank):
 
     rmx = timed_run(S, lambda: mixed_step(U), args, world, local_rank, flush, torch)
     assert torch.isfinite(U).all(), "mixed solution went non-finite"
+
+    # ---- slope form, R states, mixed precision (g = 0: the workload's linear part) ----------------
+    slope_mixed = None
+    if args.only is None and args.groups == 1:
+        Us = torch.tensor(U0, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            S.ark_slope_step_batch(Us, 0.0, wl.dt, refine=2)
+        torch.cuda.synchronize()
+        se = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+        for k in range(10):
+            flush.fill_(float(k))
+            se[k][0].record(stream)
+            S.ark_slope_step_batch(Us, 0.0, wl.dt, refine=2)
+            se[k][1].record(stream)
+        torch.cuda.synchronize()
+        sms = [a.elapsed_time(b) for a, b in se]
+        assert torch.isfinite(Us).all(), "batched slope-form state went non-finite"
+        # one step from the same states against the FP64 slope step, first and last column
+        Us = torch.tensor(U0, dtype=torch.float64, device="cuda")
+        S.ark_slope_step_batch(Us, 0.0, wl.dt, refine=2)
+        serr = 0.0
+        for j in (0, R - 1):
+            v = torch.tensor(np.ascontiguousarray(U0[:, j]), dtype=torch.float64, device="cuda")
+            S.ark_slope_step(v, 0.0, wl.dt)
+            serr = max(serr, float((Us[:, j] - v).abs().max() / v.abs().max()))
+        slope_mixed = {"value": N * STAGES * R * len(sms) / (sum(sms) * 1e-3), "unit": "DOF*stages/s",
+                       "ms_per_step": sum(sms) / len(sms), "steps": len(sms), "rhs": R, "refine": 2,
+                       "err_vs_fp64_slope": serr, "err_columns": [0, R - 1],
+                       "over_fp64_slope": None if not slope else
+                       N * STAGES * R * len(sms) / (sum(sms) * 1e-3) / slope["value"],
+                       "note": "ark_slope_step_batch: FP32 sweeps + 2 FP64 refinement sweeps per slope system "
+                               "(interface rows carry the penalization), CUDA graph replay, L2 flushed before "
+                               "every step"}
     value_mixed = replica_value(world, R * N * STAGES * args.steps, rmx["total_ms"])
     # accuracy: columns 0 and R-1 against the FP64 path run for the same number of steps
     errs = []
@@ -570,6 +603,7 @@ def bench_ours(args, rank, world, local_rank):
             "clocks": head["clocks"],
             "fp64_single_rhs": fp64,
             "fp64_slope_form": slope,
+            "mixed_slope_form": slope_mixed,
             "fp32_single_rhs_solve": None,
             "mixed_over_fp64": value_mixed / value64,
             "build_s": build_s, "wall_s": head["wall"],

@@ -303,6 +303,18 @@ int ark_step_batch(hps_handle *h, int R, double *u, double t, double dt, const h
  * hps_set_persistent); the first call allocates 7 N doubles of work memory. */
 int ark_slope_step(hps_handle *h, double *u, double t, double dt, const hps_ark_terms *terms, hps_stream_t stream);
 
+/* ark_slope_step on R states at once in mixed precision (u: N x R in place; terms->q: 6 x N_int x R
+ * stage sources, terms->f: 6 x N_bd x R slope boundary data (u_t), both stage-major, or NULL;
+ * g_kind HPS_G_NONE): every slope system by FP32 sweeps with `refine` FP64 refinement sweeps
+ * against its collocation residual, interface rows included (their right-hand side is the
+ * penalization's -(flux jump of u^n), carried by the first sweep and by every residual).  Needs
+ * hps_batch_reserve(R) with one column group, at least two leaves; the first call allocates
+ * (7 N + N_bd) x Rmax doubles of slopes.  Agrees with ark_slope_step column by column to the
+ * mixed-precision tolerance (1e-10 with refine = 2 on the tested problems; one sweep leaves about
+ * 1e-10 relative to a state whose flux jumps have decayed). */
+int ark_slope_step_batch(hps_handle *h, int R, double *u, double t, double dt, const hps_ark_terms *terms, int refine,
+                         hps_stream_t stream);
+
 /* ark_step / ark_step_batch on states held in HOST memory: u_host (N, resp. N x R doubles,
  * page-locked for asynchronous copies) is copied into a device buffer the handle keeps, stepped
  * and copied back, all in order on `stream`; terms are device pointers as above.  The first call

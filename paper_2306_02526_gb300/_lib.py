@@ -122,6 +122,9 @@ SIGNATURES = {
                                       ctypes.c_double, ctypes.POINTER(hps_ark_terms), ctypes.c_int, ctypes.c_void_p]),
     "ark_slope_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                       ctypes.POINTER(hps_ark_terms), ctypes.c_void_p]),
+    "ark_slope_step_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_double,
+                                            ctypes.c_double, ctypes.POINTER(hps_ark_terms), ctypes.c_int,
+                                            ctypes.c_void_p]),
     "ark_step_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                      ctypes.POINTER(hps_ark_terms), ctypes.c_void_p]),
     "ark_step_batch_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_double,

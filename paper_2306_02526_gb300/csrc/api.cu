@@ -797,6 +797,25 @@ int ark_slope_step(hps_handle *H, double *u, double t, double dt, const hps_ark_
   return hps::ark_slope(H, u, dt, terms, tab, (cudaStream_t)stream);
 }
 
+int ark_slope_step_batch(hps_handle *H, int R, double *u, double t, double dt, const hps_ark_terms *terms, int refine,
+                         hps_stream_t stream) {
+  if (!H || !u || !(dt > 0.0) || !std::isfinite(t) || R <= 0 || R > H->batch.Rmax || refine < 0 || refine > 8)
+    return HPS_EINVAL;
+  if (std::fabs(0.25 * dt - H->gamma_dt) > 1e-12 * H->gamma_dt) return HPS_EDT;
+  if (terms && terms->g_kind != HPS_G_NONE) return HPS_EINVAL;
+  hps::ArkTable tab;
+  const Tableau &tb = tableau();
+  std::memcpy(tab.A, tb.A, sizeof(tab.A));
+  std::memcpy(tab.Ah, tb.Ah, sizeof(tab.Ah));
+  std::memcpy(tab.b, tb.b, sizeof(tab.b));
+  const uint64_t key[hps::GraphEntry::kKey] = {
+      (uint64_t)u, (uint64_t)(terms ? terms->q : nullptr), (uint64_t)(terms ? terms->f : nullptr),
+      ((uint64_t)R << 8) | ((uint64_t)refine << 24), 0, 0, bits(dt), 4};
+  return run_graphed(H, H->g_ark_b, key,
+                     [&](cudaStream_t s) { return hps::ark_slope_batch(H, R, u, dt, terms, refine, tab, s); },
+                     (cudaStream_t)stream);
+}
+
 // Device buffer of at least n doubles for the host-buffer steps (kept by the handle).
 static int host_stage(hps_handle *H, size_t n) {
   if (H->host_stage_len >= n) return HPS_OK;

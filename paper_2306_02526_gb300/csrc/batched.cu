@@ -2827,6 +2827,30 @@ __global__ void k_b_set_boundary32(GridDims g, int R, float *__restrict__ g32, c
 
 inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// y += a x (n entries)
+__global__ void k_b_axpy(int64_t n, double a, const double *__restrict__ x, double *__restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = fma(a, x[i], y[i]);
+}
+// out[kk R + j] = a f[kk fld + foff + j] for the boundary points kk < n_bd (a scaled copy of one
+// stage of boundary data in the [N_bd][R] layout)
+__global__ void k_b_scale_bd(int64_t n_bd, int R, double a, const double *__restrict__ f, int fld, int foff,
+                             double *__restrict__ out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_bd * R) return;
+  const int64_t kk = idx / R;
+  const int j = (int)(idx % R);
+  out[idx] = a * f[kk * fld + foff + j];
+}
+// out[i] = sum_t c.coef[t] c.ptr[t][i], i < n (out may be a term: same index)
+__global__ void k_b_combine_all(int64_t n, Combo c, double *__restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = c.coef[0] == 1.0 ? c.ptr[0][i] : c.coef[0] * c.ptr[0][i];
+  for (int t = 1; t < c.n; ++t) acc = fma(c.coef[t], c.ptr[t][i], acc);
+  out[i] = acc;
+}
+
 // ---- host orchestration --------------------------------------------------------------------
 __global__ void k_relayout(const double *__restrict__ src, int ld64, int64_t str64, int rows, int cols, int64_t nops,
                            float *__restrict__ dst, int ld32) {
@@ -3356,9 +3380,11 @@ struct BdView {
 
 // Solve A u = [rhs (given by combination `c`, saved to Rsave if non-null); 0; f] with refinement.
 // The last sweep writes the stage epilogue `ep` too where its leaf kernel can (epi_done).
+// J (or null, [N][R] FP64): the interface rows' right-hand side (flux jump of u equal to J instead
+// of 0), taken by the first sweep and added to the shared-edge rows of every residual.
 int refined_solve(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, int R, const Combo &c,
                   double *Rsave, const double *Rb, BdView f, double *u, int refine, double gdt, cudaStream_t st,
-                  const StageEpi &ep, bool &epi_done) {
+                  const StageEpi &ep, bool &epi_done, const double *J = nullptr) {
   const StageEpi none{};
   epi_done = false;
   const GridDims &g = H->g;
@@ -3370,11 +3396,17 @@ int refined_solve(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &
   // the first sweep may take the 3xTF32 tensor-core leaf apply (its rounding is slightly coarser
   // than FP32 and biased); corrections use the FP32 FMA path, so the refined result keeps FP32
   // times FP32 accuracy
-  if (int e = sweep32(H, B, ops, o32, R, c, Rsave, nullptr, UOut{u, 1}, true, st, refine == 0 ? ep : none,
+  if (int e = sweep32(H, B, ops, o32, R, c, Rsave, J, UOut{u, 1}, true, st, refine == 0 ? ep : none,
                       epi_done))
     return e;
   for (int it = 0; it < refine; ++it) {
     if (int e = residual(H, B, R, u, Rb, gdt, st)) return e;
+    if (J) {  // interface rows: J - (flux jump of u)
+      const int64_t n0 = g.N_int * (int64_t)R, n1 = g.N * (int64_t)R;
+      H->trace.begin(kJump, st);
+      k_b_axpy<<<blocks(n1 - n0), 256, 0, st>>>(n1 - n0, 1.0, J + n0, B.r + n0);
+      H->trace.end(kJump, st);
+    }
     H->trace.begin(kSetBoundary, st);
     k_b_set_boundary32<<<blocks(g.N_bd * R), 256, 0, st>>>(g, R, B.g32, nullptr, 0, 0, nullptr);
     H->trace.end(kSetBoundary, st);
@@ -3503,6 +3535,92 @@ int ark_group(hps_handle *H, BatchWork &B, int R, double *u, double dt, const hp
   }
   bool done = false;
   return refined_solve(H, B, H->ident, H->batch.ident32, R, c, B.Rb, B.Rb, fv, u, refine, 0.0, st, StageEpi{}, done);
+}
+
+// One ARK step in slope form (Sec. 3.1, eq. slope0, g = 0) of one group, mixed precision: the
+// slopes times dt, kappa_j = dt k_j ([N][R] each, in W.slope), solve
+//   kappa_1 = dt L u^n + dt q_1                                     (explicit; edges: identity system)
+//   (I - gamma dt L) kappa_i = dt L u^n + sum_{j<i} a_ij dt L kappa_j + dt q_i,   i = 2..6
+// by FP32 sweeps with `refine` FP64 refinement sweeps each, and u^{n+1} = u^n + sum_j b_j kappa_j
+// at every point.  Every slope system's interface rows carry J = -(flux jump of u^n) (the
+// penalization of Sec. 3.1).  Implicit terms are kept times gamma (KL_0 = gamma dt L u^n, KL_j =
+// gamma dt L kappa_j) with their coefficients divided by it, as in ark_group.  Slope boundary data:
+// dt times the caller's u_t values (f, [6][N_bd][fld] from foff), else 0.
+// (q enters the stage combinations, whose terms are [N_int][R] vectors: qld = R, qoff = 0)
+int slope_group(hps_handle *H, BatchWork &W, int R, double *u, double dt, const hps_ark_terms *terms, int qld,
+                int qoff, int fld, int foff, int refine, const ArkTable &tb, cudaStream_t st) {
+  if (qld != R || qoff != 0) return HPS_EINVAL;
+  const GridDims &g = H->g;
+  const int64_t N = g.N, ni = g.N_int * R, nR = N * R;
+  const double *q = terms ? terms->q : nullptr;
+  const double *f = terms ? terms->f : nullptr;
+  const int64_t qstage = g.N_int * (int64_t)qld, fstage = g.N_bd * (int64_t)fld;
+  const double gam = tb.A[1][1];
+  double *kap = W.slope, *J = W.slope + 6 * nR, *fs = J + nR;
+  // interface right-hand side of every slope system: -(flux jump of u^n) (zero elsewhere)
+  if (cudaMemsetAsync(J, 0, nR * sizeof(double), st) != cudaSuccess) return HPS_ECUDA;
+  if (int e = flux_jump_rhs(H, R, u, J, st)) return e;
+  // gamma dt L u^n (KL_0) and dt L kappa_1 (KL_1) by leaf-local differentiation; dt q into KE
+  auto eval = [&](const double *v, double *kl) -> int {
+    Leaf64Args E = leaf64_args(H, kEval, R);
+    E.u = v;
+    E.out0 = kl;
+    E.out1 = W.KE;  // (not used)
+    E.dt = dt;
+    E.dtL = gam * dt;
+    E.g_kind = HPS_G_NONE;
+    return leaf64(H, E, st);
+  };
+  auto bd = [&](int i) -> BdView {  // dt u_t(t + c_i dt) on the boundary, or 0
+    if (!f) return BdView{nullptr, 0, 0};
+    H->trace.begin(kSetBoundary, st);
+    k_b_scale_bd<<<blocks(g.N_bd * R), 256, 0, st>>>(g.N_bd, R, dt, f + i * fstage, fld, foff, fs);
+    H->trace.end(kSetBoundary, st);
+    return BdView{fs, R, 0};
+  };
+  if (int e = eval(u, W.KL)) return e;
+  {  // kappa_1: interior dt (L u^n + q_1), boundary dt u_t, shared edges by the edge projection with J
+    const BdView fv = bd(0);
+    H->trace.begin(kSetBoundary, st);
+    k_b_set_boundary32<<<blocks(g.N_bd * R), 256, 0, st>>>(g, R, W.g32, fv.f, fv.ld, fv.off, kap);
+    H->trace.end(kSetBoundary, st);
+    Combo c{};
+    add_term_b(c, W.KL, 1.0 / gam);
+    if (q) add_term_b(c, q, dt);
+    if (int e = edge_projection_impl(H, R, c, kap, W.r, st, J)) return e;
+    if (int e = eval(kap, W.KL + ni)) return e;
+  }
+  for (int i = 1; i < 6; ++i) {
+    double *ki = kap + i * nR;
+    Combo c{};
+    add_term_b(c, W.KL, 1.0 / gam);
+    if (q) add_term_b(c, q + i * qstage, dt);
+    for (int j = 0; j < i; ++j) add_term_b(c, W.KL + (j + 1) * ni, tb.A[i][j] / gam);
+    // the epilogue keeps gamma dt L kappa_i = kappa_i - R_i (the last one is not needed)
+    double *kl = i < 5 ? W.KL + (i + 1) * ni : nullptr;
+    const StageEpi ep{H->batch.fuse_epilogue ? 1 : 0, W.Rb, kl, W.KE, nullptr, R, 0, HPS_G_NONE, dt, 0.0};
+    bool done = false;
+    if (int e = refined_solve(H, W, H->impl, H->batch.impl32, R, c, W.Rb, W.Rb, bd(i), ki, refine, H->gamma_dt, st,
+                              ep, done, J))
+      return e;
+    if (done || !kl) continue;
+    Leaf64Args P = leaf64_args(H, kEpilogue, R);
+    P.u = ki;
+    P.Rb = W.Rb;
+    P.out0 = kl;
+    P.out1 = W.KE;
+    P.dt = dt;
+    P.g_kind = HPS_G_NONE;
+    if (int e = leaf64(H, P, st)) return e;
+  }
+  // u^{n+1} = u^n + sum_j b_j kappa_j at every point
+  Combo c{};
+  add_term_b(c, u, 1.0);
+  for (int j = 0; j < 6; ++j) add_term_b(c, kap + j * nR, tb.b[j]);
+  H->trace.begin(kFinish, st);
+  k_b_combine_all<<<blocks(nR), 256, 0, st>>>(nR, c, u);
+  H->trace.end(kFinish, st);
+  return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
 // Run `body(group, c0, n, stream)` for every non-empty group: inline on `st` with one group,
@@ -3847,6 +3965,22 @@ int ark_batch(hps_handle *H, int R, double *u, double dt, const hps_ark_terms *t
     }
     return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
   });
+}
+
+// Batched slope-form step (one column group; the first call allocates the slopes, 7 N + N_bd
+// doubles per column).
+int ark_slope_batch(hps_handle *H, int R, double *u, double dt, const hps_ark_terms *terms, int refine,
+                    const ArkTable &tb, cudaStream_t st) {
+  if (R > H->batch.Rmax || H->batch.groups != 1 || !H->d_proj) return HPS_EINVAL;
+  BatchWork &W = H->batch.work[0];
+  const size_t need = (7 * (size_t)H->g.N + (size_t)H->g.N_bd) * H->batch.Rmax;
+  if (W.slope_len < need) {
+    if (W.slope) return HPS_EINVAL;  // reserved for fewer columns: hps_batch_reserve frees and resets it
+    if (cudaMalloc(&W.slope, need * sizeof(double)) != cudaSuccess) return HPS_ENOMEM;
+    H->allocs.push_back(W.slope);
+    W.slope_len = need;
+  }
+  return slope_group(H, W, R, u, dt, terms, R, 0, R, 0, refine, tb, st);
 }
 
 }  // namespace hps

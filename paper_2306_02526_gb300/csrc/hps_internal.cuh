@@ -149,6 +149,8 @@ struct BatchWork {
   cudaStream_t stream = nullptr;   // grouped calls: the group's own stream
   cudaEvent_t done = nullptr;
   cudaEvent_t first = nullptr;     // grouped ARK steps: the explicit first stage is done
+  double *slope = nullptr;         // batched slope form: kappa_1..6, J ([N][R] each), scaled f ([N_bd][R])
+  size_t slope_len = 0;            // doubles
 };
 
 // The batched path: FP32 operator copies (shared by all groups) and G column groups.  With
@@ -351,6 +353,8 @@ struct ArkTable {
 };
 // one ARK step in slope form (g = 0), FP64, single state (slope.cu)
 int ark_slope(hps_handle *H, double *u, double dt, const hps_ark_terms *terms, const ArkTable &tb, cudaStream_t st);
+int ark_slope_batch(hps_handle *H, int R, double *u, double dt, const hps_ark_terms *terms, int refine,
+                    const ArkTable &tb, cudaStream_t st);
 int ark_batch(hps_handle *H, int R, double *u, double dt, const hps_ark_terms *terms, int refine, const ArkTable &tb,
               cudaStream_t st);
 int leaf_eval(hps_handle *H, const double *u, double *KL, double *KE, const double *q, double dt,

@@ -311,6 +311,18 @@ class HPSSolver:
                                    int(refine), _stream_ptr(stream)), "ark_step_batch")
         return u
 
+    def ark_slope_step_batch(self, u, t, dt, q=None, kbc=None, refine=2, stream=None):
+        """ark_slope_step on R states u (N, R) in place, mixed precision (ark_slope_step_batch):
+        q (6, N_int, R) stage sources, kbc (6, N_bd, R) slope boundary data (u_t), or None."""
+        R = u.shape[1]
+        terms = _lib.hps_ark_terms()
+        terms.q = _dptr(q, 6 * self.N_int * R, "q")
+        terms.f = _dptr(kbc, 6 * self.N_bd * R, "kbc")
+        terms.g_kind = G_KINDS[None]
+        check(lib().ark_slope_step_batch(self._h, R, _dptr(u, self.N * R, "u"), float(t), float(dt),
+                                         ctypes.byref(terms), int(refine), _stream_ptr(stream)), "ark_slope_step_batch")
+        return u
+
     def ark_step_batch_host(self, u_host, t, dt, q=None, f=None, g=None, g_param=(1.0, 1.0), refine=2, stream=None):
         """ark_step_batch on R states in host memory (ark_step_batch_host): u_host (N, R) float64
         CPU tensor (pin_memory() for asynchronous copies), updated once the stream is done."""
