@@ -416,7 +416,11 @@ enum {
                                    memory (default 3; 0: one CTA per leaf)                          */
   HPS_OPT_STREAM_CHUNK_KB = 28,  /* their copies: whole operator columns of about this many KB
                                    (2..64, default 24)                                              */
-  HPS_OPT_COUNT = 29
+  HPS_OPT_SUB_LEVELS = 29,       /* D = 2..6: the lowest D merge levels of every upward sweep in one
+                                   launch, one CTA per (subtree, 8 columns), the h of the levels
+                                   inside a subtree kept in shared memory (0: one launch per level
+                                   and operator; default 0)                                         */
+  HPS_OPT_COUNT = 30
 };
 int hps_batch_set_option(hps_handle *h, int opt, int value);
 

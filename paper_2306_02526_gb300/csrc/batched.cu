@@ -2075,6 +2075,115 @@ __global__ void __launch_bounds__(kBT) k_b_gemv2(BPlan2 P, const float *__restri
 
 constexpr size_t kB2MaxSmem = 160 * 1024;
 
+// ---- the lowest merge levels of the upward sweep fused per subtree --------------------------
+// One CTA per (subtree rooted at level lb, group of up to 8 columns) runs levels lb + D - 1 (the
+// deepest) up to lb: per level, d = h^b_3 - h^a_3 (+ interface right-hand side) of each of the
+// subtree's nodes, w3 = X d (written to global memory: the downward sweep needs it) and
+// h = [h^a_1; h^b_2] + Tcat w3.  The children's h of the deepest level come from the leaf
+// kernel; the h of the levels inside the subtree stay in shared memory, and the top level's h goes
+// to global memory for the levels above.  Sums over K run in order (one output per thread), so the
+// result differs from the per-level kernels' in the order of FP32 rounding only.
+constexpr int kSubMaxLevels = 6;
+constexpr int kSubCols = 8;
+
+struct SubLevel {
+  float *w3;               // [node][n3][R]
+  const float *X, *T;      // transposed operators (column c at + c ld), per node at + k str
+  int ldX, ldT;
+  int64_t strX, strT;
+  const int *hsrc;         // [nb]: parent boundary position -> child * nbc + position
+  const int *origin;       // [node][2]
+  int nbc, nb, n3, j3a, j3b, a, c, split;
+};
+struct SubUp {
+  int lb, D, R;
+  const float *hleaf;      // h of the level below the deepest fused one: [node][nbc][R]
+  float *htop;             // h of level lb: [node][nb][R] (null when lb is the root)
+  const double *jump;      // interface right-hand side ([N][R] FP64) or null
+  GridDims g;
+  SubLevel lv[kSubMaxLevels];  // lv[i]: level lb + i
+};
+
+inline size_t sub_smem_floats(const SubUp &P) {
+  size_t hmax = 0, dmax = 0;
+  for (int i = 0; i < P.D; ++i) {
+    const SubLevel &L = P.lv[i];
+    hmax = std::max(hmax, (size_t)(1 << i) * L.nb * kSubCols);
+    dmax = std::max(dmax, (size_t)(1 << i) * L.n3 * kSubCols);
+  }
+  return 2 * hmax + 2 * dmax;  // h of two consecutive levels, d and w3 of one
+}
+
+__global__ void __launch_bounds__(kBT) k_b_up_sub(SubUp P) {
+  extern __shared__ float smu[];
+  size_t hmax = 0, dmax = 0;
+  for (int i = 0; i < P.D; ++i) {
+    hmax = max(hmax, (size_t)(1 << i) * P.lv[i].nb * kSubCols);
+    dmax = max(dmax, (size_t)(1 << i) * P.lv[i].n3 * kSubCols);
+  }
+  float *hbuf[2] = {smu, smu + hmax}, *ds = smu + 2 * hmax, *ws = ds + dmax;
+  const int s = blockIdx.x, j0 = blockIdx.y * kSubCols, RC = min(kSubCols, P.R - j0);
+  const float *hin = nullptr;  // children's h in shared memory ([local child][nbc][kSubCols]), or null: global
+  for (int i = P.D - 1; i >= 0; --i) {
+    const SubLevel &L = P.lv[i];
+    const int nn = 1 << i, k0 = s << i, n3 = L.n3, nb = L.nb, nbc = L.nbc;
+    // d of the nn nodes: [kk][cc][jj]
+    for (int idx = threadIdx.x; idx < nn * n3 * kSubCols; idx += blockDim.x) {
+      const int jj = idx % kSubCols, rest = idx / kSubCols, cc = rest % n3, kk = rest / n3;
+      float v = 0.f;
+      if (jj < RC) {
+        const int k = k0 + kk;
+        if (hin) {
+          v = hin[((2 * kk + 1) * nbc + L.j3b + cc) * kSubCols + jj] - hin[((2 * kk) * nbc + L.j3a + cc) * kSubCols + jj];
+        } else {
+          const float *hb = P.hleaf + ((int64_t)(2 * k + 1) * nbc + L.j3b + cc) * P.R + j0 + jj;
+          const float *ha = P.hleaf + ((int64_t)(2 * k) * nbc + L.j3a + cc) * P.R + j0 + jj;
+          v = *hb - *ha;
+        }
+        if (P.jump)
+          v += d2f_int(P.jump[iface_bd(P.g, L.origin[2 * k], L.origin[2 * k + 1], L.a, L.c, L.split, cc) * P.R + j0 + jj]);
+      }
+      ds[idx] = v;
+    }
+    __syncthreads();
+    // w3 = X d, to shared memory and to global memory
+    for (int idx = threadIdx.x; idx < nn * n3 * kSubCols; idx += blockDim.x) {
+      const int jj = idx % kSubCols, rest = idx / kSubCols, r = rest % n3, kk = rest / n3;
+      const int k = k0 + kk;
+      const float *x = L.X + (int64_t)k * L.strX + r;
+      const float *d = ds + (size_t)kk * n3 * kSubCols + jj;
+      float acc = 0.f;
+      for (int c2 = 0; c2 < n3; ++c2) acc = fmaf(x[(int64_t)c2 * L.ldX], d[c2 * kSubCols], acc);
+      ws[idx] = acc;
+      if (jj < RC) L.w3[((int64_t)k * n3 + r) * P.R + j0 + jj] = acc;
+    }
+    __syncthreads();
+    // h = [h^a_1; h^b_2] + Tcat w3, in shared memory (the top level: global memory)
+    const bool top = i == 0;
+    if (!top || P.htop) {
+      float *hout = hbuf[i & 1];
+      for (int idx = threadIdx.x; idx < nn * nb * kSubCols; idx += blockDim.x) {
+        const int jj = idx % kSubCols, rest = idx / kSubCols, r = rest % nb, kk = rest / nb;
+        const int k = k0 + kk, src = L.hsrc[r];  // child * nbc + position, child 0 or 1
+        float acc;
+        if (hin) acc = hin[((size_t)(2 * kk) * nbc + src) * kSubCols + jj];
+        else acc = jj < RC ? P.hleaf[((int64_t)(2 * k) * nbc + src) * P.R + j0 + jj] : 0.f;
+        const float *t = L.T + (int64_t)k * L.strT + r;
+        const float *w = ws + (size_t)kk * n3 * kSubCols + jj;
+        for (int c2 = 0; c2 < n3; ++c2) acc = fmaf(t[(int64_t)c2 * L.ldT], w[c2 * kSubCols], acc);
+        if (top) {
+          if (jj < RC) P.htop[((int64_t)k * nb + r) * P.R + j0 + jj] = acc;
+        } else {
+          hout[idx] = acc;
+        }
+      }
+      hin = hout;
+    }
+    __syncthreads();
+  }
+}
+
+
 // One merge apply of a level: the cluster split-K kernel, or (handle option, or when its K chunk
 // does not fit in shared memory) the split-K kernel with partial sums in global memory.
 template <class XL, class EP>
@@ -3188,7 +3297,55 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
     FA.seg0[nflow] = nflags;
     if (int e = flow_launch(H, B, FA, true, smem_up, nflags, st)) return e;
   }
-  for (int l = lr - 1; l >= 0; --l) {
+  // the lowest levels fused per subtree (option): levels [lb, lr)
+  int lup = lr;
+  if (H->batch.sub_levels > 0 && nflow == 0) {
+    const int D = std::min({H->batch.sub_levels, lr, kSubMaxLevels});
+    const int lb = lr - D;
+    const int cg = (R + kSubCols - 1) / kSubCols;
+    if (D >= 2) {
+      SubUp P{};
+      P.lb = lb;
+      P.D = D;
+      P.R = R;
+      P.hleaf = B.h32[lr];
+      P.htop = lb > 0 ? B.h32[lb] : nullptr;
+      P.jump = jump;
+      P.g = H->g;
+      for (int i = 0; i < D; ++i) {
+        const int l = lb + i;
+        const Level &lv = H->lev[l];
+        SubLevel &S = P.lv[i];
+        S.w3 = B.w332[l];
+        S.X = o32.X[l].p;
+        S.ldX = o32.X[l].ld;
+        S.strX = o32.X[l].str;
+        S.T = o32.Tcat[l].p;
+        S.ldT = o32.Tcat[l].ld;
+        S.strT = o32.Tcat[l].str;
+        S.hsrc = lv.d_hsrc;
+        S.origin = lv.d_origin;
+        S.nbc = lv.nbc;
+        S.nb = lv.nb;
+        S.n3 = lv.n3;
+        S.j3a = lv.j3a;
+        S.j3b = lv.j3b;
+        S.a = lv.a;
+        S.c = lv.c;
+        S.split = lv.split;
+      }
+      const size_t smem = sub_smem_floats(P) * sizeof(float);
+      if (smem <= 96 * 1024) {
+        if (int e_ = smem_optin((const void *)k_b_up_sub, smem)) return e_;
+        H->trace.begin(kMergeUpW3, st);
+        k_b_up_sub<<<dim3((unsigned)H->lev[lb].nodes, (unsigned)cg), kBT, smem, st>>>(P);
+        H->trace.end(kMergeUpW3, st);
+        if (cudaPeekAtLastError() != cudaSuccess) return HPS_ECUDA;
+        lup = lb;
+      }
+    }
+  }
+  for (int l = lup - 1; l >= 0; --l) {
     const Level &lv = H->lev[l];
     if (int e = launch_b2(H, B, kMergeUpW3, lv.n3, lv.n3, lv.nodes, R, o32.X[l].p, o32.X[l].ld, o32.X[l].str,
                           BXDiff{B.h32[l + 1], lv.nbc, lv.j3a, lv.j3b, R, jump, H->g, lv.d_origin, lv.a, lv.c, lv.split},
@@ -3766,6 +3923,7 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
     case HPS_OPT_ONE_COLUMN_SUM: flag = &Bt.one_column_merge_sum; break;
     case HPS_OPT_STREAM_LEAF: field = &Bt.stream_leaf; break;
     case HPS_OPT_STREAM_CHUNK_KB: field = &Bt.stream_chunk_kb; break;
+    case HPS_OPT_SUB_LEVELS: field = &Bt.sub_levels; break;
     case HPS_OPT_EVEN_ODD: flag = &Bt.even_odd; break;
     case HPS_OPT_FLOW_LEVELS: field = &Bt.flow_levels; break;
     case HPS_OPT_FLOW_N3_MAX: field = &Bt.flow_n3_max; break;
@@ -3804,6 +3962,7 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
   if (opt == HPS_OPT_UMMA_LEAF && v > 3) return HPS_EINVAL;
   if (opt == HPS_OPT_STREAM_LEAF && v > 4) return HPS_EINVAL;
   if (opt == HPS_OPT_STREAM_CHUNK_KB && (v < 2 || v > 64)) return HPS_EINVAL;
+  if (opt == HPS_OPT_SUB_LEVELS && v > kSubMaxLevels) return HPS_EINVAL;
   if (opt == HPS_OPT_UMMA_LEAF && v == 3)
     if (int e = umma_bf16_reserve(H)) return e;
   if (opt == HPS_OPT_FP64_PLAN_TARGET) {  // FP64 split plans: not while the persistent kernel holds tasks

@@ -190,6 +190,7 @@ struct Batch {
   bool one_column_merge_sum = true; // ... and their split-K sums by the last CTA (else k_b_reduce)
   int stream_leaf = 3;       // one to four columns: leaf operators streamed by bulk copies, CTAs per SM (0: off)
   int stream_chunk_kb = 24;  // ... in chunks of about this many KB
+  int sub_levels = 0;        // lowest merge levels of the upward sweep fused per subtree (0: per level)
   void *ainv_bf = nullptr;       // BF16 trial: their BF16 copy, K-major [leaf][row][round8(q)]
   uint64_t ainv_map_bf[16] = {}; // its TMA tensor map
   OpSet32 impl32, ident32;
