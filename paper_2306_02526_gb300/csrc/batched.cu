@@ -2104,44 +2104,48 @@ struct SubUp {
   SubLevel lv[kSubMaxLevels];  // lv[i]: level lb + i
 };
 
-inline size_t sub_smem_floats(const SubUp &P) {
-  size_t hmax = 0, dmax = 0;
-  for (int i = 0; i < P.D; ++i) {
-    const SubLevel &L = P.lv[i];
-    hmax = std::max(hmax, (size_t)(1 << i) * L.nb * kSubCols);
-    dmax = std::max(dmax, (size_t)(1 << i) * L.n3 * kSubCols);
-  }
-  return 2 * hmax + 2 * dmax;  // h of two consecutive levels, d and w3 of one
+// shared memory: two h buffers (the first takes the staged children's h of the deepest level,
+// then the two alternate between levels) and the d / w3 pair of one level
+inline size_t sub_buf_floats(const SubUp &P) {
+  size_t hmax = (size_t)(2 << (P.D - 1)) * P.lv[P.D - 1].nbc * kSubCols;  // staged children
+  for (int i = 0; i < P.D; ++i) hmax = std::max(hmax, (size_t)(1 << i) * P.lv[i].nb * kSubCols);
+  return hmax;
 }
+inline size_t sub_dbuf_floats(const SubUp &P) {
+  size_t dmax = 0;
+  for (int i = 0; i < P.D; ++i) dmax = std::max(dmax, (size_t)(1 << i) * P.lv[i].n3 * kSubCols);
+  return dmax;
+}
+inline size_t sub_smem_floats(const SubUp &P) { return 2 * sub_buf_floats(P) + 2 * sub_dbuf_floats(P); }
 
-__global__ void __launch_bounds__(kBT) k_b_up_sub(SubUp P) {
-  extern __shared__ float smu[];
-  size_t hmax = 0, dmax = 0;
-  for (int i = 0; i < P.D; ++i) {
-    hmax = max(hmax, (size_t)(1 << i) * P.lv[i].nb * kSubCols);
-    dmax = max(dmax, (size_t)(1 << i) * P.lv[i].n3 * kSubCols);
-  }
-  float *hbuf[2] = {smu, smu + hmax}, *ds = smu + 2 * hmax, *ws = ds + dmax;
+__global__ void __launch_bounds__(kBT) k_b_up_sub(SubUp P, int hmax, int dmax) {
+  extern __shared__ __align__(16) float smu[];
+  float *buf0 = smu, *buf1 = smu + hmax, *ds = smu + 2 * hmax, *ws = ds + dmax;
   const int s = blockIdx.x, j0 = blockIdx.y * kSubCols, RC = min(kSubCols, P.R - j0);
-  const float *hin = nullptr;  // children's h in shared memory ([local child][nbc][kSubCols]), or null: global
+  // the children's h of the deepest fused level: 2^D nodes from node s 2^D of the level below
+  {
+    const int nbc = P.lv[P.D - 1].nbc, nch = 2 << (P.D - 1);
+    const int64_t c0 = (int64_t)s * nch;
+    block_gather<8, float>(
+        nch * nbc * kSubCols,
+        [&](int idx) {
+          const int jj = idx % kSubCols, row = idx / kSubCols;  // row = child * nbc + position
+          return jj < RC ? P.hleaf[(c0 * nbc + row) * P.R + j0 + jj] : 0.f;
+        },
+        [&](int idx, float v) { buf0[idx] = v; });
+  }
+  __syncthreads();
+  const float *hin = buf0;
   for (int i = P.D - 1; i >= 0; --i) {
     const SubLevel &L = P.lv[i];
     const int nn = 1 << i, k0 = s << i, n3 = L.n3, nb = L.nb, nbc = L.nbc;
     // d of the nn nodes: [kk][cc][jj]
     for (int idx = threadIdx.x; idx < nn * n3 * kSubCols; idx += blockDim.x) {
       const int jj = idx % kSubCols, rest = idx / kSubCols, cc = rest % n3, kk = rest / n3;
-      float v = 0.f;
-      if (jj < RC) {
+      float v = hin[((2 * kk + 1) * nbc + L.j3b + cc) * kSubCols + jj] - hin[((2 * kk) * nbc + L.j3a + cc) * kSubCols + jj];
+      if (P.jump && jj < RC) {
         const int k = k0 + kk;
-        if (hin) {
-          v = hin[((2 * kk + 1) * nbc + L.j3b + cc) * kSubCols + jj] - hin[((2 * kk) * nbc + L.j3a + cc) * kSubCols + jj];
-        } else {
-          const float *hb = P.hleaf + ((int64_t)(2 * k + 1) * nbc + L.j3b + cc) * P.R + j0 + jj;
-          const float *ha = P.hleaf + ((int64_t)(2 * k) * nbc + L.j3a + cc) * P.R + j0 + jj;
-          v = *hb - *ha;
-        }
-        if (P.jump)
-          v += d2f_int(P.jump[iface_bd(P.g, L.origin[2 * k], L.origin[2 * k + 1], L.a, L.c, L.split, cc) * P.R + j0 + jj]);
+        v += d2f_int(P.jump[iface_bd(P.g, L.origin[2 * k], L.origin[2 * k + 1], L.a, L.c, L.split, cc) * P.R + j0 + jj]);
       }
       ds[idx] = v;
     }
@@ -2151,38 +2155,37 @@ __global__ void __launch_bounds__(kBT) k_b_up_sub(SubUp P) {
       const int jj = idx % kSubCols, rest = idx / kSubCols, r = rest % n3, kk = rest / n3;
       const int k = k0 + kk;
       const float *x = L.X + (int64_t)k * L.strX + r;
-      const float *d = ds + (size_t)kk * n3 * kSubCols + jj;
+      const float *d = ds + kk * n3 * kSubCols + jj;
       float acc = 0.f;
-      for (int c2 = 0; c2 < n3; ++c2) acc = fmaf(x[(int64_t)c2 * L.ldX], d[c2 * kSubCols], acc);
+#pragma unroll 4
+      for (int c2 = 0; c2 < n3; ++c2) acc = fmaf(__ldg(x + (int64_t)c2 * L.ldX), d[c2 * kSubCols], acc);
       ws[idx] = acc;
       if (jj < RC) L.w3[((int64_t)k * n3 + r) * P.R + j0 + jj] = acc;
     }
     __syncthreads();
-    // h = [h^a_1; h^b_2] + Tcat w3, in shared memory (the top level: global memory)
+    // h = [h^a_1; h^b_2] + Tcat w3 into the other buffer (the top level: global memory)
     const bool top = i == 0;
+    float *hout = hin == buf0 ? buf1 : buf0;
     if (!top || P.htop) {
-      float *hout = hbuf[i & 1];
       for (int idx = threadIdx.x; idx < nn * nb * kSubCols; idx += blockDim.x) {
         const int jj = idx % kSubCols, rest = idx / kSubCols, r = rest % nb, kk = rest / nb;
-        const int k = k0 + kk, src = L.hsrc[r];  // child * nbc + position, child 0 or 1
-        float acc;
-        if (hin) acc = hin[((size_t)(2 * kk) * nbc + src) * kSubCols + jj];
-        else acc = jj < RC ? P.hleaf[((int64_t)(2 * k) * nbc + src) * P.R + j0 + jj] : 0.f;
+        const int k = k0 + kk, src = __ldg(L.hsrc + r);  // child * nbc + position, child 0 or 1
+        float acc = hin[((2 * kk) * nbc + src) * kSubCols + jj];
         const float *t = L.T + (int64_t)k * L.strT + r;
-        const float *w = ws + (size_t)kk * n3 * kSubCols + jj;
-        for (int c2 = 0; c2 < n3; ++c2) acc = fmaf(t[(int64_t)c2 * L.ldT], w[c2 * kSubCols], acc);
+        const float *w = ws + kk * n3 * kSubCols + jj;
+#pragma unroll 4
+        for (int c2 = 0; c2 < n3; ++c2) acc = fmaf(__ldg(t + (int64_t)c2 * L.ldT), w[c2 * kSubCols], acc);
         if (top) {
           if (jj < RC) P.htop[((int64_t)k * nb + r) * P.R + j0 + jj] = acc;
         } else {
           hout[idx] = acc;
         }
       }
-      hin = hout;
     }
+    hin = hout;
     __syncthreads();
   }
 }
-
 
 // One merge apply of a level: the cluster split-K kernel, or (handle option, or when its K chunk
 // does not fit in shared memory) the split-K kernel with partial sums in global memory.
@@ -3338,7 +3341,8 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
       if (smem <= 96 * 1024) {
         if (int e_ = smem_optin((const void *)k_b_up_sub, smem)) return e_;
         H->trace.begin(kMergeUpW3, st);
-        k_b_up_sub<<<dim3((unsigned)H->lev[lb].nodes, (unsigned)cg), kBT, smem, st>>>(P);
+        k_b_up_sub<<<dim3((unsigned)H->lev[lb].nodes, (unsigned)cg), kBT, smem, st>>>(P, (int)sub_buf_floats(P),
+                                                                                    (int)sub_dbuf_floats(P));
         H->trace.end(kMergeUpW3, st);
         if (cudaPeekAtLastError() != cudaSuccess) return HPS_ECUDA;
         lup = lb;
