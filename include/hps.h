@@ -420,7 +420,11 @@ enum {
                                    launch, one CTA per (subtree, 8 columns), the h of the levels
                                    inside a subtree kept in shared memory (0: one launch per level
                                    and operator; default 0)                                         */
-  HPS_OPT_COUNT = 30
+  HPS_OPT_PDL = 30,              /* 1: the merge applies and their split-K sums launched as
+                                   programmatic dependents (griddepcontrol): each starts its
+                                   operator loads while the kernel before it finishes and waits for
+                                   its results in the kernel (0: ordinary launches)                */
+  HPS_OPT_COUNT = 31
 };
 int hps_batch_set_option(hps_handle *h, int opt, int value);
 

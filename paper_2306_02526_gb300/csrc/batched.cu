@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cooperative_groups.h>
 #include <cstdlib>
+#include <utility>
 
 #include "hps_internal.cuh"
 #include "tc5.cuh"
@@ -175,6 +176,14 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization may
+// start while the previous kernel in the stream finishes; pdl_wait blocks until that kernel has
+// completed and its memory operations are visible, so everything before it may only read data no
+// kernel of the step writes (the operators).  pdl_trigger lets the next such kernel be scheduled
+// once every CTA of this grid has started.  Both are no-ops without that launch attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // The stage right-hand side of one leaf, sum_t coef_t ptr_t, over its nq = q*R contiguous
 // entries from offset `off` (FP64): saved to Rsave if non-null and staged as FP32 at
@@ -1436,6 +1445,24 @@ int launch_stream(hps_handle *H, const StreamPlan &P, int cps, const float *A, c
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
+// Launch with programmatic stream serialization when `pdl` (the kernel must call pdl_wait before
+// it touches data of earlier kernels), else an ordinary launch.
+template <class... KArgs, class... Args>
+cudaError_t launch_k(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     Args &&...args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? at : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 // ---- merge applies (FP32, R columns) -------------------------------------------------------
 struct BPlan {
   int M, K, nodes, R, Rp, TC, MQ, CG;
@@ -1669,6 +1696,7 @@ __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict
                  AT + (int64_t)(node0 + t) * str + (int64_t)(c0 + c) * ld + rlo + 4 * qq);
     }
   }
+  pdl_wait();  // (the operator tile is in flight; the vector is the previous kernel's output)
   {  // vector chunk [nn][klen][Rp], four columns per load (row addresses once per 4 columns)
     const int Rq = Rp / 4, n4 = nn * klen * Rq;
     const bool pow2 = (Rq & (Rq - 1)) == 0;
@@ -1714,6 +1742,7 @@ __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict
   if (live)
     smem_fma<TC>(acc, As + (size_t)(P.shared_op ? 0 : lo) * klen * trows + (r0 - rlo), trows, klen,
                  xs + (int64_t)lo * klen * Rp + j0, Rp);
+  pdl_trigger();  // the products are done: the next kernel may take the SMs this grid frees
   const int k = node0 + lo;
   if (live)
 #pragma unroll
@@ -1760,6 +1789,8 @@ __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict
 // Sum of the split-K partials in chunk order, four columns per thread.
 template <class EP>
 __global__ void k_b_reduce(BPlan P, const float *__restrict__ partial, EP ep) {
+  pdl_trigger();
+  pdl_wait();
   const int Rq = P.Rp / 4;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P.nodes * P.M * Rq) return;
@@ -1792,15 +1823,13 @@ int launch_b(hps_handle *H, BatchWork &B, int slot, const BPlan &P, const float 
   const bool in_kernel = P.ksplit <= H->batch.last_cta_max_split &&
                          (size_t)P.node_groups * P.row_tiles <= B.tile_count_len;
   unsigned *tc = in_kernel ? B.tile_count : nullptr;
-  if (P.TC == 8)
-    k_b_gemv<8, XL, EP><<<grid, kBT, smem, st>>>(P, AT, ld, str, xl, ep, B.partial32, tc);
-  else if (P.TC == 4)
-    k_b_gemv<4, XL, EP><<<grid, kBT, smem, st>>>(P, AT, ld, str, xl, ep, B.partial32, tc);
-  else
-    k_b_gemv<2, XL, EP><<<grid, kBT, smem, st>>>(P, AT, ld, str, xl, ep, B.partial32, tc);
+  const bool pdl = H->batch.pdl;
+  auto kern = P.TC == 8 ? k_b_gemv<8, XL, EP> : P.TC == 4 ? k_b_gemv<4, XL, EP> : k_b_gemv<2, XL, EP>;
+  launch_k(pdl, kern, grid, dim3(kBT), smem, st, P, AT, ld, str, xl, ep, B.partial32, tc);
   if (P.ksplit > 1 && !in_kernel) {
     const int64_t n = (int64_t)P.nodes * P.M * (P.Rp / 4);
-    k_b_reduce<EP><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P, B.partial32, ep);
+    launch_k(pdl, k_b_reduce<EP>, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, P,
+             (const float *)B.partial32, ep);
   }
   H->trace.end(slot, st);
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
@@ -1860,10 +1889,13 @@ __global__ void __launch_bounds__(kBT) k_b_gemv1(BPlan1 P, const float *__restri
   constexpr int kU = 8;  // operator loads in flight per thread
   float4 av[kU];
   int c = c0 + wk;
-  // the first operator loads go out before the vector staging, so their latency overlaps it
+  // the first operator loads go out before the vector staging, so their latency overlaps it (and,
+  // launched dependently, the previous kernel's tail)
+  pdl_trigger();
 #pragma unroll
   for (int u = 0; u < kU; ++u)
     if (live && c + u * step < c1) av[u] = __ldg(reinterpret_cast<const float4 *>(a + (int64_t)(c + u * step) * ld));
+  pdl_wait();
   for (int i = threadIdx.x; i < (n1 - n0 + 1) * klen; i += blockDim.x) {
     const int nn = i / klen, cc = i - nn * klen;
     xs1[i] = xl(n0 + nn, c0 + cc, 0);
@@ -1957,7 +1989,8 @@ int launch_b1(hps_handle *H, BatchWork &B, int slot, int M, int K, int nodes, co
   if (int e_ = smem_optin((const void *)k_b_gemv1<XL, EP>, smem)) return e_;
   *done = true;
   H->trace.begin(slot, st);
-  k_b_gemv1<XL, EP><<<dim3((unsigned)gx, (unsigned)P.ks), kBT, smem, st>>>(P, AT, ld, str, xl, ep, B.partial32, tc);
+  launch_k(H->batch.pdl, k_b_gemv1<XL, EP>, dim3((unsigned)gx, (unsigned)P.ks), dim3(kBT), smem, st, P, AT, ld, str, xl,
+           ep, B.partial32, tc);
   if (P.ks > 1 && !tc) {
     BPlan R4{};
     R4.M = M;
@@ -1967,7 +2000,8 @@ int launch_b1(hps_handle *H, BatchWork &B, int slot, int M, int K, int nodes, co
     R4.Rp = 4;
     R4.ksplit = P.ks;
     const int64_t n = (int64_t)nodes * M;
-    k_b_reduce<EP><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(R4, B.partial32, ep);
+    launch_k(H->batch.pdl, k_b_reduce<EP>, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, R4,
+             (const float *)B.partial32, ep);
   }
   H->trace.end(slot, st);
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
@@ -3928,6 +3962,7 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
     case HPS_OPT_STREAM_LEAF: field = &Bt.stream_leaf; break;
     case HPS_OPT_STREAM_CHUNK_KB: field = &Bt.stream_chunk_kb; break;
     case HPS_OPT_SUB_LEVELS: field = &Bt.sub_levels; break;
+    case HPS_OPT_PDL: flag = &Bt.pdl; break;
     case HPS_OPT_EVEN_ODD: flag = &Bt.even_odd; break;
     case HPS_OPT_FLOW_LEVELS: field = &Bt.flow_levels; break;
     case HPS_OPT_FLOW_N3_MAX: field = &Bt.flow_n3_max; break;

@@ -191,6 +191,7 @@ struct Batch {
   int stream_leaf = 3;       // one to four columns: leaf operators streamed by bulk copies, CTAs per SM (0: off)
   int stream_chunk_kb = 24;  // ... in chunks of about this many KB
   int sub_levels = 0;        // lowest merge levels of the upward sweep fused per subtree (0: per level)
+  bool pdl = false;          // merge applies launched as programmatic dependents of the kernel before
   void *ainv_bf = nullptr;       // BF16 trial: their BF16 copy, K-major [leaf][row][round8(q)]
   uint64_t ainv_map_bf[16] = {}; // its TMA tensor map
   OpSet32 impl32, ident32;

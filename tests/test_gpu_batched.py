@@ -306,7 +306,7 @@ def _ark_pair(torch, n1, n2, p, R, dt, opt=None, val=None, autotune=False):
                                      ("fuse_jump", 0), ("fold_scale", 0), ("sa_close", 0),
                                      ("edge_projection", 0), ("eo_cols", 5), ("eo_cols", 8),
                                      ("tile_cols_down", 4), ("tile_cols_h", 8), ("sub_levels", 3),
-                                     ("sub_levels", 6)])
+                                     ("sub_levels", 6), ("pdl", 1)])
 def test_batch_option_variants_match_fp64(opt, val):
     """Every kernel variant of the batched path (handle options) gives the FP64 result to the
     mixed-precision tolerance; flow_levels = 8 puts every level of the 16 x 8 tree, root

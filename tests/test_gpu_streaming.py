@@ -20,7 +20,8 @@ VARIANTS = [dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=1, one_colu
             dict(stream_leaf=2, stream_chunk_kb=64, one_column_merge=1, one_column_sum=1),
             dict(stream_leaf=0, stream_chunk_kb=24, one_column_merge=1, one_column_sum=1),
             dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=1, one_column_sum=0),
-            dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=0, one_column_sum=0)]
+            dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=0, one_column_sum=0),
+            dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=1, one_column_sum=1, pdl=1)]
 
 
 def _nodal_solver(torch, n1, n2, p, gdt, seed=0):
