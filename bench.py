@@ -261,6 +261,36 @@ def residual_flops(p, first, flux=True):
             (2 * m * (4 * h + 2) if flux else 0))
 
 
+def step_flops(n1, n2, p, R, refine, first, nstages=5):
+    """Algorithmic flops of one batched mixed-precision ARK step (constant coefficients, edge-
+    projection close), split by pipe.  FP64: the collocation residual of every refinement sweep
+    (residual_flops), the explicit first-stage evaluation of L u^n and g (the residual's line sums
+    without flux terms, plus 6 flops per point), the stage right-hand sides (2 flops per term after
+    the leading u^n: 2 (i - 1) terms for stage i), the stage epilogue (6 flops per point: dt L U_i
+    from the stage equation, dt g), the corrections u += du (1 per point and sweep) and the close
+    (u + 6 explicit terms: 12 flops per point).  FP32: per sweep the fast-diagonalization leaf
+    apply (8 m^3 per leaf), the leaf solve (2 q b per leaf) and the merge applies (2 n3^2 +
+    2 nb n3 + 2 n3 nb per node, the root without h), all times R."""
+    m = p - 2
+    q, b = m * m, 4 * m
+    leaves = n1 * n2
+    n_int = leaves * q
+    cols = leaves * R
+    res = residual_flops(p, first, True)
+    fp64 = (nstages * refine * cols * res
+            + cols * (residual_flops(p, first, False) + 6 * q)
+            + sum(2 * 2 * (i - 1) for i in range(2, nstages + 2)) * n_int * R
+            + 6 * nstages * n_int * R
+            + nstages * refine * n_int * R
+            + 12 * n_int * R)
+    lv = tree_levels(n1, n2, m)
+    merge = sum(nodes * (2 * n3 * n3 + 2 * n3 * nb) for nodes, n3, nb in lv) + \
+        sum(nodes * 2 * nb * n3 for nodes, n3, nb in lv[1:])
+    sweeps = nstages * (1 + refine)
+    fp32 = sweeps * R * (leaves * (8 * m ** 3 + 2 * q * b) + merge)
+    return fp64, fp32
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -575,6 +605,18 @@ def bench_ours(args, rank, world, local_rank):
                 "clocks": r64["clocks"]}
         mixed_ok = err_mixed <= 1e-10
         head = rmx if mixed_ok else r64
+        step_roofline = None
+        if mixed_ok and not S.nodal:  # the whole step against the pipe that bounds it
+            first = any(float(coef.get(k_, 0.0)) != 0.0 for k_ in ("a1", "a2"))
+            f64, f32 = step_flops(wl.n1, wl.n2, wl.p, R, args.refine, first)
+            ms = head["total_ms"] / args.steps
+            t64, t32 = f64 / (peak_fp64 * 1e12) * 1e3, f32 / (peak_fp32 * 1e12) * 1e3
+            step_roofline = {"bound": "alu", "pipe": "FP64" if t64 >= t32 else "FP32",
+                             "fp64_gflop": f64 / 1e9, "fp32_gflop": f32 / 1e9, "ideal_ms": max(t64, t32),
+                             "ms_per_step": ms, "frac": max(t64, t32) / ms,
+                             "note": "algorithmic flops of the step (bench.step_flops) at the unit-count peaks "
+                                     "(FP64 %.3f, FP32 %.1f TFLOP/s); ideal = the slower pipe's time, the FP32 "
+                                     "sweeps assumed to overlap it" % (peak_fp64, peak_fp32)}
         out = {
             "metric": "DOF*stages/s (N x implicit HPS stage solves per second, ARK4(3)6L[2]SA step)",
             "value": value_mixed if mixed_ok else value64, "unit": "DOF*stages/s", "n_gpus": world,
@@ -595,6 +637,7 @@ def bench_ours(args, rank, world, local_rank):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "err_vs_fp64": err_mixed,
             "roofline": roofline(head, mixed_ok),
+            "step_roofline": step_roofline,
             "kernel_shares": head["shares"],
             "gpu_launches": head["launches"],
             "e2e": ({"value": R * N * STAGES / (emx_ms * 1e-3), "unit": "DOF*stages/s",
