@@ -1243,7 +1243,8 @@ inline StreamPlan stream_plan(int nodes, int M, int K, int ld, int64_t str, int 
   P.KS = std::max(1, kStreamConsumers / P.QQ);
   P.hint = 1;
   P.S = 0;
-  const size_t rest = stream_smem(P, role_floats), budget = (size_t)(227 * 1024) / std::max(1, cps);
+  // per CTA: a cps-th of the SM's 228 KB less the 1 KB the hardware reserves for each resident CTA
+  const size_t rest = stream_smem(P, role_floats), budget = (size_t)(228 * 1024) / std::max(1, cps) - 1024;
   if (budget > rest) P.S = (int)std::min<size_t>(kStreamMaxStages, (budget - rest) / ((size_t)P.C * ld * 4));
   return P;
 }
