@@ -292,15 +292,21 @@ int hps_solve_batch(hps_handle *h, int R, const double *rhs, const double *f, do
 int ark_step_batch(hps_handle *h, int R, double *u, double t, double dt, const hps_ark_terms *terms, int refine,
                    hps_stream_t stream);
 
-/* One ARK4(3)6L[2]SA step in slope form (Sec. 3.1, eq. slope0) for g = 0, FP64, on u (N, in
+/* One ARK4(3)6L[2]SA step in slope form (Sec. 3.1, eq. slope0; eq. slope with g), FP64, on u (N, in
  * place): slopes k_1 = L u^n + q_1 (explicit; its shared-edge values from the identity-operator
  * system), (I - gamma dt L) k_i = L u^n + dt sum_{j<i} a_ij L k_j + q_i (one HPS solve each),
  * u^{n+1} = u^n + dt sum_j b_j k_j at every point.  Every slope system's interface rows carry
  * -1/dt times the flux jump of u^n (the penalization of Sec. 3.1), so u^{n+1} has no flux jump.
  * terms->q: 6 x N_int stage sources or NULL; terms->f: 6 x N_bd slope boundary data, i.e. u_t at
- * t + c_i dt on the boundary, or NULL for zero (time-independent Dirichlet data); terms->g_kind
- * must be HPS_G_NONE.  Needs at least two leaves and the per-level merge kernels (not
- * hps_set_persistent); the first call allocates 7 N doubles of work memory. */
+ * t + c_i dt on the boundary, or NULL for zero (time-independent Dirichlet data).  With a preset g
+ * (terms->g_kind, eq. slope) explicit slopes l_i = g(U_i) join the k_i (U_i = u^n + dt sum_{j<=i}
+ * a_ij k_j + dt sum_{j<i} ahat_ij l_j at every point), dt sum_j ahat_ij L l_j enters every slope
+ * system and u^{n+1} = u^n + dt sum_j b_j (k_j + l_j); each l_i takes g at the interior points, its
+ * shared-edge values from the identity-operator system and zero boundary values, so only
+ * time-independent Dirichlet data are accepted (terms->f must be NULL, else HPS_EINVAL).
+ * HPS_G_USER is rejected.  Needs at least two leaves and the per-level merge kernels (not
+ * hps_set_persistent); the first call allocates 7 N doubles of work memory (with g 7 N + 7 N_int
+ * more). */
 int ark_slope_step(hps_handle *h, double *u, double t, double dt, const hps_ark_terms *terms, hps_stream_t stream);
 
 /* ark_slope_step on R states at once in mixed precision (u: N x R in place; terms->q: 6 x N_int x R

@@ -788,7 +788,8 @@ int ark_step(hps_handle *H, double *u, double t, double dt, const hps_ark_terms 
 int ark_slope_step(hps_handle *H, double *u, double t, double dt, const hps_ark_terms *terms, hps_stream_t stream) {
   if (!H || !u || !(dt > 0.0) || !std::isfinite(t)) return HPS_EINVAL;
   if (std::fabs(0.25 * dt - H->gamma_dt) > 1e-12 * H->gamma_dt) return HPS_EDT;
-  if ((terms && terms->g_kind != HPS_G_NONE) || H->persistent) return HPS_EINVAL;
+  const int gk = terms ? terms->g_kind : HPS_G_NONE;
+  if (gk < HPS_G_NONE || gk > HPS_G_BURGERS || H->persistent) return HPS_EINVAL;
   hps::ArkTable tab;
   const Tableau &tb = tableau();
   std::memcpy(tab.A, tb.A, sizeof(tab.A));

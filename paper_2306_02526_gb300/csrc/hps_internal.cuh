@@ -280,6 +280,7 @@ struct hps_handle {
   double *host_stage = nullptr;  // device copy of the states of ark_step(_batch)_host
   size_t host_stage_len = 0;
   double *slope_k = nullptr;     // slope form: 6 scaled slopes (N each) and the interface right-hand side
+  double *slope_l = nullptr;     // slope form with g: 6 explicit slopes, a stage value (N each), their dt L (6 N_int), scratch
   int pgrid = 0;              // its CTA count (co-resident)
   double *ppartial = nullptr; // its split-column partial sums
   size_t ppartial_len = 0;
@@ -353,7 +354,7 @@ int solve_batch(hps_handle *H, int R, const double *rhs, const double *f, double
 struct ArkTable {
   double A[6][6], Ah[6][6], b[6];
 };
-// one ARK step in slope form (g = 0), FP64, single state (slope.cu)
+// one ARK step in slope form (g = 0, or a preset g with time-independent boundary data), FP64 (slope.cu)
 int ark_slope(hps_handle *H, double *u, double dt, const hps_ark_terms *terms, const ArkTable &tb, cudaStream_t st);
 int ark_slope_batch(hps_handle *H, int R, double *u, double dt, const hps_ark_terms *terms, int refine,
                     const ArkTable &tb, cudaStream_t st);

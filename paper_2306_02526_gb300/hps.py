@@ -234,13 +234,15 @@ class HPSSolver:
             hooks[id(fn)] = (fn, _lib.G_FN(call))
         return hooks[id(fn)][1]
 
-    def ark_slope_step(self, u, t, dt, q=None, kbc=None, stream=None):
-        """One ARK step in slope form for g = 0 (ark_slope_step) in place on u: q (6, N_int) stage
-        sources or None; kbc (6, N_bd) slope boundary data (u_t at the stage times) or None (zero)."""
+    def ark_slope_step(self, u, t, dt, q=None, kbc=None, g=None, g_param=(1.0, 1.0), stream=None):
+        """One ARK step in slope form (ark_slope_step) in place on u: q (6, N_int) stage sources or
+        None; kbc (6, N_bd) slope boundary data (u_t at the stage times) or None (zero); g a preset
+        (then kbc must be None: time-independent boundary data)."""
         terms = _lib.hps_ark_terms()
         terms.q = _dptr(q, 6 * self.N_int, "q")
         terms.f = _dptr(kbc, 6 * self.N_bd, "kbc")
-        terms.g_kind = G_KINDS[None]
+        terms.g_kind = G_KINDS[g]
+        terms.g_param[0], terms.g_param[1] = float(g_param[0]), float(g_param[1])
         check(lib().ark_slope_step(self._h, _dptr(u, self.N, "u"), float(t), float(dt), ctypes.byref(terms),
                                    _stream_ptr(stream)), "ark_slope_step")
         return u

@@ -91,3 +91,40 @@ def test_slope_step_rejects_unsupported_cases():
     with pytest.raises(_lib.HPSError):  # a single leaf has no shared edges
         S.ark_slope_step(u, 0.0, 0.01)
     S.close()
+
+
+@pytest.mark.parametrize("gname,gp,nodal", [("allen_cahn", (1.5, 0.0), False), ("fisher", (0.8, 0.0), True),
+                                            ("burgers", (0.7, -0.4), False)])
+def test_slope_step_with_g_matches_oracle(gname, gp, nodal):
+    """The slope form with a nonlinear term (eq. slope): a state with flux jumps on every shared
+    edge, a source, time-independent (zero) boundary data; 3 steps against the oracle's
+    ark_slope_step_g at the FP64 tolerance."""
+    torch = need_gpu()
+    from oracle import nonlinear
+    from paper_2306_02526_gb300 import hps
+    g = Grid(4, 2, 10)
+    X, Y = g.coords()
+    I, bd = np.arange(g.N_int), g.boundary_indices()
+    coef = workloads.VarCoef128().coef(X[I], Y[I]) if nodal else {"a11": 0.8, "a22": 0.5, "a1": 0.2, "a0": -0.1}
+    gf = {"allen_cahn": lambda: nonlinear.allen_cahn(gp[0]), "fisher": lambda: nonlinear.fisher(gp[0]),
+          "burgers": lambda: nonlinear.burgers(gp[0], gp[1])}[gname]()
+    dt = 0.01
+    c = hps.hps_ark_abscissae()
+    qf = lambda t: 0.5 * np.cos(X[I] + t) * np.sin(2 * Y[I])
+    u = 0.2 * np.random.default_rng(13).standard_normal(g.N)
+    u[bd] = 0.0
+    S = _solver(torch, g, coef, 0.25 * dt)
+    Hi, Hid = HPS(g, coef, 0.25 * dt), HPS(g, coef, 0.0)
+    ug = to_dev(torch, u)
+    t = 0.0
+    for n in range(3):
+        S.ark_slope_step(ug, t, dt, q=to_dev(torch, np.stack([qf(t + cj * dt) for cj in c]).reshape(-1)),
+                         g=gname, g_param=gp)
+        u, _, _ = ark_slope.ark_slope_step_g(g, coef, Hi, Hid, u, t, dt, gf, q=qf)
+        t += dt
+        assert rel_max(ug.cpu().numpy(), u) <= TOL, (n, rel_max(ug.cpu().numpy(), u))
+    from paper_2306_02526_gb300 import _lib
+    with pytest.raises(_lib.HPSError):  # with g, time-dependent slope boundary data are not accepted
+        S.ark_slope_step(ug, t, dt, kbc=torch.zeros(6 * g.boundary_indices().size, dtype=torch.float64,
+                                                   device="cuda"), g=gname, g_param=gp)
+    S.close()
