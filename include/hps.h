@@ -311,7 +311,8 @@ int ark_slope_step(hps_handle *h, double *u, double t, double dt, const hps_ark_
 
 /* ark_slope_step on R states at once in mixed precision (u: N x R in place; terms->q: 6 x N_int x R
  * stage sources, terms->f: 6 x N_bd x R slope boundary data (u_t), both stage-major, or NULL;
- * g_kind HPS_G_NONE): every slope system by FP32 sweeps with `refine` FP64 refinement sweeps
+ * g_kind HPS_G_NONE or a preset, as for ark_slope_step: with g terms->f must be NULL and the first
+ * such call allocates (7 N + 6 N_int) x Rmax doubles more): every slope system by FP32 sweeps with `refine` FP64 refinement sweeps
  * against its collocation residual, interface rows included (their right-hand side is the
  * penalization's -(flux jump of u^n), carried by the first sweep and by every residual).  Needs
  * hps_batch_reserve(R) with one column group, at least two leaves; the first call allocates

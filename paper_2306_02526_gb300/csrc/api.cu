@@ -803,7 +803,8 @@ int ark_slope_step_batch(hps_handle *H, int R, double *u, double t, double dt, c
   if (!H || !u || !(dt > 0.0) || !std::isfinite(t) || R <= 0 || R > H->batch.Rmax || refine < 0 || refine > 8)
     return HPS_EINVAL;
   if (std::fabs(0.25 * dt - H->gamma_dt) > 1e-12 * H->gamma_dt) return HPS_EDT;
-  if (terms && terms->g_kind != HPS_G_NONE) return HPS_EINVAL;
+  const int gk = terms ? terms->g_kind : HPS_G_NONE;
+  if (gk < HPS_G_NONE || gk > HPS_G_BURGERS || (gk != HPS_G_NONE && terms->f)) return HPS_EINVAL;
   hps::ArkTable tab;
   const Tableau &tb = tableau();
   std::memcpy(tab.A, tb.A, sizeof(tab.A));
@@ -811,7 +812,8 @@ int ark_slope_step_batch(hps_handle *H, int R, double *u, double t, double dt, c
   std::memcpy(tab.b, tb.b, sizeof(tab.b));
   const uint64_t key[hps::GraphEntry::kKey] = {
       (uint64_t)u, (uint64_t)(terms ? terms->q : nullptr), (uint64_t)(terms ? terms->f : nullptr),
-      ((uint64_t)R << 8) | ((uint64_t)refine << 24), 0, 0, bits(dt), 4};
+      (uint64_t)gk | ((uint64_t)R << 8) | ((uint64_t)refine << 24), bits(terms ? terms->g_param[0] : 0.0),
+      bits(terms ? terms->g_param[1] : 0.0), bits(dt), 4};
   return run_graphed(H, H->g_ark_b, key,
                      [&](cudaStream_t s) { return hps::ark_slope_batch(H, R, u, dt, terms, refine, tab, s); },
                      (cudaStream_t)stream);

@@ -3741,7 +3741,12 @@ int ark_group(hps_handle *H, BatchWork &B, int R, double *u, double dt, const hp
 // at every point.  Every slope system's interface rows carry J = -(flux jump of u^n) (the
 // penalization of Sec. 3.1).  Implicit terms are kept times gamma (KL_0 = gamma dt L u^n, KL_j =
 // gamma dt L kappa_j) with their coefficients divided by it, as in ark_group.  Slope boundary data:
-// dt times the caller's u_t values (f, [6][N_bd][fld] from foff), else 0.
+// dt times the caller's u_t values (f, [6][N_bd][fld] from foff), else 0.  With a preset g
+// (eq. slope, time-independent boundary data: f must be null) the explicit slopes lambda_j = dt
+// g(U_j) join them as complete fields (interior g, shared edges from the identity-operator
+// system, zero boundary; W.slope_g), U_i = u^n + sum_{j<=i} a_ij kappa_j + sum_{j<i} ahat_ij
+// lambda_j, their gamma dt L lambda_j enter every slope system with ahat_ij / gamma, and
+// u^{n+1} = u^n + sum_j b_j (kappa_j + lambda_j).
 // (q enters the stage combinations, whose terms are [N_int][R] vectors: qld = R, qoff = 0)
 int slope_group(hps_handle *H, BatchWork &W, int R, double *u, double dt, const hps_ark_terms *terms, int qld,
                 int qoff, int fld, int foff, int refine, const ArkTable &tb, cudaStream_t st) {
@@ -3750,6 +3755,10 @@ int slope_group(hps_handle *H, BatchWork &W, int R, double *u, double dt, const 
   const int64_t N = g.N, ni = g.N_int * R, nR = N * R;
   const double *q = terms ? terms->q : nullptr;
   const double *f = terms ? terms->f : nullptr;
+  const int gk = terms ? terms->g_kind : HPS_G_NONE;
+  const double gp0 = terms ? terms->g_param[0] : 0.0, gp1 = terms ? terms->g_param[1] : 0.0;
+  if (gk != HPS_G_NONE && (f || !W.slope_g)) return HPS_EINVAL;
+  double *lam = W.slope_g, *Ust = lam ? lam + 6 * nR : nullptr, *dLl = Ust ? Ust + nR : nullptr;
   const int64_t qstage = g.N_int * (int64_t)qld, fstage = g.N_bd * (int64_t)fld;
   const double gam = tb.A[1][1];
   double *kap = W.slope, *J = W.slope + 6 * nR, *fs = J + nR;
@@ -3774,6 +3783,29 @@ int slope_group(hps_handle *H, BatchWork &W, int R, double *u, double dt, const 
     H->trace.end(kSetBoundary, st);
     return BdView{fs, R, 0};
   };
+  // lambda_i = dt g(v): interior by the leaf evaluation, zero boundary, shared edges from the
+  // identity-operator system; gamma dt L lambda_i into dLl_i
+  auto explicit_slope = [&](const double *v, int i) -> int {
+    double *li = lam + i * nR, *scr = W.KE + ni;
+    Leaf64Args E = leaf64_args(H, kEval, R);
+    E.u = v;
+    E.out0 = W.KE;  // (gamma dt L v: not used)
+    E.out1 = li;    // dt g(v) at the interior points
+    E.dt = dt;
+    E.dtL = gam * dt;
+    E.g_kind = gk;
+    E.gp0 = gp0;
+    E.gp1 = gp1;
+    if (int e = leaf64(H, E, st)) return e;
+    H->trace.begin(kSetBoundary, st);
+    k_b_set_boundary32<<<blocks(g.N_bd * R), 256, 0, st>>>(g, R, W.g32, nullptr, 0, 0, li);
+    H->trace.end(kSetBoundary, st);
+    if (cudaMemcpyAsync(scr, li, ni * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess) return HPS_ECUDA;
+    Combo c{};
+    add_term_b(c, scr, 1.0);
+    if (int e = edge_projection_impl(H, R, c, li, W.r, st, nullptr)) return e;
+    return eval(li, dLl + i * ni);
+  };
   if (int e = eval(u, W.KL)) return e;
   {  // kappa_1: interior dt (L u^n + q_1), boundary dt u_t, shared edges by the edge projection with J
     const BdView fv = bd(0);
@@ -3786,12 +3818,16 @@ int slope_group(hps_handle *H, BatchWork &W, int R, double *u, double dt, const 
     if (int e = edge_projection_impl(H, R, c, kap, W.r, st, J)) return e;
     if (int e = eval(kap, W.KL + ni)) return e;
   }
+  if (gk != HPS_G_NONE)
+    if (int e = explicit_slope(u, 0)) return e;
   for (int i = 1; i < 6; ++i) {
     double *ki = kap + i * nR;
     Combo c{};
     add_term_b(c, W.KL, 1.0 / gam);
     if (q) add_term_b(c, q + i * qstage, dt);
     for (int j = 0; j < i; ++j) add_term_b(c, W.KL + (j + 1) * ni, tb.A[i][j] / gam);
+    if (gk != HPS_G_NONE)
+      for (int j = 0; j < i; ++j) add_term_b(c, dLl + j * ni, tb.Ah[i][j] / gam);
     // the epilogue keeps gamma dt L kappa_i = kappa_i - R_i (the last one is not needed)
     double *kl = i < 5 ? W.KL + (i + 1) * ni : nullptr;
     const StageEpi ep{H->batch.fuse_epilogue ? 1 : 0, W.Rb, kl, W.KE, nullptr, R, 0, HPS_G_NONE, dt, 0.0};
@@ -3799,20 +3835,33 @@ int slope_group(hps_handle *H, BatchWork &W, int R, double *u, double dt, const 
     if (int e = refined_solve(H, W, H->impl, H->batch.impl32, R, c, W.Rb, W.Rb, bd(i), ki, refine, H->gamma_dt, st,
                               ep, done, J))
       return e;
-    if (done || !kl) continue;
-    Leaf64Args P = leaf64_args(H, kEpilogue, R);
-    P.u = ki;
-    P.Rb = W.Rb;
-    P.out0 = kl;
-    P.out1 = W.KE;
-    P.dt = dt;
-    P.g_kind = HPS_G_NONE;
-    if (int e = leaf64(H, P, st)) return e;
+    if (!done && kl) {
+      Leaf64Args P = leaf64_args(H, kEpilogue, R);
+      P.u = ki;
+      P.Rb = W.Rb;
+      P.out0 = kl;
+      P.out1 = W.KE;
+      P.dt = dt;
+      P.g_kind = HPS_G_NONE;
+      if (int e = leaf64(H, P, st)) return e;
+    }
+    if (gk != HPS_G_NONE) {  // U_i at every point, then lambda_i
+      Combo cu{};
+      add_term_b(cu, u, 1.0);
+      for (int j = 0; j <= i; ++j) add_term_b(cu, kap + j * nR, tb.A[i][j]);
+      for (int j = 0; j < i; ++j) add_term_b(cu, lam + j * nR, tb.Ah[i][j]);
+      H->trace.begin(kFinish, st);
+      k_b_combine_all<<<blocks(nR), 256, 0, st>>>(nR, cu, Ust);
+      H->trace.end(kFinish, st);
+      if (int e = explicit_slope(Ust, i)) return e;
+    }
   }
-  // u^{n+1} = u^n + sum_j b_j kappa_j at every point
+  // u^{n+1} = u^n + sum_j b_j (kappa_j + lambda_j) at every point (bhat = b for this tableau)
   Combo c{};
   add_term_b(c, u, 1.0);
   for (int j = 0; j < 6; ++j) add_term_b(c, kap + j * nR, tb.b[j]);
+  if (gk != HPS_G_NONE)
+    for (int j = 0; j < 6; ++j) add_term_b(c, lam + j * nR, tb.b[j]);
   H->trace.begin(kFinish, st);
   k_b_combine_all<<<blocks(nR), 256, 0, st>>>(nR, c, u);
   H->trace.end(kFinish, st);
@@ -4178,6 +4227,11 @@ int ark_slope_batch(hps_handle *H, int R, double *u, double dt, const hps_ark_te
     if (cudaMalloc(&W.slope, need * sizeof(double)) != cudaSuccess) return HPS_ENOMEM;
     H->allocs.push_back(W.slope);
     W.slope_len = need;
+  }
+  if (terms && terms->g_kind != HPS_G_NONE && !W.slope_g) {  // explicit slopes, a stage value, their L
+    const size_t ng = (7 * (size_t)H->g.N + 6 * (size_t)H->g.N_int) * H->batch.Rmax;
+    if (cudaMalloc(&W.slope_g, ng * sizeof(double)) != cudaSuccess) return HPS_ENOMEM;
+    H->allocs.push_back(W.slope_g);
   }
   return slope_group(H, W, R, u, dt, terms, R, 0, R, 0, refine, tb, st);
 }

@@ -151,6 +151,7 @@ struct BatchWork {
   cudaEvent_t first = nullptr;     // grouped ARK steps: the explicit first stage is done
   double *slope = nullptr;         // batched slope form: kappa_1..6, J ([N][R] each), scaled f ([N_bd][R])
   size_t slope_len = 0;            // doubles
+  double *slope_g = nullptr;       // ... with g: lambda_1..6, U ([N][R] each), gamma dt L lambda_1..6 ([N_int][R])
 };
 
 // The batched path: FP32 operator copies (shared by all groups) and G column groups.  With

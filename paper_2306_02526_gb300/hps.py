@@ -313,14 +313,16 @@ class HPSSolver:
                                    int(refine), _stream_ptr(stream)), "ark_step_batch")
         return u
 
-    def ark_slope_step_batch(self, u, t, dt, q=None, kbc=None, refine=2, stream=None):
+    def ark_slope_step_batch(self, u, t, dt, q=None, kbc=None, g=None, g_param=(1.0, 1.0), refine=2, stream=None):
         """ark_slope_step on R states u (N, R) in place, mixed precision (ark_slope_step_batch):
-        q (6, N_int, R) stage sources, kbc (6, N_bd, R) slope boundary data (u_t), or None."""
+        q (6, N_int, R) stage sources, kbc (6, N_bd, R) slope boundary data (u_t), or None; g a
+        preset (then kbc must be None)."""
         R = u.shape[1]
         terms = _lib.hps_ark_terms()
         terms.q = _dptr(q, 6 * self.N_int * R, "q")
         terms.f = _dptr(kbc, 6 * self.N_bd * R, "kbc")
-        terms.g_kind = G_KINDS[None]
+        terms.g_kind = G_KINDS[g]
+        terms.g_param[0], terms.g_param[1] = float(g_param[0]), float(g_param[1])
         check(lib().ark_slope_step_batch(self._h, R, _dptr(u, self.N * R, "u"), float(t), float(dt),
                                          ctypes.byref(terms), int(refine), _stream_ptr(stream)), "ark_slope_step_batch")
         return u
