@@ -467,26 +467,30 @@ def bench_ours(args, rank, world, local_rank):
         args.steps, args.warmup = 2, 1
         qR, fR = stage_terms(R)
 
-    # ---- slope form (g = 0 only): the workload's linear part on the same operators, FP64 ----------
+    # ---- slope form, FP64: the workload itself (eq. slope with its g when its boundary data are
+    # time-independent), else its linear part ------------------------------------------------------
     slope = None
+    slope_g = wl.g if f1 is None and fR is None else None
+    slope_kw = {"g": slope_g, "g_param": wl.g_param} if slope_g else {}
     if args.only is None:
         us = torch.tensor(u0, dtype=torch.float64, device="cuda")
         for _ in range(3):
-            S.ark_slope_step(us, 0.0, wl.dt)
+            S.ark_slope_step(us, 0.0, wl.dt, **slope_kw)
         torch.cuda.synchronize()
         se = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
         for k in range(10):
             flush.fill_(float(k))
             se[k][0].record(stream)
-            S.ark_slope_step(us, 0.0, wl.dt)
+            S.ark_slope_step(us, 0.0, wl.dt, **slope_kw)
             se[k][1].record(stream)
         torch.cuda.synchronize()
         sms = [a.elapsed_time(b) for a, b in se]
         assert torch.isfinite(us).all(), "slope-form state went non-finite"
         slope = {"value": N * STAGES * len(sms) / (sum(sms) * 1e-3), "unit": "DOF*stages/s",
                  "ms_per_step": sum(sms) / len(sms), "steps": len(sms), "launch": "eager",
-                 "note": "slope form with penalized interface rows (g = 0): u_t = L u of the workload, "
-                         "same grid and operators, FP64, L2 flushed before every step"}
+                 "g": slope_g,
+                 "note": "slope form with penalized interface rows (eq. slope: explicit slopes for g, zero "
+                         "slope boundary data), same grid and operators, FP64, L2 flushed before every step"}
 
     # ---- mixed precision, R right-hand sides (FP32 sweeps + FP64 refinement) ----------------------
     S.batch_reserve(R, groups=args.groups)
@@ -504,30 +508,31 @@ def bench_ours(args, rank, world, local_rank):
     if args.only is None and args.groups == 1:
         Us = torch.tensor(U0, dtype=torch.float64, device="cuda")
         for _ in range(3):
-            S.ark_slope_step_batch(Us, 0.0, wl.dt, refine=2)
+            S.ark_slope_step_batch(Us, 0.0, wl.dt, refine=2, **slope_kw)
         torch.cuda.synchronize()
         se = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
         for k in range(10):
             flush.fill_(float(k))
             se[k][0].record(stream)
-            S.ark_slope_step_batch(Us, 0.0, wl.dt, refine=2)
+            S.ark_slope_step_batch(Us, 0.0, wl.dt, refine=2, **slope_kw)
             se[k][1].record(stream)
         torch.cuda.synchronize()
         sms = [a.elapsed_time(b) for a, b in se]
         assert torch.isfinite(Us).all(), "batched slope-form state went non-finite"
         # one step from the same states against the FP64 slope step, first and last column
         Us = torch.tensor(U0, dtype=torch.float64, device="cuda")
-        S.ark_slope_step_batch(Us, 0.0, wl.dt, refine=2)
+        S.ark_slope_step_batch(Us, 0.0, wl.dt, refine=2, **slope_kw)
         serr = 0.0
         for j in (0, R - 1):
             v = torch.tensor(np.ascontiguousarray(U0[:, j]), dtype=torch.float64, device="cuda")
-            S.ark_slope_step(v, 0.0, wl.dt)
+            S.ark_slope_step(v, 0.0, wl.dt, **slope_kw)
             serr = max(serr, float((Us[:, j] - v).abs().max() / v.abs().max()))
         slope_mixed = {"value": N * STAGES * R * len(sms) / (sum(sms) * 1e-3), "unit": "DOF*stages/s",
                        "ms_per_step": sum(sms) / len(sms), "steps": len(sms), "rhs": R, "refine": 2,
                        "err_vs_fp64_slope": serr, "err_columns": [0, R - 1],
                        "over_fp64_slope": None if not slope else
                        N * STAGES * R * len(sms) / (sum(sms) * 1e-3) / slope["value"],
+                       "g": slope_g,
                        "note": "ark_slope_step_batch: FP32 sweeps + 2 FP64 refinement sweeps per slope system "
                                "(interface rows carry the penalization), CUDA graph replay, L2 flushed before "
                                "every step"}
