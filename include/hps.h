@@ -431,7 +431,10 @@ enum {
                                    programmatic dependents (griddepcontrol): each starts its
                                    operator loads while the kernel before it finishes and waits for
                                    its results in the kernel (0: ordinary launches)                */
-  HPS_OPT_COUNT = 31
+  HPS_OPT_EO_THREADS = 31,       /* threads per CTA of the FP64 even-odd leaf kernel (residual,
+                                   evaluation): 32..256 in steps of 32; 0 (default): 128 with one
+                                   column per pass, else 256                                        */
+  HPS_OPT_COUNT = 32
 };
 int hps_batch_set_option(hps_handle *h, int opt, int value);
 

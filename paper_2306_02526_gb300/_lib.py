@@ -72,7 +72,8 @@ BATCH_OPTIONS = ("tensor_leaf", "even_odd", "flow_levels", "flow_n3_max", "clust
                  "eo_cols", "tile_cols_w3", "tile_cols_h", "tile_cols_down",
                  "fp64_plan_target", "umma_leaf", "one_column_merge",
                  "one_column_sum", "stream_leaf",
-                 "stream_chunk_kb", "sub_levels", "pdl")
+                 "stream_chunk_kb", "sub_levels", "pdl",
+                 "eo_threads")
 
 
 class hps_server_stats(ctypes.Structure):

@@ -3515,7 +3515,11 @@ int leaf64(hps_handle *H, Leaf64Args A, cudaStream_t st, bool *flux_done = nullp
     }
     if (int e_ = smem_optin((const void *)k_b_leaf64_eo, smem)) return e_;
     H->trace.begin(slot, st);
-    k_b_leaf64_eo<<<grid, kBT, smem, st>>>(H->g, leaf.nodes, leaf.d_origin, A, H->d_D);
+    // (every loop of the kernel strides by blockDim: fewer threads per CTA, more CTAs per SM; with
+    // one column a pass keeps at most (p/2 - 1)^2 threads busy, and 128-thread CTAs measured 24 %
+    // faster than 256-thread ones on 128 x 128 leaves, p = 16, while with 4 or 32 columns 256 is best)
+    const int eo_threads = H->batch.eo_threads > 0 ? H->batch.eo_threads : Rc == 1 ? 128 : kBT;
+    k_b_leaf64_eo<<<grid, eo_threads, smem, st>>>(H->g, leaf.nodes, leaf.d_origin, A, H->d_D);
     H->trace.end(slot, st);
     return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
   }
@@ -4013,6 +4017,7 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
     case HPS_OPT_STREAM_CHUNK_KB: field = &Bt.stream_chunk_kb; break;
     case HPS_OPT_SUB_LEVELS: field = &Bt.sub_levels; break;
     case HPS_OPT_PDL: flag = &Bt.pdl; break;
+    case HPS_OPT_EO_THREADS: field = &Bt.eo_threads; break;
     case HPS_OPT_EVEN_ODD: flag = &Bt.even_odd; break;
     case HPS_OPT_FLOW_LEVELS: field = &Bt.flow_levels; break;
     case HPS_OPT_FLOW_N3_MAX: field = &Bt.flow_n3_max; break;
@@ -4052,6 +4057,7 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
   if (opt == HPS_OPT_STREAM_LEAF && v > 4) return HPS_EINVAL;
   if (opt == HPS_OPT_STREAM_CHUNK_KB && (v < 2 || v > 64)) return HPS_EINVAL;
   if (opt == HPS_OPT_SUB_LEVELS && v > kSubMaxLevels) return HPS_EINVAL;
+  if (opt == HPS_OPT_EO_THREADS && (v % 32 != 0 || v > kBT)) return HPS_EINVAL;
   if (opt == HPS_OPT_UMMA_LEAF && v == 3)
     if (int e = umma_bf16_reserve(H)) return e;
   if (opt == HPS_OPT_FP64_PLAN_TARGET) {  // FP64 split plans: not while the persistent kernel holds tasks

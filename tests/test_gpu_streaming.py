@@ -21,7 +21,9 @@ VARIANTS = [dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=1, one_colu
             dict(stream_leaf=0, stream_chunk_kb=24, one_column_merge=1, one_column_sum=1),
             dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=1, one_column_sum=0),
             dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=0, one_column_sum=0),
-            dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=1, one_column_sum=1, pdl=1)]
+            dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=1, one_column_sum=1, pdl=1),
+            dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=1, one_column_sum=1, eo_threads=256),
+            dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=1, one_column_sum=1, eo_threads=64)]
 
 
 def _nodal_solver(torch, n1, n2, p, gdt, seed=0):
