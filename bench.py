@@ -890,6 +890,19 @@ def bench_multi(args, flush):
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     ms = [a.elapsed_time(b) for a, b in ev]
+    # the same step in lockstep: one grouped merge launch per tree level for all instances
+    M.set_lockstep(True)
+    for _ in range(nwarm):
+        step()
+    lev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ntimed)]
+    for k in range(ntimed):
+        flush.fill_(float(k))
+        lev[k][0].record(stream)
+        step()
+        lev[k][1].record(stream)
+    torch.cuda.synchronize()
+    lock_ms = [a.elapsed_time(b) for a, b in lev]
+    M.set_lockstep(False)
     # the same step with the instances one after another on the caller's stream (no graph)
     M.set_graph(False)
     seq = []
@@ -902,7 +915,7 @@ def bench_multi(args, flush):
         b.record(stream)
         b.synchronize()
         seq.append(a.elapsed_time(b))
-    nsteps = nwarm + ntimed + 2
+    nsteps = 2 * (nwarm + ntimed) + 2
     errs = []
     for i in range(0, len(solvers), max(1, len(solvers) // 4)):
         S = solvers[i]
@@ -922,6 +935,8 @@ def bench_multi(args, flush):
             "value": units / (statistics.mean(ms) * 1e-3), "unit": "DOF*stages/s",
             "ms_per_step": statistics.mean(ms), "steps": ntimed,
             "launch": "one CUDA graph per step for all instances (hps_multi_set_graph)",
+            "lockstep_ms_per_step": statistics.mean(lock_ms),
+            "lockstep": "hps_multi_set_lockstep: grouped merge launches per tree level, one graph per step",
             "sequential_ms_per_step": statistics.mean(seq),
             "concurrent_over_sequential": statistics.mean(seq) / statistics.mean(ms),
             "refine": args.per_node_refine, "umma_leaf": args.per_node_umma,

@@ -342,11 +342,17 @@ int ark_step_batch_host(hps_handle *h, int R, double *u_host, double t, double d
  * step for all instances (the instances' own graph replay is switched off).  u[i]: device state of
  * instance i, N_i x R[i] RHS-fastest; terms: n entries (or NULL: no q, f, g); dt must match every
  * handle's gamma_dt (dt = 4 gamma_dt).  The handles must outlive the object and must not be used
- * on other streams while a step runs.  The instances' launches run concurrently inside one graph;
- * they are not fused into one kernel per tree level. */
+ * on other streams while a step runs.  The instances' launches run concurrently inside one graph.
+ * hps_multi_set_lockstep(m, 1) (every handle with one column group; HPS_EINVAL otherwise) fuses
+ * the instances' merges instead: each FP32 sweep runs every instance's leaf part on its stream,
+ * then one launch per tree level and merge operator for all instances together (upward levels
+ * counted from each tree's leaves, downward from the roots), then the leaf parts again; the
+ * residuals, epilogues and step close stay per instance.  Same results to the batched path's
+ * tolerance (the FP32 sums of a merge split differently). */
 typedef struct hps_multi hps_multi;
 int hps_multi_create(hps_handle *const *handles, int n, hps_multi **out);
 int hps_multi_set_graph(hps_multi *m, int enable);
+int hps_multi_set_lockstep(hps_multi *m, int enable);
 int hps_multi_ark_step(hps_multi *m, double *const *u, const int *R, const hps_ark_terms *terms, double dt, int refine,
                        hps_stream_t stream);
 void hps_multi_free(hps_multi *m);

@@ -138,6 +138,7 @@ SIGNATURES = {
     "hps_server_evict_after": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "hps_multi_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     "hps_multi_set_graph": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "hps_multi_set_lockstep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "hps_multi_ark_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int),
                                           ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p]),
     "hps_multi_free": (None, [ctypes.c_void_p]),

@@ -544,6 +544,16 @@ int bytes_split(const hps_tree *tree, int p, int coeff_kind, int flags, size_t *
   return HPS_OK;
 }
 
+// The ARK table of the implicit and explicit tableaus (Table 1), for the batched steps.
+ArkTable ark_table() {
+  ArkTable t;
+  const Tableau &tb = tableau();
+  std::memcpy(t.A, tb.A, sizeof(t.A));
+  std::memcpy(t.Ah, tb.Ah, sizeof(t.Ah));
+  std::memcpy(t.b, tb.b, sizeof(t.b));
+  return t;
+}
+
 }  // namespace hps
 
 namespace {

@@ -1676,13 +1676,16 @@ struct BEScatter {  // interface values: FP32 for the levels below, and into the
   }
 };
 
+// The body of one CTA (block bx, K chunk by) of a merge apply; k_b_gemv runs it for its own grid,
+// k_b_gemv_group for the blocks of many instances' applies in one launch.
 template <int TC, class XL, class EP>
-__global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict__ AT, int ld, int64_t str, XL xl,
-                                                EP ep, float *__restrict__ partial, unsigned *__restrict__ tile_count) {
+__device__ __forceinline__ void gemv_tile(const BPlan &P, const float *__restrict__ AT, int ld, int64_t str, XL xl, EP ep,
+                                          float *__restrict__ partial, unsigned *__restrict__ tile_count, int bx,
+                                          int by) {
   extern __shared__ __align__(16) float smb[];
-  const int ng = blockIdx.x / P.row_tiles, tile = blockIdx.x % P.row_tiles;
+  const int ng = bx / P.row_tiles, tile = bx % P.row_tiles;
   const int node0 = ng * P.npc, nn = min(P.npc, P.nodes - node0);
-  const int ks = blockIdx.y, c0 = ks * P.kchunk, klen = min(P.kchunk, P.K - c0);
+  const int ks = by, c0 = ks * P.kchunk, klen = min(P.kchunk, P.K - c0);
   const int Rp = P.Rp;
   // operator tile(s) [tile][klen][trows] by asynchronous copies, overlapping the vector staging
   const int trows = P.trows, rlo = P.npc > 1 ? 0 : 4 * tile * P.quads_cta;
@@ -1765,7 +1768,7 @@ __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict
   __shared__ int s_last;
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(tile_count + blockIdx.x, 1u) == (unsigned)(P.ksplit - 1);
+  if (threadIdx.x == 0) s_last = atomicAdd(tile_count + bx, 1u) == (unsigned)(P.ksplit - 1);
   __syncthreads();
   if (!s_last) return;
   __threadfence();
@@ -1784,16 +1787,19 @@ __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict
     }
     ep.template row<4>(node0 + l2, r, j0q, v);
   }
-  if (threadIdx.x == 0) tile_count[blockIdx.x] = 0u;
+  if (threadIdx.x == 0) tile_count[bx] = 0u;
+}
+
+template <int TC, class XL, class EP>
+__global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict__ AT, int ld, int64_t str, XL xl,
+                                                EP ep, float *__restrict__ partial, unsigned *__restrict__ tile_count) {
+  gemv_tile<TC>(P, AT, ld, str, xl, ep, partial, tile_count, (int)blockIdx.x, (int)blockIdx.y);
 }
 
 // Sum of the split-K partials in chunk order, four columns per thread.
 template <class EP>
-__global__ void k_b_reduce(BPlan P, const float *__restrict__ partial, EP ep) {
-  pdl_trigger();
-  pdl_wait();
+__device__ __forceinline__ void reduce_row(const BPlan &P, const float *__restrict__ partial, EP ep, int i) {
   const int Rq = P.Rp / 4;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P.nodes * P.M * Rq) return;
   const int row = i / Rq, j0 = 4 * (i - row * Rq), k = row / P.M, r = row - k * P.M;
   float v[4] = {0.f, 0.f, 0.f, 0.f};
@@ -1808,6 +1814,13 @@ __global__ void k_b_reduce(BPlan P, const float *__restrict__ partial, EP ep) {
     v[3] += x.w;
   }
   ep.template row<4>(k, r, j0, v);
+}
+
+template <class EP>
+__global__ void k_b_reduce(BPlan P, const float *__restrict__ partial, EP ep) {
+  pdl_trigger();
+  pdl_wait();
+  reduce_row(P, partial, ep, (int)(blockIdx.x * blockDim.x + threadIdx.x));
 }
 
 template <class XL, class EP>
@@ -1833,6 +1846,138 @@ int launch_b(hps_handle *H, BatchWork &B, int slot, const BPlan &P, const float 
              (const float *)B.partial32, ep);
   }
   H->trace.end(slot, st);
+  return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
+}
+
+// ---- one merge apply of many instances in one launch ------------------------------------------
+// The lockstep multi-instance step runs a tree level of every instance (levels counted from the
+// leaves upward, from the root downward) as ONE launch per operator: the blocks of all instances'
+// tiled applies in one grid, each block finding its instance in a prefix table of the kernel's
+// parameter block and running the instance's own plan (k_b_gemv's body); split-K partial sums
+// follow in one grouped reduction.
+constexpr int kGroupMax = 64;
+
+template <class XL, class EP>
+struct GemvGroup {
+  int n;
+  int block0[kGroupMax + 1];  // first block of each instance's flattened grid
+  int gx[kGroupMax];          // its grid's x extent (y: the K chunks)
+  BPlan P[kGroupMax];
+  const float *AT[kGroupMax];
+  int ld[kGroupMax];
+  int64_t str[kGroupMax];
+  XL xl[kGroupMax];
+  EP ep[kGroupMax];
+  float *partial[kGroupMax];
+};
+
+// (kernel parameters may take up to 32764 bytes)
+static_assert(sizeof(GemvGroup<BXDiff, BEStore>) <= 32000, "grouped w3 parameters");
+static_assert(sizeof(GemvGroup<BXVec, BEFlux>) <= 32000, "grouped h parameters");
+static_assert(sizeof(GemvGroup<BXBd, BEScatter>) <= 32000, "grouped down parameters");
+
+__device__ __forceinline__ int group_of(const int *block0, int n, int b) {  // block0[i] <= b < block0[i + 1]
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (block0[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <int TC, class XL, class EP>
+__global__ void __launch_bounds__(kBT) k_b_gemv_group(const __grid_constant__ GemvGroup<XL, EP> G) {
+  const int i = group_of(G.block0, G.n, (int)blockIdx.x), local = (int)blockIdx.x - G.block0[i];
+  gemv_tile<TC>(G.P[i], G.AT[i], G.ld[i], G.str[i], G.xl[i], G.ep[i], G.partial[i], nullptr, local % G.gx[i],
+                local / G.gx[i]);
+}
+
+template <class EP>
+struct ReduceGroup {
+  int n;
+  int block0[kGroupMax + 1];
+  BPlan P[kGroupMax];
+  const float *partial[kGroupMax];
+  EP ep[kGroupMax];
+};
+
+template <class EP>
+__global__ void k_b_reduce_group(const __grid_constant__ ReduceGroup<EP> G) {
+  const int i = group_of(G.block0, G.n, (int)blockIdx.x);
+  reduce_row(G.P[i], G.partial[i], G.ep[i], ((int)blockIdx.x - G.block0[i]) * (int)blockDim.x + (int)threadIdx.x);
+}
+
+// One instance's part of a grouped apply.
+template <class XL, class EP>
+struct GroupItem {
+  hps_handle *H;
+  BatchWork *B;
+  int slot, M, K, nodes, R;
+  const float *AT;
+  int ld;
+  int64_t str;
+  XL xl;
+  EP ep;
+};
+
+template <class XL, class EP>
+int launch_group(std::vector<GroupItem<XL, EP>> &items, cudaStream_t st) {
+  if (items.empty()) return HPS_OK;
+  struct Planned {
+    BPlan P;
+    const GroupItem<XL, EP> *it;
+  };
+  std::vector<Planned> pl;
+  pl.reserve(items.size());
+  for (const auto &it : items) {
+    const BPlan P = plan_b(it.M, it.K, it.nodes, it.R, plan_target(it.H), it.str == 0, plan_tune(it.H, it.slot));
+    if (P.ksplit > 1 && (size_t)P.ksplit * P.nodes * P.M * P.Rp > it.B->partial_len) return HPS_EINVAL;
+    pl.push_back({P, &it});
+  }
+  // instances with the same register-tile width share a launch (at most kGroupMax each)
+  std::stable_sort(pl.begin(), pl.end(), [](const Planned &a, const Planned &b) { return a.P.TC > b.P.TC; });
+  for (size_t g0 = 0; g0 < pl.size();) {
+    size_t g1 = g0;
+    while (g1 < pl.size() && g1 - g0 < (size_t)kGroupMax && pl[g1].P.TC == pl[g0].P.TC) ++g1;
+    GemvGroup<XL, EP> G{};
+    ReduceGroup<EP> Rg{};
+    size_t smem = 0;
+    int blocks = 0, rblocks = 0;
+    for (size_t k = g0; k < g1; ++k) {
+      const BPlan &P = pl[k].P;
+      const GroupItem<XL, EP> &it = *pl[k].it;
+      const int i = (int)(k - g0);
+      G.block0[i] = blocks;
+      G.gx[i] = P.node_groups * P.row_tiles;
+      G.P[i] = P;
+      G.AT[i] = it.AT;
+      G.ld[i] = it.ld;
+      G.str[i] = it.str;
+      G.xl[i] = it.xl;
+      G.ep[i] = it.ep;
+      G.partial[i] = it.B->partial32;
+      blocks += G.gx[i] * P.ksplit;
+      smem = std::max(smem, b_smem_floats(P) * sizeof(float));
+      if (P.ksplit > 1) {
+        const int r = Rg.n++;
+        Rg.block0[r] = rblocks;
+        Rg.P[r] = P;
+        Rg.partial[r] = it.B->partial32;
+        Rg.ep[r] = it.ep;
+        rblocks += (int)(((int64_t)P.nodes * P.M * (P.Rp / 4) + 255) / 256);
+      }
+    }
+    G.n = (int)(g1 - g0);
+    G.block0[G.n] = blocks;
+    Rg.block0[Rg.n] = rblocks;
+    const int TC = pl[g0].P.TC;
+    auto kern = TC == 8 ? k_b_gemv_group<8, XL, EP> : TC == 4 ? k_b_gemv_group<4, XL, EP> : k_b_gemv_group<2, XL, EP>;
+    if (int e_ = smem_optin((const void *)kern, smem)) return e_;
+    kern<<<blocks, kBT, smem, st>>>(G);
+    if (Rg.n > 0) k_b_reduce_group<EP><<<rblocks, 256, 0, st>>>(Rg);
+    g0 = g1;
+  }
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
@@ -3168,283 +3313,293 @@ int flow_launch(hps_handle *H, BatchWork &B, const FlowArgs &FA, bool up, size_t
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
+// Parts of a sweep (a sweep runs them in this order; the lockstep multi-instance step runs the
+// leaf parts per instance and the merges of all instances as grouped launches in between).
+enum : unsigned { kSweepLeafUp = 1, kSweepMerges = 2, kSweepLeafDown = 4, kSweepAll = 7 };
+
 // One FP32 sweep on R columns: leaf applies, merges up (with an optional FP64 interface
 // right-hand side), merges down into g32 (whose outer boundary the caller has set), leaf solves.
 int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, int R, const Combo &rhs,
             double *Rsave, const double *jump, UOut uo, bool allow_tc, cudaStream_t st, const StageEpi &ep,
-            bool &epi_done) {
+            bool &epi_done, unsigned parts = kSweepAll) {
   const int L = H->L, p = H->p, q = H->q, b = H->b, Rp = round4(R);
   const Level &leaf = H->lev[L];
   const bool tc8 = Rp % 8 == 0;
   const bool narrow = Rp == 4 && !H->shared;  // streaming per-leaf operators, one column group
   const int QQ = (q + 3) / 4, KS = std::max(1, kBT / QQ);
-  int cps = H->batch.stream_leaf;  // CTAs per SM: fewer where the rings of that many do not fit
-  StreamPlan SPu{};
-  for (; cps > 0; --cps) {
-    SPu = stream_plan(leaf.nodes, q, q, o32.Ainv.ld, o32.Ainv.str, cps, 2 * p * p, H->batch.stream_chunk_kb);
-    if (stream_fits(SPu, 2 * p * p)) break;
-  }
-  const bool stream_up = narrow && cps > 0 && !ops.identity && o32.Ainv.p;
-  if (stream_up) {
-    H->trace.begin(kLeafUp, st);
-    if (int e = launch_stream(H, SPu, cps, o32.Ainv.p,
-                              StreamUp{H->g, R, leaf.d_origin, rhs, Rsave, H->d_D, B.w32, B.h32[L]}, st))
-      return e;
-    H->trace.end(kLeafUp, st);
-  } else if (narrow) {
-    const size_t smem = (size_t)(round4(2 * p * p) + 8 * q + KS * 16 * QQ) * sizeof(float);
-    if (int e_ = smem_optin((const void *)k_b_leaf_up_narrow, smem)) return e_;
-    H->trace.begin(kLeafUp, st);
-    k_b_leaf_up_narrow<<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, o32.Ainv.p, o32.Ainv.ld,
-                                                      o32.Ainv.str, ops.identity ? 1 : 0, H->d_D, B.w32, B.h32[L]);
-    H->trace.end(kLeafUp, st);
-  } else if (H->fd.on && H->batch.fast_diag && !ops.identity) {
-    const int mp = H->fd.mp;
-    const size_t smem = (size_t)(5 * m_of(H) * mp + 2 * q * Rp) * sizeof(float);
-    if (int e_ = smem_optin((const void *)k_b_leaf_up_fd, smem)) return e_;
-    H->trace.begin(kLeafUp, st);
-    k_b_leaf_up_fd<<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, H->fd.d32, mp, B.w32,
-                                                  B.h32[L]);
-    H->trace.end(kLeafUp, st);
-  } else if (allow_tc && H->batch.afrag_hi && H->batch.tensor_leaf && H->shared && !ops.identity && Rp % 8 == 0 &&
-             Rp / 8 <= kTcMaxNT &&
-             !H->batch.leaf_split) {
-    const int MT = (q + 15) / 16, KT = (q + 7) / 8, NT = Rp / 8;
-    const size_t smem = (size_t)(round4(2 * p * p) + 2 * KT * 8 * tc_rs(Rp)) * sizeof(float);
-    auto kern = NT == 4 ? k_b_leaf_up_tc<4> : NT == 3 ? k_b_leaf_up_tc<3> : NT == 2 ? k_b_leaf_up_tc<2>
-                                                                                   : k_b_leaf_up_tc<1>;
-    if (int e_ = smem_optin((const void *)kern, smem)) return e_;
-    H->trace.begin(kLeafUp, st);
-    kern<<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, reinterpret_cast<const uint4 *>(H->batch.afrag_hi),
-                                        reinterpret_cast<const uint4 *>(H->batch.afrag_lo), MT, KT, H->d_D, B.w32,
-                                        B.h32[L]);
-    H->trace.end(kLeafUp, st);
-  } else if (allow_tc && H->batch.umma_leaf == 3 && H->batch.ainv_bf && !H->shared && !ops.identity &&
-             (Rp == 16 || Rp == 32) && umma_fits(p, R, Rp)) {
-    // BF16 trial: the first sweep's leaf applies as one BF16 product on the tensor cores
-    const size_t smem = umma_smem_bytes(p, Rp);
-    auto kern = Rp == 32 ? k_b_leaf_up_umma<32, true> : k_b_leaf_up_umma<16, true>;
-    if (int e_ = smem_optin((const void *)kern, smem)) return e_;
-    CUtensorMap map;
-    memcpy(&map, H->batch.ainv_map_bf, sizeof map);
-    H->trace.begin(kLeafUp, st);
-    const int64_t n = H->g.N_int * R;
-    k_b_combo<<<(unsigned)((n + 4 * 256 - 1) / (4 * 256)), 256, 0, st>>>(n, rhs, Rsave, B.r32);
-    kern<<<std::min(leaf.nodes, H->num_sms), kUmmaThreads, smem, st>>>(H->g, leaf.nodes, R, leaf.d_origin, B.r32,
-                                                                      map, H->d_D, B.w32, B.h32[L], H->perr);
-    H->trace.end(kLeafUp, st);
-  } else if ((allow_tc || H->batch.umma_leaf == 2) && (H->batch.umma_leaf == 1 || H->batch.umma_leaf == 2) &&
-             H->batch.ainv_k && !H->shared && !ops.identity &&
-             (Rp == 16 || Rp == 32) && umma_fits(p, R, Rp)) {
-    // per-node leaf operators on the tcgen05 tensor cores (3xTF32), persistent CTAs, after the
-    // stage right-hand side as its own streaming pass (FP64 sum saved, FP32 copy for the products)
-    const size_t smem = umma_smem_bytes(p, Rp);
-    auto kern = Rp == 32 ? k_b_leaf_up_umma<32, false> : k_b_leaf_up_umma<16, false>;
-    if (int e_ = smem_optin((const void *)kern, smem)) return e_;
-    CUtensorMap map;
-    memcpy(&map, H->batch.ainv_map, sizeof map);
-    H->trace.begin(kLeafUp, st);
-    const int64_t n = H->g.N_int * R;
-    k_b_combo<<<(unsigned)((n + 4 * 256 - 1) / (4 * 256)), 256, 0, st>>>(n, rhs, Rsave, B.r32);
-    kern<<<std::min(leaf.nodes, H->num_sms), kUmmaThreads, smem, st>>>(H->g, leaf.nodes, R, leaf.d_origin, B.r32,
-                                                                      map, H->d_D, B.w32, B.h32[L], H->perr);
-    H->trace.end(kLeafUp, st);
-  } else {
-    const size_t smem = (size_t)(round4(2 * p * p) + 2 * q * Rp) * sizeof(float);
-    if (int e_ = smem_optin((const void *)k_b_leaf_up<8>, smem)) return e_;
-    if (int e_ = smem_optin((const void *)k_b_leaf_up<4>, smem)) return e_;
-    H->trace.begin(kLeafUp, st);
-    const float *r32 = nullptr;
-    if (H->batch.leaf_split) {  // stage right-hand side as its own streaming pass
+  if (parts & kSweepLeafUp) {
+    int cps = H->batch.stream_leaf;  // CTAs per SM: fewer where the rings of that many do not fit
+    StreamPlan SPu{};
+    for (; cps > 0; --cps) {
+      SPu = stream_plan(leaf.nodes, q, q, o32.Ainv.ld, o32.Ainv.str, cps, 2 * p * p, H->batch.stream_chunk_kb);
+      if (stream_fits(SPu, 2 * p * p)) break;
+    }
+    const bool stream_up = narrow && cps > 0 && !ops.identity && o32.Ainv.p;
+    if (stream_up) {
+      H->trace.begin(kLeafUp, st);
+      if (int e = launch_stream(H, SPu, cps, o32.Ainv.p,
+                                StreamUp{H->g, R, leaf.d_origin, rhs, Rsave, H->d_D, B.w32, B.h32[L]}, st))
+        return e;
+      H->trace.end(kLeafUp, st);
+    } else if (narrow) {
+      const size_t smem = (size_t)(round4(2 * p * p) + 8 * q + KS * 16 * QQ) * sizeof(float);
+      if (int e_ = smem_optin((const void *)k_b_leaf_up_narrow, smem)) return e_;
+      H->trace.begin(kLeafUp, st);
+      k_b_leaf_up_narrow<<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, o32.Ainv.p, o32.Ainv.ld,
+                                                        o32.Ainv.str, ops.identity ? 1 : 0, H->d_D, B.w32, B.h32[L]);
+      H->trace.end(kLeafUp, st);
+    } else if (H->fd.on && H->batch.fast_diag && !ops.identity) {
+      const int mp = H->fd.mp;
+      const size_t smem = (size_t)(5 * m_of(H) * mp + 2 * q * Rp) * sizeof(float);
+      if (int e_ = smem_optin((const void *)k_b_leaf_up_fd, smem)) return e_;
+      H->trace.begin(kLeafUp, st);
+      k_b_leaf_up_fd<<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, H->fd.d32, mp, B.w32,
+                                                    B.h32[L]);
+      H->trace.end(kLeafUp, st);
+    } else if (allow_tc && H->batch.afrag_hi && H->batch.tensor_leaf && H->shared && !ops.identity && Rp % 8 == 0 &&
+               Rp / 8 <= kTcMaxNT &&
+               !H->batch.leaf_split) {
+      const int MT = (q + 15) / 16, KT = (q + 7) / 8, NT = Rp / 8;
+      const size_t smem = (size_t)(round4(2 * p * p) + 2 * KT * 8 * tc_rs(Rp)) * sizeof(float);
+      auto kern = NT == 4 ? k_b_leaf_up_tc<4> : NT == 3 ? k_b_leaf_up_tc<3> : NT == 2 ? k_b_leaf_up_tc<2>
+                                                                                     : k_b_leaf_up_tc<1>;
+      if (int e_ = smem_optin((const void *)kern, smem)) return e_;
+      H->trace.begin(kLeafUp, st);
+      kern<<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, reinterpret_cast<const uint4 *>(H->batch.afrag_hi),
+                                          reinterpret_cast<const uint4 *>(H->batch.afrag_lo), MT, KT, H->d_D, B.w32,
+                                          B.h32[L]);
+      H->trace.end(kLeafUp, st);
+    } else if (allow_tc && H->batch.umma_leaf == 3 && H->batch.ainv_bf && !H->shared && !ops.identity &&
+               (Rp == 16 || Rp == 32) && umma_fits(p, R, Rp)) {
+      // BF16 trial: the first sweep's leaf applies as one BF16 product on the tensor cores
+      const size_t smem = umma_smem_bytes(p, Rp);
+      auto kern = Rp == 32 ? k_b_leaf_up_umma<32, true> : k_b_leaf_up_umma<16, true>;
+      if (int e_ = smem_optin((const void *)kern, smem)) return e_;
+      CUtensorMap map;
+      memcpy(&map, H->batch.ainv_map_bf, sizeof map);
+      H->trace.begin(kLeafUp, st);
       const int64_t n = H->g.N_int * R;
       k_b_combo<<<(unsigned)((n + 4 * 256 - 1) / (4 * 256)), 256, 0, st>>>(n, rhs, Rsave, B.r32);
-      r32 = B.r32;
+      kern<<<std::min(leaf.nodes, H->num_sms), kUmmaThreads, smem, st>>>(H->g, leaf.nodes, R, leaf.d_origin, B.r32,
+                                                                        map, H->d_D, B.w32, B.h32[L], H->perr);
+      H->trace.end(kLeafUp, st);
+    } else if ((allow_tc || H->batch.umma_leaf == 2) && (H->batch.umma_leaf == 1 || H->batch.umma_leaf == 2) &&
+               H->batch.ainv_k && !H->shared && !ops.identity &&
+               (Rp == 16 || Rp == 32) && umma_fits(p, R, Rp)) {
+      // per-node leaf operators on the tcgen05 tensor cores (3xTF32), persistent CTAs, after the
+      // stage right-hand side as its own streaming pass (FP64 sum saved, FP32 copy for the products)
+      const size_t smem = umma_smem_bytes(p, Rp);
+      auto kern = Rp == 32 ? k_b_leaf_up_umma<32, false> : k_b_leaf_up_umma<16, false>;
+      if (int e_ = smem_optin((const void *)kern, smem)) return e_;
+      CUtensorMap map;
+      memcpy(&map, H->batch.ainv_map, sizeof map);
+      H->trace.begin(kLeafUp, st);
+      const int64_t n = H->g.N_int * R;
+      k_b_combo<<<(unsigned)((n + 4 * 256 - 1) / (4 * 256)), 256, 0, st>>>(n, rhs, Rsave, B.r32);
+      kern<<<std::min(leaf.nodes, H->num_sms), kUmmaThreads, smem, st>>>(H->g, leaf.nodes, R, leaf.d_origin, B.r32,
+                                                                        map, H->d_D, B.w32, B.h32[L], H->perr);
+      H->trace.end(kLeafUp, st);
+    } else {
+      const size_t smem = (size_t)(round4(2 * p * p) + 2 * q * Rp) * sizeof(float);
+      if (int e_ = smem_optin((const void *)k_b_leaf_up<8>, smem)) return e_;
+      if (int e_ = smem_optin((const void *)k_b_leaf_up<4>, smem)) return e_;
+      H->trace.begin(kLeafUp, st);
+      const float *r32 = nullptr;
+      if (H->batch.leaf_split) {  // stage right-hand side as its own streaming pass
+        const int64_t n = H->g.N_int * R;
+        k_b_combo<<<(unsigned)((n + 4 * 256 - 1) / (4 * 256)), 256, 0, st>>>(n, rhs, Rsave, B.r32);
+        r32 = B.r32;
+      }
+      if (tc8)
+        k_b_leaf_up<8><<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, r32, o32.Ainv.p, o32.Ainv.ld,
+                                                      o32.Ainv.str, ops.identity ? 1 : 0, H->d_D, B.w32, B.h32[L]);
+      else
+        k_b_leaf_up<4><<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, r32, o32.Ainv.p, o32.Ainv.ld,
+                                                      o32.Ainv.str, ops.identity ? 1 : 0, H->d_D, B.w32, B.h32[L]);
+      H->trace.end(kLeafUp, st);
     }
-    if (tc8)
-      k_b_leaf_up<8><<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, r32, o32.Ainv.p, o32.Ainv.ld,
-                                                    o32.Ainv.str, ops.identity ? 1 : 0, H->d_D, B.w32, B.h32[L]);
-    else
-      k_b_leaf_up<4><<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, rhs, Rsave, r32, o32.Ainv.p, o32.Ainv.ld,
-                                                    o32.Ainv.str, ops.identity ? 1 : 0, H->d_D, B.w32, B.h32[L]);
-    H->trace.end(kLeafUp, st);
   }
-  // lower levels (small nodes): one dataflow kernel per direction (levels lr .. L-1)
-  int lr = L;
-  while (lr > 0 && L - lr < std::min(kFlowMaxLevels, H->batch.flow_levels) &&
-         H->lev[lr - 1].n3 <= H->batch.flow_n3_max && (int64_t)H->lev[lr - 1].nb * Rp <= 16384)
-    --lr;
-  const int nflow = L - lr;
-  FlowArgs FA{};
-  size_t smem_up = 0, smem_down = 0;
-  int nflags = 0;
-  if (nflow > 0) {
-    FA.nlev = nflow;
-    FA.R = R;
-    FA.Rp = Rp;
-    FA.g = H->g;
-    int n3max = 0, nbmax = 0;
-    for (int t = 0; t < nflow; ++t) {
-      const int l = lr + t;
-      const Level &lv = H->lev[l];
-      FlowLevel &F = FA.lv[t];
-      F.nodes = lv.nodes;
-      F.n3 = lv.n3;
-      F.nb = lv.nb;
-      F.nbc = lv.nbc;
-      F.j3a = lv.j3a;
-      F.j3b = lv.j3b;
-      F.a = lv.a;
-      F.c = lv.c;
-      F.split = lv.split;
-      F.level = l;
-      F.origin = lv.d_origin;
-      F.hsrc = lv.d_hsrc;
-      F.X = o32.X[l].p;
-      F.ldX = o32.X[l].ld;
-      F.strX = o32.X[l].str;
-      F.T = o32.Tcat[l].p;
-      F.ldT = o32.Tcat[l].ld;
-      F.strT = o32.Tcat[l].str;
-      F.S = o32.S[l].p;
-      F.ldS = o32.S[l].ld;
-      F.strS = o32.S[l].str;
-      F.w3 = B.w332[l];
-      F.h = B.h32[l];
-      F.hC = B.h32[l + 1];
-      F.flag0 = nflags;
-      nflags += lv.nodes;
-      n3max = std::max(n3max, lv.n3);
-      nbmax = std::max(nbmax, lv.nb);
-    }
-    FA.ntasks = nflags;
-    FA.sync = B.flow_sync;
-    FA.err = H->perr;
-    FA.jump = jump;
-    FA.g32 = B.g32;
-    FA.uo = uo;
-    FA.limit_ns = 2000000000ull;
-    int nbcmax = 0;
-    for (int t = 0; t < nflow; ++t) nbcmax = std::max(nbcmax, FA.lv[t].nbc);
-    smem_up = ((size_t)round4(2 * nbcmax * R) + 2 * (size_t)n3max * Rp) * sizeof(float);
-    smem_down = ((size_t)nbmax * Rp + (size_t)n3max * R) * sizeof(float);
-    // upward ticket order: deepest level first
-    for (int s2 = 0, t = nflow - 1; t >= 0; --t, ++s2) {
-      FA.seg_t[s2] = t;
-      FA.seg0[s2] = s2 == 0 ? 0 : FA.seg0[s2 - 1] + FA.lv[FA.seg_t[s2 - 1]].nodes;
-    }
-    FA.seg0[nflow] = nflags;
-    if (int e = flow_launch(H, B, FA, true, smem_up, nflags, st)) return e;
-  }
-  // the lowest levels fused per subtree (option): levels [lb, lr)
-  int lup = lr;
-  if (H->batch.sub_levels > 0 && nflow == 0) {
-    const int D = std::min({H->batch.sub_levels, lr, kSubMaxLevels});
-    const int lb = lr - D;
-    const int cg = (R + kSubCols - 1) / kSubCols;
-    if (D >= 2) {
-      SubUp P{};
-      P.lb = lb;
-      P.D = D;
-      P.R = R;
-      P.hleaf = B.h32[lr];
-      P.htop = lb > 0 ? B.h32[lb] : nullptr;
-      P.jump = jump;
-      P.g = H->g;
-      for (int i = 0; i < D; ++i) {
-        const int l = lb + i;
+  if (parts & kSweepMerges) {
+    // lower levels (small nodes): one dataflow kernel per direction (levels lr .. L-1)
+    int lr = L;
+    while (lr > 0 && L - lr < std::min(kFlowMaxLevels, H->batch.flow_levels) &&
+           H->lev[lr - 1].n3 <= H->batch.flow_n3_max && (int64_t)H->lev[lr - 1].nb * Rp <= 16384)
+      --lr;
+    const int nflow = L - lr;
+    FlowArgs FA{};
+    size_t smem_up = 0, smem_down = 0;
+    int nflags = 0;
+    if (nflow > 0) {
+      FA.nlev = nflow;
+      FA.R = R;
+      FA.Rp = Rp;
+      FA.g = H->g;
+      int n3max = 0, nbmax = 0;
+      for (int t = 0; t < nflow; ++t) {
+        const int l = lr + t;
         const Level &lv = H->lev[l];
-        SubLevel &S = P.lv[i];
-        S.w3 = B.w332[l];
-        S.X = o32.X[l].p;
-        S.ldX = o32.X[l].ld;
-        S.strX = o32.X[l].str;
-        S.T = o32.Tcat[l].p;
-        S.ldT = o32.Tcat[l].ld;
-        S.strT = o32.Tcat[l].str;
-        S.hsrc = lv.d_hsrc;
-        S.origin = lv.d_origin;
-        S.nbc = lv.nbc;
-        S.nb = lv.nb;
-        S.n3 = lv.n3;
-        S.j3a = lv.j3a;
-        S.j3b = lv.j3b;
-        S.a = lv.a;
-        S.c = lv.c;
-        S.split = lv.split;
+        FlowLevel &F = FA.lv[t];
+        F.nodes = lv.nodes;
+        F.n3 = lv.n3;
+        F.nb = lv.nb;
+        F.nbc = lv.nbc;
+        F.j3a = lv.j3a;
+        F.j3b = lv.j3b;
+        F.a = lv.a;
+        F.c = lv.c;
+        F.split = lv.split;
+        F.level = l;
+        F.origin = lv.d_origin;
+        F.hsrc = lv.d_hsrc;
+        F.X = o32.X[l].p;
+        F.ldX = o32.X[l].ld;
+        F.strX = o32.X[l].str;
+        F.T = o32.Tcat[l].p;
+        F.ldT = o32.Tcat[l].ld;
+        F.strT = o32.Tcat[l].str;
+        F.S = o32.S[l].p;
+        F.ldS = o32.S[l].ld;
+        F.strS = o32.S[l].str;
+        F.w3 = B.w332[l];
+        F.h = B.h32[l];
+        F.hC = B.h32[l + 1];
+        F.flag0 = nflags;
+        nflags += lv.nodes;
+        n3max = std::max(n3max, lv.n3);
+        nbmax = std::max(nbmax, lv.nb);
       }
-      const size_t smem = sub_smem_floats(P) * sizeof(float);
-      if (smem <= 96 * 1024) {
-        if (int e_ = smem_optin((const void *)k_b_up_sub, smem)) return e_;
-        H->trace.begin(kMergeUpW3, st);
-        k_b_up_sub<<<dim3((unsigned)H->lev[lb].nodes, (unsigned)cg), kBT, smem, st>>>(P, (int)sub_buf_floats(P),
-                                                                                    (int)sub_dbuf_floats(P));
-        H->trace.end(kMergeUpW3, st);
-        if (cudaPeekAtLastError() != cudaSuccess) return HPS_ECUDA;
-        lup = lb;
+      FA.ntasks = nflags;
+      FA.sync = B.flow_sync;
+      FA.err = H->perr;
+      FA.jump = jump;
+      FA.g32 = B.g32;
+      FA.uo = uo;
+      FA.limit_ns = 2000000000ull;
+      int nbcmax = 0;
+      for (int t = 0; t < nflow; ++t) nbcmax = std::max(nbcmax, FA.lv[t].nbc);
+      smem_up = ((size_t)round4(2 * nbcmax * R) + 2 * (size_t)n3max * Rp) * sizeof(float);
+      smem_down = ((size_t)nbmax * Rp + (size_t)n3max * R) * sizeof(float);
+      // upward ticket order: deepest level first
+      for (int s2 = 0, t = nflow - 1; t >= 0; --t, ++s2) {
+        FA.seg_t[s2] = t;
+        FA.seg0[s2] = s2 == 0 ? 0 : FA.seg0[s2 - 1] + FA.lv[FA.seg_t[s2 - 1]].nodes;
+      }
+      FA.seg0[nflow] = nflags;
+      if (int e = flow_launch(H, B, FA, true, smem_up, nflags, st)) return e;
+    }
+    // the lowest levels fused per subtree (option): levels [lb, lr)
+    int lup = lr;
+    if (H->batch.sub_levels > 0 && nflow == 0) {
+      const int D = std::min({H->batch.sub_levels, lr, kSubMaxLevels});
+      const int lb = lr - D;
+      const int cg = (R + kSubCols - 1) / kSubCols;
+      if (D >= 2) {
+        SubUp P{};
+        P.lb = lb;
+        P.D = D;
+        P.R = R;
+        P.hleaf = B.h32[lr];
+        P.htop = lb > 0 ? B.h32[lb] : nullptr;
+        P.jump = jump;
+        P.g = H->g;
+        for (int i = 0; i < D; ++i) {
+          const int l = lb + i;
+          const Level &lv = H->lev[l];
+          SubLevel &S = P.lv[i];
+          S.w3 = B.w332[l];
+          S.X = o32.X[l].p;
+          S.ldX = o32.X[l].ld;
+          S.strX = o32.X[l].str;
+          S.T = o32.Tcat[l].p;
+          S.ldT = o32.Tcat[l].ld;
+          S.strT = o32.Tcat[l].str;
+          S.hsrc = lv.d_hsrc;
+          S.origin = lv.d_origin;
+          S.nbc = lv.nbc;
+          S.nb = lv.nb;
+          S.n3 = lv.n3;
+          S.j3a = lv.j3a;
+          S.j3b = lv.j3b;
+          S.a = lv.a;
+          S.c = lv.c;
+          S.split = lv.split;
+        }
+        const size_t smem = sub_smem_floats(P) * sizeof(float);
+        if (smem <= 96 * 1024) {
+          if (int e_ = smem_optin((const void *)k_b_up_sub, smem)) return e_;
+          H->trace.begin(kMergeUpW3, st);
+          k_b_up_sub<<<dim3((unsigned)H->lev[lb].nodes, (unsigned)cg), kBT, smem, st>>>(P, (int)sub_buf_floats(P),
+                                                                                      (int)sub_dbuf_floats(P));
+          H->trace.end(kMergeUpW3, st);
+          if (cudaPeekAtLastError() != cudaSuccess) return HPS_ECUDA;
+          lup = lb;
+        }
       }
     }
-  }
-  for (int l = lup - 1; l >= 0; --l) {
-    const Level &lv = H->lev[l];
-    if (int e = launch_b2(H, B, kMergeUpW3, lv.n3, lv.n3, lv.nodes, R, o32.X[l].p, o32.X[l].ld, o32.X[l].str,
-                          BXDiff{B.h32[l + 1], lv.nbc, lv.j3a, lv.j3b, R, jump, H->g, lv.d_origin, lv.a, lv.c, lv.split},
-                          BEStore{B.w332[l], lv.n3, R}, st))
-      return e;
-    if (l > 0)
-      if (int e = launch_b2(H, B, kMergeUpH, lv.nb, lv.n3, lv.nodes, R, o32.Tcat[l].p, o32.Tcat[l].ld, o32.Tcat[l].str,
-                            BXVec{B.w332[l], lv.n3, R}, BEFlux{lv.d_hsrc, B.h32[l + 1], lv.nbc, lv.nb, R, B.h32[l]}, st))
+    for (int l = lup - 1; l >= 0; --l) {
+      const Level &lv = H->lev[l];
+      if (int e = launch_b2(H, B, kMergeUpW3, lv.n3, lv.n3, lv.nodes, R, o32.X[l].p, o32.X[l].ld, o32.X[l].str,
+                            BXDiff{B.h32[l + 1], lv.nbc, lv.j3a, lv.j3b, R, jump, H->g, lv.d_origin, lv.a, lv.c, lv.split},
+                            BEStore{B.w332[l], lv.n3, R}, st))
         return e;
-  }
-  for (int l = 0; l < lr; ++l) {
-    const Level &lv = H->lev[l];
-    if (int e = launch_b2(H, B, kMergeDown, lv.n3, lv.nb, lv.nodes, R, o32.S[l].p, o32.S[l].ld, o32.S[l].str,
-                          BXBd{H->g, lv.d_origin, lv.a, lv.c, R, B.g32},
-                          BEScatter{H->g, lv.d_origin, lv.a, lv.c, lv.split, lv.n3, R, B.w332[l], B.g32, uo}, st))
-      return e;
-  }
-  if (nflow > 0) {
-    // downward ticket order: top flow level first
-    for (int t = 0; t < nflow; ++t) {
-      FA.seg_t[t] = t;
-      FA.seg0[t] = t == 0 ? 0 : FA.seg0[t - 1] + FA.lv[t - 1].nodes;
+      if (l > 0)
+        if (int e = launch_b2(H, B, kMergeUpH, lv.nb, lv.n3, lv.nodes, R, o32.Tcat[l].p, o32.Tcat[l].ld, o32.Tcat[l].str,
+                              BXVec{B.w332[l], lv.n3, R}, BEFlux{lv.d_hsrc, B.h32[l + 1], lv.nbc, lv.nb, R, B.h32[l]}, st))
+          return e;
     }
-    FA.seg0[nflow] = nflags;
-    if (int e = flow_launch(H, B, FA, false, smem_down, nflags, st)) return e;
+    for (int l = 0; l < lr; ++l) {
+      const Level &lv = H->lev[l];
+      if (int e = launch_b2(H, B, kMergeDown, lv.n3, lv.nb, lv.nodes, R, o32.S[l].p, o32.S[l].ld, o32.S[l].str,
+                            BXBd{H->g, lv.d_origin, lv.a, lv.c, R, B.g32},
+                            BEScatter{H->g, lv.d_origin, lv.a, lv.c, lv.split, lv.n3, R, B.w332[l], B.g32, uo}, st))
+        return e;
+    }
+    if (nflow > 0) {
+      // downward ticket order: top flow level first
+      for (int t = 0; t < nflow; ++t) {
+        FA.seg_t[t] = t;
+        FA.seg0[t] = t == 0 ? 0 : FA.seg0[t - 1] + FA.lv[t - 1].nodes;
+      }
+      FA.seg0[nflow] = nflags;
+      if (int e = flow_launch(H, B, FA, false, smem_down, nflags, st)) return e;
+    }
   }
-  H->trace.begin(kLeafDown, st);
-  int cpd = H->batch.stream_leaf;
-  StreamPlan SPd{};
-  for (; cpd > 0; --cpd) {
-    SPd = stream_plan(leaf.nodes, q, b, o32.Sleaf.ld, o32.Sleaf.str, cpd, 0, H->batch.stream_chunk_kb);
-    if (stream_fits(SPd, 0)) break;
+  if (parts & kSweepLeafDown) {
+    H->trace.begin(kLeafDown, st);
+    int cpd = H->batch.stream_leaf;
+    StreamPlan SPd{};
+    for (; cpd > 0; --cpd) {
+      SPd = stream_plan(leaf.nodes, q, b, o32.Sleaf.ld, o32.Sleaf.str, cpd, 0, H->batch.stream_chunk_kb);
+      if (stream_fits(SPd, 0)) break;
+    }
+    const bool stream_down = narrow && cpd > 0 && !ops.identity && o32.Sleaf.p;
+    if (stream_down) {
+      if (int e = launch_stream(H, SPd, cpd, o32.Sleaf.p, StreamDown{H->g, R, leaf.d_origin, B.w32, B.g32, uo}, st))
+        return e;
+    } else if (narrow)
+      k_b_leaf_down_narrow<<<leaf.nodes, kBT, (size_t)(4 * b + KS * 16 * QQ) * sizeof(float), st>>>(
+          H->g, R, leaf.d_origin, o32.Sleaf.p, o32.Sleaf.ld, o32.Sleaf.str, ops.identity ? 1 : 0, B.w32, B.g32, uo);
+    else if (H->shared && !ops.identity && (size_t)(b * o32.Sleaf.ld + (b + q) * Rp) * sizeof(float) <= 110 * 1024) {
+      const size_t smem = (size_t)(b * o32.Sleaf.ld + (b + q) * Rp) * sizeof(float);
+      const bool t8 = tc8;
+      auto kern = t8 ? k_b_leaf_down_res<8> : k_b_leaf_down_res<4>;
+      if (int e_ = smem_optin((const void *)kern, smem)) return e_;
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBT, smem) != cudaSuccess || per_sm < 1)
+        return HPS_ECUDA;
+      kern<<<std::min(leaf.nodes, per_sm * H->num_sms), kBT, smem, st>>>(H->g, leaf.nodes, R, leaf.d_origin,
+                                                                        o32.Sleaf.p, o32.Sleaf.ld, B.w32, B.g32, uo, ep);
+      epi_done = ep.on != 0;
+    } else {
+      const int staged = (size_t)(b + q) * Rp * sizeof(float) <= 96 * 1024;  // coalesced output through smem
+      const size_t smem = (size_t)(staged ? b + q : b) * Rp * sizeof(float);
+      auto kern = tc8 ? k_b_leaf_down<8> : k_b_leaf_down<4>;
+      if (int e_ = smem_optin((const void *)kern, smem)) return e_;
+      kern<<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, o32.Sleaf.p, o32.Sleaf.ld, o32.Sleaf.str,
+                                          ops.identity ? 1 : 0, staged, B.w32, B.g32, uo);
+    }
+    H->trace.end(kLeafDown, st);
   }
-  const bool stream_down = narrow && cpd > 0 && !ops.identity && o32.Sleaf.p;
-  if (stream_down) {
-    if (int e = launch_stream(H, SPd, cpd, o32.Sleaf.p, StreamDown{H->g, R, leaf.d_origin, B.w32, B.g32, uo}, st))
-      return e;
-  } else if (narrow)
-    k_b_leaf_down_narrow<<<leaf.nodes, kBT, (size_t)(4 * b + KS * 16 * QQ) * sizeof(float), st>>>(
-        H->g, R, leaf.d_origin, o32.Sleaf.p, o32.Sleaf.ld, o32.Sleaf.str, ops.identity ? 1 : 0, B.w32, B.g32, uo);
-  else if (H->shared && !ops.identity && (size_t)(b * o32.Sleaf.ld + (b + q) * Rp) * sizeof(float) <= 110 * 1024) {
-    const size_t smem = (size_t)(b * o32.Sleaf.ld + (b + q) * Rp) * sizeof(float);
-    const bool t8 = tc8;
-    auto kern = t8 ? k_b_leaf_down_res<8> : k_b_leaf_down_res<4>;
-    if (int e_ = smem_optin((const void *)kern, smem)) return e_;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBT, smem) != cudaSuccess || per_sm < 1)
-      return HPS_ECUDA;
-    kern<<<std::min(leaf.nodes, per_sm * H->num_sms), kBT, smem, st>>>(H->g, leaf.nodes, R, leaf.d_origin,
-                                                                      o32.Sleaf.p, o32.Sleaf.ld, B.w32, B.g32, uo, ep);
-    epi_done = ep.on != 0;
-  } else {
-    const int staged = (size_t)(b + q) * Rp * sizeof(float) <= 96 * 1024;  // coalesced output through smem
-    const size_t smem = (size_t)(staged ? b + q : b) * Rp * sizeof(float);
-    auto kern = tc8 ? k_b_leaf_down<8> : k_b_leaf_down<4>;
-    if (int e_ = smem_optin((const void *)kern, smem)) return e_;
-    kern<<<leaf.nodes, kBT, smem, st>>>(H->g, R, leaf.d_origin, o32.Sleaf.p, o32.Sleaf.ld, o32.Sleaf.str,
-                                        ops.identity ? 1 : 0, staged, B.w32, B.g32, uo);
-  }
-  H->trace.end(kLeafDown, st);
   return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
@@ -3735,6 +3890,206 @@ int ark_group(hps_handle *H, BatchWork &B, int R, double *u, double dt, const hp
   }
   bool done = false;
   return refined_solve(H, B, H->ident, H->batch.ident32, R, c, B.Rb, B.Rb, fv, u, refine, 0.0, st, StageEpi{}, done);
+}
+
+// ---- many instances in lockstep: one launch per tree level and operator for all of them -------
+// Instance state of a lockstep step: its handle, work buffers and stream, and the arguments of
+// the sweep in progress (the leaf parts read them on the instance's stream, the grouped merges on
+// the main stream).
+struct LsInst {
+  hps_handle *H;
+  BatchWork *B;
+  int R;
+  double *u;
+  const hps_ark_terms *terms;
+  cudaStream_t st;
+  cudaEvent_t ev;
+  Combo rhs;
+  double *Rsave;
+  const double *jump;
+  UOut uo;
+  StageEpi ep, ep_cur;
+  bool epi_done;
+  bool sa_close;
+};
+
+// The merges of one sweep of every instance: level L_i - 1 - s of instance i at upward step s (w3
+// for all, then h), level s at downward step s, each step one grouped launch per operator.
+int merges_lockstep(std::vector<LsInst> &I, cudaStream_t st) {
+  int maxL = 0;
+  for (const LsInst &x : I) maxL = std::max(maxL, x.H->L);
+  for (int s = 0; s < maxL; ++s) {
+    std::vector<GroupItem<BXDiff, BEStore>> w3;
+    std::vector<GroupItem<BXVec, BEFlux>> hh;
+    for (LsInst &x : I) {
+      const int l = x.H->L - 1 - s;
+      if (l < 0) continue;
+      hps_handle *H = x.H;
+      BatchWork &B = *x.B;
+      const Level &lv = H->lev[l];
+      const OpSet32 &o32 = H->batch.impl32;
+      w3.push_back({H, &B, kMergeUpW3, lv.n3, lv.n3, lv.nodes, x.R, o32.X[l].p, o32.X[l].ld, o32.X[l].str,
+                    BXDiff{B.h32[l + 1], lv.nbc, lv.j3a, lv.j3b, x.R, x.jump, H->g, lv.d_origin, lv.a, lv.c, lv.split},
+                    BEStore{B.w332[l], lv.n3, x.R}});
+      if (l > 0)
+        hh.push_back({H, &B, kMergeUpH, lv.nb, lv.n3, lv.nodes, x.R, o32.Tcat[l].p, o32.Tcat[l].ld, o32.Tcat[l].str,
+                      BXVec{B.w332[l], lv.n3, x.R}, BEFlux{lv.d_hsrc, B.h32[l + 1], lv.nbc, lv.nb, x.R, B.h32[l]}});
+    }
+    if (int e = launch_group(w3, st)) return e;
+    if (int e = launch_group(hh, st)) return e;
+  }
+  for (int s = 0; s < maxL; ++s) {
+    std::vector<GroupItem<BXBd, BEScatter>> dn;
+    for (LsInst &x : I) {
+      if (s >= x.H->L) continue;
+      hps_handle *H = x.H;
+      BatchWork &B = *x.B;
+      const Level &lv = H->lev[s];
+      const OpSet32 &o32 = H->batch.impl32;
+      dn.push_back({H, &B, kMergeDown, lv.n3, lv.nb, lv.nodes, x.R, o32.S[s].p, o32.S[s].ld, o32.S[s].str,
+                    BXBd{H->g, lv.d_origin, lv.a, lv.c, x.R, B.g32},
+                    BEScatter{H->g, lv.d_origin, lv.a, lv.c, lv.split, lv.n3, x.R, B.w332[s], B.g32, x.uo}});
+    }
+    if (int e = launch_group(dn, st)) return e;
+  }
+  return HPS_OK;
+}
+
+// One FP32 sweep of every instance: leaf parts on the instances' streams, merges grouped on `st`.
+int sweep_lockstep(std::vector<LsInst> &I, bool allow_tc, cudaStream_t st, cudaEvent_t evm) {
+  for (LsInst &x : I) {
+    if (int e = sweep32(x.H, *x.B, x.H->impl, x.H->batch.impl32, x.R, x.rhs, x.Rsave, x.jump, x.uo, allow_tc, x.st,
+                        x.ep_cur, x.epi_done, kSweepLeafUp))
+      return e;
+    if (cudaEventRecord(x.ev, x.st) != cudaSuccess || cudaStreamWaitEvent(st, x.ev, 0) != cudaSuccess) return HPS_ECUDA;
+  }
+  if (int e = merges_lockstep(I, st)) return e;
+  if (cudaEventRecord(evm, st) != cudaSuccess) return HPS_ECUDA;
+  for (LsInst &x : I) {
+    if (cudaStreamWaitEvent(x.st, evm, 0) != cudaSuccess) return HPS_ECUDA;
+    if (int e = sweep32(x.H, *x.B, x.H->impl, x.H->batch.impl32, x.R, x.rhs, x.Rsave, x.jump, x.uo, allow_tc, x.st,
+                        x.ep_cur, x.epi_done, kSweepLeafDown))
+      return e;
+  }
+  return HPS_OK;
+}
+
+// The batched ARK step (ark_group) of every instance in lockstep: the same stages and refinement
+// sweeps, each sweep through sweep_lockstep; the explicit evaluations, residuals, epilogues and the
+// close per instance on its own stream.
+int ark_lockstep(std::vector<LsInst> &I, double dt, int refine, const ArkTable &tb, cudaStream_t st, cudaEvent_t evm) {
+  const double gam = tb.A[1][1];
+  const StageEpi none{};
+  for (LsInst &x : I) {  // stage 1: gamma dt L u^n, dt (q_1 + g(u^n))
+    const hps_ark_terms *t = x.terms;
+    Leaf64Args E = leaf64_args(x.H, kEval, x.R);
+    E.u = x.u;
+    E.out0 = x.B->KL;
+    E.out1 = x.B->KE;
+    E.q = t ? t->q : nullptr;
+    E.qld = x.R;
+    E.qoff = 0;
+    E.dt = dt;
+    E.dtL = gam * dt;
+    E.g_kind = t ? t->g_kind : HPS_G_NONE;
+    E.gp0 = t ? t->g_param[0] : 0.0;
+    E.gp1 = t ? t->g_param[1] : 0.0;
+    if (int e = leaf64(x.H, E, x.st)) return e;
+    x.sa_close = x.H->batch.sa_close;
+    for (int j = 0; j < 6; ++j) x.sa_close = x.sa_close && tb.A[5][j] == tb.b[j];
+  }
+  for (int i = 1; i < 6; ++i) {
+    for (LsInst &x : I) {  // the stage's right-hand side, boundary data, epilogue
+      const hps_ark_terms *t = x.terms;
+      BatchWork &B = *x.B;
+      const int64_t ni = x.H->g.N_int * x.R;
+      Combo c{};
+      add_term_b(c, x.u, 1.0);
+      for (int j = 0; j < i; ++j) {
+        add_term_b(c, B.KL + j * ni, tb.A[i][j] / gam);
+        add_term_b(c, B.KE + j * ni, tb.Ah[i][j]);
+      }
+      const int gk = t ? t->g_kind : HPS_G_NONE;
+      const double *qi = t && t->q ? t->q + i * ni : nullptr;
+      const bool fuse = x.H->batch.fuse_epilogue && gk != HPS_G_BURGERS;
+      double *kl = x.sa_close && i == 5 ? nullptr : B.KL + i * ni;
+      x.ep = StageEpi{fuse ? 1 : 0, B.Rb, kl, B.KE + i * ni, qi, x.R, 0, gk, dt, dt * (t ? t->g_param[0] : 0.0)};
+      const GridDims &g = x.H->g;
+      const double *fi = t && t->f ? t->f + i * g.N_bd * (int64_t)x.R : nullptr;
+      k_b_set_boundary32<<<blocks(g.N_bd * x.R), 256, 0, x.st>>>(g, x.R, B.g32, fi, x.R, 0, B.ustage);
+      x.rhs = c;
+      x.Rsave = B.Rb;
+      x.jump = nullptr;
+      x.uo = UOut{B.ustage, 1};
+      x.ep_cur = refine == 0 ? x.ep : none;
+      x.epi_done = false;
+    }
+    if (int e = sweep_lockstep(I, true, st, evm)) return e;
+    for (int it = 0; it < refine; ++it) {
+      for (LsInst &x : I) {  // the residual of the stage system, the correction's right-hand side
+        BatchWork &B = *x.B;
+        if (int e = residual(x.H, B, x.R, B.ustage, B.Rb, x.H->gamma_dt, x.st)) return e;
+        k_b_set_boundary32<<<blocks(x.H->g.N_bd * x.R), 256, 0, x.st>>>(x.H->g, x.R, B.g32, nullptr, 0, 0, nullptr);
+        Combo cr{};
+        cr.n = 1;
+        cr.ptr[0] = B.r;
+        cr.coef[0] = 1.0;
+        x.rhs = cr;
+        x.Rsave = nullptr;
+        x.jump = B.r;
+        x.uo = UOut{B.ustage, 0};
+        x.ep_cur = it == refine - 1 ? x.ep : none;
+      }
+      if (int e = sweep_lockstep(I, false, st, evm)) return e;
+    }
+    for (LsInst &x : I) {  // the stage epilogue where the last leaf kernel could not write it
+      if (x.epi_done) continue;
+      const hps_ark_terms *t = x.terms;
+      BatchWork &B = *x.B;
+      const int64_t ni = x.H->g.N_int * x.R;
+      Leaf64Args P = leaf64_args(x.H, kEpilogue, x.R);
+      P.u = B.ustage;
+      P.Rb = B.Rb;
+      P.out0 = B.KL + i * ni;
+      P.out1 = B.KE + i * ni;
+      P.q = t && t->q ? t->q + i * ni : nullptr;
+      P.qld = x.R;
+      P.qoff = 0;
+      P.dt = dt;
+      P.g_kind = t ? t->g_kind : HPS_G_NONE;
+      P.gp0 = t ? t->g_param[0] : 0.0;
+      P.gp1 = t ? t->g_param[1] : 0.0;
+      if (int e = leaf64(x.H, P, x.st)) return e;
+    }
+  }
+  for (LsInst &x : I) {  // the step close of each instance
+    const hps_ark_terms *t = x.terms;
+    BatchWork &B = *x.B;
+    const int64_t ni = x.H->g.N_int * x.R;
+    Combo c{};
+    if (x.sa_close) {
+      add_term_b(c, B.ustage, 1.0);
+      for (int j = 0; j < 6; ++j) add_term_b(c, B.KE + j * ni, tb.b[j] - tb.Ah[5][j]);
+    } else {
+      add_term_b(c, x.u, 1.0);
+      for (int j = 0; j < 6; ++j) {
+        add_term_b(c, B.KL + j * ni, tb.b[j] / gam);
+        add_term_b(c, B.KE + j * ni, tb.b[j]);
+      }
+    }
+    const GridDims &g = x.H->g;
+    const BdView fv{t && t->f ? t->f + 5 * g.N_bd * (int64_t)x.R : nullptr, x.R, 0};
+    if (x.H->batch.edge_projection && x.H->d_proj) {
+      k_b_set_boundary32<<<blocks(g.N_bd * x.R), 256, 0, x.st>>>(g, x.R, B.g32, fv.f, fv.ld, fv.off, x.u);
+      if (int e = edge_projection_impl(x.H, x.R, c, x.u, B.r, x.st)) return e;
+    } else {
+      bool done = false;
+      if (int e = refined_solve(x.H, B, x.H->ident, x.H->batch.ident32, x.R, c, B.Rb, B.Rb, fv, x.u, refine, 0.0,
+                                x.st, StageEpi{}, done))
+        return e;
+    }
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
 // One ARK step in slope form (Sec. 3.1, eq. slope0, g = 0) of one group, mixed precision: the
@@ -4219,6 +4574,31 @@ int ark_batch(hps_handle *H, int R, double *u, double dt, const hps_ark_terms *t
     }
     return cudaPeekAtLastError() == cudaSuccess ? HPS_OK : HPS_ECUDA;
   });
+}
+
+// Many instances' batched ARK steps in lockstep (hps_multi with lockstep on): the instances'
+// streams `sts` are forked from `st` by the caller and joined back by it; evs: one event per
+// instance, evm: one for `st`.
+int ark_batch_lockstep(hps_handle *const *h, int n, double *const *u, const int *R, const hps_ark_terms *terms,
+                       double dt, int refine, const ArkTable &tb, cudaStream_t st, const cudaStream_t *sts,
+                       const cudaEvent_t *evs, cudaEvent_t evm) {
+  std::vector<LsInst> I(n);
+  for (int i = 0; i < n; ++i) {
+    hps_handle *H = h[i];
+    if (R[i] > H->batch.Rmax || H->batch.groups != 1) return HPS_EINVAL;
+    if (std::fabs(0.25 * dt - H->gamma_dt) > 1e-12 * H->gamma_dt) return HPS_EDT;
+    const hps_ark_terms *t = terms ? &terms[i] : nullptr;
+    if (t && (t->g_kind < HPS_G_NONE || t->g_kind > HPS_G_BURGERS)) return HPS_EINVAL;
+    LsInst &x = I[i];
+    x.H = H;
+    x.B = &H->batch.work[0];
+    x.R = R[i];
+    x.u = u[i];
+    x.terms = t;
+    x.st = sts[i];
+    x.ev = evs[i];
+  }
+  return ark_lockstep(I, dt, refine, tb, st, evm);
 }
 
 // Batched slope-form step (one column group; the first call allocates the slopes, 7 N + N_bd

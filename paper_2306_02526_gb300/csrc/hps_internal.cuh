@@ -360,6 +360,10 @@ struct ArkTable {
 int ark_slope(hps_handle *H, double *u, double dt, const hps_ark_terms *terms, const ArkTable &tb, cudaStream_t st);
 int ark_slope_batch(hps_handle *H, int R, double *u, double dt, const hps_ark_terms *terms, int refine,
                     const ArkTable &tb, cudaStream_t st);
+ArkTable ark_table();  // the method's ARK tables (api.cu)
+int ark_batch_lockstep(hps_handle *const *h, int n, double *const *u, const int *R, const hps_ark_terms *terms,
+                       double dt, int refine, const ArkTable &tb, cudaStream_t st, const cudaStream_t *sts,
+                       const cudaEvent_t *evs, cudaEvent_t evm);
 int ark_batch(hps_handle *H, int R, double *u, double dt, const hps_ark_terms *terms, int refine, const ArkTable &tb,
               cudaStream_t st);
 int leaf_eval(hps_handle *H, const double *u, double *KL, double *KE, const double *q, double dt,

@@ -4,7 +4,10 @@
 // of different instances run concurrently on the GPU.  In graph mode the whole multi-instance
 // step -- every instance's kernel sequence as one branch -- is recorded into ONE CUDA graph on the
 // second call with the same arguments and replayed afterwards: one graph launch per step for all
-// instances, whatever their tree sizes.
+// instances, whatever their tree sizes.  In lockstep mode the instances' FP32 sweeps share their
+// merge launches: one grouped launch per tree level and merge operator for all instances (upward
+// levels counted from each tree's leaves, downward from the roots), the leaf parts, residuals and
+// epilogues still per instance on its own stream.
 #include <cstring>
 #include <new>
 #include <vector>
@@ -16,7 +19,9 @@ struct hps_multi {
   std::vector<cudaStream_t> st;
   std::vector<cudaEvent_t> join;
   cudaEvent_t fork = nullptr;
+  cudaEvent_t merged = nullptr;  // the grouped merges of a lockstep sweep are done
   bool graph = false;
+  bool lockstep = false;
   cudaStream_t cap = nullptr;
   std::vector<uint64_t> key;  // arguments of the recorded graph
   bool seen = false;
@@ -43,6 +48,17 @@ int enqueue(hps_multi *M, double *const *u, const int *R, const hps_ark_terms *t
             cudaStream_t st) {
   if (cudaEventRecord(M->fork, st) != cudaSuccess) return HPS_ECUDA;
   int err = HPS_OK;
+  if (M->lockstep) {
+    const int n = (int)M->h.size();
+    for (int i = 0; i < n; ++i)
+      if (cudaStreamWaitEvent(M->st[i], M->fork, 0) != cudaSuccess) return HPS_ECUDA;
+    err = hps::ark_batch_lockstep(M->h.data(), n, u, R, terms, dt, refine, hps::ark_table(), st, M->st.data(),
+                                  M->join.data(), M->merged);
+    for (int i = 0; i < n; ++i)
+      if (cudaEventRecord(M->join[i], M->st[i]) != cudaSuccess || cudaStreamWaitEvent(st, M->join[i], 0) != cudaSuccess)
+        return HPS_ECUDA;
+    return err;
+  }
   for (size_t i = 0; i < M->h.size(); ++i) {
     if (cudaStreamWaitEvent(M->st[i], M->fork, 0) != cudaSuccess) return HPS_ECUDA;
     const int e = ark_step_batch(M->h[i], R[i], u[i], 0.0, dt, terms ? &terms[i] : nullptr, refine,
@@ -67,7 +83,8 @@ int hps_multi_create(hps_handle *const *handles, int n, hps_multi **out) {
   M->h.assign(handles, handles + n);
   M->st.assign(n, nullptr);
   M->join.assign(n, nullptr);
-  bool ok = cudaEventCreateWithFlags(&M->fork, cudaEventDisableTiming) == cudaSuccess;
+  bool ok = cudaEventCreateWithFlags(&M->fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&M->merged, cudaEventDisableTiming) == cudaSuccess;
   for (int i = 0; i < n && ok; ++i)
     ok = cudaStreamCreateWithFlags(&M->st[i], cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&M->join[i], cudaEventDisableTiming) == cudaSuccess;
@@ -85,6 +102,17 @@ int hps_multi_set_graph(hps_multi *M, int enable) {
   drop_graph(M);
   M->graph = enable != 0;
   for (hps_handle *h : M->h) h->graph_mode = false;  // the instances' own graphs would nest
+  return HPS_OK;
+}
+
+int hps_multi_set_lockstep(hps_multi *M, int enable) {
+  if (!M) return HPS_EINVAL;
+  if (enable)
+    for (hps_handle *h : M->h)
+      if (h->batch.groups != 1) return HPS_EINVAL;
+  cudaDeviceSynchronize();
+  drop_graph(M);
+  M->lockstep = enable != 0;
   return HPS_OK;
 }
 
@@ -147,6 +175,7 @@ void hps_multi_free(hps_multi *M) {
   for (cudaEvent_t e : M->join)
     if (e) cudaEventDestroy(e);
   if (M->fork) cudaEventDestroy(M->fork);
+  if (M->merged) cudaEventDestroy(M->merged);
   delete M;
 }
 

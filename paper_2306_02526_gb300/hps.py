@@ -355,6 +355,11 @@ class MultiStep:
     def set_graph(self, enable=True):
         check(lib().hps_multi_set_graph(self._h, 1 if enable else 0), "hps_multi_set_graph")
 
+    def set_lockstep(self, enable=True):
+        """One grouped merge launch per tree level for all instances (every solver with one
+        column group)."""
+        check(lib().hps_multi_set_lockstep(self._h, 1 if enable else 0), "hps_multi_set_lockstep")
+
     def ark_step(self, us, dt, g=None, g_param=(1.0, 1.0), refine=1, stream=None):
         """us: one (N_i, R_i) float64 CUDA tensor per instance, advanced in place."""
         n = len(self.solvers)
