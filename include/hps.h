@@ -440,7 +440,16 @@ enum {
   HPS_OPT_EO_THREADS = 31,       /* threads per CTA of the FP64 even-odd leaf kernel (residual,
                                    evaluation): 32..256 in steps of 32; 0 (default): 128 with one
                                    column per pass, else 256                                        */
-  HPS_OPT_COUNT = 32
+  HPS_OPT_PREFETCH_NEXT = 32,    /* 1: each merge apply of an FP32 sweep prefetches the operator
+                                   of the apply after it into L2 (bulk prefetch), so that the
+                                   chain of dependent level applies finds it there (0: off)        */
+  HPS_OPT_B1_ROLL = 33,          /* 1: the one-column merge applies reload each operator register as
+                                   soon as its product is taken (a rolling window of loads in
+                                   flight); 0: batches of loads, each waited for whole            */
+  HPS_OPT_B1_KW = 34,            /* most warps that split K inside a CTA of the one-column merge
+                                   applies (1, 2, 4 or 8; fewer: longer contiguous operator rows per
+                                   CTA)                                                          */
+  HPS_OPT_COUNT = 35
 };
 int hps_batch_set_option(hps_handle *h, int opt, int value);
 

@@ -1676,6 +1676,24 @@ struct BEScatter {  // interface values: FP32 for the levels below, and into the
   }
 };
 
+// An operator range to prefetch into L2 (the next apply's operator; p null: none).  p is 16-byte
+// aligned and bytes a multiple of 16 (a cudaMalloc'd operator of rows padded to 4 floats).
+struct Pf {
+  const char *p;
+  int64_t bytes;
+};
+
+// This CTA's share of the prefetch (CTA `cta` of `nctas`): pieces of 32 KB, one per lane of the
+// first warp at a time.
+__device__ __forceinline__ void prefetch_share(const Pf &f, int64_t cta, int64_t nctas) {
+  if (!f.p || threadIdx.x >= 32) return;
+  const int64_t units = f.bytes >> 4, per = (units + nctas - 1) / nctas;
+  const int64_t u0 = cta * per, u1 = min(units, u0 + per);
+  constexpr int64_t kPiece = 2048;  // 16-byte units
+  for (int64_t u = u0 + (int64_t)threadIdx.x * kPiece; u < u1; u += 32 * kPiece)
+    tc5::bulk_prefetch_l2(f.p + (u << 4), (unsigned)(min(kPiece, u1 - u) << 4));
+}
+
 // The body of one CTA (block bx, K chunk by) of a merge apply; k_b_gemv runs it for its own grid,
 // k_b_gemv_group for the blocks of many instances' applies in one launch.
 template <int TC, class XL, class EP>
@@ -1792,7 +1810,9 @@ __device__ __forceinline__ void gemv_tile(const BPlan &P, const float *__restric
 
 template <int TC, class XL, class EP>
 __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict__ AT, int ld, int64_t str, XL xl,
-                                                EP ep, float *__restrict__ partial, unsigned *__restrict__ tile_count) {
+                                                EP ep, float *__restrict__ partial, unsigned *__restrict__ tile_count,
+                                                Pf pf) {
+  prefetch_share(pf, blockIdx.x + (int64_t)blockIdx.y * gridDim.x, (int64_t)gridDim.x * gridDim.y);
   gemv_tile<TC>(P, AT, ld, str, xl, ep, partial, tile_count, (int)blockIdx.x, (int)blockIdx.y);
 }
 
@@ -1825,7 +1845,7 @@ __global__ void k_b_reduce(BPlan P, const float *__restrict__ partial, EP ep) {
 
 template <class XL, class EP>
 int launch_b(hps_handle *H, BatchWork &B, int slot, const BPlan &P, const float *AT, int ld, int64_t str, XL xl,
-             EP ep, cudaStream_t st) {
+             EP ep, cudaStream_t st, Pf pf = Pf{}) {
   const size_t smem = b_smem_floats(P) * sizeof(float);
   if (P.ksplit > 1 && (size_t)P.ksplit * P.nodes * P.M * P.Rp > B.partial_len) return HPS_EINVAL;
   if (int e_ = smem_optin((const void *)k_b_gemv<8, XL, EP>, smem)) return e_;
@@ -1839,7 +1859,7 @@ int launch_b(hps_handle *H, BatchWork &B, int slot, const BPlan &P, const float 
   unsigned *tc = in_kernel ? B.tile_count : nullptr;
   const bool pdl = H->batch.pdl;
   auto kern = P.TC == 8 ? k_b_gemv<8, XL, EP> : P.TC == 4 ? k_b_gemv<4, XL, EP> : k_b_gemv<2, XL, EP>;
-  launch_k(pdl, kern, grid, dim3(kBT), smem, st, P, AT, ld, str, xl, ep, B.partial32, tc);
+  launch_k(pdl, kern, grid, dim3(kBT), smem, st, P, AT, ld, str, xl, ep, B.partial32, tc, pf);
   if (P.ksplit > 1 && !in_kernel) {
     const int64_t n = (int64_t)P.nodes * P.M * (P.Rp / 4);
     launch_k(pdl, k_b_reduce<EP>, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, P,
@@ -1995,14 +2015,14 @@ struct BPlan1 {
   int64_t quads;
 };
 
-BPlan1 plan_b1(int M, int K, int nodes, int target) {
+BPlan1 plan_b1(int M, int K, int nodes, int target, int kw_max = 8) {
   BPlan1 P{};
   P.M = M;
   P.K = K;
   P.nodes = nodes;
   P.QN = (M + 3) / 4;
   P.quads = (int64_t)nodes * P.QN;
-  P.kw = 8;
+  P.kw = kw_max;
   while (P.kw > 1 && K / P.kw < 16) P.kw /= 2;  // at least 16 columns per warp
   P.qcta = 32 * (8 / P.kw);
   const int64_t gx = (P.quads + P.qcta - 1) / P.qcta;
@@ -2018,9 +2038,13 @@ BPlan1 plan_b1(int M, int K, int nodes, int target) {
 // right-hand side is an FP64 gather per entry).
 __host__ __device__ inline int64_t b1_node_span(const BPlan1 &P) { return P.qcta / P.QN + 2; }
 
-template <class XL, class EP>
+// ROLL: each operator register is reloaded as soon as its product is taken (a rolling window of
+// kU loads in flight per thread); else the kU loads go out as a batch after the batch's products.
+// Both add the columns in the same order (bit-identical results).
+template <class XL, class EP, bool ROLL>
 __global__ void __launch_bounds__(kBT) k_b_gemv1(BPlan1 P, const float *__restrict__ AT, int ld, int64_t str, XL xl,
-                                                 EP ep, float *__restrict__ partial, unsigned *__restrict__ tile_count) {
+                                                 EP ep, float *__restrict__ partial, unsigned *__restrict__ tile_count,
+                                                 Pf pf) {
   __shared__ float4 red[kBT / 32][32];
   extern __shared__ float xs1[];  // [node - n0][c - c0]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -2041,6 +2065,7 @@ __global__ void __launch_bounds__(kBT) k_b_gemv1(BPlan1 P, const float *__restri
 #pragma unroll
   for (int u = 0; u < kU; ++u)
     if (live && c + u * step < c1) av[u] = __ldg(reinterpret_cast<const float4 *>(a + (int64_t)(c + u * step) * ld));
+  prefetch_share(pf, blockIdx.x + (int64_t)blockIdx.y * gridDim.x, (int64_t)gridDim.x * gridDim.y);
   pdl_wait();
   for (int i = threadIdx.x; i < (n1 - n0 + 1) * klen; i += blockDim.x) {
     const int nn = i / klen, cc = i - nn * klen;
@@ -2048,7 +2073,24 @@ __global__ void __launch_bounds__(kBT) k_b_gemv1(BPlan1 P, const float *__restri
   }
   __syncthreads();
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (live) {
+  if (live && ROLL) {
+    const float *x = xs1 + (int64_t)(node - n0) * klen - c0;
+    for (; c < c1; c += kU * step) {
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int cu = c + u * step;
+        if (cu < c1) {
+          const float xv = x[cu];
+          acc.x = fmaf(av[u].x, xv, acc.x);
+          acc.y = fmaf(av[u].y, xv, acc.y);
+          acc.z = fmaf(av[u].z, xv, acc.z);
+          acc.w = fmaf(av[u].w, xv, acc.w);
+          const int cn = cu + kU * step;
+          if (cn < c1) av[u] = __ldg(reinterpret_cast<const float4 *>(a + (int64_t)cn * ld));
+        }
+      }
+    }
+  } else if (live) {
     const float *x = xs1 + (int64_t)(node - n0) * klen - c0;
     for (;;) {
 #pragma unroll
@@ -2123,20 +2165,21 @@ __global__ void __launch_bounds__(kBT) k_b_gemv1(BPlan1 P, const float *__restri
 
 template <class XL, class EP>
 int launch_b1(hps_handle *H, BatchWork &B, int slot, int M, int K, int nodes, const float *AT, int ld, int64_t str,
-              XL xl, EP ep, cudaStream_t st, bool *done) {
+              XL xl, EP ep, cudaStream_t st, bool *done, Pf pf = Pf{}) {
   *done = false;
-  const BPlan1 P = plan_b1(M, K, nodes, 4 * H->num_sms);
+  const BPlan1 P = plan_b1(M, K, nodes, 4 * H->num_sms, H->batch.b1_kw);
   const int64_t gx = (P.quads + P.qcta - 1) / P.qcta;
   // split-K sums inside the kernel (last CTA of a quad block) where the counters reach
   unsigned *tc = H->batch.one_column_merge_sum && gx <= (int64_t)B.tile_count_len ? B.tile_count : nullptr;
   if (P.ks > 1 && (size_t)P.ks * nodes * M * (tc ? 1 : 4) > B.partial_len) return HPS_OK;  // the general path
   const size_t smem = (size_t)b1_node_span(P) * P.kchunk * sizeof(float);
   if (smem > 96 * 1024) return HPS_OK;
-  if (int e_ = smem_optin((const void *)k_b_gemv1<XL, EP>, smem)) return e_;
+  auto kern = H->batch.b1_roll ? k_b_gemv1<XL, EP, true> : k_b_gemv1<XL, EP, false>;
+  if (int e_ = smem_optin((const void *)kern, smem)) return e_;
   *done = true;
   H->trace.begin(slot, st);
-  launch_k(H->batch.pdl, k_b_gemv1<XL, EP>, dim3((unsigned)gx, (unsigned)P.ks), dim3(kBT), smem, st, P, AT, ld, str, xl,
-           ep, B.partial32, tc);
+  launch_k(H->batch.pdl, kern, dim3((unsigned)gx, (unsigned)P.ks), dim3(kBT), smem, st, P, AT, ld, str, xl,
+           ep, B.partial32, tc, pf);
   if (P.ks > 1 && !tc) {
     BPlan R4{};
     R4.M = M;
@@ -2371,19 +2414,19 @@ __global__ void __launch_bounds__(kBT) k_b_up_sub(SubUp P, int hmax, int dmax) {
 // does not fit in shared memory) the split-K kernel with partial sums in global memory.
 template <class XL, class EP>
 int launch_b2(hps_handle *H, BatchWork &B, int slot, int M, int K, int nodes, int R, const float *AT, int ld,
-              int64_t str, XL xl, EP ep, cudaStream_t st) {
+              int64_t str, XL xl, EP ep, cudaStream_t st, Pf pf = Pf{}) {
   // per-node operators, one column: streaming applies (the small interface solves w3 = X d of the
   // lower levels stay on the tiled kernel, which measured faster there)
   if (R == 1 && str != 0 && H->batch.one_column_merge && !(slot == kMergeUpW3 && M < 128)) {
     bool done = false;
-    if (int e = launch_b1(H, B, slot, M, K, nodes, AT, ld, str, xl, ep, st, &done)) return e;
+    if (int e = launch_b1(H, B, slot, M, K, nodes, AT, ld, str, xl, ep, st, &done, pf)) return e;
     if (done) return HPS_OK;
   }
   const BPlan2 P = plan_b2(M, K, nodes, R);
   const size_t smem = b2_smem(P);
   if (!H->batch.gemv2 || smem > kB2MaxSmem)
     return launch_b(H, B, slot, plan_b(M, K, nodes, R, plan_target(H), str == 0, plan_tune(H, slot)), AT, ld, str,
-                    xl, ep, st);
+                    xl, ep, st, pf);
   auto kern = P.TC == 8 ? k_b_gemv2<8, XL, EP> : k_b_gemv2<4, XL, EP>;
   if (int e_ = smem_optin((const void *)kern, smem)) return e_;
   cudaLaunchConfig_t cfg{};
@@ -3244,6 +3287,12 @@ int umma_bf16_reserve(hps_handle *H) {
   return cudaDeviceSynchronize() == cudaSuccess ? HPS_OK : HPS_ECUDA;
 }
 
+// The bytes of an FP32 operator set of `nodes` nodes with `cols` columns (as convert_op lays it out).
+Pf op_range(const Op32 &o, int cols, int nodes) {
+  if (!o.p) return Pf{};
+  return Pf{reinterpret_cast<const char *>(o.p), (o.str ? (int64_t)nodes : 1) * cols * (int64_t)o.ld * (int64_t)sizeof(float)};
+}
+
 // FP32 copy of a transposed operator (rows x cols per node) with rows padded to 4 floats.
 int convert_op(hps_handle *H, const double *src, int ld64, int64_t str64, int rows, int cols, int64_t nops, Op32 &o) {
   if (!src) return HPS_OK;
@@ -3536,22 +3585,30 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
         }
       }
     }
+    // (option) each apply prefetches the operator of the apply after it into L2
+    const bool pfn = H->batch.prefetch_next && !H->shared;
+    auto opS = [&](int l) { return pfn && l < lr ? op_range(o32.S[l], H->lev[l].nb, H->lev[l].nodes) : Pf{}; };
     for (int l = lup - 1; l >= 0; --l) {
       const Level &lv = H->lev[l];
+      const Pf nw3 = !pfn ? Pf{} : l > 0 ? op_range(o32.Tcat[l], lv.n3, lv.nodes) : opS(0);
       if (int e = launch_b2(H, B, kMergeUpW3, lv.n3, lv.n3, lv.nodes, R, o32.X[l].p, o32.X[l].ld, o32.X[l].str,
                             BXDiff{B.h32[l + 1], lv.nbc, lv.j3a, lv.j3b, R, jump, H->g, lv.d_origin, lv.a, lv.c, lv.split},
-                            BEStore{B.w332[l], lv.n3, R}, st))
+                            BEStore{B.w332[l], lv.n3, R}, st, nw3))
         return e;
-      if (l > 0)
+      if (l > 0) {
+        const Pf nh = pfn ? op_range(o32.X[l - 1], H->lev[l - 1].n3, H->lev[l - 1].nodes) : Pf{};
         if (int e = launch_b2(H, B, kMergeUpH, lv.nb, lv.n3, lv.nodes, R, o32.Tcat[l].p, o32.Tcat[l].ld, o32.Tcat[l].str,
-                              BXVec{B.w332[l], lv.n3, R}, BEFlux{lv.d_hsrc, B.h32[l + 1], lv.nbc, lv.nb, R, B.h32[l]}, st))
+                              BXVec{B.w332[l], lv.n3, R}, BEFlux{lv.d_hsrc, B.h32[l + 1], lv.nbc, lv.nb, R, B.h32[l]}, st,
+                              nh))
           return e;
+      }
     }
     for (int l = 0; l < lr; ++l) {
       const Level &lv = H->lev[l];
       if (int e = launch_b2(H, B, kMergeDown, lv.n3, lv.nb, lv.nodes, R, o32.S[l].p, o32.S[l].ld, o32.S[l].str,
                             BXBd{H->g, lv.d_origin, lv.a, lv.c, R, B.g32},
-                            BEScatter{H->g, lv.d_origin, lv.a, lv.c, lv.split, lv.n3, R, B.w332[l], B.g32, uo}, st))
+                            BEScatter{H->g, lv.d_origin, lv.a, lv.c, lv.split, lv.n3, R, B.w332[l], B.g32, uo}, st,
+                            opS(l + 1)))
         return e;
     }
     if (nflow > 0) {
@@ -4373,6 +4430,9 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
     case HPS_OPT_SUB_LEVELS: field = &Bt.sub_levels; break;
     case HPS_OPT_PDL: flag = &Bt.pdl; break;
     case HPS_OPT_EO_THREADS: field = &Bt.eo_threads; break;
+    case HPS_OPT_PREFETCH_NEXT: flag = &Bt.prefetch_next; break;
+    case HPS_OPT_B1_ROLL: flag = &Bt.b1_roll; break;
+    case HPS_OPT_B1_KW: field = &Bt.b1_kw; break;
     case HPS_OPT_EVEN_ODD: flag = &Bt.even_odd; break;
     case HPS_OPT_FLOW_LEVELS: field = &Bt.flow_levels; break;
     case HPS_OPT_FLOW_N3_MAX: field = &Bt.flow_n3_max; break;
@@ -4413,6 +4473,7 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
   if (opt == HPS_OPT_STREAM_CHUNK_KB && (v < 2 || v > 64)) return HPS_EINVAL;
   if (opt == HPS_OPT_SUB_LEVELS && v > kSubMaxLevels) return HPS_EINVAL;
   if (opt == HPS_OPT_EO_THREADS && (v % 32 != 0 || v > kBT)) return HPS_EINVAL;
+  if (opt == HPS_OPT_B1_KW && v != 1 && v != 2 && v != 4 && v != 8) return HPS_EINVAL;
   if (opt == HPS_OPT_UMMA_LEAF && v == 3)
     if (int e = umma_bf16_reserve(H)) return e;
   if (opt == HPS_OPT_FP64_PLAN_TARGET) {  // FP64 split plans: not while the persistent kernel holds tasks

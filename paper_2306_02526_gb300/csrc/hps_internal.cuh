@@ -193,6 +193,9 @@ struct Batch {
   int stream_chunk_kb = 24;  // ... in chunks of about this many KB
   int sub_levels = 0;        // lowest merge levels of the upward sweep fused per subtree (0: per level)
   bool pdl = false;          // merge applies launched as programmatic dependents of the kernel before
+  bool prefetch_next = false;
+  bool b1_roll = false;  // one-column merge applies: rolling operator loads
+  int b1_kw = 8;         // one-column merge applies: most warps splitting K in a CTA  // merge applies prefetch the next apply's operator into L2
   int eo_threads = 0;        // threads per CTA of the FP64 even-odd leaf kernel (0: 128 for one column per pass, else 256)
   void *ainv_bf = nullptr;       // BF16 trial: their BF16 copy, K-major [leaf][row][round8(q)]
   uint64_t ainv_map_bf[16] = {}; // its TMA tensor map

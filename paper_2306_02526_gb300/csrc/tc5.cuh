@@ -82,6 +82,12 @@ __device__ __forceinline__ void bulk_load_hint(void *dst, const void *src, unsig
       ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
       : "memory");
 }
+// Bulk prefetch of [src, src + bytes) into L2 (src 16-byte aligned, bytes a multiple of 16): a
+// hint, nothing waits for it.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<uint64_t>(src)), "r"(bytes)
+               : "memory");
+}
 // L2 policy: lines of the accesses it tags are evicted first (data used once).
 __device__ __forceinline__ uint64_t policy_evict_first() {
   uint64_t p;
