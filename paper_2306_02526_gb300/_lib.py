@@ -73,7 +73,7 @@ BATCH_OPTIONS = ("tensor_leaf", "even_odd", "flow_levels", "flow_n3_max", "clust
                  "fp64_plan_target", "umma_leaf", "one_column_merge",
                  "one_column_sum", "stream_leaf",
                  "stream_chunk_kb", "sub_levels", "pdl",
-                 "eo_threads", "prefetch_next", "b1_roll", "b1_kw")
+                 "eo_threads", "prefetch_next", "b1_roll", "b1_kw", "stream_prefetch")
 
 
 class hps_server_stats(ctypes.Structure):

@@ -1281,6 +1281,7 @@ struct StreamUp {
   double *Rsave;
   const double *Dg;
   float *w32, *h32;
+  static constexpr int kPre = 0, kEpi = 0;  // (no per-leaf register prefetch)
   __host__ __device__ int role_floats() const { return 2 * g.p * g.p; }
   __device__ void setup(float *rs, int t0, int nt) const {
     for (int i = t0; i < 2 * g.p * g.p; i += nt) rs[i] = (float)Dg[i];
@@ -1304,8 +1305,57 @@ struct StreamDown {
   const int *origin;
   const float *w32, *g32;
   UOut uo;
-  __host__ __device__ int role_floats() const { return 0; }
+  // pre: the next leaf's boundary values and this leaf's w (and u, when adding to it) are loaded
+  // into registers before this leaf's products and stored after them (a second xs buffer in the
+  // role's floats), so no per-leaf load latency stalls the stream
+  bool pre;
+  static constexpr int kPre = 2, kEpi = 2;  // registers per consumer thread (4 b <= 480 for p <= 32)
+  __host__ __device__ int role_floats() const { return pre ? 16 * g.m : 0; }
   __device__ void setup(float *, int, int) const {}
+  __device__ float bd_value(int ix, int iy, int i) const {
+    const int pos = i >> 2, j = i & 3;
+    return j < R ? g32[box_bd(g, ix, iy, 1, 1, pos) * R + j] : 0.f;
+  }
+  __device__ void pre_load(int k, float (&v)[kPre], int t0, int nt) const {
+    const int b = 4 * g.m, ix = origin[2 * k], iy = origin[2 * k + 1];
+#pragma unroll
+    for (int s = 0; s < kPre; ++s) v[s] = t0 + s * nt < 4 * b ? bd_value(ix, iy, t0 + s * nt) : 0.f;
+  }
+  __device__ void pre_store(int k, const float (&v)[kPre], float *xs, int t0, int nt) const {
+    const int b = 4 * g.m;
+#pragma unroll
+    for (int s = 0; s < kPre; ++s)
+      if (t0 + s * nt < 4 * b) xs[t0 + s * nt] = v[s];
+    for (int i = t0 + kPre * nt; i < 4 * b; i += nt) xs[i] = bd_value(origin[2 * k], origin[2 * k + 1], i);
+  }
+  __device__ void epi_load(int k, float (&w)[kEpi], double (&u0)[kEpi], int t0, int nt) const {
+    const int q = g.m * g.m;
+    const int64_t l0 = ((int64_t)origin[2 * k + 1] * g.n1 + origin[2 * k]) * q;
+#pragma unroll
+    for (int s = 0; s < kEpi; ++s) {
+      const int idx = t0 + s * nt;
+      w[s] = idx < q * R ? w32[(int64_t)k * q * R + idx] : 0.f;
+      u0[s] = idx < q * R && !uo.assign ? uo.u[l0 * R + idx] : 0.0;
+    }
+  }
+  __device__ void epilogue_pre(int k, const float *ys, const float (&w)[kEpi], const double (&u0)[kEpi], int t0,
+                               int nt) const {
+    const int q = g.m * g.m;
+    const int64_t l0 = ((int64_t)origin[2 * k + 1] * g.n1 + origin[2 * k]) * q;
+#pragma unroll
+    for (int s = 0; s < kEpi; ++s) {
+      const int idx = t0 + s * nt;
+      if (idx < q * R) {
+        const int r = idx / R, j = idx - r * R;
+        const double d = f2d_int(w[s] + ys[r * 4 + j]);
+        uo.u[l0 * R + idx] = uo.assign ? d : u0[s] + d;
+      }
+    }
+    for (int idx = t0 + kEpi * nt; idx < q * R; idx += nt) {
+      const int r = idx / R, j = idx - r * R;
+      u_out(uo, l0 * R + idx, w32[(int64_t)k * q * R + idx] + ys[r * 4 + j]);
+    }
+  }
   __device__ void prologue(int k, float *xs, float *, int t0, int nt) const {
     const int b = 4 * g.m, ix = origin[2 * k], iy = origin[2 * k + 1];
     for (int i = t0; i < b * 4; i += nt) {
@@ -1375,9 +1425,31 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
     const int rq = ct % P.QQ, ks = ct / P.QQ;
     const bool live = ks < P.KS;
     bool failed = false;
+    constexpr bool kRegs = Role::kPre > 0;  // the role can carry per-leaf loads in registers
+    float pv[kRegs ? Role::kPre : 1], wv[kRegs ? Role::kEpi : 1];
+    double uv[kRegs ? Role::kEpi : 1];
+    bool pre = false;
+    if constexpr (kRegs) {
+      pre = role.pre;
+      if (pre && nl > 0) {
+        role.pre_load((int)blockIdx.x, pv, ct, kStreamConsumers);
+        role.pre_store((int)blockIdx.x, pv, xs, ct, kStreamConsumers);
+      }
+    }
     for (int j = 0; j < nl; ++j) {
       const int k = (int)blockIdx.x + j * (int)gridDim.x;
-      role.prologue(k, xs, rs, ct, kStreamConsumers);
+      float *xsj = xs;  // this leaf's right-hand side (alternating buffers with pre)
+      if constexpr (kRegs) {
+        if (pre) {
+          xsj = (j & 1) ? rs : xs;
+          role.epi_load(k, wv, uv, ct, kStreamConsumers);
+          if (j + 1 < nl) role.pre_load(k + (int)gridDim.x, pv, ct, kStreamConsumers);
+        } else {
+          role.prologue(k, xs, rs, ct, kStreamConsumers);
+        }
+      } else {
+        role.prologue(k, xs, rs, ct, kStreamConsumers);
+      }
       consumer_sync();
       float acc[4][RC];
 #pragma unroll
@@ -1389,7 +1461,7 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
         if (!failed && !umma_wait(&full[s], (unsigned)(c / S) & 1u, abort_flag)) failed = true;
         if (!failed && live) {
           const float *a = ring + (size_t)s * stage_f + 4 * rq;
-          const float *x = xs + 4 * i * P.C;
+          const float *x = xsj + 4 * i * P.C;
           const int cols = min(P.C, P.K - i * P.C);
           if constexpr (RC == 1) {
 #pragma unroll 4
@@ -1424,7 +1496,16 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
         ys[idx] = v;
       }
       consumer_sync();
-      role.epilogue(k, ys, rs, ct, kStreamConsumers);
+      if constexpr (kRegs) {
+        if (pre) {  // the next leaf's right-hand side into the other buffer (read after the sync below)
+          if (j + 1 < nl) role.pre_store(k + (int)gridDim.x, pv, ((j + 1) & 1) ? rs : xs, ct, kStreamConsumers);
+          role.epilogue_pre(k, ys, wv, uv, ct, kStreamConsumers);
+        } else {
+          role.epilogue(k, ys, rs, ct, kStreamConsumers);
+        }
+      } else {
+        role.epilogue(k, ys, rs, ct, kStreamConsumers);
+      }
       if (consumer_sync_or(failed || *abort_flag)) break;  // uniform: every consumer leaves together
     }
   }
@@ -3625,13 +3706,15 @@ int sweep32(hps_handle *H, BatchWork &B, const OpSet &ops, const OpSet32 &o32, i
     H->trace.begin(kLeafDown, st);
     int cpd = H->batch.stream_leaf;
     StreamPlan SPd{};
+    const bool spre = H->batch.stream_prefetch;
+    const int down_floats = spre ? 4 * b : 0;  // (StreamDown::role_floats)
     for (; cpd > 0; --cpd) {
-      SPd = stream_plan(leaf.nodes, q, b, o32.Sleaf.ld, o32.Sleaf.str, cpd, 0, H->batch.stream_chunk_kb);
-      if (stream_fits(SPd, 0)) break;
+      SPd = stream_plan(leaf.nodes, q, b, o32.Sleaf.ld, o32.Sleaf.str, cpd, down_floats, H->batch.stream_chunk_kb);
+      if (stream_fits(SPd, down_floats)) break;
     }
     const bool stream_down = narrow && cpd > 0 && !ops.identity && o32.Sleaf.p;
     if (stream_down) {
-      if (int e = launch_stream(H, SPd, cpd, o32.Sleaf.p, StreamDown{H->g, R, leaf.d_origin, B.w32, B.g32, uo}, st))
+      if (int e = launch_stream(H, SPd, cpd, o32.Sleaf.p, StreamDown{H->g, R, leaf.d_origin, B.w32, B.g32, uo, spre}, st))
         return e;
     } else if (narrow)
       k_b_leaf_down_narrow<<<leaf.nodes, kBT, (size_t)(4 * b + KS * 16 * QQ) * sizeof(float), st>>>(
@@ -4432,6 +4515,7 @@ int batch_option(hps_handle *H, int opt, const int *set, int *get) {
     case HPS_OPT_EO_THREADS: field = &Bt.eo_threads; break;
     case HPS_OPT_PREFETCH_NEXT: flag = &Bt.prefetch_next; break;
     case HPS_OPT_B1_ROLL: flag = &Bt.b1_roll; break;
+    case HPS_OPT_STREAM_PREFETCH: flag = &Bt.stream_prefetch; break;
     case HPS_OPT_B1_KW: field = &Bt.b1_kw; break;
     case HPS_OPT_EVEN_ODD: flag = &Bt.even_odd; break;
     case HPS_OPT_FLOW_LEVELS: field = &Bt.flow_levels; break;

@@ -28,7 +28,10 @@ VARIANTS = [dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=1, one_colu
             dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=0, one_column_sum=0, prefetch_next=1),
             dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=1, one_column_sum=1, b1_roll=1),
             dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=1, one_column_sum=1, b1_roll=1, b1_kw=2),
-            dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=1, one_column_sum=0, b1_roll=0, b1_kw=1)]
+            dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=1, one_column_sum=0, b1_roll=0, b1_kw=1),
+            dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=1, one_column_sum=1, stream_prefetch=1),
+            dict(stream_leaf=4, stream_chunk_kb=8, one_column_merge=1, one_column_sum=1, stream_prefetch=1),
+            dict(stream_leaf=1, stream_chunk_kb=64, one_column_merge=1, one_column_sum=1, stream_prefetch=1)]
 
 
 def _nodal_solver(torch, n1, n2, p, gdt, seed=0):
