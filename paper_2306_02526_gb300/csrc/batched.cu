@@ -1779,8 +1779,8 @@ __device__ __forceinline__ void prefetch_share(const Pf &f, int64_t cta, int64_t
 // k_b_gemv_group for the blocks of many instances' applies in one launch.
 template <int TC, class XL, class EP>
 __device__ __forceinline__ void gemv_tile(const BPlan &P, const float *__restrict__ AT, int ld, int64_t str, XL xl, EP ep,
-                                          float *__restrict__ partial, unsigned *__restrict__ tile_count, int bx,
-                                          int by) {
+                                          float *__restrict__ partial, unsigned *__restrict__ tile_count, unsigned bx,
+                                          unsigned by) {
   extern __shared__ __align__(16) float smb[];
   const int ng = bx / P.row_tiles, tile = bx % P.row_tiles;
   const int node0 = ng * P.npc, nn = min(P.npc, P.nodes - node0);
@@ -1893,8 +1893,8 @@ template <int TC, class XL, class EP>
 __global__ void __launch_bounds__(kBT) k_b_gemv(BPlan P, const float *__restrict__ AT, int ld, int64_t str, XL xl,
                                                 EP ep, float *__restrict__ partial, unsigned *__restrict__ tile_count,
                                                 Pf pf) {
+  gemv_tile<TC>(P, AT, ld, str, xl, ep, partial, tile_count, blockIdx.x, blockIdx.y);
   prefetch_share(pf, blockIdx.x + (int64_t)blockIdx.y * gridDim.x, (int64_t)gridDim.x * gridDim.y);
-  gemv_tile<TC>(P, AT, ld, str, xl, ep, partial, tile_count, (int)blockIdx.x, (int)blockIdx.y);
 }
 
 // Sum of the split-K partials in chunk order, four columns per thread.
@@ -1990,8 +1990,8 @@ __device__ __forceinline__ int group_of(const int *block0, int n, int b) {  // b
 template <int TC, class XL, class EP>
 __global__ void __launch_bounds__(kBT) k_b_gemv_group(const __grid_constant__ GemvGroup<XL, EP> G) {
   const int i = group_of(G.block0, G.n, (int)blockIdx.x), local = (int)blockIdx.x - G.block0[i];
-  gemv_tile<TC>(G.P[i], G.AT[i], G.ld[i], G.str[i], G.xl[i], G.ep[i], G.partial[i], nullptr, local % G.gx[i],
-                local / G.gx[i]);
+  gemv_tile<TC>(G.P[i], G.AT[i], G.ld[i], G.str[i], G.xl[i], G.ep[i], G.partial[i], nullptr,
+                (unsigned)(local % G.gx[i]), (unsigned)(local / G.gx[i]));
 }
 
 template <class EP>
