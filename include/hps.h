@@ -449,9 +449,11 @@ enum {
   HPS_OPT_B1_KW = 34,            /* most warps that split K inside a CTA of the one-column merge
                                    applies (1, 2, 4 or 8; fewer: longer contiguous operator rows per
                                    CTA)                                                          */
-  HPS_OPT_STREAM_PREFETCH = 35,  /* 1: the streaming downward leaf apply loads the next leaf's
-                                   boundary values and this leaf's w into registers while it takes
-                                   this leaf's products (no exposed load latency per leaf)          */
+  HPS_OPT_STREAM_PREFETCH = 35,  /* 1 (default): the streaming downward leaf apply loads the next
+                                   leaf's boundary values and this leaf's w into registers while it
+                                   takes this leaf's products, and with one column sums the K slices
+                                   straight into u (two consumer barriers per leaf instead of four);
+                                   0: loads and sums per leaf in separate phases                   */
   HPS_OPT_COUNT = 36
 };
 int hps_batch_set_option(hps_handle *h, int opt, int value);

@@ -1356,6 +1356,28 @@ struct StreamDown {
       u_out(uo, l0 * R + idx, w32[(int64_t)k * q * R + idx] + ys[r * 4 + j]);
     }
   }
+  // One column (R = 1): row r of S u_b is the sum of the K slices' partials (slice order, as the
+  // kernel's own sum), taken straight into u_i = w + S u_b.
+  __device__ void epilogue_sum(int k, const float *part, int KS, int kstride, const float (&w)[kEpi],
+                               const double (&u0)[kEpi], int t0, int nt) const {
+    const int q = g.m * g.m;
+    const int64_t l0 = ((int64_t)origin[2 * k + 1] * g.n1 + origin[2 * k]) * q;
+#pragma unroll
+    for (int s = 0; s < kEpi; ++s) {
+      const int r = t0 + s * nt;
+      if (r < q) {
+        float v = 0.f;
+        for (int k2 = 0; k2 < KS; ++k2) v += part[(size_t)k2 * kstride + 4 * r];
+        const double d = f2d_int(w[s] + v);
+        uo.u[l0 + r] = uo.assign ? d : u0[s] + d;
+      }
+    }
+    for (int r = t0 + kEpi * nt; r < q; r += nt) {
+      float v = 0.f;
+      for (int k2 = 0; k2 < KS; ++k2) v += part[(size_t)k2 * kstride + 4 * r];
+      u_out(uo, l0 + r, w32[(int64_t)k * q + r] + v);
+    }
+  }
   __device__ void prologue(int k, float *xs, float *, int t0, int nt) const {
     const int b = 4 * g.m, ix = origin[2 * k], iy = origin[2 * k + 1];
     for (int i = t0; i < b * 4; i += nt) {
@@ -1450,7 +1472,8 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
       } else {
         role.prologue(k, xs, rs, ct, kStreamConsumers);
       }
-      consumer_sync();
+      // (with pre, a later leaf's right-hand side was stored before the previous leaf's last sync)
+      if (!pre || j == 0) consumer_sync();
       float acc[4][RC];
 #pragma unroll
       for (int e = 0; e < 4; ++e)
@@ -1490,6 +1513,14 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
                       : make_float4(acc[e][0], acc[e][RC > 1 ? 1 : 0], acc[e][RC > 2 ? 2 : 0], acc[e][RC > 3 ? 3 : 0]);
       }
       consumer_sync();
+      if constexpr (kRegs && RC == 1) {
+        if (pre) {  // one column: the slice sums go straight into the outputs (no ys pass)
+          if (j + 1 < nl) role.pre_store(k + (int)gridDim.x, pv, ((j + 1) & 1) ? rs : xs, ct, kStreamConsumers);
+          role.epilogue_sum(k, part, P.KS, 16 * P.QQ, wv, uv, ct, kStreamConsumers);
+          if (consumer_sync_or(failed || *abort_flag)) break;
+          continue;
+        }
+      }
       for (int idx = ct; idx < 16 * P.QQ; idx += kStreamConsumers) {  // slices in order: deterministic
         float v = 0.f;
         for (int k2 = 0; k2 < P.KS; ++k2) v += part[(size_t)k2 * 16 * P.QQ + idx];

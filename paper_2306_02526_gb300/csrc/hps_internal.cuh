@@ -195,7 +195,7 @@ struct Batch {
   bool pdl = false;          // merge applies launched as programmatic dependents of the kernel before
   bool prefetch_next = false;
   bool b1_roll = false;
-  bool stream_prefetch = false;  // streaming downward leaf apply: per-leaf loads ahead of the products  // one-column merge applies: rolling operator loads
+  bool stream_prefetch = true;  // streaming downward leaf apply: per-leaf loads ahead of the products  // one-column merge applies: rolling operator loads
   int b1_kw = 8;         // one-column merge applies: most warps splitting K in a CTA  // merge applies prefetch the next apply's operator into L2
   int eo_threads = 0;        // threads per CTA of the FP64 even-odd leaf kernel (0: 128 for one column per pass, else 256)
   void *ainv_bf = nullptr;       // BF16 trial: their BF16 copy, K-major [leaf][row][round8(q)]

@@ -1,6 +1,7 @@
 """The HBM-bound form of the batched path: one to four right-hand sides with per-node operators
 (nodal coefficients).  Its kernels -- leaf applies streamed by bulk copies through persistent
-CTAs (option stream_leaf), one-column merge applies (one_column_merge) with in-kernel split-K sums
+CTAs (option stream_leaf, with or without the per-leaf register loads and fused one-column sums of
+stream_prefetch), one-column merge applies (one_column_merge) with in-kernel split-K sums
 (one_column_sum) -- and the general kernels they replace must all give the FP64 result after
 refinement (1e-10 relative max-norm) and agree with each other in the FP32 sweep alone."""
 import numpy as np
@@ -29,7 +30,7 @@ VARIANTS = [dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=1, one_colu
             dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=1, one_column_sum=1, b1_roll=1),
             dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=1, one_column_sum=1, b1_roll=1, b1_kw=2),
             dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=1, one_column_sum=0, b1_roll=0, b1_kw=1),
-            dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=1, one_column_sum=1, stream_prefetch=1),
+            dict(stream_leaf=3, stream_chunk_kb=24, one_column_merge=1, one_column_sum=1, stream_prefetch=0),
             dict(stream_leaf=4, stream_chunk_kb=8, one_column_merge=1, one_column_sum=1, stream_prefetch=1),
             dict(stream_leaf=1, stream_chunk_kb=64, one_column_merge=1, one_column_sum=1, stream_prefetch=1)]
 
