@@ -117,6 +117,33 @@ __device__ __forceinline__ void stage_epi_point(const StageEpi &E, int R, int64_
   E.KE[o] = e;
 }
 
+// u[u0 + idx] = (u[u0 + idx] +) val(idx, w[idx]) for idx < n (UOut semantics, exact float-to-double
+// conversion), each thread loading w and u of U points before it stores any: a store to u may
+// alias a later load of u, so a plain loop would wait out one load latency per point.
+template <int U, class Val>
+__device__ __forceinline__ void leaf_u_out(const UOut &uo, int64_t u0, const float *__restrict__ w, int n, Val val) {
+  for (int base = threadIdx.x; base < n; base += U * blockDim.x) {
+    float wv[U];
+    double uv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx < n) {
+        wv[u] = w[idx];
+        uv[u] = uo.assign ? 0.0 : uo.u[u0 + idx];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx < n) {
+        const double d = f2d_int(val(idx, wv[u]));
+        uo.u[u0 + idx] = uo.assign ? d : uv[u] + d;
+      }
+    }
+  }
+}
+
 // Block-wide loop over [0, n): every thread issues U independent loads before it uses any of
 // them (a warp issues in order, so a load-then-store loop would wait out one load latency per
 // element).
@@ -479,8 +506,8 @@ __global__ void __launch_bounds__(kBT) k_b_leaf_down(GridDims g, int R, const in
     __syncthreads();
   }
   // u_i = w + S u_b: the leaf's interior block is contiguous in both vectors
-  for (int idx = threadIdx.x; idx < q * R; idx += blockDim.x)
-    u_out(uo, l0 * R + idx, w32[(int64_t)k * q * R + idx] + (identity ? 0.f : Os[(idx / R) * Rp + idx % R]));
+  leaf_u_out<4>(uo, l0 * R, w32 + (int64_t)k * q * R, q * R,
+                [&](int idx, float w) { return w + (identity ? 0.f : Os[(idx / R) * Rp + idx % R]); });
 }
 
 // ---- leaf apply by fast diagonalization (constant coefficients) -----------------------------
